@@ -1,0 +1,202 @@
+/*
+ * libmmba -- majorization-minimization LiDAR bundle adjustment on one GPU.
+ *
+ * C ABI.  Every entry point returns a ba_status (no exception crosses the
+ * boundary); the message of the last failure on a handle is available from
+ * ba_last_error().  A handle is not thread-safe: all its work is ordered on
+ * the CUDA stream given in its configuration.  Pointers marked "host or
+ * device" are read according to the mem_kind argument (BA_MEM_HOST: ordinary
+ * or pinned host memory; BA_MEM_DEVICE: memory of the handle's device); the
+ * library copies what it keeps, so callers keep ownership of their buffers.
+ *
+ * Problem (Sec. III of the paper, Eq. 1-3): N_T scans with poses
+ * T_j = (R_j, t_j) in SE(3) mapping scan to world coordinates (q = R p + t)
+ * observe N_f planar voxels; observation o = (voxel i, scan j) is the point
+ * cluster (P_f, v_f, N) of the N points of voxel i seen by scan j, in scan
+ * coordinates (Eq. 2).  The cost is c(T) = sum_i lambda_min(cov_i(T)), the
+ * smallest eigenvalue of each voxel's world-point covariance (Eq. 1).  The
+ * optimiser is Levenberg-Marquardt on the MM surrogate of Eq. 3, which
+ * decouples the poses, so each iteration solves one damped 6x6 system per
+ * scan (Algorithm 2: CalRes, CalJH, Solver).
+ *
+ * Data formats
+ *  - pose: 12 doubles, R row-major then t (scan -> world).
+ *  - cluster ("aggregate"), 10 doubles, in one of two forms:
+ *      BA_AGG_RAW_SUMS: P_f = sum p p^T as (xx, xy, xz, yy, yz, zz),
+ *                       v_f = sum p (x, y, z), N;
+ *      BA_AGG_CENTRED:  S = sum (p - m)(p - m)^T as (xx, .., zz),
+ *                       m = v_f / N (x, y, z), N.
+ *    Raw sums are converted once at load: m = v / N and
+ *    S_ab = fma(-v_a, m_b, P_ab).  Raw sums lose digits to cancellation when
+ *    points are far from the scan origin; prefer the centred form.
+ *  - observations are voxel-major CSR: voxel i owns observations
+ *    voxel_offsets[i] .. voxel_offsets[i+1]-1; obs_scan[o] is the scan of o.
+ *  - plane record (9 doubles per voxel): lambda0 <= lambda1 <= lambda2 of the
+ *    voxel covariance, its unit eigenvector u for lambda0, the voxel
+ *    centroid c.  d = u^T c.
+ *  - increment per scan: (dphi, dt); the update is R' = Exp(dphi) R,
+ *    t' = t + dt.
+ */
+#ifndef BA_H
+#define BA_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ba_handle ba_handle;
+
+typedef enum {
+  BA_OK = 0,
+  BA_ERR_INVALID_ARG = 1, /* malformed input; nothing was changed */
+  BA_ERR_OOM = 2,         /* device allocation failed */
+  BA_ERR_CUDA = 3,        /* a CUDA call failed; the handle should be destroyed */
+  BA_ERR_STATE = 4,       /* call not valid in the handle's state (e.g. no data loaded) */
+  BA_ERR_NUMERIC = 5,     /* the cost became NaN or infinite */
+  BA_ERR_TIMEOUT = 6,     /* a bounded device-side wait gave up */
+  BA_ERR_CAPACITY = 7     /* request exceeds a fixed capacity */
+} ba_status;
+
+enum { BA_FP64 = 0, BA_MIXED = 1 };
+enum { BA_HESS_EXACT = 0, BA_HESS_GAUSS_NEWTON = 1 };
+enum { BA_MEM_HOST = 0, BA_MEM_DEVICE = 1 };
+enum { BA_AGG_RAW_SUMS = 0, BA_AGG_CENTRED = 1 };
+
+typedef void* (*ba_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*ba_free_fn)(void* ptr, size_t bytes, void* stream, void* ctx);
+
+typedef struct {
+  int32_t precision;         /* BA_FP64 (default) or BA_MIXED */
+  int32_t max_iters;         /* ba_solve limit (default 200) */
+  double rel_tol;            /* ba_solve stops after an accepted step with
+                                c - c' <= rel_tol * c + abs_tol (default 1e-8) */
+  double abs_tol;            /* default 0 */
+  double mu0;                /* initial Marquardt damping (default 1e-4) */
+  int32_t fixed_scan;        /* scan held fixed to remove the gauge freedom
+                                (default 0; -1 = none) */
+  int32_t hessian_mode;      /* BA_HESS_EXACT (default) or BA_HESS_GAUSS_NEWTON */
+  int32_t max_consec_reject; /* ba_solve stops after this many rejected steps in a row (default 10) */
+  int32_t device;            /* CUDA device ordinal (default 0) */
+  void* cuda_stream;         /* cudaStream_t for all work; NULL = the legacy default stream */
+  ba_alloc_fn alloc;         /* optional device allocator; NULL = cudaMallocAsync on the stream */
+  ba_free_fn free;
+  void* alloc_ctx;
+} ba_config;
+
+typedef struct {
+  double cost;            /* cost at the current (accepted) poses */
+  double cost_before;     /* cost when the call started */
+  double mu;              /* current damping */
+  double nu;              /* current damping growth factor */
+  double last_rho;        /* gain ratio of the last step (NaN if undefined) */
+  double last_pred;       /* predicted reduction of the last step */
+  double last_trial_cost; /* cost at the last trial poses */
+  int32_t iters;          /* LM iterations run since load (accepted or not) */
+  int32_t accepted;       /* accepted steps since load */
+  int32_t consec_reject;  /* rejected steps in a row */
+  int32_t last_accepted;
+  int32_t converged;      /* the last accepted step met the tolerance */
+  int32_t solve_failed;   /* a 6x6 factorisation failed in the last step */
+  int32_t iters_this_call;
+  int32_t reserved;
+} ba_stats;
+
+/* Fill *cfg with the defaults listed above. */
+void ba_config_default(ba_config* cfg);
+
+/* Create a handle on cfg->device.  Allocates nothing on the device yet.
+ * Errors: BA_ERR_INVALID_ARG (bad config), BA_ERR_CUDA. */
+ba_status ba_create(const ba_config* cfg, ba_handle** out);
+
+/* Load a problem given as point clusters (Eq. 2), voxel-major CSR.
+ *   n_scans >= 1, n_voxels >= 1, n_obs >= 1.
+ *   voxel_offsets: n_voxels + 1 int64, voxel_offsets[0] = 0, strictly
+ *     increasing (every voxel has at least one observation), last = n_obs.
+ *   obs_scan: n_obs int32 in [0, n_scans).
+ *   agg: n_obs x 10 doubles (row per observation) in form agg_form; every N
+ *     must be >= 1 and every value finite.
+ *   poses: n_scans x 12 doubles, initial poses; each R orthonormal to 1e-6.
+ * All four arrays live in host or device memory per mem_kind.  The library
+ * validates everything (BA_ERR_INVALID_ARG names the first violation), builds
+ * its device layout (voxel-sorted slices and a scan-major copy, Algorithm 1's
+ * mappers), and evaluates planes, cost, gradient and Hessian at the initial
+ * poses.  Replaces any previously loaded problem.  The LM state (mu, nu,
+ * counters) is reset. */
+ba_status ba_load_observations(ba_handle* h, int32_t n_scans, int64_t n_voxels, int64_t n_obs,
+                               const int64_t* voxel_offsets, const int32_t* obs_scan, const double* agg,
+                               int32_t agg_form, const double* poses, int32_t mem_kind);
+
+/* Same, from raw scan-frame points: observation o owns points
+ * point_offsets[o] .. point_offsets[o+1]-1 (n_obs + 1 int64, at least one
+ * point each), points is n_points x 3 doubles.  Clusters are formed on the
+ * device in centred form (mean, then scatter about the mean). */
+ba_status ba_load_points(ba_handle* h, int32_t n_scans, int64_t n_voxels, int64_t n_obs, const int64_t* voxel_offsets,
+                         const int32_t* obs_scan, const int64_t* point_offsets, const double* points,
+                         const double* poses, int32_t mem_kind);
+
+/* Run exactly n_iters LM iterations (each: per-scan damped solve, retraction,
+ * trial cost evaluation, accept/reject, damping update, and on acceptance the
+ * new planes, gradient and Hessian).  out may be NULL.  Synchronises the
+ * stream only when out is given.  BA_ERR_NUMERIC if the cost became
+ * non-finite.  Iterations after the solve has stopped (see ba_solve) are
+ * still run. */
+ba_status ba_iterate(ba_handle* h, int32_t n_iters, ba_stats* out);
+
+/* Iterate until an accepted step meets the tolerance, max_iters iterations
+ * have run since load, or max_consec_reject steps in a row were rejected.
+ * Synchronises the stream. */
+ba_status ba_solve(ba_handle* h, ba_stats* out);
+
+/* Current poses, n_scans x 12 doubles, to host (synchronises) or device
+ * memory (stream-ordered). */
+ba_status ba_poses(ba_handle* h, double* out, int32_t mem_kind);
+
+/* Cost at the current poses (synchronises). */
+ba_status ba_cost(ba_handle* h, double* out);
+
+/* LM state and counters (synchronises). */
+ba_status ba_get_stats(ba_handle* h, ba_stats* out);
+
+/* Replace the current poses (host or device, n_scans x 12) and the damping
+ * state, then re-evaluate planes, cost, gradient and Hessian there.  With
+ * this a solve can be resumed from saved poses.  mu <= 0 keeps the current
+ * mu; nu <= 0 keeps the current nu. */
+ba_status ba_set_state(ba_handle* h, const double* poses, double mu, double nu, int32_t mem_kind);
+
+/* Plane records (n_voxels x 9 doubles, input voxel order) at the current
+ * poses. */
+ba_status ba_planes(ba_handle* h, double* out, int32_t mem_kind);
+
+/* Surrogate gradient (n_scans x 6) and Hessian (n_scans x 36, row-major,
+ * world frame, rotation block first) at the current poses; either may be
+ * NULL. */
+ba_status ba_gradient(ba_handle* h, double* g, double* H, int32_t mem_kind);
+
+/* Number of kernel launches the handle has issued since creation. */
+int64_t ba_kernel_launches(const ba_handle* h);
+
+/* Release the handle and all its device memory.  NULL is ignored. */
+void ba_destroy(ba_handle* h);
+
+/* Message of the last failure on h (empty if none); for h == NULL, the last
+ * failure of ba_create on this thread. */
+const char* ba_last_error(const ba_handle* h);
+
+const char* ba_status_string(ba_status s);
+
+/* Stateless point-cluster formation (Eq. 2) on the device: for each of n_obs
+ * observations with points point_offsets[o] .. point_offsets[o+1]-1 of
+ * points (n x 3 doubles), write the centred cluster (S, m, N) to
+ * agg_out[10 * o ..].  All pointers are device memory; stream is a
+ * cudaStream_t (NULL = legacy default).  Observations with no point get
+ * N = 0 and zeros.  Errors: BA_ERR_INVALID_ARG (n_obs < 0 or NULL
+ * pointers), BA_ERR_CUDA. */
+ba_status ba_aggregate_points(int64_t n_obs, const int64_t* point_offsets, const double* points, double* agg_out,
+                              void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

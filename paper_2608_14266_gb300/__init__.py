@@ -1,0 +1,248 @@
+"""GB300-native majorization-minimization LiDAR bundle adjustment.
+
+Python binding of libmmba (C ABI in ``include/ba.h``).  The functions below
+carry the C names and only marshal arguments: numpy arrays are passed as host
+memory, CUDA torch tensors as device memory.  Every step of the solver runs in
+the library's CUDA kernels; importing this package never falls back to a CPU
+path (calls raise if the library is not built).
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import (BA_AGG_CENTRED, BA_AGG_RAW_SUMS, BA_FP64, BA_HESS_EXACT, BA_HESS_GAUSS_NEWTON,
+                   BA_MEM_DEVICE, BA_MEM_HOST, BA_MIXED, BaConfig, BaStats)
+
+__all__ = ["BAError", "BundleAdjuster", "ba_config_default", "ba_create", "ba_load_observations",
+           "ba_load_points", "ba_iterate", "ba_solve", "ba_poses", "ba_cost", "ba_get_stats", "ba_set_state",
+           "ba_planes", "ba_gradient", "ba_kernel_launches", "ba_destroy", "ba_last_error",
+           "ba_aggregate_points", "BA_FP64", "BA_MIXED", "BA_HESS_EXACT", "BA_HESS_GAUSS_NEWTON",
+           "BA_AGG_RAW_SUMS", "BA_AGG_CENTRED", "BA_MEM_HOST", "BA_MEM_DEVICE", "BaConfig", "BaStats"]
+
+
+class BAError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_lib.STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+def _check(status: int, handle=None):
+    if status != _lib.BA_OK:
+        msg = _lib.lib().ba_last_error(handle)
+        raise BAError(status, msg.decode() if msg else "")
+
+
+def _is_torch_cuda(x) -> bool:
+    return type(x).__module__.startswith("torch") and getattr(x, "is_cuda", False)
+
+
+class _Arg:
+    """A contiguous host (numpy) or device (torch CUDA) array of a fixed dtype."""
+
+    def __init__(self, x, np_dtype):
+        if _is_torch_cuda(x):
+            import torch
+            tdt = {np.float64: torch.float64, np.int64: torch.int64, np.int32: torch.int32}[np_dtype]
+            if x.dtype != tdt:
+                raise TypeError(f"expected {tdt}, got {x.dtype}")
+            self.keep = x.contiguous()
+            self.ptr = self.keep.data_ptr()
+            self.device = True
+            self.shape = tuple(self.keep.shape)
+        else:
+            self.keep = np.ascontiguousarray(x, dtype=np_dtype)
+            self.ptr = self.keep.ctypes.data if self.keep.size else None
+            self.device = False
+            self.shape = self.keep.shape
+
+
+def _mem_kind(*args: _Arg) -> int:
+    kinds = {a.device for a in args}
+    if len(kinds) != 1:
+        raise ValueError("inputs must be all host (numpy) or all device (CUDA tensors)")
+    return BA_MEM_DEVICE if kinds.pop() else BA_MEM_HOST
+
+
+def ba_config_default(**overrides) -> BaConfig:
+    cfg = BaConfig()
+    _lib.lib().ba_config_default(ctypes.byref(cfg))
+    for k, v in overrides.items():
+        if k == "cuda_stream" and v is not None and not isinstance(v, int):
+            v = v.cuda_stream  # a torch.cuda.Stream
+        setattr(cfg, k, v)
+    return cfg
+
+
+def ba_create(cfg: BaConfig | None = None):
+    h = ctypes.c_void_p()
+    _check(_lib.lib().ba_create(ctypes.byref(cfg) if cfg is not None else None, ctypes.byref(h)), None)
+    return h
+
+
+def ba_load_observations(h, n_scans: int, voxel_offsets, obs_scan, agg, poses, agg_form: int = BA_AGG_CENTRED):
+    vo, os_, ag, po = (_Arg(voxel_offsets, np.int64), _Arg(obs_scan, np.int32), _Arg(agg, np.float64),
+                       _Arg(poses, np.float64))
+    mk = _mem_kind(vo, os_, ag, po)
+    n_voxels = vo.shape[0] - 1
+    n_obs = os_.shape[0]
+    if int(np.prod(ag.shape)) != 10 * n_obs or int(np.prod(po.shape)) != 12 * n_scans:
+        raise ValueError("agg must hold n_obs x 10 and poses n_scans x 12 values")
+    _check(_lib.lib().ba_load_observations(h, n_scans, n_voxels, n_obs, vo.ptr, os_.ptr, ag.ptr, agg_form, po.ptr,
+                                           mk), h)
+
+
+def ba_load_points(h, n_scans: int, voxel_offsets, obs_scan, point_offsets, points, poses):
+    vo, os_, pof, pts, po = (_Arg(voxel_offsets, np.int64), _Arg(obs_scan, np.int32), _Arg(point_offsets, np.int64),
+                             _Arg(points, np.float64), _Arg(poses, np.float64))
+    mk = _mem_kind(vo, os_, pof, pts, po)
+    n_voxels = vo.shape[0] - 1
+    n_obs = os_.shape[0]
+    if pof.shape[0] != n_obs + 1 or int(np.prod(po.shape)) != 12 * n_scans:
+        raise ValueError("point_offsets must hold n_obs + 1 values and poses n_scans x 12")
+    _check(_lib.lib().ba_load_points(h, n_scans, n_voxels, n_obs, vo.ptr, os_.ptr, pof.ptr, pts.ptr, po.ptr, mk), h)
+
+
+def ba_iterate(h, n_iters: int, stats: bool = True):
+    st = BaStats()
+    _check(_lib.lib().ba_iterate(h, n_iters, ctypes.byref(st) if stats else None), h)
+    return st.as_dict() if stats else None
+
+
+def ba_solve(h):
+    st = BaStats()
+    _check(_lib.lib().ba_solve(h, ctypes.byref(st)), h)
+    return st.as_dict()
+
+
+def ba_get_stats(h):
+    st = BaStats()
+    _check(_lib.lib().ba_get_stats(h, ctypes.byref(st)), h)
+    return st.as_dict()
+
+
+def ba_poses(h, n_scans: int | None = None, out=None):
+    """Current poses; into `out` (numpy or CUDA tensor of n_scans x 12 float64) if given."""
+    if out is None:
+        if n_scans is None:
+            raise ValueError("n_scans or out is required")
+        out = np.empty((n_scans, 12))
+    o = _Arg(out, np.float64)
+    if not o.device and o.keep is not out:
+        raise ValueError("out must be a contiguous float64 array")
+    _check(_lib.lib().ba_poses(h, o.ptr, BA_MEM_DEVICE if o.device else BA_MEM_HOST), h)
+    return out
+
+
+def ba_cost(h) -> float:
+    c = ctypes.c_double()
+    _check(_lib.lib().ba_cost(h, ctypes.byref(c)), h)
+    return c.value
+
+
+def ba_set_state(h, poses, mu: float = 0.0, nu: float = 0.0):
+    p = _Arg(poses, np.float64)
+    _check(_lib.lib().ba_set_state(h, p.ptr, float(mu), float(nu), BA_MEM_DEVICE if p.device else BA_MEM_HOST), h)
+
+
+def ba_planes(h, n_voxels: int):
+    out = np.empty((n_voxels, 9))
+    _check(_lib.lib().ba_planes(h, out.ctypes.data, BA_MEM_HOST), h)
+    return out
+
+
+def ba_gradient(h, n_scans: int):
+    g = np.empty((n_scans, 6))
+    H = np.empty((n_scans, 6, 6))
+    _check(_lib.lib().ba_gradient(h, g.ctypes.data, H.ctypes.data, BA_MEM_HOST), h)
+    return g, H
+
+
+def ba_kernel_launches(h) -> int:
+    return int(_lib.lib().ba_kernel_launches(h))
+
+
+def ba_destroy(h):
+    if h:
+        _lib.lib().ba_destroy(h)
+
+
+def ba_last_error(h=None) -> str:
+    m = _lib.lib().ba_last_error(h)
+    return m.decode() if m else ""
+
+
+def ba_aggregate_points(point_offsets, points, out, stream=None):
+    """Centred point clusters on the device (CUDA tensors only)."""
+    pof, pts, o = _Arg(point_offsets, np.int64), _Arg(points, np.float64), _Arg(out, np.float64)
+    if not (pof.device and pts.device and o.device):
+        raise ValueError("ba_aggregate_points takes CUDA tensors")
+    s = None if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
+    _check(_lib.lib().ba_aggregate_points(pof.shape[0] - 1, pof.ptr, pts.ptr, o.ptr, s), None)
+    return out
+
+
+class BundleAdjuster:
+    """Owns one library handle; see include/ba.h for the semantics of each call."""
+
+    def __init__(self, **cfg):
+        self.cfg = ba_config_default(**cfg)
+        self.h = ba_create(self.cfg)
+        self.n_scans = 0
+        self.n_voxels = 0
+
+    def load_observations(self, n_scans, voxel_offsets, obs_scan, agg, poses, agg_form=BA_AGG_CENTRED):
+        ba_load_observations(self.h, n_scans, voxel_offsets, obs_scan, agg, poses, agg_form)
+        self.n_scans, self.n_voxels = n_scans, len(voxel_offsets) - 1
+        return self
+
+    def load_points(self, n_scans, voxel_offsets, obs_scan, point_offsets, points, poses):
+        ba_load_points(self.h, n_scans, voxel_offsets, obs_scan, point_offsets, points, poses)
+        self.n_scans, self.n_voxels = n_scans, len(voxel_offsets) - 1
+        return self
+
+    def iterate(self, n=1, stats=True):
+        return ba_iterate(self.h, n, stats)
+
+    def solve(self):
+        return ba_solve(self.h)
+
+    def poses(self, out=None):
+        return ba_poses(self.h, self.n_scans, out)
+
+    def cost(self):
+        return ba_cost(self.h)
+
+    def stats(self):
+        return ba_get_stats(self.h)
+
+    def set_state(self, poses, mu=0.0, nu=0.0):
+        ba_set_state(self.h, poses, mu, nu)
+
+    def planes(self):
+        return ba_planes(self.h, self.n_voxels)
+
+    def gradient(self):
+        return ba_gradient(self.h, self.n_scans)
+
+    def kernel_launches(self):
+        return ba_kernel_launches(self.h)
+
+    def close(self):
+        if self.h:
+            ba_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,428 @@
+// FP64 iteration kernels: voxel pass (CalRes), scan pass (CalJH), per-scan
+// damped solve + retraction (Solver) and the device-side LM decision
+// (Algorithm 2 and Sec. IV-C of the paper).
+#include "mmba_internal.cuh"
+#include "mmba_kernels.h"
+
+namespace mmba {
+
+// ---------------------------------------------------------------------------
+// Voxel pass: one thread per voxel over the SELL-32 slices.
+//
+// For voxel i with observations o = (i, j): q_o = R_j m_o + t_j is the posed
+// cluster mean; with an anchor a (the first q_o of the voxel) the thread sums
+//   n = sum N_o,  s = sum N_o (q_o - a),  M = sum [R_j S_o R_j^T + N_o (q_o - a)(q_o - a)^T]
+// so that the centroid is c = a + s / n and the world-point covariance of
+// Eq. 1 is A = M / n - (c - a)(c - a)^T.  The anchor keeps the subtraction
+// small (plane-sized instead of scene-sized).  Then lambda_min(A) and its
+// eigenvector give the plane (u, d = u^T c); the voxel's cost is lambda_min.
+// ---------------------------------------------------------------------------
+template <bool kFull>
+__global__ void __launch_bounds__(kVoxelThreads) voxel_pass_f64_kernel(DevLayout L, const double* __restrict__ poses2,
+                                                                      double* __restrict__ planes2,
+                                                                      double* __restrict__ full_out,
+                                                                      double* __restrict__ cost_part,
+                                                                      const DevState* __restrict__ st, int use_trial) {
+  __shared__ double red[kVoxelThreads / 32];
+  if (st->honor_stop && st->stop) return;
+  const int buf = use_trial ? 1 - st->cur : st->cur;
+  const double* __restrict__ poses = poses2 + (int64_t)buf * L.n_scans * 12;
+  double* __restrict__ planes = planes2 + (int64_t)buf * L.n_voxels * kPlaneStride;
+  const int64_t p = (int64_t)blockIdx.x * kVoxelThreads + threadIdx.x;
+  double lam0 = 0.0;
+  if (p < L.n_voxels) {
+    const int64_t s = p >> 5;
+    const int lane = (int)(p & 31);
+    const int len = L.vlen[p];
+    const int64_t base = L.slice_off[s] + lane;
+    const int64_t ne = L.n_elems;
+    double n = 0.0, ax = 0.0, ay = 0.0, az = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
+    double m00 = 0.0, m01 = 0.0, m02 = 0.0, m11 = 0.0, m12 = 0.0, m22 = 0.0;
+    for (int k = 0; k < len; ++k) {
+      const int64_t e = base + (int64_t)k * kSlice;
+      const double* __restrict__ P = poses + 12 * (int64_t)__ldg(L.ve_scan + e);
+      const double S00 = __ldg(L.ve + e), S01 = __ldg(L.ve + ne + e), S02 = __ldg(L.ve + 2 * ne + e);
+      const double S11 = __ldg(L.ve + 3 * ne + e), S12 = __ldg(L.ve + 4 * ne + e), S22 = __ldg(L.ve + 5 * ne + e);
+      const double mx = __ldg(L.ve + 6 * ne + e), my = __ldg(L.ve + 7 * ne + e), mz = __ldg(L.ve + 8 * ne + e);
+      const double N = __ldg(L.ve + 9 * ne + e);
+      const double r00 = P[0], r01 = P[1], r02 = P[2], r10 = P[3], r11 = P[4], r12 = P[5];
+      const double r20 = P[6], r21 = P[7], r22 = P[8];
+      const double qx = fma(r00, mx, fma(r01, my, fma(r02, mz, P[9])));
+      const double qy = fma(r10, mx, fma(r11, my, fma(r12, mz, P[10])));
+      const double qz = fma(r20, mx, fma(r21, my, fma(r22, mz, P[11])));
+      if (k == 0) {
+        ax = qx;
+        ay = qy;
+        az = qz;
+      }
+      const double dx = qx - ax, dy = qy - ay, dz = qz - az;
+      // T = R S (rows), then R S R^T upper triangle
+      const double t00 = fma(r00, S00, fma(r01, S01, r02 * S02));
+      const double t01 = fma(r00, S01, fma(r01, S11, r02 * S12));
+      const double t02 = fma(r00, S02, fma(r01, S12, r02 * S22));
+      const double t10 = fma(r10, S00, fma(r11, S01, r12 * S02));
+      const double t11 = fma(r10, S01, fma(r11, S11, r12 * S12));
+      const double t12 = fma(r10, S02, fma(r11, S12, r12 * S22));
+      const double t20 = fma(r20, S00, fma(r21, S01, r22 * S02));
+      const double t21 = fma(r20, S01, fma(r21, S11, r22 * S12));
+      const double t22 = fma(r20, S02, fma(r21, S12, r22 * S22));
+      const double Nx = N * dx, Ny = N * dy, Nz = N * dz;
+      m00 += fma(t00, r00, fma(t01, r01, fma(t02, r02, Nx * dx)));
+      m01 += fma(t00, r10, fma(t01, r11, fma(t02, r12, Nx * dy)));
+      m02 += fma(t00, r20, fma(t01, r21, fma(t02, r22, Nx * dz)));
+      m11 += fma(t10, r10, fma(t11, r11, fma(t12, r12, Ny * dy)));
+      m12 += fma(t10, r20, fma(t11, r21, fma(t12, r22, Ny * dz)));
+      m22 += fma(t20, r20, fma(t21, r21, fma(t22, r22, Nz * dz)));
+      sx += Nx;
+      sy += Ny;
+      sz += Nz;
+      n += N;
+    }
+    const double inv = 1.0 / n;
+    const double cx = sx * inv, cy = sy * inv, cz = sz * inv;  // centroid - anchor
+    double A[6] = {fma(-cx, cx, m00 * inv), fma(-cx, cy, m01 * inv), fma(-cx, cz, m02 * inv),
+                   fma(-cy, cy, m11 * inv), fma(-cy, cz, m12 * inv), fma(-cz, cz, m22 * inv)};
+    double lam[3], V[9];
+    eig3_sym(A, lam, V);
+    const double ux = V[0], uy = V[1], uz = V[2];
+    const double Cx = ax + cx, Cy = ay + cy, Cz = az + cz;
+    double* pl = planes + p * kPlaneStride;
+    pl[0] = ux;
+    pl[1] = uy;
+    pl[2] = uz;
+    pl[3] = fma(ux, Cx, fma(uy, Cy, uz * Cz));
+    if (kFull) {
+      double* f = full_out + 9 * (int64_t)L.vperm[p];
+      f[0] = lam[0];
+      f[1] = lam[1];
+      f[2] = lam[2];
+      f[3] = ux;
+      f[4] = uy;
+      f[5] = uz;
+      f[6] = Cx;
+      f[7] = Cy;
+      f[8] = Cz;
+    }
+    lam0 = lam[0];
+  }
+  const double tot = block_sum<kVoxelThreads>(lam0, red);
+  if (threadIdx.x == 0) cost_part[blockIdx.x] = tot;
+}
+
+// ---------------------------------------------------------------------------
+// Scan pass: one block per scan over the scan-major copy.
+//
+// Per observation (voxel i, scan j) the surrogate's gradient and Hessian are
+// accumulated in scan coordinates and rotated to the world frame once per
+// scan.  With w = R^T u (normal in scan coordinates), r = w^T m + u^T t - d
+// (residual of the cluster mean) and m' = S w + N r m:
+//   g_rot = m' x w,               g_trans = N r w,
+//   H_rr  = [w]x (S + N m m^T) [w]x^T + (w m'^T + m' w^T)/2 - (w^T m') I,
+//   H_rt  = N (m x w) w^T,        H_tt = N w w^T,
+// all carrying the factor 2 / N_i, which the scan-major copy has folded into
+// S and N.  The world-frame blocks are R (.) R^T.  Gauss-Newton mode drops
+// the (w m'^T + m' w^T)/2 - (w^T m') I term.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kScanThreads) scan_pass_f64_kernel(DevLayout L, const double* __restrict__ poses2,
+                                                                    const double* __restrict__ planes2,
+                                                                    double* __restrict__ gH,
+                                                                    const DevState* __restrict__ st, int force) {
+  __shared__ double red[kScanThreads / 32][kGH];
+  // a rejected step (or an iteration after the solve stopped) leaves g, H unchanged
+  if (!force && !st->scan_pending) return;
+  const int buf = st->cur;
+  const int j = blockIdx.x;
+  const double* __restrict__ P = poses2 + ((int64_t)buf * L.n_scans + j) * 12;
+  const double* __restrict__ planes = planes2 + (int64_t)buf * L.n_voxels * kPlaneStride;
+  const bool gn = st->hess_mode != 0;
+  const double r00 = P[0], r01 = P[1], r02 = P[2], r10 = P[3], r11 = P[4], r12 = P[5], r20 = P[6], r21 = P[7],
+               r22 = P[8];
+  const double tx = P[9], ty = P[10], tz = P[11];
+  double acc[kGH];
+#pragma unroll
+  for (int k = 0; k < kGH; ++k) acc[k] = 0.0;
+  const int64_t lo = L.scan_off[j], hi = L.scan_off[j + 1];
+  const int64_t no = L.n_obs;
+  for (int64_t o = lo + threadIdx.x; o < hi; o += kScanThreads) {
+    const double4_32a pl = *reinterpret_cast<const double4_32a*>(planes + (int64_t)__ldg(L.se_vox + o) * kPlaneStride);
+    const double S00 = __ldg(L.se + o), S01 = __ldg(L.se + no + o), S02 = __ldg(L.se + 2 * no + o);
+    const double S11 = __ldg(L.se + 3 * no + o), S12 = __ldg(L.se + 4 * no + o), S22 = __ldg(L.se + 5 * no + o);
+    const double mx = __ldg(L.se + 6 * no + o), my = __ldg(L.se + 7 * no + o), mz = __ldg(L.se + 8 * no + o);
+    const double N = __ldg(L.se + 9 * no + o);
+    // w = R^T u
+    const double wx = fma(r00, pl.x, fma(r10, pl.y, r20 * pl.z));
+    const double wy = fma(r01, pl.x, fma(r11, pl.y, r21 * pl.z));
+    const double wz = fma(r02, pl.x, fma(r12, pl.y, r22 * pl.z));
+    const double e = fma(pl.x, tx, fma(pl.y, ty, fma(pl.z, tz, -pl.w)));
+    const double r = fma(wx, mx, fma(wy, my, fma(wz, mz, e)));
+    const double Nr = N * r;
+    // S w and m' = S w + N r m
+    const double swx = fma(S00, wx, fma(S01, wy, S02 * wz));
+    const double swy = fma(S01, wx, fma(S11, wy, S12 * wz));
+    const double swz = fma(S02, wx, fma(S12, wy, S22 * wz));
+    const double mpx = fma(Nr, mx, swx), mpy = fma(Nr, my, swy), mpz = fma(Nr, mz, swz);
+    // gradient
+    acc[0] += mpy * wz - mpz * wy;
+    acc[1] += mpz * wx - mpx * wz;
+    acc[2] += mpx * wy - mpy * wx;
+    acc[3] += Nr * wx;
+    acc[4] += Nr * wy;
+    acc[5] += Nr * wz;
+    // P = S + N m m^T
+    const double Nmx = N * mx, Nmy = N * my, Nmz = N * mz;
+    const double p00 = fma(Nmx, mx, S00), p01 = fma(Nmx, my, S01), p02 = fma(Nmx, mz, S02);
+    const double p11 = fma(Nmy, my, S11), p12 = fma(Nmy, mz, S12), p22 = fma(Nmz, mz, S22);
+    // B = [w]x P  (rows: b_r = (w x P_col)...), computed as columns c of P: w x P[:, c]
+    const double b00 = wy * p02 - wz * p01, b10 = wz * p00 - wx * p02, b20 = wx * p01 - wy * p00;
+    const double b01 = wy * p12 - wz * p11, b11 = wz * p01 - wx * p12, b21 = wx * p11 - wy * p01;
+    const double b02 = wy * p22 - wz * p12, b12 = wz * p02 - wx * p22;
+    // C = B [w]x^T : C[r][c] = (B row r) x-dotted -> C[r][c] = sum_k B[r][k] [w]x[c][k]
+    // [w]x rows: (0,-wz,wy), (wz,0,-wx), (-wy,wx,0)
+    double h00 = -wz * b01 + wy * b02;
+    double h01 = wz * b00 - wx * b02;
+    double h02 = -wy * b00 + wx * b01;
+    double h11 = wz * b10 - wx * b12;
+    double h12 = -wy * b10 + wx * b11;
+    double h22 = -wy * b20 + wx * b21;
+    if (!gn) {
+      const double wm = fma(wx, mpx, fma(wy, mpy, wz * mpz));
+      h00 += wx * mpx - wm;
+      h11 += wy * mpy - wm;
+      h22 += wz * mpz - wm;
+      h01 += 0.5 * (wx * mpy + mpx * wy);
+      h02 += 0.5 * (wx * mpz + mpx * wz);
+      h12 += 0.5 * (wy * mpz + mpy * wz);
+    }
+    acc[6] += h00;
+    acc[7] += h01;
+    acc[8] += h02;
+    // rotation-translation block: N (m x w) w^T
+    const double cx = Nmy * wz - Nmz * wy, cy = Nmz * wx - Nmx * wz, cz = Nmx * wy - Nmy * wx;
+    acc[9] += cx * wx;
+    acc[10] += cx * wy;
+    acc[11] += cx * wz;
+    acc[12] += h11;
+    acc[13] += h12;
+    acc[14] += cy * wx;
+    acc[15] += cy * wy;
+    acc[16] += cy * wz;
+    acc[17] += h22;
+    acc[18] += cz * wx;
+    acc[19] += cz * wy;
+    acc[20] += cz * wz;
+    // translation block: N w w^T
+    const double Nwx = N * wx, Nwy = N * wy;
+    acc[21] += Nwx * wx;
+    acc[22] += Nwx * wy;
+    acc[23] += Nwx * wz;
+    acc[24] += Nwy * wy;
+    acc[25] += Nwy * wz;
+    acc[26] += N * wz * wz;
+  }
+  // deterministic block reduction
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 0; k < kGH; ++k) {
+    double v = acc[k];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    if (l == 0) red[w][k] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a[kGH];
+#pragma unroll
+    for (int k = 0; k < kGH; ++k) {
+      double v = 0.0;
+#pragma unroll
+      for (int q = 0; q < kScanThreads / 32; ++q) v += red[q][k];
+      a[k] = v;
+    }
+    // scan-frame 6x6 (upper triangle layout of acc[6..26], row-major over the 6x6)
+    double Hs[6][6];
+    int idx = 6;
+    for (int r = 0; r < 6; ++r)
+      for (int c = r; c < 6; ++c) {
+        Hs[r][c] = a[idx];
+        Hs[c][r] = a[idx];
+        ++idx;
+      }
+    const double R[3][3] = {{r00, r01, r02}, {r10, r11, r12}, {r20, r21, r22}};
+    double* out = gH + (int64_t)j * kGH;
+    for (int r = 0; r < 3; ++r) {
+      out[r] = R[r][0] * a[0] + R[r][1] * a[1] + R[r][2] * a[2];
+      out[3 + r] = R[r][0] * a[3] + R[r][1] * a[4] + R[r][2] * a[5];
+    }
+    // world blocks: R B R^T for each 3x3 block of Hs
+    double Hw[6][6];
+    for (int br = 0; br < 2; ++br)
+      for (int bc = 0; bc < 2; ++bc) {
+        double T[3][3];
+        for (int r = 0; r < 3; ++r)
+          for (int c = 0; c < 3; ++c)
+            T[r][c] = R[r][0] * Hs[3 * br + 0][3 * bc + c] + R[r][1] * Hs[3 * br + 1][3 * bc + c] +
+                      R[r][2] * Hs[3 * br + 2][3 * bc + c];
+        for (int r = 0; r < 3; ++r)
+          for (int c = 0; c < 3; ++c)
+            Hw[3 * br + r][3 * bc + c] = T[r][0] * R[c][0] + T[r][1] * R[c][1] + T[r][2] * R[c][2];
+      }
+    idx = 6;
+    for (int r = 0; r < 6; ++r)
+      for (int c = r; c < 6; ++c) out[idx++] = 0.5 * (Hw[r][c] + Hw[c][r]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Solver: one thread per scan.  A = H + mu diag(H), A delta = -g by LDL^T,
+// trial pose R' = Exp(dphi) R, t' = t + dt, and the scan's share of the
+// predicted reduction -(g^T delta + delta^T H delta / 2).  The fixed scan and
+// scans without observations keep their pose.
+// ---------------------------------------------------------------------------
+__global__ void solve_f64_kernel(DevLayout L, double* __restrict__ poses2, const double* __restrict__ gH,
+                                 double* __restrict__ pred_part, DevState* st) {
+  if (st->honor_stop && st->stop) return;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= L.n_scans) return;
+  const int cur = st->cur;
+  const double* P = poses2 + ((int64_t)cur * L.n_scans + j) * 12;
+  double* Pt = poses2 + ((int64_t)(1 - cur) * L.n_scans + j) * 12;
+  const int64_t nobs = L.scan_off[j + 1] - L.scan_off[j];
+  if (j == L.fixed_scan || nobs == 0) {
+    for (int k = 0; k < 12; ++k) Pt[k] = P[k];
+    pred_part[j] = 0.0;
+    return;
+  }
+  const double* a = gH + (int64_t)j * kGH;
+  double g[6], H[36], A[36], b[6], dlt[6];
+  for (int k = 0; k < 6; ++k) g[k] = a[k];
+  int idx = 6;
+  for (int r = 0; r < 6; ++r)
+    for (int c = r; c < 6; ++c) {
+      H[6 * r + c] = a[idx];
+      H[6 * c + r] = a[idx];
+      ++idx;
+    }
+  const double mu = st->mu;
+  for (int k = 0; k < 36; ++k) A[k] = H[k];
+  for (int k = 0; k < 6; ++k) {
+    A[7 * k] = fma(mu, H[7 * k], H[7 * k]);
+    b[k] = -g[k];
+  }
+  if (!ldlt6_solve(A, b, dlt)) {
+    atomicOr(&st->solve_fail_flag, 1);
+    for (int k = 0; k < 12; ++k) Pt[k] = P[k];
+    pred_part[j] = 0.0;
+    return;
+  }
+  double gd = 0.0, dhd = 0.0;
+  for (int r = 0; r < 6; ++r) {
+    gd = fma(g[r], dlt[r], gd);
+    double hr = 0.0;
+    for (int c = 0; c < 6; ++c) hr = fma(H[6 * r + c], dlt[c], hr);
+    dhd = fma(dlt[r], hr, dhd);
+  }
+  pred_part[j] = -(gd + 0.5 * dhd);
+  double E[9];
+  so3_exp(dlt, E);
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) Pt[3 * r + c] = E[3 * r] * P[c] + E[3 * r + 1] * P[3 + c] + E[3 * r + 2] * P[6 + c];
+  Pt[9] = P[9] + dlt[3];
+  Pt[10] = P[10] + dlt[4];
+  Pt[11] = P[11] + dlt[5];
+}
+
+// ---------------------------------------------------------------------------
+// LM decision (one block): sums the trial cost and the predicted reduction
+// in a fixed order, accepts iff every solve succeeded, the prediction is
+// positive and the cost decreased, and updates the damping (Nielsen's rule:
+// mu *= max(1/3, 1 - (2 rho - 1)^3), nu = 2 on acceptance; mu *= nu, nu *= 2
+// otherwise).  Acceptance flips the current pose/plane buffers.
+// With mode = 1 it only installs the summed cost as the current cost.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kDecideThreads) decide_kernel(const double* __restrict__ cost_part, int64_t n_cost,
+                                                               const double* __restrict__ pred_part, int64_t n_pred,
+                                                               DevState* st, int mode) {
+  __shared__ double red[kDecideThreads / 32];
+  if (mode == 0 && st->honor_stop && st->stop) {
+    if (threadIdx.x == 0) st->scan_pending = 0;
+    return;
+  }
+  double c = 0.0, pr = 0.0;
+  for (int64_t k = threadIdx.x; k < n_cost; k += kDecideThreads) c += cost_part[k];
+  const double csum = block_sum<kDecideThreads>(c, red);
+  if (mode == 0)
+    for (int64_t k = threadIdx.x; k < n_pred; k += kDecideThreads) pr += pred_part[k];
+  const double psum = block_sum<kDecideThreads>(pr, red);
+  if (threadIdx.x != 0) return;
+  if (mode == 1) {
+    st->cost = csum;
+    return;
+  }
+  const int fail = st->solve_fail_flag;
+  const bool accept = !fail && psum > 0.0 && csum < st->cost;
+  st->iters += 1;
+  st->last_pred = psum;
+  st->last_trial_cost = csum;
+  st->solve_failed = fail;
+  st->solve_fail_flag = 0;
+  if (accept) {
+    const double rho = (st->cost - csum) / psum;
+    const double x = 2.0 * rho - 1.0;
+    const double f = 1.0 - x * x * x;
+    st->mu *= f > (1.0 / 3.0) ? f : (1.0 / 3.0);
+    st->nu = 2.0;
+    st->last_rho = rho;
+    st->converged = (st->cost - csum) <= st->rel_tol * st->cost + st->abs_tol;
+    st->cost = csum;
+    st->cur = 1 - st->cur;
+    st->accepted += 1;
+    st->consec_reject = 0;
+  } else {
+    st->mu *= st->nu;
+    st->nu *= 2.0;
+    st->last_rho = (!fail && psum > 0.0) ? (st->cost - csum) / psum : __longlong_as_double(0x7ff8000000000000ll);
+    st->consec_reject += 1;
+  }
+  st->last_accepted = accept;
+  st->scan_pending = accept;
+  if (st->honor_stop &&
+      (st->converged || st->iters >= st->max_iters || st->consec_reject >= st->max_consec_reject))
+    st->stop = 1;
+}
+
+// ---- launchers ---------------------------------------------------------------
+
+cudaError_t launch_voxel_pass_f64(const DevLayout& L, const double* poses2, double* planes2, double* full_out,
+                                  double* cost_part, const DevState* st, int use_trial, cudaStream_t stream) {
+  const int64_t nb = voxel_pass_blocks(L.n_voxels);
+  if (full_out)
+    voxel_pass_f64_kernel<true><<<(unsigned)nb, kVoxelThreads, 0, stream>>>(L, poses2, planes2, full_out, cost_part,
+                                                                            st, use_trial);
+  else
+    voxel_pass_f64_kernel<false><<<(unsigned)nb, kVoxelThreads, 0, stream>>>(L, poses2, planes2, nullptr, cost_part,
+                                                                             st, use_trial);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scan_pass_f64(const DevLayout& L, const double* poses2, const double* planes2, double* gH,
+                                 const DevState* st, int force, cudaStream_t stream) {
+  if (L.n_scans == 0) return cudaSuccess;
+  scan_pass_f64_kernel<<<(unsigned)L.n_scans, kScanThreads, 0, stream>>>(L, poses2, planes2, gH, st, force);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_solve_f64(const DevLayout& L, double* poses2, const double* gH, double* pred_part, DevState* st,
+                             cudaStream_t stream) {
+  const int threads = 128;
+  const int blocks = (L.n_scans + threads - 1) / threads;
+  solve_f64_kernel<<<blocks, threads, 0, stream>>>(L, poses2, gH, pred_part, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_decide(const double* cost_part, int64_t n_cost, const double* pred_part, int64_t n_pred,
+                          DevState* st, int mode, cudaStream_t stream) {
+  decide_kernel<<<1, kDecideThreads, 0, stream>>>(cost_part, n_cost, pred_part, n_pred, st, mode);
+  return cudaGetLastError();
+}
+
+}  // namespace mmba

@@ -1,0 +1,546 @@
+// Device-side layout build (the index mappers of Algorithm 1) and the
+// primitives it uses: a stable LSD radix sort of (key, value) pairs, an
+// exclusive scan, input validation and point-cluster formation (Eq. 2).
+// Everything here runs once per load; none of it is on the per-iteration path.
+#include <cfloat>
+
+#include "mmba_internal.cuh"
+#include "mmba_kernels.h"
+
+namespace mmba {
+
+#define RETURN_IF(err)                   \
+  do {                                   \
+    cudaError_t e_ = (err);              \
+    if (e_ != cudaSuccess) return e_;    \
+  } while (0)
+
+// ============================================================================
+// Exclusive scan of int64 (three-phase: per-tile scan + tile sums, recursive
+// scan of the tile sums, add back).
+// ============================================================================
+constexpr int kScanBlock = 512;
+constexpr int kScanItems = 8;
+constexpr int64_t kScanTile = (int64_t)kScanBlock * kScanItems;
+
+__global__ void __launch_bounds__(kScanBlock) scan_tiles_kernel(int64_t* data, int64_t n, int64_t* tile_sums) {
+  __shared__ int64_t warp_tot[kScanBlock / 32];
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+  int64_t v[kScanItems];
+  int64_t run = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    int64_t x = (base + k < n) ? data[base + k] : 0;
+    v[k] = run;
+    run += x;
+  }
+  // exclusive scan of per-thread totals across the block
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int64_t incl = run;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int64_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) warp_tot[w] = incl;
+  __syncthreads();
+  if (w == 0) {
+    int64_t t = lane < kScanBlock / 32 ? warp_tot[lane] : 0;
+    int64_t ti = t;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int64_t y = __shfl_up_sync(0xffffffffu, ti, o);
+      if (lane >= o) ti += y;
+    }
+    if (lane < kScanBlock / 32) warp_tot[lane] = ti - t;  // exclusive warp prefix
+    if (lane == kScanBlock / 32 - 1 && tile_sums) tile_sums[blockIdx.x] = ti;
+  }
+  __syncthreads();
+  const int64_t pre = warp_tot[w] + incl - run;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k)
+    if (base + k < n) data[base + k] = v[k] + pre;
+}
+
+__global__ void scan_add_kernel(int64_t* data, int64_t n, const int64_t* tile_pre) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) data[i] += tile_pre[i / kScanTile];
+}
+
+int64_t scan_scratch_count(int64_t n) {
+  int64_t total = 0;
+  while (n > kScanTile) {
+    n = (n + kScanTile - 1) / kScanTile;
+    total += n + 1;
+  }
+  return total + 1;
+}
+
+cudaError_t exclusive_scan_i64(int64_t* data, int64_t n, int64_t* scratch, cudaStream_t stream, int64_t* launches) {
+  if (n <= 0) return cudaSuccess;
+  const int64_t tiles = (n + kScanTile - 1) / kScanTile;
+  if (tiles == 1) {
+    scan_tiles_kernel<<<1, kScanBlock, 0, stream>>>(data, n, nullptr);
+    ++*launches;
+    return cudaGetLastError();
+  }
+  int64_t* sums = scratch;
+  scan_tiles_kernel<<<(unsigned)tiles, kScanBlock, 0, stream>>>(data, n, sums);
+  ++*launches;
+  RETURN_IF(cudaGetLastError());
+  RETURN_IF(exclusive_scan_i64(sums, tiles, scratch + tiles + 1, stream, launches));
+  scan_add_kernel<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(data, n, sums);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+// ============================================================================
+// Stable LSD radix sort, 8-bit digits.
+//  pass: (1) per-tile digit histograms -> hist[digit * n_tiles + tile];
+//        (2) exclusive scan of hist (digit-major) -> global start of each
+//            (digit, tile) group;
+//        (3) each tile scatters its elements in input order: the rank of an
+//            element among equal digits of its tile comes from warp match
+//            masks plus per-warp counts, so the sort is stable and
+//            deterministic.
+// ============================================================================
+constexpr int kRadixBlock = 256;
+constexpr int kRadixItems = 16;  // chunks per tile
+constexpr int64_t kRadixTile = (int64_t)kRadixBlock * kRadixItems;
+constexpr int kRadixWarps = kRadixBlock / 32;
+
+__global__ void __launch_bounds__(kRadixBlock) radix_hist_kernel(const uint32_t* keys, int64_t n, int shift,
+                                                                 int64_t* hist, int64_t n_tiles) {
+  __shared__ int cnt[256];
+  cnt[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * kRadixTile;
+  for (int c = 0; c < kRadixItems; ++c) {
+    const int64_t i = base + (int64_t)c * kRadixBlock + threadIdx.x;
+    if (i < n) atomicAdd(&cnt[(keys[i] >> shift) & 255u], 1);
+  }
+  __syncthreads();
+  hist[(int64_t)threadIdx.x * n_tiles + blockIdx.x] = cnt[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(kRadixBlock) radix_scatter_kernel(const uint32_t* keys_in, const uint32_t* vals_in,
+                                                                    uint32_t* keys_out, uint32_t* vals_out, int64_t n,
+                                                                    int shift, const int64_t* hist, int64_t n_tiles) {
+  __shared__ int64_t start[256];      // global position of this tile's next element per digit
+  __shared__ int wcnt[kRadixWarps][256];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  start[tid] = hist[(int64_t)tid * n_tiles + blockIdx.x];
+  const int64_t base = (int64_t)blockIdx.x * kRadixTile;
+  for (int c = 0; c < kRadixItems; ++c) {
+    for (int k = 0; k < kRadixWarps; ++k) wcnt[k][tid] = 0;
+    __syncthreads();
+    const int64_t i = base + (int64_t)c * kRadixBlock + tid;
+    const bool valid = i < n;
+    uint32_t key = 0, val = 0;
+    unsigned d = 256u;  // sentinel digit for invalid lanes
+    if (valid) {
+      key = keys_in[i];
+      val = vals_in[i];
+      d = (key >> shift) & 255u;
+    }
+    const unsigned same = __match_any_sync(0xffffffffu, d);
+    const int rank = __popc(same & ((1u << lane) - 1u));
+    const int leader = __ffs(same) - 1;
+    if (valid && lane == leader) wcnt[w][d] = __popc(same);
+    __syncthreads();
+    // per digit: exclusive prefix over warps (thread tid handles digit tid)
+    {
+      int run = 0;
+      for (int k = 0; k < kRadixWarps; ++k) {
+        int x = wcnt[k][tid];
+        wcnt[k][tid] = run;
+        run += x;
+      }
+      // stash the chunk total for this digit in a register until after scatter
+      __syncthreads();
+      if (valid) {
+        const int64_t dst = start[d] + wcnt[w][d] + rank;
+        keys_out[dst] = key;
+        vals_out[dst] = val;
+      }
+      __syncthreads();
+      start[tid] += run;
+    }
+    __syncthreads();
+  }
+}
+
+int64_t radix_scratch_count(int64_t n) {
+  const int64_t tiles = (n + kRadixTile - 1) / kRadixTile;
+  const int64_t h = 256 * (tiles > 0 ? tiles : 1);
+  return h + scan_scratch_count(h);
+}
+
+cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* tmp_keys, uint32_t* tmp_vals, int64_t n,
+                             int bits, int64_t* scratch, cudaStream_t stream, int64_t* launches) {
+  if (n <= 1 || bits <= 0) return cudaSuccess;
+  const int64_t tiles = (n + kRadixTile - 1) / kRadixTile;
+  int64_t* hist = scratch;
+  int64_t* scan_scratch = scratch + 256 * tiles;
+  uint32_t *ki = keys, *vi = vals, *ko = tmp_keys, *vo = tmp_vals;
+  const int passes = (bits + 7) / 8;
+  for (int p = 0; p < passes; ++p) {
+    radix_hist_kernel<<<(unsigned)tiles, kRadixBlock, 0, stream>>>(ki, n, 8 * p, hist, tiles);
+    ++*launches;
+    RETURN_IF(cudaGetLastError());
+    RETURN_IF(exclusive_scan_i64(hist, 256 * tiles, scan_scratch, stream, launches));
+    radix_scatter_kernel<<<(unsigned)tiles, kRadixBlock, 0, stream>>>(ki, vi, ko, vo, n, 8 * p, hist, tiles);
+    ++*launches;
+    RETURN_IF(cudaGetLastError());
+    uint32_t* t = ki;
+    ki = ko;
+    ko = t;
+    t = vi;
+    vi = vo;
+    vo = t;
+  }
+  if (ki != keys) {
+    RETURN_IF(cudaMemcpyAsync(keys, ki, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, stream));
+    RETURN_IF(cudaMemcpyAsync(vals, vi, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, stream));
+  }
+  return cudaSuccess;
+}
+
+// ============================================================================
+// Validation: the first violating index of each check (atomicMin, so the
+// result does not depend on scheduling).
+// ============================================================================
+__device__ inline void amin(long long* p, long long v) { atomicMin(p, v); }
+
+__global__ void validate_voxels_kernel(LoadInput in, ValidateResult* r) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i > in.n_voxels) return;
+  const int64_t a = in.voxel_off[i];
+  if (i == 0 && a != 0) amin(&r->first_bad_offset, 0);
+  if (i == in.n_voxels) {
+    if (a != in.n_obs) amin(&r->first_bad_offset, i);
+    return;
+  }
+  const int64_t b = in.voxel_off[i + 1];
+  if (b < a || a < 0 || b > in.n_obs) amin(&r->first_bad_offset, i);
+  else if (b == a) amin(&r->first_empty_voxel, i);
+  else {
+    const int64_t len = b - a;
+    atomicMax(&r->max_len, (long long)(len > 0x7fffffff ? 0x7fffffff : len));
+  }
+}
+
+__global__ void validate_obs_kernel(LoadInput in, ValidateResult* r) {
+  const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= in.n_obs) return;
+  const int32_t j = in.obs_scan[o];
+  if (j < 0 || j >= in.n_scans) amin(&r->first_bad_scan, o);
+  const double* a = in.agg + 10 * o;
+  bool fin = true;
+#pragma unroll
+  for (int k = 0; k < 10; ++k) fin = fin && isfinite(a[k]);
+  if (!fin) amin(&r->first_nonfinite_agg, o);
+  if (!(a[9] >= 1.0)) amin(&r->first_bad_count, o);
+}
+
+__global__ void validate_poses_kernel(LoadInput in, ValidateResult* r) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= in.n_scans) return;
+  const double* P = in.poses + 12 * (int64_t)j;
+  bool ok = true;
+  for (int k = 0; k < 12; ++k) ok = ok && isfinite(P[k]);
+  for (int a = 0; a < 3 && ok; ++a)
+    for (int b = 0; b < 3; ++b) {
+      const double d = P[3 * a] * P[3 * b] + P[3 * a + 1] * P[3 * b + 1] + P[3 * a + 2] * P[3 * b + 2];
+      if (fabs(d - (a == b ? 1.0 : 0.0)) > 1e-6) ok = false;
+    }
+  if (ok) {  // proper rotation: det = +1
+    const double det = P[0] * (P[4] * P[8] - P[5] * P[7]) - P[1] * (P[3] * P[8] - P[5] * P[6]) +
+                       P[2] * (P[3] * P[7] - P[4] * P[6]);
+    if (det < 0.0) ok = false;
+  }
+  if (!ok) amin(&r->first_bad_pose, j);
+}
+
+cudaError_t launch_validate(const LoadInput& in, ValidateResult* d_res, cudaStream_t stream, int64_t* launches) {
+  validate_voxels_kernel<<<(unsigned)((in.n_voxels + 1 + 255) / 256), 256, 0, stream>>>(in, d_res);
+  ++*launches;
+  RETURN_IF(cudaGetLastError());
+  if (in.n_obs > 0) {
+    validate_obs_kernel<<<(unsigned)((in.n_obs + 255) / 256), 256, 0, stream>>>(in, d_res);
+    ++*launches;
+    RETURN_IF(cudaGetLastError());
+  }
+  validate_poses_kernel<<<(unsigned)((in.n_scans + 127) / 128), 128, 0, stream>>>(in, d_res);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+// ============================================================================
+// Layout build
+// ============================================================================
+
+// Input cluster -> centred (S, m, N).  Raw sums: m = v / N and
+// S_ab = fma(-v_a, m_b, P_ab).
+__device__ inline void to_centred(const double* a, int form, double out[10]) {
+  if (form == 1) {
+#pragma unroll
+    for (int k = 0; k < 10; ++k) out[k] = a[k];
+    return;
+  }
+  const double n = a[9];
+  const double mx = a[6] / n, my = a[7] / n, mz = a[8] / n;
+  out[0] = fma(-a[6], mx, a[0]);
+  out[1] = fma(-a[6], my, a[1]);
+  out[2] = fma(-a[6], mz, a[2]);
+  out[3] = fma(-a[7], my, a[3]);
+  out[4] = fma(-a[7], mz, a[4]);
+  out[5] = fma(-a[8], mz, a[5]);
+  out[6] = mx;
+  out[7] = my;
+  out[8] = mz;
+  out[9] = n;
+}
+
+// key = (window << len_bits) | (max_len - len): ascending order = windows in
+// input order, longest voxels first inside a window.
+__global__ void voxel_keys_kernel(const int64_t* off, int64_t n_voxels, int max_len, int len_bits, uint32_t* keys,
+                                  uint32_t* vals) {
+  const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= n_voxels) return;
+  const int64_t len = off[v + 1] - off[v];
+  const uint32_t win = (uint32_t)(v / kWindow);
+  keys[v] = (win << len_bits) | (uint32_t)(max_len - len);
+  vals[v] = (uint32_t)v;
+}
+
+__global__ void slice_len_kernel(const int64_t* off, const uint32_t* vperm, int64_t n_voxels, int64_t n_slices,
+                                 int64_t* slice_off, int32_t* vlen, int32_t* vperm_out, int32_t* vrank) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < n_voxels) {
+    const uint32_t v = vperm[p];
+    const int32_t len = (int32_t)(off[v + 1] - off[v]);
+    vlen[p] = len;
+    vperm_out[p] = (int32_t)v;
+    vrank[v] = (int32_t)p;
+    if ((p & 31) == 0) slice_off[p >> 5] = (int64_t)kSlice * len;  // first voxel is the longest of its slice
+  }
+  if (p == 0) slice_off[n_slices] = 0;
+}
+
+__global__ void fill_sell_kernel(LoadInput in, const int32_t* vperm, const int32_t* vlen, const int64_t* slice_off,
+                                 int64_t n_voxels, double* ve, int32_t* ve_scan, int64_t n_elems) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t s = p >> 5;
+  if (s * kSlice >= n_voxels) return;
+  const int lane = (int)(p & 31);
+  const int64_t base = slice_off[s] + lane;
+  const int64_t rows = (slice_off[s + 1] - slice_off[s]) / kSlice;
+  const bool real = p < n_voxels;
+  const int32_t len = real ? vlen[p] : 0;
+  const int64_t o0 = real ? in.voxel_off[vperm[p]] : 0;
+  for (int64_t k = 0; k < rows; ++k) {
+    const int64_t e = base + k * kSlice;
+    double c[10];
+    int32_t scan = 0;
+    if (k < len) {
+      to_centred(in.agg + 10 * (o0 + k), in.agg_form, c);
+      scan = in.obs_scan[o0 + k];
+    } else {
+#pragma unroll
+      for (int q = 0; q < 10; ++q) c[q] = 0.0;
+    }
+#pragma unroll
+    for (int q = 0; q < 10; ++q) ve[q * n_elems + e] = c[q];
+    ve_scan[e] = scan;
+  }
+}
+
+// voxel of every observation, and each voxel's 2 / N_i
+__global__ void obs_voxel_kernel(LoadInput in, int32_t* obs_vox, double* vscale) {
+  const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= in.n_voxels) return;
+  double n = 0.0;
+  for (int64_t o = in.voxel_off[v]; o < in.voxel_off[v + 1]; ++o) {
+    obs_vox[o] = (int32_t)v;
+    n += in.agg[10 * o + 9];
+  }
+  vscale[v] = 2.0 / n;
+}
+
+__global__ void scan_keys_kernel(LoadInput in, uint32_t* keys, uint32_t* vals, int64_t* counts) {
+  const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= in.n_obs) return;
+  keys[o] = (uint32_t)in.obs_scan[o];
+  vals[o] = (uint32_t)o;
+  atomicAdd((unsigned long long*)(counts + in.obs_scan[o]), 1ull);
+}
+
+__global__ void fill_scan_major_kernel(LoadInput in, const uint32_t* order, const int32_t* obs_vox,
+                                       const double* vscale, const int32_t* vrank, double* se, int32_t* se_vox) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= in.n_obs) return;
+  const int64_t o = order[q];
+  const int32_t v = obs_vox[o];
+  double c[10];
+  to_centred(in.agg + 10 * o, in.agg_form, c);
+  const double k = vscale[v];
+#pragma unroll
+  for (int a = 0; a < 6; ++a) c[a] *= k;
+  c[9] *= k;
+  const int64_t n = in.n_obs;
+#pragma unroll
+  for (int a = 0; a < 10; ++a) se[a * n + q] = c[a];
+  se_vox[q] = vrank[v];
+}
+
+static int bit_width(uint64_t x) {
+  int b = 0;
+  while (x) {
+    ++b;
+    x >>= 1;
+  }
+  return b;
+}
+
+cudaError_t build_layout(const LoadInput& in, int max_len, Allocator keep, Allocator temp, LayoutBuffers* out,
+                         cudaStream_t stream, int64_t* launches) {
+  const int64_t nv = in.n_voxels, no = in.n_obs;
+  const int64_t n_slices = (nv + kSlice - 1) / kSlice;
+  const int64_t nsort = nv > no ? nv : no;
+  // temporaries
+  uint32_t* keys = (uint32_t*)temp.fn(temp.self, sizeof(uint32_t) * nsort);
+  uint32_t* vals = (uint32_t*)temp.fn(temp.self, sizeof(uint32_t) * nsort);
+  uint32_t* tk = (uint32_t*)temp.fn(temp.self, sizeof(uint32_t) * nsort);
+  uint32_t* tv = (uint32_t*)temp.fn(temp.self, sizeof(uint32_t) * nsort);
+  int64_t* scratch = (int64_t*)temp.fn(temp.self, sizeof(int64_t) * (radix_scratch_count(nsort) +
+                                                                      scan_scratch_count(n_slices + no + 2)));
+  int32_t* vrank = (int32_t*)temp.fn(temp.self, sizeof(int32_t) * nv);
+  int32_t* obs_vox = (int32_t*)temp.fn(temp.self, sizeof(int32_t) * no);
+  double* vscale = (double*)temp.fn(temp.self, sizeof(double) * nv);
+  // persistent
+  out->slice_off = (int64_t*)keep.fn(keep.self, sizeof(int64_t) * (n_slices + 1));
+  out->vlen = (int32_t*)keep.fn(keep.self, sizeof(int32_t) * nv);
+  out->vperm = (int32_t*)keep.fn(keep.self, sizeof(int32_t) * nv);
+  out->scan_off = (int64_t*)keep.fn(keep.self, sizeof(int64_t) * (in.n_scans + 1));
+  out->se = (double*)keep.fn(keep.self, sizeof(double) * 10 * no);
+  out->se_vox = (int32_t*)keep.fn(keep.self, sizeof(int32_t) * no);
+  if (!keys || !vals || !tk || !tv || !scratch || !vrank || !obs_vox || !vscale || !out->slice_off || !out->vlen ||
+      !out->vperm || !out->scan_off || !out->se || !out->se_vox)
+    return cudaErrorMemoryAllocation;
+
+  // ---- voxel order: length-descending inside windows ----
+  const int len_bits = bit_width((uint64_t)max_len);
+  const int win_bits = bit_width((uint64_t)((nv - 1) / kWindow));
+  if (len_bits + win_bits > 32) return cudaErrorInvalidValue;
+  voxel_keys_kernel<<<(unsigned)((nv + 255) / 256), 256, 0, stream>>>(in.voxel_off, nv, max_len, len_bits, keys,
+                                                                      vals);
+  ++*launches;
+  RETURN_IF(cudaGetLastError());
+  RETURN_IF(radix_sort_pairs(keys, vals, tk, tv, nv, len_bits + win_bits, scratch, stream, launches));
+  slice_len_kernel<<<(unsigned)((nv + 255) / 256), 256, 0, stream>>>(in.voxel_off, vals, nv, n_slices,
+                                                                     out->slice_off, out->vlen, out->vperm, vrank);
+  ++*launches;
+  RETURN_IF(cudaGetLastError());
+  RETURN_IF(exclusive_scan_i64(out->slice_off, n_slices + 1, scratch, stream, launches));
+  int64_t n_elems = 0;
+  RETURN_IF(cudaMemcpyAsync(&n_elems, out->slice_off + n_slices, sizeof(int64_t), cudaMemcpyDeviceToHost, stream));
+  RETURN_IF(cudaStreamSynchronize(stream));
+  out->n_elems = n_elems;
+  out->n_slices = n_slices;
+  out->ve = (double*)keep.fn(keep.self, sizeof(double) * 10 * n_elems);
+  out->ve_scan = (int32_t*)keep.fn(keep.self, sizeof(int32_t) * n_elems);
+  if (!out->ve || !out->ve_scan) return cudaErrorMemoryAllocation;
+  fill_sell_kernel<<<(unsigned)((n_slices * kSlice + 255) / 256), 256, 0, stream>>>(
+      in, out->vperm, out->vlen, out->slice_off, nv, out->ve, out->ve_scan, n_elems);
+  ++*launches;
+  RETURN_IF(cudaGetLastError());
+
+  // ---- scan-major copy ----
+  obs_voxel_kernel<<<(unsigned)((nv + 255) / 256), 256, 0, stream>>>(in, obs_vox, vscale);
+  ++*launches;
+  RETURN_IF(cudaGetLastError());
+  RETURN_IF(cudaMemsetAsync(out->scan_off, 0, sizeof(int64_t) * (in.n_scans + 1), stream));
+  scan_keys_kernel<<<(unsigned)((no + 255) / 256), 256, 0, stream>>>(in, keys, vals, out->scan_off);
+  ++*launches;
+  RETURN_IF(cudaGetLastError());
+  RETURN_IF(radix_sort_pairs(keys, vals, tk, tv, no, bit_width((uint64_t)(in.n_scans - 1)), scratch, stream,
+                             launches));
+  RETURN_IF(exclusive_scan_i64(out->scan_off, in.n_scans + 1, scratch, stream, launches));
+  fill_scan_major_kernel<<<(unsigned)((no + 255) / 256), 256, 0, stream>>>(in, vals, obs_vox, vscale, vrank, out->se,
+                                                                           out->se_vox);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+// ============================================================================
+// Point clusters (Eq. 2) in centred form: one warp per observation; the
+// mean first, then the scatter about the mean (two passes over the points).
+// ============================================================================
+__global__ void aggregate_points_kernel(int64_t n_obs, const int64_t* __restrict__ off,
+                                        const double* __restrict__ pts, double* __restrict__ out) {
+  const int64_t o = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (o >= n_obs) return;
+  const int64_t a = off[o], b = off[o + 1];
+  double sx = 0.0, sy = 0.0, sz = 0.0;
+  for (int64_t k = a + lane; k < b; k += 32) {
+    sx += pts[3 * k];
+    sy += pts[3 * k + 1];
+    sz += pts[3 * k + 2];
+  }
+#pragma unroll
+  for (int w = 16; w > 0; w >>= 1) {
+    sx += __shfl_xor_sync(0xffffffffu, sx, w);
+    sy += __shfl_xor_sync(0xffffffffu, sy, w);
+    sz += __shfl_xor_sync(0xffffffffu, sz, w);
+  }
+  const double n = (double)(b - a);
+  double* r = out + 10 * o;
+  if (b <= a) {
+    if (lane < 10) r[lane] = 0.0;
+    return;
+  }
+  const double mx = sx / n, my = sy / n, mz = sz / n;
+  double c00 = 0.0, c01 = 0.0, c02 = 0.0, c11 = 0.0, c12 = 0.0, c22 = 0.0;
+  for (int64_t k = a + lane; k < b; k += 32) {
+    const double x = pts[3 * k] - mx, y = pts[3 * k + 1] - my, z = pts[3 * k + 2] - mz;
+    c00 = fma(x, x, c00);
+    c01 = fma(x, y, c01);
+    c02 = fma(x, z, c02);
+    c11 = fma(y, y, c11);
+    c12 = fma(y, z, c12);
+    c22 = fma(z, z, c22);
+  }
+#pragma unroll
+  for (int w = 16; w > 0; w >>= 1) {
+    c00 += __shfl_xor_sync(0xffffffffu, c00, w);
+    c01 += __shfl_xor_sync(0xffffffffu, c01, w);
+    c02 += __shfl_xor_sync(0xffffffffu, c02, w);
+    c11 += __shfl_xor_sync(0xffffffffu, c11, w);
+    c12 += __shfl_xor_sync(0xffffffffu, c12, w);
+    c22 += __shfl_xor_sync(0xffffffffu, c22, w);
+  }
+  if (lane == 0) {
+    r[0] = c00;
+    r[1] = c01;
+    r[2] = c02;
+    r[3] = c11;
+    r[4] = c12;
+    r[5] = c22;
+    r[6] = mx;
+    r[7] = my;
+    r[8] = mz;
+    r[9] = n;
+  }
+}
+
+cudaError_t launch_aggregate_points(int64_t n_obs, const int64_t* point_off, const double* points, double* agg_out,
+                                    cudaStream_t stream) {
+  if (n_obs <= 0) return cudaSuccess;
+  const int64_t threads = n_obs * 32;
+  aggregate_points_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, stream>>>(n_obs, point_off, points, agg_out);
+  return cudaGetLastError();
+}
+
+}  // namespace mmba

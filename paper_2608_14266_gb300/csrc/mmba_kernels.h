@@ -1,0 +1,89 @@
+// Host-side declarations of the library's kernel launchers (internal).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "mmba_internal.cuh"
+
+namespace mmba {
+
+constexpr int kVoxelThreads = 128;
+constexpr int kScanThreads = 128;
+constexpr int kDecideThreads = 256;
+
+inline int64_t voxel_pass_blocks(int64_t n_voxels) { return (n_voxels + kVoxelThreads - 1) / kVoxelThreads; }
+
+// ---- iteration (FP64) ----
+cudaError_t launch_voxel_pass_f64(const DevLayout& L, const double* poses2, double* planes2, double* full_out,
+                                  double* cost_part, const DevState* st, int use_trial, cudaStream_t stream);
+cudaError_t launch_scan_pass_f64(const DevLayout& L, const double* poses2, const double* planes2, double* gH,
+                                 const DevState* st, int force, cudaStream_t stream);
+cudaError_t launch_solve_f64(const DevLayout& L, double* poses2, const double* gH, double* pred_part, DevState* st,
+                             cudaStream_t stream);
+cudaError_t launch_decide(const double* cost_part, int64_t n_cost, const double* pred_part, int64_t n_pred,
+                          DevState* st, int mode, cudaStream_t stream);
+
+// ---- layout build / primitives ----
+// Stable LSD radix sort of (key, value) pairs on the low `bits` bits of the
+// keys.  keys/vals are sorted in place; tmp buffers of n entries each and a
+// histogram scratch of radix_scratch_count(n) int64 are supplied by the caller.
+int64_t radix_scratch_count(int64_t n);
+cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* tmp_keys, uint32_t* tmp_vals, int64_t n,
+                             int bits, int64_t* scratch, cudaStream_t stream, int64_t* launches);
+// Exclusive prefix sum of n int64 values in place; scratch of scan_scratch_count(n).
+int64_t scan_scratch_count(int64_t n);
+cudaError_t exclusive_scan_i64(int64_t* data, int64_t n, int64_t* scratch, cudaStream_t stream, int64_t* launches);
+
+struct LoadInput {
+  int32_t n_scans;
+  int64_t n_voxels;
+  int64_t n_obs;
+  const int64_t* voxel_off;  // device
+  const int32_t* obs_scan;   // device
+  const double* agg;         // device, n_obs x 10 (AoS)
+  int32_t agg_form;          // 0 raw sums, 1 centred
+  const double* poses;       // device, n_scans x 12
+};
+
+// validation results (first violating index per check, or -1)
+struct ValidateResult {
+  long long first_bad_offset;
+  long long first_empty_voxel;
+  long long first_bad_scan;
+  long long first_bad_count;
+  long long first_nonfinite_agg;
+  long long first_bad_pose;
+  long long n_obs_seen;
+  long long max_len;
+};
+cudaError_t launch_validate(const LoadInput& in, ValidateResult* d_res, cudaStream_t stream, int64_t* launches);
+
+// Build the device layout; buffers are allocated through the given allocators
+// as sizes become known.
+struct Allocator {
+  void* (*fn)(void* self, size_t bytes);
+  void* self;
+};
+struct LayoutBuffers {
+  int64_t* slice_off;
+  int32_t* vlen;
+  int32_t* vperm;
+  double* ve;
+  int32_t* ve_scan;
+  int64_t* scan_off;
+  double* se;
+  int32_t* se_vox;
+  int64_t n_elems;
+  int64_t n_slices;
+};
+// `keep` allocates the buffers of *out, `temp` the build's temporaries (the
+// caller frees those after the stream has drained).
+cudaError_t build_layout(const LoadInput& in, int max_len, Allocator keep, Allocator temp, LayoutBuffers* out,
+                         cudaStream_t stream, int64_t* launches);
+
+// points -> centred clusters
+cudaError_t launch_aggregate_points(int64_t n_obs, const int64_t* point_off, const double* points, double* agg_out,
+                                    cudaStream_t stream);
+
+}  // namespace mmba
