@@ -177,6 +177,16 @@ ba_status ba_gradient(ba_handle* h, double* g, double* H, int32_t mem_kind);
 /* Number of kernel launches the handle has issued since creation. */
 int64_t ba_kernel_launches(const ba_handle* h);
 
+/* Per-kernel timing.  While enabled, each iteration kernel the handle
+ * launches is bracketed by a pair of CUDA events recorded on the handle's
+ * stream (enabling clears earlier records).  ba_profile_read synchronises
+ * the stream and returns, for one kernel kind, the summed event time in
+ * milliseconds and the number of launches recorded.  A scan pass launched
+ * after a rejected step returns at once and is still counted. */
+enum { BA_KERNEL_VOXEL_PASS = 0, BA_KERNEL_SCAN_PASS = 1, BA_KERNEL_SOLVE = 2, BA_KERNEL_DECIDE = 3 };
+ba_status ba_profile_enable(ba_handle* h, int32_t enable);
+ba_status ba_profile_read(ba_handle* h, int32_t kind, double* total_ms, int64_t* launches);
+
 /* Release the handle and all its device memory.  NULL is ignored. */
 void ba_destroy(ba_handle* h);
 

@@ -19,7 +19,7 @@ from ._lib import (BA_AGG_CENTRED, BA_AGG_RAW_SUMS, BA_FP64, BA_HESS_EXACT, BA_H
 __all__ = ["BAError", "BundleAdjuster", "ba_config_default", "ba_create", "ba_load_observations",
            "ba_load_points", "ba_iterate", "ba_solve", "ba_poses", "ba_cost", "ba_get_stats", "ba_set_state",
            "ba_planes", "ba_gradient", "ba_kernel_launches", "ba_destroy", "ba_last_error",
-           "ba_aggregate_points", "BA_FP64", "BA_MIXED", "BA_HESS_EXACT", "BA_HESS_GAUSS_NEWTON",
+           "ba_aggregate_points", "ba_profile_enable", "ba_profile_read", "BA_FP64", "BA_MIXED", "BA_HESS_EXACT", "BA_HESS_GAUSS_NEWTON",
            "BA_AGG_RAW_SUMS", "BA_AGG_CENTRED", "BA_MEM_HOST", "BA_MEM_DEVICE", "BaConfig", "BaStats"]
 
 
@@ -164,6 +164,20 @@ def ba_kernel_launches(h) -> int:
     return int(_lib.lib().ba_kernel_launches(h))
 
 
+def ba_profile_enable(h, enable: bool = True):
+    _check(_lib.lib().ba_profile_enable(h, int(bool(enable))), h)
+
+
+def ba_profile_read(h) -> dict:
+    """{kernel kind: (total ms, launches)} of the event-timed launches."""
+    out = {}
+    for name, kind in _lib.KERNEL_KINDS.items():
+        ms, n = ctypes.c_double(), ctypes.c_int64()
+        _check(_lib.lib().ba_profile_read(h, kind, ctypes.byref(ms), ctypes.byref(n)), h)
+        out[name] = (ms.value, n.value)
+    return out
+
+
 def ba_destroy(h):
     if h:
         _lib.lib().ba_destroy(h)
@@ -229,6 +243,12 @@ class BundleAdjuster:
 
     def kernel_launches(self):
         return ba_kernel_launches(self.h)
+
+    def profile(self, enable=True):
+        ba_profile_enable(self.h, enable)
+
+    def profile_read(self):
+        return ba_profile_read(self.h)
 
     def close(self):
         if self.h:

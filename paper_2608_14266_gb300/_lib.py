@@ -60,7 +60,11 @@ _SIGNATURES = {
     "ba_last_error": (ctypes.c_char_p, [_P]),
     "ba_status_string": (ctypes.c_char_p, [_I32]),
     "ba_aggregate_points": (_I32, [_I64, _P, _P, _P, _P]),
+    "ba_profile_enable": (_I32, [_P, _I32]),
+    "ba_profile_read": (_I32, [_P, _I32, _P, _P]),
 }
+BA_KERNEL_VOXEL_PASS, BA_KERNEL_SCAN_PASS, BA_KERNEL_SOLVE, BA_KERNEL_DECIDE = 0, 1, 2, 3
+KERNEL_KINDS = {"voxel_pass": 0, "scan_pass": 1, "solve": 2, "decide": 3}
 
 _lock = threading.Lock()
 _lib = None

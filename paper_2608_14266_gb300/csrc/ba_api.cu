@@ -42,6 +42,11 @@ struct ba_handle {
   double* pred_part = nullptr;
   double* cost_part = nullptr;
   int64_t n_cost = 0;
+  // per-kernel event timing
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  std::vector<std::pair<int, size_t>> ev_marks;  // (kind, index of the start event)
 };
 
 namespace {
@@ -197,12 +202,42 @@ ba_status evaluate_current(ba_handle* h) {
   return BA_OK;
 }
 
+// Event pair around one launch when profiling (start recorded here, stop by
+// the returned index + 1 after the launch).
+cudaError_t prof_begin(ba_handle* h, int kind, size_t* idx) {
+  if (!h->profiling) return cudaSuccess;
+  while (h->ev_pool.size() < h->ev_used + 2) {
+    cudaEvent_t e;
+    cudaError_t err = cudaEventCreate(&e);
+    if (err != cudaSuccess) return err;
+    h->ev_pool.push_back(e);
+  }
+  *idx = h->ev_used;
+  h->ev_used += 2;
+  h->ev_marks.push_back({kind, *idx});
+  return cudaEventRecord(h->ev_pool[*idx], h->stream);
+}
+
+cudaError_t prof_end(ba_handle* h, size_t idx) {
+  if (!h->profiling) return cudaSuccess;
+  return cudaEventRecord(h->ev_pool[idx + 1], h->stream);
+}
+
 ba_status launch_iteration(ba_handle* h) {
+  size_t ev = 0;
+  CK(h, prof_begin(h, BA_KERNEL_SOLVE, &ev), "event");
   CK(h, launch_solve_f64(h->L, h->poses2, h->gH, h->pred_part, h->d_state, h->stream), "solve");
+  CK(h, prof_end(h, ev), "event");
+  CK(h, prof_begin(h, BA_KERNEL_VOXEL_PASS, &ev), "event");
   CK(h, launch_voxel_pass_f64(h->L, h->poses2, h->planes2, nullptr, h->cost_part, h->d_state, 1, h->stream),
      "trial voxel pass");
+  CK(h, prof_end(h, ev), "event");
+  CK(h, prof_begin(h, BA_KERNEL_DECIDE, &ev), "event");
   CK(h, launch_decide(h->cost_part, h->n_cost, h->pred_part, h->L.n_scans, h->d_state, 0, h->stream), "decide");
+  CK(h, prof_end(h, ev), "event");
+  CK(h, prof_begin(h, BA_KERNEL_SCAN_PASS, &ev), "event");
   CK(h, launch_scan_pass_f64(h->L, h->poses2, h->planes2, h->gH, h->d_state, 0, h->stream), "scan pass");
+  CK(h, prof_end(h, ev), "event");
   h->launches += 4;
   return BA_OK;
 }
@@ -627,12 +662,42 @@ ba_status ba_gradient(ba_handle* h, double* g, double* H, int32_t mem_kind) {
 
 int64_t ba_kernel_launches(const ba_handle* h) { return h ? h->launches : 0; }
 
+ba_status ba_profile_enable(ba_handle* h, int32_t enable) {
+  if (!h) return BA_ERR_INVALID_ARG;
+  DeviceGuard g(h->cfg.device);
+  CK(h, cudaStreamSynchronize(h->stream), "synchronize");
+  h->profiling = enable != 0;
+  h->ev_used = 0;
+  h->ev_marks.clear();
+  return BA_OK;
+}
+
+ba_status ba_profile_read(ba_handle* h, int32_t kind, double* total_ms, int64_t* launches) {
+  if (!h) return BA_ERR_INVALID_ARG;
+  if (!total_ms || !launches) return fail(h, BA_ERR_INVALID_ARG, "NULL output");
+  DeviceGuard g(h->cfg.device);
+  CK(h, cudaStreamSynchronize(h->stream), "synchronize");
+  double tot = 0.0;
+  int64_t n = 0;
+  for (auto& m : h->ev_marks) {
+    if (m.first != kind) continue;
+    float ms = 0.0f;
+    CK(h, cudaEventElapsedTime(&ms, h->ev_pool[m.second], h->ev_pool[m.second + 1]), "event time");
+    tot += ms;
+    ++n;
+  }
+  *total_ms = tot;
+  *launches = n;
+  return BA_OK;
+}
+
 void ba_destroy(ba_handle* h) {
   if (!h) return;
   DeviceGuard g(h->cfg.device);
   cudaStreamSynchronize(h->stream);
   release_problem(h);
   cudaStreamSynchronize(h->stream);
+  for (auto e : h->ev_pool) cudaEventDestroy(e);
   delete h;
 }
 

@@ -232,9 +232,17 @@ def test_edge_cases_match_oracle(mm, case):
         assert ba.cost() == pytest.approx(lm.cost, rel=COST_TOL)
         _compare_planes(ba.planes(), lm.planes)
         for k in range(5):
+            c_prev = lm.cost
             st = ba.iterate(1)
             acc = lm.step()
-            assert bool(st["last_accepted"]) == acc, k
+            if bool(st["last_accepted"]) != acc:
+                # only a near-tie may be decided differently: the cost change is
+                # within the rounding budget (e.g. a single scan, whose pose does
+                # not change the cost at all); then continue from the oracle state
+                assert abs(lm.st.last_trial_cost - c_prev) <= COST_TOL * c_prev, k
+                assert st["last_trial_cost"] == pytest.approx(lm.st.last_trial_cost, rel=COST_TOL)
+                ba.set_state(lm.poses, lm.mu, lm.nu)
+                continue
             assert st["cost"] == pytest.approx(lm.cost, rel=COST_TOL)
             r, t = pose_errors(ba.poses(), lm.poses)
             assert r < ROT_TOL and t < TRANS_TOL, (k, r, t)
