@@ -57,6 +57,8 @@ def _args():
     ap.add_argument("--e2e-jobs", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU budget of the oracle baseline")
+    ap.add_argument("--shrink", type=float, default=1.0,
+                    help="scale scans, voxels and area by this factor at equal density (profiling runs)")
     return ap.parse_args()
 
 
@@ -134,6 +136,16 @@ def _gpu_id(torch, dev: int) -> str | None:
 # ---------------------------------------------------------------------------
 # inputs
 # ---------------------------------------------------------------------------
+def scene_params(scenegen, args, rank):
+    p = scenegen.config(args.workload, rep=rank)
+    if args.shrink != 1.0:
+        f = args.shrink
+        side = math.sqrt(f)
+        p = scenegen.replace(p, n_scans=max(1, int(p.n_scans * f)), n_voxels=max(1, int(p.n_voxels * f)),
+                             box=(p.box[0] * side, p.box[1] * side, p.box[2]))
+    return p
+
+
 def device_clusters(scene, torch, mm, chunk_obs: int = 1 << 20):
     """Raw points generated on the host in chunks, clustered on the GPU."""
     import numpy as np
@@ -222,7 +234,7 @@ def run_reference(args):
     if rank != 0:
         return
     import scenegen
-    scene = scenegen.make_scene(scenegen.config(args.workload, rep=0))
+    scene = scenegen.make_scene(scene_params(scenegen, args, 0))
     budget = 150.0
     ips, dt, sample = time_oracle(scene, args.steps, args.warmup, budget)
     line = {
@@ -259,7 +271,7 @@ def run_ours(args):
         if dist is not None:
             dist.barrier()
 
-    scene = scenegen.make_scene(scenegen.config(args.workload, rep=rank))
+    scene = scenegen.make_scene(scene_params(scenegen, args, rank))
     dev = torch.device("cuda", local)
     agg = device_clusters(scene, torch, mm)
     voxel_off = torch.from_numpy(scene.voxel_off).to(dev)
@@ -295,6 +307,7 @@ def run_ours(args):
     clocks = ClockSampler(_gpu_id(torch, local))
     time.sleep(0.3)
     ba.profile(True)
+    torch.cuda.nvtx.range_push("timed")
     t_wall0 = time.time()
     for (e0, e1), n in zip(ev, reps):
         barrier()
@@ -307,6 +320,7 @@ def run_ours(args):
         reset()
     torch.cuda.synchronize()
     t_wall1 = time.time()
+    torch.cuda.nvtx.range_pop()
     launches = ba.kernel_launches() - launches0 - len(reps) * 4  # minus the untimed resets
     prof = ba.profile_read()
     ba.profile(False)
@@ -339,12 +353,12 @@ def run_ours(args):
             job.iterate(S, stats=False)
             job.poses(out=out_h.numpy())
         e2e_times.append(time.perf_counter() - t0)
-    e2e_s = sum(e2e_times)
+    e2e_s = sum(e2e_times) if e2e_times else float("nan")
     if dist is not None:
         t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
-    e2e_value = world * S * args.e2e_jobs / e2e_s
+    e2e_value = world * S * args.e2e_jobs / e2e_s if e2e_times else None
     h2d = agg_h.numel() * 8 + vo_h.numel() * 8 + os_h.numel() * 4 + p0_h.numel() * 8
     d2h = out_h.numel() * 8
 
