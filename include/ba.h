@@ -206,6 +206,42 @@ const char* ba_status_string(ba_status s);
 ba_status ba_aggregate_points(int64_t n_obs, const int64_t* point_offsets, const double* points, double* agg_out,
                               void* stream);
 
+/* Allocation-free cost evaluation.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory when they need
+ * a cost -- a mapping loop on a vehicle under a fixed memory budget, where
+ * cudaMalloc/cudaFree may synchronise the device and stall the loop, or an
+ * application whose own allocator already holds the GPU's memory.
+ *
+ * Computes c(T) = sum_i lambda_min(cov_i) (Eq. 1) for the caller's
+ * voxel-major CSR clusters in centred form (n_obs x 10 doubles), poses
+ * (n_scans x 12) and offsets/scan indices, all device memory of the calling
+ * thread's current device, and writes the cost to *cost_out (device) and,
+ * if lambda0_out is not NULL, each voxel's smallest eigenvalue (device,
+ * n_voxels doubles).  Work is ordered on `stream` (a cudaStream_t, NULL =
+ * legacy default); the call does not synchronise.
+ *
+ * It calls no cudaMalloc, cudaFree or allocating library routine.  Its
+ * scratch (block partials and an error word) is one file-scope device array
+ * of (BA_NOALLOC_MAX_VOXELS / 128 + 32) doubles (512 KB plus 256 bytes)
+ * that every GPU loading the library holds until the process exits.  The
+ * first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call shares the array and it keeps the last call's contents; each
+ * call overwrites the partials it sums and re-arms the error word itself, so
+ * nothing has to be cleared by the caller -- but calls whose work overlaps
+ * on the GPU (different streams, or several host threads) race on it and
+ * must be serialised by the caller.
+ *
+ * Errors: BA_ERR_INVALID_ARG (sizes below 1, n_obs < n_voxels, NULL
+ * pointers), BA_ERR_CAPACITY (n_voxels > BA_NOALLOC_MAX_VOXELS),
+ * BA_ERR_CUDA (no current device or a launch failed).  Offsets or scan
+ * indices found out of range on the device leave the cost NaN (and the
+ * voxel's lambda0 NaN); inputs are otherwise not validated. */
+#define BA_NOALLOC_MAX_VOXELS 8388608
+ba_status ba_eval_cost_noalloc(int32_t n_scans, int64_t n_voxels, int64_t n_obs, const int64_t* voxel_offsets,
+                               const int32_t* obs_scan, const double* agg_centred, const double* poses,
+                               double* cost_out, double* lambda0_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -198,6 +198,31 @@ def ba_aggregate_points(point_offsets, points, out, stream=None):
     return out
 
 
+def ba_eval_cost_noalloc(n_scans, voxel_offsets, obs_scan, agg_centred, poses, cost_out, lambda0_out=None,
+                         stream=None):
+    """Cost of the given poses without any device allocation by the library.
+
+    For callers that cannot allocate device memory at that point (a fixed
+    memory budget in an on-vehicle mapping loop, or a host whose allocator
+    already holds the GPU memory).  Every argument is a CUDA tensor owned by
+    the caller; the result lands in cost_out (one float64) and optionally
+    lambda0_out (n_voxels float64).  Asynchronous on `stream`; calls that
+    overlap on the GPU share the library's scratch and must be serialised.
+    """
+    args = [_Arg(voxel_offsets, np.int64), _Arg(obs_scan, np.int32), _Arg(agg_centred, np.float64),
+            _Arg(poses, np.float64), _Arg(cost_out, np.float64)]
+    lam = _Arg(lambda0_out, np.float64) if lambda0_out is not None else None
+    if not all(a.device for a in args) or (lam is not None and not lam.device):
+        raise ValueError("ba_eval_cost_noalloc takes CUDA tensors")
+    vo, os_, ag, po, co = args
+    s = None if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
+    status = _lib.lib().ba_eval_cost_noalloc(int(n_scans), vo.shape[0] - 1, os_.shape[0], vo.ptr, os_.ptr, ag.ptr,
+                                            po.ptr, co.ptr, lam.ptr if lam is not None else None, s)
+    if status != _lib.BA_OK:
+        raise BAError(status, "ba_eval_cost_noalloc")
+    return cost_out
+
+
 class BundleAdjuster:
     """Owns one library handle; see include/ba.h for the semantics of each call."""
 

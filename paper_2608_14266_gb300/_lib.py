@@ -62,7 +62,9 @@ _SIGNATURES = {
     "ba_aggregate_points": (_I32, [_I64, _P, _P, _P, _P]),
     "ba_profile_enable": (_I32, [_P, _I32]),
     "ba_profile_read": (_I32, [_P, _I32, _P, _P]),
+    "ba_eval_cost_noalloc": (_I32, [_I32, _I64, _I64, _P, _P, _P, _P, _P, _P, _P]),
 }
+BA_NOALLOC_MAX_VOXELS = 8388608
 BA_KERNEL_VOXEL_PASS, BA_KERNEL_SCAN_PASS, BA_KERNEL_SOLVE, BA_KERNEL_DECIDE = 0, 1, 2, 3
 KERNEL_KINDS = {"voxel_pass": 0, "scan_pass": 1, "solve": 2, "decide": 3}
 
