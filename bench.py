@@ -44,12 +44,16 @@ VOXEL_PASS_FLOP_PER_OBS = 121
 # bytes one voxel-pass launch must move per observation slot: 10 doubles + a
 # 4-byte scan index (the pose table and per-voxel outputs are small)
 VOXEL_PASS_BYTES_PER_ELEM = 84
+# mixed voxel pass: per observation 10 floats + a 4-byte scan index; per voxel
+# the anchor and frame (12 floats), its length (4 B), the plane written (16 B)
+MIXED_VOXEL_BYTES_PER_OBS = 44
+MIXED_VOXEL_BYTES_PER_VOXEL = 68
 
 
 def _args():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=300, help="timed LM iterations per rank")
+    ap.add_argument("--steps", type=int, default=3000, help="timed LM iterations per rank")
     ap.add_argument("--warmup", type=int, default=30, help="untimed warm-up iterations")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["city", "mid", "tiny"], default="city")
@@ -57,6 +61,9 @@ def _args():
     ap.add_argument("--e2e-jobs", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU budget of the oracle baseline")
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--fp64-steps", type=int, default=60,
+                    help="iterations of the plain FP64 path timed for comparison (0: skip)")
     ap.add_argument("--shrink", type=float, default=1.0,
                     help="scale scans, voxels and area by this factor at equal density (profiling runs)")
     return ap.parse_args()
@@ -165,9 +172,10 @@ def device_clusters(scene, torch, mm, chunk_obs: int = 1 << 20):
     return agg
 
 
-def kernel_source_hash() -> str:
+def kernel_source_hash(kernel: str = "voxel_pass_f64") -> str:
     h = hashlib.sha256()
-    for f in ("iter_f64.cu", "mmba_internal.cuh"):
+    main = "iter_mixed.cu" if "mixed" in kernel else "iter_f64.cu"
+    for f in (main, "mmba_internal.cuh"):
         with open(os.path.join(ROOT, "paper_2608_14266_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -181,7 +189,7 @@ def recorded_traffic(workload: str, kernel: str):
         with open(path) as f:
             rec = json.load(f)
         e = rec.get(kernel, {})
-        if e.get("source_hash") == kernel_source_hash() and workload in e.get("bytes_per_launch", {}):
+        if e.get("source_hash") == kernel_source_hash(kernel) and workload in e.get("bytes_per_launch", {}):
             return e["bytes_per_launch"][workload]
     except (OSError, ValueError):
         pass
@@ -249,8 +257,94 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def measure(mm, torch, scene, dev_inputs, precision, steps, warmup, S, barrier, local, profile=True):
+    """Times `steps` LM iterations (solves of S iterations from the initial
+    poses, state reset outside the timed region) with CUDA events on the
+    library's stream; returns the timing, the kernel breakdown and clocks."""
+    voxel_off, obs_scan, agg, pose0 = dev_inputs
+    stream = torch.cuda.current_stream()
+    ba = mm.BundleAdjuster(cuda_stream=stream, precision=precision)
+    ba.load_observations(scene.n_scans, voxel_off, obs_scan, agg, pose0)
+    cfg = ba.cfg
+
+    def reset():
+        ba.set_state(pose0, cfg.mu0, 2.0)
+
+    done = 0
+    while done < warmup:
+        n = min(S, warmup - done)
+        ba.iterate(n, stats=False)
+        done += n
+        reset()
+    torch.cuda.synchronize()
+    reps = []
+    left = steps
+    while left > 0:
+        reps.append(min(S, left))
+        left -= reps[-1]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in reps]
+    accepted = 0
+    launches = 0
+    acc0 = ba.stats()["accepted"]
+    clocks = ClockSampler(_gpu_id(torch, local)) if profile else None
+    if profile:
+        time.sleep(0.3)
+    ba.profile(profile)
+    torch.cuda.nvtx.range_push("timed")
+    t_wall0 = time.time()
+    for (e0, e1), n in zip(ev, reps):
+        barrier()
+        torch.cuda.synchronize()
+        l0 = ba.kernel_launches()
+        e0.record(stream)
+        ba.iterate(n, stats=False)
+        e1.record(stream)
+        launches += ba.kernel_launches() - l0
+        torch.cuda.synchronize()
+        acc1 = ba.stats()["accepted"]
+        accepted += acc1 - acc0
+        reset()
+        acc0 = ba.stats()["accepted"]
+    torch.cuda.synchronize()
+    t_wall1 = time.time()
+    torch.cuda.nvtx.range_pop()
+    prof = ba.profile_read() if profile else None
+    ba.profile(False)
+    clk = clocks.stop(t_wall0, t_wall1) if clocks else None
+    ms = sum(e0.elapsed_time(e1) for e0, e1 in ev)
+    ba.close()
+    return {"ms": ms, "accepted": accepted, "launches": launches, "prof": prof, "clocks": clk}
+
+
+def roofline_for(precision, scene, prof, workload):
+    vp_ms, vp_n = prof["voxel_pass"]
+    vp_avg_s = vp_ms / max(1, vp_n) / 1000.0
+    if precision == "fp64":
+        flops = VOXEL_PASS_FLOP_PER_OBS * scene.n_obs
+        achieved = flops / vp_avg_s / 1e12
+        return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": recorded_traffic(workload, "voxel_pass_f64"),
+                "kernel": "voxel_pass_f64", "avg_launch_ms": vp_avg_s * 1000.0,
+                "peak_source": "nominal GB300 FP64 rate (the measured peaks have no FP64 entry)",
+                "flop_per_launch": flops,
+                "hbm_view_gbs": VOXEL_PASS_BYTES_PER_ELEM * scene.n_obs / vp_avg_s / 1e9}
+    peak, src = hbm_peak()
+    nbytes = MIXED_VOXEL_BYTES_PER_OBS * scene.n_obs + MIXED_VOXEL_BYTES_PER_VOXEL * scene.n_voxels
+    achieved = nbytes / vp_avg_s / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": recorded_traffic(workload, "voxel_pass_mixed"), "kernel": "voxel_pass_mixed",
+            "avg_launch_ms": vp_avg_s * 1000.0, "peak_source": src, "bytes_per_launch": nbytes}
+
+
+def hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, ValueError, KeyError):
+        return HBM_PEAK_FALLBACK, "fallback 6.8 TB/s"
+
+
 def run_ours(args):
-    import numpy as np
     import torch
 
     import __graft_entry__
@@ -271,67 +365,30 @@ def run_ours(args):
         if dist is not None:
             dist.barrier()
 
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=torch.device("cuda", local))
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
     scene = scenegen.make_scene(scene_params(scenegen, args, rank))
     dev = torch.device("cuda", local)
     agg = device_clusters(scene, torch, mm)
-    voxel_off = torch.from_numpy(scene.voxel_off).to(dev)
-    obs_scan = torch.from_numpy(scene.obs_scan).to(dev)
-    pose0 = torch.from_numpy(scene.pose_init).to(dev)
-    stream = torch.cuda.current_stream()
-    ba = mm.BundleAdjuster(cuda_stream=stream)
-    ba.load_observations(scene.n_scans, voxel_off, obs_scan, agg, pose0)
-    cfg = ba.cfg
+    inputs = (torch.from_numpy(scene.voxel_off).to(dev), torch.from_numpy(scene.obs_scan).to(dev), agg,
+              torch.from_numpy(scene.pose_init).to(dev))
     S = args.iters_per_solve
-
-    def reset():
-        ba.set_state(pose0, cfg.mu0, 2.0)
-
-    # warm-up
-    done = 0
-    while done < args.warmup:
-        n = min(S, args.warmup - done)
-        ba.iterate(n, stats=False)
-        done += n
-        reset()
-    torch.cuda.synchronize()
-
-    # timed region: K iterations as solves of S iterations from the initial state
-    reps = []
-    left = args.steps
-    while left > 0:
-        reps.append(min(S, left))
-        left -= reps[-1]
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in reps]
-    launches0 = ba.kernel_launches()
-    accepted = 0
-    clocks = ClockSampler(_gpu_id(torch, local))
-    time.sleep(0.3)
-    ba.profile(True)
-    torch.cuda.nvtx.range_push("timed")
-    t_wall0 = time.time()
-    for (e0, e1), n in zip(ev, reps):
-        barrier()
-        torch.cuda.synchronize()
-        e0.record(stream)
-        ba.iterate(n, stats=False)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        accepted += ba.stats()["accepted"]
-        reset()
-    torch.cuda.synchronize()
-    t_wall1 = time.time()
-    torch.cuda.nvtx.range_pop()
-    launches = ba.kernel_launches() - launches0 - len(reps) * 4  # minus the untimed resets
-    prof = ba.profile_read()
-    ba.profile(False)
-    clk = clocks.stop(t_wall0, t_wall1)
-    ms = sum(e0.elapsed_time(e1) for e0, e1 in ev)
-    if dist is not None:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    total_iters = args.steps * world
-    value = total_iters / (ms / 1000.0)
+    prec = mm.BA_MIXED if args.precision == "mixed" else mm.BA_FP64
+    res = measure(mm, torch, scene, inputs, prec, args.steps, args.warmup, S, barrier, local)
+    ms = max_over_ranks(res["ms"])
+    value = args.steps * world / (ms / 1000.0)
+    fp64 = None
+    if args.precision == "mixed" and args.fp64_steps > 0:
+        r64 = measure(mm, torch, scene, inputs, mm.BA_FP64, args.fp64_steps, min(args.warmup, S), S, barrier,
+                      local, profile=False)
+        ms64 = max_over_ranks(r64["ms"])
+        fp64 = {"value": args.fp64_steps * world / (ms64 / 1000.0), "unit": "iter/s", "steps": args.fp64_steps,
+                "ms_per_step": ms64 / args.fp64_steps, "accepted_iters": r64["accepted"]}
 
     # end to end through the public API with pinned host buffers
     agg_h = torch.empty(agg.shape, dtype=torch.float64).pin_memory()
@@ -340,41 +397,27 @@ def run_ours(args):
     os_h = torch.from_numpy(scene.obs_scan).pin_memory()
     p0_h = torch.from_numpy(scene.pose_init).pin_memory()
     out_h = torch.empty((scene.n_scans, 12), dtype=torch.float64).pin_memory()
-    del agg
-    ba.close()
+    del agg, inputs
     torch.cuda.empty_cache()
+    stream = torch.cuda.current_stream()
     e2e_times = []
     for _ in range(args.e2e_jobs):
         barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        with mm.BundleAdjuster(cuda_stream=stream) as job:
+        with mm.BundleAdjuster(cuda_stream=stream, precision=prec) as job:
             job.load_observations(scene.n_scans, vo_h.numpy(), os_h.numpy(), agg_h.numpy(), p0_h.numpy())
             job.iterate(S, stats=False)
             job.poses(out=out_h.numpy())
         e2e_times.append(time.perf_counter() - t0)
-    e2e_s = sum(e2e_times) if e2e_times else float("nan")
-    if dist is not None:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = world * S * args.e2e_jobs / e2e_s if e2e_times else None
+    e2e_value = None
+    if e2e_times:
+        e2e_value = world * S * args.e2e_jobs / max_over_ranks(sum(e2e_times))
     h2d = agg_h.numel() * 8 + vo_h.numel() * 8 + os_h.numel() * 4 + p0_h.numel() * 8
     d2h = out_h.numel() * 8
 
-    # roofline of the dominant kernel (the voxel pass)
-    vp_ms, vp_n = prof["voxel_pass"]
-    vp_avg_s = vp_ms / max(1, vp_n) / 1000.0
-    flops = VOXEL_PASS_FLOP_PER_OBS * scene.n_obs
-    achieved = flops / vp_avg_s / 1e12
-    total_prof = sum(v[0] for v in prof.values())
-    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": recorded_traffic(args.workload, "voxel_pass_f64"),
-                "kernel": "voxel_pass_f64", "avg_launch_ms": vp_avg_s * 1000.0,
-                "peak_source": "nominal GB300 FP64 rate (no FP64 entry in the measured peaks)",
-                "flop_per_launch": flops,
-                "hbm_view_gbs": VOXEL_PASS_BYTES_PER_ELEM * scene.n_obs / vp_avg_s / 1e9}
-
+    prof = res["prof"]
+    roofline = roofline_for(args.precision, scene, prof, args.workload)
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -383,23 +426,25 @@ def run_ours(args):
     if not args.no_cpu_baseline and world == 1:
         ips, dt, sample = time_oracle(scene, 2, 1, args.cpu_seconds)
         cpu = {"value": ips, "unit": "iter/s", "cores": 1, "kind": "oracle", "sample": sample}
+    per_obs = 44 if args.precision == "mixed" else 84
     line = {
         "metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded scene generator; points clustered on GPU)",
+        "vs_baseline": None, "dtype": "f32" if args.precision == "mixed" else "f64",
+        "data": "synthetic (seeded scene generator; points clustered on GPU)",
         "config": {"workload": WORKLOAD_TEXT[args.workload], "n_scans": scene.n_scans,
-                   "n_voxels": scene.n_voxels, "n_obs": scene.n_obs, "precision": "fp64",
-                   "iters_per_solve": S, "accepted_iters": accepted,
-                   "l2": "inputs larger than L2 (clusters %.2f GB)" % (scene.n_obs * 84 / 1e9),
+                   "n_voxels": scene.n_voxels, "n_obs": scene.n_obs, "precision": args.precision,
+                   "iters_per_solve": S, "accepted_iters": res["accepted"],
+                   "l2": "inputs larger than L2 (per-pass clusters %.2f GB)" % (scene.n_obs * per_obs / 1e9),
                    "parallelism": f"{world} independent job(s), one per GPU"},
         "plane_obs_per_s": value * scene.n_obs,
-        "clocks": clk,
+        "fp64_path": fp64,
+        "clocks": res["clocks"],
         "e2e": {"value": e2e_value, "unit": "iter/s", "h2d_bytes_per_step": h2d / S, "d2h_bytes_per_step": d2h / S,
                 "jobs": args.e2e_jobs, "scope": "ba_load_observations (pinned host clusters) + "
                                                 f"{S} iterations + ba_poses to host, per job"},
-        "gpu_launches": int(launches),
+        "gpu_launches": int(res["launches"]),
         "kernel_ms": {k: {"total_ms": v[0], "launches": v[1]} for k, v in prof.items()},
-        "kernel_event_ms_total": total_prof,
         "roofline": roofline,
         "cpu_baseline": cpu,
     }

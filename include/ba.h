@@ -196,6 +196,46 @@ const char* ba_last_error(const ba_handle* h);
 
 const char* ba_status_string(ba_status s);
 
+/* ---- Batched execution --------------------------------------------------
+ * A batch steps many independent problems (jobs) together: every iteration
+ * launches each kernel kind once over a device-side table of the jobs, so
+ * hundreds of small jobs cost a handful of launches per iteration instead of
+ * four each.  Jobs are ordinary handles, loaded and read with the calls
+ * above; each keeps its own LM state (damping, acceptance, stopping rule of
+ * its own configuration) and its results are bit-identical to running it
+ * alone, because every kernel block belongs to exactly one job and runs the
+ * same work it would run in the job's own launch.  Jobs in one batch must be
+ * on the same device and of the same precision.  The batch's iterations are
+ * captured once into a CUDA graph per (membership, iteration count) and
+ * replayed.  A handle may be in one batch at a time; while it is, its own
+ * iterate/solve calls must not overlap the batch's work (the batch calls
+ * return only after the GPU has finished). */
+typedef struct ba_batch ba_batch;
+
+/* stream: cudaStream_t for the batch's work (NULL = legacy default). */
+ba_status ba_batch_create(void* stream, ba_batch** out);
+/* Add a loaded handle (BA_ERR_STATE if not loaded, BA_ERR_INVALID_ARG on a
+ * device or precision mismatch or if already present).  The batch does not
+ * own the handle: remove it before destroying it. */
+ba_status ba_batch_add(ba_batch* b, ba_handle* job);
+ba_status ba_batch_remove(ba_batch* b, ba_handle* job);
+int32_t ba_batch_size(const ba_batch* b);
+/* Exactly n_iters LM iterations of every job (ba_iterate semantics). */
+ba_status ba_batch_iterate(ba_batch* b, int32_t n_iters);
+/* Iterate every job until it stops by its own configuration (ba_solve
+ * semantics), in rounds of `chunk` iterations; a stopped job's blocks exit
+ * at once.  *n_active_out (may be NULL) receives the number of jobs still
+ * running when the call returns (0 unless max_rounds ran out;
+ * max_rounds <= 0 means no limit). */
+ba_status ba_batch_solve(ba_batch* b, int32_t chunk, int32_t max_rounds, int32_t* n_active_out);
+/* Per-job stop flags after ba_batch_solve rounds: done_out[k] = 1 if the
+ * k-th added job has stopped (n = ba_batch_size entries, host memory). */
+ba_status ba_batch_done(ba_batch* b, int32_t* done_out);
+void ba_batch_destroy(ba_batch* b);
+const char* ba_batch_last_error(const ba_batch* b);
+/* Kernel launches issued by the batch's iterations (4 per iteration). */
+int64_t ba_batch_kernel_launches(const ba_batch* b);
+
 /* Stateless point-cluster formation (Eq. 2) on the device: for each of n_obs
  * observations with points point_offsets[o] .. point_offsets[o+1]-1 of
  * points (n x 3 doubles), write the centred cluster (S, m, N) to

@@ -16,7 +16,7 @@ from . import _lib
 from ._lib import (BA_AGG_CENTRED, BA_AGG_RAW_SUMS, BA_FP64, BA_HESS_EXACT, BA_HESS_GAUSS_NEWTON,
                    BA_MEM_DEVICE, BA_MEM_HOST, BA_MIXED, BaConfig, BaStats)
 
-__all__ = ["BAError", "BundleAdjuster", "ba_config_default", "ba_create", "ba_load_observations",
+__all__ = ["BAError", "Batch", "BundleAdjuster", "ba_config_default", "ba_create", "ba_load_observations",
            "ba_load_points", "ba_iterate", "ba_solve", "ba_poses", "ba_cost", "ba_get_stats", "ba_set_state",
            "ba_planes", "ba_gradient", "ba_kernel_launches", "ba_destroy", "ba_last_error",
            "ba_aggregate_points", "ba_profile_enable", "ba_profile_read", "BA_FP64", "BA_MIXED", "BA_HESS_EXACT", "BA_HESS_GAUSS_NEWTON",
@@ -221,6 +221,66 @@ def ba_eval_cost_noalloc(n_scans, voxel_offsets, obs_scan, agg_centred, poses, c
     if status != _lib.BA_OK:
         raise BAError(status, "ba_eval_cost_noalloc")
     return cost_out
+
+
+class Batch:
+    """Steps many loaded BundleAdjuster jobs together (ba_batch_* in include/ba.h)."""
+
+    def __init__(self, stream=None):
+        s = None if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
+        self.b = ctypes.c_void_p()
+        _check(_lib.lib().ba_batch_create(s, ctypes.byref(self.b)), None)
+        self.jobs = []
+
+    def _check(self, status):
+        if status != _lib.BA_OK:
+            raise BAError(status, (_lib.lib().ba_batch_last_error(self.b) or b"").decode())
+
+    def add(self, job: "BundleAdjuster"):
+        self._check(_lib.lib().ba_batch_add(self.b, job.h))
+        self.jobs.append(job)
+
+    def remove(self, job: "BundleAdjuster"):
+        self._check(_lib.lib().ba_batch_remove(self.b, job.h))
+        self.jobs.remove(job)
+
+    def __len__(self):
+        return int(_lib.lib().ba_batch_size(self.b))
+
+    def iterate(self, n: int):
+        self._check(_lib.lib().ba_batch_iterate(self.b, int(n)))
+
+    def solve(self, chunk: int = 8, max_rounds: int = 0) -> int:
+        active = ctypes.c_int32()
+        self._check(_lib.lib().ba_batch_solve(self.b, int(chunk), int(max_rounds), ctypes.byref(active)))
+        return active.value
+
+    def done(self) -> np.ndarray:
+        out = np.zeros(len(self.jobs), dtype=np.int32)
+        if len(self.jobs):
+            self._check(_lib.lib().ba_batch_done(self.b, out.ctypes.data))
+        return out.astype(bool)
+
+    def kernel_launches(self) -> int:
+        return int(_lib.lib().ba_batch_kernel_launches(self.b))
+
+    def close(self):
+        if self.b:
+            _lib.lib().ba_batch_destroy(self.b)
+            self.b = None
+            self.jobs = []
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class BundleAdjuster:

@@ -63,6 +63,16 @@ _SIGNATURES = {
     "ba_profile_enable": (_I32, [_P, _I32]),
     "ba_profile_read": (_I32, [_P, _I32, _P, _P]),
     "ba_eval_cost_noalloc": (_I32, [_I32, _I64, _I64, _P, _P, _P, _P, _P, _P, _P]),
+    "ba_batch_create": (_I32, [_P, _P]),
+    "ba_batch_add": (_I32, [_P, _P]),
+    "ba_batch_remove": (_I32, [_P, _P]),
+    "ba_batch_size": (_I32, [_P]),
+    "ba_batch_iterate": (_I32, [_P, _I32]),
+    "ba_batch_solve": (_I32, [_P, _I32, _I32, _P]),
+    "ba_batch_done": (_I32, [_P, _P]),
+    "ba_batch_destroy": (None, [_P]),
+    "ba_batch_last_error": (ctypes.c_char_p, [_P]),
+    "ba_batch_kernel_launches": (_I64, [_P]),
 }
 BA_NOALLOC_MAX_VOXELS = 8388608
 BA_KERNEL_VOXEL_PASS, BA_KERNEL_SCAN_PASS, BA_KERNEL_SOLVE, BA_KERNEL_DECIDE = 0, 1, 2, 3

@@ -30,11 +30,17 @@ struct ba_handle {
   ba_config cfg;
   cudaStream_t stream = nullptr;
   std::string err;
+  ba_batch* batch = nullptr;  // batch this handle is in, if any
   int64_t launches = 0;
   bool loaded = false;
   std::vector<DevAlloc> keep;  // problem buffers
   std::vector<DevAlloc> temp;  // freed at the end of a load
   DevLayout L{};
+  bool mixed = false;
+  LoadInput in_keep{};   // device copies of the inputs (mixed precision re-anchors from them)
+  LayoutBuffers lb{};
+  MixedBuffers mb{};
+  DevMixed X{};
   DevState* d_state = nullptr;
   double* poses2 = nullptr;
   double* planes2 = nullptr;
@@ -125,6 +131,10 @@ void release_problem(ba_handle* h) {
   free_list(h, h->keep);
   h->loaded = false;
   h->L = DevLayout{};
+  h->lb = LayoutBuffers{};
+  h->mb = MixedBuffers{};
+  h->X = DevMixed{};
+  h->in_keep = LoadInput{};
   h->d_state = nullptr;
   h->poses2 = h->planes2 = h->gH = h->pred_part = h->cost_part = nullptr;
 }
@@ -193,11 +203,20 @@ void fill_stats(const DevState& s, double cost_before, int32_t iters_call, ba_st
 }
 
 // Evaluate planes, cost, gradient and Hessian at the current poses.
+cudaError_t voxel_pass(ba_handle* h, double* full, int use_trial) {
+  if (h->mixed) return launch_voxel_pass_mixed(h->L, h->X, full, h->cost_part, h->d_state, use_trial, h->stream);
+  return launch_voxel_pass_f64(h->L, h->poses2, h->planes2, full, h->cost_part, h->d_state, use_trial, h->stream);
+}
+
+cudaError_t scan_pass(ba_handle* h, int force) {
+  if (h->mixed) return launch_scan_pass_mixed(h->L, h->X, h->poses2, h->gH, h->d_state, force, h->stream);
+  return launch_scan_pass_f64(h->L, h->poses2, h->planes2, h->gH, h->d_state, force, h->stream);
+}
+
 ba_status evaluate_current(ba_handle* h) {
-  CK(h, launch_voxel_pass_f64(h->L, h->poses2, h->planes2, nullptr, h->cost_part, h->d_state, 0, h->stream),
-     "voxel pass");
+  CK(h, voxel_pass(h, nullptr, 0), "voxel pass");
   CK(h, launch_decide(h->cost_part, h->n_cost, h->pred_part, h->L.n_scans, h->d_state, 1, h->stream), "cost sum");
-  CK(h, launch_scan_pass_f64(h->L, h->poses2, h->planes2, h->gH, h->d_state, 1, h->stream), "scan pass");
+  CK(h, scan_pass(h, 1), "scan pass");
   h->launches += 3;
   return BA_OK;
 }
@@ -226,17 +245,18 @@ cudaError_t prof_end(ba_handle* h, size_t idx) {
 ba_status launch_iteration(ba_handle* h) {
   size_t ev = 0;
   CK(h, prof_begin(h, BA_KERNEL_SOLVE, &ev), "event");
-  CK(h, launch_solve_f64(h->L, h->poses2, h->gH, h->pred_part, h->d_state, h->stream), "solve");
+  CK(h, launch_solve_f64(h->L, h->poses2, h->gH, h->pred_part, h->d_state, h->mixed ? h->mb.sref : nullptr,
+                         h->mixed ? h->mb.stab2 : nullptr, h->stream),
+     "solve");
   CK(h, prof_end(h, ev), "event");
   CK(h, prof_begin(h, BA_KERNEL_VOXEL_PASS, &ev), "event");
-  CK(h, launch_voxel_pass_f64(h->L, h->poses2, h->planes2, nullptr, h->cost_part, h->d_state, 1, h->stream),
-     "trial voxel pass");
+  CK(h, voxel_pass(h, nullptr, 1), "trial voxel pass");
   CK(h, prof_end(h, ev), "event");
   CK(h, prof_begin(h, BA_KERNEL_DECIDE, &ev), "event");
   CK(h, launch_decide(h->cost_part, h->n_cost, h->pred_part, h->L.n_scans, h->d_state, 0, h->stream), "decide");
   CK(h, prof_end(h, ev), "event");
   CK(h, prof_begin(h, BA_KERNEL_SCAN_PASS, &ev), "event");
-  CK(h, launch_scan_pass_f64(h->L, h->poses2, h->planes2, h->gH, h->d_state, 0, h->stream), "scan pass");
+  CK(h, scan_pass(h, 0), "scan pass");
   CK(h, prof_end(h, ev), "event");
   h->launches += 4;
   return BA_OK;
@@ -312,11 +332,30 @@ ba_status load_impl(ba_handle* h, int32_t n_scans, int64_t n_voxels, int64_t n_o
   if (res.max_len >= (1ll << 24))
     return fail(h, BA_ERR_CAPACITY, "a voxel has %lld observations (limit 2^24)", res.max_len);
 
+  // mixed precision keeps device copies of the inputs: the FP32 copies are
+  // rebuilt from them when the reference poses change (ba_set_state)
+  if (h->mixed) {
+    int64_t* vo = (int64_t*)dev_alloc(h, h->keep, sizeof(int64_t) * ((size_t)n_voxels + 1));
+    int32_t* os = (int32_t*)dev_alloc(h, h->keep, sizeof(int32_t) * (size_t)n_obs);
+    double* ag = (double*)dev_alloc(h, h->keep, sizeof(double) * 10 * (size_t)n_obs);
+    if (!vo || !os || !ag) return fail(h, BA_ERR_OOM, "input copies: out of device memory");
+    CK(h, cudaMemcpyAsync(vo, in.voxel_off, sizeof(int64_t) * (n_voxels + 1), cudaMemcpyDeviceToDevice, h->stream),
+       "copy offsets");
+    CK(h, cudaMemcpyAsync(os, in.obs_scan, sizeof(int32_t) * n_obs, cudaMemcpyDeviceToDevice, h->stream),
+       "copy obs_scan");
+    CK(h, cudaMemcpyAsync(ag, in.agg, sizeof(double) * 10 * n_obs, cudaMemcpyDeviceToDevice, h->stream),
+       "copy clusters");
+    in.voxel_off = vo;
+    in.obs_scan = os;
+    in.agg = ag;
+  }
+
   // layout
-  LayoutBuffers lb{};
+  LayoutBuffers& lb = h->lb;
+  lb = LayoutBuffers{};
   Allocator keep{keep_fn, h}, temp{temp_fn, h};
   {
-    cudaError_t be = build_layout(in, (int)res.max_len, keep, temp, &lb, h->stream, &h->launches);
+    cudaError_t be = build_layout(in, (int)res.max_len, !h->mixed, keep, temp, &lb, h->stream, &h->launches);
     if (be != cudaSuccess) return cuda_fail(h, be, "layout build");
   }
   DevLayout& L = h->L;
@@ -348,6 +387,28 @@ ba_status load_impl(ba_handle* h, int32_t n_scans, int64_t n_voxels, int64_t n_o
   CK(h, cudaMemcpyAsync(h->poses2, in.poses, sizeof(double) * 12 * (size_t)n_scans, cudaMemcpyDeviceToDevice,
                         h->stream),
      "initial poses");
+  if (h->mixed) {
+    MixedBuffers& mb = h->mb;
+    mb.ve32 = (float*)dev_alloc(h, h->keep, sizeof(float) * kVe32 * (size_t)lb.n_elems);
+    mb.vstate = (float4*)dev_alloc(h, h->keep, sizeof(float4) * 2 * (size_t)n_voxels);
+    mb.se32 = (float*)dev_alloc(h, h->keep, sizeof(float) * 10 * (size_t)n_obs);
+    mb.vanchor = (float4*)dev_alloc(h, h->keep, sizeof(float4) * (size_t)n_voxels);
+    mb.sref = (double*)dev_alloc(h, h->keep, sizeof(double) * 12 * (size_t)n_scans);
+    mb.stab2 = (float*)dev_alloc(h, h->keep, sizeof(float) * 2 * kTab * (size_t)n_scans);
+    mb.planes32_2 = (float*)dev_alloc(h, h->keep, sizeof(float) * 2 * 4 * (size_t)n_voxels);
+    if (!mb.ve32 || !mb.vstate || !mb.se32 || !mb.vanchor || !mb.sref || !mb.stab2 || !mb.planes32_2)
+      return fail(h, BA_ERR_OOM, "mixed-precision copies: out of device memory");
+    h->in_keep = in;
+    h->in_keep.poses = nullptr;
+    CK(h, build_mixed(in, lb, h->poses2, mb, h->stream, &h->launches), "mixed-precision copies");
+    h->X.ve32 = mb.ve32;
+    h->X.vstate = mb.vstate;
+    h->X.se32 = mb.se32;
+    h->X.vanchor = mb.vanchor;
+    h->X.sref = mb.sref;
+    h->X.stab2 = mb.stab2;
+    h->X.planes32_2 = mb.planes32_2;
+  }
   DevState s0{};
   s0.mu = h->cfg.mu0;
   s0.nu = 2.0;
@@ -409,8 +470,6 @@ ba_status ba_create(const ba_config* cfg, ba_handle** out) {
     ba_config_default(&c);
   if (c.precision != BA_FP64 && c.precision != BA_MIXED)
     return fail(nullptr, BA_ERR_INVALID_ARG, "precision must be BA_FP64 or BA_MIXED");
-  if (c.precision == BA_MIXED)
-    return fail(nullptr, BA_ERR_INVALID_ARG, "BA_MIXED is not available in this build");
   if (c.hessian_mode != BA_HESS_EXACT && c.hessian_mode != BA_HESS_GAUSS_NEWTON)
     return fail(nullptr, BA_ERR_INVALID_ARG, "bad hessian_mode");
   if (!(c.mu0 > 0.0) || !(c.rel_tol >= 0.0) || !(c.abs_tol >= 0.0) || c.max_iters < 0 || c.max_consec_reject < 1)
@@ -424,6 +483,7 @@ ba_status ba_create(const ba_config* cfg, ba_handle** out) {
   ba_handle* h = new ba_handle();
   h->cfg = c;
   h->stream = (cudaStream_t)c.cuda_stream;
+  h->mixed = c.precision == BA_MIXED;
   *out = h;
   return BA_OK;
 }
@@ -439,6 +499,7 @@ ba_status ba_load_observations(ba_handle* h, int32_t n_scans, int64_t n_voxels, 
   if (!voxel_offsets || !obs_scan || !agg || !poses) return fail(h, BA_ERR_INVALID_ARG, "NULL input pointer");
   if (agg_form != BA_AGG_RAW_SUMS && agg_form != BA_AGG_CENTRED) return fail(h, BA_ERR_INVALID_ARG, "bad agg_form");
   if (h->cfg.fixed_scan >= n_scans) return fail(h, BA_ERR_INVALID_ARG, "fixed_scan out of range");
+  if (h->batch) return fail(h, BA_ERR_STATE, "the handle is in a batch: remove it before loading");
   release_problem(h);
   s = load_impl(h, n_scans, n_voxels, n_obs, voxel_offsets, obs_scan, agg, agg_form, poses, mem_kind, mem_kind);
   if (s != BA_OK) {
@@ -459,6 +520,7 @@ ba_status ba_load_points(ba_handle* h, int32_t n_scans, int64_t n_voxels, int64_
   if (!voxel_offsets || !obs_scan || !point_offsets || !points || !poses)
     return fail(h, BA_ERR_INVALID_ARG, "NULL input pointer");
   if (h->cfg.fixed_scan >= n_scans) return fail(h, BA_ERR_INVALID_ARG, "fixed_scan out of range");
+  if (h->batch) return fail(h, BA_ERR_STATE, "the handle is in a batch: remove it before loading");
   release_problem(h);
   // point offsets: need the point count to stage the points
   std::vector<int64_t> hoff;
@@ -609,6 +671,8 @@ ba_status ba_set_state(ba_handle* h, const double* poses, double mu, double nu, 
   CK(h, cudaMemcpyAsync(h->poses2, poses, sizeof(double) * n,
                         mem_kind == BA_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, h->stream),
      "copy poses");
+  // mixed precision: the new poses become the reference poses (re-anchoring)
+  if (h->mixed) CK(h, build_mixed(h->in_keep, h->lb, h->poses2, h->mb, h->stream, &h->launches), "re-anchor");
   if ((s = evaluate_current(h)) != BA_OK) return s;
   DevState st;
   if ((s = read_state(h, &st)) != BA_OK) return s;
@@ -625,8 +689,7 @@ ba_status ba_planes(ba_handle* h, double* out, int32_t mem_kind) {
   const size_t bytes = sizeof(double) * 9 * (size_t)h->L.n_voxels;
   double* full = mem_kind == BA_MEM_DEVICE ? out : (double*)dev_alloc(h, h->temp, bytes);
   if (!full) return fail(h, BA_ERR_OOM, "plane buffer: out of device memory");
-  CK(h, launch_voxel_pass_f64(h->L, h->poses2, h->planes2, full, h->cost_part, h->d_state, 0, h->stream),
-     "voxel pass");
+  CK(h, voxel_pass(h, full, 0), "voxel pass");
   ++h->launches;
   if (mem_kind == BA_MEM_HOST) {
     CK(h, cudaMemcpyAsync(out, full, bytes, cudaMemcpyDeviceToHost, h->stream), "read planes");
@@ -693,6 +756,7 @@ ba_status ba_profile_read(ba_handle* h, int32_t kind, double* total_ms, int64_t*
 
 void ba_destroy(ba_handle* h) {
   if (!h) return;
+  if (h->batch) ba_batch_remove(h->batch, h);
   DeviceGuard g(h->cfg.device);
   cudaStreamSynchronize(h->stream);
   release_problem(h);
@@ -726,5 +790,328 @@ ba_status ba_aggregate_points(int64_t n_obs, const int64_t* point_offsets, const
   if (e != cudaSuccess) return fail(nullptr, BA_ERR_CUDA, "aggregate points: %s", cudaGetErrorString(e));
   return BA_OK;
 }
+
+}  // extern "C"
+
+// ============================================================================
+// Batched execution
+// ============================================================================
+
+struct ba_batch {
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int device = -1;
+  bool mixed = false;
+  std::vector<ba_handle*> jobs;
+  std::string err;
+  int64_t launches = 0;
+  // device job table
+  JobView* d_jobs = nullptr;
+  int64_t* d_prefix = nullptr;  // vblk | sblk | oblk, (n + 1) each
+  int32_t* d_done = nullptr;    // per job stop flag, then the active count
+  size_t cap = 0;
+  int64_t n_vblk = 0, n_sblk = 0, n_oblk = 0;
+  bool dirty = true;
+  // captured iterations
+  cudaGraphExec_t graph = nullptr;
+  int graph_iters = -1;
+};
+
+namespace {
+
+ba_status bfail(ba_batch* b, ba_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  b->err = buf;
+  return s;
+}
+
+#define BCK(b, call, what)                                                                        \
+  do {                                                                                            \
+    cudaError_t e_ = (call);                                                                      \
+    if (e_ != cudaSuccess) return bfail(b, BA_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e_)); \
+  } while (0)
+
+JobView job_view(const ba_handle* h) {
+  JobView v{};
+  v.L = h->L;
+  v.X = h->X;
+  v.st = h->d_state;
+  v.poses2 = h->poses2;
+  v.planes2 = h->planes2;
+  v.gH = h->gH;
+  v.pred_part = h->pred_part;
+  v.cost_part = h->cost_part;
+  v.n_cost = h->n_cost;
+  return v;
+}
+
+JobTable table_of(const ba_batch* b) {
+  const size_t n = b->jobs.size();
+  JobTable T{};
+  T.jobs = b->d_jobs;
+  T.vblk = b->d_prefix;
+  T.sblk = b->d_prefix + (n + 1);
+  T.oblk = b->d_prefix + 2 * (n + 1);
+  T.n_jobs = (int32_t)n;
+  return T;
+}
+
+void drop_graph(ba_batch* b) {
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  b->graph = nullptr;
+  b->graph_iters = -1;
+}
+
+// (re)upload the job table after a membership change
+ba_status refresh(ba_batch* b) {
+  if (!b->dirty) return BA_OK;
+  const size_t n = b->jobs.size();
+  if (n > b->cap) {
+    cudaFree(b->d_jobs);
+    cudaFree(b->d_prefix);
+    cudaFree(b->d_done);
+    b->d_jobs = nullptr;
+    b->d_prefix = nullptr;
+    b->d_done = nullptr;
+    size_t cap = n < 16 ? 16 : 2 * n;
+    BCK(b, cudaMalloc(&b->d_jobs, sizeof(JobView) * cap), "batch table");
+    BCK(b, cudaMalloc(&b->d_prefix, sizeof(int64_t) * 3 * (cap + 1)), "batch table");
+    BCK(b, cudaMalloc(&b->d_done, sizeof(int32_t) * (cap + 1)), "batch table");
+    b->cap = cap;
+  }
+  std::vector<JobView> views(n);
+  std::vector<int64_t> pre(3 * (n + 1), 0);
+  for (size_t k = 0; k < n; ++k) {
+    const ba_handle* h = b->jobs[k];
+    views[k] = job_view(h);
+    pre[k + 1] = pre[k] + voxel_pass_blocks(h->L.n_voxels);
+    pre[(n + 1) + k + 1] = pre[(n + 1) + k] + h->L.n_scans;
+    pre[2 * (n + 1) + k + 1] = pre[2 * (n + 1) + k] + solve_blocks(h->L.n_scans);
+  }
+  b->n_vblk = pre[n];
+  b->n_sblk = pre[(n + 1) + n];
+  b->n_oblk = pre[2 * (n + 1) + n];
+  if (n) {
+    BCK(b, cudaMemcpyAsync(b->d_jobs, views.data(), sizeof(JobView) * n, cudaMemcpyHostToDevice, b->stream),
+        "batch table upload");
+    BCK(b, cudaMemcpyAsync(b->d_prefix, pre.data(), sizeof(int64_t) * pre.size(), cudaMemcpyHostToDevice, b->stream),
+        "batch table upload");
+    BCK(b, cudaStreamSynchronize(b->stream), "batch table upload");
+  }
+  drop_graph(b);
+  b->dirty = false;
+  return BA_OK;
+}
+
+__global__ void batch_control_kernel(JobTable T, int honor_stop, int reset_stop) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= T.n_jobs) return;
+  DevState* st = T.jobs[k].st;
+  st->honor_stop = honor_stop;
+  if (reset_stop) st->stop = 0;
+}
+
+__global__ void batch_status_kernel(JobTable T, int32_t* done) {
+  __shared__ int32_t active;
+  if (threadIdx.x == 0) active = 0;
+  __syncthreads();
+  for (int k = threadIdx.x; k < T.n_jobs; k += blockDim.x) {
+    const int32_t s = T.jobs[k].st->stop;
+    done[k] = s;
+    if (!s) atomicAdd(&active, 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) done[T.n_jobs] = active;
+}
+
+ba_status launch_batch_iteration(ba_batch* b) {
+  const JobTable T = table_of(b);
+  BCK(b, launch_batch_solve(T, b->n_oblk, b->stream), "batch solve");
+  BCK(b, b->mixed ? launch_batch_voxel_pass_mixed(T, b->n_vblk, 1, b->stream)
+                  : launch_batch_voxel_pass_f64(T, b->n_vblk, 1, b->stream),
+      "batch voxel pass");
+  BCK(b, launch_batch_decide(T, b->stream), "batch decide");
+  BCK(b, b->mixed ? launch_batch_scan_pass_mixed(T, b->n_sblk, b->stream)
+                  : launch_batch_scan_pass_f64(T, b->n_sblk, b->stream),
+      "batch scan pass");
+  return BA_OK;
+}
+
+// work a member queued on its own stream must finish before the batch's
+ba_status sync_members(ba_batch* b) {
+  std::vector<cudaStream_t> seen;
+  for (auto* h : b->jobs) {
+    bool dup = false;
+    for (auto s : seen) dup = dup || s == h->stream;
+    if (dup) continue;
+    seen.push_back(h->stream);
+    BCK(b, cudaStreamSynchronize(h->stream), "synchronize member stream");
+  }
+  return BA_OK;
+}
+
+// n iterations as one CUDA graph (captured on first use for this count)
+ba_status run_iterations(ba_batch* b, int n) {
+  if (b->graph_iters != n) {
+    drop_graph(b);
+    cudaGraph_t g = nullptr;
+    BCK(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal), "graph capture");
+    ba_status s = BA_OK;
+    for (int k = 0; k < n && s == BA_OK; ++k) s = launch_batch_iteration(b);
+    cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+    if (s != BA_OK) {
+      if (g) cudaGraphDestroy(g);
+      return s;
+    }
+    BCK(b, e, "graph capture");
+    e = cudaGraphInstantiate(&b->graph, g, 0);
+    cudaGraphDestroy(g);
+    BCK(b, e, "graph instantiate");
+    b->graph_iters = n;
+  }
+  BCK(b, cudaGraphLaunch(b->graph, b->stream), "graph launch");
+  b->launches += 4 * (int64_t)n;
+  return BA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ba_status ba_batch_create(void* stream, ba_batch** out) {
+  if (!out) return BA_ERR_INVALID_ARG;
+  *out = nullptr;
+  ba_batch* b = new ba_batch();
+  if (stream) {
+    b->stream = (cudaStream_t)stream;
+  } else {
+    // graphs cannot be captured on the legacy default stream: use a private one
+    if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete b;
+      return fail(nullptr, BA_ERR_CUDA, "batch stream creation failed");
+    }
+    b->own_stream = true;
+  }
+  *out = b;
+  return BA_OK;
+}
+
+ba_status ba_batch_add(ba_batch* b, ba_handle* h) {
+  if (!b || !h) return BA_ERR_INVALID_ARG;
+  if (!h->loaded) return bfail(b, BA_ERR_STATE, "the handle has no problem loaded");
+  if (h->batch) return bfail(b, BA_ERR_INVALID_ARG, "the handle is already in a batch");
+  if (!b->jobs.empty()) {
+    if (h->cfg.device != b->device) return bfail(b, BA_ERR_INVALID_ARG, "device differs from the batch's");
+    if (h->mixed != b->mixed) return bfail(b, BA_ERR_INVALID_ARG, "precision differs from the batch's");
+  } else {
+    b->device = h->cfg.device;
+    b->mixed = h->mixed;
+  }
+  DeviceGuard g(h->cfg.device);
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return bfail(b, BA_ERR_CUDA, "synchronize job: %s", cudaGetErrorString(e));
+  b->jobs.push_back(h);
+  h->batch = b;
+  b->dirty = true;
+  return BA_OK;
+}
+
+ba_status ba_batch_remove(ba_batch* b, ba_handle* h) {
+  if (!b || !h) return BA_ERR_INVALID_ARG;
+  for (size_t k = 0; k < b->jobs.size(); ++k)
+    if (b->jobs[k] == h) {
+      DeviceGuard g(b->device);
+      cudaStreamSynchronize(b->stream);
+      b->jobs.erase(b->jobs.begin() + (long)k);
+      h->batch = nullptr;
+      b->dirty = true;
+      return BA_OK;
+    }
+  return bfail(b, BA_ERR_INVALID_ARG, "the handle is not in this batch");
+}
+
+int32_t ba_batch_size(const ba_batch* b) { return b ? (int32_t)b->jobs.size() : 0; }
+
+int64_t ba_batch_kernel_launches(const ba_batch* b) { return b ? b->launches : 0; }
+
+ba_status ba_batch_iterate(ba_batch* b, int32_t n_iters) {
+  if (!b) return BA_ERR_INVALID_ARG;
+  if (n_iters < 0) return bfail(b, BA_ERR_INVALID_ARG, "n_iters must be >= 0");
+  if (b->jobs.empty() || n_iters == 0) return BA_OK;
+  DeviceGuard g(b->device);
+  ba_status s = refresh(b);
+  if (s != BA_OK) return s;
+  if ((s = sync_members(b)) != BA_OK) return s;
+  const JobTable T = table_of(b);
+  batch_control_kernel<<<(T.n_jobs + 127) / 128, 128, 0, b->stream>>>(T, 0, 1);
+  ++b->launches;
+  BCK(b, cudaGetLastError(), "batch control");
+  if ((s = run_iterations(b, n_iters)) != BA_OK) return s;
+  BCK(b, cudaStreamSynchronize(b->stream), "synchronize");
+  return BA_OK;
+}
+
+ba_status ba_batch_solve(ba_batch* b, int32_t chunk, int32_t max_rounds, int32_t* n_active_out) {
+  if (!b) return BA_ERR_INVALID_ARG;
+  if (chunk < 1) return bfail(b, BA_ERR_INVALID_ARG, "chunk must be >= 1");
+  if (n_active_out) *n_active_out = 0;
+  if (b->jobs.empty()) return BA_OK;
+  DeviceGuard g(b->device);
+  ba_status s = refresh(b);
+  if (s != BA_OK) return s;
+  if ((s = sync_members(b)) != BA_OK) return s;
+  const JobTable T = table_of(b);
+  const int n = T.n_jobs;
+  batch_control_kernel<<<(n + 127) / 128, 128, 0, b->stream>>>(T, 1, 0);
+  ++b->launches;
+  BCK(b, cudaGetLastError(), "batch control");
+  int32_t active = n;
+  for (int round = 0; max_rounds <= 0 || round < max_rounds; ++round) {
+    if ((s = run_iterations(b, chunk)) != BA_OK) return s;
+    batch_status_kernel<<<1, 256, 0, b->stream>>>(T, b->d_done);
+    ++b->launches;
+    BCK(b, cudaGetLastError(), "batch status");
+    BCK(b, cudaMemcpyAsync(&active, b->d_done + n, sizeof(int32_t), cudaMemcpyDeviceToHost, b->stream), "status");
+    BCK(b, cudaStreamSynchronize(b->stream), "synchronize");
+    if (active == 0) break;
+  }
+  if (n_active_out) *n_active_out = active;
+  return BA_OK;
+}
+
+ba_status ba_batch_done(ba_batch* b, int32_t* done_out) {
+  if (!b || !done_out) return BA_ERR_INVALID_ARG;
+  if (b->jobs.empty()) return BA_OK;
+  DeviceGuard g(b->device);
+  ba_status s = refresh(b);
+  if (s != BA_OK) return s;
+  const JobTable T = table_of(b);
+  batch_status_kernel<<<1, 256, 0, b->stream>>>(T, b->d_done);
+  ++b->launches;
+  BCK(b, cudaGetLastError(), "batch status");
+  BCK(b, cudaMemcpyAsync(done_out, b->d_done, sizeof(int32_t) * T.n_jobs, cudaMemcpyDeviceToHost, b->stream),
+      "status");
+  BCK(b, cudaStreamSynchronize(b->stream), "synchronize");
+  return BA_OK;
+}
+
+void ba_batch_destroy(ba_batch* b) {
+  if (!b) return;
+  DeviceGuard g(b->device >= 0 ? b->device : 0);
+  cudaStreamSynchronize(b->stream);
+  for (auto* h : b->jobs) h->batch = nullptr;
+  drop_graph(b);
+  cudaFree(b->d_jobs);
+  cudaFree(b->d_prefix);
+  cudaFree(b->d_done);
+  if (b->own_stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
+
+const char* ba_batch_last_error(const ba_batch* b) { return b ? b->err.c_str() : ""; }
 
 }  // extern "C"

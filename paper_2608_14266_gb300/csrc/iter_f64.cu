@@ -18,17 +18,15 @@ namespace mmba {
 // eigenvector give the plane (u, d = u^T c); the voxel's cost is lambda_min.
 // ---------------------------------------------------------------------------
 template <bool kFull>
-__global__ void __launch_bounds__(kVoxelThreads) voxel_pass_f64_kernel(DevLayout L, const double* __restrict__ poses2,
-                                                                      double* __restrict__ planes2,
-                                                                      double* __restrict__ full_out,
-                                                                      double* __restrict__ cost_part,
-                                                                      const DevState* __restrict__ st, int use_trial) {
-  __shared__ double red[kVoxelThreads / 32];
+__device__ __forceinline__ void voxel_pass_f64_body(const DevLayout& L, const double* __restrict__ poses2,
+                                                    double* __restrict__ planes2, double* __restrict__ full_out,
+                                                    double* __restrict__ cost_part, const DevState* __restrict__ st,
+                                                    int use_trial, int64_t blk, double* red) {
   if (st->honor_stop && st->stop) return;
   const int buf = use_trial ? 1 - st->cur : st->cur;
   const double* __restrict__ poses = poses2 + (int64_t)buf * L.n_scans * 12;
   double* __restrict__ planes = planes2 + (int64_t)buf * L.n_voxels * kPlaneStride;
-  const int64_t p = (int64_t)blockIdx.x * kVoxelThreads + threadIdx.x;
+  const int64_t p = blk * kVoxelThreads + threadIdx.x;
   double lam0 = 0.0;
   if (p < L.n_voxels) {
     const int64_t s = p >> 5;
@@ -106,7 +104,30 @@ __global__ void __launch_bounds__(kVoxelThreads) voxel_pass_f64_kernel(DevLayout
     lam0 = lam[0];
   }
   const double tot = block_sum<kVoxelThreads>(lam0, red);
-  if (threadIdx.x == 0) cost_part[blockIdx.x] = tot;
+  if (threadIdx.x == 0) cost_part[blk] = tot;
+}
+
+template <bool kFull>
+__global__ void __launch_bounds__(kVoxelThreads) voxel_pass_f64_kernel(DevLayout L, const double* __restrict__ poses2,
+                                                                      double* __restrict__ planes2,
+                                                                      double* __restrict__ full_out,
+                                                                      double* __restrict__ cost_part,
+                                                                      const DevState* __restrict__ st, int use_trial) {
+  __shared__ double red[kVoxelThreads / 32];
+  voxel_pass_f64_body<kFull>(L, poses2, planes2, full_out, cost_part, st, use_trial, blockIdx.x, red);
+}
+
+__global__ void __launch_bounds__(kVoxelThreads) voxel_pass_f64_batch_kernel(JobTable T, int use_trial) {
+  __shared__ double red[kVoxelThreads / 32];
+  __shared__ JobView J;
+  __shared__ int64_t blk;
+  if (threadIdx.x == 0) {
+    const int job = find_job(T.vblk, T.n_jobs, blockIdx.x);
+    J = T.jobs[job];
+    blk = blockIdx.x - T.vblk[job];
+  }
+  __syncthreads();
+  voxel_pass_f64_body<false>(J.L, J.poses2, J.planes2, nullptr, J.cost_part, J.st, use_trial, blk, red);
 }
 
 // ---------------------------------------------------------------------------
@@ -123,15 +144,13 @@ __global__ void __launch_bounds__(kVoxelThreads) voxel_pass_f64_kernel(DevLayout
 // S and N.  The world-frame blocks are R (.) R^T.  Gauss-Newton mode drops
 // the (w m'^T + m' w^T)/2 - (w^T m') I term.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kScanThreads) scan_pass_f64_kernel(DevLayout L, const double* __restrict__ poses2,
-                                                                    const double* __restrict__ planes2,
-                                                                    double* __restrict__ gH,
-                                                                    const DevState* __restrict__ st, int force) {
-  __shared__ double red[kScanThreads / 32][kGH];
+__device__ __forceinline__ void scan_pass_f64_body(const DevLayout& L, const double* __restrict__ poses2,
+                                                   const double* __restrict__ planes2, double* __restrict__ gH,
+                                                   const DevState* __restrict__ st, int force, int j,
+                                                   double (*red)[kGH]) {
   // a rejected step (or an iteration after the solve stopped) leaves g, H unchanged
   if (!force && !st->scan_pending) return;
   const int buf = st->cur;
-  const int j = blockIdx.x;
   const double* __restrict__ P = poses2 + ((int64_t)buf * L.n_scans + j) * 12;
   const double* __restrict__ planes = planes2 + (int64_t)buf * L.n_voxels * kPlaneStride;
   const bool gn = st->hess_mode != 0;
@@ -272,20 +291,35 @@ __global__ void __launch_bounds__(kScanThreads) scan_pass_f64_kernel(DevLayout L
   }
 }
 
+__global__ void __launch_bounds__(kScanThreads) scan_pass_f64_kernel(DevLayout L, const double* __restrict__ poses2,
+                                                                    const double* __restrict__ planes2,
+                                                                    double* __restrict__ gH,
+                                                                    const DevState* __restrict__ st, int force) {
+  __shared__ double red[kScanThreads / 32][kGH];
+  scan_pass_f64_body(L, poses2, planes2, gH, st, force, blockIdx.x, red);
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_pass_f64_batch_kernel(JobTable T) {
+  __shared__ double red[kScanThreads / 32][kGH];
+  __shared__ JobView J;
+  __shared__ int j;
+  if (threadIdx.x == 0) {
+    const int job = find_job(T.sblk, T.n_jobs, blockIdx.x);
+    J = T.jobs[job];
+    j = (int)(blockIdx.x - T.sblk[job]);
+  }
+  __syncthreads();
+  scan_pass_f64_body(J.L, J.poses2, J.planes2, J.gH, J.st, 0, j, red);
+}
+
 // ---------------------------------------------------------------------------
 // Solver: one thread per scan.  A = H + mu diag(H), A delta = -g by LDL^T,
 // trial pose R' = Exp(dphi) R, t' = t + dt, and the scan's share of the
 // predicted reduction -(g^T delta + delta^T H delta / 2).  The fixed scan and
 // scans without observations keep their pose.
 // ---------------------------------------------------------------------------
-__global__ void solve_f64_kernel(DevLayout L, double* __restrict__ poses2, const double* __restrict__ gH,
-                                 double* __restrict__ pred_part, DevState* st) {
-  if (st->honor_stop && st->stop) return;
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= L.n_scans) return;
-  const int cur = st->cur;
-  const double* P = poses2 + ((int64_t)cur * L.n_scans + j) * 12;
-  double* Pt = poses2 + ((int64_t)(1 - cur) * L.n_scans + j) * 12;
+__device__ inline void solve_scan(const DevLayout& L, int j, const double* __restrict__ P, double* __restrict__ Pt,
+                                  const double* __restrict__ gH, double* __restrict__ pred_part, DevState* st) {
   const int64_t nobs = L.scan_off[j + 1] - L.scan_off[j];
   if (j == L.fixed_scan || nobs == 0) {
     for (int k = 0; k < 12; ++k) Pt[k] = P[k];
@@ -331,6 +365,39 @@ __global__ void solve_f64_kernel(DevLayout L, double* __restrict__ poses2, const
   Pt[11] = P[11] + dlt[5];
 }
 
+// With stab2 given (mixed precision) the trial scan's FP32 table entry is
+// written too, from the trial pose and the scan's reference pose.
+__device__ __forceinline__ void solve_f64_body(const DevLayout& L, double* __restrict__ poses2,
+                                               const double* __restrict__ gH, double* __restrict__ pred_part,
+                                               DevState* st, const double* __restrict__ sref,
+                                               float* __restrict__ stab2, int64_t j) {
+  if (st->honor_stop && st->stop) return;
+  if (j >= L.n_scans) return;
+  const int cur = st->cur;
+  const double* P = poses2 + ((int64_t)cur * L.n_scans + j) * 12;
+  double* Pt = poses2 + ((int64_t)(1 - cur) * L.n_scans + j) * 12;
+  solve_scan(L, (int)j, P, Pt, gH, pred_part, st);
+  if (stab2) scan_table_entry(Pt, sref + 12 * (int64_t)j, stab2 + ((int64_t)(1 - cur) * L.n_scans + j) * kTab);
+}
+
+__global__ void solve_f64_kernel(DevLayout L, double* __restrict__ poses2, const double* __restrict__ gH,
+                                 double* __restrict__ pred_part, DevState* st, const double* __restrict__ sref,
+                                 float* __restrict__ stab2) {
+  solve_f64_body(L, poses2, gH, pred_part, st, sref, stab2, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+__global__ void __launch_bounds__(kSolveThreads) solve_f64_batch_kernel(JobTable T) {
+  __shared__ JobView J;
+  __shared__ int64_t blk;
+  if (threadIdx.x == 0) {
+    const int job = find_job(T.oblk, T.n_jobs, blockIdx.x);
+    J = T.jobs[job];
+    blk = blockIdx.x - T.oblk[job];
+  }
+  __syncthreads();
+  solve_f64_body(J.L, J.poses2, J.gH, J.pred_part, J.st, J.X.sref, J.X.stab2, blk * kSolveThreads + threadIdx.x);
+}
+
 // ---------------------------------------------------------------------------
 // LM decision (one block): sums the trial cost and the predicted reduction
 // in a fixed order, accepts iff every solve succeeded, the prediction is
@@ -339,55 +406,67 @@ __global__ void solve_f64_kernel(DevLayout L, double* __restrict__ poses2, const
 // otherwise).  Acceptance flips the current pose/plane buffers.
 // With mode = 1 it only installs the summed cost as the current cost.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kDecideThreads) decide_kernel(const double* __restrict__ cost_part, int64_t n_cost,
-                                                               const double* __restrict__ pred_part, int64_t n_pred,
-                                                               DevState* st, int mode) {
-  __shared__ double red[kDecideThreads / 32];
+__device__ __forceinline__ void decide_body(const double* __restrict__ cost_part, int64_t n_cost,
+                                            const double* __restrict__ pred_part, int64_t n_pred, DevState* st,
+                                            int mode, double* red) {
   if (mode == 0 && st->honor_stop && st->stop) {
     if (threadIdx.x == 0) st->scan_pending = 0;
     return;
   }
-  double c = 0.0, pr = 0.0;
-  for (int64_t k = threadIdx.x; k < n_cost; k += kDecideThreads) c += cost_part[k];
-  const double csum = block_sum<kDecideThreads>(c, red);
-  if (mode == 0)
-    for (int64_t k = threadIdx.x; k < n_pred; k += kDecideThreads) pr += pred_part[k];
-  const double psum = block_sum<kDecideThreads>(pr, red);
+  const double csum = block_sum<kDecideThreads>(strided_sum<kDecideThreads>(cost_part, n_cost), red);
+  const double psum =
+      block_sum<kDecideThreads>(mode == 0 ? strided_sum<kDecideThreads>(pred_part, n_pred) : 0.0, red);
   if (threadIdx.x != 0) return;
   if (mode == 1) {
     st->cost = csum;
     return;
   }
-  const int fail = st->solve_fail_flag;
-  const bool accept = !fail && psum > 0.0 && csum < st->cost;
-  st->iters += 1;
-  st->last_pred = psum;
-  st->last_trial_cost = csum;
-  st->solve_failed = fail;
-  st->solve_fail_flag = 0;
+  // work on a register copy: one load and one store of the state instead of a
+  // chain of dependent global accesses
+  DevState s = *st;
+  const int fail = s.solve_fail_flag;
+  const bool accept = !fail && psum > 0.0 && csum < s.cost;
+  s.iters += 1;
+  s.last_pred = psum;
+  s.last_trial_cost = csum;
+  s.solve_failed = fail;
+  s.solve_fail_flag = 0;
   if (accept) {
-    const double rho = (st->cost - csum) / psum;
+    const double rho = (s.cost - csum) / psum;
     const double x = 2.0 * rho - 1.0;
     const double f = 1.0 - x * x * x;
-    st->mu *= f > (1.0 / 3.0) ? f : (1.0 / 3.0);
-    st->nu = 2.0;
-    st->last_rho = rho;
-    st->converged = (st->cost - csum) <= st->rel_tol * st->cost + st->abs_tol;
-    st->cost = csum;
-    st->cur = 1 - st->cur;
-    st->accepted += 1;
-    st->consec_reject = 0;
+    s.mu *= f > (1.0 / 3.0) ? f : (1.0 / 3.0);
+    s.nu = 2.0;
+    s.last_rho = rho;
+    s.converged = (s.cost - csum) <= s.rel_tol * s.cost + s.abs_tol;
+    s.cost = csum;
+    s.cur = 1 - s.cur;
+    s.accepted += 1;
+    s.consec_reject = 0;
   } else {
-    st->mu *= st->nu;
-    st->nu *= 2.0;
-    st->last_rho = (!fail && psum > 0.0) ? (st->cost - csum) / psum : __longlong_as_double(0x7ff8000000000000ll);
-    st->consec_reject += 1;
+    s.mu *= s.nu;
+    s.nu *= 2.0;
+    s.last_rho = (!fail && psum > 0.0) ? (s.cost - csum) / psum : __longlong_as_double(0x7ff8000000000000ll);
+    s.consec_reject += 1;
   }
-  st->last_accepted = accept;
-  st->scan_pending = accept;
-  if (st->honor_stop &&
-      (st->converged || st->iters >= st->max_iters || st->consec_reject >= st->max_consec_reject))
-    st->stop = 1;
+  s.last_accepted = accept;
+  s.scan_pending = accept;
+  if (s.honor_stop && (s.converged || s.iters >= s.max_iters || s.consec_reject >= s.max_consec_reject)) s.stop = 1;
+  *st = s;
+}
+
+__global__ void __launch_bounds__(kDecideThreads) decide_kernel(const double* __restrict__ cost_part, int64_t n_cost,
+                                                               const double* __restrict__ pred_part, int64_t n_pred,
+                                                               DevState* st, int mode) {
+  __shared__ double red[kDecideThreads / 32];
+  decide_body(cost_part, n_cost, pred_part, n_pred, st, mode, red);
+}
+
+// one block per job
+__global__ void __launch_bounds__(kDecideThreads) decide_batch_kernel(JobTable T) {
+  __shared__ double red[kDecideThreads / 32];
+  const JobView& J = T.jobs[blockIdx.x];
+  decide_body(J.cost_part, J.n_cost, J.pred_part, J.L.n_scans, J.st, 0, red);
 }
 
 // ---- launchers ---------------------------------------------------------------
@@ -412,16 +491,36 @@ cudaError_t launch_scan_pass_f64(const DevLayout& L, const double* poses2, const
 }
 
 cudaError_t launch_solve_f64(const DevLayout& L, double* poses2, const double* gH, double* pred_part, DevState* st,
-                             cudaStream_t stream) {
-  const int threads = 128;
+                             const double* sref, float* stab2, cudaStream_t stream) {
+  const int threads = kSolveThreads;
   const int blocks = (L.n_scans + threads - 1) / threads;
-  solve_f64_kernel<<<blocks, threads, 0, stream>>>(L, poses2, gH, pred_part, st);
+  solve_f64_kernel<<<blocks, threads, 0, stream>>>(L, poses2, gH, pred_part, st, sref, stab2);
   return cudaGetLastError();
 }
 
 cudaError_t launch_decide(const double* cost_part, int64_t n_cost, const double* pred_part, int64_t n_pred,
                           DevState* st, int mode, cudaStream_t stream) {
   decide_kernel<<<1, kDecideThreads, 0, stream>>>(cost_part, n_cost, pred_part, n_pred, st, mode);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_solve(const JobTable& T, int64_t n_blocks, cudaStream_t stream) {
+  solve_f64_batch_kernel<<<(unsigned)n_blocks, kSolveThreads, 0, stream>>>(T);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_decide(const JobTable& T, cudaStream_t stream) {
+  decide_batch_kernel<<<(unsigned)T.n_jobs, kDecideThreads, 0, stream>>>(T);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_voxel_pass_f64(const JobTable& T, int64_t n_blocks, int use_trial, cudaStream_t stream) {
+  voxel_pass_f64_batch_kernel<<<(unsigned)n_blocks, kVoxelThreads, 0, stream>>>(T, use_trial);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_scan_pass_f64(const JobTable& T, int64_t n_blocks, cudaStream_t stream) {
+  scan_pass_f64_batch_kernel<<<(unsigned)n_blocks, kScanThreads, 0, stream>>>(T);
   return cudaGetLastError();
 }
 

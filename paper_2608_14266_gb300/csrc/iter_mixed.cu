@@ -1,0 +1,424 @@
+// Mixed-precision iteration kernels: FP32 per observation on re-centred
+// clusters (anchors and reference poses fixed at load or at ba_set_state),
+// FP64 only per scan (6x6 solve, pose composition), in the sum over voxel
+// blocks and in the set-up that builds the FP32 copies.
+#include "mmba_internal.cuh"
+#include "mmba_kernels.h"
+
+namespace mmba {
+
+// E x for E = a [phi]x + b [phi]x^2:  a (phi x x) + b (phi x (phi x x))
+__device__ __forceinline__ void apply_E(const float* ph, float a, float b, float x0, float x1, float x2, float& y0,
+                                        float& y1, float& y2) {
+  const float c0 = ph[1] * x2 - ph[2] * x1, c1 = ph[2] * x0 - ph[0] * x2, c2 = ph[0] * x1 - ph[1] * x0;
+  const float d0 = ph[1] * c2 - ph[2] * c1, d1 = ph[2] * c0 - ph[0] * c2, d2 = ph[0] * c1 - ph[1] * c0;
+  y0 = fmaf(a, c0, b * d0);
+  y1 = fmaf(a, c1, b * d1);
+  y2 = fmaf(a, c2, b * d2);
+}
+
+// ---------------------------------------------------------------------------
+// Voxel pass (mixed): one thread per voxel over SELL-32 FP32 slices.
+// Per observation, in the voxel's current frame B (rows e1, e2, n) and about
+// its latest centroid delta (world axes, relative to the anchor):
+//   x   = B (b + E l + dt - delta)                (posed mean - centroid)
+//   M_o = G diag(sigma) G^T,   G = B dR V,  dR = I + E
+// where V, sigma are the observation's stored eigen-decomposition.  The sums
+// of N x, M_o + N x x^T and N have a small normal direction in B, so FP32
+// keeps lambda_min relatively accurate; an FP32 Jacobi in B gives the plane,
+// and B and delta then move to the new eigenvectors and centroid.
+// ---------------------------------------------------------------------------
+template <bool kFull>
+__device__ __forceinline__ void voxel_pass_mixed_body(const DevLayout& L, const DevMixed& X,
+                                                      double* __restrict__ full_out, double* __restrict__ cost_part,
+                                                      const DevState* __restrict__ st, int use_trial, int64_t blk,
+                                                      float* red) {
+  if (st->honor_stop && st->stop) return;
+  const int buf = use_trial ? 1 - st->cur : st->cur;
+  const float* __restrict__ stab = X.stab2 + (int64_t)buf * L.n_scans * kTab;
+  float* __restrict__ planes = X.planes32_2 + (int64_t)buf * L.n_voxels * 4;
+  const int64_t p = blk * kVoxelThreads + threadIdx.x;
+  float lam0 = 0.f;
+  if (p < L.n_voxels) {
+    const int64_t sl = p >> 5;
+    const int lane = (int)(p & 31);
+    const int len = L.vlen[p];
+    const int64_t base = L.slice_off[sl] + lane;
+    const int64_t ne = L.n_elems;
+    const float4 an = X.vanchor[p];
+    const float4 qb = X.vstate[2 * p];
+    const float4 dw = X.vstate[2 * p + 1];
+    float B[9];
+    quat_to_mat_f(qb.x, qb.y, qb.z, qb.w, B);
+    float n = 0.f, s0 = 0.f, s1 = 0.f, s2 = 0.f;
+    float m00 = 0.f, m01 = 0.f, m02 = 0.f, m11 = 0.f, m12 = 0.f, m22 = 0.f;
+    // the streamed values of observation k + 1 are loaded while k is processed
+    int pj = 0;
+    float pv[kVe32];
+#pragma unroll
+    for (int q = 0; q < kVe32; ++q) pv[q] = 0.f;
+    if (len > 0) {
+      pj = __ldg(L.ve_scan + base);
+#pragma unroll
+      for (int q = 0; q < kVe32; ++q) pv[q] = __ldg(X.ve32 + q * ne + base);
+    }
+    for (int k = 0; k < len; ++k) {
+      const int j = pj;
+      float v[kVe32];
+#pragma unroll
+      for (int q = 0; q < kVe32; ++q) v[q] = pv[q];
+      if (k + 1 < len) {
+        const int64_t e1 = base + (int64_t)(k + 1) * kSlice;
+        pj = __ldg(L.ve_scan + e1);
+#pragma unroll
+        for (int q = 0; q < kVe32; ++q) pv[q] = __ldg(X.ve32 + q * ne + e1);
+      }
+      const float4* T4 = reinterpret_cast<const float4*>(stab + (int64_t)j * kTab);
+      const float4 t0 = __ldg(T4), t1 = __ldg(T4 + 1), t2 = __ldg(T4 + 2);
+      const float ph[3] = {t0.x, t0.y, t0.z};
+      const float ca = t0.w, cb = t1.x;
+      const float b0 = v[0], b1 = v[1], b2 = v[2], N = v[10];
+      // posed mean about the latest centroid (world axes), then voxel frame
+      const float l0 = b0 + (an.x - t2.x), l1 = b1 + (an.y - t2.y), l2 = b2 + (an.z - t2.z);
+      float el0, el1, el2;
+      apply_E(ph, ca, cb, l0, l1, l2, el0, el1, el2);
+      const float xw0 = (b0 - dw.x) + el0 + t1.y, xw1 = (b1 - dw.y) + el1 + t1.z, xw2 = (b2 - dw.z) + el2 + t1.w;
+      const float x0 = fmaf(B[0], xw0, fmaf(B[1], xw1, B[2] * xw2));
+      const float x1 = fmaf(B[3], xw0, fmaf(B[4], xw1, B[5] * xw2));
+      const float x2 = fmaf(B[6], xw0, fmaf(B[7], xw1, B[8] * xw2));
+      // G = B (V + E V): columns of V rotated by dR, then into the frame
+      float V[9];
+      quat_to_mat_f(v[6], v[7], v[8], v[9], V);
+      float G[9];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        float e0, e1, e2;
+        apply_E(ph, ca, cb, V[c], V[3 + c], V[6 + c], e0, e1, e2);
+        const float d0 = V[c] + e0, d1 = V[3 + c] + e1, d2 = V[6 + c] + e2;
+        G[c] = fmaf(B[0], d0, fmaf(B[1], d1, B[2] * d2));
+        G[3 + c] = fmaf(B[3], d0, fmaf(B[4], d1, B[5] * d2));
+        G[6 + c] = fmaf(B[6], d0, fmaf(B[7], d1, B[8] * d2));
+      }
+      const float sg0 = v[3], sg1 = v[4], sg2 = v[5];
+      // G diag(sigma) G^T + N x x^T, upper triangle
+      const float g00 = G[0] * sg0, g01 = G[1] * sg1, g02 = G[2] * sg2;
+      const float g10 = G[3] * sg0, g11 = G[4] * sg1, g12 = G[5] * sg2;
+      const float g20 = G[6] * sg0, g21 = G[7] * sg1, g22 = G[8] * sg2;
+      const float Nx0 = N * x0, Nx1 = N * x1, Nx2 = N * x2;
+      m00 += fmaf(g00, G[0], fmaf(g01, G[1], fmaf(g02, G[2], Nx0 * x0)));
+      m01 += fmaf(g00, G[3], fmaf(g01, G[4], fmaf(g02, G[5], Nx0 * x1)));
+      m02 += fmaf(g00, G[6], fmaf(g01, G[7], fmaf(g02, G[8], Nx0 * x2)));
+      m11 += fmaf(g10, G[3], fmaf(g11, G[4], fmaf(g12, G[5], Nx1 * x1)));
+      m12 += fmaf(g10, G[6], fmaf(g11, G[7], fmaf(g12, G[8], Nx1 * x2)));
+      m22 += fmaf(g20, G[6], fmaf(g21, G[7], fmaf(g22, G[8], Nx2 * x2)));
+      s0 += Nx0;
+      s1 += Nx1;
+      s2 += Nx2;
+      n += N;
+    }
+    const float inv = 1.0f / n;
+    const float d0 = s0 * inv, d1 = s1 * inv, d2 = s2 * inv;  // centroid - delta, frame axes
+    float A[6] = {fmaf(-d0, d0, m00 * inv), fmaf(-d0, d1, m01 * inv), fmaf(-d0, d2, m02 * inv),
+                  fmaf(-d1, d1, m11 * inv), fmaf(-d1, d2, m12 * inv), fmaf(-d2, d2, m22 * inv)};
+    float lam[3], W[9];
+    eig3_sym_f(A, lam, W);
+    // centroid - anchor and normal, world axes (B^T times frame vectors)
+    const float cw0 = dw.x + fmaf(B[0], d0, fmaf(B[3], d1, B[6] * d2));
+    const float cw1 = dw.y + fmaf(B[1], d0, fmaf(B[4], d1, B[7] * d2));
+    const float cw2 = dw.z + fmaf(B[2], d0, fmaf(B[5], d1, B[8] * d2));
+    float U[9];  // rows: new e1 (largest), e2, n (smallest), world axes
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int c = 2 - k;
+      U[3 * k] = fmaf(B[0], W[3 * c], fmaf(B[3], W[3 * c + 1], B[6] * W[3 * c + 2]));
+      U[3 * k + 1] = fmaf(B[1], W[3 * c], fmaf(B[4], W[3 * c + 1], B[7] * W[3 * c + 2]));
+      U[3 * k + 2] = fmaf(B[2], W[3 * c], fmaf(B[5], W[3 * c + 1], B[8] * W[3 * c + 2]));
+    }
+    const float u0 = U[6], u1 = U[7], u2 = U[8];
+    const float dp = fmaf(u0, cw0, fmaf(u1, cw1, u2 * cw2));  // u . (c - a)
+    *reinterpret_cast<float4*>(planes + 4 * p) = make_float4(u0, u1, u2, dp);
+    if (!kFull) {
+      // the frame follows the eigenvectors (made right-handed), delta the centroid
+      const float det = U[0] * (U[4] * U[8] - U[5] * U[7]) - U[1] * (U[3] * U[8] - U[5] * U[6]) +
+                        U[2] * (U[3] * U[7] - U[4] * U[6]);
+      if (det < 0.f) {
+        U[0] = -U[0];
+        U[1] = -U[1];
+        U[2] = -U[2];
+      }
+      float qn[4];
+      mat_to_quat<float>(U, qn);
+      X.vstate[2 * p] = make_float4(qn[0], qn[1], qn[2], qn[3]);
+      X.vstate[2 * p + 1] = make_float4(cw0, cw1, cw2, 0.f);
+    } else {
+      double* f = full_out + 9 * (int64_t)L.vperm[p];
+      f[0] = lam[0];
+      f[1] = lam[1];
+      f[2] = lam[2];
+      f[3] = u0;
+      f[4] = u1;
+      f[5] = u2;
+      f[6] = (double)an.x + (double)cw0;
+      f[7] = (double)an.y + (double)cw1;
+      f[8] = (double)an.z + (double)cw2;
+    }
+    lam0 = lam[0];
+  }
+  // FP32 block sum of lambda_min (relative rounding ~1e-7 of a block's cost);
+  // the sum over blocks is FP64
+  const float tot = block_sum<kVoxelThreads, float>(lam0, red);
+  if (threadIdx.x == 0) cost_part[blk] = (double)tot;
+}
+
+template <bool kFull>
+__global__ void __launch_bounds__(kVoxelThreads) voxel_pass_mixed_kernel(DevLayout L, DevMixed X,
+                                                                        double* __restrict__ full_out,
+                                                                        double* __restrict__ cost_part,
+                                                                        const DevState* __restrict__ st,
+                                                                        int use_trial) {
+  __shared__ float red[kVoxelThreads / 32];
+  voxel_pass_mixed_body<kFull>(L, X, full_out, cost_part, st, use_trial, blockIdx.x, red);
+}
+
+__global__ void __launch_bounds__(kVoxelThreads) voxel_pass_mixed_batch_kernel(JobTable T, int use_trial) {
+  __shared__ float red[kVoxelThreads / 32];
+  __shared__ JobView J;
+  __shared__ int64_t blk;
+  if (threadIdx.x == 0) {
+    const int job = find_job(T.vblk, T.n_jobs, blockIdx.x);
+    J = T.jobs[job];
+    blk = blockIdx.x - T.vblk[job];
+  }
+  __syncthreads();
+  voxel_pass_mixed_body<false>(J.L, J.X, nullptr, J.cost_part, J.st, use_trial, blk, red);
+}
+
+// ---------------------------------------------------------------------------
+// Scan pass (mixed): one block per scan.  The residual of an observation's
+// mean is r = u . (q - c) = u . x - u . (c - a) with x = b + E l + dt as in
+// the voxel pass (world axes).  The derivative terms are those of the FP64
+// scan pass written in the scan's reference axes (lever l, scatter S_ref and
+// w = dR^T u = u + E^T u), accumulated in FP32 per thread, reduced in FP32
+// per block and rotated by dR once per scan.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void scan_pass_mixed_body(const DevLayout& L, const DevMixed& X,
+                                                     double* __restrict__ gH, const DevState* __restrict__ st,
+                                                     int force, int j, float (*red)[kGH], float* tot, float* dR) {
+  if (!force && !st->scan_pending) return;
+  const int buf = st->cur;
+  const float* tb = X.stab2 + ((int64_t)buf * L.n_scans + j) * kTab;
+  const float ph[3] = {tb[0], tb[1], tb[2]};
+  const float ca = tb[3], cb = tb[4];
+  const float dt0 = tb[5], dt1 = tb[6], dt2 = tb[7], tr0 = tb[8], tr1 = tb[9], tr2 = tb[10];
+  const float* __restrict__ planes = X.planes32_2 + (int64_t)buf * L.n_voxels * 4;
+  const bool gn = st->hess_mode != 0;
+  float acc[kGH];
+#pragma unroll
+  for (int k = 0; k < kGH; ++k) acc[k] = 0.f;
+  const int64_t lo = L.scan_off[j], hi = L.scan_off[j + 1];
+  const int64_t no = L.n_obs;
+  for (int64_t o = lo + threadIdx.x; o < hi; o += kScanThreads) {
+    const int32_t pv = __ldg(L.se_vox + o);
+    const float4 pl = __ldg(reinterpret_cast<const float4*>(planes) + pv);
+    const float4 an = __ldg(X.vanchor + pv);
+    const float b0 = __ldg(X.se32 + o), b1 = __ldg(X.se32 + no + o), b2 = __ldg(X.se32 + 2 * no + o);
+    const float S00 = __ldg(X.se32 + 3 * no + o), S01 = __ldg(X.se32 + 4 * no + o),
+                S02 = __ldg(X.se32 + 5 * no + o), S11 = __ldg(X.se32 + 6 * no + o),
+                S12 = __ldg(X.se32 + 7 * no + o), S22 = __ldg(X.se32 + 8 * no + o);
+    const float N = __ldg(X.se32 + 9 * no + o);
+    const float l0 = b0 + (an.x - tr0), l1 = b1 + (an.y - tr1), l2 = b2 + (an.z - tr2);
+    float el0, el1, el2;
+    apply_E(ph, ca, cb, l0, l1, l2, el0, el1, el2);
+    const float x0 = b0 + el0 + dt0, x1 = b1 + el1 + dt1, x2 = b2 + el2 + dt2;
+    const float r = fmaf(pl.x, x0, fmaf(pl.y, x1, fmaf(pl.z, x2, -pl.w)));
+    // w = dR^T u = u + E^T u = u - a (phi x u) + b (phi x (phi x u))
+    float eu0, eu1, eu2;
+    apply_E(ph, -ca, cb, pl.x, pl.y, pl.z, eu0, eu1, eu2);
+    const float wx = pl.x + eu0, wy = pl.y + eu1, wz = pl.z + eu2;
+    const float Nr = N * r;
+    const float swx = fmaf(S00, wx, fmaf(S01, wy, S02 * wz));
+    const float swy = fmaf(S01, wx, fmaf(S11, wy, S12 * wz));
+    const float swz = fmaf(S02, wx, fmaf(S12, wy, S22 * wz));
+    const float mpx = fmaf(Nr, l0, swx), mpy = fmaf(Nr, l1, swy), mpz = fmaf(Nr, l2, swz);
+    acc[0] += mpy * wz - mpz * wy;
+    acc[1] += mpz * wx - mpx * wz;
+    acc[2] += mpx * wy - mpy * wx;
+    acc[3] += Nr * wx;
+    acc[4] += Nr * wy;
+    acc[5] += Nr * wz;
+    const float Nlx = N * l0, Nly = N * l1, Nlz = N * l2;
+    const float p00 = fmaf(Nlx, l0, S00), p01 = fmaf(Nlx, l1, S01), p02 = fmaf(Nlx, l2, S02);
+    const float p11 = fmaf(Nly, l1, S11), p12 = fmaf(Nly, l2, S12), p22 = fmaf(Nlz, l2, S22);
+    const float b00 = wy * p02 - wz * p01, b10 = wz * p00 - wx * p02, b20 = wx * p01 - wy * p00;
+    const float b01 = wy * p12 - wz * p11, b11 = wz * p01 - wx * p12, b21 = wx * p11 - wy * p01;
+    const float b02 = wy * p22 - wz * p12, b12 = wz * p02 - wx * p22;
+    float h00 = -wz * b01 + wy * b02;
+    float h01 = wz * b00 - wx * b02;
+    float h02 = -wy * b00 + wx * b01;
+    float h11 = wz * b10 - wx * b12;
+    float h12 = -wy * b10 + wx * b11;
+    float h22 = -wy * b20 + wx * b21;
+    if (!gn) {
+      const float wm = fmaf(wx, mpx, fmaf(wy, mpy, wz * mpz));
+      h00 += wx * mpx - wm;
+      h11 += wy * mpy - wm;
+      h22 += wz * mpz - wm;
+      h01 += 0.5f * (wx * mpy + mpx * wy);
+      h02 += 0.5f * (wx * mpz + mpx * wz);
+      h12 += 0.5f * (wy * mpz + mpy * wz);
+    }
+    acc[6] += h00;
+    acc[7] += h01;
+    acc[8] += h02;
+    const float cx = Nly * wz - Nlz * wy, cy = Nlz * wx - Nlx * wz, cz = Nlx * wy - Nly * wx;
+    acc[9] += cx * wx;
+    acc[10] += cx * wy;
+    acc[11] += cx * wz;
+    acc[12] += h11;
+    acc[13] += h12;
+    acc[14] += cy * wx;
+    acc[15] += cy * wy;
+    acc[16] += cy * wz;
+    acc[17] += h22;
+    acc[18] += cz * wx;
+    acc[19] += cz * wy;
+    acc[20] += cz * wz;
+    const float Nwx = N * wx, Nwy = N * wy;
+    acc[21] += Nwx * wx;
+    acc[22] += Nwx * wy;
+    acc[23] += Nwx * wz;
+    acc[24] += Nwy * wy;
+    acc[25] += Nwy * wz;
+    acc[26] += N * wz * wz;
+  }
+  // FP32 block reduction: the per-scan sums only need FP32 (their rounding is
+  // far below what moves a pose by 1e-9 rad given H's size), and GB300's FP64
+  // pipe is 1/64 of FP32, so FP64 is kept out of the reduction.
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 0; k < kGH; ++k) {
+    float v = acc[k];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    if (l == 0) red[w][k] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < kGH) {
+    float v = 0.f;
+#pragma unroll
+    for (int q = 0; q < kScanThreads / 32; ++q) v += red[q][threadIdx.x];
+    tot[threadIdx.x] = v;
+  } else if (threadIdx.x >= 32 && threadIdx.x < 41) {
+    // dR = I + a [phi]x + b [phi]x^2, entry (r, c)
+    const int r = (threadIdx.x - 32) / 3, c = (threadIdx.x - 32) % 3;
+    const float K[3][3] = {{0.f, -ph[2], ph[1]}, {ph[2], 0.f, -ph[0]}, {-ph[1], ph[0], 0.f}};
+    const float k2 = ph[r] * ph[c] - (r == c ? ph[0] * ph[0] + ph[1] * ph[1] + ph[2] * ph[2] : 0.f);
+    dR[threadIdx.x - 32] = (r == c ? 1.f : 0.f) + ca * K[r][c] + cb * k2;
+  }
+  __syncthreads();
+  // world frame: g = blockdiag(dR, dR) g', H = blockdiag(dR, dR) H' blockdiag(dR, dR)^T,
+  // one output entry per thread (6 of g, 21 of H's upper triangle)
+  if (threadIdx.x < kGH) {
+    const int t = threadIdx.x;
+    double* out = gH + (int64_t)j * kGH;
+    if (t < 6) {
+      const int b = t / 3, r = t % 3;
+      out[t] = (double)(dR[3 * r] * tot[3 * b] + dR[3 * r + 1] * tot[3 * b + 1] + dR[3 * r + 2] * tot[3 * b + 2]);
+    } else {
+      int r = 0, rem = t - 6;
+      while (rem >= 6 - r) {
+        rem -= 6 - r;
+        ++r;
+      }
+      const int c = r + rem;
+      const int br = r / 3, bc = c / 3, rr = r % 3, cc = c % 3;
+      float v = 0.f;
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+          int i = 3 * br + a, k = 3 * bc + b;
+          if (i > k) {
+            const int tmp = i;
+            i = k;
+            k = tmp;
+          }
+          const float h = tot[6 + 6 * i - i * (i - 1) / 2 + (k - i)];
+          v = fmaf(dR[3 * rr + a] * h, dR[3 * cc + b], v);
+        }
+      out[t] = (double)v;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_pass_mixed_kernel(DevLayout L, DevMixed X,
+                                                                      double* __restrict__ gH,
+                                                                      const DevState* __restrict__ st, int force) {
+  __shared__ float red[kScanThreads / 32][kGH];
+  __shared__ float tot[kGH];
+  __shared__ float dR[9];
+  scan_pass_mixed_body(L, X, gH, st, force, blockIdx.x, red, tot, dR);
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_pass_mixed_batch_kernel(JobTable T) {
+  __shared__ float red[kScanThreads / 32][kGH];
+  __shared__ float tot[kGH];
+  __shared__ float dR[9];
+  __shared__ JobView J;
+  __shared__ int j;
+  if (threadIdx.x == 0) {
+    const int job = find_job(T.sblk, T.n_jobs, blockIdx.x);
+    J = T.jobs[job];
+    j = (int)(blockIdx.x - T.sblk[job]);
+  }
+  __syncthreads();
+  scan_pass_mixed_body(J.L, J.X, J.gH, J.st, 0, j, red, tot, dR);
+}
+
+// Per-scan FP32 table of buffer `buf` from the FP64 poses of that buffer.
+__global__ void scan_table_kernel(int32_t n_scans, const double* poses2, const double* sref, float* stab2, int buf) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n_scans) return;
+  scan_table_entry(poses2 + ((int64_t)buf * n_scans + j) * 12, sref + 12 * (int64_t)j,
+                   stab2 + ((int64_t)buf * n_scans + j) * kTab);
+}
+
+// ---- launchers ---------------------------------------------------------------
+
+cudaError_t launch_voxel_pass_mixed(const DevLayout& L, const DevMixed& X, double* full_out, double* cost_part,
+                                    const DevState* st, int use_trial, cudaStream_t stream) {
+  const int64_t nb = voxel_pass_blocks(L.n_voxels);
+  if (full_out)
+    voxel_pass_mixed_kernel<true><<<(unsigned)nb, kVoxelThreads, 0, stream>>>(L, X, full_out, cost_part, st,
+                                                                              use_trial);
+  else
+    voxel_pass_mixed_kernel<false><<<(unsigned)nb, kVoxelThreads, 0, stream>>>(L, X, nullptr, cost_part, st,
+                                                                               use_trial);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scan_pass_mixed(const DevLayout& L, const DevMixed& X, const double* poses2, double* gH,
+                                   const DevState* st, int force, cudaStream_t stream) {
+  if (L.n_scans == 0) return cudaSuccess;
+  (void)poses2;
+  scan_pass_mixed_kernel<<<(unsigned)L.n_scans, kScanThreads, 0, stream>>>(L, X, gH, st, force);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_voxel_pass_mixed(const JobTable& T, int64_t n_blocks, int use_trial, cudaStream_t stream) {
+  voxel_pass_mixed_batch_kernel<<<(unsigned)n_blocks, kVoxelThreads, 0, stream>>>(T, use_trial);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_scan_pass_mixed(const JobTable& T, int64_t n_blocks, cudaStream_t stream) {
+  scan_pass_mixed_batch_kernel<<<(unsigned)n_blocks, kScanThreads, 0, stream>>>(T);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scan_table(int32_t n_scans, const double* poses2, const double* sref, float* stab2, int buf,
+                              cudaStream_t stream) {
+  scan_table_kernel<<<(n_scans + 127) / 128, 128, 0, stream>>>(n_scans, poses2, sref, stab2, buf);
+  return cudaGetLastError();
+}
+
+}  // namespace mmba

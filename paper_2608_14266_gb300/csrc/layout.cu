@@ -350,8 +350,9 @@ __global__ void fill_sell_kernel(LoadInput in, const int32_t* vperm, const int32
 #pragma unroll
       for (int q = 0; q < 10; ++q) c[q] = 0.0;
     }
+    if (ve)
 #pragma unroll
-    for (int q = 0; q < 10; ++q) ve[q * n_elems + e] = c[q];
+      for (int q = 0; q < 10; ++q) ve[q * n_elems + e] = c[q];
     ve_scan[e] = scan;
   }
 }
@@ -382,6 +383,8 @@ __global__ void fill_scan_major_kernel(LoadInput in, const uint32_t* order, cons
   if (q >= in.n_obs) return;
   const int64_t o = order[q];
   const int32_t v = obs_vox[o];
+  se_vox[q] = vrank[v];
+  if (!se) return;
   double c[10];
   to_centred(in.agg + 10 * o, in.agg_form, c);
   const double k = vscale[v];
@@ -391,7 +394,6 @@ __global__ void fill_scan_major_kernel(LoadInput in, const uint32_t* order, cons
   const int64_t n = in.n_obs;
 #pragma unroll
   for (int a = 0; a < 10; ++a) se[a * n + q] = c[a];
-  se_vox[q] = vrank[v];
 }
 
 static int bit_width(uint64_t x) {
@@ -403,31 +405,37 @@ static int bit_width(uint64_t x) {
   return b;
 }
 
-cudaError_t build_layout(const LoadInput& in, int max_len, Allocator keep, Allocator temp, LayoutBuffers* out,
-                         cudaStream_t stream, int64_t* launches) {
+cudaError_t build_layout(const LoadInput& in, int max_len, bool fill_f64, Allocator keep, Allocator temp,
+                         LayoutBuffers* out, cudaStream_t stream, int64_t* launches) {
   const int64_t nv = in.n_voxels, no = in.n_obs;
   const int64_t n_slices = (nv + kSlice - 1) / kSlice;
   const int64_t nsort = nv > no ? nv : no;
-  // temporaries
+  // temporaries (the maps are kept when the FP32 copies will be rebuilt later)
+  Allocator maps = fill_f64 ? temp : keep;
   uint32_t* keys = (uint32_t*)temp.fn(temp.self, sizeof(uint32_t) * nsort);
   uint32_t* vals = (uint32_t*)temp.fn(temp.self, sizeof(uint32_t) * nsort);
   uint32_t* tk = (uint32_t*)temp.fn(temp.self, sizeof(uint32_t) * nsort);
   uint32_t* tv = (uint32_t*)temp.fn(temp.self, sizeof(uint32_t) * nsort);
   int64_t* scratch = (int64_t*)temp.fn(temp.self, sizeof(int64_t) * (radix_scratch_count(nsort) +
                                                                       scan_scratch_count(n_slices + no + 2)));
-  int32_t* vrank = (int32_t*)temp.fn(temp.self, sizeof(int32_t) * nv);
-  int32_t* obs_vox = (int32_t*)temp.fn(temp.self, sizeof(int32_t) * no);
-  double* vscale = (double*)temp.fn(temp.self, sizeof(double) * nv);
+  int32_t* vrank = (int32_t*)maps.fn(maps.self, sizeof(int32_t) * nv);
+  int32_t* obs_vox = (int32_t*)maps.fn(maps.self, sizeof(int32_t) * no);
+  double* vscale = (double*)maps.fn(maps.self, sizeof(double) * nv);
+  uint32_t* order = fill_f64 ? nullptr : (uint32_t*)keep.fn(keep.self, sizeof(uint32_t) * no);
   // persistent
   out->slice_off = (int64_t*)keep.fn(keep.self, sizeof(int64_t) * (n_slices + 1));
   out->vlen = (int32_t*)keep.fn(keep.self, sizeof(int32_t) * nv);
   out->vperm = (int32_t*)keep.fn(keep.self, sizeof(int32_t) * nv);
   out->scan_off = (int64_t*)keep.fn(keep.self, sizeof(int64_t) * (in.n_scans + 1));
-  out->se = (double*)keep.fn(keep.self, sizeof(double) * 10 * no);
+  out->se = fill_f64 ? (double*)keep.fn(keep.self, sizeof(double) * 10 * no) : nullptr;
   out->se_vox = (int32_t*)keep.fn(keep.self, sizeof(int32_t) * no);
   if (!keys || !vals || !tk || !tv || !scratch || !vrank || !obs_vox || !vscale || !out->slice_off || !out->vlen ||
-      !out->vperm || !out->scan_off || !out->se || !out->se_vox)
+      !out->vperm || !out->scan_off || (fill_f64 && !out->se) || (!fill_f64 && !order) || !out->se_vox)
     return cudaErrorMemoryAllocation;
+  out->vrank = vrank;
+  out->obs_vox = obs_vox;
+  out->vscale = vscale;
+  out->scan_order = order;
 
   // ---- voxel order: length-descending inside windows ----
   const int len_bits = bit_width((uint64_t)max_len);
@@ -448,9 +456,9 @@ cudaError_t build_layout(const LoadInput& in, int max_len, Allocator keep, Alloc
   RETURN_IF(cudaStreamSynchronize(stream));
   out->n_elems = n_elems;
   out->n_slices = n_slices;
-  out->ve = (double*)keep.fn(keep.self, sizeof(double) * 10 * n_elems);
+  out->ve = fill_f64 ? (double*)keep.fn(keep.self, sizeof(double) * 10 * n_elems) : nullptr;
   out->ve_scan = (int32_t*)keep.fn(keep.self, sizeof(int32_t) * n_elems);
-  if (!out->ve || !out->ve_scan) return cudaErrorMemoryAllocation;
+  if ((fill_f64 && !out->ve) || !out->ve_scan) return cudaErrorMemoryAllocation;
   fill_sell_kernel<<<(unsigned)((n_slices * kSlice + 255) / 256), 256, 0, stream>>>(
       in, out->vperm, out->vlen, out->slice_off, nv, out->ve, out->ve_scan, n_elems);
   ++*launches;
@@ -470,7 +478,9 @@ cudaError_t build_layout(const LoadInput& in, int max_len, Allocator keep, Alloc
   fill_scan_major_kernel<<<(unsigned)((no + 255) / 256), 256, 0, stream>>>(in, vals, obs_vox, vscale, vrank, out->se,
                                                                            out->se_vox);
   ++*launches;
-  return cudaGetLastError();
+  RETURN_IF(cudaGetLastError());
+  if (order) RETURN_IF(cudaMemcpyAsync(order, vals, sizeof(uint32_t) * no, cudaMemcpyDeviceToDevice, stream));
+  return cudaSuccess;
 }
 
 // ============================================================================

@@ -47,6 +47,92 @@ struct DevLayout {
   const int32_t* se_vox;     // n_obs
 };
 
+// Mixed-precision copies (FP32 per observation, re-centred).  For every
+// voxel i an anchor a_i (the FP32-representable rounding of its centroid at
+// the reference poses) and an orthonormal frame B_i (rows e1, e2, n: the
+// eigenvectors of its covariance there, normal last); for every scan j a
+// reference pose (R_ref,j, t_ref,j) with t_ref FP32-representable.  With
+// dR_j = R_j R_ref,j^T = I + E_j and dt_j = t_j - t_ref,j, an observation's
+// posed mean relative to its anchor is
+//   q_o - a_i = b_o + E_j l_o + dt_j,   l_o = b_o + (a_i - t_ref,j),
+// where b_o = R_ref m_o + t_ref - a_i is stored; every quantity is
+// plane-sized except the lever l_o, which only meets the small E_j.  E_j is
+// carried as a rotation vector phi and the coefficients of
+// E = a [phi]x + b [phi]x^2 (Rodrigues).
+//
+// The voxel pass stores each observation's scatter through its own
+// eigen-decomposition R_ref S R_ref^T = V diag(sigma) V^T (sigma and the
+// quaternion of V): one scan's view of a patch is planar, so its normal
+// variance sigma_3 keeps full FP32 relative precision.  The sums run in a
+// per-voxel frame B that follows the voxel's latest eigenvectors, so the
+// normal direction of the sums stays small; G = B dR V is the only rotation
+// applied per observation.
+struct DevMixed {
+  const float* ve32;     // SELL: b (3), sigma (3), quaternion of V (4), N (1); c * n_elems + e
+  float4* vstate;        // per sorted voxel, 2 x float4: quaternion of B; (centroid - anchor) world (3), 0
+  const float* se32;     // scan-major: b (3), (2/N_i) R_ref S R_ref^T (6), (2/N_i) N (1); c * n_obs + q
+  const float4* vanchor; // per sorted voxel: a (3), 0
+  const double* sref;    // per scan: R_ref (9), t_ref (3)
+  float* stab2;          // 2 buffers x n_scans x kTab: phi (3), a, b, dt (3), t_ref (3), 0
+  float* planes32_2;     // 2 buffers x n_voxels x 4: u (3), u . (c - a)
+};
+constexpr int kTab = 12;
+constexpr int kVe32 = 11;  // FP32 components per slot of the voxel-pass copy
+
+// Rotation matrix (row-major) of the unit quaternion (w, x, y, z).
+__device__ __forceinline__ void quat_to_mat_f(float w, float x, float y, float z, float* R) {
+  const float xx = x * x, yy = y * y, zz = z * z, xy = x * y, xz = x * z, yz = y * z, wx = w * x, wy = w * y,
+              wz = w * z;
+  R[0] = 1.f - 2.f * (yy + zz);
+  R[1] = 2.f * (xy - wz);
+  R[2] = 2.f * (xz + wy);
+  R[3] = 2.f * (xy + wz);
+  R[4] = 1.f - 2.f * (xx + zz);
+  R[5] = 2.f * (yz - wx);
+  R[6] = 2.f * (xz - wy);
+  R[7] = 2.f * (yz + wx);
+  R[8] = 1.f - 2.f * (xx + yy);
+}
+
+// Unit quaternion (w, x, y, z) of a rotation matrix (row-major), from the
+// largest of 1 + tr, 1 + 2 R_kk - tr (Shepperd's method, J. Guidance and
+// Control 1, 1978), normalised.
+template <typename T>
+__device__ __forceinline__ void mat_to_quat(const T* R, T q[4]) {
+  const T tr = R[0] + R[4] + R[8];
+  T w, x, y, z;
+  if (tr >= R[0] && tr >= R[4] && tr >= R[8]) {
+    const T s = sqrt(T(1) + tr) * T(2);
+    w = T(0.25) * s;
+    x = (R[7] - R[5]) / s;
+    y = (R[2] - R[6]) / s;
+    z = (R[3] - R[1]) / s;
+  } else if (R[0] >= R[4] && R[0] >= R[8]) {
+    const T s = sqrt(T(1) + R[0] - R[4] - R[8]) * T(2);
+    w = (R[7] - R[5]) / s;
+    x = T(0.25) * s;
+    y = (R[1] + R[3]) / s;
+    z = (R[2] + R[6]) / s;
+  } else if (R[4] >= R[8]) {
+    const T s = sqrt(T(1) + R[4] - R[0] - R[8]) * T(2);
+    w = (R[2] - R[6]) / s;
+    x = (R[1] + R[3]) / s;
+    y = T(0.25) * s;
+    z = (R[5] + R[7]) / s;
+  } else {
+    const T s = sqrt(T(1) + R[8] - R[0] - R[4]) * T(2);
+    w = (R[3] - R[1]) / s;
+    x = (R[2] + R[6]) / s;
+    y = (R[5] + R[7]) / s;
+    z = T(0.25) * s;
+  }
+  const T inv = T(1) / sqrt(w * w + x * x + y * y + z * z);
+  q[0] = w * inv;
+  q[1] = x * inv;
+  q[2] = y * inv;
+  q[3] = z * inv;
+}
+
 struct DevState {
   double cost;
   double mu;
@@ -71,6 +157,44 @@ struct DevState {
   int32_t hess_mode;
   int32_t scan_pending;     // an accepted step needs g, H at the new poses
 };
+
+// One job of a batch: everything its kernels touch.  A batch launches each
+// kernel kind once per iteration over all its jobs; block b of a launch
+// belongs to the job whose prefix range holds b, and runs exactly the block
+// that the job's own launch would run, so a job's results do not depend on
+// the batch it is in.
+struct JobView {
+  DevLayout L;
+  DevMixed X;
+  DevState* st;
+  double* poses2;
+  double* planes2;
+  double* gH;
+  double* pred_part;
+  double* cost_part;
+  int64_t n_cost;
+};
+
+struct JobTable {
+  const JobView* jobs;
+  const int64_t* vblk;   // n_jobs + 1: prefix of voxel-pass blocks
+  const int64_t* sblk;   // n_jobs + 1: prefix of scan-pass blocks (one per scan)
+  const int64_t* oblk;   // n_jobs + 1: prefix of solve blocks
+  int32_t n_jobs;
+};
+
+// job owning block b: the largest i with prefix[i] <= b
+__device__ __forceinline__ int find_job(const int64_t* prefix, int n_jobs, int64_t b) {
+  int lo = 0, hi = n_jobs;  // prefix[lo] <= b < prefix[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (prefix[mid] <= b)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return lo;
+}
 
 // ---- small FP64 device math ------------------------------------------------
 
@@ -139,6 +263,112 @@ __device__ inline void eig3_sym(const double* a_in, double lam[3], double vec[9]
   }
 }
 
+// FP32 counterpart of eig3_sym for matrices expressed in a frame where they
+// are close to diagonal (small off-diagonal entries keep the smallest
+// eigenvalue relatively accurate); at most 8 sweeps.
+__device__ __forceinline__ void jacobi_rotate_f(float& app, float& aqq, float& apq, float& arp, float& arq, float* vp,
+                                                float* vq) {
+  float theta = (aqq - app) / (2.0f * apq);
+  float t = fabsf(theta) > 1e18f ? 0.5f / theta
+                                 : copysignf(1.0f, theta) / (fabsf(theta) + sqrtf(fmaf(theta, theta, 1.0f)));
+  float c = rsqrtf(fmaf(t, t, 1.0f));
+  float s = t * c;
+  app = fmaf(-t, apq, app);
+  aqq = fmaf(t, apq, aqq);
+  apq = 0.0f;
+  float rp = arp, rq = arq;
+  arp = c * rp - s * rq;
+  arq = s * rp + c * rq;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    float x = vp[k], y = vq[k];
+    vp[k] = c * x - s * y;
+    vq[k] = s * x + c * y;
+  }
+}
+
+__device__ __forceinline__ bool jacobi_small_f(float apq, float app, float aqq) {
+  return apq == 0.0f || fabsf(apq) <= 1e-9f * sqrtf(fabsf(app * aqq));
+}
+
+__device__ inline void eig3_sym_f(const float* a_in, float lam[3], float vec[9]) {
+  float a00 = a_in[0], a01 = a_in[1], a02 = a_in[2], a11 = a_in[3], a12 = a_in[4], a22 = a_in[5];
+  float v0[3] = {1.f, 0.f, 0.f}, v1[3] = {0.f, 1.f, 0.f}, v2[3] = {0.f, 0.f, 1.f};
+  for (int sweep = 0; sweep < 8; ++sweep) {
+    bool done = true;
+    if (!jacobi_small_f(a01, a00, a11)) {
+      jacobi_rotate_f(a00, a11, a01, a02, a12, v0, v1);
+      done = false;
+    }
+    if (!jacobi_small_f(a02, a00, a22)) {
+      jacobi_rotate_f(a00, a22, a02, a01, a12, v0, v2);
+      done = false;
+    }
+    if (!jacobi_small_f(a12, a11, a22)) {
+      jacobi_rotate_f(a11, a22, a12, a01, a02, v1, v2);
+      done = false;
+    }
+    if (done) break;
+  }
+  float d[3] = {a00, a11, a22};
+  int i0 = 0, i1 = 1, i2 = 2, t;
+  if (d[i1] < d[i0]) { t = i0; i0 = i1; i1 = t; }
+  if (d[i2] < d[i1]) { t = i1; i1 = i2; i2 = t; }
+  if (d[i1] < d[i0]) { t = i0; i0 = i1; i1 = t; }
+  const float* vs[3] = {v0, v1, v2};
+  int order[3] = {i0, i1, i2};
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    lam[c] = d[order[c]];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) vec[3 * c + r] = vs[order[c]][r];
+  }
+}
+
+// Per-scan FP32 table entry for the mixed path from an FP64 pose P and its
+// reference (R_ref, t_ref): dR = R R_ref^T = Exp(phi), with
+// phi = theta * v / |v|, v the axial vector of (dR - dR^T)/2 and
+// theta = atan2(|v|, (tr dR - 1)/2); a = sin(theta)/theta,
+// b = 2 sin^2(theta/2)/theta^2; dt = t - t_ref.
+__device__ inline void scan_table_entry(const double* P, const double* ref, float* out) {
+  double D[9];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) D[3 * r + c] = P[3 * r] * ref[3 * c] + P[3 * r + 1] * ref[3 * c + 1] + P[3 * r + 2] * ref[3 * c + 2];
+  const double vx = 0.5 * (D[7] - D[5]), vy = 0.5 * (D[2] - D[6]), vz = 0.5 * (D[3] - D[1]);
+  const double s2 = vx * vx + vy * vy + vz * vz;
+  const double sn = sqrt(s2);
+  const double cs = 0.5 * (D[0] + D[4] + D[8] - 1.0);
+  double f, a, b;
+  if (sn < 0.1 && cs > 0.0) {
+    // th = asin(sn): th / sn = 1 + s^2/6 + 3 s^4/40 + 5 s^6/112 + 35 s^8/1152 + ..., and the
+    // Rodrigues coefficients from their series in th^2 (the table is stored in FP32)
+    f = 1.0 + s2 * (1.0 / 6 + s2 * (3.0 / 40 + s2 * (5.0 / 112 + s2 * (35.0 / 1152))));
+    const double t2 = f * f * s2;
+    a = 1.0 + t2 * (-1.0 / 6 + t2 * (1.0 / 120 + t2 * (-1.0 / 5040)));
+    b = 0.5 + t2 * (-1.0 / 24 + t2 * (1.0 / 720 + t2 * (-1.0 / 40320)));
+  } else {
+    const double th = atan2(sn, cs);
+    f = sn > 0.0 ? th / sn : 0.0;  // th = pi exactly has no axis in the skew part
+    const double sh = sin(0.5 * th);
+    a = sin(th) / th;
+    b = 2.0 * sh * sh / (th * th);
+  }
+  out[0] = (float)(f * vx);
+  out[1] = (float)(f * vy);
+  out[2] = (float)(f * vz);
+  out[3] = (float)a;
+  out[4] = (float)b;
+  out[5] = (float)(P[9] - ref[9]);
+  out[6] = (float)(P[10] - ref[10]);
+  out[7] = (float)(P[11] - ref[11]);
+  out[8] = (float)ref[9];
+  out[9] = (float)ref[10];
+  out[10] = (float)ref[11];
+  out[11] = 0.0f;
+}
+
 // LDL^T of the symmetric 6x6 A (full, row-major) without pivoting, then
 // solve A x = b.  Returns false if a pivot is not positive and finite.
 __device__ inline bool ldlt6_solve(const double* A, const double* b, double* x) {
@@ -185,6 +415,10 @@ __device__ inline bool ldlt6_solve(const double* A, const double* b, double* x) 
 // Exp map of so(3) (Rodrigues' formula), R row-major.  Below |phi| = 1e-6 the
 // second-order series I + [phi]x + [phi]x^2 / 2 is used; otherwise
 // R = I + (sin th / th) K + (2 sin^2(th/2) / th^2) K^2.
+// Between 1e-6 and 0.1 rad the coefficients come from their Taylor series
+// sin(th)/th = sum (-1)^k th^2k / (2k+1)!, (1 - cos th)/th^2 = sum
+// (-1)^k th^2k / (2k+2)! to th^8 (truncation below 1e-17 there), which saves
+// the FP64 sin/cos.
 __device__ inline void so3_exp(const double* phi, double* R) {
   double x = phi[0], y = phi[1], z = phi[2];
   double th2 = x * x + y * y + z * z;
@@ -193,6 +427,9 @@ __device__ inline void so3_exp(const double* phi, double* R) {
   if (th < 1e-6) {
     a = 1.0;
     b = 0.5;
+  } else if (th < 0.1) {
+    a = 1.0 + th2 * (-1.0 / 6 + th2 * (1.0 / 120 + th2 * (-1.0 / 5040 + th2 * (1.0 / 362880))));
+    b = 0.5 + th2 * (-1.0 / 24 + th2 * (1.0 / 720 + th2 * (-1.0 / 40320 + th2 * (1.0 / 3628800))));
   } else {
     double sh = sin(0.5 * th);
     a = sin(th) / th;
@@ -210,15 +447,31 @@ __device__ inline void so3_exp(const double* phi, double* R) {
   R[8] = 1.0 + b * (z * z - th2);
 }
 
-// Deterministic block-wide sum (fixed shape for a given blockDim).
+// This thread's share of sum(p[0..n)) with a fixed assignment of indices:
+// four independent load streams so the loads are in flight together.
 template <int kThreads>
-__device__ inline double block_sum(double v, double* smem /* kThreads / 32 */) {
+__device__ inline double strided_sum(const double* __restrict__ p, int64_t n) {
+  double c0 = 0.0, c1 = 0.0, c2 = 0.0, c3 = 0.0;
+  int64_t k = threadIdx.x;
+  for (; k + 3 * kThreads < n; k += 4 * kThreads) {
+    c0 += p[k];
+    c1 += p[k + kThreads];
+    c2 += p[k + 2 * kThreads];
+    c3 += p[k + 3 * kThreads];
+  }
+  for (; k < n; k += kThreads) c0 += p[k];
+  return (c0 + c1) + (c2 + c3);
+}
+
+// Deterministic block-wide sum (fixed shape for a given blockDim).
+template <int kThreads, typename T = double>
+__device__ inline T block_sum(T v, T* smem /* kThreads / 32 */) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   if (l == 0) smem[w] = v;
   __syncthreads();
-  double r = 0.0;
+  T r = T(0);
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int k = 0; k < kThreads / 32; ++k) r += smem[k];

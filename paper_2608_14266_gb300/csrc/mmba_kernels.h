@@ -10,17 +10,28 @@ namespace mmba {
 
 constexpr int kVoxelThreads = 128;
 constexpr int kScanThreads = 128;
-constexpr int kDecideThreads = 256;
+constexpr int kDecideThreads = 1024;
+constexpr int kSolveThreads = 64;  // FP64-serial per scan: small blocks spread the scans over every SM
 
 inline int64_t voxel_pass_blocks(int64_t n_voxels) { return (n_voxels + kVoxelThreads - 1) / kVoxelThreads; }
+inline int64_t solve_blocks(int64_t n_scans) { return (n_scans + kSolveThreads - 1) / kSolveThreads; }
+
+// ---- batched launches over a job table (one launch per kind for all jobs) ----
+cudaError_t launch_batch_solve(const JobTable& T, int64_t n_blocks, cudaStream_t stream);
+cudaError_t launch_batch_decide(const JobTable& T, cudaStream_t stream);
+cudaError_t launch_batch_voxel_pass_f64(const JobTable& T, int64_t n_blocks, int use_trial, cudaStream_t stream);
+cudaError_t launch_batch_scan_pass_f64(const JobTable& T, int64_t n_blocks, cudaStream_t stream);
+cudaError_t launch_batch_voxel_pass_mixed(const JobTable& T, int64_t n_blocks, int use_trial, cudaStream_t stream);
+cudaError_t launch_batch_scan_pass_mixed(const JobTable& T, int64_t n_blocks, cudaStream_t stream);
 
 // ---- iteration (FP64) ----
 cudaError_t launch_voxel_pass_f64(const DevLayout& L, const double* poses2, double* planes2, double* full_out,
                                   double* cost_part, const DevState* st, int use_trial, cudaStream_t stream);
 cudaError_t launch_scan_pass_f64(const DevLayout& L, const double* poses2, const double* planes2, double* gH,
                                  const DevState* st, int force, cudaStream_t stream);
+// sref/stab2 non-null: also write the trial FP32 scan table (mixed precision)
 cudaError_t launch_solve_f64(const DevLayout& L, double* poses2, const double* gH, double* pred_part, DevState* st,
-                             cudaStream_t stream);
+                             const double* sref, float* stab2, cudaStream_t stream);
 cudaError_t launch_decide(const double* cost_part, int64_t n_cost, const double* pred_part, int64_t n_pred,
                           DevState* st, int mode, cudaStream_t stream);
 
@@ -76,11 +87,39 @@ struct LayoutBuffers {
   int32_t* se_vox;
   int64_t n_elems;
   int64_t n_slices;
+  // kept only when the FP64 copies are not built (mixed precision)
+  int32_t* vrank;        // input voxel -> sorted position
+  int32_t* obs_vox;      // observation -> input voxel
+  double* vscale;        // input voxel -> 2 / N_i
+  uint32_t* scan_order;  // scan-major position -> observation
 };
 // `keep` allocates the buffers of *out, `temp` the build's temporaries (the
 // caller frees those after the stream has drained).
-cudaError_t build_layout(const LoadInput& in, int max_len, Allocator keep, Allocator temp, LayoutBuffers* out,
-                         cudaStream_t stream, int64_t* launches);
+// With fill_f64 the FP64 cluster copies are filled; without, only the index
+// structures are built and the maps above are kept for the FP32 copies.
+cudaError_t build_layout(const LoadInput& in, int max_len, bool fill_f64, Allocator keep, Allocator temp,
+                         LayoutBuffers* out, cudaStream_t stream, int64_t* launches);
+
+// ---- mixed precision ----
+cudaError_t launch_voxel_pass_mixed(const DevLayout& L, const DevMixed& X, double* full_out, double* cost_part,
+                                    const DevState* st, int use_trial, cudaStream_t stream);
+cudaError_t launch_scan_pass_mixed(const DevLayout& L, const DevMixed& X, const double* poses2, double* gH,
+                                   const DevState* st, int force, cudaStream_t stream);
+cudaError_t launch_scan_table(int32_t n_scans, const double* poses2, const double* sref, float* stab2, int buf,
+                              cudaStream_t stream);
+// Build (or rebuild) the FP32 copies, frames, anchors and reference poses at
+// the poses of buffer 0 of poses2.
+struct MixedBuffers {
+  float* ve32;
+  float4* vstate;
+  float* se32;
+  float4* vanchor;
+  double* sref;
+  float* stab2;
+  float* planes32_2;
+};
+cudaError_t build_mixed(const LoadInput& in, const LayoutBuffers& lb, const double* poses2, MixedBuffers& mb,
+                        cudaStream_t stream, int64_t* launches);
 
 // points -> centred clusters
 cudaError_t launch_aggregate_points(int64_t n_obs, const int64_t* point_off, const double* points, double* agg_out,

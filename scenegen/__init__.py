@@ -36,6 +36,11 @@ _lock = threading.Lock()
 _lib = None
 
 
+_GPU_SRC = os.path.join(_HERE, "scenegen_gpu.cu")
+_GPU_LIB = os.path.join(_HERE, "libscenegen_gpu.so")
+_gpu_lib = None
+
+
 def build(force: bool = False) -> str:
     """Compile the generator into a shared library beside its source."""
     stale = (not os.path.exists(_LIB)) or any(
@@ -46,6 +51,31 @@ def build(force: bool = False) -> str:
                                "-lm", "-lpthread"])
         os.replace(tmp, _LIB)
     return _LIB
+
+
+def build_gpu(force: bool = False) -> str:
+    """Compile the CUDA point generator (sm_103a) beside its source."""
+    import shutil
+    stale = (not os.path.exists(_GPU_LIB)) or os.path.getmtime(_GPU_SRC) > os.path.getmtime(_GPU_LIB)
+    if force or stale:
+        nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+        tmp = _GPU_LIB + f".tmp{os.getpid()}"
+        subprocess.check_call([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-Xcompiler", "-fPIC",
+                               "-shared", "-o", tmp, _GPU_SRC])
+        os.replace(tmp, _GPU_LIB)
+    return _GPU_LIB
+
+
+def _load_gpu():
+    global _gpu_lib
+    with _lock:
+        if _gpu_lib is None:
+            lib = ctypes.CDLL(build_gpu())
+            lib.sgd_points.restype = ctypes.c_int
+            lib.sgd_points.argtypes = [ctypes.c_uint64, ctypes.c_int32, ctypes.c_double] + [ctypes.c_void_p] * 5 + \
+                [ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]
+            _gpu_lib = lib
+    return _gpu_lib
 
 
 class _Params(ctypes.Structure):
@@ -170,6 +200,28 @@ class Scene:
         rc = _load().sg_points(self._handle, obs_begin, obs_end, out.ctypes.data, nthreads)
         if rc != 0:
             raise ValueError("bad observation range")
+        return out
+
+    def points_device(self, obs_begin: int, obs_end: int, out, stream=None):
+        """Points of observations [obs_begin, obs_end) generated on the GPU into
+        `out`, a CUDA float64 tensor of shape (n, 3); same streams as points()."""
+        import torch
+        dev = out.device
+        cache = getattr(self, "_dev_cache", None)
+        if cache is None or cache[0] != dev:
+            obs_voxel = np.repeat(np.arange(self.n_voxels, dtype=np.int32), np.diff(self.voxel_off))
+            T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+            cache = (dev, T(self.plane), T(self.extent), T(self.pose_gt), T(self.obs_scan), T(obs_voxel))
+            self._dev_cache = cache
+        _, plane, extent, pose, oscan, ovox = cache
+        n = (obs_end - obs_begin) * self.params.pts_per_obs
+        assert out.dtype == torch.float64 and out.is_contiguous() and tuple(out.shape) == (n, 3)
+        s = (stream if stream is not None else torch.cuda.current_stream()).cuda_stream
+        rc = _load_gpu().sgd_points(self.params.seed, self.params.pts_per_obs, self.params.noise_sigma,
+                                    plane.data_ptr(), extent.data_ptr(), pose.data_ptr(), oscan.data_ptr(),
+                                    ovox.data_ptr(), obs_begin, obs_end, out.data_ptr(), s)
+        if rc != 0:
+            raise RuntimeError(f"scenegen GPU point generation failed (CUDA error {rc})")
         return out
 
     def close(self):

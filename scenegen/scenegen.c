@@ -202,25 +202,31 @@ static int cmp_i32(const void* a, const void* b) {
   return (x > y) - (x < y);
 }
 
-/* Pick the observing scans of voxel i (sorted ascending, distinct).  Writes
- * at most cap entries to out and returns the count.  cand/ncand: candidate
- * scans (NULL = all scans). */
+/* Pick the observing scans of voxel i (sorted ascending, distinct) and return
+ * their count.  cand/ncand: candidate scans (NULL = all scans).  k distinct
+ * pool positions are drawn with Floyd's algorithm (R. W. Floyd, "A sample of
+ * brilliance", CACM 1987): for t = pool-k .. pool-1 draw r in [0, t] and take
+ * r, or t if r was taken already. */
 static int32_t pick_scans(const sg_params* p, int64_t i, const int32_t* cand, int32_t ncand, int32_t* out,
                           int32_t* work) {
+  (void)work;
   rng_t rc = rng_make(p->seed, ST_OBS_COUNT, (uint64_t)i);
   int32_t k = (int32_t)rng_int(&rc, p->obs_min, p->obs_max);
   int32_t pool = cand ? ncand : p->n_scans;
   if (k > pool) k = pool;
   rng_t rp = rng_make(p->seed, ST_OBS_PICK, (uint64_t)i);
-  /* partial Fisher-Yates over the candidate pool */
-  for (int32_t t = 0; t < pool; ++t) work[t] = cand ? cand[t] : t;
-  for (int32_t t = 0; t < k; ++t) {
-    int32_t r = (int32_t)rng_int(&rp, t, pool - 1);
-    int32_t tmp = work[t];
-    work[t] = work[r];
-    work[r] = tmp;
-    out[t] = work[t];
+  int32_t n = 0;
+  for (int32_t t = pool - k; t < pool; ++t) {
+    int32_t r = (int32_t)rng_int(&rp, 0, t);
+    int taken = 0;
+    for (int32_t q = 0; q < n; ++q)
+      if (out[q] == r) {
+        taken = 1;
+        break;
+      }
+    out[n++] = taken ? t : r;
   }
+  for (int32_t q = 0; q < n; ++q) out[q] = cand ? cand[out[q]] : out[q];
   qsort(out, (size_t)k, sizeof(int32_t), cmp_i32);
   return k;
 }
@@ -299,7 +305,6 @@ sg_scene* sg_create(const sg_params* params) {
               if (dx * dx + dy * dy <= p->view_radius * p->view_radius) cand[nc++] = j;
             }
           }
-        qsort(cand, (size_t)nc, sizeof(int32_t), cmp_i32);
         cptr = cand;
         if (nc == 0) { /* no scan in range: fall back to scan nearest the centre */
           double best = 1e300;

@@ -1,0 +1,129 @@
+"""Parity of the mixed-precision CUDA path with the FP64 oracle.
+
+Tolerances for the mixed path: poses within 1e-6 rad and 1e-5 m, cost within
+a relative 1e-6 (FP32 per observation on re-centred clusters; FP64 per voxel
+block sum, per-scan solve and pose composition).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import scenegen
+from tests._util import pose_errors, tiny_scene
+
+pytestmark = pytest.mark.gpu
+
+ROT_TOL, TRANS_TOL, COST_TOL = 1e-6, 1e-5, 1e-6
+
+
+@pytest.fixture(scope="module")
+def mm():
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2608_14266_gb300 as mm
+    assert torch.cuda.is_available()
+    return mm
+
+
+def _mixed(mm, **cfg):
+    return mm.BundleAdjuster(precision=mm.BA_MIXED, **cfg)
+
+
+def test_mixed_cost_planes_gradient(mm):
+    s, pts, po, raw, cen = tiny_scene()
+    prob = oracle.ObsProblem(s.n_scans, s.voxel_off, s.obs_scan, cen)
+    for poses in (s.pose_init, s.pose_gt):
+        c_ref, planes = oracle.voxel_pass(prob, poses)
+        g_ref, H_ref = oracle.grad_hess(prob, poses, planes)
+        with _mixed(mm) as ba:
+            ba.load_observations(s.n_scans, s.voxel_off, s.obs_scan, cen, poses)
+            assert ba.cost() == pytest.approx(c_ref, rel=COST_TOL)
+            pl = ba.planes()
+            np.testing.assert_allclose(pl[:, 0], planes[:, 0], rtol=1e-4, atol=1e-9)
+            # FP32 normals: unit length and direction to a few FP32 ulps
+            dots = np.abs(np.sum(pl[:, 3:6] * planes[:, 3:6], axis=1))
+            assert np.all(np.abs(dots - 1) < 1e-6)
+            g, H = ba.gradient()
+            np.testing.assert_allclose(g, g_ref, rtol=0, atol=1e-5 * np.abs(g_ref).max())
+            for j in range(s.n_scans):
+                np.testing.assert_allclose(H[j], H_ref[j], rtol=0, atol=1e-5 * np.abs(H_ref[j]).max())
+
+
+def test_mixed_each_iteration_from_the_oracle_state(mm):
+    s, pts, po, raw, cen = tiny_scene()
+    prob = oracle.ObsProblem(s.n_scans, s.voxel_off, s.obs_scan, cen)
+    lm = oracle.LM(prob, s.pose_init)
+    with _mixed(mm) as ba:
+        ba.load_observations(s.n_scans, s.voxel_off, s.obs_scan, cen, s.pose_init)
+        for k in range(12):
+            c_prev = lm.cost
+            ba.set_state(lm.poses, lm.mu, lm.nu)
+            assert ba.cost() == pytest.approx(lm.cost, rel=COST_TOL)
+            st = ba.iterate(1)
+            acc = lm.step()
+            if bool(st["last_accepted"]) != acc:
+                assert abs(lm.st.last_trial_cost - c_prev) <= COST_TOL * c_prev, k
+                continue
+            assert st["cost"] == pytest.approx(lm.cost, rel=COST_TOL)
+            r, t = pose_errors(ba.poses(), lm.poses)
+            assert r < ROT_TOL and t < TRANS_TOL, (k, r, t)
+
+
+def test_mixed_twenty_iterations_match_oracle(mm):
+    s, pts, po, raw, cen = tiny_scene()
+    prob = oracle.ObsProblem(s.n_scans, s.voxel_off, s.obs_scan, cen)
+    lm = oracle.LM(prob, s.pose_init)
+    for _ in range(20):
+        lm.step()
+    with _mixed(mm) as ba:
+        ba.load_points(s.n_scans, s.voxel_off, s.obs_scan, po, pts, s.pose_init)
+        st = ba.iterate(20)
+        assert st["accepted"] == lm.st.accepted
+        assert st["cost"] == pytest.approx(lm.cost, rel=COST_TOL)
+        r, t = pose_errors(ba.poses(), lm.poses)
+        assert r < ROT_TOL and t < TRANS_TOL, (r, t)
+
+
+def test_mixed_mid_workload(mm):
+    """~1.2M clusters: cost and one iteration element by element, then ten
+    iterations of trajectory."""
+    s = scenegen.make_scene(scenegen.config("mid"))
+    pts = s.points()
+    po = s.point_offsets()
+    cen = oracle.points_to_centred(po, pts)
+    prob = oracle.ObsProblem(s.n_scans, s.voxel_off, s.obs_scan, cen)
+    lm = oracle.LM(prob, s.pose_init)
+    with _mixed(mm) as ba:
+        ba.load_points(s.n_scans, s.voxel_off, s.obs_scan, po, pts, s.pose_init)
+        del pts
+        assert ba.cost() == pytest.approx(lm.cost, rel=COST_TOL)
+        g, H = ba.gradient()
+        np.testing.assert_allclose(g, lm.g, rtol=0, atol=1e-5 * np.abs(lm.g).max())
+        for k in range(10):
+            st = ba.iterate(1)
+            acc = lm.step()
+            assert bool(st["last_accepted"]) == acc, k
+            assert st["cost"] == pytest.approx(lm.cost, rel=COST_TOL), k
+            r, t = pose_errors(ba.poses(), lm.poses)
+            assert r < ROT_TOL and t < TRANS_TOL, (k, r, t)
+
+
+def test_mixed_matches_fp64_path_on_city_slice(mm):
+    """A 0.1-scale city scene (1,000 scans, 50,000 voxels, 200 m levers): mixed
+    and FP64 GPU paths agree after 10 iterations within the mixed tolerance."""
+    p = scenegen.config("city", n_scans=1000, n_voxels=50000, box=(632.0, 632.0, 50.0))
+    s = scenegen.make_scene(p)
+    pts = s.points()
+    po = s.point_offsets()
+    with _mixed(mm) as a, mm.BundleAdjuster() as b:
+        a.load_points(s.n_scans, s.voxel_off, s.obs_scan, po, pts, s.pose_init)
+        b.load_points(s.n_scans, s.voxel_off, s.obs_scan, po, pts, s.pose_init)
+        assert a.cost() == pytest.approx(b.cost(), rel=COST_TOL)
+        for k in range(10):
+            sa = a.iterate(1)
+            sb = b.iterate(1)
+            assert sa["last_accepted"] == sb["last_accepted"]
+            assert sa["cost"] == pytest.approx(sb["cost"], rel=COST_TOL), k
+        r, t = pose_errors(a.poses(), b.poses())
+        assert r < ROT_TOL and t < TRANS_TOL, (r, t)
