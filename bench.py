@@ -44,10 +44,12 @@ VOXEL_PASS_FLOP_PER_OBS = 121
 # bytes one voxel-pass launch must move per observation slot: 10 doubles + a
 # 4-byte scan index (the pose table and per-voxel outputs are small)
 VOXEL_PASS_BYTES_PER_ELEM = 84
-# mixed voxel pass: per observation 10 floats + a 4-byte scan index; per voxel
-# the anchor and frame (12 floats), its length (4 B), the plane written (16 B)
-MIXED_VOXEL_BYTES_PER_OBS = 44
-MIXED_VOXEL_BYTES_PER_VOXEL = 68
+# mixed voxel pass: per observation one 48-byte slot (offset and N, scatter
+# eigenvalues and scan index, eigenvector quaternion); per voxel its length
+# (4 B), anchor (16 B), frame and centroid read and written (2 x 32 B) and the
+# plane written (16 B)
+MIXED_VOXEL_BYTES_PER_OBS = 48
+MIXED_VOXEL_BYTES_PER_VOXEL = 100
 
 
 def _args():
@@ -56,7 +58,12 @@ def _args():
     ap.add_argument("--steps", type=int, default=3000, help="timed LM iterations per rank")
     ap.add_argument("--warmup", type=int, default=30, help="untimed warm-up iterations")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["city", "mid", "tiny"], default="city")
+    ap.add_argument("--workload", choices=["city", "mid", "tiny", "batched", "served"], default="city")
+    ap.add_argument("--jobs", type=int, default=256, help="jobs of the batched / served workloads")
+    ap.add_argument("--fp64-jobs", type=int, default=256, help="of which solved on the plain FP64 path too")
+    ap.add_argument("--rate", type=float, default=200.0, help="served: Poisson arrival rate (jobs/s)")
+    ap.add_argument("--budget-gb", type=float, default=120.0, help="served: device memory budget")
+    ap.add_argument("--chunk", type=int, default=8, help="batched / served: LM iterations per round")
     ap.add_argument("--iters-per-solve", type=int, default=30)
     ap.add_argument("--e2e-jobs", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -170,6 +177,34 @@ def device_clusters(scene, torch, mm, chunk_obs: int = 1 << 20):
         mm.ba_aggregate_points(po, pts, agg[o0:o1], stream=torch.cuda.current_stream())
         torch.cuda.current_stream().synchronize()
     return agg
+
+
+def device_clusters_gpu(scene, torch, mm, chunk_obs: int = 1 << 20):
+    """Raw points generated on the GPU in chunks, clustered on the GPU."""
+    dev = torch.device("cuda")
+    n_obs, npo = scene.n_obs, scene.params.pts_per_obs
+    agg = torch.empty((n_obs, 10), dtype=torch.float64, device=dev)
+    buf = torch.empty((min(chunk_obs, n_obs) * npo, 3), dtype=torch.float64, device=dev)
+    for o0 in range(0, n_obs, chunk_obs):
+        o1 = min(n_obs, o0 + chunk_obs)
+        n = o1 - o0
+        pts = buf[: n * npo]
+        scene.points_device(o0, o1, pts)
+        po = torch.arange(n + 1, dtype=torch.int64, device=dev) * npo
+        mm.ba_aggregate_points(po, pts, agg[o0:o1], stream=torch.cuda.current_stream())
+    del buf
+    return agg
+
+
+def job_params(scenegen, k, scans_min, scans_max, base_seed):
+    """One job of the many-job workloads: scans log-uniform in [min, max],
+    voxels = 50 x scans, 5-30 observations per voxel, 32 points each, 2 cm
+    noise, 0.5 deg / 10 cm initial perturbation, patches in a 50 m cube."""
+    import numpy as np
+    rng = np.random.default_rng(base_seed + k)
+    n_scans = int(round(math.exp(rng.uniform(math.log(scans_min), math.log(scans_max)))))
+    return scenegen.SceneParams(n_scans=n_scans, n_voxels=50 * n_scans, obs_min=5, obs_max=30, pts_per_obs=32,
+                                noise_sigma=0.02, rot_sigma_deg=0.5, trans_sigma=0.10, seed=base_seed + k)
 
 
 def kernel_source_hash(kernel: str = "voxel_pass_f64") -> str:
@@ -352,27 +387,17 @@ def run_ours(args):
     import paper_2608_14266_gb300 as mm
     import scenegen
 
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_2608_14266_gb300 import replicas
+    rank, world, local = replicas.rank_info()
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    group = replicas.Group(dist, torch.device("cuda", local))
+    barrier, max_over_ranks = group.barrier, group.max
 
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-
-    def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=torch.device("cuda", local))
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
-    scene = scenegen.make_scene(scene_params(scenegen, args, rank))
+    scene = scenegen.make_scene(scene_params(scenegen, args, replicas.scene_rep(rank)))
     dev = torch.device("cuda", local)
     agg = device_clusters(scene, torch, mm)
     inputs = (torch.from_numpy(scene.voxel_off).to(dev), torch.from_numpy(scene.obs_scan).to(dev), agg,
@@ -426,7 +451,7 @@ def run_ours(args):
     if not args.no_cpu_baseline and world == 1:
         ips, dt, sample = time_oracle(scene, 2, 1, args.cpu_seconds)
         cpu = {"value": ips, "unit": "iter/s", "cores": 1, "kind": "oracle", "sample": sample}
-    per_obs = 44 if args.precision == "mixed" else 84
+    per_obs = MIXED_VOXEL_BYTES_PER_OBS if args.precision == "mixed" else VOXEL_PASS_BYTES_PER_ELEM
     line = {
         "metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -453,10 +478,173 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def _load_job(mm, torch, scene, prec, stream, **cfg):
+    dev = torch.device("cuda")
+    agg = device_clusters_gpu(scene, torch, mm)
+    ba = mm.BundleAdjuster(precision=prec, cuda_stream=stream, **cfg)
+    ba.load_observations(scene.n_scans, torch.from_numpy(scene.voxel_off).to(dev),
+                         torch.from_numpy(scene.obs_scan).to(dev), agg, torch.from_numpy(scene.pose_init).to(dev))
+    return ba
+
+
+def _pose_diff(P, Q):
+    import numpy as np
+    R1 = P[:, :9].reshape(-1, 3, 3)
+    R2 = Q[:, :9].reshape(-1, 3, 3)
+    D = np.einsum("nij,nkj->nik", R1, R2)
+    ang = np.arctan2(0.5 * np.linalg.norm(np.stack([D[:, 2, 1] - D[:, 1, 2], D[:, 0, 2] - D[:, 2, 0],
+                                                    D[:, 1, 0] - D[:, 0, 1]], 1), axis=1),
+                     0.5 * (np.trace(D, axis1=1, axis2=2) - 1.0))
+    return float(ang.max()), float(np.abs(P[:, 9:] - Q[:, 9:]).max())
+
+
+SOLVE_CFG = dict(rel_tol=1e-8, max_iters=200, max_consec_reject=10)
+
+
+def run_batched(args):
+    """Many independent jobs solved together in one batch (mixed precision)
+    against the same jobs solved one after another on the plain FP64 path."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2608_14266_gb300 as mm
+    import scenegen
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    scenes = [scenegen.make_scene(job_params(scenegen, k, 20, 2000, 4000)) for k in range(args.jobs)]
+    n_obs = sum(s.n_obs for s in scenes)
+    jobs = [_load_job(mm, torch, s, mm.BA_MIXED, stream, **SOLVE_CFG) for s in scenes]
+    torch.cuda.synchronize()
+    with mm.Batch(stream) as b:
+        for j in jobs:
+            b.add(j)
+        t0 = time.perf_counter()
+        active = b.solve(chunk=args.chunk)
+        torch.cuda.synchronize()
+        t_mixed = time.perf_counter() - t0
+        launches = b.kernel_launches()
+    iters_mixed = sum(j.stats()["iters"] for j in jobs)
+    mixed_poses = [j.poses() for j in jobs]
+    for j in jobs:
+        j.close()
+    torch.cuda.empty_cache()
+    # plain FP64, one job after another (loads outside the timed region)
+    t_fp64, iters_fp64, worst = 0.0, 0, (0.0, 0.0)
+    for s, mp in zip(scenes[: args.fp64_jobs], mixed_poses):
+        ba = _load_job(mm, torch, s, mm.BA_FP64, stream, **SOLVE_CFG)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = ba.solve()
+        t_fp64 += time.perf_counter() - t0
+        iters_fp64 += st["iters"]
+        r, t = _pose_diff(mp, ba.poses())
+        worst = (max(worst[0], r), max(worst[1], t))
+        ba.close()
+    n64 = min(args.jobs, args.fp64_jobs)
+    line = {
+        "metric": "batched jobs/s (mixed, one batch) vs sequential plain FP64", "workload": "batched",
+        "value": args.jobs / t_mixed, "unit": "jobs/s", "n_gpus": 1, "jobs": args.jobs, "clusters": n_obs,
+        "seconds": t_mixed, "iterations": iters_mixed, "unfinished": active, "gpu_launches": launches,
+        "fp64_sequential": {"value": n64 / t_fp64 if t_fp64 else None, "unit": "jobs/s", "jobs": n64,
+                            "seconds": t_fp64, "iterations": iters_fp64},
+        "pose_agreement_mixed_vs_fp64": {"max_rot_rad": worst[0], "max_trans_m": worst[1], "jobs": n64},
+        "config": {"scans": "log-uniform 20-2000", "voxels": "50 x scans", "obs_per_voxel": "5-30",
+                   "pts_per_obs": 32, "stop": SOLVE_CFG, "chunk": args.chunk},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_served(args):
+    """Poisson arrivals of BA jobs served by continuous batching, against the
+    same arrival stream served one job at a time on the plain FP64 path."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2608_14266_gb300 as mm
+    import scenegen
+    from paper_2608_14266_gb300.server import Job, Server, latency_summary
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    rng = np.random.default_rng(77)
+    arrivals = np.cumsum(rng.exponential(1.0 / args.rate, size=args.jobs))
+    scenes = [scenegen.make_scene(job_params(scenegen, k, 50, 5000, 9000)) for k in range(args.jobs)]
+
+    def inputs(s):
+        return (torch.from_numpy(s.voxel_off).cuda(), torch.from_numpy(s.obs_scan).cuda(),
+                device_clusters_gpu(s, torch, mm), torch.from_numpy(s.pose_init).cuda())
+
+    def make_job(k):
+        s = scenes[k]
+        return Job(job_id=k, n_scans=s.n_scans, n_voxels=s.n_voxels, n_obs=s.n_obs, arrival=float(arrivals[k]),
+                   inputs=lambda s=s: inputs(s))
+
+    def serve(prec, budget, chunk):
+        clock0 = time.perf_counter()
+        clk = lambda: time.perf_counter() - clock0
+        srv = Server(budget, chunk=chunk, clock=clk, precision=prec, cuda_stream=stream, **SOLVE_CFG)
+        k = 0
+        while k < args.jobs or not srv.idle:
+            now = clk()
+            while k < args.jobs and arrivals[k] <= now:
+                srv.submit(make_job(k))
+                k += 1
+            if srv.idle:
+                time.sleep(max(0.0, min(arrivals[k] - now, 0.01)) if k < args.jobs else 0.0)
+                continue
+            srv.step()
+        t_end = clk()
+        jobs = srv.finished
+        launches = srv.kernel_launches()
+        srv.close()
+        return jobs, t_end, launches
+
+    jobs_m, t_m, launches_m = serve(mm.BA_MIXED, args.budget_gb * (1 << 30), args.chunk)
+    torch.cuda.empty_cache()
+    # plain FP64, one job at a time in arrival order
+    clock0 = time.perf_counter()
+    lat64, done64, worst = [], 0, (0.0, 0.0)
+    poses_m = {j.job_id: j.poses for j in jobs_m}
+    for k in range(min(args.jobs, args.fp64_jobs)):
+        now = time.perf_counter() - clock0
+        if arrivals[k] > now:
+            time.sleep(arrivals[k] - now)
+        ba = mm.BundleAdjuster(precision=mm.BA_FP64, cuda_stream=stream, **SOLVE_CFG)
+        ba.load_observations(scenes[k].n_scans, *inputs(scenes[k]))
+        ba.solve()
+        P = ba.poses()
+        lat64.append(time.perf_counter() - clock0 - arrivals[k])
+        r, t = _pose_diff(poses_m[k], P)
+        worst = (max(worst[0], r), max(worst[1], t))
+        ba.close()
+        done64 += 1
+    t64 = time.perf_counter() - clock0
+    lat64 = np.array(lat64)
+    line = {
+        "metric": "served jobs/s and latency (continuous batching, mixed) vs plain FP64 per-job path",
+        "workload": "served", "value": len(jobs_m) / t_m, "unit": "jobs/s", "n_gpus": 1, "jobs": args.jobs,
+        "arrival_rate_per_s": args.rate, "seconds": t_m, "latency": latency_summary(jobs_m),
+        "gpu_launches": launches_m,
+        "fp64_per_job": {"value": done64 / t64, "unit": "jobs/s", "jobs": done64, "seconds": t64,
+                         "latency": {"p50_s": float(np.percentile(lat64, 50)), "p99_s": float(np.percentile(lat64, 99)),
+                                     "mean_s": float(lat64.mean()), "max_s": float(lat64.max())}},
+        "pose_agreement_mixed_vs_fp64": {"max_rot_rad": worst[0], "max_trans_m": worst[1], "jobs": done64},
+        "config": {"scans": "log-uniform 50-5000", "voxels": "50 x scans", "obs_per_voxel": "5-30", "pts_per_obs": 32,
+                   "budget_gb": args.budget_gb, "chunk": args.chunk, "stop": SOLVE_CFG},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = _args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched":
+        run_batched(args)
+    elif args.workload == "served":
+        run_served(args)
     else:
         run_ours(args)
 

@@ -177,6 +177,14 @@ ba_status ba_gradient(ba_handle* h, double* g, double* H, int32_t mem_kind);
 /* Number of kernel launches the handle has issued since creation. */
 int64_t ba_kernel_launches(const ba_handle* h);
 
+/* Device bytes the handle holds for its loaded problem (0 if none). */
+int64_t ba_device_bytes(const ba_handle* h);
+
+/* Upper estimate of the device bytes a handle of this precision holds for a
+ * problem of these sizes once loaded, and of the extra bytes its load needs
+ * transiently (*peak_extra, may be NULL), for admission control. */
+int64_t ba_estimate_bytes(int32_t precision, int32_t n_scans, int64_t n_voxels, int64_t n_obs, int64_t* peak_extra);
+
 /* Per-kernel timing.  While enabled, each iteration kernel the handle
  * launches is bracketed by a pair of CUDA events recorded on the handle's
  * stream (enabling clears earlier records).  ba_profile_read synchronises
@@ -235,6 +243,65 @@ void ba_batch_destroy(ba_batch* b);
 const char* ba_batch_last_error(const ba_batch* b);
 /* Kernel launches issued by the batch's iterations (4 per iteration). */
 int64_t ba_batch_kernel_launches(const ba_batch* b);
+
+/* ---- Served execution (continuous batching) -----------------------------
+ * The paper solves one problem at a time; a server keeps many independent
+ * jobs (submaps, sessions) resident on one GPU and steps them together
+ * through one batch (above).  Admission is by device memory: a job is
+ * accepted only if the bytes held by the resident jobs plus this job's
+ * upper estimate (ba_estimate_bytes, including the load's temporaries) fit
+ * in mem_budget.  A job whose own stopping rule fires leaves at the end of
+ * the step: its poses and statistics are copied to host memory kept by the
+ * server and its device memory is released, so later submissions fit.  A
+ * job's results are bit-identical to solving it alone in a batch of one
+ * with the same iterations per step.  Not thread-safe; every call runs on
+ * the configuration's stream. */
+typedef struct ba_server ba_server;
+
+/* One job's problem, as for ba_load_observations (host or device per
+ * mem_kind; the server copies what it keeps during ba_server_submit). */
+typedef struct {
+  int32_t n_scans;
+  int64_t n_voxels;
+  int64_t n_obs;
+  const int64_t* voxel_offsets; /* n_voxels + 1 */
+  const int32_t* obs_scan;      /* n_obs */
+  const double* agg;            /* n_obs x 10 */
+  int32_t agg_form;             /* BA_AGG_RAW_SUMS | BA_AGG_CENTRED */
+  const double* poses;          /* n_scans x 12, initial */
+  int32_t mem_kind;             /* BA_MEM_HOST | BA_MEM_DEVICE */
+} ba_job_desc;
+
+/* cfg configures every job (precision, stopping rule, device, stream,
+ * allocator); mem_budget > 0 bytes.  Errors: BA_ERR_INVALID_ARG. */
+ba_status ba_server_create(const ba_config* cfg, int64_t mem_budget, ba_server** out);
+/* Load a job now if it fits next to the resident jobs; *job_id receives its
+ * id (ids start at 1 and are never reused).  BA_ERR_CAPACITY: it does not
+ * fit now; nothing was loaded and the caller may submit it again after a
+ * step has retired jobs.  BA_ERR_INVALID_ARG: malformed job (as
+ * ba_load_observations) or a job larger than the whole budget. */
+ba_status ba_server_submit(ba_server* s, const ba_job_desc* job, uint64_t* job_id);
+/* One round: n_iters LM iterations (ba_solve semantics) of every resident
+ * job that has not stopped, then retirement of the jobs that stopped.
+ * *n_resident_out and *n_retired_out (either may be NULL) receive the jobs
+ * still resident and the jobs retired by this step. */
+ba_status ba_server_step(ba_server* s, int32_t n_iters, int32_t* n_resident_out, int32_t* n_retired_out);
+/* *done = 0: the job is resident.  *done = 1: it has finished; its poses
+ * (n_scans x 12 doubles, host) and statistics are copied to poses_out and
+ * stats_out (either may be NULL) and the server forgets the job, so a later
+ * poll of the same id is BA_ERR_INVALID_ARG (as is an unknown id). */
+ba_status ba_server_poll(ba_server* s, uint64_t job_id, int32_t* done, double* poses_out, ba_stats* stats_out);
+/* 1 if a job of these sizes would be admitted now, else 0 (lets a caller
+ * prepare a job's inputs only when they can be taken). */
+int32_t ba_server_fits(const ba_server* s, int32_t n_scans, int64_t n_voxels, int64_t n_obs);
+/* Device bytes held by the resident jobs (what admission charges). */
+int64_t ba_server_bytes_in_use(const ba_server* s);
+int32_t ba_server_resident(const ba_server* s);
+/* Kernel launches of the server's batch. */
+int64_t ba_server_kernel_launches(const ba_server* s);
+const char* ba_server_last_error(const ba_server* s);
+/* Releases every resident job and the finished results not yet polled. */
+void ba_server_destroy(ba_server* s);
 
 /* Stateless point-cluster formation (Eq. 2) on the device: for each of n_obs
  * observations with points point_offsets[o] .. point_offsets[o+1]-1 of

@@ -198,6 +198,17 @@ def ba_aggregate_points(point_offsets, points, out, stream=None):
     return out
 
 
+def ba_device_bytes(h) -> int:
+    return int(_lib.lib().ba_device_bytes(h))
+
+
+def ba_estimate_bytes(precision: int, n_scans: int, n_voxels: int, n_obs: int):
+    """(bytes a loaded handle holds, extra bytes its load needs transiently)."""
+    peak = ctypes.c_int64()
+    keep = _lib.lib().ba_estimate_bytes(int(precision), int(n_scans), int(n_voxels), int(n_obs), ctypes.byref(peak))
+    return int(keep), int(peak.value)
+
+
 def ba_eval_cost_noalloc(n_scans, voxel_offsets, obs_scan, agg_centred, poses, cost_out, lambda0_out=None,
                          stream=None):
     """Cost of the given poses without any device allocation by the library.
@@ -328,6 +339,9 @@ class BundleAdjuster:
 
     def kernel_launches(self):
         return ba_kernel_launches(self.h)
+
+    def device_bytes(self):
+        return ba_device_bytes(self.h)
 
     def profile(self, enable=True):
         ba_profile_enable(self.h, enable)

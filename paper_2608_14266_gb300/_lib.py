@@ -42,6 +42,11 @@ class BaStats(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_ if name != "reserved"}
 
 
+class BaJobDesc(ctypes.Structure):
+    _fields_ = [("n_scans", _I32), ("n_voxels", _I64), ("n_obs", _I64), ("voxel_offsets", _P), ("obs_scan", _P),
+                ("agg", _P), ("agg_form", _I32), ("poses", _P), ("mem_kind", _I32)]
+
+
 _SIGNATURES = {
     "ba_config_default": (None, [_P]),
     "ba_create": (_I32, [_P, _P]),
@@ -73,6 +78,18 @@ _SIGNATURES = {
     "ba_batch_destroy": (None, [_P]),
     "ba_batch_last_error": (ctypes.c_char_p, [_P]),
     "ba_batch_kernel_launches": (_I64, [_P]),
+    "ba_server_create": (_I32, [_P, _I64, _P]),
+    "ba_server_submit": (_I32, [_P, _P, _P]),
+    "ba_server_step": (_I32, [_P, _I32, _P, _P]),
+    "ba_server_poll": (_I32, [_P, ctypes.c_uint64, _P, _P, _P]),
+    "ba_server_fits": (_I32, [_P, _I32, _I64, _I64]),
+    "ba_server_bytes_in_use": (_I64, [_P]),
+    "ba_server_resident": (_I32, [_P]),
+    "ba_server_kernel_launches": (_I64, [_P]),
+    "ba_server_last_error": (ctypes.c_char_p, [_P]),
+    "ba_server_destroy": (None, [_P]),
+    "ba_device_bytes": (_I64, [_P]),
+    "ba_estimate_bytes": (_I64, [_I32, _I32, _I64, _I64, _P]),
 }
 BA_NOALLOC_MAX_VOXELS = 8388608
 BA_KERNEL_VOXEL_PASS, BA_KERNEL_SCAN_PASS, BA_KERNEL_SOLVE, BA_KERNEL_DECIDE = 0, 1, 2, 3

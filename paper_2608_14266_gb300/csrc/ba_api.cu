@@ -389,13 +389,13 @@ ba_status load_impl(ba_handle* h, int32_t n_scans, int64_t n_voxels, int64_t n_o
      "initial poses");
   if (h->mixed) {
     MixedBuffers& mb = h->mb;
-    mb.ve32 = (float*)dev_alloc(h, h->keep, sizeof(float) * kVe32 * (size_t)lb.n_elems);
+    mb.ve32 = (float4*)dev_alloc(h, h->keep, sizeof(float4) * kVe32 * (size_t)lb.n_elems);
     mb.vstate = (float4*)dev_alloc(h, h->keep, sizeof(float4) * 2 * (size_t)n_voxels);
     mb.se32 = (float*)dev_alloc(h, h->keep, sizeof(float) * 10 * (size_t)n_obs);
     mb.vanchor = (float4*)dev_alloc(h, h->keep, sizeof(float4) * (size_t)n_voxels);
     mb.sref = (double*)dev_alloc(h, h->keep, sizeof(double) * 12 * (size_t)n_scans);
     mb.stab2 = (float*)dev_alloc(h, h->keep, sizeof(float) * 2 * kTab * (size_t)n_scans);
-    mb.planes32_2 = (float*)dev_alloc(h, h->keep, sizeof(float) * 2 * 4 * (size_t)n_voxels);
+    mb.planes32_2 = (float4*)dev_alloc(h, h->keep, sizeof(float4) * 2 * 2 * (size_t)n_voxels);
     if (!mb.ve32 || !mb.vstate || !mb.se32 || !mb.vanchor || !mb.sref || !mb.stab2 || !mb.planes32_2)
       return fail(h, BA_ERR_OOM, "mixed-precision copies: out of device memory");
     h->in_keep = in;
@@ -724,6 +724,35 @@ ba_status ba_gradient(ba_handle* h, double* g, double* H, int32_t mem_kind) {
 }
 
 int64_t ba_kernel_launches(const ba_handle* h) { return h ? h->launches : 0; }
+
+int64_t ba_device_bytes(const ba_handle* h) {
+  if (!h) return 0;
+  int64_t b = 0;
+  for (auto& a : h->keep) b += (int64_t)a.bytes;
+  return b;
+}
+
+int64_t ba_estimate_bytes(int32_t precision, int32_t n_scans, int64_t n_voxels, int64_t n_obs, int64_t* peak_extra) {
+  // slots of the slice layout exceed n_obs by the padding of each slice (at
+  // most the longest voxel's length per 32 voxels); take 1/8 extra plus 64
+  const int64_t slots = n_obs + n_obs / 8 + 64;
+  int64_t per_obs, per_slot;
+  if (precision == BA_MIXED) {
+    per_obs = 80 + 4 + 40 + 4 + 4 + 4;  // kept FP64 input, obs_scan, scan-major FP32, se_vox, order, obs_vox
+    per_slot = 16 * kVe32;
+  } else {
+    per_obs = 80 + 4;  // scan-major FP64 copy + se_vox
+    per_slot = 80 + 4;
+  }
+  const int64_t per_voxel = 8 + 4 + 4 + 4 + 8 + 2 * 32 + 16 + 32 + 8 + 2 * 32 + 16;
+  const int64_t per_scan = 8 + 24 * 8 + 27 * 8 + 8 + 12 * 8 + 2 * kTab * 4;
+  const int64_t keep = per_obs * n_obs + per_slot * slots + per_voxel * n_voxels + per_scan * (int64_t)n_scans +
+                       (1 << 16);
+  // load: staged inputs (host inputs), sort keys/values and scratch
+  const int64_t nsort = n_obs > n_voxels ? n_obs : n_voxels;
+  if (peak_extra) *peak_extra = (80 + 4 + 8) * n_obs + 16 * nsort + 24 * nsort / 16 + 8 * (int64_t)n_voxels;
+  return keep;
+}
 
 ba_status ba_profile_enable(ba_handle* h, int32_t enable) {
   if (!h) return BA_ERR_INVALID_ARG;

@@ -23,6 +23,7 @@ __device__ __forceinline__ void apply_E(const float* ph, float a, float b, float
 // its latest centroid delta (world axes, relative to the anchor):
 //   x   = B (b + E l + dt - delta)                (posed mean - centroid)
 //   M_o = G diag(sigma) G^T,   G = B dR V,  dR = I + E
+// (G from the product of the quaternions of B, dR and V)
 // where V, sigma are the observation's stored eigen-decomposition.  The sums
 // of N x, M_o + N x x^T and N have a small normal direction in B, so FP32
 // keeps lambda_min relatively accurate; an FP32 Jacobi in B gives the plane,
@@ -36,7 +37,7 @@ __device__ __forceinline__ void voxel_pass_mixed_body(const DevLayout& L, const 
   if (st->honor_stop && st->stop) return;
   const int buf = use_trial ? 1 - st->cur : st->cur;
   const float* __restrict__ stab = X.stab2 + (int64_t)buf * L.n_scans * kTab;
-  float* __restrict__ planes = X.planes32_2 + (int64_t)buf * L.n_voxels * 4;
+  float4* __restrict__ planes = X.planes32_2 + (int64_t)buf * L.n_voxels * 2;
   const int64_t p = blk * kVoxelThreads + threadIdx.x;
   float lam0 = 0.f;
   if (p < L.n_voxels) {
@@ -44,7 +45,6 @@ __device__ __forceinline__ void voxel_pass_mixed_body(const DevLayout& L, const 
     const int lane = (int)(p & 31);
     const int len = L.vlen[p];
     const int64_t base = L.slice_off[sl] + lane;
-    const int64_t ne = L.n_elems;
     const float4 an = X.vanchor[p];
     const float4 qb = X.vstate[2 * p];
     const float4 dw = X.vstate[2 * p + 1];
@@ -52,54 +52,41 @@ __device__ __forceinline__ void voxel_pass_mixed_body(const DevLayout& L, const 
     quat_to_mat_f(qb.x, qb.y, qb.z, qb.w, B);
     float n = 0.f, s0 = 0.f, s1 = 0.f, s2 = 0.f;
     float m00 = 0.f, m01 = 0.f, m02 = 0.f, m11 = 0.f, m12 = 0.f, m22 = 0.f;
-    // the streamed values of observation k + 1 are loaded while k is processed
-    int pj = 0;
-    float pv[kVe32];
-#pragma unroll
-    for (int q = 0; q < kVe32; ++q) pv[q] = 0.f;
+    // the slot of observation k + 1 (three 128-bit loads) is fetched while k is processed
+    const float4* __restrict__ slot = X.ve32 + kVe32 * base;
+    float4 n0 = make_float4(0.f, 0.f, 0.f, 0.f), n1 = n0, n2 = n0;
     if (len > 0) {
-      pj = __ldg(L.ve_scan + base);
-#pragma unroll
-      for (int q = 0; q < kVe32; ++q) pv[q] = __ldg(X.ve32 + q * ne + base);
+      n0 = __ldg(slot);
+      n1 = __ldg(slot + 1);
+      n2 = __ldg(slot + 2);
     }
     for (int k = 0; k < len; ++k) {
-      const int j = pj;
-      float v[kVe32];
-#pragma unroll
-      for (int q = 0; q < kVe32; ++q) v[q] = pv[q];
+      const float4 f0 = n0, f1 = n1, f2 = n2;
       if (k + 1 < len) {
-        const int64_t e1 = base + (int64_t)(k + 1) * kSlice;
-        pj = __ldg(L.ve_scan + e1);
-#pragma unroll
-        for (int q = 0; q < kVe32; ++q) pv[q] = __ldg(X.ve32 + q * ne + e1);
+        slot += kVe32 * kSlice;
+        n0 = __ldg(slot);
+        n1 = __ldg(slot + 1);
+        n2 = __ldg(slot + 2);
       }
+      const int j = __float_as_int(f1.w);
       const float4* T4 = reinterpret_cast<const float4*>(stab + (int64_t)j * kTab);
-      const float4 t0 = __ldg(T4), t1 = __ldg(T4 + 1), t2 = __ldg(T4 + 2);
-      const float ph[3] = {t0.x, t0.y, t0.z};
-      const float ca = t0.w, cb = t1.x;
-      const float b0 = v[0], b1 = v[1], b2 = v[2], N = v[10];
-      // posed mean about the latest centroid (world axes), then voxel frame
-      const float l0 = b0 + (an.x - t2.x), l1 = b1 + (an.y - t2.y), l2 = b2 + (an.z - t2.z);
+      const float4 qd = __ldg(T4), t1 = __ldg(T4 + 1), t2 = __ldg(T4 + 2);
+      const float ph[3] = {qd.y, qd.z, qd.w};
+      const float b0 = f0.x, b1 = f0.y, b2 = f0.z, N = f0.w;
+      // posed mean about the latest centroid (world axes), then voxel frame:
+      // x = B (b + E l + dt - delta), lever l = b + a - t_ref
+      const float l0 = b0 + (an.x - t1.w), l1 = b1 + (an.y - t2.x), l2 = b2 + (an.z - t2.y);
       float el0, el1, el2;
-      apply_E(ph, ca, cb, l0, l1, l2, el0, el1, el2);
-      const float xw0 = (b0 - dw.x) + el0 + t1.y, xw1 = (b1 - dw.y) + el1 + t1.z, xw2 = (b2 - dw.z) + el2 + t1.w;
+      apply_E(ph, 2.f * qd.x, 2.f, l0, l1, l2, el0, el1, el2);
+      const float xw0 = (b0 - dw.x) + el0 + t1.x, xw1 = (b1 - dw.y) + el1 + t1.y, xw2 = (b2 - dw.z) + el2 + t1.z;
       const float x0 = fmaf(B[0], xw0, fmaf(B[1], xw1, B[2] * xw2));
       const float x1 = fmaf(B[3], xw0, fmaf(B[4], xw1, B[5] * xw2));
       const float x2 = fmaf(B[6], xw0, fmaf(B[7], xw1, B[8] * xw2));
-      // G = B (V + E V): columns of V rotated by dR, then into the frame
-      float V[9];
-      quat_to_mat_f(v[6], v[7], v[8], v[9], V);
+      // G = B dR V as one quaternion product
       float G[9];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        float e0, e1, e2;
-        apply_E(ph, ca, cb, V[c], V[3 + c], V[6 + c], e0, e1, e2);
-        const float d0 = V[c] + e0, d1 = V[3 + c] + e1, d2 = V[6 + c] + e2;
-        G[c] = fmaf(B[0], d0, fmaf(B[1], d1, B[2] * d2));
-        G[3 + c] = fmaf(B[3], d0, fmaf(B[4], d1, B[5] * d2));
-        G[6 + c] = fmaf(B[6], d0, fmaf(B[7], d1, B[8] * d2));
-      }
-      const float sg0 = v[3], sg1 = v[4], sg2 = v[5];
+      const float4 qg = quat_mul_f(quat_mul_f(qb, qd), f2);
+      quat_to_mat_f(qg.x, qg.y, qg.z, qg.w, G);
+      const float sg0 = f1.x, sg1 = f1.y, sg2 = f1.z;
       // G diag(sigma) G^T + N x x^T, upper triangle
       const float g00 = G[0] * sg0, g01 = G[1] * sg1, g02 = G[2] * sg2;
       const float g10 = G[3] * sg0, g11 = G[4] * sg1, g12 = G[5] * sg2;
@@ -136,7 +123,7 @@ __device__ __forceinline__ void voxel_pass_mixed_body(const DevLayout& L, const 
     }
     const float u0 = U[6], u1 = U[7], u2 = U[8];
     const float dp = fmaf(u0, cw0, fmaf(u1, cw1, u2 * cw2));  // u . (c - a)
-    *reinterpret_cast<float4*>(planes + 4 * p) = make_float4(u0, u1, u2, dp);
+    planes[2 * p] = make_float4(u0, u1, u2, dp);
     if (!kFull) {
       // the frame follows the eigenvectors (made right-handed), delta the centroid
       const float det = U[0] * (U[4] * U[8] - U[5] * U[7]) - U[1] * (U[3] * U[8] - U[5] * U[6]) +
@@ -171,7 +158,7 @@ __device__ __forceinline__ void voxel_pass_mixed_body(const DevLayout& L, const 
 }
 
 template <bool kFull>
-__global__ void __launch_bounds__(kVoxelThreads) voxel_pass_mixed_kernel(DevLayout L, DevMixed X,
+__global__ void __launch_bounds__(kVoxelThreads, 6) voxel_pass_mixed_kernel(DevLayout L, DevMixed X,
                                                                         double* __restrict__ full_out,
                                                                         double* __restrict__ cost_part,
                                                                         const DevState* __restrict__ st,
@@ -207,20 +194,25 @@ __device__ __forceinline__ void scan_pass_mixed_body(const DevLayout& L, const D
   if (!force && !st->scan_pending) return;
   const int buf = st->cur;
   const float* tb = X.stab2 + ((int64_t)buf * L.n_scans + j) * kTab;
-  const float ph[3] = {tb[0], tb[1], tb[2]};
-  const float ca = tb[3], cb = tb[4];
-  const float dt0 = tb[5], dt1 = tb[6], dt2 = tb[7], tr0 = tb[8], tr1 = tb[9], tr2 = tb[10];
-  const float* __restrict__ planes = X.planes32_2 + (int64_t)buf * L.n_voxels * 4;
+  // dR = I + E, E x = ca (v x x) + cb v x (v x x) for the unit quaternion (w, v) of dR
+  const float ph[3] = {tb[1], tb[2], tb[3]};
+  const float ca = 2.f * tb[0], cb = 2.f;
+  const float dt0 = tb[4], dt1 = tb[5], dt2 = tb[6], tr0 = tb[7], tr1 = tb[8], tr2 = tb[9];
+  const float4* __restrict__ prec = X.planes32_2 + (int64_t)buf * L.n_voxels * 2;
   const bool gn = st->hess_mode != 0;
   float acc[kGH];
 #pragma unroll
   for (int k = 0; k < kGH; ++k) acc[k] = 0.f;
   const int64_t lo = L.scan_off[j], hi = L.scan_off[j + 1];
   const int64_t no = L.n_obs;
+  // the voxel index of the thread's next observation is fetched one step
+  // ahead, so the plane gather does not wait on it
+  int32_t pv_next = lo + threadIdx.x < hi ? __ldg(L.se_vox + lo + threadIdx.x) : 0;
   for (int64_t o = lo + threadIdx.x; o < hi; o += kScanThreads) {
-    const int32_t pv = __ldg(L.se_vox + o);
-    const float4 pl = __ldg(reinterpret_cast<const float4*>(planes) + pv);
-    const float4 an = __ldg(X.vanchor + pv);
+    const int32_t pv = pv_next;
+    if (o + kScanThreads < hi) pv_next = __ldg(L.se_vox + o + kScanThreads);
+    // plane and anchor of the voxel: one 32-byte record
+    const float4 pl = __ldg(prec + 2 * (int64_t)pv), an = __ldg(prec + 2 * (int64_t)pv + 1);
     const float b0 = __ldg(X.se32 + o), b1 = __ldg(X.se32 + no + o), b2 = __ldg(X.se32 + 2 * no + o);
     const float S00 = __ldg(X.se32 + 3 * no + o), S01 = __ldg(X.se32 + 4 * no + o),
                 S02 = __ldg(X.se32 + 5 * no + o), S11 = __ldg(X.se32 + 6 * no + o),

@@ -60,7 +60,7 @@ __global__ void scan_ref_kernel(int32_t n_scans, const double* poses, double* sr
 // anchor (FP32-rounded centroid) and starting frame (eigenvectors, normal
 // last, proper rotation) of each voxel at the reference poses
 __global__ void voxel_frames_kernel(LoadInput in, const double* sref, const int32_t* vrank, float4* vstate,
-                                    float4* vanchor) {
+                                    float4* vanchor, float4* planes2) {
   const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= in.n_voxels) return;
   const int64_t a0 = in.voxel_off[v], a1 = in.voxel_off[v + 1];
@@ -106,6 +106,9 @@ __global__ void voxel_frames_kernel(LoadInput in, const double* sref, const int3
   const int64_t p = vrank[v];
   const float ax = (float)cx, ay = (float)cy, az = (float)cz;
   vanchor[p] = make_float4(ax, ay, az, 0.0f);
+  // the anchor also sits beside the plane in both buffers of plane records
+  planes2[2 * p + 1] = make_float4(ax, ay, az, 0.0f);
+  planes2[2 * (in.n_voxels + p) + 1] = make_float4(ax, ay, az, 0.0f);
   vstate[2 * p] = make_float4((float)q[0], (float)q[1], (float)q[2], (float)q[3]);
   // the running centroid starts where the anchor's rounding left it
   vstate[2 * p + 1] = make_float4((float)(cx - (double)ax), (float)(cy - (double)ay), (float)(cz - (double)az), 0.0f);
@@ -121,7 +124,7 @@ __device__ inline void offset_b(const double* c, const double* ref, float4 an, d
 
 __global__ void fill_sell_mixed_kernel(LoadInput in, const int32_t* vperm, const int32_t* vlen,
                                        const int64_t* slice_off, int64_t n_voxels, const double* sref,
-                                       const float4* vanchor, float* ve32, int64_t n_elems) {
+                                       const float4* vanchor, float4* ve32) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t s = p >> 5;
   if (s * kSlice >= n_voxels) return;
@@ -134,7 +137,7 @@ __global__ void fill_sell_mixed_kernel(LoadInput in, const int32_t* vperm, const
   const float4 an = real ? vanchor[p] : make_float4(0.f, 0.f, 0.f, 0.f);
   for (int64_t k = 0; k < rows; ++k) {
     const int64_t e = base + k * kSlice;
-    float out[kVe32];
+    float4 s0 = make_float4(0.f, 0.f, 0.f, 0.f), s1 = s0, s2 = s0;
     if (k < len) {
       const int64_t o = o0 + k;
       double c[10], b[3], sw[6], lam[3], vec[9];
@@ -142,9 +145,26 @@ __global__ void fill_sell_mixed_kernel(LoadInput in, const int32_t* vperm, const
       const double* ref = sref + 12 * (int64_t)in.obs_scan[o];
       offset_b(c, ref, an, b);
       rot_sym(ref, c, sw);
-      eig3_sym(sw, lam, vec);
-      // V row-major with the eigenvectors as columns, made a proper rotation
-      double V[9] = {vec[0], vec[3], vec[6], vec[1], vec[4], vec[7], vec[2], vec[5], vec[8]};
+      // eigenvectors: an FP32 Jacobi gives V0, the FP64 Jacobi then finishes on
+      // V0^T S V0, which is diagonal up to FP32 rounding (one or two sweeps
+      // instead of the four to six a full FP64 solve takes; FP64 is 1/64 rate)
+      float swf[6] = {(float)sw[0], (float)sw[1], (float)sw[2], (float)sw[3], (float)sw[4], (float)sw[5]};
+      float lamf[3], vecf[9];
+      eig3_sym_f(swf, lamf, vecf);
+      double V0[9];  // row-major, eigenvectors as columns
+      for (int r = 0; r < 3; ++r)
+        for (int cc = 0; cc < 3; ++cc) V0[3 * r + cc] = (double)vecf[3 * cc + r];
+      double V0t[9];
+      for (int r = 0; r < 3; ++r)
+        for (int cc = 0; cc < 3; ++cc) V0t[3 * r + cc] = V0[3 * cc + r];
+      double sp[6];
+      rot_sym(V0t, sw, sp);  // V0^T S V0
+      eig3_sym(sp, lam, vec);
+      // V = V0 W (W: eigenvectors of V0^T S V0 as columns), made a proper rotation
+      double V[9];
+      for (int r = 0; r < 3; ++r)
+        for (int cc = 0; cc < 3; ++cc)
+          V[3 * r + cc] = V0[3 * r] * vec[3 * cc] + V0[3 * r + 1] * vec[3 * cc + 1] + V0[3 * r + 2] * vec[3 * cc + 2];
       if (det3(V) < 0.0) {
         V[0] = -V[0];
         V[3] = -V[3];
@@ -152,14 +172,30 @@ __global__ void fill_sell_mixed_kernel(LoadInput in, const int32_t* vperm, const
       }
       double q[4];
       mat_to_quat<double>(V, q);
-      for (int t = 0; t < 3; ++t) out[t] = (float)b[t];
-      for (int t = 0; t < 3; ++t) out[3 + t] = (float)lam[t];
-      for (int t = 0; t < 4; ++t) out[6 + t] = (float)q[t];
-      out[10] = (float)c[9];
-    } else {
-      for (int t = 0; t < kVe32; ++t) out[t] = 0.0f;
+      const float qf[4] = {(float)q[0], (float)q[1], (float)q[2], (float)q[3]};
+      // sigma as Rayleigh quotients along the columns of the rotation the
+      // kernel will rebuild from the FP32 quaternion, so that the stored
+      // normal variance belongs to exactly that direction
+      const double w = qf[0], x = qf[1], y = qf[2], z = qf[3];
+      const double nq = 1.0 / (w * w + x * x + y * y + z * z);
+      const double Vf[9] = {1 - 2 * (y * y + z * z) * nq, 2 * (x * y - w * z) * nq, 2 * (x * z + w * y) * nq,
+                            2 * (x * y + w * z) * nq, 1 - 2 * (x * x + z * z) * nq, 2 * (y * z - w * x) * nq,
+                            2 * (x * z - w * y) * nq, 2 * (y * z + w * x) * nq, 1 - 2 * (x * x + y * y) * nq};
+      const double M[3][3] = {{sw[0], sw[1], sw[2]}, {sw[1], sw[3], sw[4]}, {sw[2], sw[4], sw[5]}};
+      float sg[3];
+      for (int cc = 0; cc < 3; ++cc) {
+        double acc = 0.0;
+        for (int r = 0; r < 3; ++r)
+          for (int t = 0; t < 3; ++t) acc += Vf[3 * r + cc] * M[r][t] * Vf[3 * t + cc];
+        sg[cc] = (float)acc;
+      }
+      s0 = make_float4((float)b[0], (float)b[1], (float)b[2], (float)c[9]);
+      s1 = make_float4(sg[0], sg[1], sg[2], __int_as_float(in.obs_scan[o]));
+      s2 = make_float4(qf[0], qf[1], qf[2], qf[3]);
     }
-    for (int t = 0; t < kVe32; ++t) ve32[t * n_elems + e] = out[t];
+    ve32[kVe32 * e] = s0;
+    ve32[kVe32 * e + 1] = s1;
+    ve32[kVe32 * e + 2] = s2;
   }
 }
 
@@ -195,11 +231,11 @@ cudaError_t build_mixed(const LoadInput& in, const LayoutBuffers& lb, const doub
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   voxel_frames_kernel<<<(unsigned)((nv + 127) / 128), 128, 0, stream>>>(cur, mb.sref, lb.vrank, mb.vstate,
-                                                                        mb.vanchor);
+                                                                        mb.vanchor, mb.planes32_2);
   ++*launches;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   fill_sell_mixed_kernel<<<(unsigned)((lb.n_slices * kSlice + 127) / 128), 128, 0, stream>>>(
-      cur, lb.vperm, lb.vlen, lb.slice_off, nv, mb.sref, mb.vanchor, mb.ve32, lb.n_elems);
+      cur, lb.vperm, lb.vlen, lb.slice_off, nv, mb.sref, mb.vanchor, mb.ve32);
   ++*launches;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   fill_scan_mixed_kernel<<<(unsigned)((no + 255) / 256), 256, 0, stream>>>(cur, lb.scan_order, lb.obs_vox, lb.vscale,

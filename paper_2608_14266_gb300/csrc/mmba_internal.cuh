@@ -68,16 +68,18 @@ struct DevLayout {
 // normal direction of the sums stays small; G = B dR V is the only rotation
 // applied per observation.
 struct DevMixed {
-  const float* ve32;     // SELL: b (3), sigma (3), quaternion of V (4), N (1); c * n_elems + e
+  // SELL slots, 3 float4 each (48 B, one slot after another):
+  //   (b0, b1, b2, N), (sigma0, sigma1, sigma2, scan index as int bits), quaternion of V (w, x, y, z)
+  const float4* ve32;
   float4* vstate;        // per sorted voxel, 2 x float4: quaternion of B; (centroid - anchor) world (3), 0
   const float* se32;     // scan-major: b (3), (2/N_i) R_ref S R_ref^T (6), (2/N_i) N (1); c * n_obs + q
   const float4* vanchor; // per sorted voxel: a (3), 0
   const double* sref;    // per scan: R_ref (9), t_ref (3)
-  float* stab2;          // 2 buffers x n_scans x kTab: phi (3), a, b, dt (3), t_ref (3), 0
-  float* planes32_2;     // 2 buffers x n_voxels x 4: u (3), u . (c - a)
+  float* stab2;          // 2 buffers x n_scans x kTab: q of dR (w, v), dt (3), t_ref (3), 0, 0
+  float4* planes32_2;    // 2 buffers x n_voxels x 2 float4: (u (3), u . (c - a)), (a (3), 0)
 };
 constexpr int kTab = 12;
-constexpr int kVe32 = 11;  // FP32 components per slot of the voxel-pass copy
+constexpr int kVe32 = 3;  // float4 per slot of the voxel-pass copy
 
 // Rotation matrix (row-major) of the unit quaternion (w, x, y, z).
 __device__ __forceinline__ void quat_to_mat_f(float w, float x, float y, float z, float* R) {
@@ -310,63 +312,70 @@ __device__ inline void eig3_sym_f(const float* a_in, float lam[3], float vec[9])
     }
     if (done) break;
   }
-  float d[3] = {a00, a11, a22};
-  int i0 = 0, i1 = 1, i2 = 2, t;
-  if (d[i1] < d[i0]) { t = i0; i0 = i1; i1 = t; }
-  if (d[i2] < d[i1]) { t = i1; i1 = i2; i2 = t; }
-  if (d[i1] < d[i0]) { t = i0; i0 = i1; i1 = t; }
-  const float* vs[3] = {v0, v1, v2};
-  int order[3] = {i0, i1, i2};
+  // ascending, stable on ties; swaps of values keep everything in registers
+  float d0 = a00, d1 = a11, d2 = a22;
+  auto cswap = [](float& da, float& db, float* va, float* vb) {
+    if (db < da) {
+      const float t = da;
+      da = db;
+      db = t;
 #pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    lam[c] = d[order[c]];
+      for (int r = 0; r < 3; ++r) {
+        const float u = va[r];
+        va[r] = vb[r];
+        vb[r] = u;
+      }
+    }
+  };
+  cswap(d0, d1, v0, v1);
+  cswap(d1, d2, v1, v2);
+  cswap(d0, d1, v0, v1);
+  lam[0] = d0;
+  lam[1] = d1;
+  lam[2] = d2;
 #pragma unroll
-    for (int r = 0; r < 3; ++r) vec[3 * c + r] = vs[order[c]][r];
+  for (int r = 0; r < 3; ++r) {
+    vec[r] = v0[r];
+    vec[3 + r] = v1[r];
+    vec[6 + r] = v2[r];
   }
 }
 
 // Per-scan FP32 table entry for the mixed path from an FP64 pose P and its
-// reference (R_ref, t_ref): dR = R R_ref^T = Exp(phi), with
-// phi = theta * v / |v|, v the axial vector of (dR - dR^T)/2 and
-// theta = atan2(|v|, (tr dR - 1)/2); a = sin(theta)/theta,
-// b = 2 sin^2(theta/2)/theta^2; dt = t - t_ref.
+// reference (R_ref, t_ref): the unit quaternion q = (w, v) of
+// dR = R R_ref^T (w >= 0), dt = t - t_ref and t_ref, as
+//   (w, vx, vy, vz), (dt0, dt1, dt2, t_ref0), (t_ref1, t_ref2, 0, 0).
+// For a unit q, dR x = x + E x with E x = 2w (v x x) + 2 v x (v x x).
 __device__ inline void scan_table_entry(const double* P, const double* ref, float* out) {
   double D[9];
 #pragma unroll
   for (int r = 0; r < 3; ++r)
 #pragma unroll
     for (int c = 0; c < 3; ++c) D[3 * r + c] = P[3 * r] * ref[3 * c] + P[3 * r + 1] * ref[3 * c + 1] + P[3 * r + 2] * ref[3 * c + 2];
-  const double vx = 0.5 * (D[7] - D[5]), vy = 0.5 * (D[2] - D[6]), vz = 0.5 * (D[3] - D[1]);
-  const double s2 = vx * vx + vy * vy + vz * vz;
-  const double sn = sqrt(s2);
-  const double cs = 0.5 * (D[0] + D[4] + D[8] - 1.0);
-  double f, a, b;
-  if (sn < 0.1 && cs > 0.0) {
-    // th = asin(sn): th / sn = 1 + s^2/6 + 3 s^4/40 + 5 s^6/112 + 35 s^8/1152 + ..., and the
-    // Rodrigues coefficients from their series in th^2 (the table is stored in FP32)
-    f = 1.0 + s2 * (1.0 / 6 + s2 * (3.0 / 40 + s2 * (5.0 / 112 + s2 * (35.0 / 1152))));
-    const double t2 = f * f * s2;
-    a = 1.0 + t2 * (-1.0 / 6 + t2 * (1.0 / 120 + t2 * (-1.0 / 5040)));
-    b = 0.5 + t2 * (-1.0 / 24 + t2 * (1.0 / 720 + t2 * (-1.0 / 40320)));
-  } else {
-    const double th = atan2(sn, cs);
-    f = sn > 0.0 ? th / sn : 0.0;  // th = pi exactly has no axis in the skew part
-    const double sh = sin(0.5 * th);
-    a = sin(th) / th;
-    b = 2.0 * sh * sh / (th * th);
-  }
-  out[0] = (float)(f * vx);
-  out[1] = (float)(f * vy);
-  out[2] = (float)(f * vz);
-  out[3] = (float)a;
-  out[4] = (float)b;
-  out[5] = (float)(P[9] - ref[9]);
-  out[6] = (float)(P[10] - ref[10]);
-  out[7] = (float)(P[11] - ref[11]);
-  out[8] = (float)ref[9];
-  out[9] = (float)ref[10];
-  out[10] = (float)ref[11];
+  double q[4];
+  mat_to_quat<double>(D, q);
+  const double sg = q[0] < 0.0 ? -1.0 : 1.0;
+  out[0] = (float)(sg * q[0]);
+  out[1] = (float)(sg * q[1]);
+  out[2] = (float)(sg * q[2]);
+  out[3] = (float)(sg * q[3]);
+  out[4] = (float)(P[9] - ref[9]);
+  out[5] = (float)(P[10] - ref[10]);
+  out[6] = (float)(P[11] - ref[11]);
+  out[7] = (float)ref[9];
+  out[8] = (float)ref[10];
+  out[9] = (float)ref[11];
+  out[10] = 0.0f;
   out[11] = 0.0f;
+}
+
+// Hamilton product p q of quaternions held as float4 (w, x, y, z) in the
+// fields (x, y, z, w): rot(p q) = rot(p) rot(q)
+__device__ __forceinline__ float4 quat_mul_f(float4 p, float4 q) {
+  return make_float4(fmaf(p.x, q.x, -fmaf(p.y, q.y, fmaf(p.z, q.z, p.w * q.w))),
+                     fmaf(p.x, q.y, fmaf(p.y, q.x, fmaf(p.z, q.w, -p.w * q.z))),
+                     fmaf(p.x, q.z, fmaf(-p.y, q.w, fmaf(p.z, q.x, p.w * q.y))),
+                     fmaf(p.x, q.w, fmaf(p.y, q.z, fmaf(-p.z, q.y, p.w * q.x))));
 }
 
 // LDL^T of the symmetric 6x6 A (full, row-major) without pivoting, then

@@ -110,13 +110,13 @@ cudaError_t launch_scan_table(int32_t n_scans, const double* poses2, const doubl
 // Build (or rebuild) the FP32 copies, frames, anchors and reference poses at
 // the poses of buffer 0 of poses2.
 struct MixedBuffers {
-  float* ve32;
+  float4* ve32;
   float4* vstate;
   float* se32;
   float4* vanchor;
   double* sref;
   float* stab2;
-  float* planes32_2;
+  float4* planes32_2;
 };
 cudaError_t build_mixed(const LoadInput& in, const LayoutBuffers& lb, const double* poses2, MixedBuffers& mb,
                         cudaStream_t stream, int64_t* launches);

@@ -1,0 +1,131 @@
+"""Continuous batching: a job served alongside others that arrive, run and
+leave at other times ends with exactly the poses and cost it reaches when
+solved alone, and the server keeps its resident jobs inside the memory
+budget."""
+import numpy as np
+import pytest
+
+import scenegen
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mm():
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2608_14266_gb300 as mm
+    assert torch.cuda.is_available()
+    return mm
+
+
+def _scenes(n_jobs):
+    rng = np.random.default_rng(11)
+    out = []
+    for k in range(n_jobs):
+        n_scans = int(rng.integers(6, 30))
+        p = scenegen.SceneParams(n_scans=n_scans, n_voxels=50 * n_scans, obs_min=5, obs_max=30, pts_per_obs=16,
+                                 noise_sigma=0.02, rot_sigma_deg=0.5, trans_sigma=0.1, seed=7100 + k)
+        s = scenegen.make_scene(p)
+        out.append((s, s.point_offsets(), s.points()))
+    return out
+
+
+CFG = dict(max_iters=25, rel_tol=1e-10)
+
+
+def library_clusters(mm, s, po, pts):
+    """Centred clusters formed by the library (ba_aggregate_points)."""
+    import torch
+    agg = torch.empty((s.n_obs, 10), dtype=torch.float64, device="cuda")
+    mm.ba_aggregate_points(torch.from_numpy(po).cuda(), torch.from_numpy(pts).cuda(), agg)
+    torch.cuda.synchronize()
+    return agg.cpu().numpy()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_served_equals_alone(mm, precision):
+    from paper_2608_14266_gb300.server import Job, Server
+    prec = mm.BA_MIXED if precision == "mixed" else mm.BA_FP64
+    scenes = _scenes(6)
+    chunk = 3
+    cen = [library_clusters(mm, s, po, pts) for s, po, pts in scenes]
+    alone = []
+    for (s, po, pts), agg in zip(scenes, cen):
+        ba = mm.BundleAdjuster(precision=prec, **CFG)
+        ba.load_observations(s.n_scans, s.voxel_off, s.obs_scan, agg, s.pose_init)
+        with mm.Batch() as b:
+            b.add(ba)
+            b.solve(chunk=chunk)
+            assert list(b.done()) == [1]
+        alone.append((ba.poses(), ba.cost(), ba.stats()["iters"]))
+        ba.close()
+    # a budget that holds only the two largest jobs at once
+    est = [sum(mm.ba_estimate_bytes(prec, s.n_scans, s.n_voxels, s.n_obs)) for s, _, _ in scenes]
+    budget = sum(sorted(est)[-2:])
+    srv = Server(budget, chunk=chunk, precision=prec, **CFG)
+    order = [3, 0, 5, 1, 4, 2]
+    submitted = 0
+    max_used = 0
+    while submitted < len(order) or not srv.idle:
+        if submitted < len(order):  # one arrival per round
+            k = order[submitted]
+            s = scenes[k][0]
+            srv.submit(Job(job_id=k, n_scans=s.n_scans, n_voxels=s.n_voxels, n_obs=s.n_obs,
+                           inputs=lambda s=s, agg=cen[k]: (s.voxel_off, s.obs_scan, agg, s.pose_init)))
+            submitted += 1
+        srv.step()
+        max_used = max(max_used, srv.used)
+        assert srv.used <= budget
+    launches = srv.kernel_launches()
+    srv.close()
+    assert max_used > 0 and launches > 0 and len(srv.finished) == len(scenes)
+    # at most two jobs were resident at once, so some waited in the queue
+    assert max(j.admitted for j in srv.finished) > min(j.finished for j in srv.finished)
+    for job in srv.finished:
+        poses, cost, iters = alone[job.job_id]
+        np.testing.assert_array_equal(job.poses, poses)
+        assert job.stats["cost"] == cost
+        assert job.stats["iters"] == iters
+
+
+def test_estimate_covers_device_bytes(mm):
+    """The admission estimate is an upper bound of what a loaded handle holds."""
+    for precision in (mm.BA_FP64, mm.BA_MIXED):
+        for s, po, pts in _scenes(3):
+            keep, peak = mm.ba_estimate_bytes(precision, s.n_scans, s.n_voxels, s.n_obs)
+            ba = mm.BundleAdjuster(precision=precision)
+            ba.load_points(s.n_scans, s.voxel_off, s.obs_scan, po, pts, s.pose_init)
+            assert ba.device_bytes() <= keep
+            ba.close()
+
+
+def test_server_rejects_and_polls(mm):
+    """Admission answers: a job larger than the whole budget is an invalid
+    argument; one that does not fit next to the resident jobs waits; unknown
+    ids are rejected; a finished job is handed out once."""
+    import ctypes
+    from paper_2608_14266_gb300 import _lib
+    from paper_2608_14266_gb300.server import Job, Server
+    s, po, pts = _scenes(1)[0]
+    agg = library_clusters(mm, s, po, pts)
+    keep, peak = mm.ba_estimate_bytes(mm.BA_MIXED, s.n_scans, s.n_voxels, s.n_obs)
+    with Server(keep + peak - 1, chunk=4, **CFG) as srv:
+        srv.submit(Job(0, s.n_scans, s.n_voxels, s.n_obs, inputs=lambda: (s.voxel_off, s.obs_scan, agg, s.pose_init)))
+        with pytest.raises(mm.BAError) as e:
+            srv.step()
+        assert e.value.status == 1 and "whole budget" in str(e.value) and srv.used == 0
+    with Server(keep + peak, chunk=50, **CFG) as srv:
+        for k in range(2):
+            srv.submit(Job(k, s.n_scans, s.n_voxels, s.n_obs,
+                           inputs=lambda: (s.voxel_off, s.obs_scan, agg, s.pose_init)))
+        assert srv.step() != [] and len(srv.resident) == 0 and len(srv.queue) == 1
+        first = srv.finished[0]
+        done = ctypes.c_int32()
+        # already handed out, and an id never issued
+        for jid in (first.server_id, 999):
+            assert _lib.lib().ba_server_poll(srv.s, jid, ctypes.byref(done), None, None) == 1
+        srv.step()
+        assert len(srv.finished) == 2
+        np.testing.assert_array_equal(srv.finished[0].poses, srv.finished[1].poses)
