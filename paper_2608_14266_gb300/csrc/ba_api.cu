@@ -270,16 +270,21 @@ ba_status check_loaded(ba_handle* h) {
 
 // Copy n bytes of host or device memory into a temporary device buffer
 // (device pointers are used in place).
+// With own = true the input is always copied into the handle's kept buffers
+// (from host or device memory), else host inputs go to temporaries and device
+// inputs are read in place.
 template <typename T>
-const T* stage(ba_handle* h, const T* src, size_t count, int mem_kind, cudaError_t* err) {
+const T* stage(ba_handle* h, const T* src, size_t count, int mem_kind, bool own, cudaError_t* err) {
   *err = cudaSuccess;
-  if (mem_kind == BA_MEM_DEVICE) return src;
-  T* d = (T*)dev_alloc(h, h->temp, sizeof(T) * (count ? count : 1));
+  if (mem_kind == BA_MEM_DEVICE && !own) return src;
+  T* d = (T*)dev_alloc(h, own ? h->keep : h->temp, sizeof(T) * (count ? count : 1));
   if (!d) {
     *err = cudaErrorMemoryAllocation;
     return nullptr;
   }
-  if (count) *err = cudaMemcpyAsync(d, src, sizeof(T) * count, cudaMemcpyHostToDevice, h->stream);
+  if (count)
+    *err = cudaMemcpyAsync(d, src, sizeof(T) * count,
+                           mem_kind == BA_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream);
   return d;
 }
 
@@ -292,13 +297,16 @@ ba_status load_impl(ba_handle* h, int32_t n_scans, int64_t n_voxels, int64_t n_o
   in.n_voxels = n_voxels;
   in.n_obs = n_obs;
   in.agg_form = agg_form;
-  in.voxel_off = stage(h, voxel_off, (size_t)n_voxels + 1, mem_kind, &e);
+  // mixed precision keeps device copies of the inputs: the FP32 copies are
+  // rebuilt from them when the reference poses change (ba_set_state)
+  const bool own = h->mixed;
+  in.voxel_off = stage(h, voxel_off, (size_t)n_voxels + 1, mem_kind, own, &e);
   if (e != cudaSuccess) return cuda_fail(h, e, "stage voxel offsets");
-  in.obs_scan = stage(h, obs_scan, (size_t)n_obs, mem_kind, &e);
+  in.obs_scan = stage(h, obs_scan, (size_t)n_obs, mem_kind, own, &e);
   if (e != cudaSuccess) return cuda_fail(h, e, "stage obs_scan");
-  in.agg = stage(h, agg, (size_t)n_obs * 10, agg_mem_kind, &e);
+  in.agg = stage(h, agg, (size_t)n_obs * 10, agg_mem_kind, own, &e);
   if (e != cudaSuccess) return cuda_fail(h, e, "stage clusters");
-  in.poses = stage(h, poses, (size_t)n_scans * 12, mem_kind, &e);
+  in.poses = stage(h, poses, (size_t)n_scans * 12, mem_kind, false, &e);
   if (e != cudaSuccess) return cuda_fail(h, e, "stage poses");
 
   // validation
@@ -331,24 +339,6 @@ ba_status load_impl(ba_handle* h, int32_t n_scans, int64_t n_voxels, int64_t n_o
                 res.first_bad_pose);
   if (res.max_len >= (1ll << 24))
     return fail(h, BA_ERR_CAPACITY, "a voxel has %lld observations (limit 2^24)", res.max_len);
-
-  // mixed precision keeps device copies of the inputs: the FP32 copies are
-  // rebuilt from them when the reference poses change (ba_set_state)
-  if (h->mixed) {
-    int64_t* vo = (int64_t*)dev_alloc(h, h->keep, sizeof(int64_t) * ((size_t)n_voxels + 1));
-    int32_t* os = (int32_t*)dev_alloc(h, h->keep, sizeof(int32_t) * (size_t)n_obs);
-    double* ag = (double*)dev_alloc(h, h->keep, sizeof(double) * 10 * (size_t)n_obs);
-    if (!vo || !os || !ag) return fail(h, BA_ERR_OOM, "input copies: out of device memory");
-    CK(h, cudaMemcpyAsync(vo, in.voxel_off, sizeof(int64_t) * (n_voxels + 1), cudaMemcpyDeviceToDevice, h->stream),
-       "copy offsets");
-    CK(h, cudaMemcpyAsync(os, in.obs_scan, sizeof(int32_t) * n_obs, cudaMemcpyDeviceToDevice, h->stream),
-       "copy obs_scan");
-    CK(h, cudaMemcpyAsync(ag, in.agg, sizeof(double) * 10 * n_obs, cudaMemcpyDeviceToDevice, h->stream),
-       "copy clusters");
-    in.voxel_off = vo;
-    in.obs_scan = os;
-    in.agg = ag;
-  }
 
   // layout
   LayoutBuffers& lb = h->lb;
@@ -539,9 +529,9 @@ ba_status ba_load_points(ba_handle* h, int32_t n_scans, int64_t n_voxels, int64_
       return fail(h, BA_ERR_INVALID_ARG, "observation %lld has no point", (long long)o);
   const int64_t n_points = off_host[n_obs];
   cudaError_t e;
-  const int64_t* d_off = stage(h, point_offsets, (size_t)n_obs + 1, mem_kind, &e);
+  const int64_t* d_off = stage(h, point_offsets, (size_t)n_obs + 1, mem_kind, false, &e);
   if (e != cudaSuccess) return cuda_fail(h, e, "stage point offsets");
-  const double* d_pts = stage(h, points, (size_t)n_points * 3, mem_kind, &e);
+  const double* d_pts = stage(h, points, (size_t)n_points * 3, mem_kind, false, &e);
   if (e != cudaSuccess) return cuda_fail(h, e, "stage points");
   double* d_agg = (double*)dev_alloc(h, h->temp, sizeof(double) * 10 * (size_t)n_obs);
   if (!d_agg) return fail(h, BA_ERR_OOM, "cluster buffer: out of device memory");

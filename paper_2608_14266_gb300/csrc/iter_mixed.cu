@@ -205,19 +205,40 @@ __device__ __forceinline__ void scan_pass_mixed_body(const DevLayout& L, const D
   for (int k = 0; k < kGH; ++k) acc[k] = 0.f;
   const int64_t lo = L.scan_off[j], hi = L.scan_off[j + 1];
   const int64_t no = L.n_obs;
-  // the voxel index of the thread's next observation is fetched one step
-  // ahead, so the plane gather does not wait on it
-  int32_t pv_next = lo + threadIdx.x < hi ? __ldg(L.se_vox + lo + threadIdx.x) : 0;
-  for (int64_t o = lo + threadIdx.x; o < hi; o += kScanThreads) {
-    const int32_t pv = pv_next;
-    if (o + kScanThreads < hi) pv_next = __ldg(L.se_vox + o + kScanThreads);
-    // plane and anchor of the voxel: one 32-byte record
-    const float4 pl = __ldg(prec + 2 * (int64_t)pv), an = __ldg(prec + 2 * (int64_t)pv + 1);
-    const float b0 = __ldg(X.se32 + o), b1 = __ldg(X.se32 + no + o), b2 = __ldg(X.se32 + 2 * no + o);
-    const float S00 = __ldg(X.se32 + 3 * no + o), S01 = __ldg(X.se32 + 4 * no + o),
-                S02 = __ldg(X.se32 + 5 * no + o), S11 = __ldg(X.se32 + 6 * no + o),
-                S12 = __ldg(X.se32 + 7 * no + o), S22 = __ldg(X.se32 + 8 * no + o);
-    const float N = __ldg(X.se32 + 9 * no + o);
+  const float4* __restrict__ sbN = reinterpret_cast<const float4*>(X.se32);
+  const float4* __restrict__ sS4 = sbN + no;
+  const float2* __restrict__ sS2 = reinterpret_cast<const float2*>(sS4 + no);
+  // software pipeline: the record of the thread's next observation and its
+  // voxel's plane are loaded while the current one is processed, and the
+  // voxel index one step further ahead, so no load waits on another
+  int64_t o = lo + threadIdx.x;
+  float4 nbN = make_float4(0.f, 0.f, 0.f, 0.f), nS4 = nbN, npl = nbN, nan = nbN;
+  float2 nS2 = make_float2(0.f, 0.f);
+  int32_t pv2 = 0;
+  if (o < hi) {
+    const int32_t pv1 = __ldg(L.se_vox + o);
+    if (o + kScanThreads < hi) pv2 = __ldg(L.se_vox + o + kScanThreads);
+    nbN = __ldg(sbN + o);
+    nS4 = __ldg(sS4 + o);
+    nS2 = __ldg(sS2 + o);
+    npl = __ldg(prec + 2 * (int64_t)pv1);
+    nan = __ldg(prec + 2 * (int64_t)pv1 + 1);
+  }
+  for (; o < hi; o += kScanThreads) {
+    const float4 bN = nbN, S4 = nS4, pl = npl, an = nan;
+    const float2 S2 = nS2;
+    const int64_t on = o + kScanThreads;
+    if (on < hi) {
+      nbN = __ldg(sbN + on);
+      nS4 = __ldg(sS4 + on);
+      nS2 = __ldg(sS2 + on);
+      // plane and anchor of the voxel: one 32-byte record
+      npl = __ldg(prec + 2 * (int64_t)pv2);
+      nan = __ldg(prec + 2 * (int64_t)pv2 + 1);
+      if (on + kScanThreads < hi) pv2 = __ldg(L.se_vox + on + kScanThreads);
+    }
+    const float b0 = bN.x, b1 = bN.y, b2 = bN.z, N = bN.w;
+    const float S00 = S4.x, S01 = S4.y, S02 = S4.z, S11 = S4.w, S12 = S2.x, S22 = S2.y;
     const float l0 = b0 + (an.x - tr0), l1 = b1 + (an.y - tr1), l2 = b2 + (an.z - tr2);
     float el0, el1, el2;
     apply_E(ph, ca, cb, l0, l1, l2, el0, el1, el2);

@@ -484,36 +484,42 @@ cudaError_t build_layout(const LoadInput& in, int max_len, bool fill_f64, Alloca
 }
 
 // ============================================================================
-// Point clusters (Eq. 2) in centred form: one warp per observation; the
-// mean first, then the scatter about the mean (two passes over the points).
+// Point clusters (Eq. 2) in centred form: four lanes per observation (eight
+// observations per warp, four consecutive points per load); the mean first,
+// then the scatter about the mean (two passes over the points, the second
+// from cache).  Few lanes per observation keep the FP64 shuffle reductions
+// (GB300's FP64 rate is 1/64 of FP32) small next to the per-point work.
 // ============================================================================
+constexpr int kAggLanes = 4;
+
 __global__ void aggregate_points_kernel(int64_t n_obs, const int64_t* __restrict__ off,
                                         const double* __restrict__ pts, double* __restrict__ out) {
-  const int64_t o = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (o >= n_obs) return;
+  const int64_t o = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kAggLanes;
+  const int sub = threadIdx.x & (kAggLanes - 1);
+  const unsigned mask = 0xfu << (threadIdx.x & 28);  // the four lanes of this observation
+  if (o >= n_obs) return;  // all four lanes of a group leave together
   const int64_t a = off[o], b = off[o + 1];
   double sx = 0.0, sy = 0.0, sz = 0.0;
-  for (int64_t k = a + lane; k < b; k += 32) {
+  for (int64_t k = a + sub; k < b; k += kAggLanes) {
     sx += pts[3 * k];
     sy += pts[3 * k + 1];
     sz += pts[3 * k + 2];
   }
 #pragma unroll
-  for (int w = 16; w > 0; w >>= 1) {
-    sx += __shfl_xor_sync(0xffffffffu, sx, w);
-    sy += __shfl_xor_sync(0xffffffffu, sy, w);
-    sz += __shfl_xor_sync(0xffffffffu, sz, w);
+  for (int w = kAggLanes / 2; w > 0; w >>= 1) {
+    sx += __shfl_xor_sync(mask, sx, w);
+    sy += __shfl_xor_sync(mask, sy, w);
+    sz += __shfl_xor_sync(mask, sz, w);
   }
   const double n = (double)(b - a);
   double* r = out + 10 * o;
   if (b <= a) {
-    if (lane < 10) r[lane] = 0.0;
+    for (int k = sub; k < 10; k += kAggLanes) r[k] = 0.0;
     return;
   }
   const double mx = sx / n, my = sy / n, mz = sz / n;
   double c00 = 0.0, c01 = 0.0, c02 = 0.0, c11 = 0.0, c12 = 0.0, c22 = 0.0;
-  for (int64_t k = a + lane; k < b; k += 32) {
+  for (int64_t k = a + sub; k < b; k += kAggLanes) {
     const double x = pts[3 * k] - mx, y = pts[3 * k + 1] - my, z = pts[3 * k + 2] - mz;
     c00 = fma(x, x, c00);
     c01 = fma(x, y, c01);
@@ -523,24 +529,28 @@ __global__ void aggregate_points_kernel(int64_t n_obs, const int64_t* __restrict
     c22 = fma(z, z, c22);
   }
 #pragma unroll
-  for (int w = 16; w > 0; w >>= 1) {
-    c00 += __shfl_xor_sync(0xffffffffu, c00, w);
-    c01 += __shfl_xor_sync(0xffffffffu, c01, w);
-    c02 += __shfl_xor_sync(0xffffffffu, c02, w);
-    c11 += __shfl_xor_sync(0xffffffffu, c11, w);
-    c12 += __shfl_xor_sync(0xffffffffu, c12, w);
-    c22 += __shfl_xor_sync(0xffffffffu, c22, w);
+  for (int w = kAggLanes / 2; w > 0; w >>= 1) {
+    c00 += __shfl_xor_sync(mask, c00, w);
+    c01 += __shfl_xor_sync(mask, c01, w);
+    c02 += __shfl_xor_sync(mask, c02, w);
+    c11 += __shfl_xor_sync(mask, c11, w);
+    c12 += __shfl_xor_sync(mask, c12, w);
+    c22 += __shfl_xor_sync(mask, c22, w);
   }
-  if (lane == 0) {
+  // every lane holds the sums; each writes a share of the record
+  if (sub == 0) {
     r[0] = c00;
     r[1] = c01;
     r[2] = c02;
+  } else if (sub == 1) {
     r[3] = c11;
     r[4] = c12;
     r[5] = c22;
+  } else if (sub == 2) {
     r[6] = mx;
     r[7] = my;
     r[8] = mz;
+  } else {
     r[9] = n;
   }
 }
@@ -548,7 +558,7 @@ __global__ void aggregate_points_kernel(int64_t n_obs, const int64_t* __restrict
 cudaError_t launch_aggregate_points(int64_t n_obs, const int64_t* point_off, const double* points, double* agg_out,
                                     cudaStream_t stream) {
   if (n_obs <= 0) return cudaSuccess;
-  const int64_t threads = n_obs * 32;
+  const int64_t threads = n_obs * kAggLanes;
   aggregate_points_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, stream>>>(n_obs, point_off, points, agg_out);
   return cudaGetLastError();
 }

@@ -3,8 +3,9 @@
 // poses, and the FP32 re-centred clusters in the slice layout (offset to the
 // anchor plus each observation's scatter as eigenvalues and the quaternion of
 // its eigenvectors) and in the scan-major layout (reference axes, scaled by
-// 2 / N_i).  All arithmetic here is FP64; only the stored results are rounded
-// to FP32.
+// 2 / N_i).  FP64 is used where digits would otherwise be lost (offsets of
+// scene-sized positions from the anchor, the scatter in the basis of its FP32
+// eigenvectors); the rest is FP32 (GB300's FP64 rate is 1/64 of FP32).
 #include "mmba_internal.cuh"
 #include "mmba_kernels.h"
 
@@ -32,21 +33,6 @@ __device__ inline void centred_cluster(const double* a, int form, double out[10]
   out[9] = n;
 }
 
-// R S R^T (S packed xx xy xz yy yz zz), packed result
-__device__ inline void rot_sym(const double* R, const double* S, double* out) {
-  const double M[3][3] = {{S[0], S[1], S[2]}, {S[1], S[3], S[4]}, {S[2], S[4], S[5]}};
-  double T[3][3];
-  for (int r = 0; r < 3; ++r)
-    for (int c = 0; c < 3; ++c) T[r][c] = R[3 * r] * M[0][c] + R[3 * r + 1] * M[1][c] + R[3 * r + 2] * M[2][c];
-  int idx = 0;
-  for (int r = 0; r < 3; ++r)
-    for (int c = r; c < 3; ++c) out[idx++] = T[r][0] * R[3 * c] + T[r][1] * R[3 * c + 1] + T[r][2] * R[3 * c + 2];
-}
-
-__device__ inline double det3(const double* M) {
-  return M[0] * (M[4] * M[8] - M[5] * M[7]) - M[1] * (M[3] * M[8] - M[5] * M[6]) + M[2] * (M[3] * M[7] - M[4] * M[6]);
-}
-
 // reference pose of each scan: R_ref = R, t_ref = t rounded to FP32
 __global__ void scan_ref_kernel(int32_t n_scans, const double* poses, double* sref) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -57,61 +43,105 @@ __global__ void scan_ref_kernel(int32_t n_scans, const double* poses, double* sr
   for (int k = 9; k < 12; ++k) o[k] = (double)(float)P[k];
 }
 
+// FP32 copy of the packed symmetric R S R^T (R, S in FP64, products in FP32)
+__device__ inline void rot_sym_f(const double* R, const double* S, float* out) {
+  float Rf[9], M[3][3];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) Rf[k] = (float)R[k];
+  M[0][0] = (float)S[0]; M[0][1] = M[1][0] = (float)S[1]; M[0][2] = M[2][0] = (float)S[2];
+  M[1][1] = (float)S[3]; M[1][2] = M[2][1] = (float)S[4]; M[2][2] = (float)S[5];
+  float T[3][3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) T[r][c] = fmaf(Rf[3 * r], M[0][c], fmaf(Rf[3 * r + 1], M[1][c], Rf[3 * r + 2] * M[2][c]));
+  int idx = 0;
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = r; c < 3; ++c)
+      out[idx++] = fmaf(T[r][0], Rf[3 * c], fmaf(T[r][1], Rf[3 * c + 1], T[r][2] * Rf[3 * c + 2]));
+}
+
+// posed mean of a cluster relative to the point p0 (FP64 offsets, FP32 lever)
+__device__ inline void posed_rel(const double* c, const double* R, const double* t, const double* p0, float* q) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+    q[a] = fmaf((float)R[3 * a], (float)c[6],
+                fmaf((float)R[3 * a + 1], (float)c[7], fmaf((float)R[3 * a + 2], (float)c[8], (float)(t[a] - p0[a]))));
+}
+
 // anchor (FP32-rounded centroid) and starting frame (eigenvectors, normal
-// last, proper rotation) of each voxel at the reference poses
+// last, proper rotation) of each voxel at the reference poses.  Both only seed
+// the iteration (the voxel pass moves the frame and the centroid every pass),
+// so FP32 sums about the voxel's first posed mean suffice; FP64 is used only
+// for the offsets of the scan positions from that point.
 __global__ void voxel_frames_kernel(LoadInput in, const double* sref, const int32_t* vrank, float4* vstate,
                                     float4* vanchor, float4* planes2) {
   const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= in.n_voxels) return;
   const int64_t a0 = in.voxel_off[v], a1 = in.voxel_off[v + 1];
-  double n = 0.0, cx = 0.0, cy = 0.0, cz = 0.0;
+  double p0[3];
+  {
+    double c[10];
+    centred_cluster(in.agg + 10 * a0, in.agg_form, c);
+    const double* R = sref + 12 * (int64_t)in.obs_scan[a0];
+    const double* P = in.poses + 12 * (int64_t)in.obs_scan[a0];
+    for (int a = 0; a < 3; ++a) p0[a] = R[3 * a] * c[6] + R[3 * a + 1] * c[7] + R[3 * a + 2] * c[8] + P[9 + a];
+  }
+  float n = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
   for (int64_t o = a0; o < a1; ++o) {
     double c[10];
     centred_cluster(in.agg + 10 * o, in.agg_form, c);
-    const double* R = sref + 12 * (int64_t)in.obs_scan[o];
-    const double* P = in.poses + 12 * (int64_t)in.obs_scan[o];
-    cx += c[9] * (R[0] * c[6] + R[1] * c[7] + R[2] * c[8] + P[9]);
-    cy += c[9] * (R[3] * c[6] + R[4] * c[7] + R[5] * c[8] + P[10]);
-    cz += c[9] * (R[6] * c[6] + R[7] * c[7] + R[8] * c[8] + P[11]);
-    n += c[9];
+    const int32_t j = in.obs_scan[o];
+    float q[3];
+    posed_rel(c, sref + 12 * (int64_t)j, in.poses + 12 * (int64_t)j + 9, p0, q);
+    const float N = (float)c[9];
+    cx = fmaf(N, q[0], cx);
+    cy = fmaf(N, q[1], cy);
+    cz = fmaf(N, q[2], cz);
+    n += N;
   }
   cx /= n;
   cy /= n;
   cz /= n;
-  double A[6] = {0, 0, 0, 0, 0, 0};
+  float A[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   for (int64_t o = a0; o < a1; ++o) {
-    double c[10], rs[6];
+    double c[10];
     centred_cluster(in.agg + 10 * o, in.agg_form, c);
-    const double* R = sref + 12 * (int64_t)in.obs_scan[o];
-    const double* P = in.poses + 12 * (int64_t)in.obs_scan[o];
-    const double dx = R[0] * c[6] + R[1] * c[7] + R[2] * c[8] + P[9] - cx;
-    const double dy = R[3] * c[6] + R[4] * c[7] + R[5] * c[8] + P[10] - cy;
-    const double dz = R[6] * c[6] + R[7] * c[7] + R[8] * c[8] + P[11] - cz;
-    rot_sym(R, c, rs);
-    A[0] += rs[0] + c[9] * dx * dx;
-    A[1] += rs[1] + c[9] * dx * dy;
-    A[2] += rs[2] + c[9] * dx * dz;
-    A[3] += rs[3] + c[9] * dy * dy;
-    A[4] += rs[4] + c[9] * dy * dz;
-    A[5] += rs[5] + c[9] * dz * dz;
+    const int32_t j = in.obs_scan[o];
+    float q[3], rs[6];
+    posed_rel(c, sref + 12 * (int64_t)j, in.poses + 12 * (int64_t)j + 9, p0, q);
+    rot_sym_f(sref + 12 * (int64_t)j, c, rs);
+    const float N = (float)c[9], dx = q[0] - cx, dy = q[1] - cy, dz = q[2] - cz;
+    A[0] += fmaf(N * dx, dx, rs[0]);
+    A[1] += fmaf(N * dx, dy, rs[1]);
+    A[2] += fmaf(N * dx, dz, rs[2]);
+    A[3] += fmaf(N * dy, dy, rs[3]);
+    A[4] += fmaf(N * dy, dz, rs[4]);
+    A[5] += fmaf(N * dz, dz, rs[5]);
   }
-  double lam[3], V[9];
-  eig3_sym(A, lam, V);
+  float lam[3], V[9];
+  eig3_sym_f(A, lam, V);
   // rows: e1 (largest), e2, n (smallest)
-  double U[9] = {V[6], V[7], V[8], V[3], V[4], V[5], V[0], V[1], V[2]};
-  if (det3(U) < 0.0)
+  float U[9] = {V[6], V[7], V[8], V[3], V[4], V[5], V[0], V[1], V[2]};
+  const float det = U[0] * (U[4] * U[8] - U[5] * U[7]) - U[1] * (U[3] * U[8] - U[5] * U[6]) +
+                    U[2] * (U[3] * U[7] - U[4] * U[6]);
+  if (det < 0.f)
     for (int k = 0; k < 3; ++k) U[k] = -U[k];
-  double q[4];
-  mat_to_quat<double>(U, q);
+  float q[4];
+  mat_to_quat<float>(U, q);
+  const double c64[3] = {p0[0] + (double)cx, p0[1] + (double)cy, p0[2] + (double)cz};
   const int64_t p = vrank[v];
-  const float ax = (float)cx, ay = (float)cy, az = (float)cz;
+  const float ax = (float)c64[0], ay = (float)c64[1], az = (float)c64[2];
   vanchor[p] = make_float4(ax, ay, az, 0.0f);
   // the anchor also sits beside the plane in both buffers of plane records
   planes2[2 * p + 1] = make_float4(ax, ay, az, 0.0f);
   planes2[2 * (in.n_voxels + p) + 1] = make_float4(ax, ay, az, 0.0f);
-  vstate[2 * p] = make_float4((float)q[0], (float)q[1], (float)q[2], (float)q[3]);
+  vstate[2 * p] = make_float4(q[0], q[1], q[2], q[3]);
   // the running centroid starts where the anchor's rounding left it
-  vstate[2 * p + 1] = make_float4((float)(cx - (double)ax), (float)(cy - (double)ay), (float)(cz - (double)az), 0.0f);
+  vstate[2 * p + 1] = make_float4((float)(c64[0] - (double)ax), (float)(c64[1] - (double)ay),
+                                  (float)(c64[2] - (double)az), 0.0f);
 }
 
 // b = R_ref m + t_ref - a (world axes), for an observation of a voxel whose
@@ -140,55 +170,52 @@ __global__ void fill_sell_mixed_kernel(LoadInput in, const int32_t* vperm, const
     float4 s0 = make_float4(0.f, 0.f, 0.f, 0.f), s1 = s0, s2 = s0;
     if (k < len) {
       const int64_t o = o0 + k;
-      double c[10], b[3], sw[6], lam[3], vec[9];
+      double c[10], b[3];
       centred_cluster(in.agg + 10 * o, in.agg_form, c);
       const double* ref = sref + 12 * (int64_t)in.obs_scan[o];
       offset_b(c, ref, an, b);
-      rot_sym(ref, c, sw);
-      // eigenvectors: an FP32 Jacobi gives V0, the FP64 Jacobi then finishes on
-      // V0^T S V0, which is diagonal up to FP32 rounding (one or two sweeps
-      // instead of the four to six a full FP64 solve takes; FP64 is 1/64 rate)
-      float swf[6] = {(float)sw[0], (float)sw[1], (float)sw[2], (float)sw[3], (float)sw[4], (float)sw[5]};
-      float lamf[3], vecf[9];
-      eig3_sym_f(swf, lamf, vecf);
-      double V0[9];  // row-major, eigenvectors as columns
-      for (int r = 0; r < 3; ++r)
-        for (int cc = 0; cc < 3; ++cc) V0[3 * r + cc] = (double)vecf[3 * cc + r];
-      double V0t[9];
-      for (int r = 0; r < 3; ++r)
-        for (int cc = 0; cc < 3; ++cc) V0t[3 * r + cc] = V0[3 * cc + r];
-      double sp[6];
-      rot_sym(V0t, sw, sp);  // V0^T S V0
-      eig3_sym(sp, lam, vec);
-      // V = V0 W (W: eigenvectors of V0^T S V0 as columns), made a proper rotation
-      double V[9];
-      for (int r = 0; r < 3; ++r)
-        for (int cc = 0; cc < 3; ++cc)
-          V[3 * r + cc] = V0[3 * r] * vec[3 * cc] + V0[3 * r + 1] * vec[3 * cc + 1] + V0[3 * r + 2] * vec[3 * cc + 2];
-      if (det3(V) < 0.0) {
+      // eigen-decomposition of the scatter in the scan frame: an FP32 Jacobi
+      // gives V0; W = V0^T S V0 in FP64 is diagonal up to FP32 rounding, and
+      // its FP32 Jacobi gives the variances to FP32 relative precision (the
+      // normal one included); V = V0 W_vec.  A direction error d of the
+      // stored vectors changes a variance only by (spread) d^2.
+      const float sf[6] = {(float)c[0], (float)c[1], (float)c[2], (float)c[3], (float)c[4], (float)c[5]};
+      float lam0[3], v0[9];
+      eig3_sym_f(sf, lam0, v0);  // eigenvectors as rows of v0 (vector c at v0[3c..3c+2])
+      double w[6];
+      {
+        const double S[3][3] = {{c[0], c[1], c[2]}, {c[1], c[3], c[4]}, {c[2], c[4], c[5]}};
+        double T[3][3];  // T[k] = S v_k
+        for (int k = 0; k < 3; ++k)
+          for (int r = 0; r < 3; ++r)
+            T[k][r] = S[r][0] * (double)v0[3 * k] + S[r][1] * (double)v0[3 * k + 1] + S[r][2] * (double)v0[3 * k + 2];
+        int idx = 0;
+        for (int k = 0; k < 3; ++k)
+          for (int l = k; l < 3; ++l)
+            w[idx++] = (double)v0[3 * k] * T[l][0] + (double)v0[3 * k + 1] * T[l][1] + (double)v0[3 * k + 2] * T[l][2];
+      }
+      const float wf[6] = {(float)w[0], (float)w[1], (float)w[2], (float)w[3], (float)w[4], (float)w[5]};
+      float sg[3], wv[9];
+      eig3_sym_f(wf, sg, wv);
+      // world-axis eigenvectors as columns: V = R_ref V0^T-rows ... = R_ref [v0 rows]^T W
+      float Rf[9];
+      for (int k = 0; k < 9; ++k) Rf[k] = (float)ref[k];
+      float V[9];
+      for (int cc = 0; cc < 3; ++cc) {
+        float u[3];  // scan-frame vector cc = sum_k v0_k W[k][cc]
+        for (int r = 0; r < 3; ++r)
+          u[r] = fmaf(v0[r], wv[3 * cc], fmaf(v0[3 + r], wv[3 * cc + 1], v0[6 + r] * wv[3 * cc + 2]));
+        for (int r = 0; r < 3; ++r) V[3 * r + cc] = fmaf(Rf[3 * r], u[0], fmaf(Rf[3 * r + 1], u[1], Rf[3 * r + 2] * u[2]));
+      }
+      const float det = V[0] * (V[4] * V[8] - V[5] * V[7]) - V[1] * (V[3] * V[8] - V[5] * V[6]) +
+                        V[2] * (V[3] * V[7] - V[4] * V[6]);
+      if (det < 0.f) {
         V[0] = -V[0];
         V[3] = -V[3];
         V[6] = -V[6];
       }
-      double q[4];
-      mat_to_quat<double>(V, q);
-      const float qf[4] = {(float)q[0], (float)q[1], (float)q[2], (float)q[3]};
-      // sigma as Rayleigh quotients along the columns of the rotation the
-      // kernel will rebuild from the FP32 quaternion, so that the stored
-      // normal variance belongs to exactly that direction
-      const double w = qf[0], x = qf[1], y = qf[2], z = qf[3];
-      const double nq = 1.0 / (w * w + x * x + y * y + z * z);
-      const double Vf[9] = {1 - 2 * (y * y + z * z) * nq, 2 * (x * y - w * z) * nq, 2 * (x * z + w * y) * nq,
-                            2 * (x * y + w * z) * nq, 1 - 2 * (x * x + z * z) * nq, 2 * (y * z - w * x) * nq,
-                            2 * (x * z - w * y) * nq, 2 * (y * z + w * x) * nq, 1 - 2 * (x * x + y * y) * nq};
-      const double M[3][3] = {{sw[0], sw[1], sw[2]}, {sw[1], sw[3], sw[4]}, {sw[2], sw[4], sw[5]}};
-      float sg[3];
-      for (int cc = 0; cc < 3; ++cc) {
-        double acc = 0.0;
-        for (int r = 0; r < 3; ++r)
-          for (int t = 0; t < 3; ++t) acc += Vf[3 * r + cc] * M[r][t] * Vf[3 * t + cc];
-        sg[cc] = (float)acc;
-      }
+      float qf[4];
+      mat_to_quat<float>(V, qf);
       s0 = make_float4((float)b[0], (float)b[1], (float)b[2], (float)c[9]);
       s1 = make_float4(sg[0], sg[1], sg[2], __int_as_float(in.obs_scan[o]));
       s2 = make_float4(qf[0], qf[1], qf[2], qf[3]);
@@ -207,16 +234,20 @@ __global__ void fill_scan_mixed_kernel(LoadInput in, const uint32_t* order, cons
   const int64_t o = order[q];
   const int32_t v = obs_vox[o];
   const float4 an = vanchor[vrank[v]];
-  double c[10], b[3], sw[6];
+  double c[10], b[3];
+  float sw[6];
   centred_cluster(in.agg + 10 * o, in.agg_form, c);
   const double* ref = sref + 12 * (int64_t)in.obs_scan[o];
   offset_b(c, ref, an, b);
-  rot_sym(ref, c, sw);
-  const double k = vscale[v];
+  rot_sym_f(ref, c, sw);  // the scan pass is FP32 throughout
+  const float k = (float)vscale[v];
   const int64_t n = in.n_obs;
-  for (int a = 0; a < 3; ++a) se32[a * n + q] = (float)b[a];
-  for (int a = 0; a < 6; ++a) se32[(3 + a) * n + q] = (float)(k * sw[a]);
-  se32[9 * n + q] = (float)(k * c[9]);
+  float4* bN = reinterpret_cast<float4*>(se32);
+  float4* S4 = bN + n;
+  float2* S2 = reinterpret_cast<float2*>(S4 + n);
+  bN[q] = make_float4((float)b[0], (float)b[1], (float)b[2], (float)(vscale[v] * c[9]));
+  S4[q] = make_float4(k * sw[0], k * sw[1], k * sw[2], k * sw[3]);
+  S2[q] = make_float2(k * sw[4], k * sw[5]);
 }
 
 }  // namespace

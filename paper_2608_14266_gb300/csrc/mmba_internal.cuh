@@ -72,7 +72,10 @@ struct DevMixed {
   //   (b0, b1, b2, N), (sigma0, sigma1, sigma2, scan index as int bits), quaternion of V (w, x, y, z)
   const float4* ve32;
   float4* vstate;        // per sorted voxel, 2 x float4: quaternion of B; (centroid - anchor) world (3), 0
-  const float* se32;     // scan-major: b (3), (2/N_i) R_ref S R_ref^T (6), (2/N_i) N (1); c * n_obs + q
+  // scan-major, three vector arrays one after another (k = 2/N_i):
+  //   float4 (b (3), k N) x n_obs | float4 k S (xx, xy, xz, yy) x n_obs | float2 k S (yz, zz) x n_obs
+  // with S = R_ref S_o R_ref^T
+  const float* se32;
   const float4* vanchor; // per sorted voxel: a (3), 0
   const double* sref;    // per scan: R_ref (9), t_ref (3)
   float* stab2;          // 2 buffers x n_scans x kTab: q of dR (w, v), dt (3), t_ref (3), 0, 0
