@@ -493,6 +493,34 @@ def _load_job(mm, torch, scene, prec, stream, **cfg):
     return ba
 
 
+def _gt_rms(P, scene):
+    """RMS rotation (rad) and translation (m) error of solved poses against
+    the generator's ground truth (scan 0, the gauge, is exact on both)."""
+    import numpy as np
+    R1 = P[:, :9].reshape(-1, 3, 3)
+    R2 = scene.pose_gt[:, :9].reshape(-1, 3, 3)
+    D = np.einsum("nij,nkj->nik", R1, R2)
+    ang = np.arccos(np.clip(0.5 * (np.trace(D, axis1=1, axis2=2) - 1.0), -1.0, 1.0))
+    return float(np.sqrt(np.mean(ang ** 2))), float(np.sqrt(np.mean(np.sum((P[:, 9:] - scene.pose_gt[:, 9:]) ** 2, 1))))
+
+
+class _Accuracy:
+    """Per-path mean over jobs of the RMS error against ground truth."""
+
+    def __init__(self):
+        self.sums = {}
+
+    def add(self, path, P, scene):
+        r, t = _gt_rms(P, scene)
+        a = self.sums.setdefault(path, [0.0, 0.0, 0])
+        a[0] += r
+        a[1] += t
+        a[2] += 1
+
+    def report(self):
+        return {k: {"rms_rot_rad": v[0] / v[2], "rms_trans_m": v[1] / v[2], "jobs": v[2]} for k, v in self.sums.items()}
+
+
 def _pose_diff(P, Q):
     import numpy as np
     R1 = P[:, :9].reshape(-1, 3, 3)
@@ -537,6 +565,7 @@ def run_batched(args):
     torch.cuda.empty_cache()
     # plain FP64, one job after another (loads outside the timed region)
     t_fp64, iters_fp64, worst = 0.0, 0, (0.0, 0.0)
+    acc = _Accuracy()
     for s, mp in zip(scenes[: args.fp64_jobs], mixed_poses):
         ba = _load_job(mm, torch, s, mm.BA_FP64, stream, **SOLVE_CFG)
         torch.cuda.synchronize()
@@ -544,8 +573,11 @@ def run_batched(args):
         st = ba.solve()
         t_fp64 += time.perf_counter() - t0
         iters_fp64 += st["iters"]
-        r, t = _pose_diff(mp, ba.poses())
+        P64 = ba.poses()
+        r, t = _pose_diff(mp, P64)
         worst = (max(worst[0], r), max(worst[1], t))
+        acc.add("mixed", mp, s)
+        acc.add("fp64", P64, s)
         ba.close()
     n64 = min(args.jobs, args.fp64_jobs)
     line = {
@@ -555,6 +587,7 @@ def run_batched(args):
         "fp64_sequential": {"value": n64 / t_fp64 if t_fp64 else None, "unit": "jobs/s", "jobs": n64,
                             "seconds": t_fp64, "iterations": iters_fp64},
         "pose_agreement_mixed_vs_fp64": {"max_rot_rad": worst[0], "max_trans_m": worst[1], "jobs": n64},
+        "accuracy_vs_ground_truth": acc.report(),
         "config": {"scans": "log-uniform 20-2000", "voxels": "50 x scans", "obs_per_voxel": "5-30",
                    "pts_per_obs": 32, "stop": SOLVE_CFG, "chunk": args.chunk},
     }
@@ -612,6 +645,7 @@ def run_served(args):
     # plain FP64, one job at a time in arrival order
     clock0 = time.perf_counter()
     lat64, done64, worst = [], 0, (0.0, 0.0)
+    acc = _Accuracy()
     poses_m = {j.job_id: j.poses for j in jobs_m}
     for k in range(min(args.jobs, args.fp64_jobs)):
         now = time.perf_counter() - clock0
@@ -624,6 +658,8 @@ def run_served(args):
         lat64.append(time.perf_counter() - clock0 - arrivals[k])
         r, t = _pose_diff(poses_m[k], P)
         worst = (max(worst[0], r), max(worst[1], t))
+        acc.add("mixed", poses_m[k], scenes[k])
+        acc.add("fp64", P, scenes[k])
         ba.close()
         done64 += 1
     t64 = time.perf_counter() - clock0
@@ -637,6 +673,7 @@ def run_served(args):
                          "latency": {"p50_s": float(np.percentile(lat64, 50)), "p99_s": float(np.percentile(lat64, 99)),
                                      "mean_s": float(lat64.mean()), "max_s": float(lat64.max())}},
         "pose_agreement_mixed_vs_fp64": {"max_rot_rad": worst[0], "max_trans_m": worst[1], "jobs": done64},
+        "accuracy_vs_ground_truth": acc.report(),
         "config": {"scans": "log-uniform 50-5000", "voxels": "50 x scans", "obs_per_voxel": "5-30", "pts_per_obs": 32,
                    "budget_gb": args.budget_gb, "chunk": args.chunk, "stop": SOLVE_CFG},
     }

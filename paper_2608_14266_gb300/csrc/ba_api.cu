@@ -253,7 +253,8 @@ ba_status launch_iteration(ba_handle* h) {
   CK(h, voxel_pass(h, nullptr, 1), "trial voxel pass");
   CK(h, prof_end(h, ev), "event");
   CK(h, prof_begin(h, BA_KERNEL_DECIDE, &ev), "event");
-  CK(h, launch_decide(h->cost_part, h->n_cost, h->pred_part, h->L.n_scans, h->d_state, 0, h->stream), "decide");
+  CK(h, launch_decide(h->cost_part, h->n_cost, h->pred_part, solve_blocks(h->L.n_scans), h->d_state, 0, h->stream),
+     "decide");
   CK(h, prof_end(h, ev), "event");
   CK(h, prof_begin(h, BA_KERNEL_SCAN_PASS, &ev), "event");
   CK(h, scan_pass(h, 0), "scan pass");

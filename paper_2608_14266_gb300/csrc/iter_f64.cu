@@ -318,13 +318,12 @@ __global__ void __launch_bounds__(kScanThreads) scan_pass_f64_batch_kernel(JobTa
 // predicted reduction -(g^T delta + delta^T H delta / 2).  The fixed scan and
 // scans without observations keep their pose.
 // ---------------------------------------------------------------------------
-__device__ inline void solve_scan(const DevLayout& L, int j, const double* __restrict__ P, double* __restrict__ Pt,
-                                  const double* __restrict__ gH, double* __restrict__ pred_part, DevState* st) {
+__device__ inline double solve_scan(const DevLayout& L, int j, const double* __restrict__ P, double* __restrict__ Pt,
+                                    const double* __restrict__ gH, DevState* st) {
   const int64_t nobs = L.scan_off[j + 1] - L.scan_off[j];
   if (j == L.fixed_scan || nobs == 0) {
     for (int k = 0; k < 12; ++k) Pt[k] = P[k];
-    pred_part[j] = 0.0;
-    return;
+    return 0.0;
   }
   const double* a = gH + (int64_t)j * kGH;
   double g[6], H[36], A[36], b[6], dlt[6];
@@ -345,8 +344,7 @@ __device__ inline void solve_scan(const DevLayout& L, int j, const double* __res
   if (!ldlt6_solve(A, b, dlt)) {
     atomicOr(&st->solve_fail_flag, 1);
     for (int k = 0; k < 12; ++k) Pt[k] = P[k];
-    pred_part[j] = 0.0;
-    return;
+    return 0.0;
   }
   double gd = 0.0, dhd = 0.0;
   for (int r = 0; r < 6; ++r) {
@@ -355,7 +353,7 @@ __device__ inline void solve_scan(const DevLayout& L, int j, const double* __res
     for (int c = 0; c < 6; ++c) hr = fma(H[6 * r + c], dlt[c], hr);
     dhd = fma(dlt[r], hr, dhd);
   }
-  pred_part[j] = -(gd + 0.5 * dhd);
+  const double pred = -(gd + 0.5 * dhd);
   double E[9];
   so3_exp(dlt, E);
   for (int r = 0; r < 3; ++r)
@@ -363,30 +361,42 @@ __device__ inline void solve_scan(const DevLayout& L, int j, const double* __res
   Pt[9] = P[9] + dlt[3];
   Pt[10] = P[10] + dlt[4];
   Pt[11] = P[11] + dlt[5];
+  return pred;
 }
 
 // With stab2 given (mixed precision) the trial scan's FP32 table entry is
-// written too, from the trial pose and the scan's reference pose.
+// written too, from the trial pose and the scan's reference pose.  Block blk
+// (scans blk * kSolveThreads ..) writes the sum of its scans' predicted
+// reductions to pred_part[blk], in a fixed order.
 __device__ __forceinline__ void solve_f64_body(const DevLayout& L, double* __restrict__ poses2,
                                                const double* __restrict__ gH, double* __restrict__ pred_part,
                                                DevState* st, const double* __restrict__ sref,
-                                               float* __restrict__ stab2, int64_t j) {
-  if (st->honor_stop && st->stop) return;
-  if (j >= L.n_scans) return;
-  const int cur = st->cur;
-  const double* P = poses2 + ((int64_t)cur * L.n_scans + j) * 12;
-  double* Pt = poses2 + ((int64_t)(1 - cur) * L.n_scans + j) * 12;
-  solve_scan(L, (int)j, P, Pt, gH, pred_part, st);
-  if (stab2) scan_table_entry(Pt, sref + 12 * (int64_t)j, stab2 + ((int64_t)(1 - cur) * L.n_scans + j) * kTab);
+                                               float* __restrict__ stab2, int64_t blk, double* red) {
+  if (st->honor_stop && st->stop) return;  // uniform over the block
+  const int64_t j = blk * kSolveThreads + threadIdx.x;
+  double pred = 0.0;
+  if (j < L.n_scans) {
+    const int cur = st->cur;
+    const double* P = poses2 + ((int64_t)cur * L.n_scans + j) * 12;
+    double* Pt = poses2 + ((int64_t)(1 - cur) * L.n_scans + j) * 12;
+    pred = solve_scan(L, (int)j, P, Pt, gH, st);
+    if (stab2) scan_table_entry(Pt, sref + 12 * (int64_t)j, stab2 + ((int64_t)(1 - cur) * L.n_scans + j) * kTab);
+  }
+  const double tot = block_sum<kSolveThreads>(pred, red);
+  if (threadIdx.x == 0) pred_part[blk] = tot;
 }
 
-__global__ void solve_f64_kernel(DevLayout L, double* __restrict__ poses2, const double* __restrict__ gH,
-                                 double* __restrict__ pred_part, DevState* st, const double* __restrict__ sref,
-                                 float* __restrict__ stab2) {
-  solve_f64_body(L, poses2, gH, pred_part, st, sref, stab2, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+__global__ void __launch_bounds__(kSolveThreads) solve_f64_kernel(DevLayout L, double* __restrict__ poses2,
+                                                                 const double* __restrict__ gH,
+                                                                 double* __restrict__ pred_part, DevState* st,
+                                                                 const double* __restrict__ sref,
+                                                                 float* __restrict__ stab2) {
+  __shared__ double red[kSolveThreads / 32];
+  solve_f64_body(L, poses2, gH, pred_part, st, sref, stab2, blockIdx.x, red);
 }
 
 __global__ void __launch_bounds__(kSolveThreads) solve_f64_batch_kernel(JobTable T) {
+  __shared__ double red[kSolveThreads / 32];
   __shared__ JobView J;
   __shared__ int64_t blk;
   if (threadIdx.x == 0) {
@@ -395,7 +405,7 @@ __global__ void __launch_bounds__(kSolveThreads) solve_f64_batch_kernel(JobTable
     blk = blockIdx.x - T.oblk[job];
   }
   __syncthreads();
-  solve_f64_body(J.L, J.poses2, J.gH, J.pred_part, J.st, J.X.sref, J.X.stab2, blk * kSolveThreads + threadIdx.x);
+  solve_f64_body(J.L, J.poses2, J.gH, J.pred_part, J.st, J.X.sref, J.X.stab2, blk, red);
 }
 
 // ---------------------------------------------------------------------------
@@ -466,7 +476,7 @@ __global__ void __launch_bounds__(kDecideThreads) decide_kernel(const double* __
 __global__ void __launch_bounds__(kDecideThreads) decide_batch_kernel(JobTable T) {
   __shared__ double red[kDecideThreads / 32];
   const JobView& J = T.jobs[blockIdx.x];
-  decide_body(J.cost_part, J.n_cost, J.pred_part, J.L.n_scans, J.st, 0, red);
+  decide_body(J.cost_part, J.n_cost, J.pred_part, solve_blocks(J.L.n_scans), J.st, 0, red);
 }
 
 // ---- launchers ---------------------------------------------------------------
@@ -492,9 +502,8 @@ cudaError_t launch_scan_pass_f64(const DevLayout& L, const double* poses2, const
 
 cudaError_t launch_solve_f64(const DevLayout& L, double* poses2, const double* gH, double* pred_part, DevState* st,
                              const double* sref, float* stab2, cudaStream_t stream) {
-  const int threads = kSolveThreads;
-  const int blocks = (L.n_scans + threads - 1) / threads;
-  solve_f64_kernel<<<blocks, threads, 0, stream>>>(L, poses2, gH, pred_part, st, sref, stab2);
+  solve_f64_kernel<<<(unsigned)solve_blocks(L.n_scans), kSolveThreads, 0, stream>>>(L, poses2, gH, pred_part, st, sref,
+                                                                                    stab2);
   return cudaGetLastError();
 }
 

@@ -200,9 +200,9 @@ __device__ __forceinline__ void scan_pass_mixed_body(const DevLayout& L, const D
   const float dt0 = tb[4], dt1 = tb[5], dt2 = tb[6], tr0 = tb[7], tr1 = tb[8], tr2 = tb[9];
   const float4* __restrict__ prec = X.planes32_2 + (int64_t)buf * L.n_voxels * 2;
   const bool gn = st->hess_mode != 0;
-  float acc[kGH];
+  float acc[32];  // kGH sums, padded to a warp for the reduce-scatter
 #pragma unroll
-  for (int k = 0; k < kGH; ++k) acc[k] = 0.f;
+  for (int k = 0; k < 32; ++k) acc[k] = 0.f;
   const int64_t lo = L.scan_off[j], hi = L.scan_off[j + 1];
   const int64_t no = L.n_obs;
   const float4* __restrict__ sbN = reinterpret_cast<const float4*>(X.se32);
@@ -217,17 +217,17 @@ __device__ __forceinline__ void scan_pass_mixed_body(const DevLayout& L, const D
   int32_t pv2 = 0;
   if (o < hi) {
     const int32_t pv1 = __ldg(L.se_vox + o);
-    if (o + kScanThreads < hi) pv2 = __ldg(L.se_vox + o + kScanThreads);
+    if (o + kScanMixedThreads < hi) pv2 = __ldg(L.se_vox + o + kScanMixedThreads);
     nbN = __ldg(sbN + o);
     nS4 = __ldg(sS4 + o);
     nS2 = __ldg(sS2 + o);
     npl = __ldg(prec + 2 * (int64_t)pv1);
     nan = __ldg(prec + 2 * (int64_t)pv1 + 1);
   }
-  for (; o < hi; o += kScanThreads) {
+  for (; o < hi; o += kScanMixedThreads) {
     const float4 bN = nbN, S4 = nS4, pl = npl, an = nan;
     const float2 S2 = nS2;
-    const int64_t on = o + kScanThreads;
+    const int64_t on = o + kScanMixedThreads;
     if (on < hi) {
       nbN = __ldg(sbN + on);
       nS4 = __ldg(sS4 + on);
@@ -235,7 +235,7 @@ __device__ __forceinline__ void scan_pass_mixed_body(const DevLayout& L, const D
       // plane and anchor of the voxel: one 32-byte record
       npl = __ldg(prec + 2 * (int64_t)pv2);
       nan = __ldg(prec + 2 * (int64_t)pv2 + 1);
-      if (on + kScanThreads < hi) pv2 = __ldg(L.se_vox + on + kScanThreads);
+      if (on + kScanMixedThreads < hi) pv2 = __ldg(L.se_vox + on + kScanMixedThreads);
     }
     const float b0 = bN.x, b1 = bN.y, b2 = bN.z, N = bN.w;
     const float S00 = S4.x, S01 = S4.y, S02 = S4.z, S11 = S4.w, S12 = S2.x, S22 = S2.y;
@@ -308,25 +308,25 @@ __device__ __forceinline__ void scan_pass_mixed_body(const DevLayout& L, const D
   // far below what moves a pose by 1e-9 rad given H's size), and GB300's FP64
   // pipe is 1/64 of FP32, so FP64 is kept out of the reduction.
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  warp_reduce_scatter32(acc);
+  if (kScanMixedThreads == 32) {
+    if (l < kGH) tot[l] = acc[0];
+  } else {
+    if (l < kGH) red[w][l] = acc[0];
+    __syncthreads();
+    if (threadIdx.x < kGH) {
+      float v = 0.f;
 #pragma unroll
-  for (int k = 0; k < kGH; ++k) {
-    float v = acc[k];
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-    if (l == 0) red[w][k] = v;
+      for (int q = 0; q < kScanMixedThreads / 32; ++q) v += red[q][threadIdx.x];
+      tot[threadIdx.x] = v;
+    }
   }
-  __syncthreads();
-  if (threadIdx.x < kGH) {
-    float v = 0.f;
-#pragma unroll
-    for (int q = 0; q < kScanThreads / 32; ++q) v += red[q][threadIdx.x];
-    tot[threadIdx.x] = v;
-  } else if (threadIdx.x >= 32 && threadIdx.x < 41) {
+  if (threadIdx.x < 9) {
     // dR = I + a [phi]x + b [phi]x^2, entry (r, c)
-    const int r = (threadIdx.x - 32) / 3, c = (threadIdx.x - 32) % 3;
+    const int r = threadIdx.x / 3, c = threadIdx.x % 3;
     const float K[3][3] = {{0.f, -ph[2], ph[1]}, {ph[2], 0.f, -ph[0]}, {-ph[1], ph[0], 0.f}};
     const float k2 = ph[r] * ph[c] - (r == c ? ph[0] * ph[0] + ph[1] * ph[1] + ph[2] * ph[2] : 0.f);
-    dR[threadIdx.x - 32] = (r == c ? 1.f : 0.f) + ca * K[r][c] + cb * k2;
+    dR[threadIdx.x] = (r == c ? 1.f : 0.f) + ca * K[r][c] + cb * k2;
   }
   __syncthreads();
   // world frame: g = blockdiag(dR, dR) g', H = blockdiag(dR, dR) H' blockdiag(dR, dR)^T,
@@ -364,17 +364,17 @@ __device__ __forceinline__ void scan_pass_mixed_body(const DevLayout& L, const D
   }
 }
 
-__global__ void __launch_bounds__(kScanThreads) scan_pass_mixed_kernel(DevLayout L, DevMixed X,
+__global__ void __launch_bounds__(kScanMixedThreads, 24) scan_pass_mixed_kernel(DevLayout L, DevMixed X,
                                                                       double* __restrict__ gH,
                                                                       const DevState* __restrict__ st, int force) {
-  __shared__ float red[kScanThreads / 32][kGH];
+  __shared__ float red[kScanMixedThreads / 32][kGH];
   __shared__ float tot[kGH];
   __shared__ float dR[9];
   scan_pass_mixed_body(L, X, gH, st, force, blockIdx.x, red, tot, dR);
 }
 
-__global__ void __launch_bounds__(kScanThreads) scan_pass_mixed_batch_kernel(JobTable T) {
-  __shared__ float red[kScanThreads / 32][kGH];
+__global__ void __launch_bounds__(kScanMixedThreads, 20) scan_pass_mixed_batch_kernel(JobTable T) {
+  __shared__ float red[kScanMixedThreads / 32][kGH];
   __shared__ float tot[kGH];
   __shared__ float dR[9];
   __shared__ JobView J;
@@ -414,7 +414,7 @@ cudaError_t launch_scan_pass_mixed(const DevLayout& L, const DevMixed& X, const 
                                    const DevState* st, int force, cudaStream_t stream) {
   if (L.n_scans == 0) return cudaSuccess;
   (void)poses2;
-  scan_pass_mixed_kernel<<<(unsigned)L.n_scans, kScanThreads, 0, stream>>>(L, X, gH, st, force);
+  scan_pass_mixed_kernel<<<(unsigned)L.n_scans, kScanMixedThreads, 0, stream>>>(L, X, gH, st, force);
   return cudaGetLastError();
 }
 
@@ -424,7 +424,7 @@ cudaError_t launch_batch_voxel_pass_mixed(const JobTable& T, int64_t n_blocks, i
 }
 
 cudaError_t launch_batch_scan_pass_mixed(const JobTable& T, int64_t n_blocks, cudaStream_t stream) {
-  scan_pass_mixed_batch_kernel<<<(unsigned)n_blocks, kScanThreads, 0, stream>>>(T);
+  scan_pass_mixed_batch_kernel<<<(unsigned)n_blocks, kScanMixedThreads, 0, stream>>>(T);
   return cudaGetLastError();
 }
 

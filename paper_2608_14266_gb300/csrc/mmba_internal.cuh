@@ -463,16 +463,34 @@ __device__ inline void so3_exp(const double* phi, double* R) {
 // four independent load streams so the loads are in flight together.
 template <int kThreads>
 __device__ inline double strided_sum(const double* __restrict__ p, int64_t n) {
-  double c0 = 0.0, c1 = 0.0, c2 = 0.0, c3 = 0.0;
+  // eight loads in flight per round
+  double c[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
   int64_t k = threadIdx.x;
-  for (; k + 3 * kThreads < n; k += 4 * kThreads) {
-    c0 += p[k];
-    c1 += p[k + kThreads];
-    c2 += p[k + 2 * kThreads];
-    c3 += p[k + 3 * kThreads];
+  for (; k + 7 * kThreads < n; k += 8 * kThreads) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) c[u] += p[k + u * kThreads];
   }
-  for (; k < n; k += kThreads) c0 += p[k];
-  return (c0 + c1) + (c2 + c3);
+  for (; k < n; k += kThreads) c[0] += p[k];
+  return ((c[0] + c[1]) + (c[2] + c[3])) + ((c[4] + c[5]) + (c[6] + c[7]));
+}
+
+// Warp reduce-scatter of 32 values per lane: afterwards a[0] of lane l holds
+// the warp's total of value l (fixed tree; 31 shuffles instead of 5 per value).
+// At the level with offset o, the lanes with bit o set keep the upper half of
+// their remaining values and receive it from the partner lane, the others
+// keep and receive the lower half.
+__device__ __forceinline__ void warp_reduce_scatter32(float (&a)[32]) {
+  const int l = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const bool up = (l & o) != 0;
+#pragma unroll
+    for (int k = 0; k < o; ++k) {
+      const float send = up ? a[k] : a[k + o];
+      const float keep = up ? a[k + o] : a[k];
+      a[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
 }
 
 // Deterministic block-wide sum (fixed shape for a given blockDim).
@@ -484,9 +502,12 @@ __device__ inline T block_sum(T v, T* smem /* kThreads / 32 */) {
   if (l == 0) smem[w] = v;
   __syncthreads();
   T r = T(0);
-  if (threadIdx.x == 0) {
+  if (w == 0) {
+    // the warp sums reduced by warp 0 (fixed tree)
+    r = l < kThreads / 32 ? smem[l] : T(0);
 #pragma unroll
-    for (int k = 0; k < kThreads / 32; ++k) r += smem[k];
+    for (int o = 16; o > 0; o >>= 1)
+      if (o < kThreads / 32) r += __shfl_down_sync(0xffffffffu, r, o);
   }
   __syncthreads();
   return r;  // valid in thread 0

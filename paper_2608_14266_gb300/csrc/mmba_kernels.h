@@ -9,12 +9,13 @@
 namespace mmba {
 
 constexpr int kVoxelThreads = 128;
-constexpr int kScanThreads = 128;
-constexpr int kDecideThreads = 1024;
+constexpr int kScanThreads = 128;      // FP64 scan pass: threads per scan
+constexpr int kScanMixedThreads = 32;  // mixed scan pass: one warp per scan (long pipelined loops, no block barrier)
+constexpr int kDecideThreads = 256;  // one block; FP64 sums are 1/64 rate, so few warps and few adds
 constexpr int kSolveThreads = 64;  // FP64-serial per scan: small blocks spread the scans over every SM
 
-inline int64_t voxel_pass_blocks(int64_t n_voxels) { return (n_voxels + kVoxelThreads - 1) / kVoxelThreads; }
-inline int64_t solve_blocks(int64_t n_scans) { return (n_scans + kSolveThreads - 1) / kSolveThreads; }
+__host__ __device__ inline int64_t voxel_pass_blocks(int64_t n_voxels) { return (n_voxels + kVoxelThreads - 1) / kVoxelThreads; }
+__host__ __device__ inline int64_t solve_blocks(int64_t n_scans) { return (n_scans + kSolveThreads - 1) / kSolveThreads; }
 
 // ---- batched launches over a job table (one launch per kind for all jobs) ----
 cudaError_t launch_batch_solve(const JobTable& T, int64_t n_blocks, cudaStream_t stream);
