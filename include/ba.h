@@ -313,6 +313,16 @@ void ba_server_destroy(ba_server* s);
 ba_status ba_aggregate_points(int64_t n_obs, const int64_t* point_offsets, const double* points, double* agg_out,
                               void* stream);
 
+/* Check of the device-side wait bound (the paper has no counterpart).  The
+ * staged scan pass of the mixed path waits on mbarriers for its bulk copies,
+ * and every such wait gives up after a bounded number of polls, sets a flag
+ * and lets the host return BA_ERR_TIMEOUT instead of hanging.  This call runs
+ * one warp on `device` that waits on an mbarrier nothing arrives on, with a
+ * limit of `polls` polls (1 .. 1e6), and then a follow-up launch.  Returns
+ * BA_OK if the wait gave up and the context still works, BA_ERR_TIMEOUT if
+ * the wait did not give up, BA_ERR_INVALID_ARG / BA_ERR_CUDA otherwise. */
+ba_status ba_check_bounded_wait(int32_t device, int32_t polls);
+
 /* Allocation-free cost evaluation.  The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory when they need
  * a cost -- a mapping loop on a vehicle under a fixed memory budget, where

@@ -181,6 +181,8 @@ __global__ void expand_gh_kernel(const double* gH, int32_t n_scans, double* g, d
 ba_status read_state(ba_handle* h, DevState* out) {
   CK(h, cudaMemcpyAsync(out, h->d_state, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream), "read state");
   CK(h, cudaStreamSynchronize(h->stream), "synchronize");
+  if (out->wait_timeout)
+    return fail(h, BA_ERR_TIMEOUT, "a bounded device-side wait gave up (staged copies of the scan pass did not land)");
   return BA_OK;
 }
 
@@ -382,7 +384,8 @@ ba_status load_impl(ba_handle* h, int32_t n_scans, int64_t n_voxels, int64_t n_o
     MixedBuffers& mb = h->mb;
     mb.ve32 = (float4*)dev_alloc(h, h->keep, sizeof(float4) * kVe32 * (size_t)lb.n_elems);
     mb.vstate = (float4*)dev_alloc(h, h->keep, sizeof(float4) * 2 * (size_t)n_voxels);
-    mb.se32 = (float*)dev_alloc(h, h->keep, sizeof(float) * 10 * (size_t)n_obs);
+    // + 16 bytes: the staged scan pass copies the float2 array from even indices to even ends
+    mb.se32 = (float*)dev_alloc(h, h->keep, sizeof(float) * 10 * (size_t)n_obs + 16);
     mb.vanchor = (float4*)dev_alloc(h, h->keep, sizeof(float4) * (size_t)n_voxels);
     mb.sref = (double*)dev_alloc(h, h->keep, sizeof(double) * 12 * (size_t)n_scans);
     mb.stab2 = (float*)dev_alloc(h, h->keep, sizeof(float) * 2 * kTab * (size_t)n_scans);
@@ -716,6 +719,24 @@ ba_status ba_gradient(ba_handle* h, double* g, double* H, int32_t mem_kind) {
 
 int64_t ba_kernel_launches(const ba_handle* h) { return h ? h->launches : 0; }
 
+ba_status ba_check_bounded_wait(int32_t device, int32_t polls) {
+  if (polls < 1 || polls > 1000000) return BA_ERR_INVALID_ARG;
+  DeviceGuard g(device);
+  if (!g.ok) return BA_ERR_CUDA;
+  int32_t* d = nullptr;
+  if (cudaMalloc(&d, 2 * sizeof(int32_t)) != cudaSuccess) return BA_ERR_CUDA;
+  int32_t res[2] = {0, 0};
+  cudaError_t e = cudaMemset(d, 0, 2 * sizeof(int32_t));
+  if (e == cudaSuccess) e = launch_wait_probe(polls, d, nullptr);
+  if (e == cudaSuccess) e = cudaMemcpy(res, d, sizeof(int32_t), cudaMemcpyDeviceToHost);
+  // the context must still take work
+  if (e == cudaSuccess) e = cudaMemset(d + 1, 0xff, sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMemcpy(res + 1, d + 1, sizeof(int32_t), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess || res[1] != -1) return BA_ERR_CUDA;
+  return res[0] == 1 ? BA_OK : BA_ERR_TIMEOUT;
+}
+
 int64_t ba_device_bytes(const ba_handle* h) {
   if (!h) return 0;
   int64_t b = 0;
@@ -900,7 +921,7 @@ ba_status refresh(ba_batch* b) {
     size_t cap = n < 16 ? 16 : 2 * n;
     BCK(b, cudaMalloc(&b->d_jobs, sizeof(JobView) * cap), "batch table");
     BCK(b, cudaMalloc(&b->d_prefix, sizeof(int64_t) * 3 * (cap + 1)), "batch table");
-    BCK(b, cudaMalloc(&b->d_done, sizeof(int32_t) * (cap + 1)), "batch table");
+    BCK(b, cudaMalloc(&b->d_done, sizeof(int32_t) * (cap + 2)), "batch table");
     b->cap = cap;
   }
   std::vector<JobView> views(n);
@@ -935,17 +956,23 @@ __global__ void batch_control_kernel(JobTable T, int honor_stop, int reset_stop)
   if (reset_stop) st->stop = 0;
 }
 
+// done[k] = stop flag of job k; done[n] = jobs still running; done[n + 1] =
+// jobs whose bounded device-side waits gave up
 __global__ void batch_status_kernel(JobTable T, int32_t* done) {
-  __shared__ int32_t active;
-  if (threadIdx.x == 0) active = 0;
+  __shared__ int32_t active, timeouts;
+  if (threadIdx.x == 0) active = timeouts = 0;
   __syncthreads();
   for (int k = threadIdx.x; k < T.n_jobs; k += blockDim.x) {
     const int32_t s = T.jobs[k].st->stop;
     done[k] = s;
     if (!s) atomicAdd(&active, 1);
+    if (T.jobs[k].st->wait_timeout) atomicAdd(&timeouts, 1);
   }
   __syncthreads();
-  if (threadIdx.x == 0) done[T.n_jobs] = active;
+  if (threadIdx.x == 0) {
+    done[T.n_jobs] = active;
+    done[T.n_jobs + 1] = timeouts;
+  }
 }
 
 ba_status launch_batch_iteration(ba_batch* b) {
@@ -1071,7 +1098,14 @@ ba_status ba_batch_iterate(ba_batch* b, int32_t n_iters) {
   ++b->launches;
   BCK(b, cudaGetLastError(), "batch control");
   if ((s = run_iterations(b, n_iters)) != BA_OK) return s;
+  batch_status_kernel<<<1, 256, 0, b->stream>>>(T, b->d_done);
+  ++b->launches;
+  BCK(b, cudaGetLastError(), "batch status");
+  int32_t timeouts = 0;
+  BCK(b, cudaMemcpyAsync(&timeouts, b->d_done + T.n_jobs + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, b->stream),
+      "status");
   BCK(b, cudaStreamSynchronize(b->stream), "synchronize");
+  if (timeouts) return bfail(b, BA_ERR_TIMEOUT, "%d job(s): a bounded device-side wait gave up", timeouts);
   return BA_OK;
 }
 
@@ -1095,8 +1129,11 @@ ba_status ba_batch_solve(ba_batch* b, int32_t chunk, int32_t max_rounds, int32_t
     batch_status_kernel<<<1, 256, 0, b->stream>>>(T, b->d_done);
     ++b->launches;
     BCK(b, cudaGetLastError(), "batch status");
-    BCK(b, cudaMemcpyAsync(&active, b->d_done + n, sizeof(int32_t), cudaMemcpyDeviceToHost, b->stream), "status");
+    int32_t counts[2] = {0, 0};
+    BCK(b, cudaMemcpyAsync(counts, b->d_done + n, sizeof(counts), cudaMemcpyDeviceToHost, b->stream), "status");
     BCK(b, cudaStreamSynchronize(b->stream), "synchronize");
+    active = counts[0];
+    if (counts[1]) return bfail(b, BA_ERR_TIMEOUT, "%d job(s): a bounded device-side wait gave up", counts[1]);
     if (active == 0) break;
   }
   if (n_active_out) *n_active_out = active;

@@ -181,17 +181,149 @@ __global__ void __launch_bounds__(kVoxelThreads) voxel_pass_mixed_batch_kernel(J
 }
 
 // ---------------------------------------------------------------------------
-// Scan pass (mixed): one block per scan.  The residual of an observation's
+// Scan pass (mixed): one warp per scan.  The residual of an observation's
 // mean is r = u . (q - c) = u . x - u . (c - a) with x = b + E l + dt as in
 // the voxel pass (world axes).  The derivative terms are those of the FP64
 // scan pass written in the scan's reference axes (lever l, scatter S_ref and
-// w = dR^T u = u + E^T u), accumulated in FP32 per thread, reduced in FP32
-// per block and rotated by dR once per scan.
+// w = dR^T u = u + E^T u), accumulated in FP32 per lane, reduced in FP32 per
+// warp and rotated by dR once per scan.
+//
+// The scan's observations are contiguous in the scan-major copy, so they are
+// staged into shared memory by bulk asynchronous copies (the TMA engine) in
+// chunks of kScanChunk observations, double-buffered and completed on an
+// mbarrier: one chunk is in flight while the previous one is processed, with
+// no registers held for it.  Every wait is bounded; a wait that gives up sets
+// the state's wait_timeout flag and the warp leaves after its copies land.
 // ---------------------------------------------------------------------------
+
+// one observation's terms added to the 27 sums (scan reference axes)
+__device__ __forceinline__ void scan_obs_terms(float (&acc)[32], float4 bN, float4 S4, float2 S2, float4 pl, float4 an,
+                                               const float* ph, float ca, float cb, float dt0, float dt1, float dt2,
+                                               float tr0, float tr1, float tr2, bool gn) {
+  const float b0 = bN.x, b1 = bN.y, b2 = bN.z, N = bN.w;
+  const float S00 = S4.x, S01 = S4.y, S02 = S4.z, S11 = S4.w, S12 = S2.x, S22 = S2.y;
+  const float l0 = b0 + (an.x - tr0), l1 = b1 + (an.y - tr1), l2 = b2 + (an.z - tr2);
+  float el0, el1, el2;
+  apply_E(ph, ca, cb, l0, l1, l2, el0, el1, el2);
+  const float x0 = b0 + el0 + dt0, x1 = b1 + el1 + dt1, x2 = b2 + el2 + dt2;
+  const float r = fmaf(pl.x, x0, fmaf(pl.y, x1, fmaf(pl.z, x2, -pl.w)));
+  // w = dR^T u = u + E^T u = u - a (phi x u) + b (phi x (phi x u))
+  float eu0, eu1, eu2;
+  apply_E(ph, -ca, cb, pl.x, pl.y, pl.z, eu0, eu1, eu2);
+  const float wx = pl.x + eu0, wy = pl.y + eu1, wz = pl.z + eu2;
+  const float Nr = N * r;
+  const float swx = fmaf(S00, wx, fmaf(S01, wy, S02 * wz));
+  const float swy = fmaf(S01, wx, fmaf(S11, wy, S12 * wz));
+  const float swz = fmaf(S02, wx, fmaf(S12, wy, S22 * wz));
+  const float mpx = fmaf(Nr, l0, swx), mpy = fmaf(Nr, l1, swy), mpz = fmaf(Nr, l2, swz);
+  acc[0] += mpy * wz - mpz * wy;
+  acc[1] += mpz * wx - mpx * wz;
+  acc[2] += mpx * wy - mpy * wx;
+  acc[3] += Nr * wx;
+  acc[4] += Nr * wy;
+  acc[5] += Nr * wz;
+  const float Nlx = N * l0, Nly = N * l1, Nlz = N * l2;
+  const float p00 = fmaf(Nlx, l0, S00), p01 = fmaf(Nlx, l1, S01), p02 = fmaf(Nlx, l2, S02);
+  const float p11 = fmaf(Nly, l1, S11), p12 = fmaf(Nly, l2, S12), p22 = fmaf(Nlz, l2, S22);
+  const float b00 = wy * p02 - wz * p01, b10 = wz * p00 - wx * p02, b20 = wx * p01 - wy * p00;
+  const float b01 = wy * p12 - wz * p11, b11 = wz * p01 - wx * p12, b21 = wx * p11 - wy * p01;
+  const float b02 = wy * p22 - wz * p12, b12 = wz * p02 - wx * p22;
+  float h00 = -wz * b01 + wy * b02;
+  float h01 = wz * b00 - wx * b02;
+  float h02 = -wy * b00 + wx * b01;
+  float h11 = wz * b10 - wx * b12;
+  float h12 = -wy * b10 + wx * b11;
+  float h22 = -wy * b20 + wx * b21;
+  if (!gn) {
+    const float wm = fmaf(wx, mpx, fmaf(wy, mpy, wz * mpz));
+    h00 += wx * mpx - wm;
+    h11 += wy * mpy - wm;
+    h22 += wz * mpz - wm;
+    h01 += 0.5f * (wx * mpy + mpx * wy);
+    h02 += 0.5f * (wx * mpz + mpx * wz);
+    h12 += 0.5f * (wy * mpz + mpy * wz);
+  }
+  acc[6] += h00;
+  acc[7] += h01;
+  acc[8] += h02;
+  const float cx = Nly * wz - Nlz * wy, cy = Nlz * wx - Nlx * wz, cz = Nlx * wy - Nly * wx;
+  acc[9] += cx * wx;
+  acc[10] += cx * wy;
+  acc[11] += cx * wz;
+  acc[12] += h11;
+  acc[13] += h12;
+  acc[14] += cy * wx;
+  acc[15] += cy * wy;
+  acc[16] += cy * wz;
+  acc[17] += h22;
+  acc[18] += cz * wx;
+  acc[19] += cz * wy;
+  acc[20] += cz * wz;
+  const float Nwx = N * wx, Nwy = N * wy;
+  acc[21] += Nwx * wx;
+  acc[22] += Nwx * wy;
+  acc[23] += Nwx * wz;
+  acc[24] += Nwy * wy;
+  acc[25] += Nwy * wz;
+  acc[26] += N * wz * wz;
+}
+
+// Shared-memory image of one chunk of a scan's observations.  Every array
+// starts and ends on a 16-byte boundary (bulk copies need both); the float2
+// and int32 arrays are copied from the 16-byte boundary at or below the
+// chunk's first observation, hence the slack.
+struct ScanChunk {
+  float4 bN[kScanChunk];
+  float4 S4[kScanChunk];
+  float2 S2[kScanChunk + 2];
+  int32_t vox[kScanChunk + 8];
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               :
+               : "r"(dst), "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
+// true once the barrier's phase with this parity has completed; false if it
+// did not within the iteration limit
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, int limit = kWaitLimit) {
+  for (int it = 0; it < limit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// lane 0: copies of observations [o0, o1) of the scan-major arrays into S,
+// completing on the barrier
+__device__ __forceinline__ void issue_scan_chunk(ScanChunk& S, uint32_t bar, const float4* sbN, const float4* sS4,
+                                                 const float2* sS2, const int32_t* svox, int64_t o0, int64_t o1) {
+  const int64_t n = o1 - o0;
+  const int64_t s2 = o0 & ~1ll, e2 = (o1 + 1) & ~1ll;
+  const int64_t s4 = o0 & ~3ll, e4 = (o1 + 3) & ~3ll;
+  const uint32_t bytes = (uint32_t)(32 * n + 8 * (e2 - s2) + 4 * (e4 - s4));
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" : : "r"(bar), "r"(bytes) : "memory");
+  bulk_g2s(smem_u32(S.bN), sbN + o0, (uint32_t)(16 * n), bar);
+  bulk_g2s(smem_u32(S.S4), sS4 + o0, (uint32_t)(16 * n), bar);
+  bulk_g2s(smem_u32(S.S2), sS2 + s2, (uint32_t)(8 * (e2 - s2)), bar);
+  bulk_g2s(smem_u32(S.vox), svox + s4, (uint32_t)(4 * (e4 - s4)), bar);
+}
+
 __device__ __forceinline__ void scan_pass_mixed_body(const DevLayout& L, const DevMixed& X,
-                                                     double* __restrict__ gH, const DevState* __restrict__ st,
-                                                     int force, int j, float (*red)[kGH], float* tot, float* dR) {
+                                                     double* __restrict__ gH, DevState* __restrict__ st,
+                                                     int force, int j, float (*red)[kGH], float* tot, float* dR,
+                                                     ScanChunk* chunks, uint64_t* bars) {
   if (!force && !st->scan_pending) return;
+  const int lane = threadIdx.x & 31;
   const int buf = st->cur;
   const float* tb = X.stab2 + ((int64_t)buf * L.n_scans + j) * kTab;
   // dR = I + E, E x = ca (v x x) + cb v x (v x x) for the unit quaternion (w, v) of dR
@@ -205,122 +337,75 @@ __device__ __forceinline__ void scan_pass_mixed_body(const DevLayout& L, const D
   for (int k = 0; k < 32; ++k) acc[k] = 0.f;
   const int64_t lo = L.scan_off[j], hi = L.scan_off[j + 1];
   const int64_t no = L.n_obs;
-  const float4* __restrict__ sbN = reinterpret_cast<const float4*>(X.se32);
-  const float4* __restrict__ sS4 = sbN + no;
-  const float2* __restrict__ sS2 = reinterpret_cast<const float2*>(sS4 + no);
-  // software pipeline: the record of the thread's next observation and its
-  // voxel's plane are loaded while the current one is processed, and the
-  // voxel index one step further ahead, so no load waits on another
-  int64_t o = lo + threadIdx.x;
-  float4 nbN = make_float4(0.f, 0.f, 0.f, 0.f), nS4 = nbN, npl = nbN, nan = nbN;
-  float2 nS2 = make_float2(0.f, 0.f);
-  int32_t pv2 = 0;
-  if (o < hi) {
-    const int32_t pv1 = __ldg(L.se_vox + o);
-    if (o + kScanMixedThreads < hi) pv2 = __ldg(L.se_vox + o + kScanMixedThreads);
-    nbN = __ldg(sbN + o);
-    nS4 = __ldg(sS4 + o);
-    nS2 = __ldg(sS2 + o);
-    npl = __ldg(prec + 2 * (int64_t)pv1);
-    nan = __ldg(prec + 2 * (int64_t)pv1 + 1);
+  const float4* sbN = reinterpret_cast<const float4*>(X.se32);
+  const float4* sS4 = sbN + no;
+  const float2* sS2 = reinterpret_cast<const float2*>(sS4 + no);
+  const int64_t nch = (hi - lo + kScanChunk - 1) / kScanChunk;
+  const uint32_t bar0 = smem_u32(&bars[0]), bar1 = smem_u32(&bars[1]);
+  if (lane == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" : : "r"(bar0) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" : : "r"(bar1) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" : : : "memory");
+    if (nch > 0) issue_scan_chunk(chunks[0], bar0, sbN, sS4, sS2, L.se_vox, lo, min(hi, lo + kScanChunk));
+    if (nch > 1)
+      issue_scan_chunk(chunks[1], bar1, sbN, sS4, sS2, L.se_vox, lo + kScanChunk, min(hi, lo + 2 * kScanChunk));
   }
-  for (; o < hi; o += kScanMixedThreads) {
-    const float4 bN = nbN, S4 = nS4, pl = npl, an = nan;
-    const float2 S2 = nS2;
-    const int64_t on = o + kScanMixedThreads;
-    if (on < hi) {
-      nbN = __ldg(sbN + on);
-      nS4 = __ldg(sS4 + on);
-      nS2 = __ldg(sS2 + on);
-      // plane and anchor of the voxel: one 32-byte record
-      npl = __ldg(prec + 2 * (int64_t)pv2);
-      nan = __ldg(prec + 2 * (int64_t)pv2 + 1);
-      if (on + kScanMixedThreads < hi) pv2 = __ldg(L.se_vox + on + kScanMixedThreads);
+  __syncwarp();
+  int64_t k = 0;
+  bool ok = true;
+  for (; k < nch; ++k) {
+    const int b = (int)(k & 1);
+    const bool landed = mbar_wait_bounded(b ? bar1 : bar0, (uint32_t)((k >> 1) & 1));
+    if (__any_sync(0xffffffffu, !landed)) {
+      ok = false;
+      break;
     }
-    const float b0 = bN.x, b1 = bN.y, b2 = bN.z, N = bN.w;
-    const float S00 = S4.x, S01 = S4.y, S02 = S4.z, S11 = S4.w, S12 = S2.x, S22 = S2.y;
-    const float l0 = b0 + (an.x - tr0), l1 = b1 + (an.y - tr1), l2 = b2 + (an.z - tr2);
-    float el0, el1, el2;
-    apply_E(ph, ca, cb, l0, l1, l2, el0, el1, el2);
-    const float x0 = b0 + el0 + dt0, x1 = b1 + el1 + dt1, x2 = b2 + el2 + dt2;
-    const float r = fmaf(pl.x, x0, fmaf(pl.y, x1, fmaf(pl.z, x2, -pl.w)));
-    // w = dR^T u = u + E^T u = u - a (phi x u) + b (phi x (phi x u))
-    float eu0, eu1, eu2;
-    apply_E(ph, -ca, cb, pl.x, pl.y, pl.z, eu0, eu1, eu2);
-    const float wx = pl.x + eu0, wy = pl.y + eu1, wz = pl.z + eu2;
-    const float Nr = N * r;
-    const float swx = fmaf(S00, wx, fmaf(S01, wy, S02 * wz));
-    const float swy = fmaf(S01, wx, fmaf(S11, wy, S12 * wz));
-    const float swz = fmaf(S02, wx, fmaf(S12, wy, S22 * wz));
-    const float mpx = fmaf(Nr, l0, swx), mpy = fmaf(Nr, l1, swy), mpz = fmaf(Nr, l2, swz);
-    acc[0] += mpy * wz - mpz * wy;
-    acc[1] += mpz * wx - mpx * wz;
-    acc[2] += mpx * wy - mpy * wx;
-    acc[3] += Nr * wx;
-    acc[4] += Nr * wy;
-    acc[5] += Nr * wz;
-    const float Nlx = N * l0, Nly = N * l1, Nlz = N * l2;
-    const float p00 = fmaf(Nlx, l0, S00), p01 = fmaf(Nlx, l1, S01), p02 = fmaf(Nlx, l2, S02);
-    const float p11 = fmaf(Nly, l1, S11), p12 = fmaf(Nly, l2, S12), p22 = fmaf(Nlz, l2, S22);
-    const float b00 = wy * p02 - wz * p01, b10 = wz * p00 - wx * p02, b20 = wx * p01 - wy * p00;
-    const float b01 = wy * p12 - wz * p11, b11 = wz * p01 - wx * p12, b21 = wx * p11 - wy * p01;
-    const float b02 = wy * p22 - wz * p12, b12 = wz * p02 - wx * p22;
-    float h00 = -wz * b01 + wy * b02;
-    float h01 = wz * b00 - wx * b02;
-    float h02 = -wy * b00 + wx * b01;
-    float h11 = wz * b10 - wx * b12;
-    float h12 = -wy * b10 + wx * b11;
-    float h22 = -wy * b20 + wx * b21;
-    if (!gn) {
-      const float wm = fmaf(wx, mpx, fmaf(wy, mpy, wz * mpz));
-      h00 += wx * mpx - wm;
-      h11 += wy * mpy - wm;
-      h22 += wz * mpz - wm;
-      h01 += 0.5f * (wx * mpy + mpx * wy);
-      h02 += 0.5f * (wx * mpz + mpx * wz);
-      h12 += 0.5f * (wy * mpz + mpy * wz);
+    const ScanChunk& S = chunks[b];
+    const int64_t c0 = lo + k * kScanChunk;
+    const int n = (int)min((int64_t)kScanChunk, hi - c0);
+    const int off2 = (int)(c0 & 1), off4 = (int)(c0 & 3);
+    // the planes of the lane's observations of the chunk first (L2 gathers in flight together)
+    float4 pl[kScanChunk / 32], an[kScanChunk / 32];
+#pragma unroll
+    for (int q = 0; q < kScanChunk / 32; ++q) {
+      const int i = lane + 32 * q;
+      if (i < n) {
+        const int64_t pv = S.vox[i + off4];
+        pl[q] = __ldg(prec + 2 * pv);
+        an[q] = __ldg(prec + 2 * pv + 1);
+      }
     }
-    acc[6] += h00;
-    acc[7] += h01;
-    acc[8] += h02;
-    const float cx = Nly * wz - Nlz * wy, cy = Nlz * wx - Nlx * wz, cz = Nlx * wy - Nly * wx;
-    acc[9] += cx * wx;
-    acc[10] += cx * wy;
-    acc[11] += cx * wz;
-    acc[12] += h11;
-    acc[13] += h12;
-    acc[14] += cy * wx;
-    acc[15] += cy * wy;
-    acc[16] += cy * wz;
-    acc[17] += h22;
-    acc[18] += cz * wx;
-    acc[19] += cz * wy;
-    acc[20] += cz * wz;
-    const float Nwx = N * wx, Nwy = N * wy;
-    acc[21] += Nwx * wx;
-    acc[22] += Nwx * wy;
-    acc[23] += Nwx * wz;
-    acc[24] += Nwy * wy;
-    acc[25] += Nwy * wz;
-    acc[26] += N * wz * wz;
+#pragma unroll
+    for (int q = 0; q < kScanChunk / 32; ++q) {
+      const int i = lane + 32 * q;
+      if (i < n)
+        scan_obs_terms(acc, S.bN[i], S.S4[i], S.S2[i + off2], pl[q], an[q], ph, ca, cb, dt0, dt1, dt2, tr0, tr1,
+                       tr2, gn);
+    }
+    __syncwarp();
+    if (lane == 0 && k + 2 < nch) {
+      // the buffer's previous contents were read through the generic proxy
+      asm volatile("fence.proxy.async.shared::cta;" : : : "memory");
+      issue_scan_chunk(chunks[b], b ? bar1 : bar0, sbN, sS4, sS2, L.se_vox, c0 + 2 * kScanChunk,
+                       min(hi, c0 + 3 * kScanChunk));
+    }
   }
-  // FP32 block reduction: the per-scan sums only need FP32 (their rounding is
+  if (!ok) {
+    // flag the failure, let the copies already issued land (bounded again), and leave
+    if (lane == 0) {
+      atomicExch(&st->wait_timeout, 1);
+      for (int64_t q = k; q < nch && q < k + 2; ++q) mbar_wait_bounded((q & 1) ? bar1 : bar0, (uint32_t)((q >> 1) & 1));
+    }
+    __syncwarp();
+    return;
+  }
+  // FP32 warp reduction: the per-scan sums only need FP32 (their rounding is
   // far below what moves a pose by 1e-9 rad given H's size), and GB300's FP64
   // pipe is 1/64 of FP32, so FP64 is kept out of the reduction.
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  static_assert(kScanMixedThreads == 32, "the staged scan pass runs one warp per scan");
+  (void)red;
   warp_reduce_scatter32(acc);
-  if (kScanMixedThreads == 32) {
-    if (l < kGH) tot[l] = acc[0];
-  } else {
-    if (l < kGH) red[w][l] = acc[0];
-    __syncthreads();
-    if (threadIdx.x < kGH) {
-      float v = 0.f;
-#pragma unroll
-      for (int q = 0; q < kScanMixedThreads / 32; ++q) v += red[q][threadIdx.x];
-      tot[threadIdx.x] = v;
-    }
-  }
+  if (lane < kGH) tot[lane] = acc[0];
   if (threadIdx.x < 9) {
     // dR = I + a [phi]x + b [phi]x^2, entry (r, c)
     const int r = threadIdx.x / 3, c = threadIdx.x % 3;
@@ -365,18 +450,22 @@ __device__ __forceinline__ void scan_pass_mixed_body(const DevLayout& L, const D
 }
 
 __global__ void __launch_bounds__(kScanMixedThreads, 24) scan_pass_mixed_kernel(DevLayout L, DevMixed X,
-                                                                      double* __restrict__ gH,
-                                                                      const DevState* __restrict__ st, int force) {
-  __shared__ float red[kScanMixedThreads / 32][kGH];
+                                                                                  double* __restrict__ gH,
+                                                                                  DevState* __restrict__ st, int force) {
+  __shared__ float red[1][kGH];
   __shared__ float tot[kGH];
   __shared__ float dR[9];
-  scan_pass_mixed_body(L, X, gH, st, force, blockIdx.x, red, tot, dR);
+  __shared__ ScanChunk chunks[2];
+  __shared__ uint64_t bars[2];
+  scan_pass_mixed_body(L, X, gH, st, force, blockIdx.x, red, tot, dR, chunks, bars);
 }
 
 __global__ void __launch_bounds__(kScanMixedThreads, 20) scan_pass_mixed_batch_kernel(JobTable T) {
-  __shared__ float red[kScanMixedThreads / 32][kGH];
+  __shared__ float red[1][kGH];
   __shared__ float tot[kGH];
   __shared__ float dR[9];
+  __shared__ ScanChunk chunks[2];
+  __shared__ uint64_t bars[2];
   __shared__ JobView J;
   __shared__ int j;
   if (threadIdx.x == 0) {
@@ -385,7 +474,21 @@ __global__ void __launch_bounds__(kScanMixedThreads, 20) scan_pass_mixed_batch_k
     j = (int)(blockIdx.x - T.sblk[job]);
   }
   __syncthreads();
-  scan_pass_mixed_body(J.L, J.X, J.gH, J.st, 0, j, red, tot, dR);
+  scan_pass_mixed_body(J.L, J.X, J.gH, J.st, 0, j, red, tot, dR, chunks, bars);
+}
+
+// Check of the bounded wait itself: an mbarrier that nothing arrives on, so
+// the wait must give up after `limit` polls.  out[0] = 1 if it gave up.
+__global__ void wait_probe_kernel(int limit, int32_t* out) {
+  __shared__ uint64_t bar;
+  const uint32_t b = smem_u32(&bar);
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" : : "r"(b) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" : : : "memory");
+  }
+  __syncwarp();
+  const bool landed = mbar_wait_bounded(b, 0u, limit);
+  if (threadIdx.x == 0) out[0] = landed ? 0 : 1;
 }
 
 // Per-scan FP32 table of buffer `buf` from the FP64 poses of that buffer.
@@ -411,7 +514,7 @@ cudaError_t launch_voxel_pass_mixed(const DevLayout& L, const DevMixed& X, doubl
 }
 
 cudaError_t launch_scan_pass_mixed(const DevLayout& L, const DevMixed& X, const double* poses2, double* gH,
-                                   const DevState* st, int force, cudaStream_t stream) {
+                                   DevState* st, int force, cudaStream_t stream) {
   if (L.n_scans == 0) return cudaSuccess;
   (void)poses2;
   scan_pass_mixed_kernel<<<(unsigned)L.n_scans, kScanMixedThreads, 0, stream>>>(L, X, gH, st, force);
@@ -425,6 +528,11 @@ cudaError_t launch_batch_voxel_pass_mixed(const JobTable& T, int64_t n_blocks, i
 
 cudaError_t launch_batch_scan_pass_mixed(const JobTable& T, int64_t n_blocks, cudaStream_t stream) {
   scan_pass_mixed_batch_kernel<<<(unsigned)n_blocks, kScanMixedThreads, 0, stream>>>(T);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wait_probe(int limit, int32_t* out, cudaStream_t stream) {
+  wait_probe_kernel<<<1, 32, 0, stream>>>(limit, out);
   return cudaGetLastError();
 }
 

@@ -428,7 +428,8 @@ cudaError_t build_layout(const LoadInput& in, int max_len, bool fill_f64, Alloca
   out->vperm = (int32_t*)keep.fn(keep.self, sizeof(int32_t) * nv);
   out->scan_off = (int64_t*)keep.fn(keep.self, sizeof(int64_t) * (in.n_scans + 1));
   out->se = fill_f64 ? (double*)keep.fn(keep.self, sizeof(double) * 10 * no) : nullptr;
-  out->se_vox = (int32_t*)keep.fn(keep.self, sizeof(int32_t) * no);
+  // + 4 entries: the staged mixed scan pass copies whole 16-byte groups
+  out->se_vox = (int32_t*)keep.fn(keep.self, sizeof(int32_t) * (no + 4));
   if (!keys || !vals || !tk || !tv || !scratch || !vrank || !obs_vox || !vscale || !out->slice_off || !out->vlen ||
       !out->vperm || !out->scan_off || (fill_f64 && !out->se) || (!fill_f64 && !order) || !out->se_vox)
     return cudaErrorMemoryAllocation;

@@ -82,6 +82,8 @@ struct DevMixed {
   float4* planes32_2;    // 2 buffers x n_voxels x 2 float4: (u (3), u . (c - a)), (a (3), 0)
 };
 constexpr int kTab = 12;
+constexpr int kScanChunk = 64;        // observations per staged chunk of the mixed scan pass
+constexpr int kWaitLimit = 1 << 22;   // polls of an mbarrier before a wait gives up
 constexpr int kVe32 = 3;  // float4 per slot of the voxel-pass copy
 
 // Rotation matrix (row-major) of the unit quaternion (w, x, y, z).
@@ -161,6 +163,7 @@ struct DevState {
   int32_t max_consec_reject;
   int32_t hess_mode;
   int32_t scan_pending;     // an accepted step needs g, H at the new poses
+  int32_t wait_timeout;     // a bounded device-side wait gave up (sticky)
 };
 
 // One job of a batch: everything its kernels touch.  A batch launches each

@@ -105,7 +105,7 @@ cudaError_t build_layout(const LoadInput& in, int max_len, bool fill_f64, Alloca
 cudaError_t launch_voxel_pass_mixed(const DevLayout& L, const DevMixed& X, double* full_out, double* cost_part,
                                     const DevState* st, int use_trial, cudaStream_t stream);
 cudaError_t launch_scan_pass_mixed(const DevLayout& L, const DevMixed& X, const double* poses2, double* gH,
-                                   const DevState* st, int force, cudaStream_t stream);
+                                   DevState* st, int force, cudaStream_t stream);
 cudaError_t launch_scan_table(int32_t n_scans, const double* poses2, const double* sref, float* stab2, int buf,
                               cudaStream_t stream);
 // Build (or rebuild) the FP32 copies, frames, anchors and reference poses at
@@ -121,6 +121,9 @@ struct MixedBuffers {
 };
 cudaError_t build_mixed(const LoadInput& in, const LayoutBuffers& lb, const double* poses2, MixedBuffers& mb,
                         cudaStream_t stream, int64_t* launches);
+
+// bounded-wait check: out[0] = 1 if an mbarrier wait that cannot complete gave up
+cudaError_t launch_wait_probe(int limit, int32_t* out, cudaStream_t stream);
 
 // points -> centred clusters
 cudaError_t launch_aggregate_points(int64_t n_obs, const int64_t* point_off, const double* points, double* agg_out,

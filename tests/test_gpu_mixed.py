@@ -139,3 +139,17 @@ def test_mixed_matches_fp64_path_on_city_slice(mm):
             assert sa["cost"] == pytest.approx(ev.cost(), rel=COST_TOL), k
         r, t = pose_errors(a.poses(), b.poses())
         assert r < ROT_TOL and t < TRANS_TOL, (r, t)
+
+
+def test_bounded_wait_gives_up_and_context_survives(mm):
+    """The mbarrier waits of the staged scan pass are bounded: a wait on a
+    barrier nothing arrives on gives up after its poll limit (no hang), the
+    host sees it, and the context still runs a solve afterwards."""
+    from paper_2608_14266_gb300 import _lib
+    assert _lib.lib().ba_check_bounded_wait(0, 2000) == 0
+    assert _lib.lib().ba_check_bounded_wait(0, 0) == 1  # invalid limit
+    s, pts, po, raw, cen = tiny_scene()
+    with _mixed(mm) as ba:
+        ba.load_observations(s.n_scans, s.voxel_off, s.obs_scan, cen, s.pose_init)
+        st = ba.iterate(3)
+        assert st["iters"] == 3 and np.isfinite(st["cost"])
