@@ -279,30 +279,6 @@ struct ScanChunk {
   int32_t vox[kScanChunk + 8];
 };
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-               :
-               : "r"(dst), "l"(src), "r"(bytes), "r"(bar)
-               : "memory");
-}
-
-// true once the barrier's phase with this parity has completed; false if it
-// did not within the iteration limit
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, int limit = kWaitLimit) {
-  for (int it = 0; it < limit; ++it) {
-    uint32_t done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    if (done) return true;
-  }
-  return false;
-}
-
 // lane 0: copies of observations [o0, o1) of the scan-major arrays into S,
 // completing on the barrier
 __device__ __forceinline__ void issue_scan_chunk(ScanChunk& S, uint32_t bar, const float4* sbN, const float4* sS4,
@@ -502,7 +478,7 @@ __global__ void scan_table_kernel(int32_t n_scans, const double* poses2, const d
 // ---- launchers ---------------------------------------------------------------
 
 cudaError_t launch_voxel_pass_mixed(const DevLayout& L, const DevMixed& X, double* full_out, double* cost_part,
-                                    const DevState* st, int use_trial, cudaStream_t stream) {
+                                    DevState* st, int use_trial, cudaStream_t stream) {
   const int64_t nb = voxel_pass_blocks(L.n_voxels);
   if (full_out)
     voxel_pass_mixed_kernel<true><<<(unsigned)nb, kVoxelThreads, 0, stream>>>(L, X, full_out, cost_part, st,

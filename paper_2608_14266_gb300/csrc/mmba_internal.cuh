@@ -496,6 +496,48 @@ __device__ __forceinline__ void warp_reduce_scatter32(float (&a)[32]) {
   }
 }
 
+// ---- bulk asynchronous copies (TMA engine) into shared memory ----
+// A copy needs 16-byte aligned source and destination and a size that is a
+// multiple of 16; it completes on an mbarrier as transaction bytes.
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               :
+               : "r"(dst), "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
+// true once the barrier's phase with this parity has completed; false if it
+// did not within the iteration limit
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, int limit = kWaitLimit) {
+  for (int it = 0; it < limit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" : : "r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" : : "r"(bar), "r"(bytes) : "memory");
+}
+
+// make barrier initialisation visible to the async proxy
+__device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;" : : : "memory"); }
+
+// order this thread's earlier generic-proxy accesses to shared memory before
+// later async-proxy writes (re-filling a buffer that was just read)
+__device__ __forceinline__ void async_proxy_fence() { asm volatile("fence.proxy.async.shared::cta;" : : : "memory"); }
+
 // Deterministic block-wide sum (fixed shape for a given blockDim).
 template <int kThreads, typename T = double>
 __device__ inline T block_sum(T v, T* smem /* kThreads / 32 */) {

@@ -103,7 +103,7 @@ cudaError_t build_layout(const LoadInput& in, int max_len, bool fill_f64, Alloca
 
 // ---- mixed precision ----
 cudaError_t launch_voxel_pass_mixed(const DevLayout& L, const DevMixed& X, double* full_out, double* cost_part,
-                                    const DevState* st, int use_trial, cudaStream_t stream);
+                                    DevState* st, int use_trial, cudaStream_t stream);
 cudaError_t launch_scan_pass_mixed(const DevLayout& L, const DevMixed& X, const double* poses2, double* gH,
                                    DevState* st, int force, cudaStream_t stream);
 cudaError_t launch_scan_table(int32_t n_scans, const double* poses2, const double* sref, float* stab2, int buf,
