@@ -180,6 +180,12 @@ int64_t ba_kernel_launches(const ba_handle* h);
 /* Device bytes the handle holds for its loaded problem (0 if none). */
 int64_t ba_device_bytes(const ba_handle* h);
 
+/* Without a user allocator, device memory comes from a library-owned
+ * stream-ordered pool per device that keeps freed memory for the next problem
+ * (no unmapping and remapping between jobs).  This call waits for the device
+ * to go idle and returns the pool's unused memory to the driver. */
+ba_status ba_release_cached_memory(int32_t device);
+
 /* Upper estimate of the device bytes a handle of this precision holds for a
  * problem of these sizes once loaded, and of the extra bytes its load needs
  * transiently (*peak_extra, may be NULL), for admission control. */

@@ -294,10 +294,27 @@ class Batch:
             pass
 
 
-class BundleAdjuster:
-    """Owns one library handle; see include/ba.h for the semantics of each call."""
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 
-    def __init__(self, **cfg):
+
+class BundleAdjuster:
+    """Owns one library handle; see include/ba.h for the semantics of each call.
+
+    alloc(bytes, stream) -> device pointer (int, 0 on failure) and
+    free(ptr, bytes, stream), if given, replace the library's own pool for the
+    handle's device memory (e.g. to draw from PyTorch's caching allocator)."""
+
+    def __init__(self, alloc=None, free=None, **cfg):
+        self._callbacks = None
+        if (alloc is None) != (free is None):
+            raise ValueError("alloc and free must be given together")
+        if alloc is not None:
+            a = ALLOC_FN(lambda n, stream, ctx: alloc(int(n), stream) or None)
+            f = FREE_FN(lambda ptr, n, stream, ctx: free(int(ptr), int(n), stream))
+            self._callbacks = (a, f)  # kept alive as long as the handle
+            cfg["alloc"] = ctypes.cast(a, ctypes.c_void_p)
+            cfg["free"] = ctypes.cast(f, ctypes.c_void_p)
         self.cfg = ba_config_default(**cfg)
         self.h = ba_create(self.cfg)
         self.n_scans = 0

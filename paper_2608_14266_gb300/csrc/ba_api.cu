@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -94,14 +95,46 @@ ba_status cuda_fail(ba_handle* h, cudaError_t e, const char* what) {
     if (e_ != cudaSuccess) return cuda_fail(h, e_, what); \
   } while (0)
 
+// Library-owned stream-ordered memory pool per device.  Its release threshold
+// is unlimited, so memory freed by one problem is reused by the next without
+// being unmapped and mapped again (the default pool returns it at every
+// synchronisation); ba_release_cached_memory() trims it.
+std::mutex g_pool_mu;
+cudaMemPool_t g_pools[64] = {};
+
+cudaMemPool_t lib_pool(int dev) {
+  if (dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (!g_pools[dev]) {
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    uint64_t keep_all = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep_all);
+    g_pools[dev] = pool;
+  }
+  return g_pools[dev];
+}
+
 void* dev_alloc(ba_handle* h, std::vector<DevAlloc>& list, size_t bytes) {
   if (bytes == 0) bytes = 16;
   void* p = nullptr;
   if (h->cfg.alloc) {
     p = h->cfg.alloc(bytes, (void*)h->stream, h->cfg.alloc_ctx);
-  } else if (cudaMallocAsync(&p, bytes, h->stream) != cudaSuccess) {
-    cudaGetLastError();
-    p = nullptr;
+  } else {
+    cudaMemPool_t pool = lib_pool(h->cfg.device);
+    const cudaError_t e =
+        pool ? cudaMallocFromPoolAsync(&p, bytes, pool, h->stream) : cudaMallocAsync(&p, bytes, h->stream);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+    }
   }
   if (p) list.push_back({p, bytes});
   return p;
@@ -387,7 +420,8 @@ ba_status load_impl(ba_handle* h, int32_t n_scans, int64_t n_voxels, int64_t n_o
     // + 16 bytes: the staged scan pass copies the float2 array from even indices to even ends
     mb.se32 = (float*)dev_alloc(h, h->keep, sizeof(float) * 10 * (size_t)n_obs + 16);
     mb.vanchor = (float4*)dev_alloc(h, h->keep, sizeof(float4) * (size_t)n_voxels);
-    mb.sref = (double*)dev_alloc(h, h->keep, sizeof(double) * 12 * (size_t)n_scans);
+    // FP64 reference poses, then their FP32 copy (see scan_ref_kernel)
+    mb.sref = (double*)dev_alloc(h, h->keep, (sizeof(double) + sizeof(float)) * 12 * (size_t)n_scans);
     mb.stab2 = (float*)dev_alloc(h, h->keep, sizeof(float) * 2 * kTab * (size_t)n_scans);
     mb.planes32_2 = (float4*)dev_alloc(h, h->keep, sizeof(float4) * 2 * 2 * (size_t)n_voxels);
     if (!mb.ve32 || !mb.vstate || !mb.se32 || !mb.vanchor || !mb.sref || !mb.stab2 || !mb.planes32_2)
@@ -718,6 +752,19 @@ ba_status ba_gradient(ba_handle* h, double* g, double* H, int32_t mem_kind) {
 }
 
 int64_t ba_kernel_launches(const ba_handle* h) { return h ? h->launches : 0; }
+
+ba_status ba_release_cached_memory(int32_t device) {
+  if (device < 0 || device >= 64) return BA_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (!g_pools[device]) return BA_OK;
+  DeviceGuard g(device);
+  if (!g.ok) return BA_ERR_CUDA;
+  if (cudaDeviceSynchronize() != cudaSuccess || cudaMemPoolTrimTo(g_pools[device], 0) != cudaSuccess) {
+    cudaGetLastError();
+    return BA_ERR_CUDA;
+  }
+  return BA_OK;
+}
 
 ba_status ba_check_bounded_wait(int32_t device, int32_t polls) {
   if (polls < 1 || polls > 1000000) return BA_ERR_INVALID_ARG;

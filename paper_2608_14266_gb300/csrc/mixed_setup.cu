@@ -33,23 +33,39 @@ __device__ inline void centred_cluster(const double* a, int form, double out[10]
   out[9] = n;
 }
 
-// reference pose of each scan: R_ref = R, t_ref = t rounded to FP32
+// reference pose of each scan: R_ref = R, t_ref = t rounded to FP32; the
+// sref buffer holds n_scans x 12 doubles followed by the same 12 values of
+// every scan in FP32 (sref32), so per-observation set-up needs no FP64 -> FP32
+// conversions of the rotation
 __global__ void scan_ref_kernel(int32_t n_scans, const double* poses, double* sref) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n_scans) return;
   const double* P = poses + 12 * (int64_t)j;
   double* o = sref + 12 * (int64_t)j;
-  for (int k = 0; k < 9; ++k) o[k] = P[k];
-  for (int k = 9; k < 12; ++k) o[k] = (double)(float)P[k];
+  float* f = reinterpret_cast<float*>(sref + 12 * (int64_t)n_scans) + 12 * (int64_t)j;
+  for (int k = 0; k < 9; ++k) {
+    o[k] = P[k];
+    f[k] = (float)P[k];
+  }
+  for (int k = 9; k < 12; ++k) {
+    o[k] = (double)(float)P[k];
+    f[k] = (float)P[k];
+  }
 }
 
-// FP32 copy of the packed symmetric R S R^T (R, S in FP64, products in FP32)
-__device__ inline void rot_sym_f(const double* R, const double* S, float* out) {
-  float Rf[9], M[3][3];
-#pragma unroll
-  for (int k = 0; k < 9; ++k) Rf[k] = (float)R[k];
-  M[0][0] = (float)S[0]; M[0][1] = M[1][0] = (float)S[1]; M[0][2] = M[2][0] = (float)S[2];
-  M[1][1] = (float)S[3]; M[1][2] = M[2][1] = (float)S[4]; M[2][2] = (float)S[5];
+__device__ __forceinline__ const float* sref32_of(const double* sref, int32_t n_scans, int32_t j) {
+  return reinterpret_cast<const float*>(sref + 12 * (int64_t)n_scans) + 12 * (int64_t)j;
+}
+
+// packed symmetric R S R^T in FP32 (R row-major, S packed xx xy xz yy yz zz)
+__device__ inline void rot_sym_f(const float* Rf, const float* Sf, float* out) {
+  float M[3][3];
+  M[0][0] = Sf[0];
+  M[0][1] = M[1][0] = Sf[1];
+  M[0][2] = M[2][0] = Sf[2];
+  M[1][1] = Sf[3];
+  M[1][2] = M[2][1] = Sf[4];
+  M[2][2] = Sf[5];
   float T[3][3];
 #pragma unroll
   for (int r = 0; r < 3; ++r)
@@ -64,11 +80,11 @@ __device__ inline void rot_sym_f(const double* R, const double* S, float* out) {
 }
 
 // posed mean of a cluster relative to the point p0 (FP64 offsets, FP32 lever)
-__device__ inline void posed_rel(const double* c, const double* R, const double* t, const double* p0, float* q) {
+__device__ inline void posed_rel(const double* c, const float* Rf, const double* t, const double* p0, float* q) {
+  const float m0 = (float)c[6], m1 = (float)c[7], m2 = (float)c[8];
 #pragma unroll
   for (int a = 0; a < 3; ++a)
-    q[a] = fmaf((float)R[3 * a], (float)c[6],
-                fmaf((float)R[3 * a + 1], (float)c[7], fmaf((float)R[3 * a + 2], (float)c[8], (float)(t[a] - p0[a]))));
+    q[a] = fmaf(Rf[3 * a], m0, fmaf(Rf[3 * a + 1], m1, fmaf(Rf[3 * a + 2], m2, (float)(t[a] - p0[a]))));
 }
 
 // anchor (FP32-rounded centroid) and starting frame (eigenvectors, normal
@@ -95,7 +111,7 @@ __global__ void voxel_frames_kernel(LoadInput in, const double* sref, const int3
     centred_cluster(in.agg + 10 * o, in.agg_form, c);
     const int32_t j = in.obs_scan[o];
     float q[3];
-    posed_rel(c, sref + 12 * (int64_t)j, in.poses + 12 * (int64_t)j + 9, p0, q);
+    posed_rel(c, sref32_of(sref, in.n_scans, j), in.poses + 12 * (int64_t)j + 9, p0, q);
     const float N = (float)c[9];
     cx = fmaf(N, q[0], cx);
     cy = fmaf(N, q[1], cy);
@@ -111,8 +127,10 @@ __global__ void voxel_frames_kernel(LoadInput in, const double* sref, const int3
     centred_cluster(in.agg + 10 * o, in.agg_form, c);
     const int32_t j = in.obs_scan[o];
     float q[3], rs[6];
-    posed_rel(c, sref + 12 * (int64_t)j, in.poses + 12 * (int64_t)j + 9, p0, q);
-    rot_sym_f(sref + 12 * (int64_t)j, c, rs);
+    const float* Rf = sref32_of(sref, in.n_scans, j);
+    posed_rel(c, Rf, in.poses + 12 * (int64_t)j + 9, p0, q);
+    const float Sf[6] = {(float)c[0], (float)c[1], (float)c[2], (float)c[3], (float)c[4], (float)c[5]};
+    rot_sym_f(Rf, Sf, rs);
     const float N = (float)c[9], dx = q[0] - cx, dy = q[1] - cy, dz = q[2] - cz;
     A[0] += fmaf(N * dx, dx, rs[0]);
     A[1] += fmaf(N * dx, dy, rs[1]);
@@ -175,31 +193,43 @@ __global__ void fill_sell_mixed_kernel(LoadInput in, const int32_t* vperm, const
       const double* ref = sref + 12 * (int64_t)in.obs_scan[o];
       offset_b(c, ref, an, b);
       // eigen-decomposition of the scatter in the scan frame: an FP32 Jacobi
-      // gives V0; W = V0^T S V0 in FP64 is diagonal up to FP32 rounding, and
-      // its FP32 Jacobi gives the variances to FP32 relative precision (the
-      // normal one included); V = V0 W_vec.  A direction error d of the
-      // stored vectors changes a variance only by (spread) d^2.
+      // gives V0; W = V0^T S V0 is diagonal up to FP32 rounding, and its FP32
+      // Jacobi gives the variances to FP32 relative precision (the normal one
+      // included); V = V0 W_vec.  A direction error d of the stored vectors
+      // changes a variance only by (spread) d^2.
       const float sf[6] = {(float)c[0], (float)c[1], (float)c[2], (float)c[3], (float)c[4], (float)c[5]};
       float lam0[3], v0[9];
       eig3_sym_f(sf, lam0, v0);  // eigenvectors as rows of v0 (vector c at v0[3c..3c+2])
-      double w[6];
+      // W = V0^T S V0.  The entries of the two smallest directions (W_00,
+      // W_01, W_11) are small next to S's largest entries and lose digits to
+      // cancellation in FP32, so they are formed in FP64: W_00 is the normal
+      // variance of a planar cluster, and for a rod-like cluster (two small,
+      // nearly equal variances) the voxel normal can be any direction of that
+      // pair.  The entries with the largest direction only need absolute
+      // precision (off-diagonals of order 1e-7 of the spread turn V0 by ~1e-7
+      // rad, a second-order change of the variances).
+      float wf[6];
       {
         const double S[3][3] = {{c[0], c[1], c[2]}, {c[1], c[3], c[4]}, {c[2], c[4], c[5]}};
-        double T[3][3];  // T[k] = S v_k
-        for (int k = 0; k < 3; ++k)
+        double Sv[2][3];  // S v_k, k = 0, 1 (FP64)
+        for (int k = 0; k < 2; ++k)
           for (int r = 0; r < 3; ++r)
-            T[k][r] = S[r][0] * (double)v0[3 * k] + S[r][1] * (double)v0[3 * k + 1] + S[r][2] * (double)v0[3 * k + 2];
-        int idx = 0;
-        for (int k = 0; k < 3; ++k)
-          for (int l = k; l < 3; ++l)
-            w[idx++] = (double)v0[3 * k] * T[l][0] + (double)v0[3 * k + 1] * T[l][1] + (double)v0[3 * k + 2] * T[l][2];
+            Sv[k][r] = S[r][0] * (double)v0[3 * k] + S[r][1] * (double)v0[3 * k + 1] + S[r][2] * (double)v0[3 * k + 2];
+        wf[0] = (float)((double)v0[0] * Sv[0][0] + (double)v0[1] * Sv[0][1] + (double)v0[2] * Sv[0][2]);
+        wf[1] = (float)((double)v0[0] * Sv[1][0] + (double)v0[1] * Sv[1][1] + (double)v0[2] * Sv[1][2]);
+        wf[3] = (float)((double)v0[3] * Sv[1][0] + (double)v0[4] * Sv[1][1] + (double)v0[5] * Sv[1][2]);
+        const float M[3][3] = {{sf[0], sf[1], sf[2]}, {sf[1], sf[3], sf[4]}, {sf[2], sf[4], sf[5]}};
+        float T[3];  // S v_2 (FP32)
+        for (int r = 0; r < 3; ++r) T[r] = fmaf(M[r][0], v0[6], fmaf(M[r][1], v0[7], M[r][2] * v0[8]));
+        // packed (00, 01, 02, 11, 12, 22)
+        wf[2] = fmaf(v0[0], T[0], fmaf(v0[1], T[1], v0[2] * T[2]));
+        wf[4] = fmaf(v0[3], T[0], fmaf(v0[4], T[1], v0[5] * T[2]));
+        wf[5] = fmaf(v0[6], T[0], fmaf(v0[7], T[1], v0[8] * T[2]));
       }
-      const float wf[6] = {(float)w[0], (float)w[1], (float)w[2], (float)w[3], (float)w[4], (float)w[5]};
       float sg[3], wv[9];
       eig3_sym_f(wf, sg, wv);
       // world-axis eigenvectors as columns: V = R_ref V0^T-rows ... = R_ref [v0 rows]^T W
-      float Rf[9];
-      for (int k = 0; k < 9; ++k) Rf[k] = (float)ref[k];
+      const float* Rf = sref32_of(sref, in.n_scans, in.obs_scan[o]);
       float V[9];
       for (int cc = 0; cc < 3; ++cc) {
         float u[3];  // scan-frame vector cc = sum_k v0_k W[k][cc]
@@ -237,9 +267,10 @@ __global__ void fill_scan_mixed_kernel(LoadInput in, const uint32_t* order, cons
   double c[10], b[3];
   float sw[6];
   centred_cluster(in.agg + 10 * o, in.agg_form, c);
-  const double* ref = sref + 12 * (int64_t)in.obs_scan[o];
-  offset_b(c, ref, an, b);
-  rot_sym_f(ref, c, sw);  // the scan pass is FP32 throughout
+  const int32_t j = in.obs_scan[o];
+  offset_b(c, sref + 12 * (int64_t)j, an, b);
+  const float Sf[6] = {(float)c[0], (float)c[1], (float)c[2], (float)c[3], (float)c[4], (float)c[5]};
+  rot_sym_f(sref32_of(sref, in.n_scans, j), Sf, sw);  // the scan pass is FP32 throughout
   const float k = (float)vscale[v];
   const int64_t n = in.n_obs;
   float4* bN = reinterpret_cast<float4*>(se32);

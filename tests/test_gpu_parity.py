@@ -363,3 +363,53 @@ def test_mid_workload_full_parity(mm):
         assert st["cost"] == pytest.approx(lm.cost, rel=COST_TOL)
         r, t = pose_errors(ba.poses(), lm.poses)
         assert r < ROT_TOL and t < TRANS_TOL, (r, t)
+
+
+def test_allocator_callbacks_and_injected_oom(mm):
+    """Device memory through caller callbacks (here PyTorch's caching
+    allocator): every allocation is freed through the callback, and an
+    allocation that fails (the Nth call returns NULL) makes the load return
+    BA_ERR_OOM with nothing leaked; the handle then loads with a working
+    allocator."""
+    import torch
+    s, pts, po, raw, cen = tiny_scene()
+    live = {}
+
+    def make(fail_at=None):
+        calls = [0]
+
+        def alloc(n, stream):
+            calls[0] += 1
+            if fail_at is not None and calls[0] == fail_at:
+                return 0
+            p = torch.cuda.caching_allocator_alloc(n, stream=torch.cuda.current_stream().cuda_stream)
+            live[p] = n
+            return p
+
+        def free(p, n, stream):
+            assert live.pop(p) == n
+            torch.cuda.caching_allocator_delete(p)
+        return alloc, free, calls
+
+    alloc, free, calls = make()
+    with mm.BundleAdjuster(alloc=alloc, free=free) as ba:
+        ba.load_observations(s.n_scans, s.voxel_off, s.obs_scan, cen, s.pose_init)
+        st = ba.iterate(3)
+        assert np.isfinite(st["cost"])
+        n_allocs = calls[0]
+    assert n_allocs > 5 and not live
+    for fail_at in (1, n_allocs // 2, n_allocs):
+        alloc, free, calls = make(fail_at)
+        ba = mm.BundleAdjuster(alloc=alloc, free=free)
+        with pytest.raises(mm.BAError) as e:
+            ba.load_observations(s.n_scans, s.voxel_off, s.obs_scan, cen, s.pose_init)
+        assert e.value.status == 2, str(e.value)  # BA_ERR_OOM
+        ba.close()
+        torch.cuda.synchronize()
+        assert not live, fail_at
+    # the library's own pool is unaffected, and its cache can be released
+    with mm.BundleAdjuster() as ba:
+        ba.load_observations(s.n_scans, s.voxel_off, s.obs_scan, cen, s.pose_init)
+        ba.iterate(1)
+    from paper_2608_14266_gb300 import _lib
+    assert _lib.lib().ba_release_cached_memory(0) == 0
