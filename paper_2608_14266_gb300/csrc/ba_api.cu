@@ -1,6 +1,7 @@
 // C-ABI entry points of libmmba (declared in include/ba.h).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <climits>
 #include <cmath>
 #include <cstdarg>
@@ -49,6 +50,9 @@ struct ba_handle {
   double* pred_part = nullptr;
   double* cost_part = nullptr;
   int64_t n_cost = 0;
+  // copy stream and events of a load that overlaps the clusters' copy with the set-up
+  cudaStream_t copy_stream = nullptr;
+  std::vector<cudaEvent_t> copy_events;
   // per-kernel event timing
   bool profiling = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -324,40 +328,7 @@ const T* stage(ba_handle* h, const T* src, size_t count, int mem_kind, bool own,
   return d;
 }
 
-ba_status load_impl(ba_handle* h, int32_t n_scans, int64_t n_voxels, int64_t n_obs, const int64_t* voxel_off,
-                    const int32_t* obs_scan, const double* agg, int32_t agg_form, const double* poses, int32_t mem_kind,
-                    int32_t agg_mem_kind) {
-  cudaError_t e;
-  LoadInput in{};
-  in.n_scans = n_scans;
-  in.n_voxels = n_voxels;
-  in.n_obs = n_obs;
-  in.agg_form = agg_form;
-  // mixed precision keeps device copies of the inputs: the FP32 copies are
-  // rebuilt from them when the reference poses change (ba_set_state)
-  const bool own = h->mixed;
-  in.voxel_off = stage(h, voxel_off, (size_t)n_voxels + 1, mem_kind, own, &e);
-  if (e != cudaSuccess) return cuda_fail(h, e, "stage voxel offsets");
-  in.obs_scan = stage(h, obs_scan, (size_t)n_obs, mem_kind, own, &e);
-  if (e != cudaSuccess) return cuda_fail(h, e, "stage obs_scan");
-  in.agg = stage(h, agg, (size_t)n_obs * 10, agg_mem_kind, own, &e);
-  if (e != cudaSuccess) return cuda_fail(h, e, "stage clusters");
-  in.poses = stage(h, poses, (size_t)n_scans * 12, mem_kind, false, &e);
-  if (e != cudaSuccess) return cuda_fail(h, e, "stage poses");
-
-  // validation
-  ValidateResult init;
-  init.first_bad_offset = init.first_empty_voxel = init.first_bad_scan = init.first_bad_count =
-      init.first_nonfinite_agg = init.first_bad_pose = LLONG_MAX;
-  init.n_obs_seen = 0;
-  init.max_len = 0;
-  ValidateResult* d_val = (ValidateResult*)dev_alloc(h, h->temp, sizeof(ValidateResult));
-  if (!d_val) return fail(h, BA_ERR_OOM, "validation buffer: out of device memory");
-  CK(h, cudaMemcpyAsync(d_val, &init, sizeof init, cudaMemcpyHostToDevice, h->stream), "validation init");
-  CK(h, launch_validate(in, d_val, h->stream, &h->launches), "validate");
-  ValidateResult res;
-  CK(h, cudaMemcpyAsync(&res, d_val, sizeof res, cudaMemcpyDeviceToHost, h->stream), "validation result");
-  CK(h, cudaStreamSynchronize(h->stream), "validation sync");
+ba_status check_validation(ba_handle* h, const ValidateResult& res, int32_t n_scans) {
   if (res.first_bad_offset != LLONG_MAX)
     return fail(h, BA_ERR_INVALID_ARG,
                 "voxel_offsets must start at 0, increase and end at n_obs (first violation at index %lld)",
@@ -375,13 +346,102 @@ ba_status load_impl(ba_handle* h, int32_t n_scans, int64_t n_voxels, int64_t n_o
                 res.first_bad_pose);
   if (res.max_len >= (1ll << 24))
     return fail(h, BA_ERR_CAPACITY, "a voxel has %lld observations (limit 2^24)", res.max_len);
+  return BA_OK;
+}
+
+// Waits for the copy stream when a load leaves early while its copies may
+// still be writing into buffers that the next load or destroy would free.
+struct CopyDrain {
+  cudaStream_t s = nullptr;
+  ~CopyDrain() {
+    if (s) cudaStreamSynchronize(s);
+  }
+};
+
+constexpr int kMaxCopyChunks = 8;
+
+ba_status load_impl(ba_handle* h, int32_t n_scans, int64_t n_voxels, int64_t n_obs, const int64_t* voxel_off,
+                    const int32_t* obs_scan, const double* agg, int32_t agg_form, const double* poses, int32_t mem_kind,
+                    int32_t agg_mem_kind) {
+  cudaError_t e;
+  LoadInput in{};
+  in.n_scans = n_scans;
+  in.n_voxels = n_voxels;
+  in.n_obs = n_obs;
+  in.agg_form = agg_form;
+  // mixed precision keeps device copies of the inputs: the FP32 copies are
+  // rebuilt from them when the reference poses change (ba_set_state)
+  const bool own = h->mixed;
+  // A mixed load of host inputs copies the clusters in chunks of whole
+  // length-sort windows on a copy stream, and sets up each chunk's voxels
+  // while the next chunk is on its way.
+  const bool pipelined = h->mixed && mem_kind == BA_MEM_HOST && agg_mem_kind == BA_MEM_HOST && n_voxels > kWindow;
+  in.voxel_off = stage(h, voxel_off, (size_t)n_voxels + 1, mem_kind, own, &e);
+  if (e != cudaSuccess) return cuda_fail(h, e, "stage voxel offsets");
+  in.obs_scan = stage(h, obs_scan, (size_t)n_obs, mem_kind, own, &e);
+  if (e != cudaSuccess) return cuda_fail(h, e, "stage obs_scan");
+  if (pipelined) {
+    double* d = (double*)dev_alloc(h, h->keep, sizeof(double) * 10 * (size_t)n_obs);
+    if (!d) return fail(h, BA_ERR_OOM, "clusters: out of device memory");
+    in.agg = d;
+  } else {
+    in.agg = stage(h, agg, (size_t)n_obs * 10, agg_mem_kind, own, &e);
+    if (e != cudaSuccess) return cuda_fail(h, e, "stage clusters");
+  }
+  in.poses = stage(h, poses, (size_t)n_scans * 12, mem_kind, false, &e);
+  if (e != cudaSuccess) return cuda_fail(h, e, "stage poses");
+
+  // validation (the clusters of a pipelined load are checked chunk by chunk)
+  ValidateResult init;
+  init.first_bad_offset = init.first_empty_voxel = init.first_bad_scan = init.first_bad_count =
+      init.first_nonfinite_agg = init.first_bad_pose = LLONG_MAX;
+  init.n_obs_seen = 0;
+  init.max_len = 0;
+  ValidateResult* d_val = (ValidateResult*)dev_alloc(h, h->temp, sizeof(ValidateResult));
+  if (!d_val) return fail(h, BA_ERR_OOM, "validation buffer: out of device memory");
+  CK(h, cudaMemcpyAsync(d_val, &init, sizeof init, cudaMemcpyHostToDevice, h->stream), "validation init");
+  CK(h, launch_validate(in, d_val, !pipelined, h->stream, &h->launches), "validate");
+  ValidateResult res;
+  CK(h, cudaMemcpyAsync(&res, d_val, sizeof res, cudaMemcpyDeviceToHost, h->stream), "validation result");
+  CK(h, cudaStreamSynchronize(h->stream), "validation sync");
+  ba_status vs = check_validation(h, res, n_scans);
+  if (vs != BA_OK) return vs;
+
+  // the clusters' copy, chunk by chunk, behind the allocation on the handle's stream
+  CopyDrain drain;
+  int64_t chunk_v[kMaxCopyChunks + 1] = {0};
+  int n_chunks = 0;
+  if (pipelined) {
+    if (!h->copy_stream) CK(h, cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking), "copy stream");
+    while (h->copy_events.size() < kMaxCopyChunks + 1) {
+      cudaEvent_t ev;
+      CK(h, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "copy event");
+      h->copy_events.push_back(ev);
+    }
+    CK(h, cudaEventRecord(h->copy_events[kMaxCopyChunks], h->stream), "copy order");
+    CK(h, cudaStreamWaitEvent(h->copy_stream, h->copy_events[kMaxCopyChunks], 0), "copy order");
+    drain.s = h->copy_stream;
+    const int64_t windows = (n_voxels + kWindow - 1) / kWindow;
+    n_chunks = (int)(windows < kMaxCopyChunks ? windows : kMaxCopyChunks);
+    const int64_t per = (windows + n_chunks - 1) / n_chunks;
+    for (int k = 0; k < n_chunks; ++k) {
+      const int64_t v1 = std::min(n_voxels, (int64_t)(k + 1) * per * kWindow);
+      chunk_v[k + 1] = v1;
+      const int64_t o0 = voxel_off[chunk_v[k]], o1 = voxel_off[v1];
+      CK(h, cudaMemcpyAsync(const_cast<double*>(in.agg) + 10 * o0, agg + 10 * o0, sizeof(double) * 10 * (o1 - o0),
+                            cudaMemcpyHostToDevice, h->copy_stream),
+         "copy clusters");
+      CK(h, cudaEventRecord(h->copy_events[k], h->copy_stream), "copy event");
+    }
+  }
 
   // layout
   LayoutBuffers& lb = h->lb;
   lb = LayoutBuffers{};
   Allocator keep{keep_fn, h}, temp{temp_fn, h};
   {
-    cudaError_t be = build_layout(in, (int)res.max_len, !h->mixed, keep, temp, &lb, h->stream, &h->launches);
+    cudaError_t be =
+        build_layout(in, (int)res.max_len, !h->mixed, pipelined, keep, temp, &lb, h->stream, &h->launches);
     if (be != cudaSuccess) return cuda_fail(h, be, "layout build");
   }
   DevLayout& L = h->L;
@@ -428,7 +488,22 @@ ba_status load_impl(ba_handle* h, int32_t n_scans, int64_t n_voxels, int64_t n_o
       return fail(h, BA_ERR_OOM, "mixed-precision copies: out of device memory");
     h->in_keep = in;
     h->in_keep.poses = nullptr;
-    CK(h, build_mixed(in, lb, h->poses2, mb, h->stream, &h->launches), "mixed-precision copies");
+    if (pipelined) {
+      CK(h, build_mixed_begin(in, h->poses2, mb, h->stream, &h->launches), "mixed-precision copies");
+      for (int k = 0; k < n_chunks; ++k) {
+        const int64_t v0 = chunk_v[k], v1 = chunk_v[k + 1];
+        CK(h, cudaStreamWaitEvent(h->stream, h->copy_events[k], 0), "wait for clusters");
+        CK(h, launch_validate_agg(in, voxel_off[v0], voxel_off[v1], d_val, h->stream, &h->launches), "validate");
+        CK(h, launch_vscale(in, v0, v1, lb.vscale, h->stream, &h->launches), "voxel scales");
+        CK(h, build_mixed_voxels(in, lb, h->poses2, mb, v0, v1, h->stream, &h->launches), "mixed-precision copies");
+      }
+      CK(h, build_mixed_end(in, lb, h->poses2, mb, h->stream, &h->launches), "mixed-precision copies");
+      CK(h, cudaMemcpyAsync(&res, d_val, sizeof res, cudaMemcpyDeviceToHost, h->stream), "validation result");
+      CK(h, cudaStreamSynchronize(h->stream), "validation sync");
+      if ((vs = check_validation(h, res, n_scans)) != BA_OK) return vs;
+    } else {
+      CK(h, build_mixed(in, lb, h->poses2, mb, h->stream, &h->launches), "mixed-precision copies");
+    }
     h->X.ve32 = mb.ve32;
     h->X.vstate = mb.vstate;
     h->X.se32 = mb.se32;
@@ -847,9 +922,12 @@ void ba_destroy(ba_handle* h) {
   if (h->batch) ba_batch_remove(h->batch, h);
   DeviceGuard g(h->cfg.device);
   cudaStreamSynchronize(h->stream);
+  if (h->copy_stream) cudaStreamSynchronize(h->copy_stream);
   release_problem(h);
   cudaStreamSynchronize(h->stream);
   for (auto e : h->ev_pool) cudaEventDestroy(e);
+  for (auto e : h->copy_events) cudaEventDestroy(e);
+  if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
   delete h;
 }
 

@@ -230,11 +230,17 @@ __global__ void validate_voxels_kernel(LoadInput in, ValidateResult* r) {
   }
 }
 
-__global__ void validate_obs_kernel(LoadInput in, ValidateResult* r) {
+__global__ void validate_scan_ids_kernel(LoadInput in, ValidateResult* r) {
   const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (o >= in.n_obs) return;
   const int32_t j = in.obs_scan[o];
   if (j < 0 || j >= in.n_scans) amin(&r->first_bad_scan, o);
+}
+
+// clusters of observations [o0, o1): finite, and at least one point
+__global__ void validate_agg_kernel(LoadInput in, int64_t o0, int64_t o1, ValidateResult* r) {
+  const int64_t o = o0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= o1) return;
   const double* a = in.agg + 10 * o;
   bool fin = true;
 #pragma unroll
@@ -262,16 +268,26 @@ __global__ void validate_poses_kernel(LoadInput in, ValidateResult* r) {
   if (!ok) amin(&r->first_bad_pose, j);
 }
 
-cudaError_t launch_validate(const LoadInput& in, ValidateResult* d_res, cudaStream_t stream, int64_t* launches) {
+cudaError_t launch_validate(const LoadInput& in, ValidateResult* d_res, bool with_agg, cudaStream_t stream,
+                            int64_t* launches) {
   validate_voxels_kernel<<<(unsigned)((in.n_voxels + 1 + 255) / 256), 256, 0, stream>>>(in, d_res);
   ++*launches;
   RETURN_IF(cudaGetLastError());
   if (in.n_obs > 0) {
-    validate_obs_kernel<<<(unsigned)((in.n_obs + 255) / 256), 256, 0, stream>>>(in, d_res);
+    validate_scan_ids_kernel<<<(unsigned)((in.n_obs + 255) / 256), 256, 0, stream>>>(in, d_res);
     ++*launches;
     RETURN_IF(cudaGetLastError());
+    if (with_agg) RETURN_IF(launch_validate_agg(in, 0, in.n_obs, d_res, stream, launches));
   }
   validate_poses_kernel<<<(unsigned)((in.n_scans + 127) / 128), 128, 0, stream>>>(in, d_res);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_validate_agg(const LoadInput& in, int64_t o0, int64_t o1, ValidateResult* d_res,
+                                cudaStream_t stream, int64_t* launches) {
+  if (o1 <= o0) return cudaSuccess;
+  validate_agg_kernel<<<(unsigned)((o1 - o0 + 255) / 256), 256, 0, stream>>>(in, o0, o1, d_res);
   ++*launches;
   return cudaGetLastError();
 }
@@ -357,15 +373,24 @@ __global__ void fill_sell_kernel(LoadInput in, const int32_t* vperm, const int32
   }
 }
 
-// voxel of every observation, and each voxel's 2 / N_i
+// voxel of every observation, and (unless vscale is null) each voxel's 2 / N_i
 __global__ void obs_voxel_kernel(LoadInput in, int32_t* obs_vox, double* vscale) {
   const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= in.n_voxels) return;
   double n = 0.0;
   for (int64_t o = in.voxel_off[v]; o < in.voxel_off[v + 1]; ++o) {
     obs_vox[o] = (int32_t)v;
-    n += in.agg[10 * o + 9];
+    if (vscale) n += in.agg[10 * o + 9];
   }
+  if (vscale) vscale[v] = 2.0 / n;
+}
+
+// 2 / N_i of voxels [v0, v1)
+__global__ void vscale_kernel(LoadInput in, int64_t v0, int64_t v1, double* vscale) {
+  const int64_t v = v0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= v1) return;
+  double n = 0.0;
+  for (int64_t o = in.voxel_off[v]; o < in.voxel_off[v + 1]; ++o) n += in.agg[10 * o + 9];
   vscale[v] = 2.0 / n;
 }
 
@@ -405,8 +430,16 @@ static int bit_width(uint64_t x) {
   return b;
 }
 
-cudaError_t build_layout(const LoadInput& in, int max_len, bool fill_f64, Allocator keep, Allocator temp,
-                         LayoutBuffers* out, cudaStream_t stream, int64_t* launches) {
+cudaError_t launch_vscale(const LoadInput& in, int64_t v0, int64_t v1, double* vscale, cudaStream_t stream,
+                          int64_t* launches) {
+  if (v1 <= v0) return cudaSuccess;
+  vscale_kernel<<<(unsigned)((v1 - v0 + 255) / 256), 256, 0, stream>>>(in, v0, v1, vscale);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+cudaError_t build_layout(const LoadInput& in, int max_len, bool fill_f64, bool defer_scale, Allocator keep,
+                         Allocator temp, LayoutBuffers* out, cudaStream_t stream, int64_t* launches) {
   const int64_t nv = in.n_voxels, no = in.n_obs;
   const int64_t n_slices = (nv + kSlice - 1) / kSlice;
   const int64_t nsort = nv > no ? nv : no;
@@ -457,16 +490,19 @@ cudaError_t build_layout(const LoadInput& in, int max_len, bool fill_f64, Alloca
   RETURN_IF(cudaStreamSynchronize(stream));
   out->n_elems = n_elems;
   out->n_slices = n_slices;
-  out->ve = fill_f64 ? (double*)keep.fn(keep.self, sizeof(double) * 10 * n_elems) : nullptr;
-  out->ve_scan = (int32_t*)keep.fn(keep.self, sizeof(int32_t) * n_elems);
-  if ((fill_f64 && !out->ve) || !out->ve_scan) return cudaErrorMemoryAllocation;
-  fill_sell_kernel<<<(unsigned)((n_slices * kSlice + 255) / 256), 256, 0, stream>>>(
-      in, out->vperm, out->vlen, out->slice_off, nv, out->ve, out->ve_scan, n_elems);
-  ++*launches;
-  RETURN_IF(cudaGetLastError());
+  // the FP64 slice copy (the mixed path builds its own FP32 slots)
+  if (fill_f64) {
+    out->ve = (double*)keep.fn(keep.self, sizeof(double) * 10 * n_elems);
+    out->ve_scan = (int32_t*)keep.fn(keep.self, sizeof(int32_t) * n_elems);
+    if (!out->ve || !out->ve_scan) return cudaErrorMemoryAllocation;
+    fill_sell_kernel<<<(unsigned)((n_slices * kSlice + 255) / 256), 256, 0, stream>>>(
+        in, out->vperm, out->vlen, out->slice_off, nv, out->ve, out->ve_scan, n_elems);
+    ++*launches;
+    RETURN_IF(cudaGetLastError());
+  }
 
   // ---- scan-major copy ----
-  obs_voxel_kernel<<<(unsigned)((nv + 255) / 256), 256, 0, stream>>>(in, obs_vox, vscale);
+  obs_voxel_kernel<<<(unsigned)((nv + 255) / 256), 256, 0, stream>>>(in, obs_vox, defer_scale ? nullptr : vscale);
   ++*launches;
   RETURN_IF(cudaGetLastError());
   RETURN_IF(cudaMemsetAsync(out->scan_off, 0, sizeof(int64_t) * (in.n_scans + 1), stream));

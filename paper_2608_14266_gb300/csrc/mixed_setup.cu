@@ -92,10 +92,10 @@ __device__ inline void posed_rel(const double* c, const float* Rf, const double*
 // the iteration (the voxel pass moves the frame and the centroid every pass),
 // so FP32 sums about the voxel's first posed mean suffice; FP64 is used only
 // for the offsets of the scan positions from that point.
-__global__ void voxel_frames_kernel(LoadInput in, const double* sref, const int32_t* vrank, float4* vstate,
-                                    float4* vanchor, float4* planes2) {
-  const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (v >= in.n_voxels) return;
+__global__ void voxel_frames_kernel(LoadInput in, int64_t v0, int64_t v1, const double* sref, const int32_t* vrank,
+                                    float4* vstate, float4* vanchor, float4* planes2) {
+  const int64_t v = v0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= v1) return;
   const int64_t a0 = in.voxel_off[v], a1 = in.voxel_off[v + 1];
   double p0[3];
   {
@@ -170,12 +170,13 @@ __device__ inline void offset_b(const double* c, const double* ref, float4 an, d
   b[2] = ref[6] * c[6] + ref[7] * c[7] + ref[8] * c[8] + (ref[11] - (double)an.z);
 }
 
+// slots of the slices that start at sorted positions [p0, p1) (p0 a multiple of kSlice)
 __global__ void fill_sell_mixed_kernel(LoadInput in, const int32_t* vperm, const int32_t* vlen,
-                                       const int64_t* slice_off, int64_t n_voxels, const double* sref,
-                                       const float4* vanchor, float4* ve32) {
-  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+                                       const int64_t* slice_off, int64_t n_voxels, int64_t p0, int64_t p1,
+                                       const double* sref, const float4* vanchor, float4* ve32) {
+  const int64_t p = p0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t s = p >> 5;
-  if (s * kSlice >= n_voxels) return;
+  if (s * kSlice >= n_voxels || s * kSlice >= p1) return;
   const int lane = (int)(p & 31);
   const int64_t base = slice_off[s] + lane;
   const int64_t rows = (slice_off[s + 1] - slice_off[s]) / kSlice;
@@ -283,29 +284,52 @@ __global__ void fill_scan_mixed_kernel(LoadInput in, const uint32_t* order, cons
 
 }  // namespace
 
-cudaError_t build_mixed(const LoadInput& in, const LayoutBuffers& lb, const double* poses2, MixedBuffers& mb,
-                        cudaStream_t stream, int64_t* launches) {
-  const int64_t nv = in.n_voxels, no = in.n_obs;
+cudaError_t build_mixed_begin(const LoadInput& in, const double* poses2, MixedBuffers& mb, cudaStream_t stream,
+                              int64_t* launches) {
+  scan_ref_kernel<<<(in.n_scans + 127) / 128, 128, 0, stream>>>(in.n_scans, poses2, mb.sref);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+cudaError_t build_mixed_voxels(const LoadInput& in, const LayoutBuffers& lb, const double* poses2, MixedBuffers& mb,
+                               int64_t v0, int64_t v1, cudaStream_t stream, int64_t* launches) {
+  if (v1 <= v0) return cudaSuccess;
   LoadInput cur = in;
   cur.poses = poses2;  // buffer 0
-  scan_ref_kernel<<<(in.n_scans + 127) / 128, 128, 0, stream>>>(in.n_scans, poses2, mb.sref);
+  voxel_frames_kernel<<<(unsigned)((v1 - v0 + 127) / 128), 128, 0, stream>>>(cur, v0, v1, mb.sref, lb.vrank,
+                                                                            mb.vstate, mb.vanchor, mb.planes32_2);
   ++*launches;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  voxel_frames_kernel<<<(unsigned)((nv + 127) / 128), 128, 0, stream>>>(cur, mb.sref, lb.vrank, mb.vstate,
-                                                                        mb.vanchor, mb.planes32_2);
+  // the slices of sorted positions [v0, v1): windows keep their voxels, so for
+  // window-aligned ranges these are exactly the voxels whose frames were just set
+  const int64_t p0 = v0, p1 = min(in.n_voxels, ((v1 + kSlice - 1) / kSlice) * kSlice);
+  fill_sell_mixed_kernel<<<(unsigned)((p1 - p0 + 127) / 128), 128, 0, stream>>>(
+      cur, lb.vperm, lb.vlen, lb.slice_off, in.n_voxels, p0, p1, mb.sref, mb.vanchor, mb.ve32);
   ++*launches;
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  fill_sell_mixed_kernel<<<(unsigned)((lb.n_slices * kSlice + 127) / 128), 128, 0, stream>>>(
-      cur, lb.vperm, lb.vlen, lb.slice_off, nv, mb.sref, mb.vanchor, mb.ve32);
-  ++*launches;
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+cudaError_t build_mixed_end(const LoadInput& in, const LayoutBuffers& lb, const double* poses2, MixedBuffers& mb,
+                            cudaStream_t stream, int64_t* launches) {
+  const int64_t no = in.n_obs;
+  LoadInput cur = in;
+  cur.poses = poses2;
   fill_scan_mixed_kernel<<<(unsigned)((no + 255) / 256), 256, 0, stream>>>(cur, lb.scan_order, lb.obs_vox, lb.vscale,
                                                                            lb.vrank, mb.sref, mb.vanchor, mb.se32);
   ++*launches;
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
   ++*launches;
   return launch_scan_table(in.n_scans, poses2, mb.sref, mb.stab2, 0, stream);
+}
+
+cudaError_t build_mixed(const LoadInput& in, const LayoutBuffers& lb, const double* poses2, MixedBuffers& mb,
+                        cudaStream_t stream, int64_t* launches) {
+  cudaError_t e = build_mixed_begin(in, poses2, mb, stream, launches);
+  if (e == cudaSuccess) e = build_mixed_voxels(in, lb, poses2, mb, 0, in.n_voxels, stream, launches);
+  if (e == cudaSuccess) e = build_mixed_end(in, lb, poses2, mb, stream, launches);
+  return e;
 }
 
 }  // namespace mmba

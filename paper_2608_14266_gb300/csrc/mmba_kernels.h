@@ -69,7 +69,12 @@ struct ValidateResult {
   long long n_obs_seen;
   long long max_len;
 };
-cudaError_t launch_validate(const LoadInput& in, ValidateResult* d_res, cudaStream_t stream, int64_t* launches);
+// with_agg = false leaves the clusters unchecked (launch_validate_agg checks a
+// range of them once they are on the device)
+cudaError_t launch_validate(const LoadInput& in, ValidateResult* d_res, bool with_agg, cudaStream_t stream,
+                            int64_t* launches);
+cudaError_t launch_validate_agg(const LoadInput& in, int64_t o0, int64_t o1, ValidateResult* d_res,
+                                cudaStream_t stream, int64_t* launches);
 
 // Build the device layout; buffers are allocated through the given allocators
 // as sizes become known.
@@ -98,8 +103,12 @@ struct LayoutBuffers {
 // caller frees those after the stream has drained).
 // With fill_f64 the FP64 cluster copies are filled; without, only the index
 // structures are built and the maps above are kept for the FP32 copies.
-cudaError_t build_layout(const LoadInput& in, int max_len, bool fill_f64, Allocator keep, Allocator temp,
-                         LayoutBuffers* out, cudaStream_t stream, int64_t* launches);
+// With defer_scale the clusters are not read (vscale is left for
+// launch_vscale, voxel range by voxel range, as the clusters arrive).
+cudaError_t build_layout(const LoadInput& in, int max_len, bool fill_f64, bool defer_scale, Allocator keep,
+                         Allocator temp, LayoutBuffers* out, cudaStream_t stream, int64_t* launches);
+cudaError_t launch_vscale(const LoadInput& in, int64_t v0, int64_t v1, double* vscale, cudaStream_t stream,
+                          int64_t* launches);
 
 // ---- mixed precision ----
 cudaError_t launch_voxel_pass_mixed(const DevLayout& L, const DevMixed& X, double* full_out, double* cost_part,
@@ -121,6 +130,16 @@ struct MixedBuffers {
 };
 cudaError_t build_mixed(const LoadInput& in, const LayoutBuffers& lb, const double* poses2, MixedBuffers& mb,
                         cudaStream_t stream, int64_t* launches);
+// The same in three stages, for a load that overlaps the clusters' copy:
+// begin (reference poses), voxels [v0, v1) (frames, anchors and slots; the
+// range must be window-aligned, its clusters on the device), end (scan-major
+// copy and scan table, once every voxel is done).
+cudaError_t build_mixed_begin(const LoadInput& in, const double* poses2, MixedBuffers& mb, cudaStream_t stream,
+                              int64_t* launches);
+cudaError_t build_mixed_voxels(const LoadInput& in, const LayoutBuffers& lb, const double* poses2, MixedBuffers& mb,
+                               int64_t v0, int64_t v1, cudaStream_t stream, int64_t* launches);
+cudaError_t build_mixed_end(const LoadInput& in, const LayoutBuffers& lb, const double* poses2, MixedBuffers& mb,
+                            cudaStream_t stream, int64_t* launches);
 
 // bounded-wait check: out[0] = 1 if an mbarrier wait that cannot complete gave up
 cudaError_t launch_wait_probe(int limit, int32_t* out, cudaStream_t stream);

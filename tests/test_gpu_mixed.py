@@ -153,3 +153,56 @@ def test_bounded_wait_gives_up_and_context_survives(mm):
         ba.load_observations(s.n_scans, s.voxel_off, s.obs_scan, cen, s.pose_init)
         st = ba.iterate(3)
         assert st["iters"] == 3 and np.isfinite(st["cost"])
+
+
+def _scene_20k():
+    p = scenegen.SceneParams(n_scans=200, n_voxels=20000, obs_min=5, obs_max=15, pts_per_obs=8, noise_sigma=0.02,
+                             rot_sigma_deg=0.5, trans_sigma=0.1, seed=4242)
+    s = scenegen.make_scene(p)
+    cen = oracle.points_to_centred(s.point_offsets(), s.points())
+    return s, cen
+
+
+def test_pipelined_host_load_equals_device_load(mm):
+    """A mixed load of host inputs with more than one length-sort window copies
+    the clusters in chunks and sets each chunk up while the next is copied;
+    it must build exactly what a load of the same inputs from device memory
+    (one piece) builds."""
+    import torch
+    s, cen = _scene_20k()
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    with _mixed(mm) as a, _mixed(mm) as b:
+        a.load_observations(s.n_scans, s.voxel_off, s.obs_scan, cen, s.pose_init)
+        b.load_observations(s.n_scans, dev(s.voxel_off), dev(s.obs_scan), dev(cen), dev(s.pose_init))
+        assert a.cost() == b.cost()
+        np.testing.assert_array_equal(a.planes(), b.planes())
+        ga, Ha = a.gradient()
+        gb, Hb = b.gradient()
+        np.testing.assert_array_equal(ga, gb)
+        np.testing.assert_array_equal(Ha, Hb)
+        a.iterate(3)
+        b.iterate(3)
+        np.testing.assert_array_equal(a.poses(), b.poses())
+    # and it agrees with the oracle
+    prob = oracle.ObsProblem(s.n_scans, s.voxel_off, s.obs_scan, cen)
+    c_ref, _ = oracle.voxel_pass(prob, s.pose_init)
+    with _mixed(mm) as a:
+        a.load_observations(s.n_scans, s.voxel_off, s.obs_scan, cen, s.pose_init)
+        assert a.cost() == pytest.approx(c_ref, rel=COST_TOL)
+
+
+def test_pipelined_load_reports_bad_cluster(mm):
+    """Clusters are validated chunk by chunk as they arrive: a non-finite value
+    or an empty count in the last chunk is still reported with its index."""
+    s, cen = _scene_20k()
+    for col, val, what in ((3, np.nan, "non-finite"), (9, 0.0, "below 1")):
+        bad = cen.copy()
+        o = s.n_obs - 5
+        bad[o, col] = val
+        with _mixed(mm) as a:
+            with pytest.raises(mm.BAError) as e:
+                a.load_observations(s.n_scans, s.voxel_off, s.obs_scan, bad, s.pose_init)
+            assert e.value.status == 1 and f"cluster {o}" in str(e.value) and what in str(e.value)
+            # the handle loads good inputs afterwards
+            a.load_observations(s.n_scans, s.voxel_off, s.obs_scan, cen, s.pose_init)
+            assert np.isfinite(a.cost())
