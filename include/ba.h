@@ -329,6 +329,14 @@ ba_status ba_aggregate_points(int64_t n_obs, const int64_t* point_offsets, const
  * the wait did not give up, BA_ERR_INVALID_ARG / BA_ERR_CUDA otherwise. */
 ba_status ba_check_bounded_wait(int32_t device, int32_t polls);
 
+/* Check of the set-up's integer-arithmetic conversions between binary64 and
+ * binary32 (the paper has no counterpart): n pseudo-random and special values
+ * (seeded) are converted both ways by them and by the hardware on `device`;
+ * mismatches[0] / [1] receive the number of differing binary64 -> binary32 /
+ * binary32 -> binary64 results (0 expected).  Errors: BA_ERR_INVALID_ARG,
+ * BA_ERR_CUDA. */
+ba_status ba_check_conversions(int32_t device, int64_t n, uint64_t seed, uint64_t* mismatches);
+
 /* Allocation-free cost evaluation.  The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory when they need
  * a cost -- a mapping loop on a vehicle under a fixed memory budget, where

@@ -90,6 +90,7 @@ _SIGNATURES = {
     "ba_server_destroy": (None, [_P]),
     "ba_check_bounded_wait": (_I32, [_I32, _I32]),
     "ba_release_cached_memory": (_I32, [_I32]),
+    "ba_check_conversions": (_I32, [_I32, _I64, ctypes.c_uint64, _P]),
     "ba_device_bytes": (_I64, [_P]),
     "ba_estimate_bytes": (_I64, [_I32, _I32, _I64, _I64, _P]),
 }

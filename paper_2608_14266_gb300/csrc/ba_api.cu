@@ -391,6 +391,47 @@ ba_status load_impl(ba_handle* h, int32_t n_scans, int64_t n_voxels, int64_t n_o
   in.poses = stage(h, poses, (size_t)n_scans * 12, mem_kind, false, &e);
   if (e != cudaSuccess) return cuda_fail(h, e, "stage poses");
 
+  // The clusters' copy, chunk by chunk, behind the allocation on the handle's
+  // stream, started before validation (the copy of a load that fails is
+  // drained before the load returns).  The chunk boundaries come from the
+  // host offsets, so they are checked here first: every copy stays inside the
+  // caller's array and the device buffer, whatever the rest of the offsets hold.
+  CopyDrain drain;
+  int64_t chunk_v[kMaxCopyChunks + 1] = {0};
+  int n_chunks = 0;
+  if (pipelined) {
+    const int64_t windows = (n_voxels + kWindow - 1) / kWindow;
+    n_chunks = (int)(windows < kMaxCopyChunks ? windows : kMaxCopyChunks);
+    const int64_t per = (windows + n_chunks - 1) / n_chunks;
+    bool bounds_ok = voxel_off[0] == 0 && voxel_off[n_voxels] == n_obs;
+    for (int k = 0; k < n_chunks && bounds_ok; ++k) {
+      chunk_v[k + 1] = std::min(n_voxels, (int64_t)(k + 1) * per * kWindow);
+      const int64_t o0 = voxel_off[chunk_v[k]], o1 = voxel_off[chunk_v[k + 1]];
+      bounds_ok = 0 <= o0 && o0 <= o1 && o1 <= n_obs;
+    }
+    // offsets that fail here fail the device validation below, which names the
+    // first violation; no copy is started for them
+    if (!bounds_ok) n_chunks = 0;
+  }
+  if (n_chunks > 0) {
+    if (!h->copy_stream) CK(h, cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking), "copy stream");
+    while (h->copy_events.size() < kMaxCopyChunks + 1) {
+      cudaEvent_t ev;
+      CK(h, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "copy event");
+      h->copy_events.push_back(ev);
+    }
+    CK(h, cudaEventRecord(h->copy_events[kMaxCopyChunks], h->stream), "copy order");
+    CK(h, cudaStreamWaitEvent(h->copy_stream, h->copy_events[kMaxCopyChunks], 0), "copy order");
+    drain.s = h->copy_stream;
+    for (int k = 0; k < n_chunks; ++k) {
+      const int64_t o0 = voxel_off[chunk_v[k]], o1 = voxel_off[chunk_v[k + 1]];
+      CK(h, cudaMemcpyAsync(const_cast<double*>(in.agg) + 10 * o0, agg + 10 * o0, sizeof(double) * 10 * (o1 - o0),
+                            cudaMemcpyHostToDevice, h->copy_stream),
+         "copy clusters");
+      CK(h, cudaEventRecord(h->copy_events[k], h->copy_stream), "copy event");
+    }
+  }
+
   // validation (the clusters of a pipelined load are checked chunk by chunk)
   ValidateResult init;
   init.first_bad_offset = init.first_empty_voxel = init.first_bad_scan = init.first_bad_count =
@@ -406,34 +447,7 @@ ba_status load_impl(ba_handle* h, int32_t n_scans, int64_t n_voxels, int64_t n_o
   CK(h, cudaStreamSynchronize(h->stream), "validation sync");
   ba_status vs = check_validation(h, res, n_scans);
   if (vs != BA_OK) return vs;
-
-  // the clusters' copy, chunk by chunk, behind the allocation on the handle's stream
-  CopyDrain drain;
-  int64_t chunk_v[kMaxCopyChunks + 1] = {0};
-  int n_chunks = 0;
-  if (pipelined) {
-    if (!h->copy_stream) CK(h, cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking), "copy stream");
-    while (h->copy_events.size() < kMaxCopyChunks + 1) {
-      cudaEvent_t ev;
-      CK(h, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "copy event");
-      h->copy_events.push_back(ev);
-    }
-    CK(h, cudaEventRecord(h->copy_events[kMaxCopyChunks], h->stream), "copy order");
-    CK(h, cudaStreamWaitEvent(h->copy_stream, h->copy_events[kMaxCopyChunks], 0), "copy order");
-    drain.s = h->copy_stream;
-    const int64_t windows = (n_voxels + kWindow - 1) / kWindow;
-    n_chunks = (int)(windows < kMaxCopyChunks ? windows : kMaxCopyChunks);
-    const int64_t per = (windows + n_chunks - 1) / n_chunks;
-    for (int k = 0; k < n_chunks; ++k) {
-      const int64_t v1 = std::min(n_voxels, (int64_t)(k + 1) * per * kWindow);
-      chunk_v[k + 1] = v1;
-      const int64_t o0 = voxel_off[chunk_v[k]], o1 = voxel_off[v1];
-      CK(h, cudaMemcpyAsync(const_cast<double*>(in.agg) + 10 * o0, agg + 10 * o0, sizeof(double) * 10 * (o1 - o0),
-                            cudaMemcpyHostToDevice, h->copy_stream),
-         "copy clusters");
-      CK(h, cudaEventRecord(h->copy_events[k], h->copy_stream), "copy event");
-    }
-  }
+  if (pipelined && n_chunks == 0) return fail(h, BA_ERR_CUDA, "internal: cluster copy not started");
 
   // layout
   LayoutBuffers& lb = h->lb;

@@ -490,6 +490,7 @@ cudaError_t build_layout(const LoadInput& in, int max_len, bool fill_f64, bool d
   RETURN_IF(cudaStreamSynchronize(stream));
   out->n_elems = n_elems;
   out->n_slices = n_slices;
+  out->max_len = max_len;
   // the FP64 slice copy (the mixed path builds its own FP32 slots)
   if (fill_f64) {
     out->ve = (double*)keep.fn(keep.self, sizeof(double) * 10 * n_elems);

@@ -6,12 +6,16 @@
 // 2 / N_i).  FP64 is used where digits would otherwise be lost (offsets of
 // scene-sized positions from the anchor, the scatter in the basis of its FP32
 // eigenvectors); the rest is FP32 (GB300's FP64 rate is 1/64 of FP32).
+#include <algorithm>
+
 #include "mmba_internal.cuh"
 #include "mmba_kernels.h"
 
 namespace mmba {
 
 namespace {
+
+constexpr int kFillRows = 4;  // slice rows per thread of the slot fill
 
 __device__ inline void centred_cluster(const double* a, int form, double out[10]) {
   if (form == 1) {
@@ -79,59 +83,78 @@ __device__ inline void rot_sym_f(const float* Rf, const float* Sf, float* out) {
       out[idx++] = fmaf(T[r][0], Rf[3 * c], fmaf(T[r][1], Rf[3 * c + 1], T[r][2] * Rf[3 * c + 2]));
 }
 
-// posed mean of a cluster relative to the point p0 (FP64 offsets, FP32 lever)
-__device__ inline void posed_rel(const double* c, const float* Rf, const double* t, const double* p0, float* q) {
-  const float m0 = (float)c[6], m1 = (float)c[7], m2 = (float)c[8];
+
+// warp sum (xor butterfly: every lane ends with the total, in a fixed order)
+__device__ __forceinline__ float warp_allsum(float x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+// FP32 copies of a cluster's scatter, mean and count (integer-arithmetic
+// conversions: GB300 converts on its narrow FP64 pipe)
+__device__ __forceinline__ void cluster_f32(const double* c, float* Sf, float* mf, float& N) {
+#pragma unroll
+  for (int k = 0; k < 6; ++k) Sf[k] = f64_to_f32(c[k]);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) mf[k] = f64_to_f32(c[6 + k]);
+  N = f64_to_f32(c[9]);
+}
+
+// posed mean R m + t_ref in FP32 (from the FP32 reference table: R, t_ref)
+__device__ __forceinline__ void posed_f32(const float* ref32, const float* m, float* q) {
 #pragma unroll
   for (int a = 0; a < 3; ++a)
-    q[a] = fmaf(Rf[3 * a], m0, fmaf(Rf[3 * a + 1], m1, fmaf(Rf[3 * a + 2], m2, (float)(t[a] - p0[a]))));
+    q[a] = fmaf(ref32[3 * a], m[0], fmaf(ref32[3 * a + 1], m[1], fmaf(ref32[3 * a + 2], m[2], ref32[9 + a])));
 }
 
 // anchor (FP32-rounded centroid) and starting frame (eigenvectors, normal
-// last, proper rotation) of each voxel at the reference poses.  Both only seed
-// the iteration (the voxel pass moves the frame and the centroid every pass),
-// so FP32 sums about the voxel's first posed mean suffice; FP64 is used only
-// for the offsets of the scan positions from that point.
+// last, proper rotation) of each voxel at the reference poses, one warp per
+// voxel (lanes over its observations).  Both only seed the iteration (the
+// voxel pass moves the frame and the centroid every pass, and the anchor only
+// has to be an FP32 value near the centroid), so the sums are FP32, about the
+// voxel's first posed mean: an error of the order of an FP32 ulp of the scene
+// coordinates (~1e-4 m at 2 km) moves nothing but the seed.
 __global__ void voxel_frames_kernel(LoadInput in, int64_t v0, int64_t v1, const double* sref, const int32_t* vrank,
                                     float4* vstate, float4* vanchor, float4* planes2) {
-  const int64_t v = v0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (v >= v1) return;
+  const int64_t v = v0 + ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+  const int lane = threadIdx.x & 31;
+  if (v >= v1) return;  // the whole warp
   const int64_t a0 = in.voxel_off[v], a1 = in.voxel_off[v + 1];
-  double p0[3];
+  float p0[3];
   {
+    float Sf[6], mf[3], N;
     double c[10];
     centred_cluster(in.agg + 10 * a0, in.agg_form, c);
-    const double* R = sref + 12 * (int64_t)in.obs_scan[a0];
-    const double* P = in.poses + 12 * (int64_t)in.obs_scan[a0];
-    for (int a = 0; a < 3; ++a) p0[a] = R[3 * a] * c[6] + R[3 * a + 1] * c[7] + R[3 * a + 2] * c[8] + P[9 + a];
+    cluster_f32(c, Sf, mf, N);
+    posed_f32(sref32_of(sref, in.n_scans, in.obs_scan[a0]), mf, p0);
   }
   float n = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
-  for (int64_t o = a0; o < a1; ++o) {
+  for (int64_t o = a0 + lane; o < a1; o += 32) {
     double c[10];
     centred_cluster(in.agg + 10 * o, in.agg_form, c);
-    const int32_t j = in.obs_scan[o];
-    float q[3];
-    posed_rel(c, sref32_of(sref, in.n_scans, j), in.poses + 12 * (int64_t)j + 9, p0, q);
-    const float N = (float)c[9];
-    cx = fmaf(N, q[0], cx);
-    cy = fmaf(N, q[1], cy);
-    cz = fmaf(N, q[2], cz);
+    float Sf[6], mf[3], N, q[3];
+    cluster_f32(c, Sf, mf, N);
+    posed_f32(sref32_of(sref, in.n_scans, in.obs_scan[o]), mf, q);
+    cx = fmaf(N, q[0] - p0[0], cx);
+    cy = fmaf(N, q[1] - p0[1], cy);
+    cz = fmaf(N, q[2] - p0[2], cz);
     n += N;
   }
-  cx /= n;
-  cy /= n;
-  cz /= n;
+  n = warp_allsum(n);
+  cx = warp_allsum(cx) / n;
+  cy = warp_allsum(cy) / n;
+  cz = warp_allsum(cz) / n;
   float A[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  for (int64_t o = a0; o < a1; ++o) {
+  for (int64_t o = a0 + lane; o < a1; o += 32) {
     double c[10];
     centred_cluster(in.agg + 10 * o, in.agg_form, c);
-    const int32_t j = in.obs_scan[o];
-    float q[3], rs[6];
-    const float* Rf = sref32_of(sref, in.n_scans, j);
-    posed_rel(c, Rf, in.poses + 12 * (int64_t)j + 9, p0, q);
-    const float Sf[6] = {(float)c[0], (float)c[1], (float)c[2], (float)c[3], (float)c[4], (float)c[5]};
+    float Sf[6], mf[3], N, q[3], rs[6];
+    cluster_f32(c, Sf, mf, N);
+    const float* Rf = sref32_of(sref, in.n_scans, in.obs_scan[o]);
+    posed_f32(Rf, mf, q);
     rot_sym_f(Rf, Sf, rs);
-    const float N = (float)c[9], dx = q[0] - cx, dy = q[1] - cy, dz = q[2] - cz;
+    const float dx = (q[0] - p0[0]) - cx, dy = (q[1] - p0[1]) - cy, dz = (q[2] - p0[2]) - cz;
     A[0] += fmaf(N * dx, dx, rs[0]);
     A[1] += fmaf(N * dx, dy, rs[1]);
     A[2] += fmaf(N * dx, dz, rs[2]);
@@ -139,6 +162,9 @@ __global__ void voxel_frames_kernel(LoadInput in, int64_t v0, int64_t v1, const 
     A[4] += fmaf(N * dy, dz, rs[4]);
     A[5] += fmaf(N * dz, dz, rs[5]);
   }
+#pragma unroll
+  for (int k = 0; k < 6; ++k) A[k] = warp_allsum(A[k]);
+  if (lane != 0) return;
   float lam[3], V[9];
   eig3_sym_f(A, lam, V);
   // rows: e1 (largest), e2, n (smallest)
@@ -149,28 +175,29 @@ __global__ void voxel_frames_kernel(LoadInput in, int64_t v0, int64_t v1, const 
     for (int k = 0; k < 3; ++k) U[k] = -U[k];
   float q[4];
   mat_to_quat<float>(U, q);
-  const double c64[3] = {p0[0] + (double)cx, p0[1] + (double)cy, p0[2] + (double)cz};
+  // anchor: the centroid rounded to FP32; the running centroid starts at the
+  // remainder (FP32 arithmetic, exact for the rounding step of a sum)
+  const float ax = p0[0] + cx, ay = p0[1] + cy, az = p0[2] + cz;
   const int64_t p = vrank[v];
-  const float ax = (float)c64[0], ay = (float)c64[1], az = (float)c64[2];
   vanchor[p] = make_float4(ax, ay, az, 0.0f);
   // the anchor also sits beside the plane in both buffers of plane records
   planes2[2 * p + 1] = make_float4(ax, ay, az, 0.0f);
   planes2[2 * (in.n_voxels + p) + 1] = make_float4(ax, ay, az, 0.0f);
   vstate[2 * p] = make_float4(q[0], q[1], q[2], q[3]);
-  // the running centroid starts where the anchor's rounding left it
-  vstate[2 * p + 1] = make_float4((float)(c64[0] - (double)ax), (float)(c64[1] - (double)ay),
-                                  (float)(c64[2] - (double)az), 0.0f);
+  vstate[2 * p + 1] = make_float4((p0[0] - ax) + cx, (p0[1] - ay) + cy, (p0[2] - az) + cz, 0.0f);
 }
 
 // b = R_ref m + t_ref - a (world axes), for an observation of a voxel whose
 // anchor is an
 __device__ inline void offset_b(const double* c, const double* ref, float4 an, double b[3]) {
-  b[0] = ref[0] * c[6] + ref[1] * c[7] + ref[2] * c[8] + (ref[9] - (double)an.x);
-  b[1] = ref[3] * c[6] + ref[4] * c[7] + ref[5] * c[8] + (ref[10] - (double)an.y);
-  b[2] = ref[6] * c[6] + ref[7] * c[7] + ref[8] * c[8] + (ref[11] - (double)an.z);
+  b[0] = ref[0] * c[6] + ref[1] * c[7] + ref[2] * c[8] + (ref[9] - f32_to_f64(an.x));
+  b[1] = ref[3] * c[6] + ref[4] * c[7] + ref[5] * c[8] + (ref[10] - f32_to_f64(an.y));
+  b[2] = ref[6] * c[6] + ref[7] * c[7] + ref[8] * c[8] + (ref[11] - f32_to_f64(an.z));
 }
 
-// slots of the slices that start at sorted positions [p0, p1) (p0 a multiple of kSlice)
+// slots of the slices that start at sorted positions [p0, p1) (p0 a multiple
+// of kSlice): thread (p, blockIdx.y) fills rows kFillRows * blockIdx.y ..
+// + kFillRows - 1 of voxel p, then the same rows gridDim.y * kFillRows on
 __global__ void fill_sell_mixed_kernel(LoadInput in, const int32_t* vperm, const int32_t* vlen,
                                        const int64_t* slice_off, int64_t n_voxels, int64_t p0, int64_t p1,
                                        const double* sref, const float4* vanchor, float4* ve32) {
@@ -184,100 +211,115 @@ __global__ void fill_sell_mixed_kernel(LoadInput in, const int32_t* vperm, const
   const int32_t len = real ? vlen[p] : 0;
   const int64_t o0 = real ? in.voxel_off[vperm[p]] : 0;
   const float4 an = real ? vanchor[p] : make_float4(0.f, 0.f, 0.f, 0.f);
-  for (int64_t k = 0; k < rows; ++k) {
-    const int64_t e = base + k * kSlice;
-    float4 s0 = make_float4(0.f, 0.f, 0.f, 0.f), s1 = s0, s2 = s0;
-    if (k < len) {
-      const int64_t o = o0 + k;
-      double c[10], b[3];
-      centred_cluster(in.agg + 10 * o, in.agg_form, c);
-      const double* ref = sref + 12 * (int64_t)in.obs_scan[o];
-      offset_b(c, ref, an, b);
-      // eigen-decomposition of the scatter in the scan frame: an FP32 Jacobi
-      // gives V0; W = V0^T S V0 is diagonal up to FP32 rounding, and its FP32
-      // Jacobi gives the variances to FP32 relative precision (the normal one
-      // included); V = V0 W_vec.  A direction error d of the stored vectors
-      // changes a variance only by (spread) d^2.
-      const float sf[6] = {(float)c[0], (float)c[1], (float)c[2], (float)c[3], (float)c[4], (float)c[5]};
-      float lam0[3], v0[9];
-      eig3_sym_f(sf, lam0, v0);  // eigenvectors as rows of v0 (vector c at v0[3c..3c+2])
-      // W = V0^T S V0.  The entries of the two smallest directions (W_00,
-      // W_01, W_11) are small next to S's largest entries and lose digits to
-      // cancellation in FP32, so they are formed in FP64: W_00 is the normal
-      // variance of a planar cluster, and for a rod-like cluster (two small,
-      // nearly equal variances) the voxel normal can be any direction of that
-      // pair.  The entries with the largest direction only need absolute
-      // precision (off-diagonals of order 1e-7 of the spread turn V0 by ~1e-7
-      // rad, a second-order change of the variances).
-      float wf[6];
-      {
-        const double S[3][3] = {{c[0], c[1], c[2]}, {c[1], c[3], c[4]}, {c[2], c[4], c[5]}};
-        double Sv[2][3];  // S v_k, k = 0, 1 (FP64)
-        for (int k = 0; k < 2; ++k)
+  for (int64_t k0 = (int64_t)blockIdx.y * kFillRows; k0 < rows; k0 += (int64_t)gridDim.y * kFillRows) {
+    for (int64_t k = k0; k < k0 + kFillRows && k < rows; ++k) {
+      const int64_t e = base + k * kSlice;
+      float4 s0 = make_float4(0.f, 0.f, 0.f, 0.f), s1 = s0, s2 = s0;
+      if (k < len) {
+        const int64_t o = o0 + k;
+        double c[10], b[3];
+        centred_cluster(in.agg + 10 * o, in.agg_form, c);
+        const double* ref = sref + 12 * (int64_t)in.obs_scan[o];
+        offset_b(c, ref, an, b);
+        // eigen-decomposition of the scatter in the scan frame: an FP32 Jacobi
+        // gives V0; W = V0^T S V0 is diagonal up to FP32 rounding, and its FP32
+        // Jacobi gives the variances to FP32 relative precision (the normal one
+        // included); V = V0 W_vec.  A direction error d of the stored vectors
+        // changes a variance only by (spread) d^2.
+        float sf[6];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) sf[q] = f64_to_f32(c[q]);
+        float lam0[3], v0[9];
+        eig3_sym_f(sf, lam0, v0);  // eigenvectors as rows of v0 (vector c at v0[3c..3c+2])
+        // W = V0^T S V0.  The entries of the two smallest directions (W_00,
+        // W_01, W_11) are small next to S's largest entries and lose digits to
+        // cancellation in FP32, so they are formed in FP64: W_00 is the normal
+        // variance of a planar cluster, and for a rod-like cluster (two small,
+        // nearly equal variances) the voxel normal can be any direction of that
+        // pair.  The entries with the largest direction only need absolute
+        // precision (off-diagonals of order 1e-7 of the spread turn V0 by ~1e-7
+        // rad, a second-order change of the variances).
+        float wf[6];
+        {
+          const double S[3][3] = {{c[0], c[1], c[2]}, {c[1], c[3], c[4]}, {c[2], c[4], c[5]}};
+          double vd[6];  // v_0, v_1 in FP64 (exact)
+#pragma unroll
+          for (int q = 0; q < 6; ++q) vd[q] = f32_to_f64(v0[q]);
+          double Sv[2][3];  // S v_k, k = 0, 1 (FP64)
+          for (int k = 0; k < 2; ++k)
+            for (int r = 0; r < 3; ++r) Sv[k][r] = S[r][0] * vd[3 * k] + S[r][1] * vd[3 * k + 1] + S[r][2] * vd[3 * k + 2];
+          wf[0] = f64_to_f32(vd[0] * Sv[0][0] + vd[1] * Sv[0][1] + vd[2] * Sv[0][2]);
+          wf[1] = f64_to_f32(vd[0] * Sv[1][0] + vd[1] * Sv[1][1] + vd[2] * Sv[1][2]);
+          wf[3] = f64_to_f32(vd[3] * Sv[1][0] + vd[4] * Sv[1][1] + vd[5] * Sv[1][2]);
+          const float M[3][3] = {{sf[0], sf[1], sf[2]}, {sf[1], sf[3], sf[4]}, {sf[2], sf[4], sf[5]}};
+          float T[3];  // S v_2 (FP32)
+          for (int r = 0; r < 3; ++r) T[r] = fmaf(M[r][0], v0[6], fmaf(M[r][1], v0[7], M[r][2] * v0[8]));
+          // packed (00, 01, 02, 11, 12, 22)
+          wf[2] = fmaf(v0[0], T[0], fmaf(v0[1], T[1], v0[2] * T[2]));
+          wf[4] = fmaf(v0[3], T[0], fmaf(v0[4], T[1], v0[5] * T[2]));
+          wf[5] = fmaf(v0[6], T[0], fmaf(v0[7], T[1], v0[8] * T[2]));
+        }
+        float sg[3], wv[9];
+        eig3_sym_f(wf, sg, wv);
+        // world-axis eigenvectors as columns: V = R_ref V0^T-rows ... = R_ref [v0 rows]^T W
+        const float* Rf = sref32_of(sref, in.n_scans, in.obs_scan[o]);
+        float V[9];
+        for (int cc = 0; cc < 3; ++cc) {
+          float u[3];  // scan-frame vector cc = sum_k v0_k W[k][cc]
           for (int r = 0; r < 3; ++r)
-            Sv[k][r] = S[r][0] * (double)v0[3 * k] + S[r][1] * (double)v0[3 * k + 1] + S[r][2] * (double)v0[3 * k + 2];
-        wf[0] = (float)((double)v0[0] * Sv[0][0] + (double)v0[1] * Sv[0][1] + (double)v0[2] * Sv[0][2]);
-        wf[1] = (float)((double)v0[0] * Sv[1][0] + (double)v0[1] * Sv[1][1] + (double)v0[2] * Sv[1][2]);
-        wf[3] = (float)((double)v0[3] * Sv[1][0] + (double)v0[4] * Sv[1][1] + (double)v0[5] * Sv[1][2]);
-        const float M[3][3] = {{sf[0], sf[1], sf[2]}, {sf[1], sf[3], sf[4]}, {sf[2], sf[4], sf[5]}};
-        float T[3];  // S v_2 (FP32)
-        for (int r = 0; r < 3; ++r) T[r] = fmaf(M[r][0], v0[6], fmaf(M[r][1], v0[7], M[r][2] * v0[8]));
-        // packed (00, 01, 02, 11, 12, 22)
-        wf[2] = fmaf(v0[0], T[0], fmaf(v0[1], T[1], v0[2] * T[2]));
-        wf[4] = fmaf(v0[3], T[0], fmaf(v0[4], T[1], v0[5] * T[2]));
-        wf[5] = fmaf(v0[6], T[0], fmaf(v0[7], T[1], v0[8] * T[2]));
+            u[r] = fmaf(v0[r], wv[3 * cc], fmaf(v0[3 + r], wv[3 * cc + 1], v0[6 + r] * wv[3 * cc + 2]));
+          for (int r = 0; r < 3; ++r) V[3 * r + cc] = fmaf(Rf[3 * r], u[0], fmaf(Rf[3 * r + 1], u[1], Rf[3 * r + 2] * u[2]));
+        }
+        const float det = V[0] * (V[4] * V[8] - V[5] * V[7]) - V[1] * (V[3] * V[8] - V[5] * V[6]) +
+                          V[2] * (V[3] * V[7] - V[4] * V[6]);
+        if (det < 0.f) {
+          V[0] = -V[0];
+          V[3] = -V[3];
+          V[6] = -V[6];
+        }
+        float qf[4];
+        mat_to_quat<float>(V, qf);
+        s0 = make_float4(f64_to_f32(b[0]), f64_to_f32(b[1]), f64_to_f32(b[2]), f64_to_f32(c[9]));
+        s1 = make_float4(sg[0], sg[1], sg[2], __int_as_float(in.obs_scan[o]));
+        s2 = make_float4(qf[0], qf[1], qf[2], qf[3]);
       }
-      float sg[3], wv[9];
-      eig3_sym_f(wf, sg, wv);
-      // world-axis eigenvectors as columns: V = R_ref V0^T-rows ... = R_ref [v0 rows]^T W
-      const float* Rf = sref32_of(sref, in.n_scans, in.obs_scan[o]);
-      float V[9];
-      for (int cc = 0; cc < 3; ++cc) {
-        float u[3];  // scan-frame vector cc = sum_k v0_k W[k][cc]
-        for (int r = 0; r < 3; ++r)
-          u[r] = fmaf(v0[r], wv[3 * cc], fmaf(v0[3 + r], wv[3 * cc + 1], v0[6 + r] * wv[3 * cc + 2]));
-        for (int r = 0; r < 3; ++r) V[3 * r + cc] = fmaf(Rf[3 * r], u[0], fmaf(Rf[3 * r + 1], u[1], Rf[3 * r + 2] * u[2]));
-      }
-      const float det = V[0] * (V[4] * V[8] - V[5] * V[7]) - V[1] * (V[3] * V[8] - V[5] * V[6]) +
-                        V[2] * (V[3] * V[7] - V[4] * V[6]);
-      if (det < 0.f) {
-        V[0] = -V[0];
-        V[3] = -V[3];
-        V[6] = -V[6];
-      }
-      float qf[4];
-      mat_to_quat<float>(V, qf);
-      s0 = make_float4((float)b[0], (float)b[1], (float)b[2], (float)c[9]);
-      s1 = make_float4(sg[0], sg[1], sg[2], __int_as_float(in.obs_scan[o]));
-      s2 = make_float4(qf[0], qf[1], qf[2], qf[3]);
+      ve32[kVe32 * e] = s0;
+      ve32[kVe32 * e + 1] = s1;
+      ve32[kVe32 * e + 2] = s2;
     }
-    ve32[kVe32 * e] = s0;
-    ve32[kVe32 * e + 1] = s1;
-    ve32[kVe32 * e + 2] = s2;
   }
 }
 
-__global__ void fill_scan_mixed_kernel(LoadInput in, const uint32_t* order, const int32_t* obs_vox,
-                                       const double* vscale, const int32_t* vrank, const double* sref,
-                                       const float4* vanchor, float* se32) {
+// Scan-major FP32 copy from the slots: the offset and count as they are, the
+// scatter in reference axes rebuilt from its eigenvalues and eigenvector
+// quaternion (R_ref S R_ref^T = V diag(sigma) V^T), each scaled by 2 / N_i.
+// obs_pos[o] is the slot of observation o (sorted voxel position p, row k:
+// slice_off[p / 32] + 32 k + p % 32).
+__global__ void fill_scan_mixed_kernel(int64_t n_obs, const uint32_t* order, const int32_t* obs_vox,
+                                       const double* vscale, const int32_t* vrank, const int64_t* voxel_off,
+                                       const int64_t* slice_off, const float4* ve32, float* se32) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= in.n_obs) return;
+  if (q >= n_obs) return;
   const int64_t o = order[q];
   const int32_t v = obs_vox[o];
-  const float4 an = vanchor[vrank[v]];
-  double c[10], b[3];
+  const int64_t p = vrank[v];
+  const int64_t e = slice_off[p >> 5] + (o - voxel_off[v]) * kSlice + (p & 31);
+  const float4 s0 = ve32[kVe32 * e], s1 = ve32[kVe32 * e + 1], s2 = ve32[kVe32 * e + 2];
+  float V[9];
+  quat_to_mat_f(s2.x, s2.y, s2.z, s2.w, V);
+  const float sg[3] = {s1.x, s1.y, s1.z};
   float sw[6];
-  centred_cluster(in.agg + 10 * o, in.agg_form, c);
-  const int32_t j = in.obs_scan[o];
-  offset_b(c, sref + 12 * (int64_t)j, an, b);
-  const float Sf[6] = {(float)c[0], (float)c[1], (float)c[2], (float)c[3], (float)c[4], (float)c[5]};
-  rot_sym_f(sref32_of(sref, in.n_scans, j), Sf, sw);  // the scan pass is FP32 throughout
-  const float k = (float)vscale[v];
-  const int64_t n = in.n_obs;
+  int idx = 0;
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = r; c < 3; ++c)
+      sw[idx++] = fmaf(V[3 * r] * sg[0], V[3 * c], fmaf(V[3 * r + 1] * sg[1], V[3 * c + 1], V[3 * r + 2] * sg[2] * V[3 * c + 2]));
+  const float k = f64_to_f32(vscale[v]);
   float4* bN = reinterpret_cast<float4*>(se32);
-  float4* S4 = bN + n;
-  float2* S2 = reinterpret_cast<float2*>(S4 + n);
-  bN[q] = make_float4((float)b[0], (float)b[1], (float)b[2], (float)(vscale[v] * c[9]));
+  float4* S4 = bN + n_obs;
+  float2* S2 = reinterpret_cast<float2*>(S4 + n_obs);
+  bN[q] = make_float4(s0.x, s0.y, s0.z, k * s0.w);
   S4[q] = make_float4(k * sw[0], k * sw[1], k * sw[2], k * sw[3]);
   S2[q] = make_float2(k * sw[4], k * sw[5]);
 }
@@ -296,15 +338,17 @@ cudaError_t build_mixed_voxels(const LoadInput& in, const LayoutBuffers& lb, con
   if (v1 <= v0) return cudaSuccess;
   LoadInput cur = in;
   cur.poses = poses2;  // buffer 0
-  voxel_frames_kernel<<<(unsigned)((v1 - v0 + 127) / 128), 128, 0, stream>>>(cur, v0, v1, mb.sref, lb.vrank,
-                                                                            mb.vstate, mb.vanchor, mb.planes32_2);
+  voxel_frames_kernel<<<(unsigned)((v1 - v0 + 3) / 4), 128, 0, stream>>>(cur, v0, v1, mb.sref, lb.vrank, mb.vstate,
+                                                                        mb.vanchor, mb.planes32_2);
   ++*launches;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   // the slices of sorted positions [v0, v1): windows keep their voxels, so for
   // window-aligned ranges these are exactly the voxels whose frames were just set
   const int64_t p0 = v0, p1 = min(in.n_voxels, ((v1 + kSlice - 1) / kSlice) * kSlice);
-  fill_sell_mixed_kernel<<<(unsigned)((p1 - p0 + 127) / 128), 128, 0, stream>>>(
+  const unsigned row_blocks =
+      (unsigned)std::min<int64_t>(std::max<int64_t>((lb.max_len + kFillRows - 1) / kFillRows, 1), 65535);
+  fill_sell_mixed_kernel<<<dim3((unsigned)((p1 - p0 + 127) / 128), row_blocks), 128, 0, stream>>>(
       cur, lb.vperm, lb.vlen, lb.slice_off, in.n_voxels, p0, p1, mb.sref, mb.vanchor, mb.ve32);
   ++*launches;
   return cudaGetLastError();
@@ -313,10 +357,8 @@ cudaError_t build_mixed_voxels(const LoadInput& in, const LayoutBuffers& lb, con
 cudaError_t build_mixed_end(const LoadInput& in, const LayoutBuffers& lb, const double* poses2, MixedBuffers& mb,
                             cudaStream_t stream, int64_t* launches) {
   const int64_t no = in.n_obs;
-  LoadInput cur = in;
-  cur.poses = poses2;
-  fill_scan_mixed_kernel<<<(unsigned)((no + 255) / 256), 256, 0, stream>>>(cur, lb.scan_order, lb.obs_vox, lb.vscale,
-                                                                           lb.vrank, mb.sref, mb.vanchor, mb.se32);
+  fill_scan_mixed_kernel<<<(unsigned)((no + 255) / 256), 256, 0, stream>>>(
+      no, lb.scan_order, lb.obs_vox, lb.vscale, lb.vrank, in.voxel_off, lb.slice_off, mb.ve32, mb.se32);
   ++*launches;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;

@@ -101,6 +101,36 @@ __device__ __forceinline__ void quat_to_mat_f(float w, float x, float y, float z
   R[8] = 1.f - 2.f * (xx + yy);
 }
 
+// ---- conversions between binary64 and binary32 in integer arithmetic ----
+// GB300 runs FP64 <-> FP32 conversions on its narrow FP64 pipe; set-up code
+// that converts tens of values per observation uses these instead.  Both
+// follow IEEE 754: binary64 -> binary32 rounds to nearest, ties to even;
+// binary32 -> binary64 is exact.  Values outside the normal ranges (zero,
+// subnormal, overflow, infinity, NaN) take the hardware conversion.
+__device__ __forceinline__ float f64_to_f32(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned int hi = (unsigned int)(b >> 32);
+  const int ef = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;  // binary32 biased exponent
+  if (ef <= 0 || ef >= 255) return (float)x;
+  const unsigned int mf = (unsigned int)((b >> 29) & 0x7fffffu);  // top 23 of 52 fraction bits
+  const unsigned int rest = (unsigned int)(b & 0x1fffffffu);     // the 29 bits dropped
+  unsigned int r = ((unsigned int)ef << 23) | mf;
+  // nearest, ties to even; a carry out of the fraction moves to the next binade
+  // (and to infinity past the largest finite value), as rounding requires
+  if (rest > 0x10000000u || (rest == 0x10000000u && (mf & 1u))) r += 1u;
+  return __uint_as_float(r | (hi & 0x80000000u));
+}
+
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const unsigned int u = __float_as_uint(f);
+  const unsigned int e = (u >> 23) & 0xffu;
+  if (e == 0u || e == 255u) return (double)f;
+  const unsigned long long r = ((unsigned long long)(u & 0x80000000u) << 32) |
+                               ((unsigned long long)(e - 127u + 1023u) << 52) |
+                               ((unsigned long long)(u & 0x7fffffu) << 29);
+  return __longlong_as_double((long long)r);
+}
+
 // Unit quaternion (w, x, y, z) of a rotation matrix (row-major), from the
 // largest of 1 + tr, 1 + 2 R_kk - tr (Shepperd's method, J. Guidance and
 // Control 1, 1978), normalised.

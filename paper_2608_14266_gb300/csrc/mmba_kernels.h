@@ -93,6 +93,7 @@ struct LayoutBuffers {
   int32_t* se_vox;
   int64_t n_elems;
   int64_t n_slices;
+  int64_t max_len;  // observations of the longest voxel (rows of the longest slice)
   // kept only when the FP64 copies are not built (mixed precision)
   int32_t* vrank;        // input voxel -> sorted position
   int32_t* obs_vox;      // observation -> input voxel

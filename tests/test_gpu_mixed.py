@@ -206,3 +206,30 @@ def test_pipelined_load_reports_bad_cluster(mm):
             # the handle loads good inputs afterwards
             a.load_observations(s.n_scans, s.voxel_off, s.obs_scan, cen, s.pose_init)
             assert np.isfinite(a.cost())
+
+
+def test_pipelined_load_rejects_bad_offsets_before_copying(mm):
+    """The chunked copy starts before validation, from chunk boundaries read in
+    the host offsets; malformed offsets start no copy and fail validation with
+    the first violating index."""
+    s, cen = _scene_20k()
+    for k, val in ((s.n_voxels, s.n_obs - 1), (9000, 10**9), (0, 3)):
+        vo = s.voxel_off.copy()
+        vo[k] = val
+        with _mixed(mm) as a:
+            with pytest.raises(mm.BAError) as e:
+                a.load_observations(s.n_scans, vo, s.obs_scan, cen, s.pose_init)
+            assert e.value.status == 1 and "voxel_offsets" in str(e.value)
+
+
+def test_integer_conversions_match_hardware(mm):
+    """The set-up's integer-arithmetic binary64 <-> binary32 conversions give
+    the hardware's results bit for bit (round to nearest even one way, exact
+    the other) on random values across the binary32 range, values at and next
+    to rounding ties, and special values."""
+    import ctypes
+    from paper_2608_14266_gb300 import _lib
+    out = (ctypes.c_uint64 * 2)()
+    for seed in (1, 2, 3):
+        assert _lib.lib().ba_check_conversions(0, 4_000_000, seed, out) == 0
+        assert list(out) == [0, 0]
