@@ -196,7 +196,10 @@ int64_t ba_estimate_bytes(int32_t precision, int32_t n_scans, int64_t n_voxels, 
  * stream (enabling clears earlier records).  ba_profile_read synchronises
  * the stream and returns, for one kernel kind, the summed event time in
  * milliseconds and the number of launches recorded.  A scan pass launched
- * after a rejected step returns at once and is still counted. */
+ * after a rejected step returns at once and is still counted.  The LM
+ * decision runs in the last block of each iteration's voxel pass, so its time
+ * is part of BA_KERNEL_VOXEL_PASS and BA_KERNEL_DECIDE records no launch (the
+ * kind is kept for callers that read it). */
 enum { BA_KERNEL_VOXEL_PASS = 0, BA_KERNEL_SCAN_PASS = 1, BA_KERNEL_SOLVE = 2, BA_KERNEL_DECIDE = 3 };
 ba_status ba_profile_enable(ba_handle* h, int32_t enable);
 ba_status ba_profile_read(ba_handle* h, int32_t kind, double* total_ms, int64_t* launches);
@@ -213,8 +216,8 @@ const char* ba_status_string(ba_status s);
 /* ---- Batched execution --------------------------------------------------
  * A batch steps many independent problems (jobs) together: every iteration
  * launches each kernel kind once over a device-side table of the jobs, so
- * hundreds of small jobs cost a handful of launches per iteration instead of
- * four each.  Jobs are ordinary handles, loaded and read with the calls
+ * hundreds of small jobs cost three launches per iteration instead of three
+ * each.  Jobs are ordinary handles, loaded and read with the calls
  * above; each keeps its own LM state (damping, acceptance, stopping rule of
  * its own configuration) and its results are bit-identical to running it
  * alone, because every kernel block belongs to exactly one job and runs the
@@ -247,7 +250,7 @@ ba_status ba_batch_solve(ba_batch* b, int32_t chunk, int32_t max_rounds, int32_t
 ba_status ba_batch_done(ba_batch* b, int32_t* done_out);
 void ba_batch_destroy(ba_batch* b);
 const char* ba_batch_last_error(const ba_batch* b);
-/* Kernel launches issued by the batch's iterations (4 per iteration). */
+/* Kernel launches issued by the batch's iterations (3 per iteration). */
 int64_t ba_batch_kernel_launches(const ba_batch* b);
 
 /* ---- Served execution (continuous batching) -----------------------------

@@ -241,10 +241,14 @@ void fill_stats(const DevState& s, double cost_before, int32_t iters_call, ba_st
   out->reserved = 0;
 }
 
-// Evaluate planes, cost, gradient and Hessian at the current poses.
-cudaError_t voxel_pass(ba_handle* h, double* full, int use_trial) {
-  if (h->mixed) return launch_voxel_pass_mixed(h->L, h->X, full, h->cost_part, h->d_state, use_trial, h->stream);
-  return launch_voxel_pass_f64(h->L, h->poses2, h->planes2, full, h->cost_part, h->d_state, use_trial, h->stream);
+// Voxel pass with the decision folded into its last block (decide_mode as
+// for launch_voxel_pass_*).
+cudaError_t voxel_pass(ba_handle* h, double* full, int use_trial, int decide_mode) {
+  if (h->mixed)
+    return launch_voxel_pass_mixed(h->L, h->X, full, h->cost_part, h->pred_part, h->d_state, use_trial, decide_mode,
+                                   h->stream);
+  return launch_voxel_pass_f64(h->L, h->poses2, h->planes2, full, h->cost_part, h->pred_part, h->d_state, use_trial,
+                               decide_mode, h->stream);
 }
 
 cudaError_t scan_pass(ba_handle* h, int force) {
@@ -253,10 +257,10 @@ cudaError_t scan_pass(ba_handle* h, int force) {
 }
 
 ba_status evaluate_current(ba_handle* h) {
-  CK(h, voxel_pass(h, nullptr, 0), "voxel pass");
-  CK(h, launch_decide(h->cost_part, h->n_cost, h->pred_part, h->L.n_scans, h->d_state, 1, h->stream), "cost sum");
+  // planes, and the summed cost installed as the current cost (last block)
+  CK(h, voxel_pass(h, nullptr, 0, 1), "voxel pass");
   CK(h, scan_pass(h, 1), "scan pass");
-  h->launches += 3;
+  h->launches += 2;
   return BA_OK;
 }
 
@@ -289,16 +293,13 @@ ba_status launch_iteration(ba_handle* h) {
      "solve");
   CK(h, prof_end(h, ev), "event");
   CK(h, prof_begin(h, BA_KERNEL_VOXEL_PASS, &ev), "event");
-  CK(h, voxel_pass(h, nullptr, 1), "trial voxel pass");
-  CK(h, prof_end(h, ev), "event");
-  CK(h, prof_begin(h, BA_KERNEL_DECIDE, &ev), "event");
-  CK(h, launch_decide(h->cost_part, h->n_cost, h->pred_part, solve_blocks(h->L.n_scans), h->d_state, 0, h->stream),
-     "decide");
+  // the trial cost and the LM decision (in the pass's last block)
+  CK(h, voxel_pass(h, nullptr, 1, 0), "trial voxel pass");
   CK(h, prof_end(h, ev), "event");
   CK(h, prof_begin(h, BA_KERNEL_SCAN_PASS, &ev), "event");
   CK(h, scan_pass(h, 0), "scan pass");
   CK(h, prof_end(h, ev), "event");
-  h->launches += 4;
+  h->launches += 3;
   return BA_OK;
 }
 
@@ -806,7 +807,7 @@ ba_status ba_planes(ba_handle* h, double* out, int32_t mem_kind) {
   const size_t bytes = sizeof(double) * 9 * (size_t)h->L.n_voxels;
   double* full = mem_kind == BA_MEM_DEVICE ? out : (double*)dev_alloc(h, h->temp, bytes);
   if (!full) return fail(h, BA_ERR_OOM, "plane buffer: out of device memory");
-  CK(h, voxel_pass(h, full, 0), "voxel pass");
+  CK(h, voxel_pass(h, full, 0, -1), "voxel pass");
   ++h->launches;
   if (mem_kind == BA_MEM_HOST) {
     CK(h, cudaMemcpyAsync(out, full, bytes, cudaMemcpyDeviceToHost, h->stream), "read planes");
@@ -1120,7 +1121,6 @@ ba_status launch_batch_iteration(ba_batch* b) {
   BCK(b, b->mixed ? launch_batch_voxel_pass_mixed(T, b->n_vblk, 1, b->stream)
                   : launch_batch_voxel_pass_f64(T, b->n_vblk, 1, b->stream),
       "batch voxel pass");
-  BCK(b, launch_batch_decide(T, b->stream), "batch decide");
   BCK(b, b->mixed ? launch_batch_scan_pass_mixed(T, b->n_sblk, b->stream)
                   : launch_batch_scan_pass_f64(T, b->n_sblk, b->stream),
       "batch scan pass");
@@ -1160,7 +1160,7 @@ ba_status run_iterations(ba_batch* b, int n) {
     b->graph_iters = n;
   }
   BCK(b, cudaGraphLaunch(b->graph, b->stream), "graph launch");
-  b->launches += 4 * (int64_t)n;
+  b->launches += 3 * (int64_t)n;
   return BA_OK;
 }
 

@@ -20,9 +20,15 @@ namespace mmba {
 template <bool kFull>
 __device__ __forceinline__ void voxel_pass_f64_body(const DevLayout& L, const double* __restrict__ poses2,
                                                     double* __restrict__ planes2, double* __restrict__ full_out,
-                                                    double* __restrict__ cost_part, const DevState* __restrict__ st,
-                                                    int use_trial, int64_t blk, double* red) {
-  if (st->honor_stop && st->stop) return;
+                                                    double* __restrict__ cost_part,
+                                                    const double* __restrict__ pred_part, DevState* __restrict__ st,
+                                                    int use_trial, int decide_mode, int64_t blk, double* red,
+                                                    int* is_last) {
+  if (st->honor_stop && st->stop) {
+    // a stopped solve takes no step, so no gradient is pending either
+    if (decide_mode == 0 && blk == 0 && threadIdx.x == 0) st->scan_pending = 0;
+    return;
+  }
   const int buf = use_trial ? 1 - st->cur : st->cur;
   const double* __restrict__ poses = poses2 + (int64_t)buf * L.n_scans * 12;
   double* __restrict__ planes = planes2 + (int64_t)buf * L.n_voxels * kPlaneStride;
@@ -105,6 +111,8 @@ __device__ __forceinline__ void voxel_pass_f64_body(const DevLayout& L, const do
   }
   const double tot = block_sum<kVoxelThreads>(lam0, red);
   if (threadIdx.x == 0) cost_part[blk] = tot;
+  voxel_pass_decide<kVoxelThreads>(cost_part, voxel_pass_blocks(L.n_voxels), pred_part, solve_blocks(L.n_scans), st,
+                                   decide_mode, red, is_last);
 }
 
 template <bool kFull>
@@ -112,13 +120,18 @@ __global__ void __launch_bounds__(kVoxelThreads) voxel_pass_f64_kernel(DevLayout
                                                                       double* __restrict__ planes2,
                                                                       double* __restrict__ full_out,
                                                                       double* __restrict__ cost_part,
-                                                                      const DevState* __restrict__ st, int use_trial) {
+                                                                      const double* __restrict__ pred_part,
+                                                                      DevState* __restrict__ st, int use_trial,
+                                                                      int decide_mode) {
   __shared__ double red[kVoxelThreads / 32];
-  voxel_pass_f64_body<kFull>(L, poses2, planes2, full_out, cost_part, st, use_trial, blockIdx.x, red);
+  __shared__ int is_last;
+  voxel_pass_f64_body<kFull>(L, poses2, planes2, full_out, cost_part, pred_part, st, use_trial, decide_mode,
+                             blockIdx.x, red, &is_last);
 }
 
 __global__ void __launch_bounds__(kVoxelThreads) voxel_pass_f64_batch_kernel(JobTable T, int use_trial) {
   __shared__ double red[kVoxelThreads / 32];
+  __shared__ int is_last;
   __shared__ JobView J;
   __shared__ int64_t blk;
   if (threadIdx.x == 0) {
@@ -127,7 +140,8 @@ __global__ void __launch_bounds__(kVoxelThreads) voxel_pass_f64_batch_kernel(Job
     blk = blockIdx.x - T.vblk[job];
   }
   __syncthreads();
-  voxel_pass_f64_body<false>(J.L, J.poses2, J.planes2, nullptr, J.cost_part, J.st, use_trial, blk, red);
+  voxel_pass_f64_body<false>(J.L, J.poses2, J.planes2, nullptr, J.cost_part, J.pred_part, J.st, use_trial,
+                             use_trial ? 0 : 1, blk, red, &is_last);
 }
 
 // ---------------------------------------------------------------------------
@@ -408,88 +422,32 @@ __global__ void __launch_bounds__(kSolveThreads) solve_f64_batch_kernel(JobTable
   solve_f64_body(J.L, J.poses2, J.gH, J.pred_part, J.st, J.X.sref, J.X.stab2, blk, red);
 }
 
-// ---------------------------------------------------------------------------
-// LM decision (one block): sums the trial cost and the predicted reduction
-// in a fixed order, accepts iff every solve succeeded, the prediction is
-// positive and the cost decreased, and updates the damping (Nielsen's rule:
-// mu *= max(1/3, 1 - (2 rho - 1)^3), nu = 2 on acceptance; mu *= nu, nu *= 2
-// otherwise).  Acceptance flips the current pose/plane buffers.
-// With mode = 1 it only installs the summed cost as the current cost.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void decide_body(const double* __restrict__ cost_part, int64_t n_cost,
-                                            const double* __restrict__ pred_part, int64_t n_pred, DevState* st,
-                                            int mode, double* red) {
-  if (mode == 0 && st->honor_stop && st->stop) {
-    if (threadIdx.x == 0) st->scan_pending = 0;
-    return;
-  }
-  const double csum = block_sum<kDecideThreads>(strided_sum<kDecideThreads>(cost_part, n_cost), red);
-  const double psum =
-      block_sum<kDecideThreads>(mode == 0 ? strided_sum<kDecideThreads>(pred_part, n_pred) : 0.0, red);
-  if (threadIdx.x != 0) return;
-  if (mode == 1) {
-    st->cost = csum;
-    return;
-  }
-  // work on a register copy: one load and one store of the state instead of a
-  // chain of dependent global accesses
-  DevState s = *st;
-  const int fail = s.solve_fail_flag;
-  const bool accept = !fail && psum > 0.0 && csum < s.cost;
-  s.iters += 1;
-  s.last_pred = psum;
-  s.last_trial_cost = csum;
-  s.solve_failed = fail;
-  s.solve_fail_flag = 0;
-  if (accept) {
-    const double rho = (s.cost - csum) / psum;
-    const double x = 2.0 * rho - 1.0;
-    const double f = 1.0 - x * x * x;
-    s.mu *= f > (1.0 / 3.0) ? f : (1.0 / 3.0);
-    s.nu = 2.0;
-    s.last_rho = rho;
-    s.converged = (s.cost - csum) <= s.rel_tol * s.cost + s.abs_tol;
-    s.cost = csum;
-    s.cur = 1 - s.cur;
-    s.accepted += 1;
-    s.consec_reject = 0;
-  } else {
-    s.mu *= s.nu;
-    s.nu *= 2.0;
-    s.last_rho = (!fail && psum > 0.0) ? (s.cost - csum) / psum : __longlong_as_double(0x7ff8000000000000ll);
-    s.consec_reject += 1;
-  }
-  s.last_accepted = accept;
-  s.scan_pending = accept;
-  if (s.honor_stop && (s.converged || s.iters >= s.max_iters || s.consec_reject >= s.max_consec_reject)) s.stop = 1;
-  *st = s;
-}
-
 __global__ void __launch_bounds__(kDecideThreads) decide_kernel(const double* __restrict__ cost_part, int64_t n_cost,
                                                                const double* __restrict__ pred_part, int64_t n_pred,
                                                                DevState* st, int mode) {
   __shared__ double red[kDecideThreads / 32];
-  decide_body(cost_part, n_cost, pred_part, n_pred, st, mode, red);
+  decide_body<kDecideThreads>(cost_part, n_cost, pred_part, n_pred, st, mode, red);
 }
 
 // one block per job
 __global__ void __launch_bounds__(kDecideThreads) decide_batch_kernel(JobTable T) {
   __shared__ double red[kDecideThreads / 32];
   const JobView& J = T.jobs[blockIdx.x];
-  decide_body(J.cost_part, J.n_cost, J.pred_part, solve_blocks(J.L.n_scans), J.st, 0, red);
+  decide_body<kDecideThreads>(J.cost_part, J.n_cost, J.pred_part, solve_blocks(J.L.n_scans), J.st, 0, red);
 }
 
 // ---- launchers ---------------------------------------------------------------
 
 cudaError_t launch_voxel_pass_f64(const DevLayout& L, const double* poses2, double* planes2, double* full_out,
-                                  double* cost_part, const DevState* st, int use_trial, cudaStream_t stream) {
+                                  double* cost_part, const double* pred_part, DevState* st, int use_trial,
+                                  int decide_mode, cudaStream_t stream) {
   const int64_t nb = voxel_pass_blocks(L.n_voxels);
   if (full_out)
     voxel_pass_f64_kernel<true><<<(unsigned)nb, kVoxelThreads, 0, stream>>>(L, poses2, planes2, full_out, cost_part,
-                                                                            st, use_trial);
+                                                                            pred_part, st, use_trial, decide_mode);
   else
     voxel_pass_f64_kernel<false><<<(unsigned)nb, kVoxelThreads, 0, stream>>>(L, poses2, planes2, nullptr, cost_part,
-                                                                             st, use_trial);
+                                                                             pred_part, st, use_trial, decide_mode);
   return cudaGetLastError();
 }
 

@@ -32,9 +32,14 @@ __device__ __forceinline__ void apply_E(const float* ph, float a, float b, float
 template <bool kFull>
 __device__ __forceinline__ void voxel_pass_mixed_body(const DevLayout& L, const DevMixed& X,
                                                       double* __restrict__ full_out, double* __restrict__ cost_part,
-                                                      const DevState* __restrict__ st, int use_trial, int64_t blk,
-                                                      float* red) {
-  if (st->honor_stop && st->stop) return;
+                                                      const double* __restrict__ pred_part, DevState* __restrict__ st,
+                                                      int use_trial, int decide_mode, int64_t blk, float* red,
+                                                      double* dred, int* is_last) {
+  if (st->honor_stop && st->stop) {
+    // a stopped solve takes no step, so no gradient is pending either
+    if (decide_mode == 0 && blk == 0 && threadIdx.x == 0) st->scan_pending = 0;
+    return;
+  }
   const int buf = use_trial ? 1 - st->cur : st->cur;
   const float* __restrict__ stab = X.stab2 + (int64_t)buf * L.n_scans * kTab;
   float4* __restrict__ planes = X.planes32_2 + (int64_t)buf * L.n_voxels * 2;
@@ -155,20 +160,28 @@ __device__ __forceinline__ void voxel_pass_mixed_body(const DevLayout& L, const 
   // the sum over blocks is FP64
   const float tot = block_sum<kVoxelThreads, float>(lam0, red);
   if (threadIdx.x == 0) cost_part[blk] = (double)tot;
+  voxel_pass_decide<kVoxelThreads>(cost_part, voxel_pass_blocks(L.n_voxels), pred_part, solve_blocks(L.n_scans), st,
+                                   decide_mode, dred, is_last);
 }
 
 template <bool kFull>
 __global__ void __launch_bounds__(kVoxelThreads, 6) voxel_pass_mixed_kernel(DevLayout L, DevMixed X,
                                                                         double* __restrict__ full_out,
                                                                         double* __restrict__ cost_part,
-                                                                        const DevState* __restrict__ st,
-                                                                        int use_trial) {
+                                                                        const double* __restrict__ pred_part,
+                                                                        DevState* __restrict__ st, int use_trial,
+                                                                        int decide_mode) {
   __shared__ float red[kVoxelThreads / 32];
-  voxel_pass_mixed_body<kFull>(L, X, full_out, cost_part, st, use_trial, blockIdx.x, red);
+  __shared__ double dred[kVoxelThreads / 32];
+  __shared__ int is_last;
+  voxel_pass_mixed_body<kFull>(L, X, full_out, cost_part, pred_part, st, use_trial, decide_mode, blockIdx.x, red,
+                               dred, &is_last);
 }
 
 __global__ void __launch_bounds__(kVoxelThreads) voxel_pass_mixed_batch_kernel(JobTable T, int use_trial) {
   __shared__ float red[kVoxelThreads / 32];
+  __shared__ double dred[kVoxelThreads / 32];
+  __shared__ int is_last;
   __shared__ JobView J;
   __shared__ int64_t blk;
   if (threadIdx.x == 0) {
@@ -177,7 +190,8 @@ __global__ void __launch_bounds__(kVoxelThreads) voxel_pass_mixed_batch_kernel(J
     blk = blockIdx.x - T.vblk[job];
   }
   __syncthreads();
-  voxel_pass_mixed_body<false>(J.L, J.X, nullptr, J.cost_part, J.st, use_trial, blk, red);
+  voxel_pass_mixed_body<false>(J.L, J.X, nullptr, J.cost_part, J.pred_part, J.st, use_trial, use_trial ? 0 : 1, blk,
+                               red, dred, &is_last);
 }
 
 // ---------------------------------------------------------------------------
@@ -478,14 +492,15 @@ __global__ void scan_table_kernel(int32_t n_scans, const double* poses2, const d
 // ---- launchers ---------------------------------------------------------------
 
 cudaError_t launch_voxel_pass_mixed(const DevLayout& L, const DevMixed& X, double* full_out, double* cost_part,
-                                    DevState* st, int use_trial, cudaStream_t stream) {
+                                    const double* pred_part, DevState* st, int use_trial, int decide_mode,
+                                    cudaStream_t stream) {
   const int64_t nb = voxel_pass_blocks(L.n_voxels);
   if (full_out)
-    voxel_pass_mixed_kernel<true><<<(unsigned)nb, kVoxelThreads, 0, stream>>>(L, X, full_out, cost_part, st,
-                                                                              use_trial);
+    voxel_pass_mixed_kernel<true><<<(unsigned)nb, kVoxelThreads, 0, stream>>>(L, X, full_out, cost_part, pred_part,
+                                                                              st, use_trial, decide_mode);
   else
-    voxel_pass_mixed_kernel<false><<<(unsigned)nb, kVoxelThreads, 0, stream>>>(L, X, nullptr, cost_part, st,
-                                                                               use_trial);
+    voxel_pass_mixed_kernel<false><<<(unsigned)nb, kVoxelThreads, 0, stream>>>(L, X, nullptr, cost_part, pred_part,
+                                                                               st, use_trial, decide_mode);
   return cudaGetLastError();
 }
 

@@ -194,6 +194,7 @@ struct DevState {
   int32_t hess_mode;
   int32_t scan_pending;     // an accepted step needs g, H at the new poses
   int32_t wait_timeout;     // a bounded device-side wait gave up (sticky)
+  uint32_t blocks_done;     // voxel-pass blocks finished in the current launch (decision in the last)
 };
 
 // One job of a batch: everything its kernels touch.  A batch launches each
@@ -501,9 +502,9 @@ __device__ inline double strided_sum(const double* __restrict__ p, int64_t n) {
   int64_t k = threadIdx.x;
   for (; k + 7 * kThreads < n; k += 8 * kThreads) {
 #pragma unroll
-    for (int u = 0; u < 8; ++u) c[u] += p[k + u * kThreads];
+    for (int u = 0; u < 8; ++u) c[u] += __ldcg(p + k + u * kThreads);
   }
-  for (; k < n; k += kThreads) c[0] += p[k];
+  for (; k < n; k += kThreads) c[0] += __ldcg(p + k);
   return ((c[0] + c[1]) + (c[2] + c[3])) + ((c[4] + c[5]) + (c[6] + c[7]));
 }
 
@@ -586,6 +587,89 @@ __device__ inline T block_sum(T v, T* smem /* kThreads / 32 */) {
   }
   __syncthreads();
   return r;  // valid in thread 0
+}
+
+// ---------------------------------------------------------------------------
+// LM decision (one block): sums the trial cost and the predicted reduction
+// in a fixed order, accepts iff every solve succeeded, the prediction is
+// positive and the cost decreased, and updates the damping (Nielsen's rule:
+// mu *= max(1/3, 1 - (2 rho - 1)^3), nu = 2 on acceptance; mu *= nu, nu *= 2
+// otherwise).  Acceptance flips the current pose/plane buffers.
+// With mode = 1 it only installs the summed cost as the current cost.
+// ---------------------------------------------------------------------------
+template <int kThreads>
+__device__ __forceinline__ void decide_body(const double* __restrict__ cost_part, int64_t n_cost,
+                                            const double* __restrict__ pred_part, int64_t n_pred, DevState* st,
+                                            int mode, double* red) {
+  if (mode == 0 && st->honor_stop && st->stop) {
+    if (threadIdx.x == 0) st->scan_pending = 0;
+    return;
+  }
+  const double csum = block_sum<kThreads>(strided_sum<kThreads>(cost_part, n_cost), red);
+  const double psum =
+      block_sum<kThreads>(mode == 0 ? strided_sum<kThreads>(pred_part, n_pred) : 0.0, red);
+  if (threadIdx.x != 0) return;
+  if (mode == 1) {
+    st->cost = csum;
+    return;
+  }
+  // work on a register copy: one load and one store of the state instead of a
+  // chain of dependent global accesses
+  DevState s = *st;
+  const int fail = s.solve_fail_flag;
+  const bool accept = !fail && psum > 0.0 && csum < s.cost;
+  s.iters += 1;
+  s.last_pred = psum;
+  s.last_trial_cost = csum;
+  s.solve_failed = fail;
+  s.solve_fail_flag = 0;
+  if (accept) {
+    const double rho = (s.cost - csum) / psum;
+    const double x = 2.0 * rho - 1.0;
+    const double f = 1.0 - x * x * x;
+    s.mu *= f > (1.0 / 3.0) ? f : (1.0 / 3.0);
+    s.nu = 2.0;
+    s.last_rho = rho;
+    s.converged = (s.cost - csum) <= s.rel_tol * s.cost + s.abs_tol;
+    s.cost = csum;
+    s.cur = 1 - s.cur;
+    s.accepted += 1;
+    s.consec_reject = 0;
+  } else {
+    s.mu *= s.nu;
+    s.nu *= 2.0;
+    s.last_rho = (!fail && psum > 0.0) ? (s.cost - csum) / psum : __longlong_as_double(0x7ff8000000000000ll);
+    s.consec_reject += 1;
+  }
+  s.last_accepted = accept;
+  s.scan_pending = accept;
+  if (s.honor_stop && (s.converged || s.iters >= s.max_iters || s.consec_reject >= s.max_consec_reject)) s.stop = 1;
+  *st = s;
+}
+
+
+// Epilogue of a voxel pass that decides in its last block: every block adds
+// one to the state's counter after its cost partial is visible device-wide;
+// the block that brings the counter to n_cost sums all partials (in the same
+// fixed order as a separate decision launch, so results do not depend on which
+// block finishes last), decides, and re-arms the counter.  mode as for
+// decide_body; with mode < 0 nothing is decided.
+template <int kThreads>
+__device__ __forceinline__ void voxel_pass_decide(const double* cost_part, int64_t n_cost, const double* pred_part,
+                                                  int64_t n_pred, DevState* st, int mode, double* red,
+                                                  int* is_last) {
+  if (mode < 0) return;
+  __syncthreads();  // thread 0 has written this block's partial
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned prev = atomicAdd(&st->blocks_done, 1u);
+    *is_last = prev == (unsigned)(n_cost - 1);
+  }
+  __syncthreads();
+  if (!*is_last) return;
+  __threadfence();
+  decide_body<kThreads>(cost_part, n_cost, pred_part, n_pred, st, mode, red);
+  if (threadIdx.x == 0) st->blocks_done = 0u;
 }
 
 }  // namespace mmba

@@ -26,8 +26,12 @@ cudaError_t launch_batch_voxel_pass_mixed(const JobTable& T, int64_t n_blocks, i
 cudaError_t launch_batch_scan_pass_mixed(const JobTable& T, int64_t n_blocks, cudaStream_t stream);
 
 // ---- iteration (FP64) ----
+// decide_mode: 0 = LM decision in the launch's last block (an iteration's
+// trial pass), 1 = only install the summed cost (evaluation at the current
+// poses), -1 = no decision (planes for output)
 cudaError_t launch_voxel_pass_f64(const DevLayout& L, const double* poses2, double* planes2, double* full_out,
-                                  double* cost_part, const DevState* st, int use_trial, cudaStream_t stream);
+                                  double* cost_part, const double* pred_part, DevState* st, int use_trial,
+                                  int decide_mode, cudaStream_t stream);
 cudaError_t launch_scan_pass_f64(const DevLayout& L, const double* poses2, const double* planes2, double* gH,
                                  const DevState* st, int force, cudaStream_t stream);
 // sref/stab2 non-null: also write the trial FP32 scan table (mixed precision)
@@ -113,7 +117,8 @@ cudaError_t launch_vscale(const LoadInput& in, int64_t v0, int64_t v1, double* v
 
 // ---- mixed precision ----
 cudaError_t launch_voxel_pass_mixed(const DevLayout& L, const DevMixed& X, double* full_out, double* cost_part,
-                                    DevState* st, int use_trial, cudaStream_t stream);
+                                    const double* pred_part, DevState* st, int use_trial, int decide_mode,
+                                    cudaStream_t stream);
 cudaError_t launch_scan_pass_mixed(const DevLayout& L, const DevMixed& X, const double* poses2, double* gH,
                                    DevState* st, int force, cudaStream_t stream);
 cudaError_t launch_scan_table(int32_t n_scans, const double* poses2, const double* sref, float* stab2, int buf,
