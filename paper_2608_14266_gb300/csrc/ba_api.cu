@@ -495,8 +495,9 @@ ba_status load_impl(ba_handle* h, int32_t n_scans, int64_t n_voxels, int64_t n_o
     // + 16 bytes: the staged scan pass copies the float2 array from even indices to even ends
     mb.se32 = (float*)dev_alloc(h, h->keep, sizeof(float) * 10 * (size_t)n_obs + 16);
     mb.vanchor = (float4*)dev_alloc(h, h->keep, sizeof(float4) * (size_t)n_voxels);
-    // FP64 reference poses, then their FP32 copy (see scan_ref_kernel)
-    mb.sref = (double*)dev_alloc(h, h->keep, (sizeof(double) + sizeof(float)) * 12 * (size_t)n_scans);
+    // FP64 reference poses, their FP32 copy (see scan_ref_kernel), then the FP64
+    // quaternions of dR of both pose buffers (sq2_of)
+    mb.sref = (double*)dev_alloc(h, h->keep, (18 + 8) * sizeof(double) * (size_t)n_scans);
     mb.stab2 = (float*)dev_alloc(h, h->keep, sizeof(float) * 2 * kTab * (size_t)n_scans);
     mb.planes32_2 = (float4*)dev_alloc(h, h->keep, sizeof(float4) * 2 * 2 * (size_t)n_voxels);
     if (!mb.ve32 || !mb.vstate || !mb.se32 || !mb.vanchor || !mb.sref || !mb.stab2 || !mb.planes32_2)
@@ -894,7 +895,7 @@ int64_t ba_estimate_bytes(int32_t precision, int32_t n_scans, int64_t n_voxels, 
     per_slot = 80 + 4;
   }
   const int64_t per_voxel = 8 + 4 + 4 + 4 + 8 + 2 * 32 + 16 + 32 + 8 + 2 * 32 + 16;
-  const int64_t per_scan = 8 + 24 * 8 + 27 * 8 + 8 + 12 * 8 + 2 * kTab * 4;
+  const int64_t per_scan = 8 + 24 * 8 + 27 * 8 + 8 + 26 * 8 + 2 * kTab * 4;
   const int64_t keep = per_obs * n_obs + per_slot * slots + per_voxel * n_voxels + per_scan * (int64_t)n_scans +
                        (1 << 16);
   // load: staged inputs (host inputs), sort keys/values and scratch

@@ -332,15 +332,18 @@ __global__ void __launch_bounds__(kScanThreads) scan_pass_f64_batch_kernel(JobTa
 // predicted reduction -(g^T delta + delta^T H delta / 2).  The fixed scan and
 // scans without observations keep their pose.
 // ---------------------------------------------------------------------------
+// *stepped = false: the pose is kept (fixed scan, no observation, failed
+// factorisation); otherwise dlt holds the increment.
 __device__ inline double solve_scan(const DevLayout& L, int j, const double* __restrict__ P, double* __restrict__ Pt,
-                                    const double* __restrict__ gH, DevState* st) {
+                                    const double* __restrict__ gH, DevState* st, double* dlt, bool* stepped) {
+  *stepped = false;
   const int64_t nobs = L.scan_off[j + 1] - L.scan_off[j];
   if (j == L.fixed_scan || nobs == 0) {
     for (int k = 0; k < 12; ++k) Pt[k] = P[k];
     return 0.0;
   }
   const double* a = gH + (int64_t)j * kGH;
-  double g[6], H[36], A[36], b[6], dlt[6];
+  double g[6], H[36], A[36], b[6];
   for (int k = 0; k < 6; ++k) g[k] = a[k];
   int idx = 6;
   for (int r = 0; r < 6; ++r)
@@ -375,6 +378,7 @@ __device__ inline double solve_scan(const DevLayout& L, int j, const double* __r
   Pt[9] = P[9] + dlt[3];
   Pt[10] = P[10] + dlt[4];
   Pt[11] = P[11] + dlt[5];
+  *stepped = true;
   return pred;
 }
 
@@ -393,8 +397,26 @@ __device__ __forceinline__ void solve_f64_body(const DevLayout& L, double* __res
     const int cur = st->cur;
     const double* P = poses2 + ((int64_t)cur * L.n_scans + j) * 12;
     double* Pt = poses2 + ((int64_t)(1 - cur) * L.n_scans + j) * 12;
-    pred = solve_scan(L, (int)j, P, Pt, gH, st);
-    if (stab2) scan_table_entry(Pt, sref + 12 * (int64_t)j, stab2 + ((int64_t)(1 - cur) * L.n_scans + j) * kTab);
+    double dlt[6];
+    bool stepped;
+    pred = solve_scan(L, (int)j, P, Pt, gH, st, dlt, &stepped);
+    if (stab2) {
+      // FP64 quaternion of the trial dR: the step's Exp composed onto the
+      // current one (no matrix-to-quaternion conversion per step)
+      double* sq2 = sq2_of(sref, L.n_scans);
+      const double* qc = sq2 + ((int64_t)cur * L.n_scans + j) * 4;
+      double* qt = sq2 + ((int64_t)(1 - cur) * L.n_scans + j) * 4;
+      double qn[4];
+      if (stepped) {
+        double qe[4];
+        so3_exp_quat(dlt, qe);
+        quat_mul_d(qe, qc, qn);
+      } else {
+        for (int k = 0; k < 4; ++k) qn[k] = qc[k];
+      }
+      for (int k = 0; k < 4; ++k) qt[k] = qn[k];
+      scan_table_from_quat(qn, Pt, sref + 12 * (int64_t)j, stab2 + ((int64_t)(1 - cur) * L.n_scans + j) * kTab);
+    }
   }
   const double tot = block_sum<kSolveThreads>(pred, red);
   if (threadIdx.x == 0) pred_part[blk] = tot;

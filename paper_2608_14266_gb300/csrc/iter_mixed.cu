@@ -411,7 +411,7 @@ __device__ __forceinline__ void scan_pass_mixed_body(const DevLayout& L, const D
     double* out = gH + (int64_t)j * kGH;
     if (t < 6) {
       const int b = t / 3, r = t % 3;
-      out[t] = (double)(dR[3 * r] * tot[3 * b] + dR[3 * r + 1] * tot[3 * b + 1] + dR[3 * r + 2] * tot[3 * b + 2]);
+      out[t] = f32_to_f64(dR[3 * r] * tot[3 * b] + dR[3 * r + 1] * tot[3 * b + 1] + dR[3 * r + 2] * tot[3 * b + 2]);
     } else {
       int r = 0, rem = t - 6;
       while (rem >= 6 - r) {
@@ -434,7 +434,7 @@ __device__ __forceinline__ void scan_pass_mixed_body(const DevLayout& L, const D
           const float h = tot[6 + 6 * i - i * (i - 1) / 2 + (k - i)];
           v = fmaf(dR[3 * rr + a] * h, dR[3 * cc + b], v);
         }
-      out[t] = (double)v;
+      out[t] = f32_to_f64(v);
     }
   }
 }
@@ -486,7 +486,7 @@ __global__ void scan_table_kernel(int32_t n_scans, const double* poses2, const d
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n_scans) return;
   scan_table_entry(poses2 + ((int64_t)buf * n_scans + j) * 12, sref + 12 * (int64_t)j,
-                   stab2 + ((int64_t)buf * n_scans + j) * kTab);
+                   stab2 + ((int64_t)buf * n_scans + j) * kTab, sq2_of(sref, n_scans) + ((int64_t)buf * n_scans + j) * 4);
 }
 
 // ---- launchers ---------------------------------------------------------------

@@ -383,27 +383,66 @@ __device__ inline void eig3_sym_f(const float* a_in, float lam[3], float vec[9])
 // dR = R R_ref^T (w >= 0), dt = t - t_ref and t_ref, as
 //   (w, vx, vy, vz), (dt0, dt1, dt2, t_ref0), (t_ref1, t_ref2, 0, 0).
 // For a unit q, dR x = x + E x with E x = 2w (v x x) + 2 v x (v x x).
-__device__ inline void scan_table_entry(const double* P, const double* ref, float* out) {
+// The entry from the FP64 quaternion q of dR and the pose's translation.
+__device__ inline void scan_table_from_quat(const double* q, const double* P, const double* ref, float* out) {
+  const double sg = q[0] < 0.0 ? -1.0 : 1.0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) out[k] = f64_to_f32(sg * q[k]);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    out[4 + k] = f64_to_f32(P[9 + k] - ref[9 + k]);
+    out[7 + k] = f64_to_f32(ref[9 + k]);
+  }
+  out[10] = 0.0f;
+  out[11] = 0.0f;
+}
+
+// The entry from the pose matrix (at set-up); the FP64 quaternion of dR,
+// kept to compose later steps onto, is written to qout.
+__device__ inline void scan_table_entry(const double* P, const double* ref, float* out, double* qout) {
   double D[9];
 #pragma unroll
   for (int r = 0; r < 3; ++r)
 #pragma unroll
     for (int c = 0; c < 3; ++c) D[3 * r + c] = P[3 * r] * ref[3 * c] + P[3 * r + 1] * ref[3 * c + 1] + P[3 * r + 2] * ref[3 * c + 2];
-  double q[4];
-  mat_to_quat<double>(D, q);
-  const double sg = q[0] < 0.0 ? -1.0 : 1.0;
-  out[0] = (float)(sg * q[0]);
-  out[1] = (float)(sg * q[1]);
-  out[2] = (float)(sg * q[2]);
-  out[3] = (float)(sg * q[3]);
-  out[4] = (float)(P[9] - ref[9]);
-  out[5] = (float)(P[10] - ref[10]);
-  out[6] = (float)(P[11] - ref[11]);
-  out[7] = (float)ref[9];
-  out[8] = (float)ref[10];
-  out[9] = (float)ref[11];
-  out[10] = 0.0f;
-  out[11] = 0.0f;
+  mat_to_quat<double>(D, qout);
+  scan_table_from_quat(qout, P, ref, out);
+}
+
+// The FP64 quaternions of dR of both pose buffers, after the FP64 and FP32
+// reference poses in the sref allocation: 2 x n_scans x 4 doubles.
+__device__ __forceinline__ double* sq2_of(const double* sref, int64_t n_scans) {
+  return const_cast<double*>(sref) + 18 * n_scans;  // 12 doubles + 12 floats per scan before it
+}
+
+// Hamilton product p q of FP64 quaternions (w, x, y, z)
+__device__ __forceinline__ void quat_mul_d(const double* p, const double* q, double* r) {
+  r[0] = p[0] * q[0] - p[1] * q[1] - p[2] * q[2] - p[3] * q[3];
+  r[1] = p[0] * q[1] + p[1] * q[0] + p[2] * q[3] - p[3] * q[2];
+  r[2] = p[0] * q[2] - p[1] * q[3] + p[2] * q[0] + p[3] * q[1];
+  r[3] = p[0] * q[3] + p[1] * q[2] - p[2] * q[1] + p[3] * q[0];
+}
+
+// Unit quaternion of Exp(phi): (cos(th/2), sin(th/2) phi / th), th = |phi|;
+// below th = 0.1 from the Taylor series of both functions (terms to th^8;
+// the first dropped term is below 1e-19).
+__device__ inline void so3_exp_quat(const double* phi, double* q) {
+  const double x = phi[0], y = phi[1], z = phi[2];
+  const double t2 = x * x + y * y + z * z;
+  double c, s;  // cos(th/2), sin(th/2) / th
+  if (t2 < 0.01) {
+    c = 1.0 + t2 * (-1.0 / 8 + t2 * (1.0 / 384 + t2 * (-1.0 / 46080 + t2 * (1.0 / 10321920))));
+    s = 0.5 + t2 * (-1.0 / 48 + t2 * (1.0 / 3840 + t2 * (-1.0 / 645120 + t2 * (1.0 / 185794560))));
+  } else {
+    const double th = sqrt(t2);
+    double sh;
+    sincos(0.5 * th, &sh, &c);
+    s = sh / th;
+  }
+  q[0] = c;
+  q[1] = s * x;
+  q[2] = s * y;
+  q[3] = s * z;
 }
 
 // Hamilton product p q of quaternions held as float4 (w, x, y, z) in the
