@@ -21,6 +21,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "mmba_oracle.c")
 _HDR = os.path.join(_HERE, "mmba_oracle.h")
+_SRCS = (_SRC, os.path.join(_HERE, "voxelize_oracle.c"))
+_HDRS = (_HDR, os.path.join(_HERE, "voxelize_oracle.h"))
 _LIB = os.path.join(_HERE, "libmmba_oracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -33,11 +35,11 @@ _D = ctypes.c_double
 def build(force: bool = False) -> str:
     """Compile the oracle (gcc, -O2, no fast-math, no contraction)."""
     stale = (not os.path.exists(_LIB)) or any(
-        os.path.getmtime(s) > os.path.getmtime(_LIB) for s in (_SRC, _HDR))
+        os.path.getmtime(s) > os.path.getmtime(_LIB) for s in _SRCS + _HDRS)
     if force or stale:
         tmp = _LIB + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
-                               "-o", tmp, _SRC, "-lm"])
+                               "-o", tmp, *_SRCS, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -82,6 +84,11 @@ def _load():
                 "orc_lm_init": (None, [_P, _P, _P, _P, _P, _P, _P]),
                 "orc_lm_step": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
                 "orc_lm_solve": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
+                "orc_world_point": (None, [_P, _P, _P]),
+                "orc_merge_clusters": (None, [_P, _P, _P]),
+                "orc_voxelize": (ctypes.c_int, [ctypes.c_int32, _P, _P, _P, _D, ctypes.c_int32, _D, ctypes.c_int32,
+                                                _P]),
+                "orc_voxels_free": (None, [_P]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(lib, name)
@@ -282,3 +289,52 @@ class LM:
     @property
     def nu(self):
         return self.st.nu
+
+
+# ---- preprocessing: L1 voxelisation, bottom-up levels, selection (Sec. IV-B) --
+
+class _Voxels(ctypes.Structure):
+    _fields_ = [("n_voxels", _I64), ("n_obs", _I64), ("voxel_off", _P), ("obs_scan", _P), ("agg", _P),
+                ("level", _P), ("index", _P)]
+
+
+def world_point(pose, p):
+    pose, p = _c(pose, np.float64), _c(p, np.float64)
+    w = np.zeros(3)
+    _load().orc_world_point(_ptr(pose), _ptr(p), _ptr(w))
+    return w
+
+
+def merge_clusters(a, b):
+    a, b = _c(a, np.float64), _c(b, np.float64)
+    out = np.zeros(10)
+    _load().orc_merge_clusters(_ptr(a), _ptr(b), _ptr(out))
+    return out
+
+
+def voxelize(scan_point_off, pts, poses, voxel_size, levels=1, tau=0.0, min_obs=1):
+    """Raw scans (points of scan j at scan_point_off[j]..) -> voxel-major
+    clusters: dict with voxel_off, obs_scan, agg (centred), level, index."""
+    spo = _c(scan_point_off, np.int64)
+    pts = _c(pts, np.float64).reshape(-1, 3)
+    poses = _c(poses, np.float64).reshape(-1, 12)
+    v = _Voxels()
+    rc = _load().orc_voxelize(int(spo.shape[0] - 1), _ptr(spo), _ptr(pts), _ptr(poses), float(voxel_size),
+                              int(levels), float(tau), int(min_obs), ctypes.byref(v))
+    if rc != 0:
+        raise ValueError("voxelize failed (index out of range or out of memory)")
+    try:
+        nv, no = v.n_voxels, v.n_obs
+
+        def arr(ptr, dtype, n, shape):
+            if n == 0:
+                return np.zeros(shape, dtype=dtype)
+            ct = ctypes.POINTER(np.ctypeslib.as_ctypes_type(dtype))
+            return np.ctypeslib.as_array(ctypes.cast(ptr, ct), shape=(n,)).reshape(shape).copy()
+        return {"voxel_off": arr(v.voxel_off, np.int64, nv + 1, (nv + 1,)),
+                "obs_scan": arr(v.obs_scan, np.int32, no, (no,)),
+                "agg": arr(v.agg, np.float64, 10 * no, (no, 10)),
+                "level": arr(v.level, np.int32, nv, (nv,)),
+                "index": arr(v.index, np.int32, 3 * nv, (nv, 3))}
+    finally:
+        _load().orc_voxels_free(ctypes.byref(v))
