@@ -322,6 +322,53 @@ void ba_server_destroy(ba_server* s);
 ba_status ba_aggregate_points(int64_t n_obs, const int64_t* point_offsets, const double* points, double* agg_out,
                               void* stream);
 
+/* ---- Preprocessing: raw scans -> observations (Sec. IV-B, Algorithm 1) -----
+ * L1 voxelisation (Eq. 4): every point p of scan j goes to world coordinates
+ * w = R_j p + t_j (each axis fma(R_a0, p0, fma(R_a1, p1, fma(R_a2, p2,
+ * t_a))), the index floor(w / d) per axis; the points of one scan in one
+ * voxel form one centred cluster (Eq. 2; mean, then scatter about it, in
+ * point order).  Bottom-up levels (Eq. 5): the level-k index of a level-(k-1)
+ * cluster is floor(index / 2) per axis, and the clusters with the same
+ * (level-k index, scan) are merged; level k has voxel size 2^(k-1) d.
+ * Selection (Algorithm 1, Selection): a voxel is kept if it has at least
+ * min_obs observations and, for tau > 0, the smallest eigenvalue of the
+ * covariance of its points at the given poses is below tau times the second
+ * smallest (tau <= 0 keeps every voxel).
+ * Output: voxels of all levels (level 1 first, each level by index x, y, z),
+ * the observations of a voxel by scan; voxel_off / obs_scan / agg (centred,
+ * scan coordinates) load directly with ba_load_observations(BA_AGG_CENTRED).
+ * Indices must lie in [-2^20, 2^20) (BA_ERR_CAPACITY otherwise); at most
+ * 2^32 - 1 points per call. */
+typedef struct {
+  double voxel_size;  /* d, the level-1 voxel edge (default 1.0) */
+  int32_t levels;     /* L >= 1 (default 1) */
+  double tau;         /* planarity threshold (default 0: keep all) */
+  int32_t min_obs;    /* observations a voxel needs to be kept (default 1) */
+  int32_t device;     /* CUDA device (default 0) */
+  void* cuda_stream;  /* cudaStream_t (NULL = legacy default) */
+} ba_voxelize_config;
+
+typedef struct ba_voxels ba_voxels;
+
+void ba_voxelize_config_default(ba_voxelize_config* cfg);
+/* Points of scan j are points[scan_point_off[j] .. scan_point_off[j+1]-1]
+ * (n x 3 doubles, scan frame); poses n_scans x 12 (scan -> world).  All three
+ * arrays in host or device memory per mem_kind (the library copies them).
+ * On success *out owns the result on the device (free with
+ * ba_voxels_destroy).  Errors: BA_ERR_INVALID_ARG (malformed offsets,
+ * non-finite poses, bad config), BA_ERR_CAPACITY, BA_ERR_OOM, BA_ERR_CUDA;
+ * the message is in ba_voxelize_last_error() of the calling thread. */
+ba_status ba_voxelize(const ba_voxelize_config* cfg, int32_t n_scans, const int64_t* scan_point_off,
+                      const double* points, const double* poses, int32_t mem_kind, ba_voxels** out);
+ba_status ba_voxels_size(const ba_voxels* v, int64_t* n_voxels, int64_t* n_obs);
+/* Copy the result out (any pointer may be NULL): voxel_off (n_voxels + 1),
+ * obs_scan (n_obs), agg (n_obs x 10), level (n_voxels), index (n_voxels x 3). */
+ba_status ba_voxels_read(const ba_voxels* v, int64_t* voxel_off, int32_t* obs_scan, double* agg, int32_t* level,
+                         int32_t* index, int32_t mem_kind);
+int64_t ba_voxels_kernel_launches(const ba_voxels* v);
+const char* ba_voxelize_last_error(void);
+void ba_voxels_destroy(ba_voxels* v);
+
 /* Check of the device-side wait bound (the paper has no counterpart).  The
  * staged scan pass of the mixed path waits on mbarriers for its bulk copies,
  * and every such wait gives up after a bounded number of polls, sets a flag

@@ -16,7 +16,7 @@ from . import _lib
 from ._lib import (BA_AGG_CENTRED, BA_AGG_RAW_SUMS, BA_FP64, BA_HESS_EXACT, BA_HESS_GAUSS_NEWTON,
                    BA_MEM_DEVICE, BA_MEM_HOST, BA_MIXED, BaConfig, BaStats)
 
-__all__ = ["BAError", "Batch", "BundleAdjuster", "ba_config_default", "ba_create", "ba_load_observations",
+__all__ = ["BAError", "Batch", "BundleAdjuster", "voxelize", "ba_config_default", "ba_create", "ba_load_observations",
            "ba_load_points", "ba_iterate", "ba_solve", "ba_poses", "ba_cost", "ba_get_stats", "ba_set_state",
            "ba_planes", "ba_gradient", "ba_kernel_launches", "ba_destroy", "ba_last_error",
            "ba_aggregate_points", "ba_profile_enable", "ba_profile_read", "BA_FP64", "BA_MIXED", "BA_HESS_EXACT", "BA_HESS_GAUSS_NEWTON",
@@ -292,6 +292,55 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def voxelize(scan_point_off, points, poses, voxel_size, levels=1, tau=0.0, min_obs=1, device=0, stream=None,
+             out="host"):
+    """Raw scans -> voxel-major observations (ba_voxelize, include/ba.h).
+
+    Points of scan j are points[scan_point_off[j]:scan_point_off[j+1]] (scan
+    frame); inputs are all numpy (host) or all CUDA tensors (device).  Returns
+    a dict voxel_off, obs_scan, agg (centred), level, index, as numpy arrays
+    (out="host") or CUDA tensors (out="device"), plus the kernel launch count."""
+    spo, pts, T = _Arg(scan_point_off, np.int64), _Arg(points, np.float64), _Arg(poses, np.float64)
+    mk = _mem_kind(spo, pts, T)
+    cfg = _lib.BaVoxelizeConfig()
+    _lib.lib().ba_voxelize_config_default(ctypes.byref(cfg))
+    cfg.voxel_size, cfg.levels, cfg.tau, cfg.min_obs, cfg.device = float(voxel_size), int(levels), float(tau), \
+        int(min_obs), int(device)
+    if stream is not None:
+        cfg.cuda_stream = stream if isinstance(stream, int) else stream.cuda_stream
+    v = ctypes.c_void_p()
+    status = _lib.lib().ba_voxelize(ctypes.byref(cfg), spo.shape[0] - 1, spo.ptr, pts.ptr, T.ptr, mk, ctypes.byref(v))
+    if status != _lib.BA_OK:
+        raise BAError(status, (_lib.lib().ba_voxelize_last_error() or b"").decode())
+    try:
+        nv, no = ctypes.c_int64(), ctypes.c_int64()
+        _lib.lib().ba_voxels_size(v, ctypes.byref(nv), ctypes.byref(no))
+        nv, no = nv.value, no.value
+        if out == "device":
+            import torch
+            dev = torch.device("cuda", int(device))
+            res = {"voxel_off": torch.empty(nv + 1, dtype=torch.int64, device=dev),
+                   "obs_scan": torch.empty(no, dtype=torch.int32, device=dev),
+                   "agg": torch.empty((no, 10), dtype=torch.float64, device=dev),
+                   "level": torch.empty(nv, dtype=torch.int32, device=dev),
+                   "index": torch.empty((nv, 3), dtype=torch.int32, device=dev)}
+            ptr = lambda t: t.data_ptr() if t.numel() else None
+            kind = BA_MEM_DEVICE
+        else:
+            res = {"voxel_off": np.empty(nv + 1, np.int64), "obs_scan": np.empty(no, np.int32),
+                   "agg": np.empty((no, 10)), "level": np.empty(nv, np.int32), "index": np.empty((nv, 3), np.int32)}
+            ptr = lambda a: a.ctypes.data if a.size else None
+            kind = BA_MEM_HOST
+        status = _lib.lib().ba_voxels_read(v, ptr(res["voxel_off"]), ptr(res["obs_scan"]), ptr(res["agg"]),
+                                           ptr(res["level"]), ptr(res["index"]), kind)
+        if status != _lib.BA_OK:
+            raise BAError(status, (_lib.lib().ba_voxelize_last_error() or b"").decode())
+        res["launches"] = int(_lib.lib().ba_voxels_kernel_launches(v))
+        return res
+    finally:
+        _lib.lib().ba_voxels_destroy(v)
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)

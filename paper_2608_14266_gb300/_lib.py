@@ -42,6 +42,11 @@ class BaStats(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_ if name != "reserved"}
 
 
+class BaVoxelizeConfig(ctypes.Structure):
+    _fields_ = [("voxel_size", _D), ("levels", _I32), ("tau", _D), ("min_obs", _I32), ("device", _I32),
+                ("cuda_stream", _P)]
+
+
 class BaJobDesc(ctypes.Structure):
     _fields_ = [("n_scans", _I32), ("n_voxels", _I64), ("n_obs", _I64), ("voxel_offsets", _P), ("obs_scan", _P),
                 ("agg", _P), ("agg_form", _I32), ("poses", _P), ("mem_kind", _I32)]
@@ -91,6 +96,13 @@ _SIGNATURES = {
     "ba_check_bounded_wait": (_I32, [_I32, _I32]),
     "ba_release_cached_memory": (_I32, [_I32]),
     "ba_check_conversions": (_I32, [_I32, _I64, ctypes.c_uint64, _P]),
+    "ba_voxelize_config_default": (None, [_P]),
+    "ba_voxelize": (_I32, [_P, _I32, _P, _P, _P, _I32, _P]),
+    "ba_voxels_size": (_I32, [_P, _P, _P]),
+    "ba_voxels_read": (_I32, [_P, _P, _P, _P, _P, _P, _I32]),
+    "ba_voxels_kernel_launches": (_I64, [_P]),
+    "ba_voxelize_last_error": (ctypes.c_char_p, []),
+    "ba_voxels_destroy": (None, [_P]),
     "ba_device_bytes": (_I64, [_P]),
     "ba_estimate_bytes": (_I64, [_I32, _I32, _I64, _I64, _P]),
 }

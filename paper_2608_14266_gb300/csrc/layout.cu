@@ -109,7 +109,8 @@ constexpr int kRadixItems = 16;  // chunks per tile
 constexpr int64_t kRadixTile = (int64_t)kRadixBlock * kRadixItems;
 constexpr int kRadixWarps = kRadixBlock / 32;
 
-__global__ void __launch_bounds__(kRadixBlock) radix_hist_kernel(const uint32_t* keys, int64_t n, int shift,
+template <typename K>
+__global__ void __launch_bounds__(kRadixBlock) radix_hist_kernel(const K* keys, int64_t n, int shift,
                                                                  int64_t* hist, int64_t n_tiles) {
   __shared__ int cnt[256];
   cnt[threadIdx.x] = 0;
@@ -117,14 +118,15 @@ __global__ void __launch_bounds__(kRadixBlock) radix_hist_kernel(const uint32_t*
   const int64_t base = (int64_t)blockIdx.x * kRadixTile;
   for (int c = 0; c < kRadixItems; ++c) {
     const int64_t i = base + (int64_t)c * kRadixBlock + threadIdx.x;
-    if (i < n) atomicAdd(&cnt[(keys[i] >> shift) & 255u], 1);
+    if (i < n) atomicAdd(&cnt[(unsigned)(keys[i] >> shift) & 255u], 1);
   }
   __syncthreads();
   hist[(int64_t)threadIdx.x * n_tiles + blockIdx.x] = cnt[threadIdx.x];
 }
 
-__global__ void __launch_bounds__(kRadixBlock) radix_scatter_kernel(const uint32_t* keys_in, const uint32_t* vals_in,
-                                                                    uint32_t* keys_out, uint32_t* vals_out, int64_t n,
+template <typename K>
+__global__ void __launch_bounds__(kRadixBlock) radix_scatter_kernel(const K* keys_in, const uint32_t* vals_in,
+                                                                    K* keys_out, uint32_t* vals_out, int64_t n,
                                                                     int shift, const int64_t* hist, int64_t n_tiles) {
   __shared__ int64_t start[256];      // global position of this tile's next element per digit
   __shared__ int wcnt[kRadixWarps][256];
@@ -136,12 +138,13 @@ __global__ void __launch_bounds__(kRadixBlock) radix_scatter_kernel(const uint32
     __syncthreads();
     const int64_t i = base + (int64_t)c * kRadixBlock + tid;
     const bool valid = i < n;
-    uint32_t key = 0, val = 0;
+    K key = 0;
+    uint32_t val = 0;
     unsigned d = 256u;  // sentinel digit for invalid lanes
     if (valid) {
       key = keys_in[i];
       val = vals_in[i];
-      d = (key >> shift) & 255u;
+      d = (unsigned)(key >> shift) & 255u;
     }
     const unsigned same = __match_any_sync(0xffffffffu, d);
     const int rank = __popc(same & ((1u << lane) - 1u));
@@ -176,34 +179,46 @@ int64_t radix_scratch_count(int64_t n) {
   return h + scan_scratch_count(h);
 }
 
-cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* tmp_keys, uint32_t* tmp_vals, int64_t n,
-                             int bits, int64_t* scratch, cudaStream_t stream, int64_t* launches) {
+template <typename K>
+static cudaError_t radix_sort_pairs_t(K* keys, uint32_t* vals, K* tmp_keys, uint32_t* tmp_vals, int64_t n, int bits,
+                                      int64_t* scratch, cudaStream_t stream, int64_t* launches) {
   if (n <= 1 || bits <= 0) return cudaSuccess;
   const int64_t tiles = (n + kRadixTile - 1) / kRadixTile;
   int64_t* hist = scratch;
   int64_t* scan_scratch = scratch + 256 * tiles;
-  uint32_t *ki = keys, *vi = vals, *ko = tmp_keys, *vo = tmp_vals;
+  K *ki = keys, *ko = tmp_keys;
+  uint32_t *vi = vals, *vo = tmp_vals;
   const int passes = (bits + 7) / 8;
   for (int p = 0; p < passes; ++p) {
-    radix_hist_kernel<<<(unsigned)tiles, kRadixBlock, 0, stream>>>(ki, n, 8 * p, hist, tiles);
+    radix_hist_kernel<K><<<(unsigned)tiles, kRadixBlock, 0, stream>>>(ki, n, 8 * p, hist, tiles);
     ++*launches;
     RETURN_IF(cudaGetLastError());
     RETURN_IF(exclusive_scan_i64(hist, 256 * tiles, scan_scratch, stream, launches));
-    radix_scatter_kernel<<<(unsigned)tiles, kRadixBlock, 0, stream>>>(ki, vi, ko, vo, n, 8 * p, hist, tiles);
+    radix_scatter_kernel<K><<<(unsigned)tiles, kRadixBlock, 0, stream>>>(ki, vi, ko, vo, n, 8 * p, hist, tiles);
     ++*launches;
     RETURN_IF(cudaGetLastError());
-    uint32_t* t = ki;
+    K* t = ki;
     ki = ko;
     ko = t;
-    t = vi;
+    uint32_t* u = vi;
     vi = vo;
-    vo = t;
+    vo = u;
   }
   if (ki != keys) {
-    RETURN_IF(cudaMemcpyAsync(keys, ki, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, stream));
+    RETURN_IF(cudaMemcpyAsync(keys, ki, sizeof(K) * n, cudaMemcpyDeviceToDevice, stream));
     RETURN_IF(cudaMemcpyAsync(vals, vi, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, stream));
   }
   return cudaSuccess;
+}
+
+cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* tmp_keys, uint32_t* tmp_vals, int64_t n,
+                             int bits, int64_t* scratch, cudaStream_t stream, int64_t* launches) {
+  return radix_sort_pairs_t<uint32_t>(keys, vals, tmp_keys, tmp_vals, n, bits, scratch, stream, launches);
+}
+
+cudaError_t radix_sort_pairs64(uint64_t* keys, uint32_t* vals, uint64_t* tmp_keys, uint32_t* tmp_vals, int64_t n,
+                               int bits, int64_t* scratch, cudaStream_t stream, int64_t* launches) {
+  return radix_sort_pairs_t<uint64_t>(keys, vals, tmp_keys, tmp_vals, n, bits, scratch, stream, launches);
 }
 
 // ============================================================================
