@@ -58,7 +58,7 @@ def _args():
     ap.add_argument("--steps", type=int, default=3000, help="timed LM iterations per rank")
     ap.add_argument("--warmup", type=int, default=30, help="untimed warm-up iterations")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["city", "mid", "tiny", "batched", "served"], default="city")
+    ap.add_argument("--workload", choices=["city", "mid", "tiny", "batched", "served", "voxelize"], default="city")
     ap.add_argument("--jobs", type=int, default=256, help="jobs of the batched / served workloads")
     ap.add_argument("--fp64-jobs", type=int, default=256, help="of which solved on the plain FP64 path too")
     ap.add_argument("--rate", type=float, default=200.0, help="served: Poisson arrival rate (jobs/s)")
@@ -694,10 +694,103 @@ def run_served(args):
     print(json.dumps(line), flush=True)
 
 
+# preprocessing: algorithmic bytes per point of one ba_voxelize call with
+# levels > 1 dominated by level 1: read the point (24 B) and write its key,
+# index and scan (16 B); 8 passes of the stable radix sort over 64-bit keys
+# with 32-bit values (read and write 12 B each); the head flags and scan of
+# the sorted keys (8 B key + 8 B flag written and read); the cluster pass
+# (sorted index 4 B, point 24 B)
+VOXELIZE_BYTES_PER_POINT = 24 + 16 + 8 * 24 + 32 + 28
+
+
+def run_voxelize(args):
+    """Raw scans -> voxels on the device (ba_voxelize: L1 voxelisation, bottom-
+    up levels, selection) for the 1,000-scan workload's ~120M points."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2608_14266_gb300 as mm
+    import scenegen
+    torch.cuda.set_device(0)
+    s = scenegen.make_scene(scenegen.config("mid"))
+    n_obs, npo = s.n_obs, s.params.pts_per_obs
+    P = torch.empty((n_obs * npo, 3), dtype=torch.float64, device="cuda")
+    s.points_device(0, n_obs, P)
+    order = torch.from_numpy(np.argsort(s.obs_scan, kind="stable")).cuda()
+    P = P.view(n_obs, npo, 3)[order].reshape(-1, 3).contiguous()
+    counts = np.bincount(s.obs_scan, minlength=s.n_scans) * npo
+    spo_h = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    spo, poses = torch.from_numpy(spo_h).cuda(), torch.from_numpy(s.pose_init).cuda()
+    n_pts = int(spo_h[-1])
+    cfg = dict(voxel_size=0.5, levels=3, tau=0.1, min_obs=2)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        mm.voxelize(spo, P, poses, stream=stream, out="device", **cfg)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    steps = max(1, min(args.steps, 10))
+    clocks = ClockSampler(_gpu_id(torch, 0))
+    time.sleep(0.3)
+    t_wall0 = time.time()
+    e0.record(stream)
+    for _ in range(steps):
+        v = mm.voxelize(spo, P, poses, stream=stream, out="device", **cfg)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_wall1 = time.time()
+    clk = clocks.stop(t_wall0, t_wall1)
+    ms = e0.elapsed_time(e1) / steps
+    # end to end: host inputs (pinned) through the same call, results read back to host
+    spo_p, P_p, T_p = spo.cpu().pin_memory(), P.cpu().pin_memory(), poses.cpu().pin_memory()
+    host = lambda t: t.numpy()
+    r = mm.voxelize(host(spo_p), host(P_p), host(T_p), **cfg)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        r = mm.voxelize(host(spo_p), host(P_p), host(T_p), **cfg)
+    e2e_s = (time.perf_counter() - t0) / steps
+    h2d = spo_p.numel() * 8 + P_p.numel() * 8 + T_p.numel() * 8
+    d2h = sum(a.nbytes for k, a in r.items() if k != "launches")
+    peak, src = hbm_peak()
+    achieved = VOXELIZE_BYTES_PER_POINT * n_pts / (ms / 1000.0) / 1e9
+    # oracle on the first scans' points (bounded sample), scaled by points
+    import oracle
+    k = 1
+    while k < s.n_scans and spo_h[k] < 25_000_000:
+        k += 1
+    Ph = P[: int(spo_h[k])].cpu().numpy()
+    t0 = time.perf_counter()
+    oracle.voxelize(spo_h[: k + 1], Ph, s.pose_init[:k], **cfg)
+    cpu_s = time.perf_counter() - t0
+    line = {
+        "metric": "preprocessing points/s (L1 voxelisation, 3 levels, selection)", "workload": "voxelize",
+        "value": n_pts / (ms / 1000.0), "unit": "points/s", "n_gpus": 1, "steps": steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "points": n_pts, "voxels_out": int(v["level"].numel()),
+        "obs_out": int(v["obs_scan"].numel()), "gpu_launches": int(v["launches"]) * steps, "clocks": clk,
+        "e2e": {"value": n_pts / e2e_s, "unit": "points/s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_s * 1000.0},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "kernel": "whole call (sort-dominated)", "peak_source": src,
+                     "bytes_per_point": VOXELIZE_BYTES_PER_POINT},
+        "cpu_baseline": {"value": int(spo_h[k]) / cpu_s, "unit": "points/s", "cores": 1, "kind": "oracle",
+                         "sample": f"points of the first {k} scans ({int(spo_h[k])} points)"},
+        "config": {"workload": f"raw scans of the {s.n_scans}-scan scene ({n_pts} points) -> voxels",
+                   "scans": s.n_scans, "voxel_size_m": cfg["voxel_size"], "levels": cfg["levels"],
+                   "tau": cfg["tau"], "min_obs": cfg["min_obs"],
+                   "inputs": "points resident on the device, larger than L2"},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = _args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "voxelize":
+        run_voxelize(args)
     elif args.workload == "batched":
         run_batched(args)
     elif args.workload == "served":

@@ -325,11 +325,14 @@ ba_status ba_aggregate_points(int64_t n_obs, const int64_t* point_offsets, const
 /* ---- Preprocessing: raw scans -> observations (Sec. IV-B, Algorithm 1) -----
  * L1 voxelisation (Eq. 4): every point p of scan j goes to world coordinates
  * w = R_j p + t_j (each axis fma(R_a0, p0, fma(R_a1, p1, fma(R_a2, p2,
- * t_a))), the index floor(w / d) per axis; the points of one scan in one
- * voxel form one centred cluster (Eq. 2; mean, then scatter about it, in
- * point order).  Bottom-up levels (Eq. 5): the level-k index of a level-(k-1)
- * cluster is floor(index / 2) per axis, and the clusters with the same
- * (level-k index, scan) are merged; level k has voxel size 2^(k-1) d.
+ * t_a))), the index floor(w / d) per axis, the floor of the correctly
+ * rounded quotient; the points of one scan in one voxel form one centred
+ * cluster (Eq. 2), summed in point order as shifted sums (deviations from
+ * the run's first point) in fixed chunks, so results are deterministic and
+ * agree with the mean-then-scatter definition to rounding.  Bottom-up levels
+ * (Eq. 5): the level-k index of a level-(k-1) cluster is floor(index / 2)
+ * per axis, and the clusters with the same (level-k index, scan) are merged
+ * in scan-then-child order; level k has voxel size 2^(k-1) d.
  * Selection (Algorithm 1, Selection): a voxel is kept if it has at least
  * min_obs observations and, for tau > 0, the smallest eigenvalue of the
  * covariance of its points at the given poses is below tau times the second

@@ -563,6 +563,10 @@ ba_status check_sizes(ba_handle* h, int32_t n_scans, int64_t n_voxels, int64_t n
 
 }  // namespace
 
+namespace mmba {
+cudaMemPool_t library_pool(int device) { return lib_pool(device); }
+}  // namespace mmba
+
 extern "C" {
 
 void ba_config_default(ba_config* cfg) {

@@ -50,6 +50,10 @@ cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* tmp_keys,
 // The same for 64-bit keys (bits up to 64).
 cudaError_t radix_sort_pairs64(uint64_t* keys, uint32_t* vals, uint64_t* tmp_keys, uint32_t* tmp_vals, int64_t n,
                                int bits, int64_t* scratch, cudaStream_t stream, int64_t* launches);
+// The library's stream-ordered memory pool of a device (freed memory stays
+// mapped for reuse); NULL if it cannot be created.
+cudaMemPool_t library_pool(int device);
+
 // Exclusive prefix sum of n int64 values in place; scratch of scan_scratch_count(n).
 int64_t scan_scratch_count(int64_t n);
 cudaError_t exclusive_scan_i64(int64_t* data, int64_t n, int64_t* scratch, cudaStream_t stream, int64_t* launches);

@@ -5,11 +5,15 @@
 //
 // Order of the output (shared with the CPU reference of the tests): voxels by
 // level, then by integer index (x, y, z); the observations of a voxel by scan.
-// The arithmetic that decides indices and forms clusters uses explicitly
-// rounded operations (no contraction), so indices and clusters do not depend
-// on the compiler's choices.
+// Indices are exactly floor(RN(w / d)) with w formed by explicit fma, so the
+// integer structure does not depend on the compiler's choices.  GB300 runs
+// FP64 on a narrow pipe: divisions are replaced by a multiply and an exact
+// check, cluster sums are one pass over fixed chunks of sorted points with
+// no divergence between threads, and the planarity test runs in FP32 unless
+// it is too close to call.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <climits>
 #include <cmath>
 #include <cstdarg>
@@ -25,20 +29,34 @@ using namespace mmba;
 
 namespace {
 
-constexpr long long kKeyRange = 1ll << 20;  // indices in [-2^20, 2^20) per axis
-constexpr int kKeyBits = 63;                // 21 bits per axis
+constexpr int kKeyRange = 1 << 20;  // indices in [-2^20, 2^20) per axis
 
-__device__ __forceinline__ uint64_t pack_key(long long ix, long long iy, long long iz) {
+// Voxel keys: the index of each axis offset by its smallest value at this
+// level and packed x | y | z with just the bits the level's index range needs,
+// so that sorting keys sorts voxels by (x, y, z) and the radix sort runs as
+// few digit passes as possible.  Level k+1 (Eq. 5) halves the range per axis.
+struct KeyPack {
+  int lo[3];  // smallest index per axis
+  int w[3];   // bits per axis
+};
+
+__host__ __device__ __forceinline__ uint64_t pack_key(const KeyPack& p, int ix, int iy, int iz) {
+  return ((uint64_t)(unsigned)(ix - p.lo[0]) << (p.w[1] + p.w[2])) | ((uint64_t)(unsigned)(iy - p.lo[1]) << p.w[2]) |
+         (uint64_t)(unsigned)(iz - p.lo[2]);
+}
+
+__host__ __device__ __forceinline__ void unpack_key(const KeyPack& p, uint64_t k, int* i) {
+  i[2] = (int)(k & ((1ull << p.w[2]) - 1ull)) + p.lo[2];
+  i[1] = (int)((k >> p.w[2]) & ((1ull << p.w[1]) - 1ull)) + p.lo[1];
+  i[0] = (int)(k >> (p.w[1] + p.w[2])) + p.lo[0];
+}
+
+// the raw level-1 key before the index range is known: 21 bits per axis
+__device__ __forceinline__ uint64_t raw_key(int ix, int iy, int iz) {
   return ((uint64_t)(ix + kKeyRange) << 42) | ((uint64_t)(iy + kKeyRange) << 21) | (uint64_t)(iz + kKeyRange);
 }
 
-__device__ __forceinline__ void unpack_key(uint64_t k, long long* i) {
-  i[0] = (long long)((k >> 42) & 0x1fffffull) - kKeyRange;
-  i[1] = (long long)((k >> 21) & 0x1fffffull) - kKeyRange;
-  i[2] = (long long)(k & 0x1fffffull) - kKeyRange;
-}
-
-__device__ __forceinline__ long long half_floor(long long i) { return i >= 0 ? i / 2 : -((-i + 1) / 2); }
+__host__ __device__ __forceinline__ int half_floor(int i) { return i >= 0 ? i / 2 : -((-i + 1) / 2); }
 
 // scan offsets: start at 0, never decrease, end at n (first violation, or
 // LLONG_MAX); poses finite
@@ -57,142 +75,357 @@ __global__ void check_inputs_kernel(int32_t n_scans, const int64_t* spo, int64_t
   if (!fin) atomicMin(bad_pose, (long long)j);
 }
 
-// L1 (Eq. 4): world point w = R p + t, index floor(w / d), 64-bit key
-__global__ void l1_keys_kernel(int32_t n_scans, const int64_t* spo, const double* pts, const double* poses, double d,
-                               int64_t n, uint64_t* keys, uint32_t* vals, int32_t* pscan, long long* bad) {
+// floor(w / d) of Eq. 4, the floor of the correctly rounded quotient, from
+// q, an approximation of w / d within 2^-29 (the pose pre-divided by d).
+// Adding 1.5 * 2^32 rounding down leaves q rounded down to a multiple of
+// 2^-20 (the spacing of doubles in [2^32, 2^33)), read back as the integer
+// z = floor(q * 2^20): z >> 20 = floor(q), and when the low 20 bits show q at
+// least 2^-20 from an integer, w / d and its rounding have that floor too.
+// Otherwise (and for |q| >= 2^21 or NaN) returns false: the caller divides.
+__device__ __forceinline__ bool floor_fast(double q, int* k, bool* ok) {
+  const unsigned ex = (unsigned)((unsigned long long)__double_as_longlong(q) >> 52) & 0x7ffu;
+  if (ex >= 1023u + 21u) return false;
+  const double M = 6442450944.0;  // 1.5 * 2^32
+  const long long z = __double_as_longlong(__dadd_rd(q, M)) - __double_as_longlong(M);
+  const long long fr = z & 0xfffffll;
+  if (fr == 0 || fr == 0xfffffll) return false;
+  const long long f = z >> 20;
+  *ok = f >= -(long long)kKeyRange && f < (long long)kKeyRange;
+  *k = *ok ? (int)f : 0;
+  return true;
+}
+
+// poses divided by the voxel size, for the fast index path
+__global__ void scaled_poses_kernel(int32_t n_scans, const double* poses, double rd, double* out) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  int lo = 0, hi = n_scans;  // the scan of point i: the last j with spo[j] <= i
-  while (hi - lo > 1) {
-    const int mid = (lo + hi) >> 1;
-    if (spo[mid] <= i)
-      lo = mid;
-    else
-      hi = mid;
+  if (i < 12 * (int64_t)n_scans) out[i] = poses[i] * rd;
+}
+
+// L1 (Eq. 4): world point w = R p + t, index floor(w / d), raw key; the
+// index bounding box (one atomic per block) and the first point whose index
+// leaves the key range.  Grid-stride over points.
+__global__ void __launch_bounds__(256) l1_keys_kernel(int32_t n_scans, const int64_t* spo, const double* pts,
+                                                      const double* poses, const double* sposes, double d, int64_t n,
+                                                      uint64_t* keys, uint32_t* vals, int32_t* pscan, long long* bad,
+                                                      int* bbox) {
+  int mn[3] = {INT_MAX, INT_MAX, INT_MAX}, mx[3] = {INT_MIN, INT_MIN, INT_MIN};
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    int lo = 0, hi = n_scans;  // the scan of point i: the last j with spo[j] <= i
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (spo[mid] <= i)
+        lo = mid;
+      else
+        hi = mid;
+    }
+    const double* S = sposes + 12 * (int64_t)lo;
+    const double p0 = pts[3 * i], p1 = pts[3 * i + 1], p2 = pts[3 * i + 2];
+    int ix[3];
+    bool ok = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      bool oka = false;
+      const double q = fma(S[3 * a], p0, fma(S[3 * a + 1], p1, fma(S[3 * a + 2], p2, S[9 + a])));
+      if (!floor_fast(q, &ix[a], &oka)) {
+        const double* T = poses + 12 * (int64_t)lo;
+        const double w = fma(T[3 * a], p0, fma(T[3 * a + 1], p1, fma(T[3 * a + 2], p2, T[9 + a])));
+        const double f = floor(__ddiv_rn(w, d));
+        oka = f >= -(double)kKeyRange && f < (double)kKeyRange;
+        ix[a] = oka ? (int)f : 0;
+      }
+      ok = ok && oka;
+    }
+    if (!ok) {
+      atomicMin(bad, (long long)i);
+    } else {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        mn[a] = min(mn[a], ix[a]);
+        mx[a] = max(mx[a], ix[a]);
+      }
+    }
+    keys[i] = ok ? raw_key(ix[0], ix[1], ix[2]) : 0;
+    vals[i] = (uint32_t)i;
+    pscan[i] = lo;
   }
-  const double* T = poses + 12 * (int64_t)lo;
-  const double* p = pts + 3 * i;
-  long long ix[3];
-  bool ok = true;
+  __shared__ int red[6][8];
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    const double w = fma(T[3 * a], p[0], fma(T[3 * a + 1], p[1], fma(T[3 * a + 2], p[2], T[9 + a])));
-    const double f = floor(__ddiv_rn(w, d));
-    ok = ok && f >= -(double)kKeyRange && f < (double)kKeyRange;
-    ix[a] = ok ? (long long)f : 0;
+    const int a0 = __reduce_min_sync(full, mn[a]), a1 = __reduce_max_sync(full, mx[a]);
+    if (lane == 0) {
+      red[a][w] = a0;
+      red[3 + a][w] = a1;
+    }
   }
-  if (!ok) atomicMin(bad, (long long)i);
-  keys[i] = pack_key(ix[0], ix[1], ix[2]);
-  vals[i] = (uint32_t)i;
-  pscan[i] = lo;
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    const int a = threadIdx.x;
+    int v = red[a][0];
+    for (int k = 1; k < (int)(blockDim.x >> 5); ++k) v = a < 3 ? min(v, red[a][k]) : max(v, red[a][k]);
+    if (a < 3 && v != INT_MAX) atomicMin(bbox + a, v);
+    if (a >= 3 && v != INT_MIN) atomicMax(bbox + a, v);
+  }
+}
+
+// raw keys -> level-1 keys packed to the index range
+template <typename K>
+__global__ void repack_kernel(int64_t n, const uint64_t* raw, KeyPack p, K* keys) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint64_t r = raw[i];
+  const int ix = (int)((r >> 42) & 0x1fffffull) - kKeyRange, iy = (int)((r >> 21) & 0x1fffffull) - kKeyRange,
+            iz = (int)(r & 0x1fffffull) - kKeyRange;
+  keys[i] = (K)pack_key(p, ix, iy, iz);
 }
 
 // 1 where a new (key, scan) group starts in sorted order
-__device__ __forceinline__ bool group_head(int64_t i, const uint64_t* keys, const uint32_t* vals, const int32_t* scan) {
+template <typename K>
+__device__ __forceinline__ bool group_head(int64_t i, const K* keys, const uint32_t* vals, const int32_t* scan) {
   return i == 0 || keys[i] != keys[i - 1] || scan[vals[i]] != scan[vals[i - 1]];
 }
 
-__global__ void heads_kernel(int64_t n, const uint64_t* keys, const uint32_t* vals, const int32_t* scan,
-                             int64_t* pos) {
+template <typename K>
+__global__ void heads_kernel(int64_t n, const K* keys, const uint32_t* vals, const int32_t* scan, int64_t* pos) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) pos[i] = group_head(i, keys, vals, scan) ? 1 : 0;
 }
 
 // after the exclusive scan: start of every group, and the end sentinel
-__global__ void starts_kernel(int64_t n, const uint64_t* keys, const uint32_t* vals, const int32_t* scan,
+template <typename K>
+__global__ void starts_kernel(int64_t n, const K* keys, const uint32_t* vals, const int32_t* scan,
                               const int64_t* pos, int64_t* start, int64_t n_groups) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n && group_head(i, keys, vals, scan)) start[pos[i]] = i;
   if (i == 0) start[n_groups] = n;
 }
 
-// L1 clusters (Eq. 2, centred): mean, then scatter about it, over the group's
-// points in point order
-__global__ void l1_clusters_kernel(int64_t n1, const int64_t* start, const uint32_t* vals, const uint64_t* keys,
-                                   const int32_t* pscan, const double* pts, double* c, uint64_t* ckey,
-                                   int32_t* cscan) {
-  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= n1) return;
-  const int64_t a = start[g], b = start[g + 1];
-  double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-  for (int64_t k = a; k < b; ++k) {
-    const double* p = pts + 3 * (int64_t)vals[k];
-    s0 = __dadd_rn(s0, p[0]);
-    s1 = __dadd_rn(s1, p[1]);
-    s2 = __dadd_rn(s2, p[2]);
+// ---- clusters (Eq. 2, centred) from shifted sums ----------------------------
+// A piece of a cluster: n points, shift s (its first point), a = sum (p - s),
+// b = sum (p - s)(p - s)^T (xx, xy, xz, yy, yz, zz).  Pieces merge exactly in
+// real arithmetic (shift to the first piece's s); the centred cluster is
+// m = s + a/n, S = b - a a^T / n.  The shift keeps every term small (a voxel's
+// extent), so no large cancellation occurs.
+struct Piece {
+  double n, s[3], a[3], b[6];
+};
+constexpr int kPieceDoubles = 13;
+
+// one more point of a piece holding cnt points (cnt = 0: p becomes the shift)
+__device__ __forceinline__ void piece_add(Piece& P, int cnt, double p0, double p1, double p2) {
+  if (cnt == 0) {
+    P.s[0] = p0;
+    P.s[1] = p1;
+    P.s[2] = p2;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) P.a[q] = 0.0;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) P.b[q] = 0.0;
+    return;
   }
-  const double n = (double)(b - a);
-  const double m0 = __ddiv_rn(s0, n), m1 = __ddiv_rn(s1, n), m2 = __ddiv_rn(s2, n);
-  double S[6] = {0, 0, 0, 0, 0, 0};
-  for (int64_t k = a; k < b; ++k) {
-    const double* p = pts + 3 * (int64_t)vals[k];
-    const double x = __dsub_rn(p[0], m0), y = __dsub_rn(p[1], m1), z = __dsub_rn(p[2], m2);
-    S[0] = __dadd_rn(S[0], __dmul_rn(x, x));
-    S[1] = __dadd_rn(S[1], __dmul_rn(x, y));
-    S[2] = __dadd_rn(S[2], __dmul_rn(x, z));
-    S[3] = __dadd_rn(S[3], __dmul_rn(y, y));
-    S[4] = __dadd_rn(S[4], __dmul_rn(y, z));
-    S[5] = __dadd_rn(S[5], __dmul_rn(z, z));
+  const double d[3] = {p0 - P.s[0], p1 - P.s[1], p2 - P.s[2]};
+  int k = 0;
+#pragma unroll
+  for (int x = 0; x < 3; ++x) {
+    P.a[x] += d[x];
+#pragma unroll
+    for (int y = x; y < 3; ++y) {
+      P.b[k] = fma(d[x], d[y], P.b[k]);
+      ++k;
+    }
   }
-  double* o = c + 10 * g;
-  for (int q = 0; q < 6; ++q) o[q] = S[q];
-  o[6] = m0;
-  o[7] = m1;
-  o[8] = m2;
-  o[9] = n;
-  ckey[g] = keys[a];
-  cscan[g] = pscan[vals[a]];
 }
 
-// Eq. 5: parent key of every cluster; sort keys (scan first, then parent)
-__global__ void parent_keys_kernel(int64_t nc, const uint64_t* ckey, const int32_t* cscan, uint64_t* pkey,
-                                   uint32_t* skey, uint32_t* vals) {
+__device__ __forceinline__ void piece_merge(Piece& A, const Piece& B) {
+  if (B.n == 0.0) return;
+  if (A.n == 0.0) {
+    A = B;
+    return;
+  }
+  const double dl[3] = {B.s[0] - A.s[0], B.s[1] - A.s[1], B.s[2] - A.s[2]};
+  int k = 0;
+#pragma unroll
+  for (int x = 0; x < 3; ++x) {
+    const double nd = B.n * dl[x];
+#pragma unroll
+    for (int y = x; y < 3; ++y) {
+      double t = fma(B.a[x], dl[y], B.b[k]);
+      t = fma(dl[x], B.a[y], t);
+      A.b[k] += fma(nd, dl[y], t);
+      ++k;
+    }
+  }
+#pragma unroll
+  for (int x = 0; x < 3; ++x) A.a[x] += fma(B.n, dl[x], B.a[x]);
+  A.n += B.n;
+}
+
+__device__ __forceinline__ void piece_store(double* o, const Piece& P) {
+  o[0] = P.n;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) o[1 + q] = P.s[q];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) o[4 + q] = P.a[q];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) o[7 + q] = P.b[q];
+}
+
+__device__ __forceinline__ Piece piece_load(const double* o) {
+  Piece P;
+  P.n = o[0];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) P.s[q] = o[1 + q];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) P.a[q] = o[4 + q];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) P.b[q] = o[7 + q];
+  return P;
+}
+
+// centred cluster record (S xx..zz, m, N)
+__device__ __forceinline__ void piece_finish(const Piece& P, double* c) {
+  const double r = __drcp_rn(P.n);
+  const double u[3] = {P.a[0] * r, P.a[1] * r, P.a[2] * r};
+  int k = 0;
+#pragma unroll
+  for (int x = 0; x < 3; ++x)
+#pragma unroll
+    for (int y = x; y < 3; ++y) {
+      c[k] = fma(-u[x], P.a[y], P.b[k]);
+      ++k;
+    }
+#pragma unroll
+  for (int q = 0; q < 3; ++q) c[6 + q] = P.s[q] + u[q];
+  c[9] = P.n;
+}
+
+constexpr int kChunk = 32;  // sorted points per thread
+
+// L1 clusters, pass 1: each thread sums a chunk of kChunk sorted points, one
+// piece per (key, scan) run (pos = exclusive count of run heads, so e is a
+// head iff pos[e + 1] != pos[e]).  The piece where a run starts goes to
+// head_piece[run], the piece of a run continuing from the previous chunk to
+// carry[chunk]; counts are stored as integers (no FP64 work in the
+// divergent stores).
+template <typename K>
+__global__ void l1_pieces_kernel(int64_t n, const K* keys, const uint32_t* vals, const int32_t* pscan,
+                                 const double* pts, const int64_t* pos, double* head_piece, double* carry,
+                                 uint64_t* ckey, int32_t* cscan) {
+  const int64_t ch = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t e0 = ch * kChunk;
+  if (e0 >= n) return;
+  const int64_t e1 = e0 + kChunk < n ? e0 + kChunk : n;
+  int64_t prev = pos[e0 + 1];
+  int64_t g = prev - 1;  // run of element e0
+  bool open = prev == pos[e0];
+  if (!open) {
+    ckey[g] = (uint64_t)keys[e0];
+    cscan[g] = pscan[vals[e0]];
+  }
+  Piece P;
+  int cnt = 0;
+  auto flush = [&]() {
+    P.n = __longlong_as_double((long long)cnt);
+    piece_store(open ? carry + kPieceDoubles * ch : head_piece + kPieceDoubles * g, P);
+  };
+  for (int64_t e = e0; e < e1; ++e) {
+    const int64_t pe = pos[e + 1];
+    const uint32_t v = vals[e];
+    if (pe != prev) {
+      flush();
+      ++g;
+      open = false;
+      cnt = 0;
+      prev = pe;
+      ckey[g] = (uint64_t)keys[e];
+      cscan[g] = pscan[v];
+    }
+    const double* p = pts + 3 * (int64_t)v;
+    piece_add(P, cnt, p[0], p[1], p[2]);
+    ++cnt;
+  }
+  flush();
+}
+
+__device__ __forceinline__ Piece piece_load_counted(const double* o) {
+  Piece P = piece_load(o);
+  P.n = (double)__double_as_longlong(P.n);
+  return P;
+}
+
+// L1 clusters, pass 2 (per run): the head piece merged in order with the
+// carries of the chunks the run covers, then the centred cluster
+__global__ void l1_finish_kernel(int64_t n1, const int64_t* start, const double* head_piece, const double* carry,
+                                 double* c) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n1) return;
+  Piece acc = piece_load_counted(head_piece + kPieceDoubles * g);
+  const int64_t cs = start[g] / kChunk, ce = (start[g + 1] - 1) / kChunk;
+  for (int64_t c2 = cs + 1; c2 <= ce; ++c2) piece_merge(acc, piece_load_counted(carry + kPieceDoubles * c2));
+  piece_finish(acc, c + 10 * g);
+}
+
+// Eq. 5: parent key of every cluster (level packing pc -> pp); sort keys
+// (scan first, then parent)
+__global__ void parent_keys_kernel(int64_t nc, const uint64_t* ckey, const int32_t* cscan, KeyPack pc, KeyPack pp,
+                                   uint64_t* pkey, uint32_t* skey, uint32_t* vals) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nc) return;
-  long long ix[3];
-  unpack_key(ckey[i], ix);
-  pkey[i] = pack_key(half_floor(ix[0]), half_floor(ix[1]), half_floor(ix[2]));
+  int ix[3];
+  unpack_key(pc, ckey[i], ix);
+  pkey[i] = pack_key(pp, half_floor(ix[0]), half_floor(ix[1]), half_floor(ix[2]));
   skey[i] = (uint32_t)cscan[i];
   vals[i] = (uint32_t)i;
 }
 
-__global__ void gather_keys_kernel(int64_t n, const uint64_t* src, const uint32_t* vals, uint64_t* dst) {
+template <typename K>
+__global__ void gather_keys_kernel(int64_t n, const uint64_t* src, const uint32_t* vals, K* dst) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) dst[i] = src[vals[i]];
+  if (i < n) dst[i] = (K)src[vals[i]];
 }
 
-// merge of two centred clusters, the operations in a fixed order:
-// N = Na + Nb, d = mb - ma, S = Sa + Sb + (Na Nb / N) d d^T, m = ma + (Nb / N) d
-__device__ __forceinline__ void merge_into(double* acc, const double* b) {
-  const double na = acc[9], nb = b[9], n = __dadd_rn(na, nb);
-  const double d[3] = {__dsub_rn(b[6], acc[6]), __dsub_rn(b[7], acc[7]), __dsub_rn(b[8], acc[8])};
-  const double f = __ddiv_rn(__dmul_rn(na, nb), n);
-  int idx = 0;
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = i; j < 3; ++j) {
-      acc[idx] = __dadd_rn(__dadd_rn(acc[idx], b[idx]), __dmul_rn(__dmul_rn(f, d[i]), d[j]));
-      ++idx;
-    }
-  const double w = __ddiv_rn(nb, n);
-#pragma unroll
-  for (int i = 0; i < 3; ++i) acc[6 + i] = __dadd_rn(acc[6 + i], __dmul_rn(w, d[i]));
-  acc[9] = n;
-}
-
-// level-k clusters: the children of each (parent, scan) group merged in order
+// level-k clusters: the children of each (parent, scan) group merged in
+// order, shifted to the first child's mean (a centred child has a = 0, so
+// its merge is b += S + N dl dl^T, a += N dl)
+template <typename K>
 __global__ void merge_kernel(int64_t np, const int64_t* start, const uint32_t* vals, const double* child,
-                             const uint64_t* pkeys_sorted, const int32_t* cscan, double* c, uint64_t* ckey,
+                             const K* pkeys_sorted, const int32_t* cscan, double* c, uint64_t* ckey,
                              int32_t* oscan) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= np) return;
   const int64_t a = start[g], b = start[g + 1];
-  double acc[10];
-  for (int q = 0; q < 10; ++q) acc[q] = child[10 * (int64_t)vals[a] + q];
-  for (int64_t k = a + 1; k < b; ++k) merge_into(acc, child + 10 * (int64_t)vals[k]);
-  for (int q = 0; q < 10; ++q) c[10 * g + q] = acc[q];
-  ckey[g] = pkeys_sorted[a];
+  Piece acc;
+  {
+    const double* ch = child + 10 * (int64_t)vals[a];
+    acc.n = ch[9];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      acc.s[q] = ch[6 + q];
+      acc.a[q] = 0.0;
+    }
+#pragma unroll
+    for (int q = 0; q < 6; ++q) acc.b[q] = ch[q];
+  }
+  for (int64_t k = a + 1; k < b; ++k) {
+    const double* ch = child + 10 * (int64_t)vals[k];
+    const double N = ch[9];
+    const double dl[3] = {ch[6] - acc.s[0], ch[7] - acc.s[1], ch[8] - acc.s[2]};
+    int q = 0;
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+      const double nd = N * dl[x];
+      acc.a[x] += nd;
+#pragma unroll
+      for (int y = x; y < 3; ++y) {
+        acc.b[q] += fma(nd, dl[y], ch[q]);
+        ++q;
+      }
+    }
+    acc.n += N;
+  }
+  piece_finish(acc, c + 10 * g);
+  ckey[g] = (uint64_t)pkeys_sorted[a];
   oscan[g] = cscan[vals[a]];
 }
 
@@ -209,13 +442,102 @@ __global__ void voxel_starts_kernel(int64_t nc, const uint64_t* ckey, const int6
   if (i == 0) vstart[nv] = nc;
 }
 
-// Selection (Algorithm 1): voxel covariance at the poses (Eq. 1-2, centred),
-// kept if it has min_obs observations and lambda0 < tau lambda1 (tau > 0).
-// keep[v] = observations kept (0 or the voxel's count); the partial sums use
-// the CPU reference's order of operations.
-__global__ void select_kernel(int64_t nv, const int64_t* vstart, const double* c, const int32_t* cscan,
-                              const double* poses, double tau, int32_t min_obs, int64_t* keep_obs,
-                              int64_t* keep_vox) {
+// Selection, per observation: world mean w = R m + t (FP64, with N) and the
+// rotated scatter R S R^T (FP32: it enters the planarity test only, whose
+// FP32 answer is checked against its error bound below)
+__global__ void world_terms_kernel(int64_t nc, const double* c, const int32_t* cscan, const double* poses,
+                                   double4_32a* wn, float4* rsr) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nc) return;
+  const double* cl = c + 10 * t;
+  const double* T = poses + 12 * (int64_t)cscan[t];
+  double w[3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) w[q] = fma(T[3 * q], cl[6], fma(T[3 * q + 1], cl[7], fma(T[3 * q + 2], cl[8], T[9 + q])));
+  wn[t] = make_double4_32a(w[0], w[1], w[2], cl[9]);
+  float R[9], S[6];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) R[q] = f64_to_f32(T[q]);
+#pragma unroll
+  for (int q = 0; q < 6; ++q) S[q] = f64_to_f32(cl[q]);
+  const float Sm[3][3] = {{S[0], S[1], S[2]}, {S[1], S[3], S[4]}, {S[2], S[4], S[5]}};
+  float RS[3][3];
+#pragma unroll
+  for (int x = 0; x < 3; ++x)
+#pragma unroll
+    for (int y = 0; y < 3; ++y) RS[x][y] = fmaf(R[3 * x], Sm[0][y], fmaf(R[3 * x + 1], Sm[1][y], R[3 * x + 2] * Sm[2][y]));
+  float o[8];
+  int k = 0;
+#pragma unroll
+  for (int x = 0; x < 3; ++x)
+#pragma unroll
+    for (int y = x; y < 3; ++y) o[k++] = fmaf(RS[x][0], R[3 * y], fmaf(RS[x][1], R[3 * y + 1], RS[x][2] * R[3 * y + 2]));
+  o[6] = o[7] = 0.0f;
+  rsr[2 * t] = make_float4(o[0], o[1], o[2], o[3]);
+  rsr[2 * t + 1] = make_float4(o[4], o[5], o[6], o[7]);
+}
+
+// FP64 covariance (times n) of a voxel's points at the poses, for the cases
+// the FP32 test cannot call
+__device__ __noinline__ void voxel_cov_f64(int64_t a, int64_t b, const double* c, const int32_t* cscan,
+                                           const double* poses, double* A) {
+  double n = 0.0, m[3] = {0, 0, 0};
+  for (int64_t t = a; t < b; ++t) {
+    const double* cl = c + 10 * t;
+    const double* T = poses + 12 * (int64_t)cscan[t];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const double w = fma(T[3 * q], cl[6], fma(T[3 * q + 1], cl[7], fma(T[3 * q + 2], cl[8], T[9 + q])));
+      m[q] = fma(cl[9], w, m[q]);
+    }
+    n += cl[9];
+  }
+#pragma unroll
+  for (int q = 0; q < 3; ++q) m[q] /= n;
+#pragma unroll
+  for (int q = 0; q < 6; ++q) A[q] = 0.0;
+  for (int64_t t = a; t < b; ++t) {
+    const double* cl = c + 10 * t;
+    const double* R = poses + 12 * (int64_t)cscan[t];
+    double d[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) d[q] = fma(R[3 * q], cl[6], fma(R[3 * q + 1], cl[7], fma(R[3 * q + 2], cl[8], R[9 + q]))) - m[q];
+    const double Sm[3][3] = {{cl[0], cl[1], cl[2]}, {cl[1], cl[3], cl[4]}, {cl[2], cl[4], cl[5]}};
+    double RS[3][3];
+#pragma unroll
+    for (int x = 0; x < 3; ++x)
+#pragma unroll
+      for (int y = 0; y < 3; ++y) RS[x][y] = fma(R[3 * x], Sm[0][y], fma(R[3 * x + 1], Sm[1][y], R[3 * x + 2] * Sm[2][y]));
+    int k = 0;
+#pragma unroll
+    for (int x = 0; x < 3; ++x)
+#pragma unroll
+      for (int y = x; y < 3; ++y) {
+        const double rsr = fma(RS[x][0], R[3 * y], fma(RS[x][1], R[3 * y + 1], RS[x][2] * R[3 * y + 2]));
+        A[k] += fma(cl[9] * d[x], d[y], rsr);
+        ++k;
+      }
+  }
+}
+
+__device__ __noinline__ bool planar_f64(const double* A, double tau) {
+  double lam[3], V[9];
+  eig3_sym(A, lam, V);
+  return lam[0] < tau * lam[1];
+}
+
+// Selection (Algorithm 1), per voxel: the covariance of its points at the
+// poses, n A = sum_t [R S R^T + N_t (w_t - m)(w_t - m)^T] (the scale n does
+// not change the test), kept if the voxel has min_obs observations and
+// lambda0 < tau lambda1 (tau > 0).  m and w_t - m in FP64, the sum and the
+// eigenvalues (Jacobi sweeps) in FP32: every term is positive semidefinite,
+// so the FP32 error is within (k + 16) 2^-22 tr(nA) for k observations; the
+// answer stands when lambda0 - tau lambda1 is farther than 3 times that (and
+// 1e-4 lambda2) from zero, else the FP64 covariance and sweeps decide.
+// keep_obs[v] = observations kept (0 or the voxel's count).
+__global__ void select_kernel(int64_t nv, const int64_t* vstart, const double4_32a* wn, const float4* rsr,
+                              const double* c, const int32_t* cscan, const double* poses, double tau,
+                              int32_t min_obs, int64_t* keep_obs, int64_t* keep_vox) {
   const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= nv) return;
   const int64_t a = vstart[v], b = vstart[v + 1];
@@ -223,50 +545,52 @@ __global__ void select_kernel(int64_t nv, const int64_t* vstart, const double* c
   if (keep && tau > 0.0) {
     double n = 0.0, m[3] = {0, 0, 0};
     for (int64_t t = a; t < b; ++t) {
-      const double* cl = c + 10 * t;
-      const double* T = poses + 12 * (int64_t)cscan[t];
-      for (int q = 0; q < 3; ++q) {
-        const double w = fma(T[3 * q], cl[6], fma(T[3 * q + 1], cl[7], fma(T[3 * q + 2], cl[8], T[9 + q])));
-        m[q] = __dadd_rn(m[q], __dmul_rn(cl[9], w));
-      }
-      n = __dadd_rn(n, cl[9]);
+      const double4_32a o = wn[t];
+      m[0] = fma(o.w, o.x, m[0]);
+      m[1] = fma(o.w, o.y, m[1]);
+      m[2] = fma(o.w, o.z, m[2]);
+      n += o.w;
     }
-    for (int q = 0; q < 3; ++q) m[q] = __ddiv_rn(m[q], n);
-    double A[6] = {0, 0, 0, 0, 0, 0};
+    const double r = __drcp_rn(n);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) m[q] *= r;
+    float A[6] = {0, 0, 0, 0, 0, 0};
     for (int64_t t = a; t < b; ++t) {
-      const double* cl = c + 10 * t;
-      const double* R = poses + 12 * (int64_t)cscan[t];
-      double dd[3];
-      for (int q = 0; q < 3; ++q) {
-        const double w = fma(R[3 * q], cl[6], fma(R[3 * q + 1], cl[7], fma(R[3 * q + 2], cl[8], R[9 + q])));
-        dd[q] = __dsub_rn(w, m[q]);
-      }
-      const double Sm[3][3] = {{cl[0], cl[1], cl[2]}, {cl[1], cl[3], cl[4]}, {cl[2], cl[4], cl[5]}};
-      double RS[3][3];
-      for (int x = 0; x < 3; ++x)
-        for (int y = 0; y < 3; ++y)
-          RS[x][y] = __dadd_rn(__dadd_rn(__dmul_rn(R[3 * x], Sm[0][y]), __dmul_rn(R[3 * x + 1], Sm[1][y])),
-                               __dmul_rn(R[3 * x + 2], Sm[2][y]));
-      int idx = 0;
-      for (int x = 0; x < 3; ++x)
+      const double4_32a o = wn[t];
+      const float4 r0 = rsr[2 * t], r1 = rsr[2 * t + 1];
+      const float M[6] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y};
+      const float d[3] = {f64_to_f32(o.x - m[0]), f64_to_f32(o.y - m[1]), f64_to_f32(o.z - m[2])};
+      const float N = f64_to_f32(o.w);
+      int k = 0;
+#pragma unroll
+      for (int x = 0; x < 3; ++x) {
+        const float nd = N * d[x];
+#pragma unroll
         for (int y = x; y < 3; ++y) {
-          const double rsr = __dadd_rn(__dadd_rn(__dmul_rn(RS[x][0], R[3 * y]), __dmul_rn(RS[x][1], R[3 * y + 1])),
-                                       __dmul_rn(RS[x][2], R[3 * y + 2]));
-          A[idx] = __dadd_rn(A[idx], __dadd_rn(rsr, __dmul_rn(__dmul_rn(cl[9], dd[x]), dd[y])));
-          ++idx;
+          A[k] += fmaf(nd, d[y], M[k]);
+          ++k;
         }
+      }
     }
-    for (int q = 0; q < 6; ++q) A[q] = __ddiv_rn(A[q], n);
-    double lam[3], V[9];
-    eig3_sym(A, lam, V);
-    keep = lam[0] < tau * lam[1];
+    float lf[3], vf[9];
+    eig3_sym_f(A, lf, vf);
+    const float margin = lf[0] - (float)tau * lf[1];
+    const float tr = fabsf(A[0]) + fabsf(A[3]) + fabsf(A[5]);
+    const float err = 3.0f * (float)(b - a + 16) * 2.384185791e-7f * tr;  // 3 (k + 16) 2^-22 tr
+    if (fabsf(margin) > fmaxf(err, 1e-4f * fabsf(lf[2]))) {
+      keep = margin < 0.0f;
+    } else {
+      double Ad[6];
+      voxel_cov_f64(a, b, c, cscan, poses, Ad);
+      keep = planar_f64(Ad, tau);
+    }
   }
   keep_obs[v] = keep ? (b - a) : 0;
   keep_vox[v] = keep ? 1 : 0;
 }
 
 // kept voxels of a level written at their places in the output
-__global__ void emit_kernel(int64_t nv, const int64_t* vstart, const uint64_t* ckey, const int32_t* cscan,
+__global__ void emit_kernel(int64_t nv, const int64_t* vstart, const uint64_t* ckey, KeyPack pk, const int32_t* cscan,
                             const double* c, const int64_t* obs_pos, const int64_t* vox_pos, const int64_t* keep_vox,
                             int32_t level, int64_t v_base, int64_t o_base, int64_t* voxel_off, int32_t* obs_scan,
                             double* agg, int32_t* lev, int32_t* index) {
@@ -276,9 +600,9 @@ __global__ void emit_kernel(int64_t nv, const int64_t* vstart, const uint64_t* c
   const int64_t ov = v_base + vox_pos[v], oo = o_base + obs_pos[v];
   voxel_off[ov + 1] = oo + (b - a);
   lev[ov] = level;
-  long long ix[3];
-  unpack_key(ckey[a], ix);
-  for (int q = 0; q < 3; ++q) index[3 * ov + q] = (int32_t)ix[q];
+  int ix[3];
+  unpack_key(pk, ckey[a], ix);
+  for (int q = 0; q < 3; ++q) index[3 * ov + q] = ix[q];
   for (int64_t t = a; t < b; ++t) {
     obs_scan[oo + (t - a)] = cscan[t];
     for (int q = 0; q < 10; ++q) agg[10 * (oo + (t - a)) + q] = c[10 * t + q];
@@ -289,17 +613,20 @@ __global__ void emit_kernel(int64_t nv, const int64_t* vstart, const uint64_t* c
 
 thread_local std::string g_vox_error;
 
+// stream-ordered temporaries from the library pool, freed on scope exit
 struct Buf {
   std::vector<void*> ptrs;
   cudaStream_t s;
-  explicit Buf(cudaStream_t st) : s(st) {}
+  cudaMemPool_t pool;
+  Buf(cudaStream_t st, int device) : s(st), pool(library_pool(device)) {}
   ~Buf() {
     for (void* p : ptrs) cudaFreeAsync(p, s);
   }
   template <typename T>
   T* get(int64_t n) {
     void* p = nullptr;
-    if (cudaMallocAsync(&p, sizeof(T) * (size_t)(n > 0 ? n : 1), s) != cudaSuccess) {
+    const size_t bytes = sizeof(T) * (size_t)(n > 0 ? n : 1);
+    if ((pool ? cudaMallocFromPoolAsync(&p, bytes, pool, s) : cudaMallocAsync(&p, bytes, s)) != cudaSuccess) {
       cudaGetLastError();
       return nullptr;
     }
@@ -337,13 +664,16 @@ ba_status vfail(ba_status s, const char* fmt, ...) {
                                              : vfail(BA_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e_)); \
   } while (0)
 
-// group starts of a sorted (key, scan) sequence; returns the group count
-ba_status group_starts(int64_t n, const uint64_t* keys, const uint32_t* vals, const int32_t* scan, Buf& tmp,
-                       int64_t** start_out, int64_t* n_groups, cudaStream_t st, int64_t* launches) {
+// group starts of a sorted (key, scan) sequence: pos = exclusive count of
+// group heads (n + 1 entries), start (n_groups + 1 entries)
+template <typename K>
+ba_status group_starts(int64_t n, const K* keys, const uint32_t* vals, const int32_t* scan, Buf& tmp,
+                       int64_t** pos_out, int64_t** start_out, int64_t* n_groups, cudaStream_t st,
+                       int64_t* launches) {
   int64_t* pos = tmp.get<int64_t>(n + 1);
   int64_t* scr = tmp.get<int64_t>(scan_scratch_count(n + 1));
   if (!pos || !scr) return vfail(BA_ERR_OOM, "voxelize: out of device memory");
-  heads_kernel<<<blocks_for(n), 256, 0, st>>>(n, keys, vals, scan, pos);
+  heads_kernel<K><<<blocks_for(n), 256, 0, st>>>(n, keys, vals, scan, pos);
   VCK(cudaGetLastError(), "voxelize");
   VCK(cudaMemsetAsync(pos + n, 0, sizeof(int64_t), st), "voxelize");
   VCK(exclusive_scan_i64(pos, n + 1, scr, st, launches), "voxelize");
@@ -352,11 +682,115 @@ ba_status group_starts(int64_t n, const uint64_t* keys, const uint32_t* vals, co
   VCK(cudaStreamSynchronize(st), "voxelize");
   int64_t* start = tmp.get<int64_t>(ng + 1);
   if (!start) return vfail(BA_ERR_OOM, "voxelize: out of device memory");
-  starts_kernel<<<blocks_for(n), 256, 0, st>>>(n, keys, vals, scan, pos, start, ng);
+  starts_kernel<K><<<blocks_for(n), 256, 0, st>>>(n, keys, vals, scan, pos, start, ng);
   VCK(cudaGetLastError(), "voxelize");
   *launches += 2;
+  *pos_out = pos;
   *start_out = start;
   *n_groups = ng;
+  return BA_OK;
+}
+
+// packing of a level whose indices per axis lie in [lo, hi]
+KeyPack make_pack(const int* lo, const int* hi) {
+  KeyPack p;
+  for (int a = 0; a < 3; ++a) {
+    p.lo[a] = lo[a];
+    p.w[a] = bit_width_u((uint64_t)(hi[a] - lo[a]));
+  }
+  return p;
+}
+
+int pack_bits(const KeyPack& p) { return p.w[0] + p.w[1] + p.w[2]; }
+
+struct Level {
+  int64_t nc = 0, nv = 0;
+  double* c = nullptr;
+  uint64_t* key = nullptr;
+  int32_t* scan = nullptr;
+  int64_t* vstart = nullptr;
+  KeyPack pk{};
+  int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+};
+
+// level 1: raw keys -> packed keys, sort, (key, scan) runs, clusters
+template <typename K>
+ba_status level1(int64_t n, const uint64_t* raw, uint32_t* vals, const int32_t* pscan, const double* pts, Level& L,
+                 Buf& tmp, cudaStream_t st, int64_t* launches) {
+  K* keys = tmp.get<K>(n);
+  K* tkeys = tmp.get<K>(n);
+  uint32_t* tvals = tmp.get<uint32_t>(n);
+  int64_t* scr = tmp.get<int64_t>(radix_scratch_count(n));
+  if (!keys || !tkeys || !tvals || !scr) return vfail(BA_ERR_OOM, "voxelize: out of device memory");
+  repack_kernel<K><<<blocks_for(n), 256, 0, st>>>(n, raw, L.pk, keys);
+  ++*launches;
+  VCK(cudaGetLastError(), "voxelize keys");
+  // stable by key over points in scan order: groups ordered by (key, scan, point)
+  if (sizeof(K) == 4)
+    VCK(radix_sort_pairs((uint32_t*)keys, vals, (uint32_t*)tkeys, tvals, n, pack_bits(L.pk), scr, st, launches),
+        "voxelize sort");
+  else
+    VCK(radix_sort_pairs64((uint64_t*)keys, vals, (uint64_t*)tkeys, tvals, n, pack_bits(L.pk), scr, st, launches),
+        "voxelize sort");
+  int64_t *pos = nullptr, *start = nullptr;
+  int64_t n1 = 0;
+  ba_status s = group_starts<K>(n, keys, vals, pscan, tmp, &pos, &start, &n1, st, launches);
+  if (s != BA_OK) return s;
+  L.nc = n1;
+  L.c = tmp.get<double>(10 * n1);
+  L.key = tmp.get<uint64_t>(n1);
+  L.scan = tmp.get<int32_t>(n1);
+  const int64_t n_chunks = (n + kChunk - 1) / kChunk;
+  double* hp = tmp.get<double>(kPieceDoubles * n1);
+  double* cr = tmp.get<double>(kPieceDoubles * n_chunks);
+  if (!L.c || !L.key || !L.scan || !hp || !cr) return vfail(BA_ERR_OOM, "voxelize: out of device memory");
+  l1_pieces_kernel<K><<<blocks_for(n_chunks), 256, 0, st>>>(n, keys, vals, pscan, pts, pos, hp, cr, L.key, L.scan);
+  l1_finish_kernel<<<blocks_for(n1), 256, 0, st>>>(n1, start, hp, cr, L.c);
+  *launches += 2;
+  VCK(cudaGetLastError(), "voxelize clusters");
+  return BA_OK;
+}
+
+// level k+1 (Eq. 5) from level k: parents, sort (scan, then parent), merge
+template <typename K>
+ba_status level_up(const Level& ch, Level& P, int32_t n_scans, Buf& tmp, cudaStream_t st, int64_t* launches) {
+  const int64_t nc = ch.nc;
+  uint64_t* pkey = tmp.get<uint64_t>(nc);
+  K* k2 = tmp.get<K>(nc);
+  K* t2 = tmp.get<K>(nc);
+  uint32_t* skey = tmp.get<uint32_t>(nc);
+  uint32_t* tsk = tmp.get<uint32_t>(nc);
+  uint32_t* cv = tmp.get<uint32_t>(nc);
+  uint32_t* tcv = tmp.get<uint32_t>(nc);
+  int64_t* scr = tmp.get<int64_t>(radix_scratch_count(nc));
+  if (!pkey || !k2 || !t2 || !skey || !tsk || !cv || !tcv || !scr)
+    return vfail(BA_ERR_OOM, "voxelize: out of device memory");
+  parent_keys_kernel<<<blocks_for(nc), 256, 0, st>>>(nc, ch.key, ch.scan, ch.pk, P.pk, pkey, skey, cv);
+  ++*launches;
+  VCK(cudaGetLastError(), "voxelize levels");
+  VCK(radix_sort_pairs(skey, cv, tsk, tcv, nc, bit_width_u((uint64_t)(n_scans - 1)), scr, st, launches),
+      "voxelize sort");
+  gather_keys_kernel<K><<<blocks_for(nc), 256, 0, st>>>(nc, pkey, cv, k2);
+  ++*launches;
+  VCK(cudaGetLastError(), "voxelize levels");
+  if (sizeof(K) == 4)
+    VCK(radix_sort_pairs((uint32_t*)k2, cv, (uint32_t*)t2, tcv, nc, pack_bits(P.pk), scr, st, launches),
+        "voxelize sort");
+  else
+    VCK(radix_sort_pairs64((uint64_t*)k2, cv, (uint64_t*)t2, tcv, nc, pack_bits(P.pk), scr, st, launches),
+        "voxelize sort");
+  int64_t *pos = nullptr, *pst = nullptr;
+  int64_t np = 0;
+  ba_status s = group_starts<K>(nc, k2, cv, ch.scan, tmp, &pos, &pst, &np, st, launches);
+  if (s != BA_OK) return s;
+  P.nc = np;
+  P.c = tmp.get<double>(10 * np);
+  P.key = tmp.get<uint64_t>(np);
+  P.scan = tmp.get<int32_t>(np);
+  if (!P.c || !P.key || !P.scan) return vfail(BA_ERR_OOM, "voxelize: out of device memory");
+  merge_kernel<K><<<blocks_for(np), 256, 0, st>>>(np, pst, cv, ch.c, k2, ch.scan, P.c, P.key, P.scan);
+  ++*launches;
+  VCK(cudaGetLastError(), "voxelize merge");
   return BA_OK;
 }
 
@@ -371,6 +805,7 @@ struct ba_voxels {
   int32_t* level = nullptr;
   int32_t* index = nullptr;
   int64_t launches = 0;
+  bool pooled = false;  // arrays from the library pool (stream-ordered frees)
 };
 
 extern "C" {
@@ -406,7 +841,7 @@ ba_status ba_voxelize(const ba_voxelize_config* cfg, int32_t n_scans, const int6
     }
   } restore{prev};
   cudaStream_t st = (cudaStream_t)cfg->cuda_stream;
-  Buf tmp(st);
+  Buf tmp(st, cfg->device);
   int64_t launches = 0;
 
   // stage the inputs
@@ -450,83 +885,48 @@ ba_status ba_voxelize(const ba_voxelize_config* cfg, int32_t n_scans, const int6
                  (long long)n, res[0]);
   if (res[1] != LLONG_MAX) return vfail(BA_ERR_INVALID_ARG, "pose %lld is not finite", res[1]);
 
-  std::vector<int64_t*> lv_start;  // per level: voxel starts (device), counts
-  struct Level {
-    int64_t nc = 0, nv = 0;
-    double* c = nullptr;
-    uint64_t* key = nullptr;
-    int32_t* scan = nullptr;
-    int64_t* vstart = nullptr;
-  };
   std::vector<Level> lv(cfg->levels);
   if (n > 0) {
-    uint64_t* keys = tmp.get<uint64_t>(n);
-    uint64_t* tkeys = tmp.get<uint64_t>(n);
+    uint64_t* raw = tmp.get<uint64_t>(n);
     uint32_t* vals = tmp.get<uint32_t>(n);
-    uint32_t* tvals = tmp.get<uint32_t>(n);
     int32_t* pscan = tmp.get<int32_t>(n);
-    int64_t* scr = tmp.get<int64_t>(radix_scratch_count(n));
-    if (!keys || !tkeys || !vals || !tvals || !pscan || !scr) return vfail(BA_ERR_OOM, "voxelize: out of device memory");
-    l1_keys_kernel<<<blocks_for(n), 256, 0, st>>>(n_scans, spo, pts, T, cfg->voxel_size, n, keys, vals, pscan,
-                                                  bad + 2);
-    ++launches;
+    int* bbox = tmp.get<int>(6);
+    if (!raw || !vals || !pscan || !bbox) return vfail(BA_ERR_OOM, "voxelize: out of device memory");
+    const int bb_init[6] = {INT_MAX, INT_MAX, INT_MAX, INT_MIN, INT_MIN, INT_MIN};
+    VCK(cudaMemcpyAsync(bbox, bb_init, sizeof bb_init, cudaMemcpyHostToDevice, st), "voxelize");
+    double* sposes = tmp.get<double>(12 * (int64_t)n_scans);
+    if (!sposes) return vfail(BA_ERR_OOM, "voxelize: out of device memory");
+    scaled_poses_kernel<<<blocks_for(12 * (int64_t)n_scans), 256, 0, st>>>(n_scans, T, 1.0 / cfg->voxel_size, sposes);
+    int n_sm = 0;
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, cfg->device);
+    const int64_t key_blocks = std::min<int64_t>(blocks_for(n), (int64_t)(n_sm > 0 ? n_sm : 1) * 8);
+    l1_keys_kernel<<<(unsigned)key_blocks, 256, 0, st>>>(n_scans, spo, pts, T, sposes, cfg->voxel_size, n, raw, vals,
+                                                          pscan, bad + 2, bbox);
+    launches += 2;
     VCK(cudaGetLastError(), "voxelize keys");
+    int bb[6];
     VCK(cudaMemcpyAsync(res + 2, bad + 2, sizeof(long long), cudaMemcpyDeviceToHost, st), "voxelize");
+    VCK(cudaMemcpyAsync(bb, bbox, sizeof bb, cudaMemcpyDeviceToHost, st), "voxelize");
     VCK(cudaStreamSynchronize(st), "voxelize");
     if (res[2] != LLONG_MAX)
       return vfail(BA_ERR_CAPACITY, "point %lld lies outside the voxel index range [-2^20, 2^20) at this voxel size",
                    res[2]);
-    // stable by key over points in scan order: groups ordered by (key, scan, point)
-    VCK(radix_sort_pairs64(keys, vals, tkeys, tvals, n, kKeyBits, scr, st, &launches), "voxelize sort");
-    int64_t* start = nullptr;
-    int64_t n1 = 0;
-    ba_status s = group_starts(n, keys, vals, pscan, tmp, &start, &n1, st, &launches);
+    for (int k = 0; k < cfg->levels; ++k) {
+      Level& L = lv[k];
+      for (int a = 0; a < 3; ++a) {
+        L.lo[a] = k == 0 ? bb[a] : half_floor(lv[k - 1].lo[a]);
+        L.hi[a] = k == 0 ? bb[3 + a] : half_floor(lv[k - 1].hi[a]);
+      }
+      L.pk = make_pack(L.lo, L.hi);
+    }
+    ba_status s = pack_bits(lv[0].pk) <= 32 ? level1<uint32_t>(n, raw, vals, pscan, pts, lv[0], tmp, st, &launches)
+                                            : level1<uint64_t>(n, raw, vals, pscan, pts, lv[0], tmp, st, &launches);
     if (s != BA_OK) return s;
-    Level& L1 = lv[0];
-    L1.nc = n1;
-    L1.c = tmp.get<double>(10 * n1);
-    L1.key = tmp.get<uint64_t>(n1);
-    L1.scan = tmp.get<int32_t>(n1);
-    if (!L1.c || !L1.key || !L1.scan) return vfail(BA_ERR_OOM, "voxelize: out of device memory");
-    l1_clusters_kernel<<<blocks_for(n1), 256, 0, st>>>(n1, start, vals, keys, pscan, pts, L1.c, L1.key, L1.scan);
-    ++launches;
-    VCK(cudaGetLastError(), "voxelize clusters");
     // levels 2..L (Eq. 5)
     for (int k = 1; k < cfg->levels; ++k) {
-      const Level& ch = lv[k - 1];
-      const int64_t nc = ch.nc;
-      uint64_t* pkey = tmp.get<uint64_t>(nc);
-      uint64_t* k64 = tmp.get<uint64_t>(nc);
-      uint64_t* t64 = tmp.get<uint64_t>(nc);
-      uint32_t* skey = tmp.get<uint32_t>(nc);
-      uint32_t* tsk = tmp.get<uint32_t>(nc);
-      uint32_t* cv = tmp.get<uint32_t>(nc);
-      uint32_t* tcv = tmp.get<uint32_t>(nc);
-      int64_t* scr2 = tmp.get<int64_t>(radix_scratch_count(nc));
-      if (!pkey || !k64 || !t64 || !skey || !tsk || !cv || !tcv || !scr2)
-        return vfail(BA_ERR_OOM, "voxelize: out of device memory");
-      parent_keys_kernel<<<blocks_for(nc), 256, 0, st>>>(nc, ch.key, ch.scan, pkey, skey, cv);
-      ++launches;
-      VCK(cudaGetLastError(), "voxelize levels");
-      // by scan (stable), then by parent key (stable): order (parent, scan, child)
-      VCK(radix_sort_pairs(skey, cv, tsk, tcv, nc, bit_width_u((uint64_t)(n_scans - 1)), scr2, st, &launches),
-          "voxelize sort");
-      gather_keys_kernel<<<blocks_for(nc), 256, 0, st>>>(nc, pkey, cv, k64);
-      ++launches;
-      VCK(cudaGetLastError(), "voxelize levels");
-      VCK(radix_sort_pairs64(k64, cv, t64, tcv, nc, kKeyBits, scr2, st, &launches), "voxelize sort");
-      int64_t* pst = nullptr;
-      int64_t np = 0;
-      if ((s = group_starts(nc, k64, cv, ch.scan, tmp, &pst, &np, st, &launches)) != BA_OK) return s;
-      Level& P = lv[k];
-      P.nc = np;
-      P.c = tmp.get<double>(10 * np);
-      P.key = tmp.get<uint64_t>(np);
-      P.scan = tmp.get<int32_t>(np);
-      if (!P.c || !P.key || !P.scan) return vfail(BA_ERR_OOM, "voxelize: out of device memory");
-      merge_kernel<<<blocks_for(np), 256, 0, st>>>(np, pst, cv, ch.c, k64, ch.scan, P.c, P.key, P.scan);
-      ++launches;
-      VCK(cudaGetLastError(), "voxelize merge");
+      s = pack_bits(lv[k].pk) <= 32 ? level_up<uint32_t>(lv[k - 1], lv[k], n_scans, tmp, st, &launches)
+                                    : level_up<uint64_t>(lv[k - 1], lv[k], n_scans, tmp, st, &launches);
+      if (s != BA_OK) return s;
     }
   }
 
@@ -563,9 +963,19 @@ ba_status ba_voxelize(const ba_voxelize_config* cfg, int32_t n_scans, const int6
     if (!L.vstart || !keep_obs[k] || !keep_vox[k] || !obs_pos[k] || !vox_pos[k] || !scr3)
       return vfail(BA_ERR_OOM, "voxelize: out of device memory");
     voxel_starts_kernel<<<blocks_for(L.nc), 256, 0, st>>>(L.nc, L.key, pos, L.vstart, L.nv);
-    select_kernel<<<blocks_for(L.nv), 256, 0, st>>>(L.nv, L.vstart, L.c, L.scan, T, cfg->tau, cfg->min_obs,
+    launches += 2;
+    double4_32a* wn = nullptr;
+    float4* rsr = nullptr;
+    if (cfg->tau > 0.0) {
+      wn = tmp.get<double4_32a>(L.nc);
+      rsr = tmp.get<float4>(2 * L.nc);
+      if (!wn || !rsr) return vfail(BA_ERR_OOM, "voxelize: out of device memory");
+      world_terms_kernel<<<blocks_for(L.nc), 256, 0, st>>>(L.nc, L.c, L.scan, T, wn, rsr);
+      ++launches;
+    }
+    select_kernel<<<blocks_for(L.nv), 256, 0, st>>>(L.nv, L.vstart, wn, rsr, L.c, L.scan, T, cfg->tau, cfg->min_obs,
                                                    keep_obs[k], keep_vox[k]);
-    launches += 3;
+    ++launches;
     VCK(cudaGetLastError(), "voxelize select");
     VCK(cudaMemsetAsync(keep_obs[k] + L.nv, 0, sizeof(int64_t), st), "voxelize");
     VCK(cudaMemsetAsync(keep_vox[k] + L.nv, 0, sizeof(int64_t), st), "voxelize");
@@ -583,11 +993,17 @@ ba_status ba_voxelize(const ba_voxelize_config* cfg, int32_t n_scans, const int6
   }
   v->n_voxels = total_v;
   v->n_obs = total_o;
-  if (cudaMalloc(&v->voxel_off, sizeof(int64_t) * (total_v + 1)) != cudaSuccess ||
-      cudaMalloc(&v->obs_scan, sizeof(int32_t) * (total_o > 0 ? total_o : 1)) != cudaSuccess ||
-      cudaMalloc(&v->agg, sizeof(double) * 10 * (total_o > 0 ? total_o : 1)) != cudaSuccess ||
-      cudaMalloc(&v->level, sizeof(int32_t) * (total_v > 0 ? total_v : 1)) != cudaSuccess ||
-      cudaMalloc(&v->index, sizeof(int32_t) * 3 * (total_v > 0 ? total_v : 1)) != cudaSuccess) {
+  // the result lives in the library pool too (freed by ba_voxels_destroy)
+  cudaMemPool_t pool = library_pool(cfg->device);
+  auto out_alloc = [&](void** p, size_t bytes) {
+    return pool ? cudaMallocFromPoolAsync(p, bytes, pool, st) : cudaMalloc(p, bytes);
+  };
+  v->pooled = pool != nullptr;
+  if (out_alloc((void**)&v->voxel_off, sizeof(int64_t) * (total_v + 1)) != cudaSuccess ||
+      out_alloc((void**)&v->obs_scan, sizeof(int32_t) * (total_o > 0 ? total_o : 1)) != cudaSuccess ||
+      out_alloc((void**)&v->agg, sizeof(double) * 10 * (total_o > 0 ? total_o : 1)) != cudaSuccess ||
+      out_alloc((void**)&v->level, sizeof(int32_t) * (total_v > 0 ? total_v : 1)) != cudaSuccess ||
+      out_alloc((void**)&v->index, sizeof(int32_t) * 3 * (total_v > 0 ? total_v : 1)) != cudaSuccess) {
     cudaGetLastError();
     return vfail(BA_ERR_OOM, "voxelize output: out of device memory");
   }
@@ -596,7 +1012,7 @@ ba_status ba_voxelize(const ba_voxelize_config* cfg, int32_t n_scans, const int6
   for (int k = 0; k < cfg->levels; ++k) {
     const Level& L = lv[k];
     if (L.nv == 0) continue;
-    emit_kernel<<<blocks_for(L.nv), 256, 0, st>>>(L.nv, L.vstart, L.key, L.scan, L.c, obs_pos[k], vox_pos[k],
+    emit_kernel<<<blocks_for(L.nv), 256, 0, st>>>(L.nv, L.vstart, L.key, L.pk, L.scan, L.c, obs_pos[k], vox_pos[k],
                                                  keep_vox[k], k + 1, vb, ob, v->voxel_off, v->obs_scan, v->agg,
                                                  v->level, v->index);
     ++launches;
@@ -645,11 +1061,14 @@ void ba_voxels_destroy(ba_voxels* v) {
   int prev = -1;
   cudaGetDevice(&prev);
   cudaSetDevice(v->device);
-  cudaFree(v->voxel_off);
-  cudaFree(v->obs_scan);
-  cudaFree(v->agg);
-  cudaFree(v->level);
-  cudaFree(v->index);
+  void* ptrs[5] = {v->voxel_off, v->obs_scan, v->agg, v->level, v->index};
+  for (void* p : ptrs) {
+    if (!p) continue;
+    if (v->pooled)
+      cudaFreeAsync(p, nullptr);
+    else
+      cudaFree(p);
+  }
   if (prev >= 0) cudaSetDevice(prev);
   delete v;
 }
