@@ -209,7 +209,7 @@ def job_params(scenegen, k, scans_min, scans_max, base_seed):
 
 def kernel_source_hash(kernel: str = "voxel_pass_f64") -> str:
     h = hashlib.sha256()
-    main = "iter_mixed.cu" if "mixed" in kernel else "iter_f64.cu"
+    main = "voxelize.cu" if kernel.startswith("l1_") else "iter_mixed.cu" if "mixed" in kernel else "iter_f64.cu"
     for f in (main, "mmba_internal.cuh"):
         with open(os.path.join(ROOT, "paper_2608_14266_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
@@ -694,13 +694,17 @@ def run_served(args):
     print(json.dumps(line), flush=True)
 
 
-# preprocessing: algorithmic bytes per point of one ba_voxelize call with
-# levels > 1 dominated by level 1: read the point (24 B) and write its key,
-# index and scan (16 B); 8 passes of the stable radix sort over 64-bit keys
-# with 32-bit values (read and write 12 B each); the head flags and scan of
-# the sorted keys (8 B key + 8 B flag written and read); the cluster pass
-# (sorted index 4 B, point 24 B)
-VOXELIZE_BYTES_PER_POINT = 24 + 16 + 8 * 24 + 32 + 28
+# preprocessing: FP64 peak from the unit counts (152 SMs x 2 FP64 FMA lanes
+# per clock x 2 flops x 2.07 GHz max SM clock)
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# algorithmic work per point of the dominant stages: world point and index
+# (9 FMA + 3 adds = 21 flops); the clusters' shifted sums (3 subtractions,
+# 3 additions, 6 FMA = 18 flops); the level-1 sort of packed 32-bit keys
+# (repack: read 8 B, write 4 B; per 8-bit pass: histogram reads the 4-byte
+# key, scatter reads and writes key and value, 4 + 16 B)
+VOX_KEYS_FLOPS_PER_POINT = 21
+VOX_CLUSTER_FLOPS_PER_POINT = 18
+VOX_SORT_BYTES_PER_POINT = lambda passes: 12 + 20 * passes
 
 
 def run_voxelize(args):
@@ -722,8 +726,11 @@ def run_voxelize(args):
     P = P.view(n_obs, npo, 3)[order].reshape(-1, 3).contiguous()
     counts = np.bincount(s.obs_scan, minlength=s.n_scans) * npo
     spo_h = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
-    spo, poses = torch.from_numpy(spo_h).cuda(), torch.from_numpy(s.pose_init).cuda()
+    n_scans = max(1, int(round(s.n_scans * args.shrink)))  # a prefix of the scans (profiling captures)
+    spo_h = spo_h[: n_scans + 1]
     n_pts = int(spo_h[-1])
+    P = P[:n_pts].contiguous()
+    spo, poses = torch.from_numpy(spo_h).cuda(), torch.from_numpy(s.pose_init[:n_scans]).cuda()
     cfg = dict(voxel_size=0.5, levels=3, tau=0.1, min_obs=2)
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
@@ -733,10 +740,15 @@ def run_voxelize(args):
     steps = max(1, min(args.steps, 10))
     clocks = ClockSampler(_gpu_id(torch, 0))
     time.sleep(0.3)
+    stage_ms = {}
+    launches = 0
     t_wall0 = time.time()
     e0.record(stream)
     for _ in range(steps):
-        v = mm.voxelize(spo, P, poses, stream=stream, out="device", **cfg)
+        v = mm.voxelize(spo, P, poses, stream=stream, out="device", profile=True, **cfg)
+        launches += v["launches"]
+        for k, x in v["stage_ms"].items():
+            stage_ms[k] = stage_ms.get(k, 0.0) + x / steps
     e1.record(stream)
     torch.cuda.synchronize()
     t_wall1 = time.time()
@@ -753,12 +765,30 @@ def run_voxelize(args):
     e2e_s = (time.perf_counter() - t0) / steps
     h2d = spo_p.numel() * 8 + P_p.numel() * 8 + T_p.numel() * 8
     d2h = sum(a.nbytes for k, a in r.items() if k != "launches")
-    peak, src = hbm_peak()
-    achieved = VOXELIZE_BYTES_PER_POINT * n_pts / (ms / 1000.0) / 1e9
+    hbm, src = hbm_peak()
+    # the level-1 sort runs ceil(bits / 8) passes over the packed keys
+    span = _world_index_range(P_p.numpy(), spo_h, s.pose_init[:n_scans], cfg["voxel_size"])
+    passes = -(-int(sum(int(x).bit_length() for x in span)) // 8)
+    rl = {
+        "cluster_pass": {"bound": "alu", "achieved": VOX_CLUSTER_FLOPS_PER_POINT * n_pts / (stage_ms["cluster_pass"] / 1e3) / 1e12,
+                         "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s"},
+        "keys": {"bound": "alu", "achieved": VOX_KEYS_FLOPS_PER_POINT * n_pts / (stage_ms["keys"] / 1e3) / 1e12,
+                 "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s"},
+        "sort": {"bound": "hbm", "achieved": VOX_SORT_BYTES_PER_POINT(passes) * n_pts / (stage_ms["sort"] / 1e3) / 1e9,
+                 "peak": hbm, "unit": "GB/s"},
+    }
+    for x in rl.values():
+        x["frac"] = x["achieved"] / x["peak"]
+    top = max(rl, key=lambda k: stage_ms[k])
+    kname = {"cluster_pass": "l1_pieces", "keys": "l1_keys", "sort": "radix sort of the level-1 keys"}[top]
+    tr = recorded_traffic(f"voxelize_{n_scans}", kname)
+    roof = dict(rl[top], traffic=tr, kernel=kname,
+                stage_ms=stage_ms[top], peak_source="FP64: 152 SMs x 2 FMA/clk x 2 flops x 2.07 GHz"
+                if rl[top]["bound"] == "alu" else src)
     # oracle on the first scans' points (bounded sample), scaled by points
     import oracle
     k = 1
-    while k < s.n_scans and spo_h[k] < 25_000_000:
+    while k < n_scans and spo_h[k] < 25_000_000:
         k += 1
     Ph = P[: int(spo_h[k])].cpu().numpy()
     t0 = time.perf_counter()
@@ -769,20 +799,34 @@ def run_voxelize(args):
         "value": n_pts / (ms / 1000.0), "unit": "points/s", "n_gpus": 1, "steps": steps, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "points": n_pts, "voxels_out": int(v["level"].numel()),
-        "obs_out": int(v["obs_scan"].numel()), "gpu_launches": int(v["launches"]) * steps, "clocks": clk,
+        "obs_out": int(v["obs_scan"].numel()), "gpu_launches": int(launches), "clocks": clk,
         "e2e": {"value": n_pts / e2e_s, "unit": "points/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_s * 1000.0},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None, "kernel": "whole call (sort-dominated)", "peak_source": src,
-                     "bytes_per_point": VOXELIZE_BYTES_PER_POINT},
+        "roofline": roof,
+        "stages_ms": {k2: round(x, 3) for k2, x in stage_ms.items()},
+        "stage_rooflines": {k2: {"frac": round(x["frac"], 3), "bound": x["bound"]} for k2, x in rl.items()},
         "cpu_baseline": {"value": int(spo_h[k]) / cpu_s, "unit": "points/s", "cores": 1, "kind": "oracle",
                          "sample": f"points of the first {k} scans ({int(spo_h[k])} points)"},
-        "config": {"workload": f"raw scans of the {s.n_scans}-scan scene ({n_pts} points) -> voxels",
-                   "scans": s.n_scans, "voxel_size_m": cfg["voxel_size"], "levels": cfg["levels"],
-                   "tau": cfg["tau"], "min_obs": cfg["min_obs"],
+        "config": {"workload": f"raw scans of the {n_scans}-scan scene ({n_pts} points) -> voxels",
+                   "scans": n_scans, "voxel_size_m": cfg["voxel_size"], "levels": cfg["levels"],
+                   "tau": cfg["tau"], "min_obs": cfg["min_obs"], "sort_passes": passes,
                    "inputs": "points resident on the device, larger than L2"},
     }
     print(json.dumps(line), flush=True)
+
+
+def _world_index_range(P, spo, poses, d):
+    """Per axis, the span of the level-1 voxel indices (max - min), from the
+    poses applied to each scan's points (host arithmetic, for the pass count)."""
+    import numpy as np
+    lo, hi = np.full(3, np.inf), np.full(3, -np.inf)
+    for j in range(len(spo) - 1):
+        Q = P[spo[j]:spo[j + 1]]
+        if len(Q) == 0:
+            continue
+        W = Q @ poses[j, :9].reshape(3, 3).T + poses[j, 9:]
+        lo, hi = np.minimum(lo, W.min(axis=0)), np.maximum(hi, W.max(axis=0))
+    return np.floor(hi / d) - np.floor(lo / d)
 
 
 def main():

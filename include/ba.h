@@ -349,7 +349,26 @@ typedef struct {
   int32_t min_obs;    /* observations a voxel needs to be kept (default 1) */
   int32_t device;     /* CUDA device (default 0) */
   void* cuda_stream;  /* cudaStream_t (NULL = legacy default) */
+  int32_t profile;    /* nonzero: time the stages with CUDA events (default 0) */
 } ba_voxelize_config;
+
+/* Stages timed when profile is set (ba_voxels_stage_ms): world points and
+ * level-1 keys; the level-1 sort (with the key packing); the (voxel, scan)
+ * runs of the sorted points (includes one host synchronisation); the
+ * clusters' chunked sums; their per-run finish; all higher levels (includes
+ * host synchronisations); the selection's per-observation terms and
+ * per-voxel test; the output writes. */
+enum {
+  BA_VOX_KEYS = 0,
+  BA_VOX_SORT = 1,
+  BA_VOX_RUNS = 2,
+  BA_VOX_CLUSTER_PASS = 3,
+  BA_VOX_CLUSTER_FINISH = 4,
+  BA_VOX_LEVELS = 5,
+  BA_VOX_SELECT = 6,
+  BA_VOX_EMIT = 7,
+  BA_VOX_STAGES = 8
+};
 
 typedef struct ba_voxels ba_voxels;
 
@@ -369,6 +388,9 @@ ba_status ba_voxels_size(const ba_voxels* v, int64_t* n_voxels, int64_t* n_obs);
 ba_status ba_voxels_read(const ba_voxels* v, int64_t* voxel_off, int32_t* obs_scan, double* agg, int32_t* level,
                          int32_t* index, int32_t mem_kind);
 int64_t ba_voxels_kernel_launches(const ba_voxels* v);
+/* Device milliseconds of one stage (summed over levels) of the call that made
+ * v; 0 when it was not profiled.  BA_ERR_INVALID_ARG for a bad stage. */
+ba_status ba_voxels_stage_ms(const ba_voxels* v, int32_t stage, double* ms);
 const char* ba_voxelize_last_error(void);
 void ba_voxels_destroy(ba_voxels* v);
 

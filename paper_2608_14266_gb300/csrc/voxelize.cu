@@ -635,6 +635,52 @@ struct Buf {
   }
 };
 
+// CUDA-event timing of the stages on the call's stream (when profiling)
+struct StageTimer {
+  bool on = false;
+  cudaStream_t st = nullptr;
+  struct Rec {
+    int stage;
+    cudaEvent_t a, b;
+  };
+  std::vector<Rec> recs;
+  cudaEvent_t open_ev = nullptr;
+  int open_stage = -1;
+  void begin(int stage) {
+    if (!on) return;
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return;
+    cudaEventRecord(e, st);
+    open_ev = e;
+    open_stage = stage;
+  }
+  void end() {
+    if (!on || !open_ev) return;
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) == cudaSuccess) {
+      cudaEventRecord(e, st);
+      recs.push_back({open_stage, open_ev, e});
+    } else {
+      cudaEventDestroy(open_ev);
+    }
+    open_ev = nullptr;
+  }
+  // after the stream has been synchronised
+  void collect(double* ms) const {
+    for (const Rec& r : recs) {
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) ms[r.stage] += t;
+    }
+  }
+  ~StageTimer() {
+    if (open_ev) cudaEventDestroy(open_ev);
+    for (const Rec& r : recs) {
+      cudaEventDestroy(r.a);
+      cudaEventDestroy(r.b);
+    }
+  }
+};
+
 unsigned blocks_for(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t > 0 ? (n + t - 1) / t : 1); }
 
 int bit_width_u(uint64_t x) {
@@ -716,12 +762,13 @@ struct Level {
 // level 1: raw keys -> packed keys, sort, (key, scan) runs, clusters
 template <typename K>
 ba_status level1(int64_t n, const uint64_t* raw, uint32_t* vals, const int32_t* pscan, const double* pts, Level& L,
-                 Buf& tmp, cudaStream_t st, int64_t* launches) {
+                 Buf& tmp, StageTimer& tm, cudaStream_t st, int64_t* launches) {
   K* keys = tmp.get<K>(n);
   K* tkeys = tmp.get<K>(n);
   uint32_t* tvals = tmp.get<uint32_t>(n);
   int64_t* scr = tmp.get<int64_t>(radix_scratch_count(n));
   if (!keys || !tkeys || !tvals || !scr) return vfail(BA_ERR_OOM, "voxelize: out of device memory");
+  tm.begin(BA_VOX_SORT);
   repack_kernel<K><<<blocks_for(n), 256, 0, st>>>(n, raw, L.pk, keys);
   ++*launches;
   VCK(cudaGetLastError(), "voxelize keys");
@@ -732,9 +779,12 @@ ba_status level1(int64_t n, const uint64_t* raw, uint32_t* vals, const int32_t* 
   else
     VCK(radix_sort_pairs64((uint64_t*)keys, vals, (uint64_t*)tkeys, tvals, n, pack_bits(L.pk), scr, st, launches),
         "voxelize sort");
+  tm.end();
   int64_t *pos = nullptr, *start = nullptr;
   int64_t n1 = 0;
+  tm.begin(BA_VOX_RUNS);
   ba_status s = group_starts<K>(n, keys, vals, pscan, tmp, &pos, &start, &n1, st, launches);
+  tm.end();
   if (s != BA_OK) return s;
   L.nc = n1;
   L.c = tmp.get<double>(10 * n1);
@@ -744,8 +794,12 @@ ba_status level1(int64_t n, const uint64_t* raw, uint32_t* vals, const int32_t* 
   double* hp = tmp.get<double>(kPieceDoubles * n1);
   double* cr = tmp.get<double>(kPieceDoubles * n_chunks);
   if (!L.c || !L.key || !L.scan || !hp || !cr) return vfail(BA_ERR_OOM, "voxelize: out of device memory");
+  tm.begin(BA_VOX_CLUSTER_PASS);
   l1_pieces_kernel<K><<<blocks_for(n_chunks), 256, 0, st>>>(n, keys, vals, pscan, pts, pos, hp, cr, L.key, L.scan);
+  tm.end();
+  tm.begin(BA_VOX_CLUSTER_FINISH);
   l1_finish_kernel<<<blocks_for(n1), 256, 0, st>>>(n1, start, hp, cr, L.c);
+  tm.end();
   *launches += 2;
   VCK(cudaGetLastError(), "voxelize clusters");
   return BA_OK;
@@ -806,6 +860,7 @@ struct ba_voxels {
   int32_t* index = nullptr;
   int64_t launches = 0;
   bool pooled = false;  // arrays from the library pool (stream-ordered frees)
+  double stage_ms[BA_VOX_STAGES] = {};
 };
 
 extern "C" {
@@ -818,6 +873,7 @@ void ba_voxelize_config_default(ba_voxelize_config* cfg) {
   cfg->min_obs = 1;
   cfg->device = 0;
   cfg->cuda_stream = nullptr;
+  cfg->profile = 0;
 }
 
 const char* ba_voxelize_last_error(void) { return g_vox_error.c_str(); }
@@ -842,6 +898,9 @@ ba_status ba_voxelize(const ba_voxelize_config* cfg, int32_t n_scans, const int6
   } restore{prev};
   cudaStream_t st = (cudaStream_t)cfg->cuda_stream;
   Buf tmp(st, cfg->device);
+  StageTimer tm;
+  tm.on = cfg->profile != 0;
+  tm.st = st;
   int64_t launches = 0;
 
   // stage the inputs
@@ -900,8 +959,10 @@ ba_status ba_voxelize(const ba_voxelize_config* cfg, int32_t n_scans, const int6
     int n_sm = 0;
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, cfg->device);
     const int64_t key_blocks = std::min<int64_t>(blocks_for(n), (int64_t)(n_sm > 0 ? n_sm : 1) * 8);
+    tm.begin(BA_VOX_KEYS);
     l1_keys_kernel<<<(unsigned)key_blocks, 256, 0, st>>>(n_scans, spo, pts, T, sposes, cfg->voxel_size, n, raw, vals,
                                                           pscan, bad + 2, bbox);
+    tm.end();
     launches += 2;
     VCK(cudaGetLastError(), "voxelize keys");
     int bb[6];
@@ -919,13 +980,16 @@ ba_status ba_voxelize(const ba_voxelize_config* cfg, int32_t n_scans, const int6
       }
       L.pk = make_pack(L.lo, L.hi);
     }
-    ba_status s = pack_bits(lv[0].pk) <= 32 ? level1<uint32_t>(n, raw, vals, pscan, pts, lv[0], tmp, st, &launches)
-                                            : level1<uint64_t>(n, raw, vals, pscan, pts, lv[0], tmp, st, &launches);
+    ba_status s = pack_bits(lv[0].pk) <= 32
+                      ? level1<uint32_t>(n, raw, vals, pscan, pts, lv[0], tmp, tm, st, &launches)
+                      : level1<uint64_t>(n, raw, vals, pscan, pts, lv[0], tmp, tm, st, &launches);
     if (s != BA_OK) return s;
     // levels 2..L (Eq. 5)
     for (int k = 1; k < cfg->levels; ++k) {
+      tm.begin(BA_VOX_LEVELS);
       s = pack_bits(lv[k].pk) <= 32 ? level_up<uint32_t>(lv[k - 1], lv[k], n_scans, tmp, st, &launches)
                                     : level_up<uint64_t>(lv[k - 1], lv[k], n_scans, tmp, st, &launches);
+      tm.end();
       if (s != BA_OK) return s;
     }
   }
@@ -970,11 +1034,14 @@ ba_status ba_voxelize(const ba_voxelize_config* cfg, int32_t n_scans, const int6
       wn = tmp.get<double4_32a>(L.nc);
       rsr = tmp.get<float4>(2 * L.nc);
       if (!wn || !rsr) return vfail(BA_ERR_OOM, "voxelize: out of device memory");
+      tm.begin(BA_VOX_SELECT);
       world_terms_kernel<<<blocks_for(L.nc), 256, 0, st>>>(L.nc, L.c, L.scan, T, wn, rsr);
       ++launches;
     }
+    if (!wn) tm.begin(BA_VOX_SELECT);
     select_kernel<<<blocks_for(L.nv), 256, 0, st>>>(L.nv, L.vstart, wn, rsr, L.c, L.scan, T, cfg->tau, cfg->min_obs,
                                                    keep_obs[k], keep_vox[k]);
+    tm.end();
     ++launches;
     VCK(cudaGetLastError(), "voxelize select");
     VCK(cudaMemsetAsync(keep_obs[k] + L.nv, 0, sizeof(int64_t), st), "voxelize");
@@ -1012,9 +1079,11 @@ ba_status ba_voxelize(const ba_voxelize_config* cfg, int32_t n_scans, const int6
   for (int k = 0; k < cfg->levels; ++k) {
     const Level& L = lv[k];
     if (L.nv == 0) continue;
+    tm.begin(BA_VOX_EMIT);
     emit_kernel<<<blocks_for(L.nv), 256, 0, st>>>(L.nv, L.vstart, L.key, L.pk, L.scan, L.c, obs_pos[k], vox_pos[k],
                                                  keep_vox[k], k + 1, vb, ob, v->voxel_off, v->obs_scan, v->agg,
                                                  v->level, v->index);
+    tm.end();
     ++launches;
     VCK(cudaGetLastError(), "voxelize emit");
     vb += lv_nv[k];
@@ -1022,6 +1091,7 @@ ba_status ba_voxelize(const ba_voxelize_config* cfg, int32_t n_scans, const int6
   }
   VCK(cudaStreamSynchronize(st), "voxelize");
   v->launches = launches;
+  tm.collect(v->stage_ms);
   *out = v;
   v = nullptr;  // handed out
   return BA_OK;
@@ -1055,6 +1125,12 @@ ba_status ba_voxels_read(const ba_voxels* v, int64_t* voxel_off, int32_t* obs_sc
 }
 
 int64_t ba_voxels_kernel_launches(const ba_voxels* v) { return v ? v->launches : 0; }
+
+ba_status ba_voxels_stage_ms(const ba_voxels* v, int32_t stage, double* ms) {
+  if (!v || !ms || stage < 0 || stage >= BA_VOX_STAGES) return BA_ERR_INVALID_ARG;
+  *ms = v->stage_ms[stage];
+  return BA_OK;
+}
 
 void ba_voxels_destroy(ba_voxels* v) {
   if (!v) return;
