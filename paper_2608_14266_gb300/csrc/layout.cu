@@ -99,10 +99,13 @@ cudaError_t exclusive_scan_i64(int64_t* data, int64_t n, int64_t* scratch, cudaS
 //  pass: (1) per-tile digit histograms -> hist[digit * n_tiles + tile];
 //        (2) exclusive scan of hist (digit-major) -> global start of each
 //            (digit, tile) group;
-//        (3) each tile scatters its elements in input order: the rank of an
-//            element among equal digits of its tile comes from warp match
-//            masks plus per-warp counts, so the sort is stable and
-//            deterministic.
+//        (3) each tile loads its elements (all loads issued up front); each
+//            warp ranks its 512 consecutive elements in order with match
+//            masks and warp-private digit counters (stable, deterministic,
+//            no block barrier); per-digit prefix sums over the warps and the
+//            digits place the tile digit-sorted in shared memory, and every
+//            digit's run goes to its global place with consecutive threads on
+//            consecutive addresses (full-sector writes).
 // ============================================================================
 constexpr int kRadixBlock = 256;
 constexpr int kRadixItems = 16;  // chunks per tile
@@ -125,51 +128,91 @@ __global__ void __launch_bounds__(kRadixBlock) radix_hist_kernel(const K* keys, 
 }
 
 template <typename K>
+constexpr size_t radix_scatter_smem() {
+  return (size_t)kRadixTile * (sizeof(K) + sizeof(uint32_t));
+}
+
+template <typename K>
 __global__ void __launch_bounds__(kRadixBlock) radix_scatter_kernel(const K* keys_in, const uint32_t* vals_in,
                                                                     K* keys_out, uint32_t* vals_out, int64_t n,
                                                                     int shift, const int64_t* hist, int64_t n_tiles) {
-  __shared__ int64_t start[256];      // global position of this tile's next element per digit
-  __shared__ int wcnt[kRadixWarps][256];
+  extern __shared__ __align__(16) unsigned char radix_smem[];
+  K* skey = reinterpret_cast<K*>(radix_smem);
+  uint32_t* sval = reinterpret_cast<uint32_t*>(radix_smem + sizeof(K) * kRadixTile);
+  __shared__ int64_t gstart[256];          // global start of this tile's run of each digit
+  __shared__ int lstart[256];              // tile-local start of each digit
+  __shared__ int wc[kRadixWarps][256];     // per warp: count, then start, of each digit
+  __shared__ int wsum[kRadixWarps];
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  start[tid] = hist[(int64_t)tid * n_tiles + blockIdx.x];
   const int64_t base = (int64_t)blockIdx.x * kRadixTile;
-  for (int c = 0; c < kRadixItems; ++c) {
-    for (int k = 0; k < kRadixWarps; ++k) wcnt[k][tid] = 0;
-    __syncthreads();
-    const int64_t i = base + (int64_t)c * kRadixBlock + tid;
-    const bool valid = i < n;
-    K key = 0;
-    uint32_t val = 0;
-    unsigned d = 256u;  // sentinel digit for invalid lanes
-    if (valid) {
-      key = keys_in[i];
-      val = vals_in[i];
-      d = (unsigned)(key >> shift) & 255u;
+  const int tile_n = (int)(n - base < kRadixTile ? n - base : kRadixTile);
+  gstart[tid] = hist[(int64_t)tid * n_tiles + blockIdx.x];
+#pragma unroll
+  for (int k = 0; k < kRadixWarps; ++k) wc[k][tid] = 0;
+  // warp w owns the tile's elements [w * 512, (w + 1) * 512), 32 per round
+  K key[kRadixItems];
+  uint32_t val[kRadixItems];
+  unsigned dig[kRadixItems];
+#pragma unroll
+  for (int j = 0; j < kRadixItems; ++j) {
+    const int li = w * (32 * kRadixItems) + j * 32 + lane;
+    dig[j] = 256u;  // sentinel for lanes past the end
+    if (li < tile_n) {
+      key[j] = keys_in[base + li];
+      val[j] = vals_in[base + li];
+      dig[j] = (unsigned)(key[j] >> shift) & 255u;
     }
+  }
+  __syncthreads();
+  // rank within the warp, in element order (rounds, then lanes)
+  int rk[kRadixItems];
+#pragma unroll
+  for (int j = 0; j < kRadixItems; ++j) {
+    const unsigned d = dig[j];
     const unsigned same = __match_any_sync(0xffffffffu, d);
-    const int rank = __popc(same & ((1u << lane) - 1u));
-    const int leader = __ffs(same) - 1;
-    if (valid && lane == leader) wcnt[w][d] = __popc(same);
-    __syncthreads();
-    // per digit: exclusive prefix over warps (thread tid handles digit tid)
-    {
-      int run = 0;
-      for (int k = 0; k < kRadixWarps; ++k) {
-        int x = wcnt[k][tid];
-        wcnt[k][tid] = run;
-        run += x;
-      }
-      // stash the chunk total for this digit in a register until after scatter
-      __syncthreads();
-      if (valid) {
-        const int64_t dst = start[d] + wcnt[w][d] + rank;
-        keys_out[dst] = key;
-        vals_out[dst] = val;
-      }
-      __syncthreads();
-      start[tid] += run;
+    const int before = d < 256u ? wc[w][d] : 0;
+    rk[j] = before + __popc(same & ((1u << lane) - 1u));
+    __syncwarp();
+    if (d < 256u && lane == __ffs(same) - 1) wc[w][d] = before + __popc(same);
+    __syncwarp();
+  }
+  __syncthreads();
+  // per digit (thread tid = digit): warps' starts within the digit, tile total
+  int run = 0;
+#pragma unroll
+  for (int k = 0; k < kRadixWarps; ++k) {
+    const int x = wc[k][tid];
+    wc[k][tid] = run;
+    run += x;
+  }
+  int incl = run;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) wsum[w] = incl;
+  __syncthreads();
+  int wpre = 0;
+  for (int k = 0; k < w; ++k) wpre += wsum[k];
+  lstart[tid] = wpre + incl - run;
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < kRadixItems; ++j) {
+    const unsigned d = dig[j];
+    if (d < 256u) {
+      const int p = lstart[d] + wc[w][d] + rk[j];
+      skey[p] = key[j];
+      sval[p] = val[j];
     }
-    __syncthreads();
+  }
+  __syncthreads();
+  for (int p = tid; p < tile_n; p += kRadixBlock) {
+    const K k = skey[p];
+    const unsigned d = (unsigned)(k >> shift) & 255u;
+    const int64_t dst = gstart[d] + (p - lstart[d]);
+    keys_out[dst] = k;
+    vals_out[dst] = sval[p];
   }
 }
 
@@ -189,12 +232,15 @@ static cudaError_t radix_sort_pairs_t(K* keys, uint32_t* vals, K* tmp_keys, uint
   K *ki = keys, *ko = tmp_keys;
   uint32_t *vi = vals, *vo = tmp_vals;
   const int passes = (bits + 7) / 8;
+  RETURN_IF(cudaFuncSetAttribute(radix_scatter_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)radix_scatter_smem<K>()));
   for (int p = 0; p < passes; ++p) {
     radix_hist_kernel<K><<<(unsigned)tiles, kRadixBlock, 0, stream>>>(ki, n, 8 * p, hist, tiles);
     ++*launches;
     RETURN_IF(cudaGetLastError());
     RETURN_IF(exclusive_scan_i64(hist, 256 * tiles, scan_scratch, stream, launches));
-    radix_scatter_kernel<K><<<(unsigned)tiles, kRadixBlock, 0, stream>>>(ki, vi, ko, vo, n, 8 * p, hist, tiles);
+    radix_scatter_kernel<K><<<(unsigned)tiles, kRadixBlock, radix_scatter_smem<K>(), stream>>>(ki, vi, ko, vo, n,
+                                                                                              8 * p, hist, tiles);
     ++*launches;
     RETURN_IF(cudaGetLastError());
     K* t = ki;

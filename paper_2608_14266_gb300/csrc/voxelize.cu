@@ -186,19 +186,33 @@ __device__ __forceinline__ bool group_head(int64_t i, const K* keys, const uint3
   return i == 0 || keys[i] != keys[i - 1] || scan[vals[i]] != scan[vals[i - 1]];
 }
 
+// group heads as one 32-bit word per 32 elements (bit k: element 32 w + k
+// starts a group) and the number of heads of each word
 template <typename K>
-__global__ void heads_kernel(int64_t n, const K* keys, const uint32_t* vals, const int32_t* scan, int64_t* pos) {
+__global__ void head_mask_kernel(int64_t n, const K* keys, const uint32_t* vals, const int32_t* scan, uint32_t* mask,
+                                 int64_t* wcount) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) pos[i] = group_head(i, keys, vals, scan) ? 1 : 0;
+  const bool h = i < n && group_head(i, keys, vals, scan);
+  const uint32_t m = __ballot_sync(0xffffffffu, h);
+  if ((threadIdx.x & 31) == 0 && i < n) {
+    mask[i >> 5] = m;
+    wcount[i >> 5] = __popc(m);
+  }
 }
 
-// after the exclusive scan: start of every group, and the end sentinel
-template <typename K>
-__global__ void starts_kernel(int64_t n, const K* keys, const uint32_t* vals, const int32_t* scan,
-                              const int64_t* pos, int64_t* start, int64_t n_groups) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n && group_head(i, keys, vals, scan)) start[pos[i]] = i;
-  if (i == 0) start[n_groups] = n;
+// group starts from the mask and the words' exclusive head counts, and the
+// end sentinel
+__global__ void mask_starts_kernel(int64_t n_words, const uint32_t* mask, const int64_t* base, int64_t n,
+                                   int64_t* start, int64_t n_groups) {
+  const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= n_words) return;
+  uint32_t m = mask[w];
+  int64_t b = base[w];
+  while (m) {
+    start[b++] = 32 * w + (__ffs(m) - 1);
+    m &= m - 1u;
+  }
+  if (w == 0) start[n_groups] = n;
 }
 
 // ---- clusters (Eq. 2, centred) from shifted sums ----------------------------
@@ -302,50 +316,72 @@ __device__ __forceinline__ void piece_finish(const Piece& P, double* c) {
 
 constexpr int kChunk = 32;  // sorted points per thread
 
-// L1 clusters, pass 1: each thread sums a chunk of kChunk sorted points, one
-// piece per (key, scan) run (pos = exclusive count of run heads, so e is a
-// head iff pos[e + 1] != pos[e]).  The piece where a run starts goes to
-// head_piece[run], the piece of a run continuing from the previous chunk to
-// carry[chunk]; counts are stored as integers (no FP64 work in the
-// divergent stores).
+// L1 clusters, pass 1: each thread sums a chunk of kChunk = 32 sorted points,
+// one piece per (key, scan) run; hmask[chunk] flags the run heads of the
+// chunk and base[chunk] counts the heads before it.  The piece where a run starts
+// goes to head_piece[run], the piece of a run continuing from the previous
+// chunk to carry[chunk]; counts are stored as integers (no FP64 work in the
+// divergent stores).  Indices come in as two 16-byte loads and the points of
+// 8 of them are loaded together, so a thread's sectors are used while cached.
 template <typename K>
-__global__ void l1_pieces_kernel(int64_t n, const K* keys, const uint32_t* vals, const int32_t* pscan,
-                                 const double* pts, const int64_t* pos, double* head_piece, double* carry,
-                                 uint64_t* ckey, int32_t* cscan) {
+__global__ void __launch_bounds__(256, 2) l1_pieces_kernel(int64_t n, const K* keys, const uint32_t* vals,
+                                                        const int32_t* pscan, const double* pts, const int64_t* base,
+                                                        const uint32_t* hmask, double* head_piece, double* carry,
+                                                        uint64_t* ckey, int32_t* cscan) {
+  static_assert(kChunk == 32, "one head-mask word per chunk");
   const int64_t ch = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t e0 = ch * kChunk;
   if (e0 >= n) return;
   const int64_t e1 = e0 + kChunk < n ? e0 + kChunk : n;
-  int64_t prev = pos[e0 + 1];
-  int64_t g = prev - 1;  // run of element e0
-  bool open = prev == pos[e0];
-  if (!open) {
-    ckey[g] = (uint64_t)keys[e0];
-    cscan[g] = pscan[vals[e0]];
-  }
+  const uint32_t hm = hmask[ch];
+  const bool open = !(hm & 1u);  // the first run continues from the previous chunk
+  const int64_t g0 = base[ch] - 1;  // the run holding e0 - 1 (a head at e0 starts run g0 + 1)
+  int64_t g = g0;
   Piece P;
   int cnt = 0;
-  auto flush = [&]() {
-    P.n = __longlong_as_double((long long)cnt);
-    piece_store(open ? carry + kPieceDoubles * ch : head_piece + kPieceDoubles * g, P);
-  };
-  for (int64_t e = e0; e < e1; ++e) {
-    const int64_t pe = pos[e + 1];
-    const uint32_t v = vals[e];
-    if (pe != prev) {
-      flush();
-      ++g;
-      open = false;
-      cnt = 0;
-      prev = pe;
-      ckey[g] = (uint64_t)keys[e];
-      cscan[g] = pscan[v];
+  bool first = true;
+#pragma unroll 1
+  for (int64_t eb = e0; eb < e1; eb += 8) {
+    uint32_t v[8];
+    if (eb + 8 <= e1) {
+      const uint4 a = *reinterpret_cast<const uint4*>(vals + eb);
+      const uint4 b = *reinterpret_cast<const uint4*>(vals + eb + 4);
+      v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w, v[4] = b.x, v[5] = b.y, v[6] = b.z, v[7] = b.w;
+    } else {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) v[k] = eb + k < e1 ? vals[eb + k] : 0u;
     }
-    const double* p = pts + 3 * (int64_t)v;
-    piece_add(P, cnt, p[0], p[1], p[2]);
-    ++cnt;
+    double px[8], py[8], pz[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      if (eb + k < e1) {
+        const double* p = pts + 3 * (int64_t)v[k];
+        px[k] = p[0];
+        py[k] = p[1];
+        pz[k] = p[2];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int64_t e = eb + k;
+      if (e >= e1) break;
+      if ((hm >> (int)(e - e0)) & 1u) {
+        if (!first) {  // close the previous run's piece
+          P.n = __longlong_as_double((long long)cnt);
+          piece_store((g == g0 && open) ? carry + kPieceDoubles * ch : head_piece + kPieceDoubles * g, P);
+        }
+        ++g;
+        cnt = 0;
+        ckey[g] = (uint64_t)keys[e];
+        cscan[g] = pscan[v[k]];
+      }
+      first = false;
+      piece_add(P, cnt, px[k], py[k], pz[k]);
+      ++cnt;
+    }
   }
-  flush();
+  P.n = __longlong_as_double((long long)cnt);
+  piece_store((g == g0 && open) ? carry + kPieceDoubles * ch : head_piece + kPieceDoubles * g, P);
 }
 
 __device__ __forceinline__ Piece piece_load_counted(const double* o) {
@@ -710,28 +746,32 @@ ba_status vfail(ba_status s, const char* fmt, ...) {
                                              : vfail(BA_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e_)); \
   } while (0)
 
-// group starts of a sorted (key, scan) sequence: pos = exclusive count of
-// group heads (n + 1 entries), start (n_groups + 1 entries)
+// groups of a sorted (key, scan) sequence: mask (one word per 32 elements),
+// base = exclusive head count before each word (n_words + 1 entries), start
+// (n_groups + 1 entries)
 template <typename K>
 ba_status group_starts(int64_t n, const K* keys, const uint32_t* vals, const int32_t* scan, Buf& tmp,
-                       int64_t** pos_out, int64_t** start_out, int64_t* n_groups, cudaStream_t st,
-                       int64_t* launches) {
-  int64_t* pos = tmp.get<int64_t>(n + 1);
-  int64_t* scr = tmp.get<int64_t>(scan_scratch_count(n + 1));
-  if (!pos || !scr) return vfail(BA_ERR_OOM, "voxelize: out of device memory");
-  heads_kernel<K><<<blocks_for(n), 256, 0, st>>>(n, keys, vals, scan, pos);
+                       uint32_t** mask_out, int64_t** base_out, int64_t** start_out, int64_t* n_groups,
+                       cudaStream_t st, int64_t* launches) {
+  const int64_t nw = (n + 31) / 32;
+  uint32_t* mask = tmp.get<uint32_t>(nw);
+  int64_t* base = tmp.get<int64_t>(nw + 1);
+  int64_t* scr = tmp.get<int64_t>(scan_scratch_count(nw + 1));
+  if (!mask || !base || !scr) return vfail(BA_ERR_OOM, "voxelize: out of device memory");
+  head_mask_kernel<K><<<blocks_for(n), 256, 0, st>>>(n, keys, vals, scan, mask, base);
   VCK(cudaGetLastError(), "voxelize");
-  VCK(cudaMemsetAsync(pos + n, 0, sizeof(int64_t), st), "voxelize");
-  VCK(exclusive_scan_i64(pos, n + 1, scr, st, launches), "voxelize");
+  VCK(cudaMemsetAsync(base + nw, 0, sizeof(int64_t), st), "voxelize");
+  VCK(exclusive_scan_i64(base, nw + 1, scr, st, launches), "voxelize");
   int64_t ng = 0;
-  VCK(cudaMemcpyAsync(&ng, pos + n, sizeof ng, cudaMemcpyDeviceToHost, st), "voxelize");
+  VCK(cudaMemcpyAsync(&ng, base + nw, sizeof ng, cudaMemcpyDeviceToHost, st), "voxelize");
   VCK(cudaStreamSynchronize(st), "voxelize");
   int64_t* start = tmp.get<int64_t>(ng + 1);
   if (!start) return vfail(BA_ERR_OOM, "voxelize: out of device memory");
-  starts_kernel<K><<<blocks_for(n), 256, 0, st>>>(n, keys, vals, scan, pos, start, ng);
+  mask_starts_kernel<<<blocks_for(nw), 256, 0, st>>>(nw, mask, base, n, start, ng);
   VCK(cudaGetLastError(), "voxelize");
   *launches += 2;
-  *pos_out = pos;
+  *mask_out = mask;
+  *base_out = base;
   *start_out = start;
   *n_groups = ng;
   return BA_OK;
@@ -780,22 +820,24 @@ ba_status level1(int64_t n, const uint64_t* raw, uint32_t* vals, const int32_t* 
     VCK(radix_sort_pairs64((uint64_t*)keys, vals, (uint64_t*)tkeys, tvals, n, pack_bits(L.pk), scr, st, launches),
         "voxelize sort");
   tm.end();
-  int64_t *pos = nullptr, *start = nullptr;
+  int64_t *base = nullptr, *start = nullptr;
+  uint32_t* hmask = nullptr;
   int64_t n1 = 0;
+  const int64_t n_chunks = (n + kChunk - 1) / kChunk;
   tm.begin(BA_VOX_RUNS);
-  ba_status s = group_starts<K>(n, keys, vals, pscan, tmp, &pos, &start, &n1, st, launches);
+  ba_status s = group_starts<K>(n, keys, vals, pscan, tmp, &hmask, &base, &start, &n1, st, launches);
   tm.end();
   if (s != BA_OK) return s;
   L.nc = n1;
   L.c = tmp.get<double>(10 * n1);
   L.key = tmp.get<uint64_t>(n1);
   L.scan = tmp.get<int32_t>(n1);
-  const int64_t n_chunks = (n + kChunk - 1) / kChunk;
   double* hp = tmp.get<double>(kPieceDoubles * n1);
   double* cr = tmp.get<double>(kPieceDoubles * n_chunks);
   if (!L.c || !L.key || !L.scan || !hp || !cr) return vfail(BA_ERR_OOM, "voxelize: out of device memory");
   tm.begin(BA_VOX_CLUSTER_PASS);
-  l1_pieces_kernel<K><<<blocks_for(n_chunks), 256, 0, st>>>(n, keys, vals, pscan, pts, pos, hp, cr, L.key, L.scan);
+  l1_pieces_kernel<K><<<blocks_for(n_chunks), 256, 0, st>>>(n, keys, vals, pscan, pts, base, hmask, hp, cr, L.key,
+                                                              L.scan);
   tm.end();
   tm.begin(BA_VOX_CLUSTER_FINISH);
   l1_finish_kernel<<<blocks_for(n1), 256, 0, st>>>(n1, start, hp, cr, L.c);
@@ -833,9 +875,10 @@ ba_status level_up(const Level& ch, Level& P, int32_t n_scans, Buf& tmp, cudaStr
   else
     VCK(radix_sort_pairs64((uint64_t*)k2, cv, (uint64_t*)t2, tcv, nc, pack_bits(P.pk), scr, st, launches),
         "voxelize sort");
-  int64_t *pos = nullptr, *pst = nullptr;
+  int64_t *base = nullptr, *pst = nullptr;
+  uint32_t* hmask = nullptr;
   int64_t np = 0;
-  ba_status s = group_starts<K>(nc, k2, cv, ch.scan, tmp, &pos, &pst, &np, st, launches);
+  ba_status s = group_starts<K>(nc, k2, cv, ch.scan, tmp, &hmask, &base, &pst, &np, st, launches);
   if (s != BA_OK) return s;
   P.nc = np;
   P.c = tmp.get<double>(10 * np);
