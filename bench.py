@@ -764,7 +764,7 @@ def run_voxelize(args):
         r = mm.voxelize(host(spo_p), host(P_p), host(T_p), **cfg)
     e2e_s = (time.perf_counter() - t0) / steps
     h2d = spo_p.numel() * 8 + P_p.numel() * 8 + T_p.numel() * 8
-    d2h = sum(a.nbytes for k, a in r.items() if k != "launches")
+    d2h = sum(a.nbytes for a in r.values() if hasattr(a, "nbytes"))
     hbm, src = hbm_peak()
     # the level-1 sort runs ceil(bits / 8) passes over the packed keys
     span = _world_index_range(P_p.numpy(), spo_h, s.pose_init[:n_scans], cfg["voxel_size"])
@@ -801,7 +801,10 @@ def run_voxelize(args):
         "data": "synthetic", "points": n_pts, "voxels_out": int(v["level"].numel()),
         "obs_out": int(v["obs_scan"].numel()), "gpu_launches": int(launches), "clocks": clk,
         "e2e": {"value": n_pts / e2e_s, "unit": "points/s", "h2d_bytes_per_step": int(h2d),
-                "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_s * 1000.0},
+                "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_s * 1000.0,
+                "scope": "ba_voxelize from pinned host points (adaptive loader: batches copied on a second "
+                         "stream under the clustering) + ba_voxels_read to host",
+                "loader_batches": int(r["batches"])},
         "roofline": roof,
         "stages_ms": {k2: round(x, 3) for k2, x in stage_ms.items()},
         "stage_rooflines": {k2: {"frac": round(x["frac"], 3), "bound": x["bound"]} for k2, x in rl.items()},

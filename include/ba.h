@@ -341,7 +341,17 @@ ba_status ba_aggregate_points(int64_t n_obs, const int64_t* point_offsets, const
  * the observations of a voxel by scan; voxel_off / obs_scan / agg (centred,
  * scan coordinates) load directly with ba_load_observations(BA_AGG_CENTRED).
  * Indices must lie in [-2^20, 2^20) (BA_ERR_CAPACITY otherwise); at most
- * 2^32 - 1 points per call. */
+ * 2^32 - 1 points per call.
+ * Adaptive asynchronous loader (Sec. IV-B): points in host memory, or more
+ * points than one batch holds, are processed in batches of whole scans (a
+ * scan longer than a batch is split) of batch_points points, or of the share
+ * alpha of the free device memory.  Host batches are copied on a separate
+ * stream, by a library thread, into two device buffers while the previous
+ * batch is clustered, so only two batches of points are ever on the device;
+ * the batches' level-1 clusters are then ordered by one sort and the pieces
+ * of split scans merged.  Pinned host memory lets the copies run at full
+ * speed; pageable memory works too.  The result does not depend on the
+ * batching beyond the rounding of clusters of split scans. */
 typedef struct {
   double voxel_size;  /* d, the level-1 voxel edge (default 1.0) */
   int32_t levels;     /* L >= 1 (default 1) */
@@ -350,6 +360,8 @@ typedef struct {
   int32_t device;     /* CUDA device (default 0) */
   void* cuda_stream;  /* cudaStream_t (NULL = legacy default) */
   int32_t profile;    /* nonzero: time the stages with CUDA events (default 0) */
+  int64_t batch_points; /* points per batch of the loader (0 = from alpha) */
+  double alpha;         /* share of free device memory for point batches (default 0.25) */
 } ba_voxelize_config;
 
 /* Stages timed when profile is set (ba_voxels_stage_ms): world points and
@@ -357,7 +369,8 @@ typedef struct {
  * runs of the sorted points (includes one host synchronisation); the
  * clusters' chunked sums; their per-run finish; all higher levels (includes
  * host synchronisations); the selection's per-observation terms and
- * per-voxel test; the output writes. */
+ * per-voxel test; the output writes; the ordering of the batches' level-1
+ * clusters (batched calls only). */
 enum {
   BA_VOX_KEYS = 0,
   BA_VOX_SORT = 1,
@@ -367,7 +380,8 @@ enum {
   BA_VOX_LEVELS = 5,
   BA_VOX_SELECT = 6,
   BA_VOX_EMIT = 7,
-  BA_VOX_STAGES = 8
+  BA_VOX_MERGE = 8,
+  BA_VOX_STAGES = 9
 };
 
 typedef struct ba_voxels ba_voxels;
@@ -388,6 +402,8 @@ ba_status ba_voxels_size(const ba_voxels* v, int64_t* n_voxels, int64_t* n_obs);
 ba_status ba_voxels_read(const ba_voxels* v, int64_t* voxel_off, int32_t* obs_scan, double* agg, int32_t* level,
                          int32_t* index, int32_t mem_kind);
 int64_t ba_voxels_kernel_launches(const ba_voxels* v);
+/* Number of loader batches the call used (0 when there were no points). */
+int64_t ba_voxels_batches(const ba_voxels* v);
 /* Device milliseconds of one stage (summed over levels) of the call that made
  * v; 0 when it was not profiled.  BA_ERR_INVALID_ARG for a bad stage. */
 ba_status ba_voxels_stage_ms(const ba_voxels* v, int32_t stage, double* ms);

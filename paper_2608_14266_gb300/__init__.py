@@ -295,14 +295,15 @@ class Batch:
 
 
 def voxelize(scan_point_off, points, poses, voxel_size, levels=1, tau=0.0, min_obs=1, device=0, stream=None,
-             out="host", profile=False):
+             out="host", profile=False, batch_points=0, alpha=0.25):
     """Raw scans -> voxel-major observations (ba_voxelize, include/ba.h).
 
     Points of scan j are points[scan_point_off[j]:scan_point_off[j+1]] (scan
     frame); inputs are all numpy (host) or all CUDA tensors (device).  Returns
     a dict voxel_off, obs_scan, agg (centred), level, index, as numpy arrays
     (out="host") or CUDA tensors (out="device"), plus the kernel launch count
-    and, with profile=True, "stage_ms": device milliseconds per stage."""
+    and, with profile=True, "stage_ms": device milliseconds per stage.
+    batch_points / alpha size the loader's batches (include/ba.h)."""
     spo, pts, T = _Arg(scan_point_off, np.int64), _Arg(points, np.float64), _Arg(poses, np.float64)
     mk = _mem_kind(spo, pts, T)
     cfg = _lib.BaVoxelizeConfig()
@@ -310,6 +311,7 @@ def voxelize(scan_point_off, points, poses, voxel_size, levels=1, tau=0.0, min_o
     cfg.voxel_size, cfg.levels, cfg.tau, cfg.min_obs, cfg.device = float(voxel_size), int(levels), float(tau), \
         int(min_obs), int(device)
     cfg.profile = 1 if profile else 0
+    cfg.batch_points, cfg.alpha = int(batch_points), float(alpha)
     if stream is not None:
         cfg.cuda_stream = stream if isinstance(stream, int) else stream.cuda_stream
     v = ctypes.c_void_p()
@@ -340,6 +342,7 @@ def voxelize(scan_point_off, points, poses, voxel_size, levels=1, tau=0.0, min_o
         if status != _lib.BA_OK:
             raise BAError(status, (_lib.lib().ba_voxelize_last_error() or b"").decode())
         res["launches"] = int(_lib.lib().ba_voxels_kernel_launches(v))
+        res["batches"] = int(_lib.lib().ba_voxels_batches(v))
         if profile:
             ms = ctypes.c_double()
             res["stage_ms"] = {}

@@ -44,7 +44,7 @@ class BaStats(ctypes.Structure):
 
 class BaVoxelizeConfig(ctypes.Structure):
     _fields_ = [("voxel_size", _D), ("levels", _I32), ("tau", _D), ("min_obs", _I32), ("device", _I32),
-                ("cuda_stream", _P), ("profile", _I32)]
+                ("cuda_stream", _P), ("profile", _I32), ("batch_points", _I64), ("alpha", _D)]
 
 
 class BaJobDesc(ctypes.Structure):
@@ -102,6 +102,7 @@ _SIGNATURES = {
     "ba_voxels_read": (_I32, [_P, _P, _P, _P, _P, _P, _I32]),
     "ba_voxels_kernel_launches": (_I64, [_P]),
     "ba_voxels_stage_ms": (_I32, [_P, _I32, _P]),
+    "ba_voxels_batches": (_I64, [_P]),
     "ba_voxelize_last_error": (ctypes.c_char_p, []),
     "ba_voxels_destroy": (None, [_P]),
     "ba_device_bytes": (_I64, [_P]),
@@ -109,7 +110,7 @@ _SIGNATURES = {
 }
 BA_NOALLOC_MAX_VOXELS = 8388608
 BA_KERNEL_VOXEL_PASS, BA_KERNEL_SCAN_PASS, BA_KERNEL_SOLVE, BA_KERNEL_DECIDE = 0, 1, 2, 3
-VOX_STAGES = ("keys", "sort", "runs", "cluster_pass", "cluster_finish", "levels", "select", "emit")
+VOX_STAGES = ("keys", "sort", "runs", "cluster_pass", "cluster_finish", "levels", "select", "emit", "merge")
 KERNEL_KINDS = {"voxel_pass": 0, "scan_pass": 1, "solve": 2, "decide": 3}
 
 _lock = threading.Lock()

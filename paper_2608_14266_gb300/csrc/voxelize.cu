@@ -15,6 +15,9 @@
 
 #include <algorithm>
 #include <climits>
+#include <condition_variable>
+#include <mutex>
+#include <thread>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -103,17 +106,19 @@ __global__ void scaled_poses_kernel(int32_t n_scans, const double* poses, double
 
 // L1 (Eq. 4): world point w = R p + t, index floor(w / d), raw key; the
 // index bounding box (one atomic per block) and the first point whose index
-// leaves the key range.  Grid-stride over points.
+// leaves the key range.  Grid-stride over the n points of a batch starting
+// at global point p0 (pts, keys, vals and pscan are indexed within the batch).
 __global__ void __launch_bounds__(256) l1_keys_kernel(int32_t n_scans, const int64_t* spo, const double* pts,
-                                                      const double* poses, const double* sposes, double d, int64_t n,
-                                                      uint64_t* keys, uint32_t* vals, int32_t* pscan, long long* bad,
-                                                      int* bbox) {
+                                                      const double* poses, const double* sposes, double d, int64_t p0,
+                                                      int64_t n, uint64_t* keys, uint32_t* vals, int32_t* pscan,
+                                                      long long* bad, int* bbox) {
   int mn[3] = {INT_MAX, INT_MAX, INT_MAX}, mx[3] = {INT_MIN, INT_MIN, INT_MIN};
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    int lo = 0, hi = n_scans;  // the scan of point i: the last j with spo[j] <= i
+    const int64_t gi = p0 + i;
+    int lo = 0, hi = n_scans;  // the scan of point gi: the last j with spo[j] <= gi
     while (hi - lo > 1) {
       const int mid = (lo + hi) >> 1;
-      if (spo[mid] <= i)
+      if (spo[mid] <= gi)
         lo = mid;
       else
         hi = mid;
@@ -136,7 +141,7 @@ __global__ void __launch_bounds__(256) l1_keys_kernel(int32_t n_scans, const int
       ok = ok && oka;
     }
     if (!ok) {
-      atomicMin(bad, (long long)i);
+      atomicMin(bad, (long long)gi);
     } else {
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
@@ -317,7 +322,8 @@ __device__ __forceinline__ void piece_finish(const Piece& P, double* c) {
 constexpr int kChunk = 32;  // sorted points per thread
 
 // L1 clusters, pass 1: each thread sums a chunk of kChunk = 32 sorted points,
-// one piece per (key, scan) run; hmask[chunk] flags the run heads of the
+// one piece per (key, scan) run (its key: the packed key, or raw[point] if
+// raw is given); hmask[chunk] flags the run heads of the
 // chunk and base[chunk] counts the heads before it.  The piece where a run starts
 // goes to head_piece[run], the piece of a run continuing from the previous
 // chunk to carry[chunk]; counts are stored as integers (no FP64 work in the
@@ -326,8 +332,9 @@ constexpr int kChunk = 32;  // sorted points per thread
 template <typename K>
 __global__ void __launch_bounds__(256, 2) l1_pieces_kernel(int64_t n, const K* keys, const uint32_t* vals,
                                                         const int32_t* pscan, const double* pts, const int64_t* base,
-                                                        const uint32_t* hmask, double* head_piece, double* carry,
-                                                        uint64_t* ckey, int32_t* cscan) {
+                                                        const uint32_t* hmask, const uint64_t* raw,
+                                                        double* head_piece, double* carry, uint64_t* ckey,
+                                                        int32_t* cscan) {
   static_assert(kChunk == 32, "one head-mask word per chunk");
   const int64_t ch = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t e0 = ch * kChunk;
@@ -372,7 +379,7 @@ __global__ void __launch_bounds__(256, 2) l1_pieces_kernel(int64_t n, const K* k
         }
         ++g;
         cnt = 0;
-        ckey[g] = (uint64_t)keys[e];
+        ckey[g] = raw ? raw[v[k]] : (uint64_t)keys[e];
         cscan[g] = pscan[v[k]];
       }
       first = false;
@@ -463,6 +470,25 @@ __global__ void merge_kernel(int64_t np, const int64_t* start, const uint32_t* v
   piece_finish(acc, c + 10 * g);
   ckey[g] = (uint64_t)pkeys_sorted[a];
   oscan[g] = cscan[vals[a]];
+}
+
+// batched level 1: clusters of all batches in (key, scan) order (vals = the
+// sorted order of the concatenated batches' clusters)
+template <typename K>
+__global__ void gather_clusters_kernel(int64_t m, const uint32_t* vals, const K* keys, const double* c_in,
+                                       const int32_t* scan_in, double* c, uint64_t* ckey, int32_t* cscan) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  const int64_t src = vals[i];
+#pragma unroll
+  for (int q = 0; q < 10; ++q) c[10 * i + q] = c_in[10 * src + q];
+  ckey[i] = (uint64_t)keys[i];
+  cscan[i] = scan_in[src];
+}
+
+__global__ void iota_kernel(int64_t n, uint32_t* v) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) v[i] = (uint32_t)i;
 }
 
 // voxels of a level: runs of equal key among its clusters (sorted by key, scan)
@@ -800,9 +826,10 @@ struct Level {
 };
 
 // level 1: raw keys -> packed keys, sort, (key, scan) runs, clusters
+// (the clusters go to out, the rest to tmp; raw_keys: clusters keep raw keys)
 template <typename K>
 ba_status level1(int64_t n, const uint64_t* raw, uint32_t* vals, const int32_t* pscan, const double* pts, Level& L,
-                 Buf& tmp, StageTimer& tm, cudaStream_t st, int64_t* launches) {
+                 bool raw_keys, Buf& out, Buf& tmp, StageTimer& tm, cudaStream_t st, int64_t* launches) {
   K* keys = tmp.get<K>(n);
   K* tkeys = tmp.get<K>(n);
   uint32_t* tvals = tmp.get<uint32_t>(n);
@@ -829,15 +856,15 @@ ba_status level1(int64_t n, const uint64_t* raw, uint32_t* vals, const int32_t* 
   tm.end();
   if (s != BA_OK) return s;
   L.nc = n1;
-  L.c = tmp.get<double>(10 * n1);
-  L.key = tmp.get<uint64_t>(n1);
-  L.scan = tmp.get<int32_t>(n1);
+  L.c = out.get<double>(10 * n1);
+  L.key = out.get<uint64_t>(n1);
+  L.scan = out.get<int32_t>(n1);
   double* hp = tmp.get<double>(kPieceDoubles * n1);
   double* cr = tmp.get<double>(kPieceDoubles * n_chunks);
   if (!L.c || !L.key || !L.scan || !hp || !cr) return vfail(BA_ERR_OOM, "voxelize: out of device memory");
   tm.begin(BA_VOX_CLUSTER_PASS);
-  l1_pieces_kernel<K><<<blocks_for(n_chunks), 256, 0, st>>>(n, keys, vals, pscan, pts, base, hmask, hp, cr, L.key,
-                                                              L.scan);
+  l1_pieces_kernel<K><<<blocks_for(n_chunks), 256, 0, st>>>(n, keys, vals, pscan, pts, base, hmask,
+                                                              raw_keys ? raw : nullptr, hp, cr, L.key, L.scan);
   tm.end();
   tm.begin(BA_VOX_CLUSTER_FINISH);
   l1_finish_kernel<<<blocks_for(n1), 256, 0, st>>>(n1, start, hp, cr, L.c);
@@ -891,6 +918,292 @@ ba_status level_up(const Level& ch, Level& P, int32_t n_scans, Buf& tmp, cudaStr
   return BA_OK;
 }
 
+// ---- level 1 over a point range, and the adaptive loader ---------------------
+struct L1Ctx {
+  int32_t n_scans;
+  const int64_t* spo;     // device, n_scans + 1
+  const double* T;        // device poses
+  const double* sposes;   // device poses / d
+  double d;
+  long long* bad;         // device: bad[2] = first point out of the key range
+  int* bbox;              // device scratch, 6 ints
+  int n_sm;
+  cudaStream_t st;
+  StageTimer* tm;
+  int64_t* launches;
+};
+
+// level-1 clusters of the points [p0, p0 + m) at pts (device): keys, sort,
+// runs, cluster sums.  bb receives the range's index box; raw_keys: the
+// clusters carry raw keys (batches are merged later), else keys packed to bb.
+ba_status l1_range(const L1Ctx& c, int64_t p0, int64_t m, const double* pts, bool raw_keys, Level& L, int* bb,
+                   Buf& out, Buf& tmp) {
+  uint64_t* raw = tmp.get<uint64_t>(m);
+  uint32_t* vals = tmp.get<uint32_t>(m);
+  int32_t* pscan = tmp.get<int32_t>(m);
+  if (!raw || !vals || !pscan) return vfail(BA_ERR_OOM, "voxelize: out of device memory");
+  const int bb_init[6] = {INT_MAX, INT_MAX, INT_MAX, INT_MIN, INT_MIN, INT_MIN};
+  const long long none = LLONG_MAX;
+  VCK(cudaMemcpyAsync(c.bbox, bb_init, sizeof bb_init, cudaMemcpyHostToDevice, c.st), "voxelize");
+  VCK(cudaMemcpyAsync(c.bad + 2, &none, sizeof none, cudaMemcpyHostToDevice, c.st), "voxelize");
+  const int64_t key_blocks = std::min<int64_t>(blocks_for(m), (int64_t)c.n_sm * 8);
+  c.tm->begin(BA_VOX_KEYS);
+  l1_keys_kernel<<<(unsigned)key_blocks, 256, 0, c.st>>>(c.n_scans, c.spo, pts, c.T, c.sposes, c.d, p0, m, raw, vals,
+                                                          pscan, c.bad + 2, c.bbox);
+  c.tm->end();
+  ++*c.launches;
+  VCK(cudaGetLastError(), "voxelize keys");
+  long long b2 = 0;
+  VCK(cudaMemcpyAsync(&b2, c.bad + 2, sizeof b2, cudaMemcpyDeviceToHost, c.st), "voxelize");
+  VCK(cudaMemcpyAsync(bb, c.bbox, 6 * sizeof(int), cudaMemcpyDeviceToHost, c.st), "voxelize");
+  VCK(cudaStreamSynchronize(c.st), "voxelize");
+  if (b2 != LLONG_MAX)
+    return vfail(BA_ERR_CAPACITY, "point %lld lies outside the voxel index range [-2^20, 2^20) at this voxel size",
+                 b2);
+  L.pk = make_pack(bb, bb + 3);
+  return pack_bits(L.pk) <= 32 ? level1<uint32_t>(m, raw, vals, pscan, pts, L, raw_keys, out, tmp, *c.tm, c.st,
+                                                  c.launches)
+                               : level1<uint64_t>(m, raw, vals, pscan, pts, L, raw_keys, out, tmp, *c.tm, c.st,
+                                                  c.launches);
+}
+
+ba_status l1_single(const L1Ctx& c, int64_t n, const double* pts, Level& L, int* bb, Buf& tmp) {
+  return l1_range(c, 0, n, pts, false, L, bb, tmp, tmp);
+}
+
+struct Batch {
+  int64_t p0, p1;
+};
+
+// points per batch: batch_points if set; else the share alpha of the free
+// device memory at kBatchBytesPerPoint per point in flight (two point buffers
+// and the batch's keys, indices, sort and cluster temporaries); host inputs
+// get at least four batches so that copies run under the clustering
+constexpr int64_t kBatchBytesPerPoint = 2 * 24 + 96;
+
+int64_t batch_size(const ba_voxelize_config* cfg, int64_t n, int32_t mem_kind) {
+  if (cfg->batch_points > 0) return cfg->batch_points;
+  size_t fr = 0, tot = 0;
+  if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+    cudaGetLastError();
+    fr = 0;
+  }
+  int64_t B = std::max<int64_t>((int64_t)(cfg->alpha * (double)fr / (double)kBatchBytesPerPoint), 1ll << 20);
+  if (mem_kind == BA_MEM_HOST) B = std::min<int64_t>(B, std::max<int64_t>((n + 3) / 4, 1ll << 22));
+  return B;
+}
+
+// consecutive point ranges of at most B points, ending at scan boundaries
+// where a boundary lies in the range (a scan longer than B is split)
+std::vector<Batch> plan_batches(const std::vector<int64_t>& spo, int64_t B) {
+  std::vector<Batch> plan;
+  const int64_t n = spo.back();
+  int64_t p = 0;
+  while (p < n) {
+    int64_t e = std::min(p + B, n);
+    if (e < n) {
+      auto it = std::upper_bound(spo.begin(), spo.end(), e);  // first offset > e
+      const int64_t snap = *(it - 1);                        // last offset <= e
+      if (snap > p) e = snap;
+    }
+    plan.push_back({p, e});
+    p = e;
+  }
+  return plan;
+}
+
+// level-1 clusters of all batches in (key, scan) order: one stable sort of
+// the concatenated clusters by the globally packed key, then either a gather
+// or, where a scan was split between batches, a merge of its pieces
+template <typename K>
+ba_status assemble_batches(const L1Ctx& c, int64_t m, const double* c_all, const uint64_t* raw_all,
+                           const int32_t* scan_all, bool any_split, Level& L, Buf& out, Buf& tmp) {
+  K* keys = tmp.get<K>(m);
+  K* tkeys = tmp.get<K>(m);
+  uint32_t* vals = tmp.get<uint32_t>(m);
+  uint32_t* tvals = tmp.get<uint32_t>(m);
+  int64_t* scr = tmp.get<int64_t>(radix_scratch_count(m));
+  if (!keys || !tkeys || !vals || !tvals || !scr) return vfail(BA_ERR_OOM, "voxelize: out of device memory");
+  repack_kernel<K><<<blocks_for(m), 256, 0, c.st>>>(m, raw_all, L.pk, keys);
+  iota_kernel<<<blocks_for(m), 256, 0, c.st>>>(m, vals);
+  *c.launches += 2;
+  VCK(cudaGetLastError(), "voxelize merge");
+  if (sizeof(K) == 4)
+    VCK(radix_sort_pairs((uint32_t*)keys, vals, (uint32_t*)tkeys, tvals, m, pack_bits(L.pk), scr, c.st, c.launches),
+        "voxelize sort");
+  else
+    VCK(radix_sort_pairs64((uint64_t*)keys, vals, (uint64_t*)tkeys, tvals, m, pack_bits(L.pk), scr, c.st,
+                           c.launches),
+        "voxelize sort");
+  if (!any_split) {
+    L.nc = m;
+    L.c = out.get<double>(10 * m);
+    L.key = out.get<uint64_t>(m);
+    L.scan = out.get<int32_t>(m);
+    if (!L.c || !L.key || !L.scan) return vfail(BA_ERR_OOM, "voxelize: out of device memory");
+    gather_clusters_kernel<K><<<blocks_for(m), 256, 0, c.st>>>(m, vals, keys, c_all, scan_all, L.c, L.key, L.scan);
+    ++*c.launches;
+    VCK(cudaGetLastError(), "voxelize merge");
+    return BA_OK;
+  }
+  uint32_t* hmask = nullptr;
+  int64_t *base = nullptr, *start = nullptr;
+  int64_t ng = 0;
+  ba_status s = group_starts<K>(m, keys, vals, scan_all, tmp, &hmask, &base, &start, &ng, c.st, c.launches);
+  if (s != BA_OK) return s;
+  L.nc = ng;
+  L.c = out.get<double>(10 * ng);
+  L.key = out.get<uint64_t>(ng);
+  L.scan = out.get<int32_t>(ng);
+  if (!L.c || !L.key || !L.scan) return vfail(BA_ERR_OOM, "voxelize: out of device memory");
+  merge_kernel<K><<<blocks_for(ng), 256, 0, c.st>>>(ng, start, vals, c_all, keys, scan_all, L.c, L.key, L.scan);
+  ++*c.launches;
+  VCK(cudaGetLastError(), "voxelize merge");
+  return BA_OK;
+}
+
+// Host points: a thread issues each batch's copy on a copy stream into one of
+// two device buffers (after the clustering of the batch that used the buffer
+// before has been enqueued), while this thread clusters the previous batch.
+struct CopyPipeline {
+  cudaStream_t cs = nullptr;
+  std::vector<cudaEvent_t> copied, freed;
+  std::mutex mu;
+  std::condition_variable cv;
+  int issued = 0, released = 0;
+  bool stop = false;
+  cudaError_t err = cudaSuccess;
+  std::thread th;
+  ~CopyPipeline() {
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      stop = true;
+    }
+    cv.notify_all();
+    if (th.joinable()) th.join();
+    if (cs) cudaStreamSynchronize(cs);
+    for (cudaEvent_t e : copied)
+      if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : freed)
+      if (e) cudaEventDestroy(e);
+    if (cs) cudaStreamDestroy(cs);
+  }
+};
+
+// any_split: some batch edge lies inside a scan
+ba_status l1_batched(const L1Ctx& c, const std::vector<Batch>& plan, bool any_split, const double* points,
+                     int32_t mem_kind, int device, Level& L, int* bb, Buf& out) {
+  const int nb = (int)plan.size();
+  std::vector<Level> part(nb);
+  int64_t maxb = 0, m = 0;
+  for (const Batch& b : plan) maxb = std::max(maxb, b.p1 - b.p0);
+  for (int a = 0; a < 3; ++a) {
+    bb[a] = INT_MAX;
+    bb[3 + a] = INT_MIN;
+  }
+  auto one = [&](int k, const double* pts) -> ba_status {
+    Buf btmp(c.st, device);
+    int bk[6];
+    ba_status s = l1_range(c, plan[k].p0, plan[k].p1 - plan[k].p0, pts, true, part[k], bk, out, btmp);
+    if (s != BA_OK) return s;
+    for (int a = 0; a < 3; ++a) {
+      bb[a] = std::min(bb[a], bk[a]);
+      bb[3 + a] = std::max(bb[3 + a], bk[3 + a]);
+    }
+    m += part[k].nc;
+    return BA_OK;
+  };
+  if (mem_kind == BA_MEM_DEVICE) {
+    for (int k = 0; k < nb; ++k) {
+      ba_status s = one(k, points + 3 * plan[k].p0);
+      if (s != BA_OK) return s;
+    }
+  } else {
+    double* buf[2] = {out.get<double>(3 * maxb), nb > 1 ? out.get<double>(3 * maxb) : nullptr};
+    if (!buf[0] || (nb > 1 && !buf[1])) return vfail(BA_ERR_OOM, "voxelize point buffers: out of device memory");
+    VCK(cudaStreamSynchronize(c.st), "voxelize");  // buffers allocated before the copy stream uses them
+    CopyPipeline cp;
+    VCK(cudaStreamCreateWithFlags(&cp.cs, cudaStreamNonBlocking), "voxelize copy stream");
+    cp.copied.assign(nb, nullptr);
+    cp.freed.assign(nb, nullptr);
+    for (int k = 0; k < nb; ++k) {
+      VCK(cudaEventCreateWithFlags(&cp.copied[k], cudaEventDisableTiming), "voxelize");
+      VCK(cudaEventCreateWithFlags(&cp.freed[k], cudaEventDisableTiming), "voxelize");
+    }
+    cp.th = std::thread([&cp, &plan, points, buf, nb, device]() {
+      cudaSetDevice(device);
+      for (int k = 0; k < nb; ++k) {
+        {
+          std::unique_lock<std::mutex> lk(cp.mu);
+          cp.cv.wait(lk, [&] { return cp.stop || k < 2 || cp.released >= k - 1; });
+          if (cp.stop) return;
+        }
+        cudaError_t e = cudaSuccess;
+        if (k >= 2) e = cudaStreamWaitEvent(cp.cs, cp.freed[k - 2], 0);
+        if (e == cudaSuccess)
+          e = cudaMemcpyAsync(buf[k & 1], points + 3 * plan[k].p0, sizeof(double) * 3 * (plan[k].p1 - plan[k].p0),
+                              cudaMemcpyHostToDevice, cp.cs);
+        if (e == cudaSuccess) e = cudaEventRecord(cp.copied[k], cp.cs);
+        {
+          std::lock_guard<std::mutex> lk(cp.mu);
+          if (e != cudaSuccess) {
+            cp.err = e;
+            cp.stop = true;
+          } else {
+            cp.issued = k + 1;
+          }
+        }
+        cp.cv.notify_all();
+        if (e != cudaSuccess) return;
+      }
+    });
+    for (int k = 0; k < nb; ++k) {
+      {
+        std::unique_lock<std::mutex> lk(cp.mu);
+        cp.cv.wait(lk, [&] { return cp.err != cudaSuccess || cp.issued > k; });
+        if (cp.err != cudaSuccess) {
+          cudaGetLastError();
+          return vfail(cp.err == cudaErrorMemoryAllocation ? BA_ERR_OOM : BA_ERR_CUDA, "voxelize copy: %s",
+                       cudaGetErrorString(cp.err));
+        }
+      }
+      VCK(cudaStreamWaitEvent(c.st, cp.copied[k], 0), "voxelize");
+      ba_status s = one(k, buf[k & 1]);
+      if (s != BA_OK) return s;
+      VCK(cudaEventRecord(cp.freed[k], c.st), "voxelize");
+      {
+        std::lock_guard<std::mutex> lk(cp.mu);
+        cp.released = k + 1;
+      }
+      cp.cv.notify_all();
+    }
+  }
+  // concatenate and order the batches' clusters
+  c.tm->begin(BA_VOX_MERGE);
+  Buf atmp(c.st, device);
+  double* c_all = atmp.get<double>(10 * m);
+  uint64_t* raw_all = atmp.get<uint64_t>(m);
+  int32_t* scan_all = atmp.get<int32_t>(m);
+  if (!c_all || !raw_all || !scan_all) return vfail(BA_ERR_OOM, "voxelize: out of device memory");
+  int64_t o = 0;
+  for (int k = 0; k < nb; ++k) {
+    const int64_t q = part[k].nc;
+    if (q == 0) continue;
+    VCK(cudaMemcpyAsync(c_all + 10 * o, part[k].c, sizeof(double) * 10 * q, cudaMemcpyDeviceToDevice, c.st),
+        "voxelize");
+    VCK(cudaMemcpyAsync(raw_all + o, part[k].key, sizeof(uint64_t) * q, cudaMemcpyDeviceToDevice, c.st), "voxelize");
+    VCK(cudaMemcpyAsync(scan_all + o, part[k].scan, sizeof(int32_t) * q, cudaMemcpyDeviceToDevice, c.st),
+        "voxelize");
+    o += q;
+  }
+  L.pk = make_pack(bb, bb + 3);
+  ba_status s = pack_bits(L.pk) <= 32
+                    ? assemble_batches<uint32_t>(c, m, c_all, raw_all, scan_all, any_split, L, out, atmp)
+                    : assemble_batches<uint64_t>(c, m, c_all, raw_all, scan_all, any_split, L, out, atmp);
+  c.tm->end();
+  return s;
+}
+
 }  // namespace
 
 struct ba_voxels {
@@ -904,6 +1217,7 @@ struct ba_voxels {
   int64_t launches = 0;
   bool pooled = false;  // arrays from the library pool (stream-ordered frees)
   double stage_ms[BA_VOX_STAGES] = {};
+  int64_t batches = 0;  // loader batches of the call (0: no points)
 };
 
 extern "C" {
@@ -917,6 +1231,8 @@ void ba_voxelize_config_default(ba_voxelize_config* cfg) {
   cfg->device = 0;
   cfg->cuda_stream = nullptr;
   cfg->profile = 0;
+  cfg->batch_points = 0;
+  cfg->alpha = 0.25;
 }
 
 const char* ba_voxelize_last_error(void) { return g_vox_error.c_str(); }
@@ -946,22 +1262,20 @@ ba_status ba_voxelize(const ba_voxelize_config* cfg, int32_t n_scans, const int6
   tm.st = st;
   int64_t launches = 0;
 
-  // stage the inputs
+  // offsets and poses on the device (small); the points stay where they are
   int64_t n = 0;
+  std::vector<int64_t> spo_host;
   const int64_t* spo = scan_point_off;
-  const double *pts = points, *T = poses;
+  const double* T = poses;
   if (mem_kind == BA_MEM_HOST) {
     n = scan_point_off[n_scans];
     if (n < 0) return vfail(BA_ERR_INVALID_ARG, "scan_point_off must end at the point count");
     int64_t* d_spo = tmp.get<int64_t>(n_scans + 1);
-    double* d_pts = tmp.get<double>(3 * n);
     double* d_T = tmp.get<double>(12 * (int64_t)n_scans);
-    if (!d_spo || !d_pts || !d_T) return vfail(BA_ERR_OOM, "voxelize inputs: out of device memory");
+    if (!d_spo || !d_T) return vfail(BA_ERR_OOM, "voxelize inputs: out of device memory");
     VCK(cudaMemcpyAsync(d_spo, spo, sizeof(int64_t) * (n_scans + 1), cudaMemcpyHostToDevice, st), "stage");
-    if (n) VCK(cudaMemcpyAsync(d_pts, pts, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st), "stage");
     VCK(cudaMemcpyAsync(d_T, T, sizeof(double) * 12 * n_scans, cudaMemcpyHostToDevice, st), "stage");
     spo = d_spo;
-    pts = d_pts;
     T = d_T;
   } else {
     VCK(cudaMemcpyAsync(&n, scan_point_off + n_scans, sizeof n, cudaMemcpyDeviceToHost, st), "read point count");
@@ -970,8 +1284,10 @@ ba_status ba_voxelize(const ba_voxelize_config* cfg, int32_t n_scans, const int6
   }
   if (n >= (1ll << 32)) return vfail(BA_ERR_CAPACITY, "at most 2^32 - 1 points per call");
   if (n > 0 && !points) return vfail(BA_ERR_INVALID_ARG, "NULL points");
+  if (cfg->batch_points < 0) return vfail(BA_ERR_INVALID_ARG, "batch_points must be >= 0");
+  if (!(cfg->alpha > 0.0 && cfg->alpha <= 1.0)) return vfail(BA_ERR_INVALID_ARG, "alpha must be in (0, 1]");
 
-  // validation of the offsets and poses, then the L1 keys
+  // validation of the offsets and poses
   long long* bad = tmp.get<long long>(3);
   if (!bad) return vfail(BA_ERR_OOM, "voxelize: out of device memory");
   const long long init[3] = {LLONG_MAX, LLONG_MAX, LLONG_MAX};
@@ -988,45 +1304,49 @@ ba_status ba_voxelize(const ba_voxelize_config* cfg, int32_t n_scans, const int6
   if (res[1] != LLONG_MAX) return vfail(BA_ERR_INVALID_ARG, "pose %lld is not finite", res[1]);
 
   std::vector<Level> lv(cfg->levels);
+  int64_t n_batches = 0;
   if (n > 0) {
-    uint64_t* raw = tmp.get<uint64_t>(n);
-    uint32_t* vals = tmp.get<uint32_t>(n);
-    int32_t* pscan = tmp.get<int32_t>(n);
-    int* bbox = tmp.get<int>(6);
-    if (!raw || !vals || !pscan || !bbox) return vfail(BA_ERR_OOM, "voxelize: out of device memory");
-    const int bb_init[6] = {INT_MAX, INT_MAX, INT_MAX, INT_MIN, INT_MIN, INT_MIN};
-    VCK(cudaMemcpyAsync(bbox, bb_init, sizeof bb_init, cudaMemcpyHostToDevice, st), "voxelize");
     double* sposes = tmp.get<double>(12 * (int64_t)n_scans);
-    if (!sposes) return vfail(BA_ERR_OOM, "voxelize: out of device memory");
+    int* bbox = tmp.get<int>(6);
+    if (!sposes || !bbox) return vfail(BA_ERR_OOM, "voxelize: out of device memory");
     scaled_poses_kernel<<<blocks_for(12 * (int64_t)n_scans), 256, 0, st>>>(n_scans, T, 1.0 / cfg->voxel_size, sposes);
+    ++launches;
     int n_sm = 0;
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, cfg->device);
-    const int64_t key_blocks = std::min<int64_t>(blocks_for(n), (int64_t)(n_sm > 0 ? n_sm : 1) * 8);
-    tm.begin(BA_VOX_KEYS);
-    l1_keys_kernel<<<(unsigned)key_blocks, 256, 0, st>>>(n_scans, spo, pts, T, sposes, cfg->voxel_size, n, raw, vals,
-                                                          pscan, bad + 2, bbox);
-    tm.end();
-    launches += 2;
-    VCK(cudaGetLastError(), "voxelize keys");
+    L1Ctx ctx{n_scans, spo, T, sposes, cfg->voxel_size, bad, bbox, n_sm > 0 ? n_sm : 1, st, &tm, &launches};
+    // the adaptive loader (Sec. IV-B): batches of whole scans sized by alpha
+    const int64_t B = batch_size(cfg, n, mem_kind);
     int bb[6];
-    VCK(cudaMemcpyAsync(res + 2, bad + 2, sizeof(long long), cudaMemcpyDeviceToHost, st), "voxelize");
-    VCK(cudaMemcpyAsync(bb, bbox, sizeof bb, cudaMemcpyDeviceToHost, st), "voxelize");
-    VCK(cudaStreamSynchronize(st), "voxelize");
-    if (res[2] != LLONG_MAX)
-      return vfail(BA_ERR_CAPACITY, "point %lld lies outside the voxel index range [-2^20, 2^20) at this voxel size",
-                   res[2]);
+    ba_status s;
+    if (mem_kind == BA_MEM_DEVICE && n <= B) {
+      n_batches = 1;
+      s = l1_single(ctx, n, points, lv[0], bb, tmp);
+    } else {
+      spo_host.resize(n_scans + 1);
+      if (mem_kind == BA_MEM_HOST) {
+        std::copy(scan_point_off, scan_point_off + n_scans + 1, spo_host.begin());
+      } else {
+        VCK(cudaMemcpyAsync(spo_host.data(), scan_point_off, sizeof(int64_t) * (n_scans + 1), cudaMemcpyDeviceToHost,
+                            st),
+            "voxelize");
+        VCK(cudaStreamSynchronize(st), "voxelize");
+      }
+      const std::vector<Batch> plan = plan_batches(spo_host, B);
+      n_batches = (int64_t)plan.size();
+      bool any_split = false;
+      for (size_t k = 1; k < plan.size(); ++k)
+        any_split = any_split || !std::binary_search(spo_host.begin(), spo_host.end(), plan[k].p0);
+      s = l1_batched(ctx, plan, any_split, points, mem_kind, cfg->device, lv[0], bb, tmp);
+    }
+    if (s != BA_OK) return s;
     for (int k = 0; k < cfg->levels; ++k) {
       Level& L = lv[k];
       for (int a = 0; a < 3; ++a) {
         L.lo[a] = k == 0 ? bb[a] : half_floor(lv[k - 1].lo[a]);
         L.hi[a] = k == 0 ? bb[3 + a] : half_floor(lv[k - 1].hi[a]);
       }
-      L.pk = make_pack(L.lo, L.hi);
+      if (k > 0) L.pk = make_pack(L.lo, L.hi);
     }
-    ba_status s = pack_bits(lv[0].pk) <= 32
-                      ? level1<uint32_t>(n, raw, vals, pscan, pts, lv[0], tmp, tm, st, &launches)
-                      : level1<uint64_t>(n, raw, vals, pscan, pts, lv[0], tmp, tm, st, &launches);
-    if (s != BA_OK) return s;
     // levels 2..L (Eq. 5)
     for (int k = 1; k < cfg->levels; ++k) {
       tm.begin(BA_VOX_LEVELS);
@@ -1134,6 +1454,7 @@ ba_status ba_voxelize(const ba_voxelize_config* cfg, int32_t n_scans, const int6
   }
   VCK(cudaStreamSynchronize(st), "voxelize");
   v->launches = launches;
+  v->batches = n_batches;
   tm.collect(v->stage_ms);
   *out = v;
   v = nullptr;  // handed out
@@ -1168,6 +1489,8 @@ ba_status ba_voxels_read(const ba_voxels* v, int64_t* voxel_off, int32_t* obs_sc
 }
 
 int64_t ba_voxels_kernel_launches(const ba_voxels* v) { return v ? v->launches : 0; }
+
+int64_t ba_voxels_batches(const ba_voxels* v) { return v ? v->batches : 0; }
 
 ba_status ba_voxels_stage_ms(const ba_voxels* v, int32_t stage, double* ms) {
   if (!v || !ms || stage < 0 || stage >= BA_VOX_STAGES) return BA_ERR_INVALID_ARG;

@@ -111,7 +111,7 @@ def test_device_inputs_equal_host_inputs(mm, scans):
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     a = mm.voxelize(spo, P, s.pose_gt, 1.0, levels=2)
     b = mm.voxelize(dev(spo), dev(P), dev(s.pose_gt), 1.0, levels=2, out="device")
-    _same_structure(a, {k: v.cpu().numpy() for k, v in b.items() if k != "launches"})
+    _same_structure(a, {k: v.cpu().numpy() for k, v in b.items() if hasattr(v, "cpu")})
     np.testing.assert_array_equal(a["agg"], b["agg"].cpu().numpy())
 
 
@@ -142,6 +142,47 @@ def test_voxelize_edge_cases_and_errors(mm, scans):
         mm.voxelize(spo, P, s.pose_gt, -1.0)
     with pytest.raises(mm.BAError):
         mm.voxelize(spo, P, s.pose_gt, 1.0, levels=0)
+
+
+@pytest.mark.parametrize("batch", ["whole_scans", "split_scans"])
+def test_loader_batches_match_oracle(mm, scans, batch):
+    """The adaptive loader (Sec. IV-B): host points in batches (whole scans,
+    or batches shorter than a scan so that scans are split and their pieces
+    merged) give the oracle's structure and clusters."""
+    s, spo, P = scans
+    per_scan = int(np.diff(spo).max())
+    bp = 3 * per_scan + 17 if batch == "whole_scans" else max(1, per_scan // 3)
+    got = mm.voxelize(spo, P, s.pose_gt, 1.0, levels=3, batch_points=bp)
+    ref = oracle.voxelize(spo, P, s.pose_gt, 1.0, levels=3)
+    assert got["batches"] >= (len(P) + bp - 1) // bp > 1
+    _same_structure(got, ref)
+    _close_clusters(got, ref, 1.0)
+
+
+def test_loader_device_batches_and_pinned_host(mm, scans):
+    """Device points processed in batches, and pinned host points, equal the
+    single pass in structure; a bad point in a later batch is reported by its
+    global index."""
+    import torch
+    s, spo, P = scans
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    one = mm.voxelize(dev(spo), dev(P), dev(s.pose_gt), 0.5, levels=2, out="device")
+    assert one["batches"] == 1
+    many = mm.voxelize(dev(spo), dev(P), dev(s.pose_gt), 0.5, levels=2, out="device", batch_points=len(P) // 7)
+    assert many["batches"] >= 7
+    _same_structure({k: v.cpu().numpy() for k, v in one.items() if hasattr(v, "cpu")},
+                    {k: v.cpu().numpy() for k, v in many.items() if hasattr(v, "cpu")})
+    pinned = torch.from_numpy(P).pin_memory()
+    h = mm.voxelize(spo, pinned.numpy(), s.pose_gt, 0.5, levels=2, batch_points=len(P) // 5)
+    _same_structure(h, {k: v.cpu().numpy() for k, v in one.items() if hasattr(v, "cpu")})
+    far = P.copy()
+    q = len(P) - 3
+    far[q] = [5.0e6, 0.0, 0.0]
+    with pytest.raises(mm.BAError) as e:
+        mm.voxelize(spo, far, s.pose_gt, 1.0, batch_points=len(P) // 4)
+    assert e.value.status == 7 and f"point {q}" in str(e.value)
+    with pytest.raises(mm.BAError):
+        mm.voxelize(spo, P, s.pose_gt, 1.0, alpha=0.0)
 
 
 def _near(poses, rot_rad, trans_m, seed):
