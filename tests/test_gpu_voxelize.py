@@ -219,3 +219,79 @@ def test_voxelised_scans_solve(mm, scans):
     c_ref, _ = oracle.voxel_pass(prob, poses)
     assert cost == pytest.approx(c_ref, rel=1e-10)
     assert st["accepted"] > 0
+
+
+def _planar_decisions(voxel_off, obs_scan, agg, poses, tau, min_obs, idx):
+    """Keep decision (and whether it is a near-tie) of voxels idx from their
+    clusters at the poses, in FP64 numpy: covariance of the voxel's world
+    points (Eq. 1-2) and numpy.linalg.eigvalsh."""
+    keep, tie = [], []
+    for v in idx:
+        o0, o1 = voxel_off[v], voxel_off[v + 1]
+        if o1 - o0 < min_obs:
+            keep.append(False)
+            tie.append(False)
+            continue
+        c = agg[o0:o1]
+        T = poses[obs_scan[o0:o1]]
+        R, t = T[:, :9].reshape(-1, 3, 3), T[:, 9:]
+        S = c[:, [0, 1, 2, 1, 3, 4, 2, 4, 5]].reshape(-1, 3, 3)
+        w = np.einsum("kab,kb->ka", R, c[:, 6:9]) + t
+        n = c[:, 9]
+        m = (n[:, None] * w).sum(0) / n.sum()
+        d = w - m
+        A = (np.einsum("kab,kbc,kdc->ad", R, S, R) + np.einsum("k,ka,kb->ab", n, d, d)) / n.sum()
+        lam = np.linalg.eigvalsh(A)
+        keep.append(lam[0] < tau * lam[1])
+        tie.append(abs(lam[0] - tau * lam[1]) <= 1e-9 * lam[2])
+    return np.array(keep), np.array(tie)
+
+
+def test_full_size_sampled_parity(mm):
+    """The bench's workload and launch configuration (the 1,000-scan scene's
+    120M raw points on the device, d = 0.5 m, 3 levels, tau = 0.1, min_obs = 2):
+    every observation of three sampled scans equals the oracle run on that
+    scan's points alone (clusters of one scan depend on its points only);
+    sampled voxels' selection decisions equal the FP64 decision from their
+    clusters (up to near-ties); host-batched input gives the same output."""
+    import torch
+    s = scenegen.make_scene(scenegen.config("mid"))
+    npo = s.params.pts_per_obs
+    P = torch.empty((s.n_obs * npo, 3), dtype=torch.float64, device="cuda")
+    s.points_device(0, s.n_obs, P)
+    order = torch.from_numpy(np.argsort(s.obs_scan, kind="stable")).cuda()
+    P = P.view(s.n_obs, npo, 3)[order].reshape(-1, 3).contiguous()
+    counts = np.bincount(s.obs_scan, minlength=s.n_scans) * npo
+    spo = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    dspo, dT = torch.from_numpy(spo).cuda(), torch.from_numpy(s.pose_init).cuda()
+    d, levels, tau, min_obs = 0.5, 3, 0.1, 2
+    host = lambda r: {k: (v.cpu().numpy() if hasattr(v, "cpu") else v) for k, v in r.items()}
+    allv = host(mm.voxelize(dspo, P, dT, d, levels=levels, out="device"))
+    sel = host(mm.voxelize(dspo, P, dT, d, levels=levels, tau=tau, min_obs=min_obs, out="device"))
+    rng = np.random.default_rng(7)
+    vox_of_obs = np.repeat(np.arange(len(allv["level"])), np.diff(allv["voxel_off"]))
+    for j in rng.choice(s.n_scans, 3, replace=False):
+        Pj = P[spo[j]:spo[j + 1]].cpu().numpy()
+        ref = oracle.voxelize(np.array([0, len(Pj)], np.int64), Pj, s.pose_init[j:j + 1], d, levels=levels)
+        mine = np.nonzero(allv["obs_scan"] == j)[0]
+        assert len(mine) == len(ref["level"])
+        v = vox_of_obs[mine]
+        key_got = np.column_stack([allv["level"][v], allv["index"][v]])
+        key_ref = np.column_stack([ref["level"], ref["index"]])
+        np.testing.assert_array_equal(key_got, key_ref)
+        got_one = {"agg": allv["agg"][mine], "level": ref["level"], "voxel_off": np.arange(len(mine) + 1)}
+        _close_clusters(got_one, {"agg": ref["agg"], "level": ref["level"], "voxel_off": np.arange(len(mine) + 1)}, d)
+    # selection: sampled voxels of the unselected output
+    idx = rng.choice(len(allv["level"]), 4000, replace=False)
+    keep, tie = _planar_decisions(allv["voxel_off"], allv["obs_scan"], allv["agg"], s.pose_init, tau, min_obs, idx)
+    kept = {(int(l), *map(int, i)) for l, i in zip(sel["level"], sel["index"])}
+    for v, k, t in zip(idx, keep, tie):
+        if t:
+            continue
+        assert ((int(allv["level"][v]), *map(int, allv["index"][v])) in kept) == k, v
+    assert keep.sum() > 50 and (~keep).sum() > 50
+    # the loader from pinned host memory, in batches
+    Ph = P.cpu().pin_memory()
+    hb = mm.voxelize(spo, Ph.numpy(), s.pose_init, d, levels=levels, tau=tau, min_obs=min_obs)
+    assert hb["batches"] > 1
+    _same_structure(hb, sel)
