@@ -7,6 +7,12 @@
 
 namespace mmba {
 
+// rows of the voxel-pass slots fetched into L2 ahead of the current one
+constexpr int kVoxPrefetch = 2;
+
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
+
 // E x for E = a [phi]x + b [phi]x^2:  a (phi x x) + b (phi x (phi x x))
 __device__ __forceinline__ void apply_E(const float* ph, float a, float b, float x0, float x1, float x2, float& y0,
                                         float& y1, float& y2) {
@@ -67,6 +73,9 @@ __device__ __forceinline__ void voxel_pass_mixed_body(const DevLayout& L, const 
     }
     for (int k = 0; k < len; ++k) {
       const float4 f0 = n0, f1 = n1, f2 = n2;
+      // rows further ahead go to L2 without holding registers (the lanes'
+      // 48-byte slots tile the row, so the warp covers all of its lines)
+      if (k + kVoxPrefetch < len) prefetch_l2(slot + kVoxPrefetch * kVe32 * kSlice);
       if (k + 1 < len) {
         slot += kVe32 * kSlice;
         n0 = __ldg(slot);
