@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(kVoxelThreads, 6) voxel_pass_mixed_kernel(DevL
                                dred, &is_last);
 }
 
-__global__ void __launch_bounds__(kVoxelThreads) voxel_pass_mixed_batch_kernel(JobTable T, int use_trial) {
+__global__ void __launch_bounds__(kVoxelThreads, 6) voxel_pass_mixed_batch_kernel(JobTable T, int use_trial) {
   __shared__ float red[kVoxelThreads / 32];
   __shared__ double dred[kVoxelThreads / 32];
   __shared__ int is_last;
