@@ -504,19 +504,28 @@ __global__ void voxel_starts_kernel(int64_t nc, const uint64_t* ckey, const int6
   if (i == 0) vstart[nv] = nc;
 }
 
-// Selection, per observation: world mean w = R m + t (FP64, with N) and the
-// rotated scatter R S R^T (FP32: it enters the planarity test only, whose
-// FP32 answer is checked against its error bound below)
+// Selection, per observation: its world mean relative to that of its voxel's
+// first observation, w_t - w_a (w = R m + t in FP64, the difference rounded
+// to FP32; it is shorter than two voxel diagonals), with N, and the rotated
+// scatter R S R^T (FP32).  These enter the planarity test only, whose FP32
+// answer is checked against its error bound.  vpos[t + 1] - 1 is t's voxel.
 __global__ void world_terms_kernel(int64_t nc, const double* c, const int32_t* cscan, const double* poses,
-                                   double4_32a* wn, float4* rsr) {
+                                   const int64_t* vpos, const int64_t* vstart, float4* rel, float4* rsr) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nc) return;
+  const int64_t a = vstart[vpos[t + 1] - 1];
   const double* cl = c + 10 * t;
   const double* T = poses + 12 * (int64_t)cscan[t];
-  double w[3];
+  const double* ca = c + 10 * a;
+  const double* Ta = poses + 12 * (int64_t)cscan[a];
+  float d[3];
 #pragma unroll
-  for (int q = 0; q < 3; ++q) w[q] = fma(T[3 * q], cl[6], fma(T[3 * q + 1], cl[7], fma(T[3 * q + 2], cl[8], T[9 + q])));
-  wn[t] = make_double4_32a(w[0], w[1], w[2], cl[9]);
+  for (int q = 0; q < 3; ++q) {
+    const double w = fma(T[3 * q], cl[6], fma(T[3 * q + 1], cl[7], fma(T[3 * q + 2], cl[8], T[9 + q])));
+    const double wa = fma(Ta[3 * q], ca[6], fma(Ta[3 * q + 1], ca[7], fma(Ta[3 * q + 2], ca[8], Ta[9 + q])));
+    d[q] = f64_to_f32(w - wa);
+  }
+  rel[t] = make_float4(d[0], d[1], d[2], f64_to_f32(cl[9]));
   float R[9], S[6];
 #pragma unroll
   for (int q = 0; q < 9; ++q) R[q] = f64_to_f32(T[q]);
@@ -591,42 +600,44 @@ __device__ __noinline__ bool planar_f64(const double* A, double tau) {
 // Selection (Algorithm 1), per voxel: the covariance of its points at the
 // poses, n A = sum_t [R S R^T + N_t (w_t - m)(w_t - m)^T] (the scale n does
 // not change the test), kept if the voxel has min_obs observations and
-// lambda0 < tau lambda1 (tau > 0).  m and w_t - m in FP64, the sum and the
-// eigenvalues (Jacobi sweeps) in FP32: every term is positive semidefinite,
-// so the FP32 error is within (k + 16) 2^-22 tr(nA) for k observations; the
-// answer stands when lambda0 - tau lambda1 is farther than 3 times that (and
-// 1e-4 lambda2) from zero, else the FP64 covariance and sweeps decide.
-// keep_obs[v] = observations kept (0 or the voxel's count).
-__global__ void select_kernel(int64_t nv, const int64_t* vstart, const double4_32a* wn, const float4* rsr,
-                              const double* c, const int32_t* cscan, const double* poses, double tau,
-                              int32_t min_obs, int64_t* keep_obs, int64_t* keep_vox) {
+// lambda0 < tau lambda1 (tau > 0).  All in FP32 on the relative means: every
+// term is positive semidefinite, so the FP32 error is within (k + 16) 2^-22
+// tr(nA) for k observations; the answer stands when lambda0 - tau lambda1 is
+// farther than 3 times that (and 1e-4 lambda2) from zero, else the voxel goes
+// to a list that select_close_kernel decides with the FP64 covariance and
+// sweeps (about 1% of the voxels, kept out of this kernel so that their FP64
+// work does not stall whole warps).  keep_obs[v] = observations kept (0 or the
+// voxel's count).
+__global__ void select_kernel(int64_t nv, const int64_t* vstart, const float4* rel, const float4* rsr, float tau,
+                              int32_t min_obs, int64_t* keep_obs, int64_t* keep_vox, uint32_t* close,
+                              unsigned long long* n_close) {
   const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= nv) return;
   const int64_t a = vstart[v], b = vstart[v + 1];
   bool keep = (b - a) >= (int64_t)min_obs;
-  if (keep && tau > 0.0) {
-    double n = 0.0, m[3] = {0, 0, 0};
+  if (keep && tau > 0.0f) {
+    float n = 0.f, m0 = 0.f, m1 = 0.f, m2 = 0.f;
     for (int64_t t = a; t < b; ++t) {
-      const double4_32a o = wn[t];
-      m[0] = fma(o.w, o.x, m[0]);
-      m[1] = fma(o.w, o.y, m[1]);
-      m[2] = fma(o.w, o.z, m[2]);
+      const float4 o = rel[t];
+      m0 = fmaf(o.w, o.x, m0);
+      m1 = fmaf(o.w, o.y, m1);
+      m2 = fmaf(o.w, o.z, m2);
       n += o.w;
     }
-    const double r = __drcp_rn(n);
-#pragma unroll
-    for (int q = 0; q < 3; ++q) m[q] *= r;
+    const float r = 1.0f / n;
+    m0 *= r;
+    m1 *= r;
+    m2 *= r;
     float A[6] = {0, 0, 0, 0, 0, 0};
     for (int64_t t = a; t < b; ++t) {
-      const double4_32a o = wn[t];
+      const float4 o = rel[t];
       const float4 r0 = rsr[2 * t], r1 = rsr[2 * t + 1];
       const float M[6] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y};
-      const float d[3] = {f64_to_f32(o.x - m[0]), f64_to_f32(o.y - m[1]), f64_to_f32(o.z - m[2])};
-      const float N = f64_to_f32(o.w);
+      const float d[3] = {o.x - m0, o.y - m1, o.z - m2};
       int k = 0;
 #pragma unroll
       for (int x = 0; x < 3; ++x) {
-        const float nd = N * d[x];
+        const float nd = o.w * d[x];
 #pragma unroll
         for (int y = x; y < 3; ++y) {
           A[k] += fmaf(nd, d[y], M[k]);
@@ -636,19 +647,34 @@ __global__ void select_kernel(int64_t nv, const int64_t* vstart, const double4_3
     }
     float lf[3], vf[9];
     eig3_sym_f(A, lf, vf);
-    const float margin = lf[0] - (float)tau * lf[1];
+    const float margin = lf[0] - tau * lf[1];
     const float tr = fabsf(A[0]) + fabsf(A[3]) + fabsf(A[5]);
     const float err = 3.0f * (float)(b - a + 16) * 2.384185791e-7f * tr;  // 3 (k + 16) 2^-22 tr
     if (fabsf(margin) > fmaxf(err, 1e-4f * fabsf(lf[2]))) {
       keep = margin < 0.0f;
     } else {
-      double Ad[6];
-      voxel_cov_f64(a, b, c, cscan, poses, Ad);
-      keep = planar_f64(Ad, tau);
+      close[atomicAdd(n_close, 1ull)] = (uint32_t)v;  // decided by select_close_kernel
     }
   }
   keep_obs[v] = keep ? (b - a) : 0;
   keep_vox[v] = keep ? 1 : 0;
+}
+
+// the voxels too close to call in FP32, one thread each (grid-stride over the
+// list; its order does not matter, each decision is the voxel's own)
+__global__ void select_close_kernel(const uint32_t* close, const unsigned long long* n_close, const int64_t* vstart,
+                                    const double* c, const int32_t* cscan, const double* poses, double tau,
+                                    int64_t* keep_obs, int64_t* keep_vox) {
+  const int64_t m = (int64_t)*n_close;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t v = close[i];
+    const int64_t a = vstart[v], b = vstart[v + 1];
+    double Ad[6];
+    voxel_cov_f64(a, b, c, cscan, poses, Ad);
+    const bool keep = planar_f64(Ad, tau);
+    keep_obs[v] = keep ? (b - a) : 0;
+    keep_vox[v] = keep ? 1 : 0;
+  }
 }
 
 // kept voxels of a level written at their places in the output
@@ -1391,21 +1417,33 @@ ba_status ba_voxelize(const ba_voxelize_config* cfg, int32_t n_scans, const int6
       return vfail(BA_ERR_OOM, "voxelize: out of device memory");
     voxel_starts_kernel<<<blocks_for(L.nc), 256, 0, st>>>(L.nc, L.key, pos, L.vstart, L.nv);
     launches += 2;
-    double4_32a* wn = nullptr;
-    float4* rsr = nullptr;
+    tm.begin(BA_VOX_SELECT);
+    float4 *rel = nullptr, *rsr = nullptr;
+    uint32_t* close = nullptr;
+    unsigned long long* n_close = nullptr;
     if (cfg->tau > 0.0) {
-      wn = tmp.get<double4_32a>(L.nc);
+      rel = tmp.get<float4>(L.nc);
       rsr = tmp.get<float4>(2 * L.nc);
-      if (!wn || !rsr) return vfail(BA_ERR_OOM, "voxelize: out of device memory");
-      tm.begin(BA_VOX_SELECT);
-      world_terms_kernel<<<blocks_for(L.nc), 256, 0, st>>>(L.nc, L.c, L.scan, T, wn, rsr);
+      close = tmp.get<uint32_t>(L.nv);
+      n_close = tmp.get<unsigned long long>(1);
+      if (!rel || !rsr || !close || !n_close) return vfail(BA_ERR_OOM, "voxelize: out of device memory");
+      VCK(cudaMemsetAsync(n_close, 0, sizeof(unsigned long long), st), "voxelize");
+      world_terms_kernel<<<blocks_for(L.nc), 256, 0, st>>>(L.nc, L.c, L.scan, T, pos, L.vstart, rel, rsr);
       ++launches;
     }
-    if (!wn) tm.begin(BA_VOX_SELECT);
-    select_kernel<<<blocks_for(L.nv), 256, 0, st>>>(L.nv, L.vstart, wn, rsr, L.c, L.scan, T, cfg->tau, cfg->min_obs,
-                                                   keep_obs[k], keep_vox[k]);
-    tm.end();
+    // tau rounded to FP32 moves the test by 2^-24 tau lambda1, inside the error band
+    select_kernel<<<blocks_for(L.nv), 256, 0, st>>>(L.nv, L.vstart, rel, rsr, cfg->tau > 0.0 ? (float)cfg->tau : 0.0f,
+                                                   cfg->min_obs, keep_obs[k], keep_vox[k], close, n_close);
     ++launches;
+    if (cfg->tau > 0.0) {
+      int n_sm = 0;
+      cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, cfg->device);
+      const int64_t cb = std::min<int64_t>(blocks_for(L.nv, 128), (int64_t)(n_sm > 0 ? n_sm : 1) * 4);
+      select_close_kernel<<<(unsigned)cb, 128, 0, st>>>(close, n_close, L.vstart, L.c, L.scan, T, cfg->tau,
+                                                        keep_obs[k], keep_vox[k]);
+      ++launches;
+    }
+    tm.end();
     VCK(cudaGetLastError(), "voxelize select");
     VCK(cudaMemsetAsync(keep_obs[k] + L.nv, 0, sizeof(int64_t), st), "voxelize");
     VCK(cudaMemsetAsync(keep_vox[k] + L.nv, 0, sizeof(int64_t), st), "voxelize");
