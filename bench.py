@@ -624,6 +624,8 @@ def run_batched(args):
         for j in jobs:
             b.add(j)
         t0 = time.perf_counter()
+        # the tuner's trials are the solve's first iterations (results do not depend on its choice)
+        tune = b.autotune(iters_per_trial=1, passes=1)
         active = b.solve(chunk=args.chunk)
         torch.cuda.synchronize()
         t_mixed = time.perf_counter() - t0
@@ -659,7 +661,11 @@ def run_batched(args):
         "pose_agreement_mixed_vs_fp64": {"max_rot_rad": worst[0], "max_trans_m": worst[1], "jobs": n64},
         "accuracy_vs_ground_truth": acc.report(),
         "config": {"scans": "log-uniform 20-2000", "voxels": "50 x scans", "obs_per_voxel": "5-30",
-                   "pts_per_obs": 32, "stop": SOLVE_CFG, "chunk": args.chunk},
+                   "pts_per_obs": 32, "stop": SOLVE_CFG, "chunk": args.chunk,
+                   "autotune": {"passes": tune["passes"], "iterations": tune["iterations"],
+                                "chosen": tune["candidates"][tune["chosen"]] if tune["chosen"] >= 0 else None,
+                                "ms_per_iter": {f"mb{c['min_blocks']}_pf{c['prefetch']}": round(c["ms_per_iter"], 4)
+                                                for c in tune["candidates"]}}},
     }
     print(json.dumps(line), flush=True)
 

@@ -253,6 +253,27 @@ const char* ba_batch_last_error(const ba_batch* b);
 /* Kernel launches issued by the batch's iterations (3 per iteration). */
 int64_t ba_batch_kernel_launches(const ba_batch* b);
 
+/* Autotuner of the batch's launch settings (mixed precision only): times
+ * every candidate of (register cap of the voxel pass: 4, 6 or 8 resident
+ * blocks of 128 threads per SM) x (L2 prefetch distance of its slot rows: 0,
+ * 2 or 4) over iters_per_trial solve iterations of the batch's own jobs, the
+ * candidates interleaved over `passes` passes, and keeps the fastest for the
+ * batch's later iterations.  Only settings that change no arithmetic are
+ * candidates, so results are bit-identical whatever it picks; the tuning
+ * iterations are real iterations of the jobs' solves (ba_batch_solve
+ * semantics).  A pass during which a job stops is not counted; with no
+ * complete pass the settings stay as they were (chosen = -1).  FP64 batches
+ * have nothing to tune (n_candidates = 0). */
+typedef struct {
+  int32_t n_candidates;
+  int32_t chosen;           /* index of the kept candidate, -1 if none */
+  int32_t passes;           /* complete passes measured */
+  int32_t min_blocks[16];
+  int32_t prefetch[16];
+  double ms_per_iter[16];   /* mean over the complete passes */
+} ba_tune_report;
+ba_status ba_batch_autotune(ba_batch* b, int32_t iters_per_trial, int32_t passes, ba_tune_report* out);
+
 /* ---- Served execution (continuous batching) -----------------------------
  * The paper solves one problem at a time; a server keeps many independent
  * jobs (submaps, sessions) resident on one GPU and steps them together

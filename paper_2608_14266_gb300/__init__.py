@@ -275,6 +275,16 @@ class Batch:
     def kernel_launches(self) -> int:
         return int(_lib.lib().ba_batch_kernel_launches(self.b))
 
+    def autotune(self, iters_per_trial: int = 2, passes: int = 2) -> dict:
+        """ba_batch_autotune: picks the voxel pass's launch settings on the
+        batch's own iterations; returns the candidates, timings and choice."""
+        r = _lib.BaTuneReport()
+        self._check(_lib.lib().ba_batch_autotune(self.b, int(iters_per_trial), int(passes), ctypes.byref(r)))
+        cands = [{"min_blocks": r.min_blocks[k], "prefetch": r.prefetch[k], "ms_per_iter": r.ms_per_iter[k]}
+                 for k in range(r.n_candidates)]
+        return {"candidates": cands, "chosen": r.chosen, "passes": r.passes,
+                "iterations": r.n_candidates * int(iters_per_trial) * int(passes)}
+
     def close(self):
         if self.b:
             _lib.lib().ba_batch_destroy(self.b)

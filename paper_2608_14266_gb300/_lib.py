@@ -47,6 +47,11 @@ class BaVoxelizeConfig(ctypes.Structure):
                 ("cuda_stream", _P), ("profile", _I32), ("batch_points", _I64), ("alpha", _D)]
 
 
+class BaTuneReport(ctypes.Structure):
+    _fields_ = [("n_candidates", _I32), ("chosen", _I32), ("passes", _I32), ("min_blocks", _I32 * 16),
+                ("prefetch", _I32 * 16), ("ms_per_iter", _D * 16)]
+
+
 class BaJobDesc(ctypes.Structure):
     _fields_ = [("n_scans", _I32), ("n_voxels", _I64), ("n_obs", _I64), ("voxel_offsets", _P), ("obs_scan", _P),
                 ("agg", _P), ("agg_form", _I32), ("poses", _P), ("mem_kind", _I32)]
@@ -96,6 +101,7 @@ _SIGNATURES = {
     "ba_check_bounded_wait": (_I32, [_I32, _I32]),
     "ba_release_cached_memory": (_I32, [_I32]),
     "ba_check_conversions": (_I32, [_I32, _I64, ctypes.c_uint64, _P]),
+    "ba_batch_autotune": (_I32, [_P, _I32, _I32, _P]),
     "ba_voxelize_config_default": (None, [_P]),
     "ba_voxelize": (_I32, [_P, _I32, _P, _P, _P, _I32, _P]),
     "ba_voxels_size": (_I32, [_P, _P, _P]),

@@ -1001,6 +1001,9 @@ struct ba_batch {
   // captured iterations
   cudaGraphExec_t graph = nullptr;
   int graph_iters = -1;
+  // tuned launch settings of the mixed voxel pass (results do not depend on them)
+  int vp_min_blocks = 6;
+  int vp_prefetch = 2;
 };
 
 namespace {
@@ -1123,7 +1126,7 @@ __global__ void batch_status_kernel(JobTable T, int32_t* done) {
 ba_status launch_batch_iteration(ba_batch* b) {
   const JobTable T = table_of(b);
   BCK(b, launch_batch_solve(T, b->n_oblk, b->stream), "batch solve");
-  BCK(b, b->mixed ? launch_batch_voxel_pass_mixed(T, b->n_vblk, 1, b->stream)
+  BCK(b, b->mixed ? launch_batch_voxel_pass_mixed(T, b->n_vblk, 1, b->stream, b->vp_min_blocks, b->vp_prefetch)
                   : launch_batch_voxel_pass_f64(T, b->n_vblk, 1, b->stream),
       "batch voxel pass");
   BCK(b, b->mixed ? launch_batch_scan_pass_mixed(T, b->n_sblk, b->stream)
@@ -1146,7 +1149,7 @@ ba_status sync_members(ba_batch* b) {
 }
 
 // n iterations as one CUDA graph (captured on first use for this count)
-ba_status run_iterations(ba_batch* b, int n) {
+ba_status prepare_graph(ba_batch* b, int n) {
   if (b->graph_iters != n) {
     drop_graph(b);
     cudaGraph_t g = nullptr;
@@ -1164,8 +1167,28 @@ ba_status run_iterations(ba_batch* b, int n) {
     BCK(b, e, "graph instantiate");
     b->graph_iters = n;
   }
+  return BA_OK;
+}
+
+ba_status run_iterations(ba_batch* b, int n) {
+  ba_status s = prepare_graph(b, n);
+  if (s != BA_OK) return s;
   BCK(b, cudaGraphLaunch(b->graph, b->stream), "graph launch");
   b->launches += 3 * (int64_t)n;
+  return BA_OK;
+}
+
+// jobs still running (after the work queued so far)
+ba_status active_jobs(ba_batch* b, int32_t* active) {
+  const JobTable T = table_of(b);
+  batch_status_kernel<<<1, 256, 0, b->stream>>>(T, b->d_done);
+  ++b->launches;
+  BCK(b, cudaGetLastError(), "batch status");
+  int32_t counts[2] = {0, 0};
+  BCK(b, cudaMemcpyAsync(counts, b->d_done + T.n_jobs, sizeof(counts), cudaMemcpyDeviceToHost, b->stream), "status");
+  BCK(b, cudaStreamSynchronize(b->stream), "synchronize");
+  if (counts[1]) return bfail(b, BA_ERR_TIMEOUT, "%d job(s): a bounded device-side wait gave up", counts[1]);
+  *active = counts[0];
   return BA_OK;
 }
 
@@ -1297,6 +1320,89 @@ ba_status ba_batch_done(ba_batch* b, int32_t* done_out) {
   BCK(b, cudaMemcpyAsync(done_out, b->d_done, sizeof(int32_t) * T.n_jobs, cudaMemcpyDeviceToHost, b->stream),
       "status");
   BCK(b, cudaStreamSynchronize(b->stream), "synchronize");
+  return BA_OK;
+}
+
+ba_status ba_batch_autotune(ba_batch* b, int32_t iters_per_trial, int32_t passes, ba_tune_report* out) {
+  if (!b || !out) return BA_ERR_INVALID_ARG;
+  if (iters_per_trial < 1 || passes < 1) return bfail(b, BA_ERR_INVALID_ARG, "iters_per_trial and passes must be >= 1");
+  *out = ba_tune_report{};
+  out->chosen = -1;
+  if (b->jobs.empty() || !b->mixed) return BA_OK;  // the FP64 voxel pass has no such knobs
+  DeviceGuard g(b->device);
+  ba_status s = refresh(b);
+  if (s != BA_OK) return s;
+  if ((s = sync_members(b)) != BA_OK) return s;
+  const JobTable T = table_of(b);
+  batch_control_kernel<<<(T.n_jobs + 127) / 128, 128, 0, b->stream>>>(T, 1, 0);  // these are solve iterations
+  ++b->launches;
+  BCK(b, cudaGetLastError(), "batch control");
+  const int mb[3] = {4, 6, 8}, pf[3] = {0, 2, 4};
+  int n = 0;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j, ++n) {
+      out->min_blocks[n] = mb[i];
+      out->prefetch[n] = pf[j];
+    }
+  out->n_candidates = n;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  BCK(b, cudaEventCreate(&e0), "tuner events");
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return bfail(b, BA_ERR_CUDA, "tuner events");
+  }
+  struct Events {
+    cudaEvent_t a, b;
+    ~Events() {
+      cudaEventDestroy(a);
+      cudaEventDestroy(b);
+    }
+  } ev{e0, e1};
+  const int keep_mb = b->vp_min_blocks, keep_pf = b->vp_prefetch;
+  std::vector<double> sum(n, 0.0);
+  int full_passes = 0;
+  // candidates interleaved pass by pass, so that jobs stopping along the way
+  // (less work per iteration) affect every candidate alike; only complete
+  // passes with every job still running count
+  for (int pass = 0; pass < passes; ++pass) {
+    std::vector<double> ms(n, 0.0);
+    for (int c = 0; c < n; ++c) {
+      if (b->vp_min_blocks != out->min_blocks[c] || b->vp_prefetch != out->prefetch[c]) {
+        b->vp_min_blocks = out->min_blocks[c];
+        b->vp_prefetch = out->prefetch[c];
+        drop_graph(b);
+      }
+      if ((s = prepare_graph(b, iters_per_trial)) != BA_OK) return s;
+      BCK(b, cudaEventRecord(e0, b->stream), "tuner events");
+      BCK(b, cudaGraphLaunch(b->graph, b->stream), "graph launch");
+      b->launches += 3 * (int64_t)iters_per_trial;
+      BCK(b, cudaEventRecord(e1, b->stream), "tuner events");
+      BCK(b, cudaEventSynchronize(e1), "tuner events");
+      float t = 0.f;
+      BCK(b, cudaEventElapsedTime(&t, e0, e1), "tuner events");
+      ms[c] = t / iters_per_trial;
+    }
+    int32_t active = 0;
+    if ((s = active_jobs(b, &active)) != BA_OK) return s;
+    if (active < T.n_jobs) break;  // a job stopped during this pass: the pass is not comparable
+    for (int c = 0; c < n; ++c) sum[c] += ms[c];
+    ++full_passes;
+  }
+  out->passes = full_passes;
+  if (full_passes == 0) {
+    b->vp_min_blocks = keep_mb;
+    b->vp_prefetch = keep_pf;
+  } else {
+    int best = 0;
+    for (int c = 0; c < n; ++c) {
+      out->ms_per_iter[c] = sum[c] / full_passes;
+      if (sum[c] < sum[best]) best = c;
+    }
+    out->chosen = best;
+    b->vp_min_blocks = out->min_blocks[best];
+    b->vp_prefetch = out->prefetch[best];
+  }
+  drop_graph(b);
   return BA_OK;
 }
 

@@ -7,7 +7,8 @@
 
 namespace mmba {
 
-// rows of the voxel-pass slots fetched into L2 ahead of the current one
+// rows of the voxel-pass slots fetched into L2 ahead of the current one (the
+// batch executor's tuner may pick another distance; results do not depend on it)
 constexpr int kVoxPrefetch = 2;
 
 __device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
@@ -40,7 +41,7 @@ __device__ __forceinline__ void voxel_pass_mixed_body(const DevLayout& L, const 
                                                       double* __restrict__ full_out, double* __restrict__ cost_part,
                                                       const double* __restrict__ pred_part, DevState* __restrict__ st,
                                                       int use_trial, int decide_mode, int64_t blk, float* red,
-                                                      double* dred, int* is_last) {
+                                                      double* dred, int* is_last, int pf) {
   if (st->honor_stop && st->stop) {
     // a stopped solve takes no step, so no gradient is pending either
     if (decide_mode == 0 && blk == 0 && threadIdx.x == 0) st->scan_pending = 0;
@@ -75,7 +76,7 @@ __device__ __forceinline__ void voxel_pass_mixed_body(const DevLayout& L, const 
       const float4 f0 = n0, f1 = n1, f2 = n2;
       // rows further ahead go to L2 without holding registers (the lanes'
       // 48-byte slots tile the row, so the warp covers all of its lines)
-      if (k + kVoxPrefetch < len) prefetch_l2(slot + kVoxPrefetch * kVe32 * kSlice);
+      if (pf > 0 && k + pf < len) prefetch_l2(slot + pf * kVe32 * kSlice);
       if (k + 1 < len) {
         slot += kVe32 * kSlice;
         n0 = __ldg(slot);
@@ -184,10 +185,14 @@ __global__ void __launch_bounds__(kVoxelThreads, 6) voxel_pass_mixed_kernel(DevL
   __shared__ double dred[kVoxelThreads / 32];
   __shared__ int is_last;
   voxel_pass_mixed_body<kFull>(L, X, full_out, cost_part, pred_part, st, use_trial, decide_mode, blockIdx.x, red,
-                               dred, &is_last);
+                               dred, &is_last, kVoxPrefetch);
 }
 
-__global__ void __launch_bounds__(kVoxelThreads, 6) voxel_pass_mixed_batch_kernel(JobTable T, int use_trial) {
+// kMinBlocks (resident blocks per SM the registers are capped for) and pf are
+// the batch tuner's knobs: neither changes any arithmetic
+template <int kMinBlocks>
+__global__ void __launch_bounds__(kVoxelThreads, kMinBlocks) voxel_pass_mixed_batch_kernel(JobTable T, int use_trial,
+                                                                                           int pf) {
   __shared__ float red[kVoxelThreads / 32];
   __shared__ double dred[kVoxelThreads / 32];
   __shared__ int is_last;
@@ -200,7 +205,7 @@ __global__ void __launch_bounds__(kVoxelThreads, 6) voxel_pass_mixed_batch_kerne
   }
   __syncthreads();
   voxel_pass_mixed_body<false>(J.L, J.X, nullptr, J.cost_part, J.pred_part, J.st, use_trial, use_trial ? 0 : 1, blk,
-                               red, dred, &is_last);
+                               red, dred, &is_last, pf);
 }
 
 // ---------------------------------------------------------------------------
@@ -521,8 +526,18 @@ cudaError_t launch_scan_pass_mixed(const DevLayout& L, const DevMixed& X, const 
   return cudaGetLastError();
 }
 
-cudaError_t launch_batch_voxel_pass_mixed(const JobTable& T, int64_t n_blocks, int use_trial, cudaStream_t stream) {
-  voxel_pass_mixed_batch_kernel<<<(unsigned)n_blocks, kVoxelThreads, 0, stream>>>(T, use_trial);
+cudaError_t launch_batch_voxel_pass_mixed(const JobTable& T, int64_t n_blocks, int use_trial, cudaStream_t stream,
+                                          int min_blocks, int pf) {
+  switch (min_blocks) {
+    case 4:
+      voxel_pass_mixed_batch_kernel<4><<<(unsigned)n_blocks, kVoxelThreads, 0, stream>>>(T, use_trial, pf);
+      break;
+    case 8:
+      voxel_pass_mixed_batch_kernel<8><<<(unsigned)n_blocks, kVoxelThreads, 0, stream>>>(T, use_trial, pf);
+      break;
+    default:
+      voxel_pass_mixed_batch_kernel<6><<<(unsigned)n_blocks, kVoxelThreads, 0, stream>>>(T, use_trial, pf);
+  }
   return cudaGetLastError();
 }
 

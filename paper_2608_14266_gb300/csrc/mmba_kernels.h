@@ -22,7 +22,10 @@ cudaError_t launch_batch_solve(const JobTable& T, int64_t n_blocks, cudaStream_t
 cudaError_t launch_batch_decide(const JobTable& T, cudaStream_t stream);
 cudaError_t launch_batch_voxel_pass_f64(const JobTable& T, int64_t n_blocks, int use_trial, cudaStream_t stream);
 cudaError_t launch_batch_scan_pass_f64(const JobTable& T, int64_t n_blocks, cudaStream_t stream);
-cudaError_t launch_batch_voxel_pass_mixed(const JobTable& T, int64_t n_blocks, int use_trial, cudaStream_t stream);
+// min_blocks in {4, 6, 8} (register cap of the batch voxel pass), pf = L2
+// prefetch distance in slot rows (0 = none); neither changes the results
+cudaError_t launch_batch_voxel_pass_mixed(const JobTable& T, int64_t n_blocks, int use_trial, cudaStream_t stream,
+                                          int min_blocks = 6, int pf = 2);
 cudaError_t launch_batch_scan_pass_mixed(const JobTable& T, int64_t n_blocks, cudaStream_t stream);
 
 // ---- iteration (FP64) ----

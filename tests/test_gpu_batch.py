@@ -161,3 +161,43 @@ def test_batch_membership_changes(mm):
                                 scenes[1][2], scenes[1][0].pose_init)
     for j in jobs:
         j.close()
+
+
+def test_autotune_leaves_results_bit_identical(mm):
+    """The batch tuner times its nine launch settings on the jobs' own solve
+    iterations and keeps the fastest; since no candidate changes arithmetic,
+    a tuned solve ends with the same bits, iteration counts and stop flags as
+    an untuned one.  FP64 batches have nothing to tune."""
+    scenes = _job_scenes(6, seed=4)
+    cfg = dict(precision=mm.BA_MIXED, rel_tol=1e-12, max_iters=60)
+    plain = [_load(mm, s, po, pts, **cfg) for s, po, pts in scenes]
+    with mm.Batch() as b:
+        for j in plain:
+            b.add(j)
+        assert b.solve(chunk=4) == 0
+    ref = [(j.poses(), j.cost(), j.stats()["iters"]) for j in plain]
+    tuned = [_load(mm, s, po, pts, **cfg) for s, po, pts in scenes]
+    with mm.Batch() as b:
+        for j in tuned:
+            b.add(j)
+        rep = b.autotune(iters_per_trial=1, passes=2)
+        assert len(rep["candidates"]) == 9
+        assert {(c["min_blocks"], c["prefetch"]) for c in rep["candidates"]} == \
+            {(m, p) for m in (4, 6, 8) for p in (0, 2, 4)}
+        if rep["passes"] > 0:
+            ms = [c["ms_per_iter"] for c in rep["candidates"]]
+            assert rep["chosen"] == int(np.argmin(ms)) and min(ms) > 0
+        assert b.solve(chunk=4) == 0
+    for j, (poses, cost, iters) in zip(tuned, ref):
+        np.testing.assert_array_equal(j.poses(), poses)
+        assert j.cost() == cost
+        assert j.stats()["iters"] == iters
+    for j in plain + tuned:
+        j.close()
+    (s, po, pts), = _job_scenes(1, seed=5)
+    j = _load(mm, s, po, pts, precision=mm.BA_FP64)
+    with mm.Batch() as b:
+        b.add(j)
+        rep = b.autotune()
+        assert rep["candidates"] == [] and rep["chosen"] == -1
+    j.close()
