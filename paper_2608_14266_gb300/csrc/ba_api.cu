@@ -528,6 +528,23 @@ ba_status load_impl(ba_handle* h, int32_t n_scans, int64_t n_voxels, int64_t n_o
     h->X.stab2 = mb.stab2;
     h->X.planes32_2 = mb.planes32_2;
   }
+  {
+    // scan-pass block order: scans by decreasing observation count (ties by
+    // index), so the longest start first
+    std::vector<int64_t> so((size_t)n_scans + 1);
+    CK(h, cudaMemcpyAsync(so.data(), lb.scan_off, sizeof(int64_t) * so.size(), cudaMemcpyDeviceToHost, h->stream),
+       "scan order");
+    CK(h, cudaStreamSynchronize(h->stream), "scan order");
+    std::vector<int32_t> ord((size_t)n_scans);
+    for (int32_t j = 0; j < n_scans; ++j) ord[j] = j;
+    std::stable_sort(ord.begin(), ord.end(),
+                     [&](int32_t a, int32_t b) { return so[a + 1] - so[a] > so[b + 1] - so[b]; });
+    int32_t* d_ord = (int32_t*)dev_alloc(h, h->keep, sizeof(int32_t) * (size_t)n_scans);
+    if (!d_ord) return fail(h, BA_ERR_OOM, "scan order: out of device memory");
+    CK(h, cudaMemcpyAsync(d_ord, ord.data(), sizeof(int32_t) * ord.size(), cudaMemcpyHostToDevice, h->stream),
+       "scan order");
+    L.scan_order = d_ord;
+  }
   DevState s0{};
   s0.mu = h->cfg.mu0;
   s0.nu = 2.0;

@@ -310,7 +310,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_pass_f64_kernel(DevLayout L
                                                                     double* __restrict__ gH,
                                                                     const DevState* __restrict__ st, int force) {
   __shared__ double red[kScanThreads / 32][kGH];
-  scan_pass_f64_body(L, poses2, planes2, gH, st, force, blockIdx.x, red);
+  scan_pass_f64_body(L, poses2, planes2, gH, st, force, scan_of_block(L, blockIdx.x), red);
 }
 
 __global__ void __launch_bounds__(kScanThreads) scan_pass_f64_batch_kernel(JobTable T) {
@@ -320,7 +320,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_pass_f64_batch_kernel(JobTa
   if (threadIdx.x == 0) {
     const int job = find_job(T.sblk, T.n_jobs, blockIdx.x);
     J = T.jobs[job];
-    j = (int)(blockIdx.x - T.sblk[job]);
+    j = scan_of_block(J.L, blockIdx.x - T.sblk[job]);
   }
   __syncthreads();
   scan_pass_f64_body(J.L, J.poses2, J.planes2, J.gH, J.st, 0, j, red);

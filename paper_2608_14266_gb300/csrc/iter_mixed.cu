@@ -461,7 +461,7 @@ __global__ void __launch_bounds__(kScanMixedThreads, 24) scan_pass_mixed_kernel(
   __shared__ float dR[9];
   __shared__ ScanChunk chunks[2];
   __shared__ uint64_t bars[2];
-  scan_pass_mixed_body(L, X, gH, st, force, blockIdx.x, red, tot, dR, chunks, bars);
+  scan_pass_mixed_body(L, X, gH, st, force, scan_of_block(L, blockIdx.x), red, tot, dR, chunks, bars);
 }
 
 __global__ void __launch_bounds__(kScanMixedThreads, 20) scan_pass_mixed_batch_kernel(JobTable T) {
@@ -475,7 +475,7 @@ __global__ void __launch_bounds__(kScanMixedThreads, 20) scan_pass_mixed_batch_k
   if (threadIdx.x == 0) {
     const int job = find_job(T.sblk, T.n_jobs, blockIdx.x);
     J = T.jobs[job];
-    j = (int)(blockIdx.x - T.sblk[job]);
+    j = scan_of_block(J.L, blockIdx.x - T.sblk[job]);
   }
   __syncthreads();
   scan_pass_mixed_body(J.L, J.X, J.gH, J.st, 0, j, red, tot, dR, chunks, bars);

@@ -45,7 +45,15 @@ struct DevLayout {
   const int64_t* scan_off;   // n_scans + 1
   const double* se;          // 10 x n_obs
   const int32_t* se_vox;     // n_obs
+  // scans by decreasing observation count: scan-pass block b works on scan
+  // scan_order[b], so the longest scans start first and the tail is short
+  // (NULL = block b, scan b)
+  const int32_t* scan_order;
 };
+
+__device__ __forceinline__ int scan_of_block(const DevLayout& L, int64_t b) {
+  return L.scan_order ? L.scan_order[b] : (int)b;
+}
 
 // Mixed-precision copies (FP32 per observation, re-centred).  For every
 // voxel i an anchor a_i (the FP32-representable rounding of its centroid at
