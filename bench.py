@@ -58,7 +58,8 @@ def _args():
     ap.add_argument("--steps", type=int, default=3000, help="timed LM iterations per rank")
     ap.add_argument("--warmup", type=int, default=30, help="untimed warm-up iterations")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["city", "mid", "tiny", "batched", "served", "voxelize"], default="city")
+    ap.add_argument("--workload", choices=["city", "mid", "tiny", "batched", "served", "voxelize", "sweep"],
+                    default="city")
     ap.add_argument("--jobs", type=int, default=256, help="jobs of the batched / served workloads")
     ap.add_argument("--fp64-jobs", type=int, default=256, help="of which solved on the plain FP64 path too")
     ap.add_argument("--rate", type=float, default=200.0, help="served: Poisson arrival rate (jobs/s)")
@@ -905,12 +906,97 @@ def _world_index_range(P, spo, poses, d):
     return np.floor(hi / d) - np.floor(lo / d)
 
 
+def _line_fit(x, y):
+    """Least-squares line y = a x + b and its R^2."""
+    import numpy as np
+    x, y = np.asarray(x, float), np.asarray(y, float)
+    a, b = np.polyfit(x, y, 1)
+    ss_res = float(((y - (a * x + b)) ** 2).sum())
+    ss_tot = float(((y - y.mean()) ** 2).sum())
+    return {"slope": float(a), "intercept": float(b), "r2": 1.0 - ss_res / ss_tot if ss_tot > 0 else 1.0}
+
+
+def run_sweep(args):
+    """The paper's scaling figure (Sec. V, Fig. 3) in shape: per-iteration
+    evaluation time (voxel and scan passes, mixed path) against the number of
+    clusters and the solver's time against the number of poses, on city
+    scenes of 1/8 to full size; preprocessing time against the number of
+    points on 1/8 to all of the 1,000-scan raw scans.  Each series gets a
+    least-squares line and its R^2 (the paper reports linear growth)."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2608_14266_gb300 as mm
+    import scenegen
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    fracs = [0.125, 0.25, 0.5, 1.0]
+    ev, sv = [], []
+    for f in fracs:
+        p = scenegen.config("city")
+        side = math.sqrt(f)
+        p = scenegen.replace(p, n_scans=int(p.n_scans * f), n_voxels=int(p.n_voxels * f),
+                             box=(p.box[0] * side, p.box[1] * side, p.box[2]))
+        scene = scenegen.make_scene(p)
+        inputs = (torch.from_numpy(scene.voxel_off).to(dev), torch.from_numpy(scene.obs_scan).to(dev),
+                  device_clusters_gpu(scene, torch, mm), torch.from_numpy(scene.pose_init).to(dev))
+        res = measure(mm, torch, scene, inputs, mm.BA_MIXED, 300, 30, 30, lambda: None, 0)
+        prof = res["prof"]
+        per = {k: prof[k][0] / max(1, prof[k][1]) for k in ("voxel_pass", "scan_pass", "solve")}
+        ev.append((scene.n_obs, per["voxel_pass"] + per["scan_pass"]))
+        sv.append((scene.n_scans, per["solve"]))
+        del inputs
+        torch.cuda.empty_cache()
+    # preprocessing: prefixes of the 1,000-scan raw scans
+    s = scenegen.make_scene(scenegen.config("mid"))
+    npo = s.params.pts_per_obs
+    P = torch.empty((s.n_obs * npo, 3), dtype=torch.float64, device=dev)
+    s.points_device(0, s.n_obs, P)
+    order = torch.from_numpy(np.argsort(s.obs_scan, kind="stable")).to(dev)
+    P = P.view(s.n_obs, npo, 3)[order].reshape(-1, 3).contiguous()
+    spo_all = np.concatenate([[0], np.cumsum(np.bincount(s.obs_scan, minlength=s.n_scans) * npo)]).astype(np.int64)
+    stream = torch.cuda.current_stream()
+    pv = []
+    for f in fracs:
+        k = max(1, int(round(s.n_scans * f)))
+        spo = torch.from_numpy(spo_all[: k + 1]).to(dev)
+        n = int(spo_all[k])
+        Pk, T = P[:n], torch.from_numpy(s.pose_init[:k]).to(dev)
+        cfg = dict(voxel_size=0.5, levels=3, tau=0.1, min_obs=2, stream=stream, out="device")
+        mm.voxelize(spo, Pk, T, **cfg)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(3):
+            mm.voxelize(spo, Pk, T, **cfg)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        pv.append((n, e0.elapsed_time(e1) / 3))
+    line = {
+        "metric": "scaling sweep (the paper's Fig. 3 in shape): times against problem size",
+        "workload": "sweep", "n_gpus": 1, "higher_is_better": False, "dtype": "f32 (iterations) / f64 (preprocessing)",
+        "data": "synthetic",
+        "series": {
+            "evaluation_ms_vs_clusters": {"points": ev, "fit": _line_fit(*zip(*ev))},
+            "solve_ms_vs_poses": {"points": sv, "fit": _line_fit(*zip(*sv))},
+            "preprocess_ms_vs_points": {"points": pv, "fit": _line_fit(*zip(*pv))},
+        },
+        "config": {"workload": "city scenes at 1/8, 1/4, 1/2 and full size (mixed path, 300 timed iterations "
+                               "each); prefixes of the 1,000-scan raw scans (d = 0.5 m, 3 levels)"},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = _args()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "voxelize":
         run_voxelize(args)
+    elif args.workload == "sweep":
+        run_sweep(args)
     elif args.workload == "batched":
         run_batched(args)
     elif args.workload == "served":
