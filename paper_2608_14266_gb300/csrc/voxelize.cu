@@ -736,6 +736,8 @@ struct StageTimer {
   int open_stage = -1;
   void begin(int stage) {
     if (!on) return;
+    if (open_ev) cudaEventDestroy(open_ev);  // a stage left open by an error path
+    open_ev = nullptr;
     cudaEvent_t e = nullptr;
     if (cudaEventCreate(&e) != cudaSuccess) return;
     cudaEventRecord(e, st);
