@@ -474,6 +474,23 @@ ba_status load_impl(ba_handle* h, int32_t n_scans, int64_t n_voxels, int64_t n_o
   L.scan_off = lb.scan_off;
   L.se = lb.se;
   L.se_vox = lb.se_vox;
+  {
+    // scan-pass block order: scans by decreasing observation count (ties by
+    // index), so the longest start first
+    std::vector<int64_t> so((size_t)n_scans + 1);
+    CK(h, cudaMemcpyAsync(so.data(), lb.scan_off, sizeof(int64_t) * so.size(), cudaMemcpyDeviceToHost, h->stream),
+       "scan order");
+    CK(h, cudaStreamSynchronize(h->stream), "scan order");
+    std::vector<int32_t> ord((size_t)n_scans);
+    for (int32_t j = 0; j < n_scans; ++j) ord[j] = j;
+    std::stable_sort(ord.begin(), ord.end(),
+                     [&](int32_t a, int32_t b) { return so[a + 1] - so[a] > so[b + 1] - so[b]; });
+    int32_t* d_ord = (int32_t*)dev_alloc(h, h->keep, sizeof(int32_t) * (size_t)n_scans);
+    if (!d_ord) return fail(h, BA_ERR_OOM, "scan order: out of device memory");
+    CK(h, cudaMemcpyAsync(d_ord, ord.data(), sizeof(int32_t) * ord.size(), cudaMemcpyHostToDevice, h->stream),
+       "scan order");
+    L.scan_order = d_ord;
+  }
 
   // iteration buffers
   h->n_cost = voxel_pass_blocks(n_voxels);
@@ -512,8 +529,10 @@ ba_status load_impl(ba_handle* h, int32_t n_scans, int64_t n_voxels, int64_t n_o
         CK(h, launch_validate_agg(in, voxel_off[v0], voxel_off[v1], d_val, h->stream, &h->launches), "validate");
         CK(h, launch_vscale(in, v0, v1, lb.vscale, h->stream, &h->launches), "voxel scales");
         CK(h, build_mixed_voxels(in, lb, h->poses2, mb, v0, v1, h->stream, &h->launches), "mixed-precision copies");
+        CK(h, build_mixed_scan_range(in, lb, mb, voxel_off[v0], voxel_off[v1], h->stream, &h->launches),
+           "mixed-precision copies");
       }
-      CK(h, build_mixed_end(in, lb, h->poses2, mb, h->stream, &h->launches), "mixed-precision copies");
+      CK(h, build_mixed_end(in, lb, h->poses2, mb, h->stream, &h->launches, true), "mixed-precision copies");
       CK(h, cudaMemcpyAsync(&res, d_val, sizeof res, cudaMemcpyDeviceToHost, h->stream), "validation result");
       CK(h, cudaStreamSynchronize(h->stream), "validation sync");
       if ((vs = check_validation(h, res, n_scans)) != BA_OK) return vs;
@@ -527,23 +546,6 @@ ba_status load_impl(ba_handle* h, int32_t n_scans, int64_t n_voxels, int64_t n_o
     h->X.sref = mb.sref;
     h->X.stab2 = mb.stab2;
     h->X.planes32_2 = mb.planes32_2;
-  }
-  {
-    // scan-pass block order: scans by decreasing observation count (ties by
-    // index), so the longest start first
-    std::vector<int64_t> so((size_t)n_scans + 1);
-    CK(h, cudaMemcpyAsync(so.data(), lb.scan_off, sizeof(int64_t) * so.size(), cudaMemcpyDeviceToHost, h->stream),
-       "scan order");
-    CK(h, cudaStreamSynchronize(h->stream), "scan order");
-    std::vector<int32_t> ord((size_t)n_scans);
-    for (int32_t j = 0; j < n_scans; ++j) ord[j] = j;
-    std::stable_sort(ord.begin(), ord.end(),
-                     [&](int32_t a, int32_t b) { return so[a + 1] - so[a] > so[b + 1] - so[b]; });
-    int32_t* d_ord = (int32_t*)dev_alloc(h, h->keep, sizeof(int32_t) * (size_t)n_scans);
-    if (!d_ord) return fail(h, BA_ERR_OOM, "scan order: out of device memory");
-    CK(h, cudaMemcpyAsync(d_ord, ord.data(), sizeof(int32_t) * ord.size(), cudaMemcpyHostToDevice, h->stream),
-       "scan order");
-    L.scan_order = d_ord;
   }
   DevState s0{};
   s0.mu = h->cfg.mu0;
@@ -563,6 +565,7 @@ ba_status load_impl(ba_handle* h, int32_t n_scans, int64_t n_voxels, int64_t n_o
   st = read_state(h, &s);  // also drains the stream before temporaries are freed
   if (st != BA_OK) return st;
   free_list(h, h->temp);
+  h->lb.scan_pos = nullptr;  // a temporary of the load
   h->loaded = true;
   if (!std::isfinite(s.cost)) return fail(h, BA_ERR_NUMERIC, "cost at the initial poses is not finite");
   return BA_OK;

@@ -499,6 +499,12 @@ cudaError_t launch_vscale(const LoadInput& in, int64_t v0, int64_t v1, double* v
   return cudaGetLastError();
 }
 
+// inv[perm[q]] = q
+__global__ void inverse_perm_kernel(int64_t n, const uint32_t* perm, uint32_t* inv) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < n) inv[perm[q]] = (uint32_t)q;
+}
+
 cudaError_t build_layout(const LoadInput& in, int max_len, bool fill_f64, bool defer_scale, Allocator keep,
                          Allocator temp, LayoutBuffers* out, cudaStream_t stream, int64_t* launches) {
   const int64_t nv = in.n_voxels, no = in.n_obs;
@@ -516,6 +522,7 @@ cudaError_t build_layout(const LoadInput& in, int max_len, bool fill_f64, bool d
   int32_t* obs_vox = (int32_t*)maps.fn(maps.self, sizeof(int32_t) * no);
   double* vscale = (double*)maps.fn(maps.self, sizeof(double) * nv);
   uint32_t* order = fill_f64 ? nullptr : (uint32_t*)keep.fn(keep.self, sizeof(uint32_t) * no);
+  uint32_t* pos = !fill_f64 && defer_scale ? (uint32_t*)temp.fn(temp.self, sizeof(uint32_t) * no) : nullptr;
   // persistent
   out->slice_off = (int64_t*)keep.fn(keep.self, sizeof(int64_t) * (n_slices + 1));
   out->vlen = (int32_t*)keep.fn(keep.self, sizeof(int32_t) * nv);
@@ -525,8 +532,10 @@ cudaError_t build_layout(const LoadInput& in, int max_len, bool fill_f64, bool d
   // + 4 entries: the staged mixed scan pass copies whole 16-byte groups
   out->se_vox = (int32_t*)keep.fn(keep.self, sizeof(int32_t) * (no + 4));
   if (!keys || !vals || !tk || !tv || !scratch || !vrank || !obs_vox || !vscale || !out->slice_off || !out->vlen ||
-      !out->vperm || !out->scan_off || (fill_f64 && !out->se) || (!fill_f64 && !order) || !out->se_vox)
+      !out->vperm || !out->scan_off || (fill_f64 && !out->se) || (!fill_f64 && !order) || !out->se_vox ||
+      (!fill_f64 && defer_scale && !pos))
     return cudaErrorMemoryAllocation;
+  out->scan_pos = pos;
   out->vrank = vrank;
   out->obs_vox = obs_vox;
   out->vscale = vscale;
@@ -579,6 +588,11 @@ cudaError_t build_layout(const LoadInput& in, int max_len, bool fill_f64, bool d
   ++*launches;
   RETURN_IF(cudaGetLastError());
   if (order) RETURN_IF(cudaMemcpyAsync(order, vals, sizeof(uint32_t) * no, cudaMemcpyDeviceToDevice, stream));
+  if (pos) {
+    inverse_perm_kernel<<<(unsigned)((no + 255) / 256), 256, 0, stream>>>(no, vals, pos);
+    ++*launches;
+    RETURN_IF(cudaGetLastError());
+  }
   return cudaSuccess;
 }
 

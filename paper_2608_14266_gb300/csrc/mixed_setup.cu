@@ -295,12 +295,9 @@ __global__ void fill_sell_mixed_kernel(LoadInput in, const int32_t* vperm, const
 // quaternion (R_ref S R_ref^T = V diag(sigma) V^T), each scaled by 2 / N_i.
 // obs_pos[o] is the slot of observation o (sorted voxel position p, row k:
 // slice_off[p / 32] + 32 k + p % 32).
-__global__ void fill_scan_mixed_kernel(int64_t n_obs, const uint32_t* order, const int32_t* obs_vox,
-                                       const double* vscale, const int32_t* vrank, const int64_t* voxel_off,
-                                       const int64_t* slice_off, const float4* ve32, float* se32) {
-  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= n_obs) return;
-  const int64_t o = order[q];
+__device__ __forceinline__ void fill_scan_one(int64_t q, int64_t o, int64_t n_obs, const int32_t* obs_vox,
+                                              const double* vscale, const int32_t* vrank, const int64_t* voxel_off,
+                                              const int64_t* slice_off, const float4* ve32, float* se32) {
   const int32_t v = obs_vox[o];
   const int64_t p = vrank[v];
   const int64_t e = slice_off[p >> 5] + (o - voxel_off[v]) * kSlice + (p & 31);
@@ -322,6 +319,23 @@ __global__ void fill_scan_mixed_kernel(int64_t n_obs, const uint32_t* order, con
   bN[q] = make_float4(s0.x, s0.y, s0.z, k * s0.w);
   S4[q] = make_float4(k * sw[0], k * sw[1], k * sw[2], k * sw[3]);
   S2[q] = make_float2(k * sw[4], k * sw[5]);
+}
+
+// thread per scan-major position q (order[q] = its observation)
+__global__ void fill_scan_mixed_kernel(int64_t n_obs, const uint32_t* order, const int32_t* obs_vox,
+                                       const double* vscale, const int32_t* vrank, const int64_t* voxel_off,
+                                       const int64_t* slice_off, const float4* ve32, float* se32) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < n_obs) fill_scan_one(q, order[q], n_obs, obs_vox, vscale, vrank, voxel_off, slice_off, ve32, se32);
+}
+
+// thread per observation o in [o0, o1) (pos[o] = its scan-major position)
+__global__ void fill_scan_range_kernel(int64_t o0, int64_t o1, int64_t n_obs, const uint32_t* pos,
+                                       const int32_t* obs_vox, const double* vscale, const int32_t* vrank,
+                                       const int64_t* voxel_off, const int64_t* slice_off, const float4* ve32,
+                                       float* se32) {
+  const int64_t o = o0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (o < o1) fill_scan_one(pos[o], o, n_obs, obs_vox, vscale, vrank, voxel_off, slice_off, ve32, se32);
 }
 
 }  // namespace
@@ -354,14 +368,25 @@ cudaError_t build_mixed_voxels(const LoadInput& in, const LayoutBuffers& lb, con
   return cudaGetLastError();
 }
 
-cudaError_t build_mixed_end(const LoadInput& in, const LayoutBuffers& lb, const double* poses2, MixedBuffers& mb,
-                            cudaStream_t stream, int64_t* launches) {
-  const int64_t no = in.n_obs;
-  fill_scan_mixed_kernel<<<(unsigned)((no + 255) / 256), 256, 0, stream>>>(
-      no, lb.scan_order, lb.obs_vox, lb.vscale, lb.vrank, in.voxel_off, lb.slice_off, mb.ve32, mb.se32);
+cudaError_t build_mixed_scan_range(const LoadInput& in, const LayoutBuffers& lb, MixedBuffers& mb, int64_t o0,
+                                   int64_t o1, cudaStream_t stream, int64_t* launches) {
+  if (o1 <= o0) return cudaSuccess;
+  fill_scan_range_kernel<<<(unsigned)((o1 - o0 + 255) / 256), 256, 0, stream>>>(
+      o0, o1, in.n_obs, lb.scan_pos, lb.obs_vox, lb.vscale, lb.vrank, in.voxel_off, lb.slice_off, mb.ve32, mb.se32);
   ++*launches;
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+cudaError_t build_mixed_end(const LoadInput& in, const LayoutBuffers& lb, const double* poses2, MixedBuffers& mb,
+                            cudaStream_t stream, int64_t* launches, bool scan_filled) {
+  const int64_t no = in.n_obs;
+  if (!scan_filled) {
+    fill_scan_mixed_kernel<<<(unsigned)((no + 255) / 256), 256, 0, stream>>>(
+        no, lb.scan_order, lb.obs_vox, lb.vscale, lb.vrank, in.voxel_off, lb.slice_off, mb.ve32, mb.se32);
+    ++*launches;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   ++*launches;
   return launch_scan_table(in.n_scans, poses2, mb.sref, mb.stab2, 0, stream);
 }
