@@ -321,6 +321,10 @@ ba_status ba_server_step(ba_server* s, int32_t n_iters, int32_t* n_resident_out,
  * stats_out (either may be NULL) and the server forgets the job, so a later
  * poll of the same id is BA_ERR_INVALID_ARG (as is an unknown id). */
 ba_status ba_server_poll(ba_server* s, uint64_t job_id, int32_t* done, double* poses_out, ba_stats* stats_out);
+/* Cancel a job: a resident job leaves the batch at once (its device memory
+ * is released; the other jobs' results do not change), a finished job's
+ * unpolled results are dropped.  BA_ERR_INVALID_ARG for an unknown id. */
+ba_status ba_server_cancel(ba_server* s, uint64_t job_id);
 /* 1 if a job of these sizes would be admitted now, else 0 (lets a caller
  * prepare a job's inputs only when they can be taken). */
 int32_t ba_server_fits(const ba_server* s, int32_t n_scans, int64_t n_voxels, int64_t n_obs);

@@ -98,6 +98,7 @@ _SIGNATURES = {
     "ba_server_kernel_launches": (_I64, [_P]),
     "ba_server_last_error": (ctypes.c_char_p, [_P]),
     "ba_server_destroy": (None, [_P]),
+    "ba_server_cancel": (_I32, [_P, ctypes.c_uint64]),
     "ba_check_bounded_wait": (_I32, [_I32, _I32]),
     "ba_release_cached_memory": (_I32, [_I32]),
     "ba_check_conversions": (_I32, [_I32, _I64, ctypes.c_uint64, _P]),

@@ -161,6 +161,22 @@ ba_status ba_server_poll(ba_server* s, uint64_t job_id, int32_t* done, double* p
   return BA_OK;
 }
 
+ba_status ba_server_cancel(ba_server* s, uint64_t job_id) {
+  if (!s) return BA_ERR_INVALID_ARG;
+  if (s->finished.erase(job_id)) return BA_OK;
+  for (size_t k = 0; k < s->resident.size(); ++k) {
+    if (s->resident[k].id != job_id) continue;
+    Resident r = s->resident[k];
+    ba_status st = ba_batch_remove(s->batch, r.h);
+    if (st != BA_OK) return sfail(s, st, "job %llu: %s", (unsigned long long)r.id, ba_batch_last_error(s->batch));
+    ba_destroy(r.h);
+    s->used -= r.bytes;
+    s->resident.erase(s->resident.begin() + (long)k);
+    return BA_OK;
+  }
+  return sfail(s, BA_ERR_INVALID_ARG, "unknown job id %llu", (unsigned long long)job_id);
+}
+
 int32_t ba_server_fits(const ba_server* s, int32_t n_scans, int64_t n_voxels, int64_t n_obs) {
   if (!s || n_scans < 1 || n_voxels < 0 || n_obs < 0) return 0;
   int64_t peak = 0;

@@ -44,6 +44,7 @@ class Job:
     finished: float | None = None
     poses: np.ndarray | None = None
     stats: dict | None = None
+    error: str | None = None  # set when the job failed (its inputs, or the library refused them)
     server_id: int = field(default=0, repr=False)
 
     @property
@@ -68,6 +69,7 @@ class Server:
         self.queue: collections.deque[Job] = collections.deque()
         self.resident: list[Job] = []
         self.finished: list[Job] = []
+        self.failed: list[Job] = []  # jobs whose inputs failed or were refused; the others carry on
 
     def _check(self, status):
         if status != _lib.BA_OK:
@@ -92,12 +94,18 @@ class Server:
                 self._check(L.ba_server_submit(self.s, ctypes.byref(desc), ctypes.byref(ctypes.c_uint64())))
                 raise AssertionError("unreachable")
             self.queue.popleft()
-            vo, os_, ag, po = job.inputs()
-            a = (_Arg(vo, np.int64), _Arg(os_, np.int32), _Arg(ag, np.float64), _Arg(po, np.float64))
-            desc = BaJobDesc(job.n_scans, job.n_voxels, job.n_obs, a[0].ptr, a[1].ptr, a[2].ptr, BA_AGG_CENTRED,
-                             a[3].ptr, _mem_kind(*a))
-            jid = ctypes.c_uint64()
-            self._check(L.ba_server_submit(self.s, ctypes.byref(desc), ctypes.byref(jid)))
+            try:
+                vo, os_, ag, po = job.inputs()
+                a = (_Arg(vo, np.int64), _Arg(os_, np.int32), _Arg(ag, np.float64), _Arg(po, np.float64))
+                desc = BaJobDesc(job.n_scans, job.n_voxels, job.n_obs, a[0].ptr, a[1].ptr, a[2].ptr,
+                                 BA_AGG_CENTRED, a[3].ptr, _mem_kind(*a))
+                jid = ctypes.c_uint64()
+                self._check(L.ba_server_submit(self.s, ctypes.byref(desc), ctypes.byref(jid)))
+            except Exception as exc:  # a failed job is reported, the stream goes on
+                job.error = f"{type(exc).__name__}: {exc}"
+                job.finished = self.clock()
+                self.failed.append(job)
+                continue
             job.server_id = jid.value
             job.admitted = self.clock()
             self.resident.append(job)
@@ -129,6 +137,20 @@ class Server:
                 self.finished.append(job)
                 out.append(job)
         return out
+
+    def cancel(self, job: Job) -> None:
+        """Withdraw a queued or resident job (a resident one leaves the batch
+        at once and its memory is released)."""
+        if job in self.queue:
+            self.queue.remove(job)
+        elif job in self.resident:
+            self._check(_lib.lib().ba_server_cancel(self.s, job.server_id))
+            self.resident.remove(job)
+        else:
+            raise ValueError(f"job {job.job_id} is neither queued nor resident")
+        job.error = "cancelled"
+        job.finished = self.clock()
+        self.failed.append(job)
 
     @property
     def used(self) -> int:

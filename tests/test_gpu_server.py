@@ -129,3 +129,62 @@ def test_server_rejects_and_polls(mm):
         srv.step()
         assert len(srv.finished) == 2
         np.testing.assert_array_equal(srv.finished[0].poses, srv.finished[1].poses)
+
+
+def test_served_failures_and_cancellation_leave_others_unchanged(mm):
+    """Failures injected on the host into a served stream: a job whose input
+    source raises, a job with a non-finite cluster (refused by the load's
+    validation), and a resident job cancelled mid-solve.  Each is reported
+    with its reason, its memory is released, and the other jobs end with the
+    bits they reach alone."""
+    from paper_2608_14266_gb300.server import Job, Server
+    prec = mm.BA_MIXED
+    scenes = _scenes(6)
+    chunk = 3
+    cen = [library_clusters(mm, s, po, pts) for s, po, pts in scenes]
+    alone = {}
+    for k in (0, 2, 4):
+        s = scenes[k][0]
+        ba = mm.BundleAdjuster(precision=prec, **CFG)
+        ba.load_observations(s.n_scans, s.voxel_off, s.obs_scan, cen[k], s.pose_init)
+        with mm.Batch() as b:
+            b.add(ba)
+            b.solve(chunk=chunk)
+        alone[k] = (ba.poses(), ba.cost(), ba.stats()["iters"])
+        ba.close()
+    bad = cen[3].copy()
+    bad[5, 0] = np.nan
+
+    def source_fails():
+        raise RuntimeError("input source failed")
+
+    def inputs(k):
+        s = scenes[k][0]
+        if k == 1:
+            return source_fails
+        agg = bad if k == 3 else cen[k]
+        return lambda: (s.voxel_off, s.obs_scan, agg, s.pose_init)
+
+    jobs = {k: Job(k, scenes[k][0].n_scans, scenes[k][0].n_voxels, scenes[k][0].n_obs, inputs=inputs(k))
+            for k in range(6)}
+    with Server(1 << 34, chunk=chunk, precision=prec, **CFG) as srv:
+        for k in range(6):
+            srv.submit(jobs[k])
+        srv.step()
+        assert {j.job_id for j in srv.failed} == {1, 3}
+        assert "input source failed" in jobs[1].error and "BAError" in jobs[3].error
+        assert len(srv.resident) == 4  # 0, 2, 4, 5 are running
+        before = srv.used
+        srv.cancel(jobs[5])
+        assert srv.used < before and jobs[5].error == "cancelled"
+        with pytest.raises(ValueError):
+            srv.cancel(jobs[5])
+        while not srv.idle:
+            srv.step()
+        assert srv.used == 0
+        assert {j.job_id for j in srv.finished} == {0, 2, 4}
+        assert {j.job_id for j in srv.failed} == {1, 3, 5}
+        for job in srv.finished:
+            poses, cost, iters = alone[job.job_id]
+            np.testing.assert_array_equal(job.poses, poses)
+            assert job.stats["cost"] == cost and job.stats["iters"] == iters
