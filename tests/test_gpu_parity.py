@@ -200,7 +200,7 @@ def _edge_problem(rng, n_scans, lens, pts_per_obs=12):
 
 
 @pytest.mark.parametrize("case", ["single_obs_voxels", "long_voxels", "ragged_37", "idle_scans", "one_scan",
-                                  "no_fixed_scan"])
+                                  "no_fixed_scan", "one_voxel", "two_scans"])
 def test_edge_cases_match_oracle(mm, case):
     rng = np.random.default_rng(zlib.crc32(case.encode()))
     cfg = {}
@@ -216,6 +216,10 @@ def test_edge_cases_match_oracle(mm, case):
     elif case == "one_scan":
         n_scans, lens = 1, list(rng.integers(1, 4, 30))
         cfg = {"fixed_scan": -1}
+    elif case == "one_voxel":  # the whole problem is one plane seen by four scans
+        n_scans, lens = 4, [4]
+    elif case == "two_scans":
+        n_scans, lens = 2, list(rng.integers(1, 3, 25))
     else:
         n_scans, lens = 6, list(rng.integers(3, 10, 70))
         cfg = {"fixed_scan": -1}
