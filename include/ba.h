@@ -273,6 +273,10 @@ typedef struct {
   double ms_per_iter[16];   /* mean over the complete passes */
 } ba_tune_report;
 ba_status ba_batch_autotune(ba_batch* b, int32_t iters_per_trial, int32_t passes, ba_tune_report* out);
+/* Apply launch settings chosen earlier (e.g. a cached ba_batch_autotune
+ * result): min_blocks in {4, 6, 8}, prefetch in [0, 16].  Results do not
+ * depend on them.  BA_ERR_INVALID_ARG outside those ranges. */
+ba_status ba_batch_set_launch(ba_batch* b, int32_t min_blocks, int32_t prefetch);
 
 /* ---- Served execution (continuous batching) -----------------------------
  * The paper solves one problem at a time; a server keeps many independent

@@ -275,15 +275,45 @@ class Batch:
     def kernel_launches(self) -> int:
         return int(_lib.lib().ba_batch_kernel_launches(self.b))
 
-    def autotune(self, iters_per_trial: int = 2, passes: int = 2) -> dict:
+    def autotune(self, iters_per_trial: int = 2, passes: int = 2, cache: str | None = None) -> dict:
         """ba_batch_autotune: picks the voxel pass's launch settings on the
-        batch's own iterations; returns the candidates, timings and choice."""
+        batch's own iterations; returns the candidates, timings and choice.
+        With cache (a JSON file path), a choice stored for this device is
+        applied without trials, and a new choice is stored under the device's
+        name."""
+        key = None
+        if cache is not None:
+            import json
+            import os
+            import torch
+            key = torch.cuda.get_device_name(self.jobs[0].cfg.device if self.jobs else 0)
+            if os.path.exists(cache):
+                with open(cache) as f:
+                    known = json.load(f).get(key)
+                if known:
+                    self.set_launch(known["min_blocks"], known["prefetch"])
+                    return {"candidates": [], "chosen": -1, "passes": 0, "iterations": 0, "cached": known}
         r = _lib.BaTuneReport()
         self._check(_lib.lib().ba_batch_autotune(self.b, int(iters_per_trial), int(passes), ctypes.byref(r)))
         cands = [{"min_blocks": r.min_blocks[k], "prefetch": r.prefetch[k], "ms_per_iter": r.ms_per_iter[k]}
                  for k in range(r.n_candidates)]
-        return {"candidates": cands, "chosen": r.chosen, "passes": r.passes,
-                "iterations": r.n_candidates * int(iters_per_trial) * int(passes)}
+        out = {"candidates": cands, "chosen": r.chosen, "passes": r.passes,
+               "iterations": r.n_candidates * int(iters_per_trial) * int(passes)}
+        if key is not None and r.chosen >= 0:
+            import json
+            import os
+            table = {}
+            if os.path.exists(cache):
+                with open(cache) as f:
+                    table = json.load(f)
+            table[key] = {k: cands[r.chosen][k] for k in ("min_blocks", "prefetch")}
+            with open(cache, "w") as f:
+                json.dump(table, f, indent=1)
+        return out
+
+    def set_launch(self, min_blocks: int, prefetch: int):
+        """ba_batch_set_launch: apply stored launch settings (results do not depend on them)."""
+        self._check(_lib.lib().ba_batch_set_launch(self.b, int(min_blocks), int(prefetch)))
 
     def close(self):
         if self.b:

@@ -103,6 +103,7 @@ _SIGNATURES = {
     "ba_release_cached_memory": (_I32, [_I32]),
     "ba_check_conversions": (_I32, [_I32, _I64, ctypes.c_uint64, _P]),
     "ba_batch_autotune": (_I32, [_P, _I32, _I32, _P]),
+    "ba_batch_set_launch": (_I32, [_P, _I32, _I32]),
     "ba_voxelize_config_default": (None, [_P]),
     "ba_voxelize": (_I32, [_P, _I32, _P, _P, _P, _I32, _P]),
     "ba_voxels_size": (_I32, [_P, _P, _P]),

@@ -1426,6 +1426,18 @@ ba_status ba_batch_autotune(ba_batch* b, int32_t iters_per_trial, int32_t passes
   return BA_OK;
 }
 
+ba_status ba_batch_set_launch(ba_batch* b, int32_t min_blocks, int32_t prefetch) {
+  if (!b) return BA_ERR_INVALID_ARG;
+  if ((min_blocks != 4 && min_blocks != 6 && min_blocks != 8) || prefetch < 0 || prefetch > 16)
+    return bfail(b, BA_ERR_INVALID_ARG, "min_blocks must be 4, 6 or 8 and prefetch in [0, 16]");
+  if (b->vp_min_blocks != min_blocks || b->vp_prefetch != prefetch) {
+    b->vp_min_blocks = min_blocks;
+    b->vp_prefetch = prefetch;
+    drop_graph(b);
+  }
+  return BA_OK;
+}
+
 void ba_batch_destroy(ba_batch* b) {
   if (!b) return;
   DeviceGuard g(b->device >= 0 ? b->device : 0);

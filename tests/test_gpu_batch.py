@@ -201,3 +201,37 @@ def test_autotune_leaves_results_bit_identical(mm):
         rep = b.autotune()
         assert rep["candidates"] == [] and rep["chosen"] == -1
     j.close()
+
+
+def test_autotune_cache_and_set_launch(mm, tmp_path):
+    """A tuned choice is stored under the device's name; a later batch
+    applies it without trials; stored or explicit settings leave the results
+    bit-identical; settings outside the variants are refused."""
+    import json
+    scenes = _job_scenes(3, seed=6)
+    cfg = dict(precision=mm.BA_MIXED, rel_tol=1e-12, max_iters=40)
+    cache = str(tmp_path / "tune.json")
+    runs = []
+    for mode in ("tune", "cached", "explicit"):
+        jobs = [_load(mm, s, po, pts, **cfg) for s, po, pts in scenes]
+        with mm.Batch() as b:
+            for j in jobs:
+                b.add(j)
+            if mode == "explicit":
+                b.set_launch(4, 0)
+                with pytest.raises(mm.BAError):
+                    b.set_launch(5, 0)
+            else:
+                rep = b.autotune(iters_per_trial=1, passes=1, cache=cache)
+                if mode == "cached":
+                    assert rep["iterations"] == 0 and "cached" in rep
+            b.solve(chunk=4)
+        runs.append([(j.poses(), j.cost(), j.stats()["iters"]) for j in jobs])
+        for j in jobs:
+            j.close()
+    table = json.load(open(cache))
+    assert len(table) == 1 and set(next(iter(table.values()))) == {"min_blocks", "prefetch"}
+    for other in runs[1:]:
+        for (p0, c0, i0), (p1, c1, i1) in zip(runs[0], other):
+            np.testing.assert_array_equal(p0, p1)
+            assert c0 == c1 and i0 == i1
