@@ -10,7 +10,9 @@ import os
 import threading
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libmmba.so")
+# MMBA_CHECKED=1 loads the checked variant (index checks in the kernels, see
+# build.build(checked=True)); it is built on request, never implied
+LIB_PATH = os.path.join(HERE, "libmmba_checked.so" if os.environ.get("MMBA_CHECKED") == "1" else "libmmba.so")
 
 BA_OK = 0
 STATUS_NAMES = {0: "BA_OK", 1: "BA_ERR_INVALID_ARG", 2: "BA_ERR_OOM", 3: "BA_ERR_CUDA", 4: "BA_ERR_STATE",

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "../../include/ba.h"
+#include "checked.cuh"
 #include "mmba_internal.cuh"
 #include "mmba_kernels.h"
 
@@ -218,6 +219,8 @@ __global__ void expand_gh_kernel(const double* gH, int32_t n_scans, double* g, d
 ba_status read_state(ba_handle* h, DevState* out) {
   CK(h, cudaMemcpyAsync(out, h->d_state, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream), "read state");
   CK(h, cudaStreamSynchronize(h->stream), "synchronize");
+  if (out->wait_timeout == kErrIndex)
+    return fail(h, BA_ERR_STATE, "a kernel read an index out of range (checked build)");
   if (out->wait_timeout)
     return fail(h, BA_ERR_TIMEOUT, "a bounded device-side wait gave up (staged copies of the scan pass did not land)");
   return BA_OK;

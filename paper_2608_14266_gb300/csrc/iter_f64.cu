@@ -1,6 +1,7 @@
 // FP64 iteration kernels: voxel pass (CalRes), scan pass (CalJH), per-scan
 // damped solve + retraction (Solver) and the device-side LM decision
 // (Algorithm 2 and Sec. IV-C of the paper).
+#include "checked.cuh"
 #include "mmba_internal.cuh"
 #include "mmba_kernels.h"
 
@@ -44,7 +45,7 @@ __device__ __forceinline__ void voxel_pass_f64_body(const DevLayout& L, const do
     double m00 = 0.0, m01 = 0.0, m02 = 0.0, m11 = 0.0, m12 = 0.0, m22 = 0.0;
     for (int k = 0; k < len; ++k) {
       const int64_t e = base + (int64_t)k * kSlice;
-      const double* __restrict__ P = poses + 12 * (int64_t)__ldg(L.ve_scan + e);
+      const double* __restrict__ P = poses + 12 * (int64_t)MMBA_IDX(__ldg(L.ve_scan + e), L.n_scans, st);
       const double S00 = __ldg(L.ve + e), S01 = __ldg(L.ve + ne + e), S02 = __ldg(L.ve + 2 * ne + e);
       const double S11 = __ldg(L.ve + 3 * ne + e), S12 = __ldg(L.ve + 4 * ne + e), S22 = __ldg(L.ve + 5 * ne + e);
       const double mx = __ldg(L.ve + 6 * ne + e), my = __ldg(L.ve + 7 * ne + e), mz = __ldg(L.ve + 8 * ne + e);
@@ -177,7 +178,8 @@ __device__ __forceinline__ void scan_pass_f64_body(const DevLayout& L, const dou
   const int64_t lo = L.scan_off[j], hi = L.scan_off[j + 1];
   const int64_t no = L.n_obs;
   for (int64_t o = lo + threadIdx.x; o < hi; o += kScanThreads) {
-    const double4_32a pl = *reinterpret_cast<const double4_32a*>(planes + (int64_t)__ldg(L.se_vox + o) * kPlaneStride);
+    const double4_32a pl =
+        *reinterpret_cast<const double4_32a*>(planes + (int64_t)MMBA_IDX(__ldg(L.se_vox + o), L.n_voxels, st) * kPlaneStride);
     const double S00 = __ldg(L.se + o), S01 = __ldg(L.se + no + o), S02 = __ldg(L.se + 2 * no + o);
     const double S11 = __ldg(L.se + 3 * no + o), S12 = __ldg(L.se + 4 * no + o), S22 = __ldg(L.se + 5 * no + o);
     const double mx = __ldg(L.se + 6 * no + o), my = __ldg(L.se + 7 * no + o), mz = __ldg(L.se + 8 * no + o);
@@ -310,7 +312,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_pass_f64_kernel(DevLayout L
                                                                     double* __restrict__ gH,
                                                                     const DevState* __restrict__ st, int force) {
   __shared__ double red[kScanThreads / 32][kGH];
-  scan_pass_f64_body(L, poses2, planes2, gH, st, force, scan_of_block(L, blockIdx.x), red);
+  scan_pass_f64_body(L, poses2, planes2, gH, st, force, MMBA_IDX(scan_of_block(L, blockIdx.x), L.n_scans, st), red);
 }
 
 __global__ void __launch_bounds__(kScanThreads) scan_pass_f64_batch_kernel(JobTable T) {

@@ -2,6 +2,7 @@
 // clusters (anchors and reference poses fixed at load or at ba_set_state),
 // FP64 only per scan (6x6 solve, pose composition), in the sum over voxel
 // blocks and in the set-up that builds the FP32 copies.
+#include "checked.cuh"
 #include "mmba_internal.cuh"
 #include "mmba_kernels.h"
 
@@ -83,7 +84,7 @@ __device__ __forceinline__ void voxel_pass_mixed_body(const DevLayout& L, const 
         n1 = __ldg(slot + 1);
         n2 = __ldg(slot + 2);
       }
-      const int j = __float_as_int(f1.w);
+      const int j = MMBA_IDX(__float_as_int(f1.w), L.n_scans, st);
       const float4* T4 = reinterpret_cast<const float4*>(stab + (int64_t)j * kTab);
       const float4 qd = __ldg(T4), t1 = __ldg(T4 + 1), t2 = __ldg(T4 + 2);
       const float ph[3] = {qd.y, qd.z, qd.w};
@@ -374,7 +375,7 @@ __device__ __forceinline__ void scan_pass_mixed_body(const DevLayout& L, const D
     for (int q = 0; q < kScanChunk / 32; ++q) {
       const int i = lane + 32 * q;
       if (i < n) {
-        const int64_t pv = S.vox[i + off4];
+        const int64_t pv = MMBA_IDX((int64_t)S.vox[i + off4], L.n_voxels, st);
         pl[q] = __ldg(prec + 2 * pv);
         an[q] = __ldg(prec + 2 * pv + 1);
       }
@@ -397,7 +398,7 @@ __device__ __forceinline__ void scan_pass_mixed_body(const DevLayout& L, const D
   if (!ok) {
     // flag the failure, let the copies already issued land (bounded again), and leave
     if (lane == 0) {
-      atomicExch(&st->wait_timeout, 1);
+      atomicExch(&st->wait_timeout, kErrTimeout);
       for (int64_t q = k; q < nch && q < k + 2; ++q) mbar_wait_bounded((q & 1) ? bar1 : bar0, (uint32_t)((q >> 1) & 1));
     }
     __syncwarp();
@@ -461,7 +462,8 @@ __global__ void __launch_bounds__(kScanMixedThreads, 24) scan_pass_mixed_kernel(
   __shared__ float dR[9];
   __shared__ ScanChunk chunks[2];
   __shared__ uint64_t bars[2];
-  scan_pass_mixed_body(L, X, gH, st, force, scan_of_block(L, blockIdx.x), red, tot, dR, chunks, bars);
+  scan_pass_mixed_body(L, X, gH, st, force, MMBA_IDX(scan_of_block(L, blockIdx.x), L.n_scans, st), red, tot, dR,
+                       chunks, bars);
 }
 
 __global__ void __launch_bounds__(kScanMixedThreads, 20) scan_pass_mixed_batch_kernel(JobTable T) {
