@@ -1020,6 +1020,14 @@ struct ba_batch {
   int32_t* d_done = nullptr;    // per job stop flag, then the active count
   size_t cap = 0;
   int64_t n_vblk = 0, n_sblk = 0, n_oblk = 0;
+  // the iteration kernels' job groups (kernel parameters), with each group's
+  // voxel-pass, scan-pass and solve block counts
+  std::vector<JobGroup> groups;
+  std::vector<int64_t> group_blocks;  // 3 per group
+  // branch streams and events of the captured graph (group g >= 1 runs on
+  // branch g - 1; the groups' jobs are independent)
+  std::vector<cudaStream_t> branch;
+  std::vector<cudaEvent_t> branch_ev;  // fork, then one join per branch
   bool dirty = true;
   // captured iterations
   cudaGraphExec_t graph = nullptr;
@@ -1107,6 +1115,33 @@ ba_status refresh(ba_batch* b) {
   b->n_vblk = pre[n];
   b->n_sblk = pre[(n + 1) + n];
   b->n_oblk = pre[2 * (n + 1) + n];
+  const size_t ng = (n + kGroupJobs - 1) / kGroupJobs;
+  b->groups.assign(ng, JobGroup{});
+  b->group_blocks.assign(3 * ng, 0);
+  for (size_t g = 0; g < ng; ++g) {
+    JobGroup& G = b->groups[g];
+    const size_t k0 = g * kGroupJobs, k1 = std::min(n, k0 + kGroupJobs);
+    G.n_jobs = (int32_t)(k1 - k0);
+    int64_t v = 0, sc = 0, o = 0;
+    for (size_t k = k0; k < k1; ++k) {
+      const int i = (int)(k - k0);
+      G.jobs[i] = views[k];
+      G.vblk[i] = (int32_t)v;
+      G.sblk[i] = (int32_t)sc;
+      G.oblk[i] = (int32_t)o;
+      v += pre[k + 1] - pre[k];
+      sc += pre[(n + 1) + k + 1] - pre[(n + 1) + k];
+      o += pre[2 * (n + 1) + k + 1] - pre[2 * (n + 1) + k];
+    }
+    if (v > INT32_MAX || sc > INT32_MAX || o > INT32_MAX)
+      return bfail(b, BA_ERR_CAPACITY, "a group of %d jobs needs more than 2^31 - 1 blocks per launch", G.n_jobs);
+    G.vblk[G.n_jobs] = (int32_t)v;
+    G.sblk[G.n_jobs] = (int32_t)sc;
+    G.oblk[G.n_jobs] = (int32_t)o;
+    b->group_blocks[3 * g] = v;
+    b->group_blocks[3 * g + 1] = sc;
+    b->group_blocks[3 * g + 2] = o;
+  }
   if (n) {
     BCK(b, cudaMemcpyAsync(b->d_jobs, views.data(), sizeof(JobView) * n, cudaMemcpyHostToDevice, b->stream),
         "batch table upload");
@@ -1146,14 +1181,15 @@ __global__ void batch_status_kernel(JobTable T, int32_t* done) {
   }
 }
 
-ba_status launch_batch_iteration(ba_batch* b) {
-  const JobTable T = table_of(b);
-  BCK(b, launch_batch_solve(T, b->n_oblk, b->stream), "batch solve");
-  BCK(b, b->mixed ? launch_batch_voxel_pass_mixed(T, b->n_vblk, 1, b->stream, b->vp_min_blocks, b->vp_prefetch)
-                  : launch_batch_voxel_pass_f64(T, b->n_vblk, 1, b->stream),
+// one iteration of the jobs of group g, on stream
+ba_status launch_group_iteration(ba_batch* b, size_t g, cudaStream_t stream) {
+  const JobGroup& G = b->groups[g];
+  const int64_t* nb = &b->group_blocks[3 * g];
+  BCK(b, launch_batch_solve(G, nb[2], stream), "batch solve");
+  BCK(b, b->mixed ? launch_batch_voxel_pass_mixed(G, nb[0], 1, stream, b->vp_min_blocks, b->vp_prefetch)
+                  : launch_batch_voxel_pass_f64(G, nb[0], 1, stream),
       "batch voxel pass");
-  BCK(b, b->mixed ? launch_batch_scan_pass_mixed(T, b->n_sblk, b->stream)
-                  : launch_batch_scan_pass_f64(T, b->n_sblk, b->stream),
+  BCK(b, b->mixed ? launch_batch_scan_pass_mixed(G, nb[1], stream) : launch_batch_scan_pass_f64(G, nb[1], stream),
       "batch scan pass");
   return BA_OK;
 }
@@ -1175,11 +1211,38 @@ ba_status sync_members(ba_batch* b) {
 ba_status prepare_graph(ba_batch* b, int n) {
   if (b->graph_iters != n) {
     drop_graph(b);
+    const size_t ng = b->groups.size();
+    while (b->branch.size() + 1 < ng) {
+      cudaStream_t st = nullptr;
+      BCK(b, cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking), "branch stream");
+      b->branch.push_back(st);
+    }
+    while (b->branch_ev.size() < ng) {
+      cudaEvent_t ev = nullptr;
+      BCK(b, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "branch event");
+      b->branch_ev.push_back(ev);
+    }
     cudaGraph_t g = nullptr;
     BCK(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal), "graph capture");
+    // group 0 on the batch's stream, every other group on a branch forked
+    // from it and joined back at the end
     ba_status s = BA_OK;
-    for (int k = 0; k < n && s == BA_OK; ++k) s = launch_batch_iteration(b);
-    cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+    cudaError_t e = cudaSuccess;
+    if (ng > 1) {
+      e = cudaEventRecord(b->branch_ev[0], b->stream);
+      for (size_t k = 1; k < ng && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(b->branch[k - 1], b->branch_ev[0], 0);
+    }
+    if (e != cudaSuccess) s = bfail(b, BA_ERR_CUDA, "graph fork: %s", cudaGetErrorString(e));
+    for (size_t grp = 0; grp < ng && s == BA_OK; ++grp) {
+      cudaStream_t st = grp == 0 ? b->stream : b->branch[grp - 1];
+      for (int k = 0; k < n && s == BA_OK; ++k) s = launch_group_iteration(b, grp, st);
+    }
+    for (size_t k = 1; k < ng; ++k) {
+      cudaError_t ej = cudaEventRecord(b->branch_ev[k], b->branch[k - 1]);
+      if (ej == cudaSuccess) ej = cudaStreamWaitEvent(b->stream, b->branch_ev[k], 0);
+      if (ej != cudaSuccess && s == BA_OK) s = bfail(b, BA_ERR_CUDA, "graph join: %s", cudaGetErrorString(ej));
+    }
+    e = cudaStreamEndCapture(b->stream, &g);
     if (s != BA_OK) {
       if (g) cudaGraphDestroy(g);
       return s;
@@ -1197,7 +1260,7 @@ ba_status run_iterations(ba_batch* b, int n) {
   ba_status s = prepare_graph(b, n);
   if (s != BA_OK) return s;
   BCK(b, cudaGraphLaunch(b->graph, b->stream), "graph launch");
-  b->launches += 3 * (int64_t)n;
+  b->launches += 3 * (int64_t)n * (int64_t)b->groups.size();
   return BA_OK;
 }
 
@@ -1398,7 +1461,7 @@ ba_status ba_batch_autotune(ba_batch* b, int32_t iters_per_trial, int32_t passes
       if ((s = prepare_graph(b, iters_per_trial)) != BA_OK) return s;
       BCK(b, cudaEventRecord(e0, b->stream), "tuner events");
       BCK(b, cudaGraphLaunch(b->graph, b->stream), "graph launch");
-      b->launches += 3 * (int64_t)iters_per_trial;
+      b->launches += 3 * (int64_t)iters_per_trial * (int64_t)b->groups.size();
       BCK(b, cudaEventRecord(e1, b->stream), "tuner events");
       BCK(b, cudaEventSynchronize(e1), "tuner events");
       float t = 0.f;
@@ -1450,6 +1513,8 @@ void ba_batch_destroy(ba_batch* b) {
   cudaFree(b->d_jobs);
   cudaFree(b->d_prefix);
   cudaFree(b->d_done);
+  for (auto st : b->branch) cudaStreamDestroy(st);
+  for (auto ev : b->branch_ev) cudaEventDestroy(ev);
   if (b->own_stream) cudaStreamDestroy(b->stream);
   delete b;
 }

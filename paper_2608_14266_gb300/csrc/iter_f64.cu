@@ -130,19 +130,14 @@ __global__ void __launch_bounds__(kVoxelThreads) voxel_pass_f64_kernel(DevLayout
                              blockIdx.x, red, &is_last);
 }
 
-__global__ void __launch_bounds__(kVoxelThreads) voxel_pass_f64_batch_kernel(JobTable T, int use_trial) {
+__global__ void __launch_bounds__(kVoxelThreads) voxel_pass_f64_batch_kernel(const __grid_constant__ JobGroup G,
+                                                                             int use_trial) {
   __shared__ double red[kVoxelThreads / 32];
   __shared__ int is_last;
-  __shared__ JobView J;
-  __shared__ int64_t blk;
-  if (threadIdx.x == 0) {
-    const int job = find_job(T.vblk, T.n_jobs, blockIdx.x);
-    J = T.jobs[job];
-    blk = blockIdx.x - T.vblk[job];
-  }
-  __syncthreads();
+  const int job = find_job(G.vblk, G.n_jobs, blockIdx.x);
+  const JobView& J = G.jobs[job];
   voxel_pass_f64_body<false>(J.L, J.poses2, J.planes2, nullptr, J.cost_part, J.pred_part, J.st, use_trial,
-                             use_trial ? 0 : 1, blk, red, &is_last);
+                             use_trial ? 0 : 1, (int64_t)blockIdx.x - G.vblk[job], red, &is_last);
 }
 
 // ---------------------------------------------------------------------------
@@ -315,17 +310,12 @@ __global__ void __launch_bounds__(kScanThreads) scan_pass_f64_kernel(DevLayout L
   scan_pass_f64_body(L, poses2, planes2, gH, st, force, MMBA_IDX(scan_of_block(L, blockIdx.x), L.n_scans, st), red);
 }
 
-__global__ void __launch_bounds__(kScanThreads) scan_pass_f64_batch_kernel(JobTable T) {
+__global__ void __launch_bounds__(kScanThreads) scan_pass_f64_batch_kernel(const __grid_constant__ JobGroup G) {
   __shared__ double red[kScanThreads / 32][kGH];
-  __shared__ JobView J;
-  __shared__ int j;
-  if (threadIdx.x == 0) {
-    const int job = find_job(T.sblk, T.n_jobs, blockIdx.x);
-    J = T.jobs[job];
-    j = scan_of_block(J.L, blockIdx.x - T.sblk[job]);
-  }
-  __syncthreads();
-  scan_pass_f64_body(J.L, J.poses2, J.planes2, J.gH, J.st, 0, j, red);
+  const int job = find_job(G.sblk, G.n_jobs, blockIdx.x);
+  const JobView& J = G.jobs[job];
+  scan_pass_f64_body(J.L, J.poses2, J.planes2, J.gH, J.st, 0,
+                     MMBA_IDX(scan_of_block(J.L, (int64_t)blockIdx.x - G.sblk[job]), J.L.n_scans, J.st), red);
 }
 
 // ---------------------------------------------------------------------------
@@ -433,17 +423,11 @@ __global__ void __launch_bounds__(kSolveThreads) solve_f64_kernel(DevLayout L, d
   solve_f64_body(L, poses2, gH, pred_part, st, sref, stab2, blockIdx.x, red);
 }
 
-__global__ void __launch_bounds__(kSolveThreads) solve_f64_batch_kernel(JobTable T) {
+__global__ void __launch_bounds__(kSolveThreads) solve_f64_batch_kernel(const __grid_constant__ JobGroup G) {
   __shared__ double red[kSolveThreads / 32];
-  __shared__ JobView J;
-  __shared__ int64_t blk;
-  if (threadIdx.x == 0) {
-    const int job = find_job(T.oblk, T.n_jobs, blockIdx.x);
-    J = T.jobs[job];
-    blk = blockIdx.x - T.oblk[job];
-  }
-  __syncthreads();
-  solve_f64_body(J.L, J.poses2, J.gH, J.pred_part, J.st, J.X.sref, J.X.stab2, blk, red);
+  const int job = find_job(G.oblk, G.n_jobs, blockIdx.x);
+  const JobView& J = G.jobs[job];
+  solve_f64_body(J.L, J.poses2, J.gH, J.pred_part, J.st, J.X.sref, J.X.stab2, (int64_t)blockIdx.x - G.oblk[job], red);
 }
 
 __global__ void __launch_bounds__(kDecideThreads) decide_kernel(const double* __restrict__ cost_part, int64_t n_cost,
@@ -451,13 +435,6 @@ __global__ void __launch_bounds__(kDecideThreads) decide_kernel(const double* __
                                                                DevState* st, int mode) {
   __shared__ double red[kDecideThreads / 32];
   decide_body<kDecideThreads>(cost_part, n_cost, pred_part, n_pred, st, mode, red);
-}
-
-// one block per job
-__global__ void __launch_bounds__(kDecideThreads) decide_batch_kernel(JobTable T) {
-  __shared__ double red[kDecideThreads / 32];
-  const JobView& J = T.jobs[blockIdx.x];
-  decide_body<kDecideThreads>(J.cost_part, J.n_cost, J.pred_part, solve_blocks(J.L.n_scans), J.st, 0, red);
 }
 
 // ---- launchers ---------------------------------------------------------------
@@ -495,22 +472,17 @@ cudaError_t launch_decide(const double* cost_part, int64_t n_cost, const double*
   return cudaGetLastError();
 }
 
-cudaError_t launch_batch_solve(const JobTable& T, int64_t n_blocks, cudaStream_t stream) {
+cudaError_t launch_batch_solve(const JobGroup& T, int64_t n_blocks, cudaStream_t stream) {
   solve_f64_batch_kernel<<<(unsigned)n_blocks, kSolveThreads, 0, stream>>>(T);
   return cudaGetLastError();
 }
 
-cudaError_t launch_batch_decide(const JobTable& T, cudaStream_t stream) {
-  decide_batch_kernel<<<(unsigned)T.n_jobs, kDecideThreads, 0, stream>>>(T);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_batch_voxel_pass_f64(const JobTable& T, int64_t n_blocks, int use_trial, cudaStream_t stream) {
+cudaError_t launch_batch_voxel_pass_f64(const JobGroup& T, int64_t n_blocks, int use_trial, cudaStream_t stream) {
   voxel_pass_f64_batch_kernel<<<(unsigned)n_blocks, kVoxelThreads, 0, stream>>>(T, use_trial);
   return cudaGetLastError();
 }
 
-cudaError_t launch_batch_scan_pass_f64(const JobTable& T, int64_t n_blocks, cudaStream_t stream) {
+cudaError_t launch_batch_scan_pass_f64(const JobGroup& T, int64_t n_blocks, cudaStream_t stream) {
   scan_pass_f64_batch_kernel<<<(unsigned)n_blocks, kScanThreads, 0, stream>>>(T);
   return cudaGetLastError();
 }

@@ -192,21 +192,15 @@ __global__ void __launch_bounds__(kVoxelThreads, 6) voxel_pass_mixed_kernel(DevL
 // kMinBlocks (resident blocks per SM the registers are capped for) and pf are
 // the batch tuner's knobs: neither changes any arithmetic
 template <int kMinBlocks>
-__global__ void __launch_bounds__(kVoxelThreads, kMinBlocks) voxel_pass_mixed_batch_kernel(JobTable T, int use_trial,
-                                                                                           int pf) {
+__global__ void __launch_bounds__(kVoxelThreads, kMinBlocks)
+    voxel_pass_mixed_batch_kernel(const __grid_constant__ JobGroup G, int use_trial, int pf) {
   __shared__ float red[kVoxelThreads / 32];
   __shared__ double dred[kVoxelThreads / 32];
   __shared__ int is_last;
-  __shared__ JobView J;
-  __shared__ int64_t blk;
-  if (threadIdx.x == 0) {
-    const int job = find_job(T.vblk, T.n_jobs, blockIdx.x);
-    J = T.jobs[job];
-    blk = blockIdx.x - T.vblk[job];
-  }
-  __syncthreads();
-  voxel_pass_mixed_body<false>(J.L, J.X, nullptr, J.cost_part, J.pred_part, J.st, use_trial, use_trial ? 0 : 1, blk,
-                               red, dred, &is_last, pf);
+  const int job = find_job(G.vblk, G.n_jobs, blockIdx.x);
+  const JobView& J = G.jobs[job];
+  voxel_pass_mixed_body<false>(J.L, J.X, nullptr, J.cost_part, J.pred_part, J.st, use_trial, use_trial ? 0 : 1,
+                               (int64_t)blockIdx.x - G.vblk[job], red, dred, &is_last, pf);
 }
 
 // ---------------------------------------------------------------------------
@@ -466,21 +460,18 @@ __global__ void __launch_bounds__(kScanMixedThreads, 24) scan_pass_mixed_kernel(
                        chunks, bars);
 }
 
-__global__ void __launch_bounds__(kScanMixedThreads, 20) scan_pass_mixed_batch_kernel(JobTable T) {
+__global__ void __launch_bounds__(kScanMixedThreads, 24)
+    scan_pass_mixed_batch_kernel(const __grid_constant__ JobGroup G) {
   __shared__ float red[1][kGH];
   __shared__ float tot[kGH];
   __shared__ float dR[9];
   __shared__ ScanChunk chunks[2];
   __shared__ uint64_t bars[2];
-  __shared__ JobView J;
-  __shared__ int j;
-  if (threadIdx.x == 0) {
-    const int job = find_job(T.sblk, T.n_jobs, blockIdx.x);
-    J = T.jobs[job];
-    j = scan_of_block(J.L, blockIdx.x - T.sblk[job]);
-  }
-  __syncthreads();
-  scan_pass_mixed_body(J.L, J.X, J.gH, J.st, 0, j, red, tot, dR, chunks, bars);
+  const int job = find_job(G.sblk, G.n_jobs, blockIdx.x);
+  const JobView& J = G.jobs[job];
+  scan_pass_mixed_body(J.L, J.X, J.gH, J.st, 0,
+                       MMBA_IDX(scan_of_block(J.L, (int64_t)blockIdx.x - G.sblk[job]), J.L.n_scans, J.st), red, tot,
+                       dR, chunks, bars);
 }
 
 // Check of the bounded wait itself: an mbarrier that nothing arrives on, so
@@ -528,7 +519,7 @@ cudaError_t launch_scan_pass_mixed(const DevLayout& L, const DevMixed& X, const 
   return cudaGetLastError();
 }
 
-cudaError_t launch_batch_voxel_pass_mixed(const JobTable& T, int64_t n_blocks, int use_trial, cudaStream_t stream,
+cudaError_t launch_batch_voxel_pass_mixed(const JobGroup& T, int64_t n_blocks, int use_trial, cudaStream_t stream,
                                           int min_blocks, int pf) {
   switch (min_blocks) {
     case 4:
@@ -543,7 +534,7 @@ cudaError_t launch_batch_voxel_pass_mixed(const JobTable& T, int64_t n_blocks, i
   return cudaGetLastError();
 }
 
-cudaError_t launch_batch_scan_pass_mixed(const JobTable& T, int64_t n_blocks, cudaStream_t stream) {
+cudaError_t launch_batch_scan_pass_mixed(const JobGroup& T, int64_t n_blocks, cudaStream_t stream) {
   scan_pass_mixed_batch_kernel<<<(unsigned)n_blocks, kScanMixedThreads, 0, stream>>>(T);
   return cudaGetLastError();
 }

@@ -230,8 +230,27 @@ struct JobTable {
   int32_t n_jobs;
 };
 
+// The iteration kernels of a batch take their jobs by value, as a kernel
+// parameter: a group of up to kGroupJobs job views with block prefixes
+// relative to the group.  The views then sit in the constant bank like the
+// arguments of a single job's launch, so the per-job bases the observation
+// loops use cost no registers (read from a table in global memory they are
+// held in registers across the loops, and the passes spill).  A batch of more
+// jobs launches one group per kernel kind and group, each group's chain of
+// launches on its own branch of the captured graph.
+constexpr int kGroupJobs = 128;
+struct JobGroup {
+  JobView jobs[kGroupJobs];
+  int32_t vblk[kGroupJobs + 1];  // prefix of voxel-pass blocks
+  int32_t sblk[kGroupJobs + 1];  // prefix of scan-pass blocks (one per scan)
+  int32_t oblk[kGroupJobs + 1];  // prefix of solve blocks
+  int32_t n_jobs;
+};
+static_assert(sizeof(JobGroup) <= 32000, "a job group must fit the kernel parameter space");
+
 // job owning block b: the largest i with prefix[i] <= b
-__device__ __forceinline__ int find_job(const int64_t* prefix, int n_jobs, int64_t b) {
+template <typename P>
+__device__ __forceinline__ int find_job(const P* prefix, int n_jobs, int64_t b) {
   int lo = 0, hi = n_jobs;  // prefix[lo] <= b < prefix[hi]
   while (hi - lo > 1) {
     const int mid = (lo + hi) >> 1;

@@ -17,16 +17,15 @@ constexpr int kSolveThreads = 64;  // FP64-serial per scan: small blocks spread 
 __host__ __device__ inline int64_t voxel_pass_blocks(int64_t n_voxels) { return (n_voxels + kVoxelThreads - 1) / kVoxelThreads; }
 __host__ __device__ inline int64_t solve_blocks(int64_t n_scans) { return (n_scans + kSolveThreads - 1) / kSolveThreads; }
 
-// ---- batched launches over a job table (one launch per kind for all jobs) ----
-cudaError_t launch_batch_solve(const JobTable& T, int64_t n_blocks, cudaStream_t stream);
-cudaError_t launch_batch_decide(const JobTable& T, cudaStream_t stream);
-cudaError_t launch_batch_voxel_pass_f64(const JobTable& T, int64_t n_blocks, int use_trial, cudaStream_t stream);
-cudaError_t launch_batch_scan_pass_f64(const JobTable& T, int64_t n_blocks, cudaStream_t stream);
+// ---- batched launches over a job group (one launch per kind for the group's jobs) ----
+cudaError_t launch_batch_solve(const JobGroup& T, int64_t n_blocks, cudaStream_t stream);
+cudaError_t launch_batch_voxel_pass_f64(const JobGroup& T, int64_t n_blocks, int use_trial, cudaStream_t stream);
+cudaError_t launch_batch_scan_pass_f64(const JobGroup& T, int64_t n_blocks, cudaStream_t stream);
 // min_blocks in {4, 6, 8} (register cap of the batch voxel pass), pf = L2
 // prefetch distance in slot rows (0 = none); neither changes the results
-cudaError_t launch_batch_voxel_pass_mixed(const JobTable& T, int64_t n_blocks, int use_trial, cudaStream_t stream,
+cudaError_t launch_batch_voxel_pass_mixed(const JobGroup& T, int64_t n_blocks, int use_trial, cudaStream_t stream,
                                           int min_blocks = 6, int pf = 2);
-cudaError_t launch_batch_scan_pass_mixed(const JobTable& T, int64_t n_blocks, cudaStream_t stream);
+cudaError_t launch_batch_scan_pass_mixed(const JobGroup& T, int64_t n_blocks, cudaStream_t stream);
 
 // ---- iteration (FP64) ----
 // decide_mode: 0 = LM decision in the launch's last block (an iteration's

@@ -84,6 +84,43 @@ def test_batch_iterations_equal_alone(mm, precision):
         j.close()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batch_of_several_job_groups_equals_alone(mm, precision):
+    """More jobs than one launch parameter group holds (128): the groups run
+    on separate branches of the captured graph, and every job still ends with
+    the bits it reaches alone, the last, partial group included."""
+    prec = mm.BA_MIXED if precision == "mixed" else mm.BA_FP64
+    rng = np.random.default_rng(77)
+    scenes = []
+    for k in range(2 * 128 + 3):
+        n_scans = int(rng.integers(3, 9))
+        p = scenegen.SceneParams(n_scans=n_scans, n_voxels=20 * n_scans, obs_min=3, obs_max=8, pts_per_obs=8,
+                                 noise_sigma=0.02, rot_sigma_deg=0.5, trans_sigma=0.1, seed=7100 + k)
+        sc = scenegen.make_scene(p)
+        scenes.append((sc, sc.point_offsets(), sc.points()))
+    alone = []
+    for s, po, pts in scenes:
+        ba = _load(mm, s, po, pts, precision=prec)
+        with mm.Batch() as one:
+            one.add(ba)
+            one.iterate(3)
+        alone.append((ba.poses(), ba.cost()))
+        ba.close()
+    jobs = [_load(mm, s, po, pts, precision=prec) for s, po, pts in scenes]
+    with mm.Batch() as b:
+        for j in jobs:
+            b.add(j)
+        l0 = b.kernel_launches()
+        b.iterate(3)
+        # 3 iterations x 3 kernel kinds x 3 groups, plus the control and status launches
+        assert b.kernel_launches() - l0 == 3 * 3 * 3 + 2
+        for j, (poses, cost) in zip(jobs, alone):
+            np.testing.assert_array_equal(j.poses(), poses)
+            assert j.cost() == cost
+    for j in jobs:
+        j.close()
+
+
 def test_batch_matches_oracle_for_one_job(mm):
     (s, po, pts), = _job_scenes(1, seed=3)
     cen = oracle.points_to_centred(po, pts)
