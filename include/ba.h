@@ -121,8 +121,9 @@ ba_status ba_create(const ba_config* cfg, ba_handle** out);
  * All four arrays live in host or device memory per mem_kind.  The library
  * validates everything (BA_ERR_INVALID_ARG names the first violation), builds
  * its device layout (voxel-sorted slices and a scan-major copy, Algorithm 1's
- * mappers), and evaluates planes, cost, gradient and Hessian at the initial
- * poses.  Replaces any previously loaded problem.  The LM state (mu, nu,
+ * mappers; the voxels in a spatial order taken from the initial positions of
+ * the scans observing them, whatever their input order), and evaluates
+ * planes, cost, gradient and Hessian at the initial poses.  Replaces any previously loaded problem.  The LM state (mu, nu,
  * counters) is reset. */
 ba_status ba_load_observations(ba_handle* h, int32_t n_scans, int64_t n_voxels, int64_t n_obs,
                                const int64_t* voxel_offsets, const int32_t* obs_scan, const double* agg,
@@ -162,7 +163,11 @@ ba_status ba_get_stats(ba_handle* h, ba_stats* out);
 /* Replace the current poses (host or device, n_scans x 12) and the damping
  * state, then re-evaluate planes, cost, gradient and Hessian there.  With
  * this a solve can be resumed from saved poses.  mu <= 0 keeps the current
- * mu; nu <= 0 keeps the current nu. */
+ * mu; nu <= 0 keeps the current nu.  The device layout (the voxel order,
+ * and with it the order of every floating-point sum) is a function of the
+ * loaded inputs, the poses passed to the load included: a resume reproduces
+ * an uninterrupted solve bit for bit when it loads the same inputs and then
+ * sets the saved state. */
 ba_status ba_set_state(ba_handle* h, const double* poses, double mu, double nu, int32_t mem_kind);
 
 /* Plane records (n_voxels x 9 doubles, input voxel order) at the current

@@ -376,9 +376,10 @@ ba_status load_impl(ba_handle* h, int32_t n_scans, int64_t n_voxels, int64_t n_o
   // mixed precision keeps device copies of the inputs: the FP32 copies are
   // rebuilt from them when the reference poses change (ba_set_state)
   const bool own = h->mixed;
-  // A mixed load of host inputs copies the clusters in chunks of whole
-  // length-sort windows on a copy stream, and sets up each chunk's voxels
-  // while the next chunk is on its way.
+  // A mixed load of host inputs copies the clusters in chunks of input
+  // voxels on a copy stream, and sets up each chunk's voxels (frames,
+  // anchors, slots wherever their slices lie, their scan-major entries) while
+  // the next chunk is on its way.
   const bool pipelined = h->mixed && mem_kind == BA_MEM_HOST && agg_mem_kind == BA_MEM_HOST && n_voxels > kWindow;
   in.voxel_off = stage(h, voxel_off, (size_t)n_voxels + 1, mem_kind, own, &e);
   if (e != cudaSuccess) return cuda_fail(h, e, "stage voxel offsets");
@@ -526,16 +527,21 @@ ba_status load_impl(ba_handle* h, int32_t n_scans, int64_t n_voxels, int64_t n_o
     h->in_keep.poses = nullptr;
     if (pipelined) {
       CK(h, build_mixed_begin(in, h->poses2, mb, h->stream, &h->launches), "mixed-precision copies");
+      // slots staged in input order while the chunks arrive, placed in their
+      // slices (spatial windows draw voxels from every chunk) at the end
+      float4* staging = (float4*)dev_alloc(h, h->temp, sizeof(float4) * 3 * (size_t)n_obs);
+      if (!staging) return fail(h, BA_ERR_OOM, "slot staging: out of device memory");
       for (int k = 0; k < n_chunks; ++k) {
         const int64_t v0 = chunk_v[k], v1 = chunk_v[k + 1];
         CK(h, cudaStreamWaitEvent(h->stream, h->copy_events[k], 0), "wait for clusters");
         CK(h, launch_validate_agg(in, voxel_off[v0], voxel_off[v1], d_val, h->stream, &h->launches), "validate");
         CK(h, launch_vscale(in, v0, v1, lb.vscale, h->stream, &h->launches), "voxel scales");
-        CK(h, build_mixed_voxels(in, lb, h->poses2, mb, v0, v1, h->stream, &h->launches), "mixed-precision copies");
-        CK(h, build_mixed_scan_range(in, lb, mb, voxel_off[v0], voxel_off[v1], h->stream, &h->launches),
+        CK(h, build_mixed_voxels(in, lb, h->poses2, mb, v0, v1, voxel_off[v0], voxel_off[v1], staging, h->stream,
+                                 &h->launches),
            "mixed-precision copies");
       }
-      CK(h, build_mixed_end(in, lb, h->poses2, mb, h->stream, &h->launches, true), "mixed-precision copies");
+      CK(h, build_mixed_place(in, lb, mb, staging, h->stream, &h->launches), "mixed-precision copies");
+      CK(h, build_mixed_end(in, lb, h->poses2, mb, h->stream, &h->launches), "mixed-precision copies");
       CK(h, cudaMemcpyAsync(&res, d_val, sizeof res, cudaMemcpyDeviceToHost, h->stream), "validation result");
       CK(h, cudaStreamSynchronize(h->stream), "validation sync");
       if ((vs = check_validation(h, res, n_scans)) != BA_OK) return vs;
@@ -568,7 +574,6 @@ ba_status load_impl(ba_handle* h, int32_t n_scans, int64_t n_voxels, int64_t n_o
   st = read_state(h, &s);  // also drains the stream before temporaries are freed
   if (st != BA_OK) return st;
   free_list(h, h->temp);
-  h->lb.scan_pos = nullptr;  // a temporary of the load
   h->loaded = true;
   if (!std::isfinite(s.cost)) return fail(h, BA_ERR_NUMERIC, "cost at the initial poses is not finite");
   return BA_OK;
@@ -925,9 +930,13 @@ int64_t ba_estimate_bytes(int32_t precision, int32_t n_scans, int64_t n_voxels, 
   const int64_t per_scan = 8 + 24 * 8 + 27 * 8 + 8 + 26 * 8 + 2 * kTab * 4;
   const int64_t keep = per_obs * n_obs + per_slot * slots + per_voxel * n_voxels + per_scan * (int64_t)n_scans +
                        (1 << 16);
-  // load: staged inputs (host inputs), sort keys/values and scratch
+  // load: staged inputs (host inputs), sort keys/values and scratch, the
+  // spatial order's per-voxel means and prefixes, and (mixed loads of host
+  // inputs) the slots staged in input order
   const int64_t nsort = n_obs > n_voxels ? n_obs : n_voxels;
-  if (peak_extra) *peak_extra = (80 + 4 + 8) * n_obs + 16 * nsort + 24 * nsort / 16 + 8 * (int64_t)n_voxels;
+  if (peak_extra)
+    *peak_extra = (80 + 4 + 8 + (precision == BA_MIXED ? 16 * kVe32 : 0)) * n_obs + 16 * nsort + 24 * nsort / 16 +
+                  (8 + 16 + 8 + 8) * (int64_t)n_voxels;
   return keep;
 }
 

@@ -381,14 +381,87 @@ __device__ inline void to_centred(const double* a, int form, double out[10]) {
 
 // key = (window << len_bits) | (max_len - len): ascending order = windows in
 // input order, longest voxels first inside a window.
-__global__ void voxel_keys_kernel(const int64_t* off, int64_t n_voxels, int max_len, int len_bits, uint32_t* keys,
-                                  uint32_t* vals) {
+// ---- spatial order of the voxels ----
+// Mean translation of the scans observing each voxel (FP32, summed in the
+// voxel's observation order), and the bounding box of those means as
+// order-preserving unsigned encodings of the floats (min and max are exact,
+// so the box does not depend on the order of the atomics).
+__device__ __forceinline__ uint32_t float_order_key(float f) {
+  const uint32_t b = __float_as_uint(f);
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float float_from_order_key(uint32_t k) {
+  return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
+__global__ void observer_mean_kernel(const int64_t* __restrict__ off, const int32_t* __restrict__ obs_scan,
+                                     const double* __restrict__ poses, int64_t n_voxels, float4* __restrict__ mean,
+                                     uint32_t* __restrict__ box) {
+  __shared__ uint32_t sbox[6];
+  if (threadIdx.x < 6) sbox[threadIdx.x] = threadIdx.x < 3 ? 0xffffffffu : 0u;
+  __syncthreads();
+  const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v < n_voxels) {
+    const int64_t a0 = off[v], a1 = off[v + 1];
+    float x = 0.f, y = 0.f, z = 0.f;
+    for (int64_t o = a0; o < a1; ++o) {
+      const double* t = poses + 12 * (int64_t)obs_scan[o] + 9;
+      x += f64_to_f32(t[0]);
+      y += f64_to_f32(t[1]);
+      z += f64_to_f32(t[2]);
+    }
+    const float inv = 1.0f / (float)(a1 - a0);
+    const float m[3] = {x * inv, y * inv, z * inv};
+    mean[v] = make_float4(m[0], m[1], m[2], 0.f);
+    for (int c = 0; c < 3; ++c) {
+      atomicMin(&sbox[c], float_order_key(m[c]));
+      atomicMax(&sbox[3 + c], float_order_key(m[c]));
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) atomicMin(&box[threadIdx.x], sbox[threadIdx.x]);
+  else if (threadIdx.x < 6) atomicMax(&box[threadIdx.x], sbox[threadIdx.x]);
+}
+
+// 10 bits of each coordinate spread to every third bit
+__device__ __forceinline__ uint32_t spread3(uint32_t v) {
+  v &= 0x3ffu;
+  v = (v | (v << 16)) & 0x030000ffu;
+  v = (v | (v << 8)) & 0x0300f00fu;
+  v = (v | (v << 4)) & 0x030c30c3u;
+  v = (v | (v << 2)) & 0x09249249u;
+  return v;
+}
+
+__global__ void morton_keys_kernel(const float4* __restrict__ mean, int64_t n_voxels, const uint32_t* __restrict__ box,
+                                   uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
   const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= n_voxels) return;
-  const int64_t len = off[v + 1] - off[v];
-  const uint32_t win = (uint32_t)(v / kWindow);
-  keys[v] = (win << len_bits) | (uint32_t)(max_len - len);
+  const float4 m = mean[v];
+  const float mc[3] = {m.x, m.y, m.z};
+  uint32_t code = 0;
+  for (int c = 0; c < 3; ++c) {
+    const float lo = float_from_order_key(box[c]), hi = float_from_order_key(box[3 + c]);
+    uint32_t q = 0;
+    if (hi > lo) {
+      const float t = (mc[c] - lo) / (hi - lo) * 1023.0f;
+      q = t <= 0.f ? 0u : t >= 1023.f ? 1023u : (uint32_t)t;
+    }
+    code |= spread3(q) << c;
+  }
+  keys[v] = code;
   vals[v] = (uint32_t)v;
+}
+
+// after the spatial sort (vals[r] = voxel of spatial rank r): window of the
+// rank, then length descending
+__global__ void window_keys_kernel(const int64_t* __restrict__ off, const uint32_t* __restrict__ vals,
+                                   int64_t n_voxels, int max_len, int len_bits, uint32_t* __restrict__ keys) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n_voxels) return;
+  const uint32_t v = vals[r];
+  const int64_t len = off[v + 1] - off[v];
+  keys[r] = ((uint32_t)(r / kWindow) << len_bits) | (uint32_t)(max_len - len);
 }
 
 __global__ void slice_len_kernel(const int64_t* off, const uint32_t* vperm, int64_t n_voxels, int64_t n_slices,
@@ -455,12 +528,25 @@ __global__ void vscale_kernel(LoadInput in, int64_t v0, int64_t v1, double* vsca
   vscale[v] = 2.0 / n;
 }
 
-__global__ void scan_keys_kernel(LoadInput in, uint32_t* keys, uint32_t* vals, int64_t* counts) {
+// observations listed by sorted voxel position (pbase[p] = observations of
+// the voxels before position p), keyed by scan for the stable sort that makes
+// the scan-major copy: inside a scan, observations follow the voxel order, so
+// the scan pass gathers the plane records of nearby voxels
+__global__ void scan_keys_kernel(LoadInput in, const int32_t* obs_vox, const int32_t* vrank, const int64_t* pbase,
+                                 uint32_t* keys, uint32_t* vals, int64_t* counts) {
   const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (o >= in.n_obs) return;
-  keys[o] = (uint32_t)in.obs_scan[o];
-  vals[o] = (uint32_t)o;
+  const int32_t v = obs_vox[o];
+  const int64_t q = pbase[vrank[v]] + (o - in.voxel_off[v]);
+  keys[q] = (uint32_t)in.obs_scan[o];
+  vals[q] = (uint32_t)o;
   atomicAdd((unsigned long long*)(counts + in.obs_scan[o]), 1ull);
+}
+
+__global__ void vlen_i64_kernel(const int32_t* vlen, int64_t n_voxels, int64_t* out) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < n_voxels) out[p] = vlen[p];
+  if (p == 0) out[n_voxels] = 0;
 }
 
 __global__ void fill_scan_major_kernel(LoadInput in, const uint32_t* order, const int32_t* obs_vox,
@@ -500,11 +586,6 @@ cudaError_t launch_vscale(const LoadInput& in, int64_t v0, int64_t v1, double* v
 }
 
 // inv[perm[q]] = q
-__global__ void inverse_perm_kernel(int64_t n, const uint32_t* perm, uint32_t* inv) {
-  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q < n) inv[perm[q]] = (uint32_t)q;
-}
-
 cudaError_t build_layout(const LoadInput& in, int max_len, bool fill_f64, bool defer_scale, Allocator keep,
                          Allocator temp, LayoutBuffers* out, cudaStream_t stream, int64_t* launches) {
   const int64_t nv = in.n_voxels, no = in.n_obs;
@@ -522,7 +603,6 @@ cudaError_t build_layout(const LoadInput& in, int max_len, bool fill_f64, bool d
   int32_t* obs_vox = (int32_t*)maps.fn(maps.self, sizeof(int32_t) * no);
   double* vscale = (double*)maps.fn(maps.self, sizeof(double) * nv);
   uint32_t* order = fill_f64 ? nullptr : (uint32_t*)keep.fn(keep.self, sizeof(uint32_t) * no);
-  uint32_t* pos = !fill_f64 && defer_scale ? (uint32_t*)temp.fn(temp.self, sizeof(uint32_t) * no) : nullptr;
   // persistent
   out->slice_off = (int64_t*)keep.fn(keep.self, sizeof(int64_t) * (n_slices + 1));
   out->vlen = (int32_t*)keep.fn(keep.self, sizeof(int32_t) * nv);
@@ -532,23 +612,33 @@ cudaError_t build_layout(const LoadInput& in, int max_len, bool fill_f64, bool d
   // + 4 entries: the staged mixed scan pass copies whole 16-byte groups
   out->se_vox = (int32_t*)keep.fn(keep.self, sizeof(int32_t) * (no + 4));
   if (!keys || !vals || !tk || !tv || !scratch || !vrank || !obs_vox || !vscale || !out->slice_off || !out->vlen ||
-      !out->vperm || !out->scan_off || (fill_f64 && !out->se) || (!fill_f64 && !order) || !out->se_vox ||
-      (!fill_f64 && defer_scale && !pos))
+      !out->vperm || !out->scan_off || (fill_f64 && !out->se) || (!fill_f64 && !order) || !out->se_vox)
     return cudaErrorMemoryAllocation;
-  out->scan_pos = pos;
   out->vrank = vrank;
   out->obs_vox = obs_vox;
   out->vscale = vscale;
   out->scan_order = order;
 
-  // ---- voxel order: length-descending inside windows ----
+  // ---- voxel order: spatial windows, length-descending inside each ----
   const int len_bits = bit_width((uint64_t)max_len);
   const int win_bits = bit_width((uint64_t)((nv - 1) / kWindow));
   if (len_bits + win_bits > 32) return cudaErrorInvalidValue;
-  voxel_keys_kernel<<<(unsigned)((nv + 255) / 256), 256, 0, stream>>>(in.voxel_off, nv, max_len, len_bits, keys,
-                                                                      vals);
-  ++*launches;
-  RETURN_IF(cudaGetLastError());
+  {
+    float4* mean = (float4*)temp.fn(temp.self, sizeof(float4) * nv);
+    uint32_t* box = (uint32_t*)temp.fn(temp.self, sizeof(uint32_t) * 8);
+    if (!mean || !box) return cudaErrorMemoryAllocation;
+    RETURN_IF(cudaMemsetAsync(box, 0xff, sizeof(uint32_t) * 3, stream));  // minima
+    RETURN_IF(cudaMemsetAsync(box + 3, 0, sizeof(uint32_t) * 3, stream));  // maxima
+    const unsigned nb = (unsigned)((nv + 255) / 256);
+    observer_mean_kernel<<<nb, 256, 0, stream>>>(in.voxel_off, in.obs_scan, in.poses, nv, mean, box);
+    morton_keys_kernel<<<nb, 256, 0, stream>>>(mean, nv, box, keys, vals);
+    *launches += 2;
+    RETURN_IF(cudaGetLastError());
+    RETURN_IF(radix_sort_pairs(keys, vals, tk, tv, nv, 30, scratch, stream, launches));
+    window_keys_kernel<<<nb, 256, 0, stream>>>(in.voxel_off, vals, nv, max_len, len_bits, keys);
+    ++*launches;
+    RETURN_IF(cudaGetLastError());
+  }
   RETURN_IF(radix_sort_pairs(keys, vals, tk, tv, nv, len_bits + win_bits, scratch, stream, launches));
   slice_len_kernel<<<(unsigned)((nv + 255) / 256), 256, 0, stream>>>(in.voxel_off, vals, nv, n_slices,
                                                                      out->slice_off, out->vlen, out->vperm, vrank);
@@ -577,9 +667,19 @@ cudaError_t build_layout(const LoadInput& in, int max_len, bool fill_f64, bool d
   ++*launches;
   RETURN_IF(cudaGetLastError());
   RETURN_IF(cudaMemsetAsync(out->scan_off, 0, sizeof(int64_t) * (in.n_scans + 1), stream));
-  scan_keys_kernel<<<(unsigned)((no + 255) / 256), 256, 0, stream>>>(in, keys, vals, out->scan_off);
-  ++*launches;
-  RETURN_IF(cudaGetLastError());
+  {
+    int64_t* pbase = (int64_t*)temp.fn(temp.self, sizeof(int64_t) * (nv + 1));
+    int64_t* pscratch = (int64_t*)temp.fn(temp.self, sizeof(int64_t) * scan_scratch_count(nv + 1));
+    if (!pbase || !pscratch) return cudaErrorMemoryAllocation;
+    vlen_i64_kernel<<<(unsigned)((nv + 255) / 256), 256, 0, stream>>>(out->vlen, nv, pbase);
+    ++*launches;
+    RETURN_IF(cudaGetLastError());
+    RETURN_IF(exclusive_scan_i64(pbase, nv + 1, pscratch, stream, launches));
+    scan_keys_kernel<<<(unsigned)((no + 255) / 256), 256, 0, stream>>>(in, obs_vox, vrank, pbase, keys, vals,
+                                                                       out->scan_off);
+    ++*launches;
+    RETURN_IF(cudaGetLastError());
+  }
   RETURN_IF(radix_sort_pairs(keys, vals, tk, tv, no, bit_width((uint64_t)(in.n_scans - 1)), scratch, stream,
                              launches));
   RETURN_IF(exclusive_scan_i64(out->scan_off, in.n_scans + 1, scratch, stream, launches));
@@ -588,11 +688,6 @@ cudaError_t build_layout(const LoadInput& in, int max_len, bool fill_f64, bool d
   ++*launches;
   RETURN_IF(cudaGetLastError());
   if (order) RETURN_IF(cudaMemcpyAsync(order, vals, sizeof(uint32_t) * no, cudaMemcpyDeviceToDevice, stream));
-  if (pos) {
-    inverse_perm_kernel<<<(unsigned)((no + 255) / 256), 256, 0, stream>>>(no, vals, pos);
-    ++*launches;
-    RETURN_IF(cudaGetLastError());
-  }
   return cudaSuccess;
 }
 

@@ -195,6 +195,77 @@ __device__ inline void offset_b(const double* c, const double* ref, float4 an, d
   b[2] = ref[6] * c[6] + ref[7] * c[7] + ref[8] * c[8] + (ref[11] - f32_to_f64(an.z));
 }
 
+// the slot of observation o of a voxel with anchor an: offset to the anchor
+// and count, eigenvalues of the scatter and scan id, eigenvector quaternion
+__device__ void mixed_slot(const LoadInput& in, int64_t o, const double* sref, float4 an, float4& s0, float4& s1,
+                           float4& s2) {
+  double c[10], b[3];
+  centred_cluster(in.agg + 10 * o, in.agg_form, c);
+  const double* ref = sref + 12 * (int64_t)in.obs_scan[o];
+  offset_b(c, ref, an, b);
+  // eigen-decomposition of the scatter in the scan frame: an FP32 Jacobi
+  // gives V0; W = V0^T S V0 is diagonal up to FP32 rounding, and its FP32
+  // Jacobi gives the variances to FP32 relative precision (the normal one
+  // included); V = V0 W_vec.  A direction error d of the stored vectors
+  // changes a variance only by (spread) d^2.
+  float sf[6];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) sf[q] = f64_to_f32(c[q]);
+  float lam0[3], v0[9];
+  eig3_sym_f(sf, lam0, v0);  // eigenvectors as rows of v0 (vector c at v0[3c..3c+2])
+  // W = V0^T S V0.  The entries of the two smallest directions (W_00,
+  // W_01, W_11) are small next to S's largest entries and lose digits to
+  // cancellation in FP32, so they are formed in FP64: W_00 is the normal
+  // variance of a planar cluster, and for a rod-like cluster (two small,
+  // nearly equal variances) the voxel normal can be any direction of that
+  // pair.  The entries with the largest direction only need absolute
+  // precision (off-diagonals of order 1e-7 of the spread turn V0 by ~1e-7
+  // rad, a second-order change of the variances).
+  float wf[6];
+  {
+    const double S[3][3] = {{c[0], c[1], c[2]}, {c[1], c[3], c[4]}, {c[2], c[4], c[5]}};
+    double vd[6];  // v_0, v_1 in FP64 (exact)
+#pragma unroll
+    for (int q = 0; q < 6; ++q) vd[q] = f32_to_f64(v0[q]);
+    double Sv[2][3];  // S v_k, k = 0, 1 (FP64)
+    for (int k = 0; k < 2; ++k)
+      for (int r = 0; r < 3; ++r) Sv[k][r] = S[r][0] * vd[3 * k] + S[r][1] * vd[3 * k + 1] + S[r][2] * vd[3 * k + 2];
+    wf[0] = f64_to_f32(vd[0] * Sv[0][0] + vd[1] * Sv[0][1] + vd[2] * Sv[0][2]);
+    wf[1] = f64_to_f32(vd[0] * Sv[1][0] + vd[1] * Sv[1][1] + vd[2] * Sv[1][2]);
+    wf[3] = f64_to_f32(vd[3] * Sv[1][0] + vd[4] * Sv[1][1] + vd[5] * Sv[1][2]);
+    const float M[3][3] = {{sf[0], sf[1], sf[2]}, {sf[1], sf[3], sf[4]}, {sf[2], sf[4], sf[5]}};
+    float T[3];  // S v_2 (FP32)
+    for (int r = 0; r < 3; ++r) T[r] = fmaf(M[r][0], v0[6], fmaf(M[r][1], v0[7], M[r][2] * v0[8]));
+    // packed (00, 01, 02, 11, 12, 22)
+    wf[2] = fmaf(v0[0], T[0], fmaf(v0[1], T[1], v0[2] * T[2]));
+    wf[4] = fmaf(v0[3], T[0], fmaf(v0[4], T[1], v0[5] * T[2]));
+    wf[5] = fmaf(v0[6], T[0], fmaf(v0[7], T[1], v0[8] * T[2]));
+  }
+  float sg[3], wv[9];
+  eig3_sym_f(wf, sg, wv);
+  // world-axis eigenvectors as columns: V = R_ref V0^T-rows ... = R_ref [v0 rows]^T W
+  const float* Rf = sref32_of(sref, in.n_scans, in.obs_scan[o]);
+  float V[9];
+  for (int cc = 0; cc < 3; ++cc) {
+    float u[3];  // scan-frame vector cc = sum_k v0_k W[k][cc]
+    for (int r = 0; r < 3; ++r)
+      u[r] = fmaf(v0[r], wv[3 * cc], fmaf(v0[3 + r], wv[3 * cc + 1], v0[6 + r] * wv[3 * cc + 2]));
+    for (int r = 0; r < 3; ++r) V[3 * r + cc] = fmaf(Rf[3 * r], u[0], fmaf(Rf[3 * r + 1], u[1], Rf[3 * r + 2] * u[2]));
+  }
+  const float det = V[0] * (V[4] * V[8] - V[5] * V[7]) - V[1] * (V[3] * V[8] - V[5] * V[6]) +
+                    V[2] * (V[3] * V[7] - V[4] * V[6]);
+  if (det < 0.f) {
+    V[0] = -V[0];
+    V[3] = -V[3];
+    V[6] = -V[6];
+  }
+  float qf[4];
+  mat_to_quat<float>(V, qf);
+  s0 = make_float4(f64_to_f32(b[0]), f64_to_f32(b[1]), f64_to_f32(b[2]), f64_to_f32(c[9]));
+  s1 = make_float4(sg[0], sg[1], sg[2], __int_as_float(in.obs_scan[o]));
+  s2 = make_float4(qf[0], qf[1], qf[2], qf[3]);
+}
+
 // slots of the slices that start at sorted positions [p0, p1) (p0 a multiple
 // of kSlice): thread (p, blockIdx.y) fills rows kFillRows * blockIdx.y ..
 // + kFillRows - 1 of voxel p, then the same rows gridDim.y * kFillRows on
@@ -215,73 +286,51 @@ __global__ void fill_sell_mixed_kernel(LoadInput in, const int32_t* vperm, const
     for (int64_t k = k0; k < k0 + kFillRows && k < rows; ++k) {
       const int64_t e = base + k * kSlice;
       float4 s0 = make_float4(0.f, 0.f, 0.f, 0.f), s1 = s0, s2 = s0;
+      if (k < len) mixed_slot(in, o0 + k, sref, an, s0, s1, s2);
+      ve32[kVe32 * e] = s0;
+      ve32[kVe32 * e + 1] = s1;
+      ve32[kVe32 * e + 2] = s2;
+    }
+  }
+}
+
+// The same slots staged in input order (slot of observation o at
+// staging[3 o]): a pipelined load computes each arriving chunk's slots there,
+// then places them all in their slices once every chunk is done.
+__global__ void fill_staging_kernel(LoadInput in, int64_t o0, int64_t o1, const int32_t* obs_vox,
+                                    const int32_t* vrank, const double* sref, const float4* vanchor,
+                                    float4* staging) {
+  const int64_t o = o0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= o1) return;
+  float4 s0, s1, s2;
+  mixed_slot(in, o, sref, vanchor[vrank[obs_vox[o]]], s0, s1, s2);
+  staging[3 * o] = s0;
+  staging[3 * o + 1] = s1;
+  staging[3 * o + 2] = s2;
+}
+
+// staged slots to their slices, padding rows zero; thread (p, blockIdx.y)
+// as in fill_sell_mixed_kernel (coalesced writes)
+__global__ void place_slots_kernel(const int64_t* voxel_off, const int32_t* vperm, const int32_t* vlen,
+                                   const int64_t* slice_off, int64_t n_voxels, int64_t n_slices,
+                                   const float4* staging, float4* ve32) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t s = p >> 5;
+  if (s >= n_slices) return;
+  const int64_t base = slice_off[s] + (p & 31);
+  const int64_t rows = (slice_off[s + 1] - slice_off[s]) / kSlice;
+  const bool real = p < n_voxels;
+  const int32_t len = real ? vlen[p] : 0;
+  const int64_t o0 = real ? voxel_off[vperm[p]] : 0;
+  for (int64_t k0 = (int64_t)blockIdx.y * kFillRows; k0 < rows; k0 += (int64_t)gridDim.y * kFillRows) {
+    for (int64_t k = k0; k < k0 + kFillRows && k < rows; ++k) {
+      const int64_t e = base + k * kSlice;
+      float4 s0 = make_float4(0.f, 0.f, 0.f, 0.f), s1 = s0, s2 = s0;
       if (k < len) {
-        const int64_t o = o0 + k;
-        double c[10], b[3];
-        centred_cluster(in.agg + 10 * o, in.agg_form, c);
-        const double* ref = sref + 12 * (int64_t)in.obs_scan[o];
-        offset_b(c, ref, an, b);
-        // eigen-decomposition of the scatter in the scan frame: an FP32 Jacobi
-        // gives V0; W = V0^T S V0 is diagonal up to FP32 rounding, and its FP32
-        // Jacobi gives the variances to FP32 relative precision (the normal one
-        // included); V = V0 W_vec.  A direction error d of the stored vectors
-        // changes a variance only by (spread) d^2.
-        float sf[6];
-#pragma unroll
-        for (int q = 0; q < 6; ++q) sf[q] = f64_to_f32(c[q]);
-        float lam0[3], v0[9];
-        eig3_sym_f(sf, lam0, v0);  // eigenvectors as rows of v0 (vector c at v0[3c..3c+2])
-        // W = V0^T S V0.  The entries of the two smallest directions (W_00,
-        // W_01, W_11) are small next to S's largest entries and lose digits to
-        // cancellation in FP32, so they are formed in FP64: W_00 is the normal
-        // variance of a planar cluster, and for a rod-like cluster (two small,
-        // nearly equal variances) the voxel normal can be any direction of that
-        // pair.  The entries with the largest direction only need absolute
-        // precision (off-diagonals of order 1e-7 of the spread turn V0 by ~1e-7
-        // rad, a second-order change of the variances).
-        float wf[6];
-        {
-          const double S[3][3] = {{c[0], c[1], c[2]}, {c[1], c[3], c[4]}, {c[2], c[4], c[5]}};
-          double vd[6];  // v_0, v_1 in FP64 (exact)
-#pragma unroll
-          for (int q = 0; q < 6; ++q) vd[q] = f32_to_f64(v0[q]);
-          double Sv[2][3];  // S v_k, k = 0, 1 (FP64)
-          for (int k = 0; k < 2; ++k)
-            for (int r = 0; r < 3; ++r) Sv[k][r] = S[r][0] * vd[3 * k] + S[r][1] * vd[3 * k + 1] + S[r][2] * vd[3 * k + 2];
-          wf[0] = f64_to_f32(vd[0] * Sv[0][0] + vd[1] * Sv[0][1] + vd[2] * Sv[0][2]);
-          wf[1] = f64_to_f32(vd[0] * Sv[1][0] + vd[1] * Sv[1][1] + vd[2] * Sv[1][2]);
-          wf[3] = f64_to_f32(vd[3] * Sv[1][0] + vd[4] * Sv[1][1] + vd[5] * Sv[1][2]);
-          const float M[3][3] = {{sf[0], sf[1], sf[2]}, {sf[1], sf[3], sf[4]}, {sf[2], sf[4], sf[5]}};
-          float T[3];  // S v_2 (FP32)
-          for (int r = 0; r < 3; ++r) T[r] = fmaf(M[r][0], v0[6], fmaf(M[r][1], v0[7], M[r][2] * v0[8]));
-          // packed (00, 01, 02, 11, 12, 22)
-          wf[2] = fmaf(v0[0], T[0], fmaf(v0[1], T[1], v0[2] * T[2]));
-          wf[4] = fmaf(v0[3], T[0], fmaf(v0[4], T[1], v0[5] * T[2]));
-          wf[5] = fmaf(v0[6], T[0], fmaf(v0[7], T[1], v0[8] * T[2]));
-        }
-        float sg[3], wv[9];
-        eig3_sym_f(wf, sg, wv);
-        // world-axis eigenvectors as columns: V = R_ref V0^T-rows ... = R_ref [v0 rows]^T W
-        const float* Rf = sref32_of(sref, in.n_scans, in.obs_scan[o]);
-        float V[9];
-        for (int cc = 0; cc < 3; ++cc) {
-          float u[3];  // scan-frame vector cc = sum_k v0_k W[k][cc]
-          for (int r = 0; r < 3; ++r)
-            u[r] = fmaf(v0[r], wv[3 * cc], fmaf(v0[3 + r], wv[3 * cc + 1], v0[6 + r] * wv[3 * cc + 2]));
-          for (int r = 0; r < 3; ++r) V[3 * r + cc] = fmaf(Rf[3 * r], u[0], fmaf(Rf[3 * r + 1], u[1], Rf[3 * r + 2] * u[2]));
-        }
-        const float det = V[0] * (V[4] * V[8] - V[5] * V[7]) - V[1] * (V[3] * V[8] - V[5] * V[6]) +
-                          V[2] * (V[3] * V[7] - V[4] * V[6]);
-        if (det < 0.f) {
-          V[0] = -V[0];
-          V[3] = -V[3];
-          V[6] = -V[6];
-        }
-        float qf[4];
-        mat_to_quat<float>(V, qf);
-        s0 = make_float4(f64_to_f32(b[0]), f64_to_f32(b[1]), f64_to_f32(b[2]), f64_to_f32(c[9]));
-        s1 = make_float4(sg[0], sg[1], sg[2], __int_as_float(in.obs_scan[o]));
-        s2 = make_float4(qf[0], qf[1], qf[2], qf[3]);
+        const float4* src = staging + 3 * (o0 + k);
+        s0 = src[0];
+        s1 = src[1];
+        s2 = src[2];
       }
       ve32[kVe32 * e] = s0;
       ve32[kVe32 * e + 1] = s1;
@@ -329,15 +378,6 @@ __global__ void fill_scan_mixed_kernel(int64_t n_obs, const uint32_t* order, con
   if (q < n_obs) fill_scan_one(q, order[q], n_obs, obs_vox, vscale, vrank, voxel_off, slice_off, ve32, se32);
 }
 
-// thread per observation o in [o0, o1) (pos[o] = its scan-major position)
-__global__ void fill_scan_range_kernel(int64_t o0, int64_t o1, int64_t n_obs, const uint32_t* pos,
-                                       const int32_t* obs_vox, const double* vscale, const int32_t* vrank,
-                                       const int64_t* voxel_off, const int64_t* slice_off, const float4* ve32,
-                                       float* se32) {
-  const int64_t o = o0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (o < o1) fill_scan_one(pos[o], o, n_obs, obs_vox, vscale, vrank, voxel_off, slice_off, ve32, se32);
-}
-
 }  // namespace
 
 cudaError_t build_mixed_begin(const LoadInput& in, const double* poses2, MixedBuffers& mb, cudaStream_t stream,
@@ -348,7 +388,8 @@ cudaError_t build_mixed_begin(const LoadInput& in, const double* poses2, MixedBu
 }
 
 cudaError_t build_mixed_voxels(const LoadInput& in, const LayoutBuffers& lb, const double* poses2, MixedBuffers& mb,
-                               int64_t v0, int64_t v1, cudaStream_t stream, int64_t* launches) {
+                               int64_t v0, int64_t v1, int64_t o0, int64_t o1, float4* staging, cudaStream_t stream,
+                               int64_t* launches) {
   if (v1 <= v0) return cudaSuccess;
   LoadInput cur = in;
   cur.poses = poses2;  // buffer 0
@@ -356,37 +397,33 @@ cudaError_t build_mixed_voxels(const LoadInput& in, const LayoutBuffers& lb, con
                                                                         mb.vanchor, mb.planes32_2);
   ++*launches;
   cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  // the slices of sorted positions [v0, v1): windows keep their voxels, so for
-  // window-aligned ranges these are exactly the voxels whose frames were just set
-  const int64_t p0 = v0, p1 = min(in.n_voxels, ((v1 + kSlice - 1) / kSlice) * kSlice);
-  const unsigned row_blocks =
-      (unsigned)std::min<int64_t>(std::max<int64_t>((lb.max_len + kFillRows - 1) / kFillRows, 1), 65535);
-  fill_sell_mixed_kernel<<<dim3((unsigned)((p1 - p0 + 127) / 128), row_blocks), 128, 0, stream>>>(
-      cur, lb.vperm, lb.vlen, lb.slice_off, in.n_voxels, p0, p1, mb.sref, mb.vanchor, mb.ve32);
+  if (e != cudaSuccess || o1 <= o0) return e;
+  fill_staging_kernel<<<(unsigned)((o1 - o0 + 127) / 128), 128, 0, stream>>>(cur, o0, o1, lb.obs_vox, lb.vrank,
+                                                                            mb.sref, mb.vanchor, staging);
   ++*launches;
   return cudaGetLastError();
 }
 
-cudaError_t build_mixed_scan_range(const LoadInput& in, const LayoutBuffers& lb, MixedBuffers& mb, int64_t o0,
-                                   int64_t o1, cudaStream_t stream, int64_t* launches) {
-  if (o1 <= o0) return cudaSuccess;
-  fill_scan_range_kernel<<<(unsigned)((o1 - o0 + 255) / 256), 256, 0, stream>>>(
-      o0, o1, in.n_obs, lb.scan_pos, lb.obs_vox, lb.vscale, lb.vrank, in.voxel_off, lb.slice_off, mb.ve32, mb.se32);
+cudaError_t build_mixed_place(const LoadInput& in, const LayoutBuffers& lb, MixedBuffers& mb, const float4* staging,
+                              cudaStream_t stream, int64_t* launches) {
+  const int64_t n = lb.n_slices * kSlice;
+  if (n == 0) return cudaSuccess;
+  const unsigned row_blocks =
+      (unsigned)std::min<int64_t>(std::max<int64_t>((lb.max_len + kFillRows - 1) / kFillRows, 1), 65535);
+  place_slots_kernel<<<dim3((unsigned)((n + 127) / 128), row_blocks), 128, 0, stream>>>(
+      in.voxel_off, lb.vperm, lb.vlen, lb.slice_off, in.n_voxels, lb.n_slices, staging, mb.ve32);
   ++*launches;
   return cudaGetLastError();
 }
 
 cudaError_t build_mixed_end(const LoadInput& in, const LayoutBuffers& lb, const double* poses2, MixedBuffers& mb,
-                            cudaStream_t stream, int64_t* launches, bool scan_filled) {
+                            cudaStream_t stream, int64_t* launches) {
   const int64_t no = in.n_obs;
-  if (!scan_filled) {
-    fill_scan_mixed_kernel<<<(unsigned)((no + 255) / 256), 256, 0, stream>>>(
-        no, lb.scan_order, lb.obs_vox, lb.vscale, lb.vrank, in.voxel_off, lb.slice_off, mb.ve32, mb.se32);
-    ++*launches;
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-  }
+  fill_scan_mixed_kernel<<<(unsigned)((no + 255) / 256), 256, 0, stream>>>(
+      no, lb.scan_order, lb.obs_vox, lb.vscale, lb.vrank, in.voxel_off, lb.slice_off, mb.ve32, mb.se32);
+  ++*launches;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
   ++*launches;
   return launch_scan_table(in.n_scans, poses2, mb.sref, mb.stab2, 0, stream);
 }
@@ -394,9 +431,25 @@ cudaError_t build_mixed_end(const LoadInput& in, const LayoutBuffers& lb, const 
 cudaError_t build_mixed(const LoadInput& in, const LayoutBuffers& lb, const double* poses2, MixedBuffers& mb,
                         cudaStream_t stream, int64_t* launches) {
   cudaError_t e = build_mixed_begin(in, poses2, mb, stream, launches);
-  if (e == cudaSuccess) e = build_mixed_voxels(in, lb, poses2, mb, 0, in.n_voxels, stream, launches);
-  if (e == cudaSuccess) e = build_mixed_end(in, lb, poses2, mb, stream, launches);
-  return e;
+  if (e != cudaSuccess) return e;
+  LoadInput cur = in;
+  cur.poses = poses2;  // buffer 0
+  const int64_t nv = in.n_voxels;
+  if (nv > 0) {
+    voxel_frames_kernel<<<(unsigned)((nv + 3) / 4), 128, 0, stream>>>(cur, 0, nv, mb.sref, lb.vrank, mb.vstate,
+                                                                      mb.vanchor, mb.planes32_2);
+    ++*launches;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // every slot, padding included, by sorted position (coalesced writes)
+    const int64_t p1 = ((nv + kSlice - 1) / kSlice) * kSlice;
+    const unsigned row_blocks =
+        (unsigned)std::min<int64_t>(std::max<int64_t>((lb.max_len + kFillRows - 1) / kFillRows, 1), 65535);
+    fill_sell_mixed_kernel<<<dim3((unsigned)((p1 + 127) / 128), row_blocks), 128, 0, stream>>>(
+        cur, lb.vperm, lb.vlen, lb.slice_off, nv, 0, p1, mb.sref, mb.vanchor, mb.ve32);
+    ++*launches;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return build_mixed_end(in, lb, poses2, mb, stream, launches);
 }
 
 }  // namespace mmba

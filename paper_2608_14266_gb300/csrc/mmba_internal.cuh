@@ -2,9 +2,13 @@
 //
 // Device layout of a loaded problem (all in the handle's device memory):
 //
-//  * Voxel-sorted slices (SELL-32): voxels are sorted by observation count
-//    (descending) inside windows of kWindow consecutive input voxels, and
-//    grouped 32 to a slice; one thread owns one voxel.  Row k of slice s holds
+//  * Voxel-sorted slices (SELL-32): voxels are put in a spatial order (the
+//    Morton code of the mean position of the scans observing each voxel, at
+//    the input poses), cut into windows of kWindow voxels consecutive in that
+//    order, sorted by observation count (descending) inside each window, and
+//    grouped 32 to a slice; one thread owns one voxel.  Voxels seen by the
+//    same scans share slices, so a slice row reads few distinct per-scan
+//    entries, and a scan's observations gather plane records that lie close.  Row k of slice s holds
 //    the k-th observation of each of its 32 voxels at
 //    slice_off[s] + 32 * k + lane, so a warp reading row k touches 32
 //    consecutive elements.  Rows past a voxel's own length are padding
@@ -26,7 +30,7 @@
 namespace mmba {
 
 constexpr int kSlice = 32;          // voxels per slice (one warp)
-constexpr int64_t kWindow = 8192;   // length sort window (multiple of kSlice)
+constexpr int64_t kWindow = 8192;   // length sort window, in spatial order (multiple of kSlice)
 constexpr int kPlaneStride = 4;     // plane record used by the scan pass: u (3), d
 constexpr int kGH = 27;             // per-scan g (6) then upper triangle of H (21)
 

@@ -112,7 +112,6 @@ struct LayoutBuffers {
   int32_t* obs_vox;      // observation -> input voxel
   double* vscale;        // input voxel -> 2 / N_i
   uint32_t* scan_order;  // scan-major position -> observation
-  uint32_t* scan_pos;    // observation -> scan-major position (pipelined mixed loads; temporary)
 };
 // `keep` allocates the buffers of *out, `temp` the build's temporaries (the
 // caller frees those after the stream has drained).
@@ -146,20 +145,21 @@ struct MixedBuffers {
 };
 cudaError_t build_mixed(const LoadInput& in, const LayoutBuffers& lb, const double* poses2, MixedBuffers& mb,
                         cudaStream_t stream, int64_t* launches);
-// The same in three stages, for a load that overlaps the clusters' copy:
-// begin (reference poses), voxels [v0, v1) (frames, anchors and slots; the
-// range must be window-aligned, its clusters on the device), end (scan-major
-// copy and scan table, once every voxel is done).
+// The same in stages, for a load that overlaps the clusters' copy: begin
+// (reference poses); input voxels [v0, v1) with their observations [o0, o1)
+// (frames and anchors, and the slots staged in input order, 3 float4 per
+// observation; their clusters on the device); place (every staged slot to its
+// slice, padding zero); end (scan-major copy and scan table, once every slot
+// is placed).
 cudaError_t build_mixed_begin(const LoadInput& in, const double* poses2, MixedBuffers& mb, cudaStream_t stream,
                               int64_t* launches);
 cudaError_t build_mixed_voxels(const LoadInput& in, const LayoutBuffers& lb, const double* poses2, MixedBuffers& mb,
-                               int64_t v0, int64_t v1, cudaStream_t stream, int64_t* launches);
+                               int64_t v0, int64_t v1, int64_t o0, int64_t o1, float4* staging, cudaStream_t stream,
+                               int64_t* launches);
+cudaError_t build_mixed_place(const LoadInput& in, const LayoutBuffers& lb, MixedBuffers& mb, const float4* staging,
+                              cudaStream_t stream, int64_t* launches);
 cudaError_t build_mixed_end(const LoadInput& in, const LayoutBuffers& lb, const double* poses2, MixedBuffers& mb,
-                            cudaStream_t stream, int64_t* launches, bool scan_filled = false);
-// scan-major FP32 copy of observations [o0, o1) (input order), once their
-// voxels' slots and scales are set (needs lb.scan_pos)
-cudaError_t build_mixed_scan_range(const LoadInput& in, const LayoutBuffers& lb, MixedBuffers& mb, int64_t o0,
-                                   int64_t o1, cudaStream_t stream, int64_t* launches);
+                            cudaStream_t stream, int64_t* launches);
 
 // bounded-wait check: out[0] = 1 if an mbarrier wait that cannot complete gave up
 cudaError_t launch_wait_probe(int limit, int32_t* out, cudaStream_t stream);

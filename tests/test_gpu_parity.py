@@ -311,8 +311,11 @@ def test_checkpoint_resume_equals_uninterrupted(mm):
         b.iterate(4)
         saved, st = b.poses(), b.stats()
         b.close()
+        # the resumed handle loads the same problem (clusters and initial
+        # poses, which fix the layout and so the order of every sum) and
+        # takes the saved state
         c = mm.BundleAdjuster()
-        c.load_observations(s.n_scans, s.voxel_off, s.obs_scan, cen, saved)
+        c.load_observations(s.n_scans, s.voxel_off, s.obs_scan, cen, s.pose_init)
         c.set_state(saved, st["mu"], st["nu"])
         c.iterate(6)
         r, t = pose_errors(a.poses(), c.poses())
