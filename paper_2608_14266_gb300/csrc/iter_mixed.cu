@@ -219,76 +219,72 @@ __global__ void __launch_bounds__(kVoxelThreads, kMinBlocks)
 // the state's wait_timeout flag and the warp leaves after its copies land.
 // ---------------------------------------------------------------------------
 
-// one observation's terms added to the 27 sums (scan reference axes)
+// one observation's terms added to the 27 sums (scan reference axes); E is
+// dR - I of the scan, row-major
 __device__ __forceinline__ void scan_obs_terms(float (&acc)[32], float4 bN, float4 S4, float2 S2, float4 pl, float4 an,
-                                               const float* ph, float ca, float cb, float dt0, float dt1, float dt2,
-                                               float tr0, float tr1, float tr2, bool gn) {
+                                               const float (&E)[9], float dt0, float dt1, float dt2, float tr0,
+                                               float tr1, float tr2, bool gn) {
   const float b0 = bN.x, b1 = bN.y, b2 = bN.z, N = bN.w;
   const float S00 = S4.x, S01 = S4.y, S02 = S4.z, S11 = S4.w, S12 = S2.x, S22 = S2.y;
   const float l0 = b0 + (an.x - tr0), l1 = b1 + (an.y - tr1), l2 = b2 + (an.z - tr2);
-  float el0, el1, el2;
-  apply_E(ph, ca, cb, l0, l1, l2, el0, el1, el2);
+  const float el0 = fmaf(E[0], l0, fmaf(E[1], l1, E[2] * l2));
+  const float el1 = fmaf(E[3], l0, fmaf(E[4], l1, E[5] * l2));
+  const float el2 = fmaf(E[6], l0, fmaf(E[7], l1, E[8] * l2));
   const float x0 = b0 + el0 + dt0, x1 = b1 + el1 + dt1, x2 = b2 + el2 + dt2;
   const float r = fmaf(pl.x, x0, fmaf(pl.y, x1, fmaf(pl.z, x2, -pl.w)));
-  // w = dR^T u = u + E^T u = u - a (phi x u) + b (phi x (phi x u))
-  float eu0, eu1, eu2;
-  apply_E(ph, -ca, cb, pl.x, pl.y, pl.z, eu0, eu1, eu2);
-  const float wx = pl.x + eu0, wy = pl.y + eu1, wz = pl.z + eu2;
+  // w = dR^T u = u + E^T u
+  const float wx = fmaf(E[0], pl.x, fmaf(E[3], pl.y, fmaf(E[6], pl.z, pl.x)));
+  const float wy = fmaf(E[1], pl.x, fmaf(E[4], pl.y, fmaf(E[7], pl.z, pl.y)));
+  const float wz = fmaf(E[2], pl.x, fmaf(E[5], pl.y, fmaf(E[8], pl.z, pl.z)));
   const float Nr = N * r;
   const float swx = fmaf(S00, wx, fmaf(S01, wy, S02 * wz));
   const float swy = fmaf(S01, wx, fmaf(S11, wy, S12 * wz));
   const float swz = fmaf(S02, wx, fmaf(S12, wy, S22 * wz));
   const float mpx = fmaf(Nr, l0, swx), mpy = fmaf(Nr, l1, swy), mpz = fmaf(Nr, l2, swz);
-  acc[0] += mpy * wz - mpz * wy;
-  acc[1] += mpz * wx - mpx * wz;
-  acc[2] += mpx * wy - mpy * wx;
-  acc[3] += Nr * wx;
-  acc[4] += Nr * wy;
-  acc[5] += Nr * wz;
+  acc[0] = fmaf(mpy, wz, fmaf(-mpz, wy, acc[0]));
+  acc[1] = fmaf(mpz, wx, fmaf(-mpx, wz, acc[1]));
+  acc[2] = fmaf(mpx, wy, fmaf(-mpy, wx, acc[2]));
+  acc[3] = fmaf(Nr, wx, acc[3]);
+  acc[4] = fmaf(Nr, wy, acc[4]);
+  acc[5] = fmaf(Nr, wz, acc[5]);
   const float Nlx = N * l0, Nly = N * l1, Nlz = N * l2;
   const float p00 = fmaf(Nlx, l0, S00), p01 = fmaf(Nlx, l1, S01), p02 = fmaf(Nlx, l2, S02);
   const float p11 = fmaf(Nly, l1, S11), p12 = fmaf(Nly, l2, S12), p22 = fmaf(Nlz, l2, S22);
   const float b00 = wy * p02 - wz * p01, b10 = wz * p00 - wx * p02, b20 = wx * p01 - wy * p00;
   const float b01 = wy * p12 - wz * p11, b11 = wz * p01 - wx * p12, b21 = wx * p11 - wy * p01;
   const float b02 = wy * p22 - wz * p12, b12 = wz * p02 - wx * p22;
-  float h00 = -wz * b01 + wy * b02;
-  float h01 = wz * b00 - wx * b02;
-  float h02 = -wy * b00 + wx * b01;
-  float h11 = wz * b10 - wx * b12;
-  float h12 = -wy * b10 + wx * b11;
-  float h22 = -wy * b20 + wx * b21;
+  acc[6] = fmaf(wy, b02, fmaf(-wz, b01, acc[6]));
+  acc[7] = fmaf(-wx, b02, fmaf(wz, b00, acc[7]));
+  acc[8] = fmaf(wx, b01, fmaf(-wy, b00, acc[8]));
+  acc[12] = fmaf(-wx, b12, fmaf(wz, b10, acc[12]));
+  acc[13] = fmaf(wx, b11, fmaf(-wy, b10, acc[13]));
+  acc[17] = fmaf(wx, b21, fmaf(-wy, b20, acc[17]));
   if (!gn) {
     const float wm = fmaf(wx, mpx, fmaf(wy, mpy, wz * mpz));
-    h00 += wx * mpx - wm;
-    h11 += wy * mpy - wm;
-    h22 += wz * mpz - wm;
-    h01 += 0.5f * (wx * mpy + mpx * wy);
-    h02 += 0.5f * (wx * mpz + mpx * wz);
-    h12 += 0.5f * (wy * mpz + mpy * wz);
+    acc[6] = fmaf(wx, mpx, acc[6] - wm);
+    acc[12] = fmaf(wy, mpy, acc[12] - wm);
+    acc[17] = fmaf(wz, mpz, acc[17] - wm);
+    acc[7] = fmaf(0.5f, fmaf(wx, mpy, mpx * wy), acc[7]);
+    acc[8] = fmaf(0.5f, fmaf(wx, mpz, mpx * wz), acc[8]);
+    acc[13] = fmaf(0.5f, fmaf(wy, mpz, mpy * wz), acc[13]);
   }
-  acc[6] += h00;
-  acc[7] += h01;
-  acc[8] += h02;
   const float cx = Nly * wz - Nlz * wy, cy = Nlz * wx - Nlx * wz, cz = Nlx * wy - Nly * wx;
-  acc[9] += cx * wx;
-  acc[10] += cx * wy;
-  acc[11] += cx * wz;
-  acc[12] += h11;
-  acc[13] += h12;
-  acc[14] += cy * wx;
-  acc[15] += cy * wy;
-  acc[16] += cy * wz;
-  acc[17] += h22;
-  acc[18] += cz * wx;
-  acc[19] += cz * wy;
-  acc[20] += cz * wz;
-  const float Nwx = N * wx, Nwy = N * wy;
-  acc[21] += Nwx * wx;
-  acc[22] += Nwx * wy;
-  acc[23] += Nwx * wz;
-  acc[24] += Nwy * wy;
-  acc[25] += Nwy * wz;
-  acc[26] += N * wz * wz;
+  acc[9] = fmaf(cx, wx, acc[9]);
+  acc[10] = fmaf(cx, wy, acc[10]);
+  acc[11] = fmaf(cx, wz, acc[11]);
+  acc[14] = fmaf(cy, wx, acc[14]);
+  acc[15] = fmaf(cy, wy, acc[15]);
+  acc[16] = fmaf(cy, wz, acc[16]);
+  acc[18] = fmaf(cz, wx, acc[18]);
+  acc[19] = fmaf(cz, wy, acc[19]);
+  acc[20] = fmaf(cz, wz, acc[20]);
+  const float Nwx = N * wx, Nwy = N * wy, Nwz = N * wz;
+  acc[21] = fmaf(Nwx, wx, acc[21]);
+  acc[22] = fmaf(Nwx, wy, acc[22]);
+  acc[23] = fmaf(Nwx, wz, acc[23]);
+  acc[24] = fmaf(Nwy, wy, acc[24]);
+  acc[25] = fmaf(Nwy, wz, acc[25]);
+  acc[26] = fmaf(Nwz, wz, acc[26]);
 }
 
 // Shared-memory image of one chunk of a scan's observations.  Every array
@@ -328,6 +324,20 @@ __device__ __forceinline__ void scan_pass_mixed_body(const DevLayout& L, const D
   // dR = I + E, E x = ca (v x x) + cb v x (v x x) for the unit quaternion (w, v) of dR
   const float ph[3] = {tb[1], tb[2], tb[3]};
   const float ca = 2.f * tb[0], cb = 2.f;
+  // E = dR - I = ca [phi]x + cb [phi]x^2 (row-major), once per scan
+  float E[9];
+  {
+    const float vx = ph[0], vy = ph[1], vz = ph[2];
+    E[0] = -cb * (vy * vy + vz * vz);
+    E[4] = -cb * (vx * vx + vz * vz);
+    E[8] = -cb * (vx * vx + vy * vy);
+    E[1] = fmaf(cb * vx, vy, -ca * vz);
+    E[3] = fmaf(cb * vx, vy, ca * vz);
+    E[2] = fmaf(cb * vx, vz, ca * vy);
+    E[6] = fmaf(cb * vx, vz, -ca * vy);
+    E[5] = fmaf(cb * vy, vz, -ca * vx);
+    E[7] = fmaf(cb * vy, vz, ca * vx);
+  }
   const float dt0 = tb[4], dt1 = tb[5], dt2 = tb[6], tr0 = tb[7], tr1 = tb[8], tr2 = tb[9];
   const float4* __restrict__ prec = X.planes32_2 + (int64_t)buf * L.n_voxels * 2;
   const bool gn = st->hess_mode != 0;
@@ -378,8 +388,7 @@ __device__ __forceinline__ void scan_pass_mixed_body(const DevLayout& L, const D
     for (int q = 0; q < kScanChunk / 32; ++q) {
       const int i = lane + 32 * q;
       if (i < n)
-        scan_obs_terms(acc, S.bN[i], S.S4[i], S.S2[i + off2], pl[q], an[q], ph, ca, cb, dt0, dt1, dt2, tr0, tr1,
-                       tr2, gn);
+        scan_obs_terms(acc, S.bN[i], S.S4[i], S.S2[i + off2], pl[q], an[q], E, dt0, dt1, dt2, tr0, tr1, tr2, gn);
     }
     __syncwarp();
     if (lane == 0 && k + 2 < nch) {
