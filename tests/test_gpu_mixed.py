@@ -233,3 +233,39 @@ def test_integer_conversions_match_hardware(mm):
     for seed in (1, 2, 3):
         assert _lib.lib().ba_check_conversions(0, 4_000_000, seed, out) == 0
         assert list(out) == [0, 0]
+
+
+def _permuted(s, cen, perm):
+    """The same problem with its voxels listed in the order perm."""
+    off = s.voxel_off
+    cnt = np.diff(off)[perm]
+    noff = np.concatenate([[0], np.cumsum(cnt)]).astype(np.int64)
+    idx = np.repeat(off[:-1][perm], cnt) + (np.arange(int(off[-1])) - np.repeat(noff[:-1], cnt))
+    return noff, s.obs_scan[idx], cen[idx]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_voxel_input_order_changes_only_rounding(mm, precision):
+    """The device layout puts the voxels in its own spatial order, so a
+    problem given with its voxels in another order is the same problem: the
+    planes come back identical and in the caller's order, and the cost and the
+    poses after a few iterations agree within the precision's rounding (the
+    order of the sums over voxels and scans follows the layout)."""
+    prec = mm.BA_MIXED if precision == "mixed" else mm.BA_FP64
+    s, cen = _scene_20k()
+    rng = np.random.default_rng(11)
+    perm = rng.permutation(s.n_voxels)
+    noff, nscan, ncen = _permuted(s, cen, perm)
+    cost_tol, rot_tol, tr_tol = (1e-6, 1e-6, 1e-5) if precision == "mixed" else (1e-11, 1e-10, 1e-9)
+    with mm.BundleAdjuster(precision=prec) as a, mm.BundleAdjuster(precision=prec) as b:
+        a.load_observations(s.n_scans, s.voxel_off, s.obs_scan, cen, s.pose_init)
+        b.load_observations(s.n_scans, noff, nscan, ncen, s.pose_init)
+        assert b.cost() == pytest.approx(a.cost(), rel=cost_tol)
+        # a voxel's plane is computed from its own observations in their own
+        # order whatever the layout: identical records, in the caller's order
+        np.testing.assert_array_equal(b.planes(), a.planes()[perm])
+        a.iterate(3)
+        b.iterate(3)
+        r, t = pose_errors(a.poses(), b.poses())
+        assert r < rot_tol and t < tr_tol
+        assert b.cost() == pytest.approx(a.cost(), rel=cost_tol)
