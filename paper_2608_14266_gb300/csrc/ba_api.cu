@@ -540,8 +540,15 @@ ba_status load_impl(ba_handle* h, int32_t n_scans, int64_t n_voxels, int64_t n_o
                                  &h->launches),
            "mixed-precision copies");
       }
+      // the slots to their slices on this stream and the scan-major copy from
+      // the staged slots on the (now idle) copy stream, concurrently
+      CK(h, cudaEventRecord(h->copy_events[kMaxCopyChunks], h->stream), "set-up order");
+      CK(h, cudaStreamWaitEvent(h->copy_stream, h->copy_events[kMaxCopyChunks], 0), "set-up order");
+      CK(h, build_mixed_scan_major(in, lb, mb, staging, h->copy_stream, &h->launches), "mixed-precision copies");
+      CK(h, cudaEventRecord(h->copy_events[0], h->copy_stream), "set-up order");
       CK(h, build_mixed_place(in, lb, mb, staging, h->stream, &h->launches), "mixed-precision copies");
-      CK(h, build_mixed_end(in, lb, h->poses2, mb, h->stream, &h->launches), "mixed-precision copies");
+      CK(h, cudaStreamWaitEvent(h->stream, h->copy_events[0], 0), "set-up order");
+      CK(h, build_mixed_end(in, lb, h->poses2, mb, h->stream, &h->launches, true), "mixed-precision copies");
       CK(h, cudaMemcpyAsync(&res, d_val, sizeof res, cudaMemcpyDeviceToHost, h->stream), "validation result");
       CK(h, cudaStreamSynchronize(h->stream), "validation sync");
       if ((vs = check_validation(h, res, n_scans)) != BA_OK) return vs;

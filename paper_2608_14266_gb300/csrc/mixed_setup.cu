@@ -344,13 +344,21 @@ __global__ void place_slots_kernel(const int64_t* voxel_off, const int32_t* vper
 // quaternion (R_ref S R_ref^T = V diag(sigma) V^T), each scaled by 2 / N_i.
 // obs_pos[o] is the slot of observation o (sorted voxel position p, row k:
 // slice_off[p / 32] + 32 k + p % 32).
+// With staging non-null the slot is read there (input order: 3 float4 per
+// observation) instead of in its slice.
 __device__ __forceinline__ void fill_scan_one(int64_t q, int64_t o, int64_t n_obs, const int32_t* obs_vox,
                                               const double* vscale, const int32_t* vrank, const int64_t* voxel_off,
-                                              const int64_t* slice_off, const float4* ve32, float* se32) {
+                                              const int64_t* slice_off, const float4* ve32, const float4* staging,
+                                              float* se32) {
   const int32_t v = obs_vox[o];
-  const int64_t p = vrank[v];
-  const int64_t e = slice_off[p >> 5] + (o - voxel_off[v]) * kSlice + (p & 31);
-  const float4 s0 = ve32[kVe32 * e], s1 = ve32[kVe32 * e + 1], s2 = ve32[kVe32 * e + 2];
+  const float4* src;
+  if (staging) {
+    src = staging + 3 * o;
+  } else {
+    const int64_t p = vrank[v];
+    src = ve32 + kVe32 * (slice_off[p >> 5] + (o - voxel_off[v]) * kSlice + (p & 31));
+  }
+  const float4 s0 = src[0], s1 = src[1], s2 = src[2];
   float V[9];
   quat_to_mat_f(s2.x, s2.y, s2.z, s2.w, V);
   const float sg[3] = {s1.x, s1.y, s1.z};
@@ -373,9 +381,11 @@ __device__ __forceinline__ void fill_scan_one(int64_t q, int64_t o, int64_t n_ob
 // thread per scan-major position q (order[q] = its observation)
 __global__ void fill_scan_mixed_kernel(int64_t n_obs, const uint32_t* order, const int32_t* obs_vox,
                                        const double* vscale, const int32_t* vrank, const int64_t* voxel_off,
-                                       const int64_t* slice_off, const float4* ve32, float* se32) {
+                                       const int64_t* slice_off, const float4* ve32, const float4* staging,
+                                       float* se32) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q < n_obs) fill_scan_one(q, order[q], n_obs, obs_vox, vscale, vrank, voxel_off, slice_off, ve32, se32);
+  if (q < n_obs)
+    fill_scan_one(q, order[q], n_obs, obs_vox, vscale, vrank, voxel_off, slice_off, ve32, staging, se32);
 }
 
 }  // namespace
@@ -416,14 +426,21 @@ cudaError_t build_mixed_place(const LoadInput& in, const LayoutBuffers& lb, Mixe
   return cudaGetLastError();
 }
 
-cudaError_t build_mixed_end(const LoadInput& in, const LayoutBuffers& lb, const double* poses2, MixedBuffers& mb,
-                            cudaStream_t stream, int64_t* launches) {
+cudaError_t build_mixed_scan_major(const LoadInput& in, const LayoutBuffers& lb, MixedBuffers& mb,
+                                   const float4* staging, cudaStream_t stream, int64_t* launches) {
   const int64_t no = in.n_obs;
   fill_scan_mixed_kernel<<<(unsigned)((no + 255) / 256), 256, 0, stream>>>(
-      no, lb.scan_order, lb.obs_vox, lb.vscale, lb.vrank, in.voxel_off, lb.slice_off, mb.ve32, mb.se32);
+      no, lb.scan_order, lb.obs_vox, lb.vscale, lb.vrank, in.voxel_off, lb.slice_off, mb.ve32, staging, mb.se32);
   ++*launches;
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+cudaError_t build_mixed_end(const LoadInput& in, const LayoutBuffers& lb, const double* poses2, MixedBuffers& mb,
+                            cudaStream_t stream, int64_t* launches, bool scan_filled) {
+  if (!scan_filled) {
+    cudaError_t e = build_mixed_scan_major(in, lb, mb, nullptr, stream, launches);
+    if (e != cudaSuccess) return e;
+  }
   ++*launches;
   return launch_scan_table(in.n_scans, poses2, mb.sref, mb.stab2, 0, stream);
 }

@@ -149,8 +149,9 @@ cudaError_t build_mixed(const LoadInput& in, const LayoutBuffers& lb, const doub
 // (reference poses); input voxels [v0, v1) with their observations [o0, o1)
 // (frames and anchors, and the slots staged in input order, 3 float4 per
 // observation; their clusters on the device); place (every staged slot to its
-// slice, padding zero); end (scan-major copy and scan table, once every slot
-// is placed).
+// slice, padding zero) and the scan-major copy from the staged slots (the two
+// may run concurrently); end (the scan table; with scan_filled false also the
+// scan-major copy from the placed slots).
 cudaError_t build_mixed_begin(const LoadInput& in, const double* poses2, MixedBuffers& mb, cudaStream_t stream,
                               int64_t* launches);
 cudaError_t build_mixed_voxels(const LoadInput& in, const LayoutBuffers& lb, const double* poses2, MixedBuffers& mb,
@@ -158,8 +159,10 @@ cudaError_t build_mixed_voxels(const LoadInput& in, const LayoutBuffers& lb, con
                                int64_t* launches);
 cudaError_t build_mixed_place(const LoadInput& in, const LayoutBuffers& lb, MixedBuffers& mb, const float4* staging,
                               cudaStream_t stream, int64_t* launches);
+cudaError_t build_mixed_scan_major(const LoadInput& in, const LayoutBuffers& lb, MixedBuffers& mb,
+                                   const float4* staging, cudaStream_t stream, int64_t* launches);
 cudaError_t build_mixed_end(const LoadInput& in, const LayoutBuffers& lb, const double* poses2, MixedBuffers& mb,
-                            cudaStream_t stream, int64_t* launches);
+                            cudaStream_t stream, int64_t* launches, bool scan_filled = false);
 
 // bounded-wait check: out[0] = 1 if an mbarrier wait that cannot complete gave up
 cudaError_t launch_wait_probe(int limit, int32_t* out, cudaStream_t stream);
