@@ -327,66 +327,74 @@ constexpr int kChunk = 32;  // sorted points per thread
 // chunk and base[chunk] counts the heads before it.  The piece where a run starts
 // goes to head_piece[run], the piece of a run continuing from the previous
 // chunk to carry[chunk]; counts are stored as integers (no FP64 work in the
-// divergent stores).  Indices come in as two 16-byte loads and the points of
-// 8 of them are loaded together, so a thread's sectors are used while cached.
+// divergent stores).  The points reach each thread through shared memory, 8
+// at a time, gathered by its whole warp.
 template <typename K>
-__global__ void __launch_bounds__(256, 2) l1_pieces_kernel(int64_t n, const K* keys, const uint32_t* vals,
+__global__ void __launch_bounds__(128, 4) l1_pieces_kernel(int64_t n, const K* keys, const uint32_t* vals,
                                                         const int32_t* pscan, const double* pts, const int64_t* base,
                                                         const uint32_t* hmask, const uint64_t* raw,
                                                         double* head_piece, double* carry, uint64_t* ckey,
                                                         int32_t* cscan) {
   static_assert(kChunk == 32, "one head-mask word per chunk");
-  const int64_t ch = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  // per warp, one round of 8 points of each lane's chunk, staged by the whole
+  // warp: lanes 8q..8q+7 load 8 consecutive sorted points of one chunk, so a
+  // load instruction touches 4 runs of consecutive points instead of 32
+  // scattered ones (a chunk's points mostly lie together in the input)
+  __shared__ double sx[4][32][9], sy[4][32][9], sz[4][32][9];
+  __shared__ uint32_t sv[4][32][9];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t wch = ((int64_t)blockIdx.x * blockDim.x) + 32 * w;  // the warp's first chunk
+  const int64_t ch = wch + lane;
   const int64_t e0 = ch * kChunk;
-  if (e0 >= n) return;
+  const bool active = e0 < n;
   const int64_t e1 = e0 + kChunk < n ? e0 + kChunk : n;
-  const uint32_t hm = hmask[ch];
+  const uint32_t hm = active ? hmask[ch] : 0u;
   const bool open = !(hm & 1u);  // the first run continues from the previous chunk
-  const int64_t g0 = base[ch] - 1;  // the run holding e0 - 1 (a head at e0 starts run g0 + 1)
+  const int64_t g0 = active ? base[ch] - 1 : 0;  // the run holding e0 - 1 (a head at e0 starts run g0 + 1)
   int64_t g = g0;
   Piece P;
   int cnt = 0;
   bool first = true;
 #pragma unroll 1
-  for (int64_t eb = e0; eb < e1; eb += 8) {
-    uint32_t v[8];
-    if (eb + 8 <= e1) {
-      const uint4 a = *reinterpret_cast<const uint4*>(vals + eb);
-      const uint4 b = *reinterpret_cast<const uint4*>(vals + eb + 4);
-      v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w, v[4] = b.x, v[5] = b.y, v[6] = b.z, v[7] = b.w;
-    } else {
+  for (int r = 0; r < kChunk / 8; ++r) {
 #pragma unroll
-      for (int k = 0; k < 8; ++k) v[k] = eb + k < e1 ? vals[eb + k] : 0u;
-    }
-    double px[8], py[8], pz[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      if (eb + k < e1) {
-        const double* p = pts + 3 * (int64_t)v[k];
-        px[k] = p[0];
-        py[k] = p[1];
-        pz[k] = p[2];
+    for (int i = 0; i < 8; ++i) {
+      const int t = 4 * i + (lane >> 3), k = lane & 7;
+      const int64_t e = (wch + t) * kChunk + 8 * r + k;
+      if (e < n) {
+        const uint32_t v = vals[e];
+        const double* p = pts + 3 * (int64_t)v;
+        sx[w][t][k] = p[0];
+        sy[w][t][k] = p[1];
+        sz[w][t][k] = p[2];
+        sv[w][t][k] = v;
       }
     }
+    __syncwarp();
+    if (active) {
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const int64_t e = eb + k;
-      if (e >= e1) break;
-      if ((hm >> (int)(e - e0)) & 1u) {
-        if (!first) {  // close the previous run's piece
-          P.n = __longlong_as_double((long long)cnt);
-          piece_store((g == g0 && open) ? carry + kPieceDoubles * ch : head_piece + kPieceDoubles * g, P);
+      for (int k = 0; k < 8; ++k) {
+        const int64_t e = e0 + 8 * r + k;
+        if (e >= e1) break;
+        const uint32_t v = sv[w][lane][k];
+        if ((hm >> (int)(e - e0)) & 1u) {
+          if (!first) {  // close the previous run's piece
+            P.n = __longlong_as_double((long long)cnt);
+            piece_store((g == g0 && open) ? carry + kPieceDoubles * ch : head_piece + kPieceDoubles * g, P);
+          }
+          ++g;
+          cnt = 0;
+          ckey[g] = raw ? raw[v] : (uint64_t)keys[e];
+          cscan[g] = pscan[v];
         }
-        ++g;
-        cnt = 0;
-        ckey[g] = raw ? raw[v[k]] : (uint64_t)keys[e];
-        cscan[g] = pscan[v[k]];
+        first = false;
+        piece_add(P, cnt, sx[w][lane][k], sy[w][lane][k], sz[w][lane][k]);
+        ++cnt;
       }
-      first = false;
-      piece_add(P, cnt, px[k], py[k], pz[k]);
-      ++cnt;
     }
+    __syncwarp();
   }
+  if (!active) return;
   P.n = __longlong_as_double((long long)cnt);
   piece_store((g == g0 && open) ? carry + kPieceDoubles * ch : head_piece + kPieceDoubles * g, P);
 }
@@ -891,7 +899,7 @@ ba_status level1(int64_t n, const uint64_t* raw, uint32_t* vals, const int32_t* 
   double* cr = tmp.get<double>(kPieceDoubles * n_chunks);
   if (!L.c || !L.key || !L.scan || !hp || !cr) return vfail(BA_ERR_OOM, "voxelize: out of device memory");
   tm.begin(BA_VOX_CLUSTER_PASS);
-  l1_pieces_kernel<K><<<blocks_for(n_chunks), 256, 0, st>>>(n, keys, vals, pscan, pts, base, hmask,
+  l1_pieces_kernel<K><<<blocks_for(n_chunks, 128), 128, 0, st>>>(n, keys, vals, pscan, pts, base, hmask,
                                                               raw_keys ? raw : nullptr, hp, cr, L.key, L.scan);
   tm.end();
   tm.begin(BA_VOX_CLUSTER_FINISH);
