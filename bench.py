@@ -755,9 +755,10 @@ def run_served(args):
         "workload": "served", "value": len(jobs_m) / t_m, "unit": "jobs/s", "n_gpus": 1, "jobs": args.jobs,
         "arrival_rate_per_s": args.rate, "seconds": t_m, "latency": latency_summary(jobs_m),
         "gpu_launches": launches_m,
-        "fp64_per_job": {"value": done64 / t64, "unit": "jobs/s", "jobs": done64, "seconds": t64,
-                         "latency": {"p50_s": float(np.percentile(lat64, 50)), "p99_s": float(np.percentile(lat64, 99)),
-                                     "mean_s": float(lat64.mean()), "max_s": float(lat64.max())}},
+        "fp64_per_job": None if done64 == 0 else {
+            "value": done64 / t64, "unit": "jobs/s", "jobs": done64, "seconds": t64,
+            "latency": {"p50_s": float(np.percentile(lat64, 50)), "p99_s": float(np.percentile(lat64, 99)),
+                        "mean_s": float(lat64.mean()), "max_s": float(lat64.max())}},
         "pose_agreement_mixed_vs_fp64": {"max_rot_rad": worst[0], "max_trans_m": worst[1], "jobs": done64},
         "accuracy_vs_ground_truth": acc.report(),
         "config": {"scans": "log-uniform 50-5000", "voxels": "50 x scans", "obs_per_voxel": "5-30", "pts_per_obs": 32,
