@@ -379,8 +379,6 @@ __device__ inline void to_centred(const double* a, int form, double out[10]) {
   out[9] = n;
 }
 
-// key = (window << len_bits) | (max_len - len): ascending order = windows in
-// input order, longest voxels first inside a window.
 // ---- spatial order of the voxels ----
 // Mean translation of the scans observing each voxel (FP32, summed in the
 // voxel's observation order), and the bounding box of those means as
@@ -585,7 +583,6 @@ cudaError_t launch_vscale(const LoadInput& in, int64_t v0, int64_t v1, double* v
   return cudaGetLastError();
 }
 
-// inv[perm[q]] = q
 cudaError_t build_layout(const LoadInput& in, int max_len, bool fill_f64, bool defer_scale, Allocator keep,
                          Allocator temp, LayoutBuffers* out, cudaStream_t stream, int64_t* launches) {
   const int64_t nv = in.n_voxels, no = in.n_obs;

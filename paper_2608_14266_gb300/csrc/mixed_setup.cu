@@ -342,10 +342,9 @@ __global__ void place_slots_kernel(const int64_t* voxel_off, const int32_t* vper
 // Scan-major FP32 copy from the slots: the offset and count as they are, the
 // scatter in reference axes rebuilt from its eigenvalues and eigenvector
 // quaternion (R_ref S R_ref^T = V diag(sigma) V^T), each scaled by 2 / N_i.
-// obs_pos[o] is the slot of observation o (sorted voxel position p, row k:
-// slice_off[p / 32] + 32 k + p % 32).
-// With staging non-null the slot is read there (input order: 3 float4 per
-// observation) instead of in its slice.
+// Observation o's slot is at sorted voxel position p, row k:
+// slice_off[p / 32] + 32 k + p % 32, or, with staging non-null, at staging[3 o]
+// (input order).
 __device__ __forceinline__ void fill_scan_one(int64_t q, int64_t o, int64_t n_obs, const int32_t* obs_vox,
                                               const double* vscale, const int32_t* vrank, const int64_t* voxel_off,
                                               const int64_t* slice_off, const float4* ve32, const float4* staging,
