@@ -82,3 +82,22 @@ def test_package_does_not_import_the_oracle():
     code = ("import sys; sys.path.insert(0, %r); import paper_2608_14266_gb300, scenegen; "
             "assert 'oracle' not in sys.modules, 'product imported the oracle'") % ROOT
     subprocess.check_call([sys.executable, "-c", code])
+
+
+def test_memory_estimate_is_host_only_and_grows_with_the_problem(built):
+    """ba_estimate_bytes (the server's admission figure) needs no device: it
+    grows with each size, linearly in the clusters, and its load peak includes
+    the mixed path's input-order slot staging (48 bytes per cluster)."""
+    import paper_2608_14266_gb300 as mm
+    for prec in (mm.BA_FP64, mm.BA_MIXED):
+        k0, p0 = mm.ba_estimate_bytes(prec, 100, 10_000, 200_000)
+        assert k0 > 0 and p0 > 0
+        for args in ((200, 10_000, 200_000), (100, 20_000, 200_000), (100, 10_000, 400_000)):
+            k, p = mm.ba_estimate_bytes(prec, *args)
+            assert k > k0 and p >= p0
+        k2, _ = mm.ba_estimate_bytes(prec, 100, 10_000, 400_000)
+        k4, _ = mm.ba_estimate_bytes(prec, 100, 10_000, 800_000)
+        assert abs((k4 - k2) - 2 * (k2 - k0)) <= 1024  # linear in the clusters (200k, 400k, 800k)
+    _, p64 = mm.ba_estimate_bytes(mm.BA_FP64, 100, 10_000, 200_000)
+    _, pmx = mm.ba_estimate_bytes(mm.BA_MIXED, 100, 10_000, 200_000)
+    assert pmx - p64 == 48 * 200_000
