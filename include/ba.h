@@ -137,31 +137,48 @@ ba_status ba_load_points(ba_handle* h, int32_t n_scans, int64_t n_voxels, int64_
                          const int32_t* obs_scan, const int64_t* point_offsets, const double* points,
                          const double* poses, int32_t mem_kind);
 
-/* Run exactly n_iters LM iterations (each: per-scan damped solve, retraction,
- * trial cost evaluation, accept/reject, damping update, and on acceptance the
- * new planes, gradient and Hessian).  out may be NULL.  Synchronises the
+/* Run exactly n_iters LM iterations (Algorithm 2 and Sec. IV-C-1: per-scan
+ * damped solve A = H + mu diag(H), A delta = -g by LDL^T ("Solver"),
+ * retraction, trial cost evaluation of Eq. 1 ("CalRes"), accept/reject by
+ * the gain ratio and damping update ("PredResReduction", "Adjust"; the
+ * Levenberg-Marquardt rule of Fig. 1, read as Nielsen's update), and on
+ * acceptance the new planes, gradient and Hessian of Eq. 3 ("CalJH")).
+ * The predicted reduction is L = sum_j -(g_j^T D_j + D_j^T H_j D_j / 2); a
+ * step is accepted iff every factorisation succeeded, L > 0 and
+ * c(T') < c(T); then mu *= max(1/3, 1 - (2 rho - 1)^3), nu = 2 with
+ * rho = (c(T) - c(T')) / L, else mu *= nu, nu *= 2.  out may be NULL.  Synchronises the
  * stream only when out is given.  BA_ERR_NUMERIC if the cost became
  * non-finite.  Iterations after the solve has stopped (see ba_solve) are
  * still run. */
 ba_status ba_iterate(ba_handle* h, int32_t n_iters, ba_stats* out);
 
-/* Iterate until an accepted step meets the tolerance, max_iters iterations
- * have run since load, or max_consec_reject steps in a row were rejected.
- * Synchronises the stream. */
+/* Iterate (Algorithm 2's outer loop, Sec. IV-C-1) until an accepted step
+ * meets the tolerance, max_iters iterations have run since load, or
+ * max_consec_reject steps in a row were rejected.  The paper gives no stop
+ * rule beyond its iteration; this one is the relative cost change of an
+ * accepted step.  Synchronises the stream. */
 ba_status ba_solve(ba_handle* h, ba_stats* out);
 
-/* Current poses, n_scans x 12 doubles, to host (synchronises) or device
- * memory (stream-ordered). */
+/* Current poses, n_scans x 12 doubles (R row-major, then t; scan -> world),
+ * to host (synchronises) or device memory (stream-ordered).  They are the
+ * accepted iterates of the update T <- T + Delta T of Sec. IV-C-1, read as
+ * the retraction R' = Exp(dphi) R, t' = t + dt (Exp by Rodrigues' formula,
+ * its second-order series below 1e-6 rad). */
 ba_status ba_poses(ba_handle* h, double* out, int32_t mem_kind);
 
-/* Cost at the current poses (synchronises). */
+/* Cost c(T) = sum_i lambda_min(cov_i) of Eq. 1 at the current poses: the
+ * smallest eigenvalue of each voxel's world-point covariance (1/N_i
+ * normalisation), summed over voxels (synchronises). */
 ba_status ba_cost(ba_handle* h, double* out);
 
-/* LM state and counters (synchronises). */
+/* LM state and counters of Algorithm 2's loop: damping mu (Sec. IV-C-1),
+ * its growth factor nu, the last gain ratio and predicted reduction
+ * (synchronises). */
 ba_status ba_get_stats(ba_handle* h, ba_stats* out);
 
 /* Replace the current poses (host or device, n_scans x 12) and the damping
- * state, then re-evaluate planes, cost, gradient and Hessian there.  With
+ * state (mu, nu of Sec. IV-C-1), then re-evaluate planes, cost, gradient and
+ * Hessian there (Eq. 1, Eq. 3).  With
  * this a solve can be resumed from saved poses.  mu <= 0 keeps the current
  * mu; nu <= 0 keeps the current nu.  The device layout (the voxel order,
  * and with it the order of every floating-point sum) is a function of the
@@ -171,12 +188,20 @@ ba_status ba_get_stats(ba_handle* h, ba_stats* out);
 ba_status ba_set_state(ba_handle* h, const double* poses, double mu, double nu, int32_t mem_kind);
 
 /* Plane records (n_voxels x 9 doubles, input voxel order) at the current
- * poses. */
+ * poses: the eigen-decomposition of each voxel's covariance that Eq. 1 and
+ * Eq. 3 use (lambda0..2, the normal u of lambda0, the centroid c). */
 ba_status ba_planes(ba_handle* h, double* out, int32_t mem_kind);
 
-/* Surrogate gradient (n_scans x 6) and Hessian (n_scans x 36, row-major,
- * world frame, rotation block first) at the current poses; either may be
- * NULL. */
+/* Gradient (n_scans x 6) and Hessian (n_scans x 36, row-major, world frame,
+ * rotation block first) of the MM surrogate of Eq. 3 at the current poses
+ * (Algorithm 2, "CalJH"), with respect to the increment (dphi, dt) of the
+ * retraction above.  The paper defers these derivatives to earlier work;
+ * they are derived here from Eq. 3 in its fixed-plane form
+ * c_M = (1/N_i) sum_k (u^T (R p_k + t) - d)^2: per observation, with
+ * w = R^T u, e = u^T t - d, s = w^T v_f + N e, m = R (P_f w + e v_f),
+ * g = (2/N_i) [m x u; s u] and the exact second-order H (the term
+ * (u m^T + m u^T)/2 - (u^T m) I of its rotation block is dropped under
+ * BA_HESS_GAUSS_NEWTON).  Either output may be NULL. */
 ba_status ba_gradient(ba_handle* h, double* g, double* H, int32_t mem_kind);
 
 /* Number of kernel launches the handle has issued since creation. */
@@ -468,7 +493,8 @@ ba_status ba_check_conversions(int32_t device, int64_t n, uint64_t seed, uint64_
  * cudaMalloc/cudaFree may synchronise the device and stall the loop, or an
  * application whose own allocator already holds the GPU's memory.
  *
- * Computes c(T) = sum_i lambda_min(cov_i) (Eq. 1) for the caller's
+ * Computes the cost -- the sum over voxels of the smallest eigenvalue of the
+ * covariance of the voxel's points placed by the poses -- for the caller's
  * voxel-major CSR clusters in centred form (n_obs x 10 doubles), poses
  * (n_scans x 12) and offsets/scan indices, all device memory of the calling
  * thread's current device, and writes the cost to *cost_out (device) and,
@@ -488,9 +514,15 @@ ba_status ba_check_conversions(int32_t device, int64_t n, uint64_t seed, uint64_
  * on the GPU (different streams, or several host threads) race on it and
  * must be serialised by the caller.
  *
+ * The looked-up address is cached per device for the life of the process;
+ * it does not survive cudaDeviceReset or any other teardown of the device's
+ * primary context, so do not call this entry point across such a reset.
+ *
  * Errors: BA_ERR_INVALID_ARG (sizes below 1, n_obs < n_voxels, NULL
  * pointers), BA_ERR_CAPACITY (n_voxels > BA_NOALLOC_MAX_VOXELS),
- * BA_ERR_CUDA (no current device or a launch failed).  Offsets or scan
+ * BA_ERR_CUDA (no current device or one of its launches failed; an error
+ * left pending by earlier, unrelated work on the calling thread is cleared
+ * on entry and not reported by this call).  Offsets or scan
  * indices found out of range on the device leave the cost NaN (and the
  * voxel's lambda0 NaN); inputs are otherwise not validated. */
 #define BA_NOALLOC_MAX_VOXELS 8388608

@@ -215,20 +215,45 @@ def ba_eval_cost_noalloc(n_scans, voxel_offsets, obs_scan, agg_centred, poses, c
 
     For callers that cannot allocate device memory at that point (a fixed
     memory budget in an on-vehicle mapping loop, or a host whose allocator
-    already holds the GPU memory).  Every argument is a CUDA tensor owned by
-    the caller; the result lands in cost_out (one float64) and optionally
-    lambda0_out (n_voxels float64).  Asynchronous on `stream`; calls that
-    overlap on the GPU share the library's scratch and must be serialised.
+    already holds the GPU memory).  Every argument is a contiguous CUDA tensor
+    owned by the caller: voxel_offsets (n_voxels + 1 int64), obs_scan (n_obs
+    int32), agg_centred (n_obs x 10 float64), poses (n_scans x 12 float64);
+    the result lands in cost_out (at least one float64) and optionally
+    lambda0_out (at least n_voxels float64).  Nothing is copied: a
+    non-contiguous or wrongly shaped tensor raises instead (a copy would be
+    an allocation, and an output copy would never reach the caller).
+    Asynchronous on `stream`; calls that overlap on the GPU share the
+    library's scratch and must be serialised.
     """
-    args = [_Arg(voxel_offsets, np.int64), _Arg(obs_scan, np.int32), _Arg(agg_centred, np.float64),
-            _Arg(poses, np.float64), _Arg(cost_out, np.float64)]
-    lam = _Arg(lambda0_out, np.float64) if lambda0_out is not None else None
-    if not all(a.device for a in args) or (lam is not None and not lam.device):
-        raise ValueError("ba_eval_cost_noalloc takes CUDA tensors")
-    vo, os_, ag, po, co = args
+    import torch
+    want = {"voxel_offsets": (voxel_offsets, torch.int64), "obs_scan": (obs_scan, torch.int32),
+            "agg_centred": (agg_centred, torch.float64), "poses": (poses, torch.float64),
+            "cost_out": (cost_out, torch.float64)}
+    if lambda0_out is not None:
+        want["lambda0_out"] = (lambda0_out, torch.float64)
+    for name, (t, dt) in want.items():
+        if not _is_torch_cuda(t):
+            raise ValueError(f"ba_eval_cost_noalloc: {name} must be a CUDA tensor")
+        if t.dtype != dt:
+            raise TypeError(f"ba_eval_cost_noalloc: {name} must be {dt}, got {t.dtype}")
+        if not t.is_contiguous():
+            raise ValueError(f"ba_eval_cost_noalloc: {name} must be contiguous (no copy is made)")
+    if voxel_offsets.dim() != 1 or obs_scan.dim() != 1:
+        raise ValueError("ba_eval_cost_noalloc: voxel_offsets and obs_scan must be 1-D")
+    n_voxels, n_obs = voxel_offsets.shape[0] - 1, obs_scan.shape[0]
+    if tuple(agg_centred.shape) != (n_obs, 10):
+        raise ValueError(f"ba_eval_cost_noalloc: agg_centred must be ({n_obs}, 10), got {tuple(agg_centred.shape)}")
+    if poses.numel() < 12 * int(n_scans):
+        raise ValueError(f"ba_eval_cost_noalloc: poses must hold n_scans x 12 = {12 * int(n_scans)} values")
+    if cost_out.numel() < 1:
+        raise ValueError("ba_eval_cost_noalloc: cost_out must hold one value")
+    if lambda0_out is not None and lambda0_out.numel() < n_voxels:
+        raise ValueError(f"ba_eval_cost_noalloc: lambda0_out must hold n_voxels = {n_voxels} values")
     s = None if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
-    status = _lib.lib().ba_eval_cost_noalloc(int(n_scans), vo.shape[0] - 1, os_.shape[0], vo.ptr, os_.ptr, ag.ptr,
-                                            po.ptr, co.ptr, lam.ptr if lam is not None else None, s)
+    status = _lib.lib().ba_eval_cost_noalloc(int(n_scans), n_voxels, n_obs, voxel_offsets.data_ptr(),
+                                            obs_scan.data_ptr(), agg_centred.data_ptr(), poses.data_ptr(),
+                                            cost_out.data_ptr(),
+                                            lambda0_out.data_ptr() if lambda0_out is not None else None, s)
     if status != _lib.BA_OK:
         raise BAError(status, "ba_eval_cost_noalloc")
     return cost_out

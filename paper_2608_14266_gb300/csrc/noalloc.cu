@@ -9,7 +9,11 @@
 // file-scope __device__ array that every GPU loading the library holds until
 // the process exits.  Host code may not use the array's name as a device
 // address, so the address is fetched once per device with
-// cudaGetSymbolAddress and passed to the kernels.
+// cudaGetSymbolAddress and passed to the kernels.  The cached address belongs
+// to the device's context of that moment: after cudaDeviceReset (or anything
+// else that tears down and recreates the primary context) the library's
+// module is loaded anew and the cache is stale, so the entry point must not
+// be used across a device reset.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -147,9 +151,14 @@ extern "C" ba_status ba_eval_cost_noalloc(int32_t n_scans, int64_t n_voxels, int
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int64_t blocks = (n_voxels + kThreads - 1) / kThreads;
+  // an error left pending by earlier, unrelated work on this thread is not
+  // this call's to report: clear it, then check each launch on its own
+  (void)cudaGetLastError();
   noalloc_reset_kernel<<<1, 1, 0, s>>>(scratch);
+  if (cudaGetLastError() != cudaSuccess) return BA_ERR_CUDA;
   noalloc_cost_kernel<<<(unsigned)blocks, kThreads, 0, s>>>(n_voxels, n_obs, voxel_offsets, obs_scan, agg_centred,
                                                             poses, n_scans, lambda0_out, scratch);
+  if (cudaGetLastError() != cudaSuccess) return BA_ERR_CUDA;
   noalloc_sum_kernel<<<1, 256, 0, s>>>(blocks, scratch, cost_out);
   return cudaGetLastError() == cudaSuccess ? BA_OK : BA_ERR_CUDA;
 }

@@ -436,3 +436,119 @@ def test_lm_rejects_when_damping_solve_fails():
     assert lm.st.solve_failed == 1
     np.testing.assert_array_equal(lm.poses, before)
     assert lm.mu == pytest.approx(2.0 * mu)
+
+
+# ---- LM rule: predicted reduction and Nielsen damping update (Sec. IV-C, Algorithm 2
+# PredResReduction / Adjust; the rule of Madsen, Nielsen & Tingleff 2004) ---------------
+#
+# The predicted reduction L is the decrease of the quadratic model of the MM surrogate,
+# and the surrogate (Eq. 3, fixed-plane form) is evaluated here by brute force over the
+# raw points (oracle.surrogate_points, pinned above), so L is checked against the
+# function it models rather than against its own formula.
+
+def _surrogate(s, po, pts, poses, planes_l):
+    return oracle.surrogate_points(s.voxel_off, s.obs_scan, po, pts, poses, planes_l)
+
+
+def _translation_only(lm):
+    """Decouple the rotation block from g and H (oracle state, CPU): the damped
+    solve then returns a zero rotation increment, so the trial pose moves only
+    t, along which the surrogate is exactly quadratic."""
+    lm.g[:, :3] = 0.0
+    lm.H[:, :3, 3:] = 0.0
+    lm.H[:, 3:, :3] = 0.0
+
+
+def _translation_step(lm, s):
+    """The trial poses of a translation-only step, from numpy's solver:
+    (H_tt + mu diag(H_tt)) dt = -g_t per scan, scan 0 (the gauge) fixed."""
+    P1 = lm.poses.copy()
+    seen = np.bincount(s.obs_scan, minlength=s.n_scans) > 0
+    for j in range(1, s.n_scans):
+        if not seen[j]:
+            continue
+        Htt = lm.H[j, 3:, 3:]
+        P1[j, 9:] += np.linalg.solve(Htt + lm.mu * np.diag(np.diag(Htt)), -lm.g[j, 3:])
+    return P1
+
+
+def test_lm_prediction_equals_surrogate_decrease_for_translation_steps():
+    """Along t the surrogate is a quadratic, so L = c_M(T^l) - c_M(T') to rounding."""
+    s, pts, po, raw, cen = tiny_scene()
+    lm = oracle.LM(oracle.ObsProblem(s.n_scans, s.voxel_off, s.obs_scan, cen), s.pose_init)
+    P0, planes_l = lm.poses.copy(), lm.planes.copy()
+    _translation_only(lm)
+    expect = _translation_step(lm, s)
+    assert lm.step()
+    np.testing.assert_array_equal(lm.poses[:, :9], P0[:, :9])  # Exp(0) R = R exactly
+    np.testing.assert_allclose(lm.poses[:, 9:], expect[:, 9:], rtol=0, atol=1e-12)
+    dec = _surrogate(s, po, pts, P0, planes_l) - _surrogate(s, po, pts, lm.poses, planes_l)
+    assert dec > 0
+    assert lm.st.last_pred == pytest.approx(dec, rel=1e-10)
+
+
+def test_lm_prediction_matches_surrogate_to_third_order():
+    """For a general increment the model error is O(|D|^3): the third-order
+    coefficient err / |D|^3 stays put while the step shrinks by 30x (a wrong
+    weight of the quadratic term, or a wrong rotation term of the exact
+    Hessian, leaves an O(|D|^2) error, whose coefficient grows as 1/|D|)."""
+    from tests._util import rot_angle
+    s, pts, po, raw, cen = tiny_scene()
+    prob = oracle.ObsProblem(s.n_scans, s.voxel_off, s.obs_scan, cen)
+    coef, rel = [], []
+    for mu in (30.0, 100.0, 300.0, 1000.0):
+        lm = oracle.LM(prob, s.pose_init)
+        lm.st.mu = mu
+        P0, planes_l = lm.poses.copy(), lm.planes.copy()
+        assert lm.step()
+        P1 = lm.poses
+        d = max(np.hypot(rot_angle(b[:9].reshape(3, 3) @ a[:9].reshape(3, 3).T), np.linalg.norm(b[9:] - a[9:]))
+                for a, b in zip(P0, P1))
+        dec = _surrogate(s, po, pts, P0, planes_l) - _surrogate(s, po, pts, P1, planes_l)
+        err = abs(lm.st.last_pred - dec)
+        coef.append(err / d ** 3)
+        rel.append(err / dec)
+    assert max(coef) < 2.0 * min(coef), coef
+    assert rel[-1] < 1e-8, rel
+
+
+@pytest.mark.parametrize("rho", [0.2, 0.5, 0.75, 0.9, 1.3])
+def test_lm_damping_update_follows_nielsen(rho):
+    """After an accepted step mu' = mu max(1/3, 1 - (2 rho - 1)^3) and nu = 2, with
+    rho = (c - c') / (c_M(T^l) - c_M(T')) formed here: c' by brute force over the
+    raw points, the surrogate decrease likewise.  The cost the step starts from is
+    set so that the step has the chosen gain ratio."""
+    s, pts, po, raw, cen = tiny_scene()
+    lm = oracle.LM(oracle.ObsProblem(s.n_scans, s.voxel_off, s.obs_scan, cen), s.pose_init)
+    P0, planes_l = lm.poses.copy(), lm.planes.copy()
+    _translation_only(lm)
+    P1 = _translation_step(lm, s)
+    c1, _ = oracle.cost_points(s.voxel_off, s.obs_scan, po, pts, P1)
+    L = _surrogate(s, po, pts, P0, planes_l) - _surrogate(s, po, pts, P1, planes_l)
+    lm.st.cost = c1 + rho * L
+    lm.st.nu = 8.0
+    mu = lm.mu
+    assert lm.step()
+    assert lm.st.last_rho == pytest.approx(rho, rel=1e-8)
+    assert lm.mu == pytest.approx(mu * max(1.0 / 3.0, 1.0 - (2.0 * rho - 1.0) ** 3), rel=1e-8)
+    assert lm.nu == 2.0
+    assert lm.cost == pytest.approx(c1, rel=1e-12)
+
+
+def test_lm_rejection_by_cost_raises_damping():
+    """c(T') >= c(T) rejects: poses kept, mu *= nu, nu *= 2, twice in a row."""
+    s, pts, po, raw, cen = tiny_scene()
+    lm = oracle.LM(oracle.ObsProblem(s.n_scans, s.voxel_off, s.obs_scan, cen), s.pose_init)
+    P0 = lm.poses.copy()
+    _translation_only(lm)
+    P1 = _translation_step(lm, s)
+    c1, _ = oracle.cost_points(s.voxel_off, s.obs_scan, po, pts, P1)
+    lm.st.cost = c1 * (1.0 - 1e-9)
+    mu = lm.mu
+    assert not lm.step()
+    np.testing.assert_array_equal(lm.poses, P0)
+    assert lm.mu == pytest.approx(2.0 * mu) and lm.nu == 4.0
+    assert lm.st.last_rho < 0
+    assert not lm.step()
+    assert lm.mu == pytest.approx(8.0 * mu) and lm.nu == 8.0
+    assert lm.st.consec_reject == 2
