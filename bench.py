@@ -44,10 +44,15 @@ VOXEL_PASS_FLOP_PER_OBS = 121
 # bytes one voxel-pass launch must move per observation slot: 10 doubles + a
 # 4-byte scan index (the pose table and per-voxel outputs are small)
 VOXEL_PASS_BYTES_PER_ELEM = 84
-# mixed voxel pass: per observation one 48-byte slot (offset and N, scatter
-# eigenvalues and scan index, eigenvector quaternion); per voxel its length
-# (4 B), anchor (16 B), frame and centroid read and written (2 x 32 B) and the
-# plane written (16 B)
+# The method's bytes of one mixed voxel pass (the roofline's numerator): per
+# observation its cluster, 10 FP32 values, and a 4-byte scan index; per voxel
+# its observation count (4 B) and a 32-byte plane record written.
+MIXED_ALG_BYTES_PER_OBS = 44
+MIXED_ALG_BYTES_PER_VOXEL = 36
+# What this layout moves per launch (reported beside it): per observation one
+# 48-byte slot (offset and N, scatter eigenvalues and scan index, eigenvector
+# quaternion); per voxel its length (4 B), anchor (16 B), frame and centroid
+# read and written (2 x 32 B) and the plane written (16 B)
 MIXED_VOXEL_BYTES_PER_OBS = 48
 MIXED_VOXEL_BYTES_PER_VOXEL = 100
 
@@ -60,8 +65,16 @@ def _args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["city", "mid", "tiny", "batched", "served", "voxelize", "sweep"],
                     default="city")
-    ap.add_argument("--jobs", type=int, default=256, help="jobs of the batched / served workloads")
-    ap.add_argument("--fp64-jobs", type=int, default=256, help="of which solved on the plain FP64 path too")
+    ap.add_argument("--batched-jobs", type=int, default=256, help="jobs of the batched workload")
+    ap.add_argument("--fp64-jobs", type=int, default=256, help="batched: of which solved on the plain FP64 path too")
+    ap.add_argument("--served-jobs", type=int, default=20000, help="jobs of the served stream")
+    ap.add_argument("--served-fp64-jobs", type=int, default=200,
+                    help="served: the stream's first arrivals also served by the plain FP64 path")
+    ap.add_argument("--burst-jobs", type=int, default=2000, help="served: jobs of the capacity burst")
+    ap.add_argument("--agreement-jobs", type=int, default=16, help="batched: jobs of the pose-agreement study")
+    ap.add_argument("--cpu-jobs", type=int, default=20, help="batched / served: jobs timed on the CPU oracle")
+    ap.add_argument("--no-batched", action="store_true", help="default run: skip the batched workload")
+    ap.add_argument("--no-served", action="store_true", help="default run: skip the served workload")
     ap.add_argument("--rate", type=float, default=200.0, help="served: Poisson arrival rate (jobs/s)")
     ap.add_argument("--budget-gb", type=float, default=120.0, help="served: device memory budget")
     ap.add_argument("--chunk", type=int, default=0,
@@ -422,11 +435,15 @@ def roofline_for(precision, scene, prof, workload):
                 "flop_per_launch": flops,
                 "hbm_view_gbs": VOXEL_PASS_BYTES_PER_ELEM * scene.n_obs / vp_avg_s / 1e9}
     peak, src = hbm_peak()
-    nbytes = MIXED_VOXEL_BYTES_PER_OBS * scene.n_obs + MIXED_VOXEL_BYTES_PER_VOXEL * scene.n_voxels
+    nbytes = MIXED_ALG_BYTES_PER_OBS * scene.n_obs + MIXED_ALG_BYTES_PER_VOXEL * scene.n_voxels
+    layout = MIXED_VOXEL_BYTES_PER_OBS * scene.n_obs + MIXED_VOXEL_BYTES_PER_VOXEL * scene.n_voxels
     achieved = nbytes / vp_avg_s / 1e9
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": recorded_traffic(workload, "voxel_pass_mixed"), "kernel": "voxel_pass_mixed",
-            "avg_launch_ms": vp_avg_s * 1000.0, "peak_source": src, "bytes_per_launch": nbytes}
+            "avg_launch_ms": vp_avg_s * 1000.0, "peak_source": src, "bytes_per_launch": nbytes,
+            "basis": "the method's bytes: 44 B per observation (10 FP32 cluster values + scan index) + "
+                     "36 B per voxel (count + 32-byte plane record)",
+            "layout_bytes_per_launch": layout, "layout_gbs": layout / vp_avg_s / 1e9}
 
 
 def hbm_peak():
@@ -551,29 +568,28 @@ def run_ours(args):
         "roofline": roofline,
         "cpu_baseline": cpu,
     }
+    # configs 4 and 5 (one GPU): nested in the same line
+    if world == 1:
+        import oracle
+        ora = None if args.no_cpu_baseline else oracle
+        if not args.no_batched:
+            line["batched"] = batched_result(args, mm, torch, scenegen, ora)
+        if not args.no_served:
+            line["served"] = served_result(args, mm, torch, scenegen, ora)
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
 
 
-def _load_job(mm, torch, scene, prec, stream, **cfg):
-    dev = torch.device("cuda")
-    agg = device_clusters_gpu(scene, torch, mm)
-    ba = mm.BundleAdjuster(precision=prec, cuda_stream=stream, **cfg)
-    ba.load_observations(scene.n_scans, torch.from_numpy(scene.voxel_off).to(dev),
-                         torch.from_numpy(scene.obs_scan).to(dev), agg, torch.from_numpy(scene.pose_init).to(dev))
-    return ba
-
-
-def _gt_rms(P, scene):
+def _gt_rms(P, gt):
     """RMS rotation (rad) and translation (m) error of solved poses against
-    the generator's ground truth (scan 0, the gauge, is exact on both)."""
+    the generator's ground truth gt (scan 0, the gauge, is exact on both)."""
     import numpy as np
     R1 = P[:, :9].reshape(-1, 3, 3)
-    R2 = scene.pose_gt[:, :9].reshape(-1, 3, 3)
+    R2 = gt[:, :9].reshape(-1, 3, 3)
     D = np.einsum("nij,nkj->nik", R1, R2)
     ang = np.arccos(np.clip(0.5 * (np.trace(D, axis1=1, axis2=2) - 1.0), -1.0, 1.0))
-    return float(np.sqrt(np.mean(ang ** 2))), float(np.sqrt(np.mean(np.sum((P[:, 9:] - scene.pose_gt[:, 9:]) ** 2, 1))))
+    return float(np.sqrt(np.mean(ang ** 2))), float(np.sqrt(np.mean(np.sum((P[:, 9:] - gt[:, 9:]) ** 2, 1))))
 
 
 class _Accuracy:
@@ -582,8 +598,8 @@ class _Accuracy:
     def __init__(self):
         self.sums = {}
 
-    def add(self, path, P, scene):
-        r, t = _gt_rms(P, scene)
+    def add(self, path, P, gt):
+        r, t = _gt_rms(P, gt)
         a = self.sums.setdefault(path, [0.0, 0.0, 0])
         a[0] += r
         a[1] += t
@@ -607,21 +623,150 @@ def _pose_diff(P, Q):
 SOLVE_CFG = dict(rel_tol=1e-8, max_iters=200, max_consec_reject=10)
 
 
-def run_batched(args):
-    """Many independent jobs solved together in one batch (mixed precision)
-    against the same jobs solved one after another on the plain FP64 path."""
-    args.chunk = args.chunk or 8
-    import torch
+class JobFactory:
+    """Jobs of the many-job workloads generated on the GPU, all queued on one
+    stream: structure, poses and patches by the scene generator's device
+    kernels (the host generator's streams), points drawn in FP32 from the same
+    per-observation counters (scenegen_gpu.cu), clusters formed by the
+    library (ba_aggregate_points)."""
 
-    import __graft_entry__
-    __graft_entry__.build()
-    import paper_2608_14266_gb300 as mm
-    import scenegen
-    torch.cuda.set_device(0)
+    def __init__(self, mm, torch, stream, chunk_obs: int = 1 << 20, pts_per_obs: int = 32):
+        self.mm, self.torch, self.stream = mm, torch, stream
+        self.chunk, self.npo = chunk_obs, pts_per_obs
+        with torch.cuda.stream(stream):
+            self.buf = torch.empty((chunk_obs * pts_per_obs, 3), dtype=torch.float64, device="cuda")
+            self.po = torch.arange(chunk_obs + 1, dtype=torch.int64, device="cuda") * pts_per_obs
+
+    def make(self, params, offsets=None):
+        import scenegen
+        assert params.pts_per_obs == self.npo
+        torch = self.torch
+        sc = scenegen.make_scene_device(params, stream=self.stream, offsets=offsets)
+        with torch.cuda.stream(self.stream):
+            agg = torch.empty((max(sc.n_obs, 1), 10), dtype=torch.float64, device="cuda")[: sc.n_obs]
+        for o0 in range(0, sc.n_obs, self.chunk):
+            o1 = min(sc.n_obs, o0 + self.chunk)
+            pts = self.buf[: (o1 - o0) * self.npo]
+            sc.points_fast(o0, o1, pts, stream=self.stream)
+            self.mm.ba_aggregate_points(self.po[: o1 - o0 + 1], pts, agg[o0:o1], stream=self.stream)
+        return sc, agg
+
+
+def _dev_inputs(sc, agg):
+    return sc.voxel_off, sc.obs_scan, agg, sc.pose_init
+
+
+def _oracle_seconds_per_job(oracle_mod, samples):
+    """Oracle seconds per job on a sample: one timed oracle LM iteration per
+    job (after its set-up), times the iterations the plain FP64 GPU path
+    needed for that job.  samples: (n_scans, voxel_off, obs_scan, agg, poses,
+    iterations) on the host."""
+    per_job = []
+    for n_scans, vo, os_, ag, po, iters in samples:
+        lm = oracle_mod.LM(oracle_mod.ObsProblem(n_scans, vo, os_, ag), po)
+        t0 = time.perf_counter()
+        lm.step()
+        per_job.append((time.perf_counter() - t0) * max(1, iters))
+    return float(sum(per_job) / len(per_job))
+
+
+def _host_sample(sc, agg, iters):
+    return (sc.n_scans, sc.voxel_off.cpu().numpy(), sc.obs_scan.cpu().numpy(), agg.cpu().numpy(),
+            sc.pose_init.cpu().numpy(), iters)
+
+
+def _pose_agreement(mm, torch, items, stream):
+    """Mixed against plain FP64 poses three ways, on jobs given as (scene,
+    clusters) on the device: (a) both paths at the FP64 solve's iteration
+    count; (b) both solved to a common tight stop (rel_tol 0: 10 rejected
+    steps in a row or 200 iterations); (c) the mixed path stopped by the
+    FP64 cost of its own poses (the allocation-free FP64 cost evaluation,
+    relative change below 1e-8 on an accepted step), against the FP64 path's
+    ordinary stop."""
+    worst = {"equal_iterations": [0.0, 0.0], "tight_stop": [0.0, 0.0], "fp64_decided_stop": [0.0, 0.0],
+             "default_stop": [0.0, 0.0]}
+    iters = {"fp64_default": 0, "mixed_default": 0, "mixed_fp64_decided": 0, "fp64_tight": 0, "mixed_tight": 0}
+
+    def upd(key, P, Q):
+        r, t = _pose_diff(P, Q)
+        worst[key][0] = max(worst[key][0], r)
+        worst[key][1] = max(worst[key][1], t)
+
+    def load(prec, sc, agg, **cfg):
+        ba = mm.BundleAdjuster(precision=prec, cuda_stream=stream, **cfg)
+        ba.load_observations(sc.n_scans, *_dev_inputs(sc, agg))
+        return ba
+
+    for sc, agg in items:
+        with load(mm.BA_FP64, sc, agg, **SOLVE_CFG) as b64:
+            n64 = b64.solve()["iters"]
+            P64 = b64.poses()
+        with load(mm.BA_MIXED, sc, agg, **SOLVE_CFG) as bm:
+            st = bm.solve()
+            upd("default_stop", bm.poses(), P64)
+            iters["mixed_default"] += st["iters"]
+        iters["fp64_default"] += n64
+        with load(mm.BA_MIXED, sc, agg, **SOLVE_CFG) as bm:
+            bm.iterate(n64, stats=False)
+            upd("equal_iterations", bm.poses(), P64)
+        tight = dict(SOLVE_CFG, rel_tol=0.0)
+        with load(mm.BA_FP64, sc, agg, **tight) as b64, load(mm.BA_MIXED, sc, agg, **tight) as bm:
+            iters["fp64_tight"] += b64.solve()["iters"]
+            iters["mixed_tight"] += bm.solve()["iters"]
+            upd("tight_stop", bm.poses(), b64.poses())
+        # (c): FP64 cost of the mixed iterate after every accepted step
+        cost = torch.empty(1, dtype=torch.float64, device="cuda")
+        pd = torch.empty((sc.n_scans, 12), dtype=torch.float64, device="cuda")
+        with load(mm.BA_MIXED, sc, agg, **tight) as bm:
+            prev = None
+            n = 0
+            while n < SOLVE_CFG["max_iters"]:
+                st = bm.iterate(1)
+                n += 1
+                if not st["last_accepted"]:
+                    if st["consec_reject"] >= SOLVE_CFG["max_consec_reject"]:
+                        break
+                    continue
+                bm.poses(out=pd)
+                with torch.cuda.stream(stream):
+                    mm.ba_eval_cost_noalloc(sc.n_scans, sc.voxel_off, sc.obs_scan, agg, pd, cost, stream=stream)
+                c = float(cost.item())
+                if prev is None:
+                    with torch.cuda.stream(stream):
+                        mm.ba_eval_cost_noalloc(sc.n_scans, sc.voxel_off, sc.obs_scan, agg, sc.pose_init, cost,
+                                                stream=stream)
+                    prev = float(cost.item())
+                if prev - c <= SOLVE_CFG["rel_tol"] * prev:
+                    break
+                prev = c
+            iters["mixed_fp64_decided"] += n
+            upd("fp64_decided_stop", bm.poses(), P64)
+    out = {k: {"max_rot_rad": v[0], "max_trans_m": v[1]} for k, v in worst.items()}
+    out["iterations_total"] = iters
+    out["jobs"] = len(items)
+    return out
+
+
+def batched_result(args, mm, torch, scenegen, oracle_mod=None):
+    """Config 4: many independent jobs solved together in one batch (mixed
+    precision, autotuned launch settings, CUDA-graph iterations) against the
+    same jobs solved one after another on the plain FP64 path."""
+    import numpy as np
+    chunk = args.chunk or 8
+    n_jobs = args.batched_jobs
     stream = torch.cuda.current_stream()
-    scenes = [scenegen.make_scene(job_params(scenegen, k, 20, 2000, 4000)) for k in range(args.jobs)]
-    n_obs = sum(s.n_obs for s in scenes)
-    jobs = [_load_job(mm, torch, s, mm.BA_MIXED, stream, **SOLVE_CFG) for s in scenes]
+    params = [job_params(scenegen, k, 20, 2000, 4000) for k in range(n_jobs)]
+    fac = JobFactory(mm, torch, stream)
+    made = [fac.make(p) for p in params]
+    gts = [sc.pose_gt.cpu().numpy() for sc, _ in made]
+    torch.cuda.synchronize()
+    n_obs = sum(sc.n_obs for sc, _ in made)
+    n_vox = sum(sc.n_voxels for sc, _ in made)
+    jobs = []
+    for sc, agg in made:
+        ba = mm.BundleAdjuster(precision=mm.BA_MIXED, cuda_stream=stream, **SOLVE_CFG)
+        ba.load_observations(sc.n_scans, *_dev_inputs(sc, agg))
+        jobs.append(ba)
     torch.cuda.synchronize()
     with mm.Batch(stream) as b:
         for j in jobs:
@@ -629,144 +774,246 @@ def run_batched(args):
         t0 = time.perf_counter()
         # the tuner's trials are the solve's first iterations (results do not depend on its choice)
         tune = b.autotune(iters_per_trial=1, passes=1)
-        active = b.solve(chunk=args.chunk)
+        active = b.solve(chunk=chunk)
         torch.cuda.synchronize()
         t_mixed = time.perf_counter() - t0
         launches = b.kernel_launches()
-    iters_mixed = sum(j.stats()["iters"] for j in jobs)
-    mixed_poses = [j.poses() for j in jobs]
+        iters_mixed = sum(j.stats()["iters"] for j in jobs)
+        mixed_poses = [j.poses() for j in jobs]
+        # roofline of the batch kernels: every job back at its initial poses,
+        # four iterations with per-kernel events (every launch covers every job)
+        for j, (sc, _) in zip(jobs, made):
+            j.set_state(sc.pose_init, 1e-4, 2.0)
+        torch.cuda.synchronize()
+        b.profile(True)
+        b.iterate(4)
+        prof = b.profile_read()
+        b.profile(False)
     for j in jobs:
         j.close()
-    torch.cuda.empty_cache()
+    peak, src = hbm_peak()
+    vp_ms, vp_n = prof["voxel_pass"]
+    vbytes = 4 * (MIXED_ALG_BYTES_PER_OBS * n_obs + MIXED_ALG_BYTES_PER_VOXEL * n_vox)
+    achieved = vbytes / (vp_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "voxel_pass_mixed_batch", "avg_launch_ms": vp_ms / max(1, vp_n),
+                "launches": vp_n, "peak_source": src,
+                "bytes_per_launch": vbytes / max(1, vp_n),
+                "basis": "44 B per observation + 36 B per voxel (the method's bytes), all jobs of a group per launch",
+                "kernel_ms": {k: {"total_ms": v[0], "launches": v[1]} for k, v in prof.items()}}
     # plain FP64, one job after another (loads outside the timed region)
     t_fp64, iters_fp64, worst = 0.0, 0, (0.0, 0.0)
     acc = _Accuracy()
-    for s, mp in zip(scenes[: args.fp64_jobs], mixed_poses):
-        ba = _load_job(mm, torch, s, mm.BA_FP64, stream, **SOLVE_CFG)
+    fp64_iters = []
+    n64 = min(n_jobs, args.fp64_jobs)
+    for k in range(n64):
+        sc, agg = made[k]
+        ba = mm.BundleAdjuster(precision=mm.BA_FP64, cuda_stream=stream, **SOLVE_CFG)
+        ba.load_observations(sc.n_scans, *_dev_inputs(sc, agg))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         st = ba.solve()
         t_fp64 += time.perf_counter() - t0
         iters_fp64 += st["iters"]
+        fp64_iters.append(st["iters"])
         P64 = ba.poses()
-        r, t = _pose_diff(mp, P64)
+        r, t = _pose_diff(mixed_poses[k], P64)
         worst = (max(worst[0], r), max(worst[1], t))
-        acc.add("mixed", mp, s)
-        acc.add("fp64", P64, s)
+        acc.add("mixed", mixed_poses[k], gts[k])
+        acc.add("fp64", P64, gts[k])
         ba.close()
-    n64 = min(args.jobs, args.fp64_jobs)
-    line = {
+    agreement = _pose_agreement(mm, torch, made[: args.agreement_jobs], stream)
+    cpu = None
+    if oracle_mod is not None:
+        k_s = min(args.cpu_jobs, n64)
+        samples = [_host_sample(made[k][0], made[k][1], fp64_iters[k]) for k in range(k_s)]
+        s_per_job = _oracle_seconds_per_job(oracle_mod, samples)
+        cpu = {"value": 1.0 / s_per_job, "unit": "jobs/s", "cores": 1, "kind": "oracle",
+               "sample": f"jobs 0-{k_s - 1} of the batch: one oracle LM iteration each, timed, times the "
+                         "iterations the plain FP64 GPU path needed for that job"}
+    del made
+    torch.cuda.empty_cache()
+    return {
         "metric": "batched jobs/s (mixed, one batch) vs sequential plain FP64", "workload": "batched",
-        "value": args.jobs / t_mixed, "unit": "jobs/s", "n_gpus": 1, "jobs": args.jobs, "clusters": n_obs,
+        "value": n_jobs / t_mixed, "unit": "jobs/s", "jobs": n_jobs, "clusters": n_obs, "voxels": n_vox,
         "seconds": t_mixed, "iterations": iters_mixed, "unfinished": active, "gpu_launches": launches,
         "fp64_sequential": {"value": n64 / t_fp64 if t_fp64 else None, "unit": "jobs/s", "jobs": n64,
                             "seconds": t_fp64, "iterations": iters_fp64},
-        "pose_agreement_mixed_vs_fp64": {"max_rot_rad": worst[0], "max_trans_m": worst[1], "jobs": n64},
+        "speedup_vs_fp64": (n_jobs / t_mixed) / (n64 / t_fp64) if t_fp64 else None,
+        "pose_agreement_mixed_vs_fp64": {"max_rot_rad": worst[0], "max_trans_m": worst[1], "jobs": n64,
+                                         "stop": "each path's own stop rule (rel_tol 1e-8)"},
+        "pose_agreement_study": agreement,
         "accuracy_vs_ground_truth": acc.report(),
-        "config": {"scans": "log-uniform 20-2000", "voxels": "50 x scans", "obs_per_voxel": "5-30",
-                   "pts_per_obs": 32, "stop": SOLVE_CFG, "chunk": args.chunk,
+        "roofline": roofline, "cpu_baseline": cpu,
+        "config": {"workload": "256 jobs: scans log-uniform 20-2000, voxels = 50 x scans, 5-30 obs/voxel, "
+                               "32 pts/obs, 2 cm noise, 0.5 deg / 10 cm perturbation",
+                   "inputs": "each job generated on the GPU (structure, poses, points drawn in FP32, clusters by "
+                             "ba_aggregate_points) before the timed region",
+                   "stop": SOLVE_CFG, "chunk": chunk,
                    "autotune": {"passes": tune["passes"], "iterations": tune["iterations"],
                                 "chosen": tune["candidates"][tune["chosen"]] if tune["chosen"] >= 0 else None,
                                 "ms_per_iter": {f"mb{c['min_blocks']}_pf{c['prefetch']}": round(c["ms_per_iter"], 4)
                                                 for c in tune["candidates"]}}},
     }
-    print(json.dumps(line), flush=True)
 
 
-def run_served(args):
-    """Poisson arrivals of BA jobs served by continuous batching, against the
-    same arrival stream served one job at a time on the plain FP64 path."""
-    args.chunk = args.chunk or 16
+def served_result(args, mm, torch, scenegen, oracle_mod=None):
+    """Config 5: an open-loop Poisson stream of BA jobs served by continuous
+    batching (mixed precision), each job generated on the GPU from its seed
+    when it is admitted, on a side stream, and loaded by the library's loader
+    thread while the resident jobs step; against the same stream served one
+    job at a time on the plain FP64 path (a stated sample of it)."""
+    import collections
+    from concurrent.futures import ThreadPoolExecutor
+
     import numpy as np
+
+    from paper_2608_14266_gb300.server import Job, Server, latency_summary
+    chunk = args.chunk or 16
+    n_jobs = args.served_jobs
+    rng = np.random.default_rng(77)
+    arrivals = np.cumsum(rng.exponential(1.0 / args.rate, size=n_jobs))
+    params = [job_params(scenegen, k, 50, 5000, 9000) for k in range(n_jobs)]
+    main = torch.cuda.current_stream()
+    side = torch.cuda.Stream()
+    fac = JobFactory(mm, torch, side)
+    n_sample = min(n_jobs, args.served_fp64_jobs)
+    pool = ThreadPoolExecutor(max(2, min(8, (os.cpu_count() or 2) // 2)))
+
+    def serve(order_arrivals, budget, sample_gt):
+        """Serves jobs 0..len(order_arrivals)-1 arriving at the given times."""
+        m = len(order_arrivals)
+        ahead = collections.deque()
+        nxt = 0  # next job whose offsets are requested
+        gt_host = {}
+        clock0 = time.perf_counter()
+        clk = lambda: time.perf_counter() - clock0
+        srv = Server(budget, chunk=chunk, clock=clk, precision=mm.BA_MIXED, cuda_stream=main,
+                     async_admission=True, input_stream=side, **SOLVE_CFG)
+
+        def inputs(k, off):
+            sc, agg = fac.make(params[k], offsets=off)
+            if sample_gt and k < n_sample:
+                h = torch.empty((sc.n_scans, 12), dtype=torch.float64).pin_memory()
+                with torch.cuda.stream(side):
+                    h.copy_(sc.pose_gt, non_blocking=True)
+                gt_host[k] = h
+            return _dev_inputs(sc, agg)
+
+        k = 0
+        while k < m or not srv.idle:
+            while nxt < m and nxt < k + 64:  # the offsets (count stream, host) of the next arrivals
+                ahead.append(pool.submit(scenegen.pinned_voxel_offsets, params[nxt]))
+                nxt += 1
+            now = clk()
+            while k < m and order_arrivals[k] <= now:
+                if not ahead:  # a burst ran past the look-ahead
+                    ahead.append(pool.submit(scenegen.pinned_voxel_offsets, params[nxt]))
+                    nxt += 1
+                off = ahead.popleft().result()
+                p = params[k]
+                srv.submit(Job(job_id=k, n_scans=p.n_scans, n_voxels=p.n_voxels, n_obs=int(off[-1]),
+                               arrival=float(order_arrivals[k]), inputs=lambda k=k, off=off: inputs(k, off)))
+                k += 1
+            if srv.idle:
+                time.sleep(max(0.0, min(order_arrivals[k] - now, 0.01)) if k < m else 0.0)
+                continue
+            srv.step()
+        t_end = clk()
+        out = (srv.finished, srv.failed, t_end, srv.kernel_launches())
+        srv.close()
+        torch.cuda.synchronize()
+        return out + (gt_host,)
+
+    budget = args.budget_gb * (1 << 30)
+    jobs_m, failed_m, t_m, launches_m, gt_host = serve(arrivals, budget, True)
+    # capacity: a burst of the first jobs all arriving at once
+    n_burst = min(n_jobs, args.burst_jobs)
+    jobs_b, failed_b, t_b, _, _ = serve(np.zeros(n_burst), budget, False)
+    pool.shutdown()
+    torch.cuda.empty_cache()
+    # plain FP64, one job at a time, on the first n_sample arrivals of the same stream
+    clock0 = time.perf_counter()
+    lat64, worst, acc, fp64_iters, samples = [], (0.0, 0.0), _Accuracy(), [], []
+    poses_m = {j.job_id: j.poses for j in jobs_m}
+    for k in range(n_sample):
+        now = time.perf_counter() - clock0
+        if arrivals[k] > now:
+            time.sleep(arrivals[k] - now)
+        sc, agg = fac.make(params[k])
+        side.synchronize()
+        ba = mm.BundleAdjuster(precision=mm.BA_FP64, cuda_stream=main, **SOLVE_CFG)
+        ba.load_observations(sc.n_scans, *_dev_inputs(sc, agg))
+        st = ba.solve()
+        P = ba.poses()
+        lat64.append(time.perf_counter() - clock0 - arrivals[k])
+        fp64_iters.append(st["iters"])
+        gt = gt_host[k].numpy()
+        if k in poses_m:
+            r, t = _pose_diff(poses_m[k], P)
+            worst = (max(worst[0], r), max(worst[1], t))
+            acc.add("mixed", poses_m[k], gt)
+        acc.add("fp64", P, gt)
+        if oracle_mod is not None and len(samples) < args.cpu_jobs:
+            samples.append(_host_sample(sc, agg, st["iters"]))
+        ba.close()
+        del sc, agg
+    t64 = time.perf_counter() - clock0
+    lat64 = np.array(lat64)
+    cpu = None
+    if samples:
+        s_per_job = _oracle_seconds_per_job(oracle_mod, samples)
+        cpu = {"value": 1.0 / s_per_job, "unit": "jobs/s", "cores": 1, "kind": "oracle",
+               "sample": f"the stream's first {len(samples)} jobs: one oracle LM iteration each, timed, times "
+                         "the iterations the plain FP64 GPU path needed for that job"}
+    lat = latency_summary(jobs_m)
+    adm = np.array([j.admitted - j.arrival for j in jobs_m if j.admitted is not None])
+    iters = np.array([j.stats["iters"] for j in jobs_m])
+    value = len(jobs_m) / t_m
+    fp64_value = n_sample / t64 if n_sample else None
+    return {
+        "metric": "served jobs/s and p50/p99 latency (continuous batching, mixed) vs plain FP64 per-job path",
+        "workload": "served", "value": value, "unit": "jobs/s", "jobs": n_jobs, "finished": len(jobs_m),
+        "failed": len(failed_m), "arrival_rate_per_s": args.rate, "seconds": t_m, "latency": lat,
+        "admission_wait_s": {"p50": float(np.percentile(adm, 50)), "p99": float(np.percentile(adm, 99))}
+        if adm.size else None,
+        "iterations_per_job": {"mean": float(iters.mean()), "max": int(iters.max())} if iters.size else None,
+        "capacity_burst": {"value": len(jobs_b) / t_b, "unit": "jobs/s", "jobs": n_burst, "seconds": t_b,
+                           "failed": len(failed_b), "latency": latency_summary(jobs_b)},
+        "gpu_launches": launches_m,
+        "fp64_per_job": None if n_sample == 0 else {
+            "value": fp64_value, "unit": "jobs/s", "jobs": n_sample, "seconds": t64,
+            "latency": {"p50_s": float(np.percentile(lat64, 50)), "p99_s": float(np.percentile(lat64, 99)),
+                        "mean_s": float(lat64.mean()), "max_s": float(lat64.max())},
+            "sample": f"the stream's first {n_sample} arrivals, at their arrival times, one job at a time"},
+        "speedup_vs_fp64_capacity": (len(jobs_b) / t_b) / fp64_value if fp64_value else None,
+        "pose_agreement_mixed_vs_fp64": {"max_rot_rad": worst[0], "max_trans_m": worst[1], "jobs": n_sample,
+                                         "stop": "each path's own stop rule (rel_tol 1e-8)"},
+        "accuracy_vs_ground_truth": acc.report(),
+        "cpu_baseline": cpu,
+        "config": {"workload": f"{n_jobs} jobs, Poisson arrivals at {args.rate:g}/s: scans log-uniform 50-5000, "
+                               "voxels = 50 x scans, 5-30 obs/voxel, 32 pts/obs, 2 cm noise, 0.5 deg / 10 cm",
+                   "budget_gb": args.budget_gb, "chunk": chunk, "stop": SOLVE_CFG,
+                   "inputs": "each job generated on the GPU from its seed at admission, on a side stream "
+                             "(structure, poses and patches from the generator's streams, points drawn in FP32, "
+                             "clusters by ba_aggregate_points); its load and set-up run on the library's loader "
+                             "thread and stream while the resident jobs step; the per-job observation counts "
+                             "(host count stream, ~1 ms) are drawn by a host thread pool ahead of arrival"},
+    }
+
+
+def _standalone(fn, args):
     import torch
 
     import __graft_entry__
     __graft_entry__.build()
+    import oracle
     import paper_2608_14266_gb300 as mm
     import scenegen
-    from paper_2608_14266_gb300.server import Job, Server, latency_summary
     torch.cuda.set_device(0)
-    stream = torch.cuda.current_stream()
-    rng = np.random.default_rng(77)
-    arrivals = np.cumsum(rng.exponential(1.0 / args.rate, size=args.jobs))
-    scenes = [scenegen.make_scene(job_params(scenegen, k, 50, 5000, 9000)) for k in range(args.jobs)]
-
-    def inputs(s):
-        return (torch.from_numpy(s.voxel_off).cuda(), torch.from_numpy(s.obs_scan).cuda(),
-                device_clusters_gpu(s, torch, mm), torch.from_numpy(s.pose_init).cuda())
-
-    # every job's clusters are on the device before the stream starts (the
-    # arriving data; generating them from the seeds is the input generator's
-    # work, not the server's); admission, load and set-up are timed
-    ready = [inputs(s) for s in scenes]
-    torch.cuda.synchronize()
-
-    def make_job(k):
-        s = scenes[k]
-        return Job(job_id=k, n_scans=s.n_scans, n_voxels=s.n_voxels, n_obs=s.n_obs, arrival=float(arrivals[k]),
-                   inputs=lambda k=k: ready[k])
-
-    def serve(prec, budget, chunk):
-        clock0 = time.perf_counter()
-        clk = lambda: time.perf_counter() - clock0
-        srv = Server(budget, chunk=chunk, clock=clk, precision=prec, cuda_stream=stream, **SOLVE_CFG)
-        k = 0
-        while k < args.jobs or not srv.idle:
-            now = clk()
-            while k < args.jobs and arrivals[k] <= now:
-                srv.submit(make_job(k))
-                k += 1
-            if srv.idle:
-                time.sleep(max(0.0, min(arrivals[k] - now, 0.01)) if k < args.jobs else 0.0)
-                continue
-            srv.step()
-        t_end = clk()
-        jobs = srv.finished
-        launches = srv.kernel_launches()
-        srv.close()
-        return jobs, t_end, launches
-
-    jobs_m, t_m, launches_m = serve(mm.BA_MIXED, args.budget_gb * (1 << 30), args.chunk)
-    torch.cuda.empty_cache()
-    # plain FP64, one job at a time in arrival order
-    clock0 = time.perf_counter()
-    lat64, done64, worst = [], 0, (0.0, 0.0)
-    acc = _Accuracy()
-    poses_m = {j.job_id: j.poses for j in jobs_m}
-    for k in range(min(args.jobs, args.fp64_jobs)):
-        now = time.perf_counter() - clock0
-        if arrivals[k] > now:
-            time.sleep(arrivals[k] - now)
-        ba = mm.BundleAdjuster(precision=mm.BA_FP64, cuda_stream=stream, **SOLVE_CFG)
-        ba.load_observations(scenes[k].n_scans, *ready[k])
-        ba.solve()
-        P = ba.poses()
-        lat64.append(time.perf_counter() - clock0 - arrivals[k])
-        r, t = _pose_diff(poses_m[k], P)
-        worst = (max(worst[0], r), max(worst[1], t))
-        acc.add("mixed", poses_m[k], scenes[k])
-        acc.add("fp64", P, scenes[k])
-        ba.close()
-        done64 += 1
-    t64 = time.perf_counter() - clock0
-    lat64 = np.array(lat64)
-    line = {
-        "metric": "served jobs/s and latency (continuous batching, mixed) vs plain FP64 per-job path",
-        "workload": "served", "value": len(jobs_m) / t_m, "unit": "jobs/s", "n_gpus": 1, "jobs": args.jobs,
-        "arrival_rate_per_s": args.rate, "seconds": t_m, "latency": latency_summary(jobs_m),
-        "gpu_launches": launches_m,
-        "fp64_per_job": None if done64 == 0 else {
-            "value": done64 / t64, "unit": "jobs/s", "jobs": done64, "seconds": t64,
-            "latency": {"p50_s": float(np.percentile(lat64, 50)), "p99_s": float(np.percentile(lat64, 99)),
-                        "mean_s": float(lat64.mean()), "max_s": float(lat64.max())}},
-        "pose_agreement_mixed_vs_fp64": {"max_rot_rad": worst[0], "max_trans_m": worst[1], "jobs": done64},
-        "accuracy_vs_ground_truth": acc.report(),
-        "config": {"scans": "log-uniform 50-5000", "voxels": "50 x scans", "obs_per_voxel": "5-30", "pts_per_obs": 32,
-                   "budget_gb": args.budget_gb, "chunk": args.chunk, "stop": SOLVE_CFG,
-                   "inputs": "each job's clusters resident on the device before its arrival (generated from its "
-                             "seed ahead of the stream); admission, load and set-up inside the timed loop"},
-    }
-    print(json.dumps(line), flush=True)
+    res = fn(args, mm, torch, scenegen, None if args.no_cpu_baseline else oracle)
+    res.setdefault("n_gpus", 1)
+    print(json.dumps(res), flush=True)
 
 
 # preprocessing: FP64 peak from the unit counts (152 SMs x 2 FP64 FMA lanes
@@ -999,9 +1246,9 @@ def main():
     elif args.workload == "sweep":
         run_sweep(args)
     elif args.workload == "batched":
-        run_batched(args)
+        _standalone(batched_result, args)
     elif args.workload == "served":
-        run_served(args)
+        _standalone(served_result, args)
     else:
         run_ours(args)
 

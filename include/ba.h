@@ -303,6 +303,15 @@ typedef struct {
   double ms_per_iter[16];   /* mean over the complete passes */
 } ba_tune_report;
 ba_status ba_batch_autotune(ba_batch* b, int32_t iters_per_trial, int32_t passes, ba_tune_report* out);
+/* Per-kernel timing of the batch's iterations.  While enabled, iterations
+ * are launched directly instead of through the CUDA graph (groups one after
+ * another on the batch's stream), each kernel launch bracketed by a pair of
+ * CUDA events; enabling clears earlier records.  ba_batch_profile_read
+ * synchronises and returns, for one kernel kind (BA_KERNEL_VOXEL_PASS,
+ * BA_KERNEL_SCAN_PASS, BA_KERNEL_SOLVE), the summed event time in
+ * milliseconds and the number of launches (one per group and iteration). */
+ba_status ba_batch_profile_enable(ba_batch* b, int32_t enable);
+ba_status ba_batch_profile_read(ba_batch* b, int32_t kind, double* total_ms, int64_t* launches);
 /* Apply launch settings chosen earlier (e.g. a cached ba_batch_autotune
  * result): min_blocks in {4, 6, 8}, prefetch in [0, 16].  Results do not
  * depend on them.  BA_ERR_INVALID_ARG outside those ranges. */
@@ -345,20 +354,52 @@ ba_status ba_server_create(const ba_config* cfg, int64_t mem_budget, ba_server**
  * step has retired jobs.  BA_ERR_INVALID_ARG: malformed job (as
  * ba_load_observations) or a job larger than the whole budget. */
 ba_status ba_server_submit(ba_server* s, const ba_job_desc* job, uint64_t* job_id);
-/* One round: n_iters LM iterations (ba_solve semantics) of every resident
- * job that has not stopped, then retirement of the jobs that stopped.
- * *n_resident_out and *n_retired_out (either may be NULL) receive the jobs
- * still resident and the jobs retired by this step. */
+/* One round: first the asynchronously submitted jobs whose load has finished
+ * join the batch (when nothing is resident but loads are in flight, the call
+ * waits up to 100 ms for one); then n_iters LM iterations (ba_solve
+ * semantics) of every resident job that has not stopped, then retirement of
+ * the jobs that stopped.  *n_resident_out and *n_retired_out (either may be
+ * NULL) receive the jobs still resident and the jobs retired by this step. */
 ba_status ba_server_step(ba_server* s, int32_t n_iters, int32_t* n_resident_out, int32_t* n_retired_out);
-/* *done = 0: the job is resident.  *done = 1: it has finished; its poses
- * (n_scans x 12 doubles, host) and statistics are copied to poses_out and
- * stats_out (either may be NULL) and the server forgets the job, so a later
- * poll of the same id is BA_ERR_INVALID_ARG (as is an unknown id). */
+/* *done = 0: the job is resident or still being admitted.  *done = 1: it has
+ * finished; its poses (n_scans x 12 doubles, host) and statistics are copied
+ * to poses_out and stats_out (either may be NULL) and the server forgets the
+ * job, so a later poll of the same id is BA_ERR_INVALID_ARG (as is an
+ * unknown id).  A job whose asynchronous admission failed polls once with
+ * *done = 1 and the failure's status (its message in
+ * ba_server_last_error); the server then forgets it. */
 ba_status ba_server_poll(ba_server* s, uint64_t job_id, int32_t* done, double* poses_out, ba_stats* stats_out);
 /* Cancel a job: a resident job leaves the batch at once (its device memory
  * is released; the other jobs' results do not change), a finished job's
- * unpolled results are dropped.  BA_ERR_INVALID_ARG for an unknown id. */
+ * unpolled results are dropped, a job still being admitted is dropped when
+ * its load returns (at once if the load has not started).
+ * BA_ERR_INVALID_ARG for an unknown id. */
 ba_status ba_server_cancel(ba_server* s, uint64_t job_id);
+/* Asynchronous admission.  Charges the job's estimate plus its load's
+ * transient peak against the budget now (BA_ERR_CAPACITY / BA_ERR_INVALID_ARG
+ * as ba_server_submit) and returns its id at once; a library thread then
+ * creates the job's handle on a CUDA stream of its own, makes that stream
+ * wait for the work already queued on input_stream (a cudaStream_t the
+ * caller produced the inputs on, e.g. a side stream generating them; NULL =
+ * the inputs are ready now), loads the job (validation, layout build,
+ * set-up) and synchronises that stream, while the caller's thread goes on
+ * stepping the resident jobs.  The job joins the batch at the first
+ * ba_server_step after its load finished, and from then on is charged like
+ * a synchronously admitted job.  The inputs described by job (host or device
+ * memory) must stay valid and unchanged until ba_server_job_state leaves
+ * BA_JOB_LOADING.  A failed load is reported by ba_server_poll.  A user
+ * allocator in the configuration is then called from the library thread.
+ * The other ba_server_* calls stay single-threaded: make them from one
+ * thread. */
+enum { BA_JOB_UNKNOWN = -1, BA_JOB_LOADING = 0, BA_JOB_RESIDENT = 1, BA_JOB_FINISHED = 2, BA_JOB_FAILED = 3 };
+ba_status ba_server_submit_async(ba_server* s, const ba_job_desc* job, void* input_stream, uint64_t* job_id);
+/* Where a job is: BA_JOB_LOADING (its inputs are still read), BA_JOB_RESIDENT
+ * (loaded; joined or about to join the batch), BA_JOB_FINISHED (results
+ * waiting for ba_server_poll), BA_JOB_FAILED (admission failed; poll it for
+ * the reason), BA_JOB_UNKNOWN. */
+int32_t ba_server_job_state(ba_server* s, uint64_t job_id);
+/* Jobs submitted asynchronously that have not joined the batch yet. */
+int32_t ba_server_loading(const ba_server* s);
 /* 1 if a job of these sizes would be admitted now, else 0 (lets a caller
  * prepare a job's inputs only when they can be taken). */
 int32_t ba_server_fits(const ba_server* s, int32_t n_scans, int64_t n_voxels, int64_t n_obs);

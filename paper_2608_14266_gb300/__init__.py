@@ -300,6 +300,21 @@ class Batch:
     def kernel_launches(self) -> int:
         return int(_lib.lib().ba_batch_kernel_launches(self.b))
 
+    def profile(self, enable: bool = True):
+        """Per-kernel event timing of later iterations (launched without the graph)."""
+        self._check(_lib.lib().ba_batch_profile_enable(self.b, int(bool(enable))))
+
+    def profile_read(self) -> dict:
+        """{kernel kind: (total ms, launches)} of the event-timed launches."""
+        out = {}
+        for name, kind in _lib.KERNEL_KINDS.items():
+            if name == "decide":
+                continue
+            ms, n = ctypes.c_double(), ctypes.c_int64()
+            self._check(_lib.lib().ba_batch_profile_read(self.b, kind, ctypes.byref(ms), ctypes.byref(n)))
+            out[name] = (ms.value, n.value)
+        return out
+
     def autotune(self, iters_per_trial: int = 2, passes: int = 2, cache: str | None = None) -> dict:
         """ba_batch_autotune: picks the voxel pass's launch settings on the
         batch's own iterations; returns the candidates, timings and choice.

@@ -21,6 +21,7 @@ BA_FP64, BA_MIXED = 0, 1
 BA_HESS_EXACT, BA_HESS_GAUSS_NEWTON = 0, 1
 BA_MEM_HOST, BA_MEM_DEVICE = 0, 1
 BA_AGG_RAW_SUMS, BA_AGG_CENTRED = 0, 1
+BA_JOB_UNKNOWN, BA_JOB_LOADING, BA_JOB_RESIDENT, BA_JOB_FINISHED, BA_JOB_FAILED = -1, 0, 1, 2, 3
 
 _P = ctypes.c_void_p
 _I32 = ctypes.c_int32
@@ -101,6 +102,11 @@ _SIGNATURES = {
     "ba_server_last_error": (ctypes.c_char_p, [_P]),
     "ba_server_destroy": (None, [_P]),
     "ba_server_cancel": (_I32, [_P, ctypes.c_uint64]),
+    "ba_server_submit_async": (_I32, [_P, _P, _P, _P]),
+    "ba_batch_profile_enable": (_I32, [_P, _I32]),
+    "ba_batch_profile_read": (_I32, [_P, _I32, _P, _P]),
+    "ba_server_job_state": (_I32, [_P, ctypes.c_uint64]),
+    "ba_server_loading": (_I32, [_P]),
     "ba_check_bounded_wait": (_I32, [_I32, _I32]),
     "ba_release_cached_memory": (_I32, [_I32]),
     "ba_check_conversions": (_I32, [_I32, _I64, ctypes.c_uint64, _P]),

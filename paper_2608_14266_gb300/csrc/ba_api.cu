@@ -1051,6 +1051,12 @@ struct ba_batch {
   // tuned launch settings of the mixed voxel pass (results do not depend on them)
   int vp_min_blocks = 6;
   int vp_prefetch = 2;
+  // per-kernel timing: while on, iterations are launched directly (no graph)
+  // with an event pair around each kernel launch
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  std::vector<std::pair<int, size_t>> ev_marks;  // (kernel kind, first event)
 };
 
 namespace {
@@ -1197,16 +1203,44 @@ __global__ void batch_status_kernel(JobTable T, int32_t* done) {
   }
 }
 
+// event pair around one launch when profiling (start recorded here, stop at
+// the returned index + 1 after the launch)
+cudaError_t bprof_begin(ba_batch* b, int kind, cudaStream_t stream, size_t* idx) {
+  if (!b->profiling) return cudaSuccess;
+  while (b->ev_pool.size() < b->ev_used + 2) {
+    cudaEvent_t e;
+    cudaError_t err = cudaEventCreate(&e);
+    if (err != cudaSuccess) return err;
+    b->ev_pool.push_back(e);
+  }
+  *idx = b->ev_used;
+  b->ev_used += 2;
+  b->ev_marks.push_back({kind, *idx});
+  return cudaEventRecord(b->ev_pool[*idx], stream);
+}
+
+cudaError_t bprof_end(ba_batch* b, cudaStream_t stream, size_t idx) {
+  if (!b->profiling) return cudaSuccess;
+  return cudaEventRecord(b->ev_pool[idx + 1], stream);
+}
+
 // one iteration of the jobs of group g, on stream
 ba_status launch_group_iteration(ba_batch* b, size_t g, cudaStream_t stream) {
   const JobGroup& G = b->groups[g];
   const int64_t* nb = &b->group_blocks[3 * g];
+  size_t ev = 0;
+  BCK(b, bprof_begin(b, BA_KERNEL_SOLVE, stream, &ev), "event");
   BCK(b, launch_batch_solve(G, nb[2], stream), "batch solve");
+  BCK(b, bprof_end(b, stream, ev), "event");
+  BCK(b, bprof_begin(b, BA_KERNEL_VOXEL_PASS, stream, &ev), "event");
   BCK(b, b->mixed ? launch_batch_voxel_pass_mixed(G, nb[0], 1, stream, b->vp_min_blocks, b->vp_prefetch)
                   : launch_batch_voxel_pass_f64(G, nb[0], 1, stream),
       "batch voxel pass");
+  BCK(b, bprof_end(b, stream, ev), "event");
+  BCK(b, bprof_begin(b, BA_KERNEL_SCAN_PASS, stream, &ev), "event");
   BCK(b, b->mixed ? launch_batch_scan_pass_mixed(G, nb[1], stream) : launch_batch_scan_pass_f64(G, nb[1], stream),
       "batch scan pass");
+  BCK(b, bprof_end(b, stream, ev), "event");
   return BA_OK;
 }
 
@@ -1273,6 +1307,15 @@ ba_status prepare_graph(ba_batch* b, int n) {
 }
 
 ba_status run_iterations(ba_batch* b, int n) {
+  if (b->profiling) {  // direct launches, groups one after another on the batch's stream
+    for (int k = 0; k < n; ++k)
+      for (size_t grp = 0; grp < b->groups.size(); ++grp) {
+        ba_status s = launch_group_iteration(b, grp, b->stream);
+        if (s != BA_OK) return s;
+      }
+    b->launches += 3 * (int64_t)n * (int64_t)b->groups.size();
+    return BA_OK;
+  }
   ba_status s = prepare_graph(b, n);
   if (s != BA_OK) return s;
   BCK(b, cudaGraphLaunch(b->graph, b->stream), "graph launch");
@@ -1508,6 +1551,39 @@ ba_status ba_batch_autotune(ba_batch* b, int32_t iters_per_trial, int32_t passes
   return BA_OK;
 }
 
+ba_status ba_batch_profile_enable(ba_batch* b, int32_t enable) {
+  if (!b) return BA_ERR_INVALID_ARG;
+  if (b->device >= 0) {
+    DeviceGuard g(b->device);
+    BCK(b, cudaStreamSynchronize(b->stream), "synchronize");
+  }
+  b->profiling = enable != 0;
+  b->ev_used = 0;
+  b->ev_marks.clear();
+  return BA_OK;
+}
+
+ba_status ba_batch_profile_read(ba_batch* b, int32_t kind, double* total_ms, int64_t* launches) {
+  if (!b) return BA_ERR_INVALID_ARG;
+  if (!total_ms || !launches) return bfail(b, BA_ERR_INVALID_ARG, "NULL output");
+  double tot = 0.0;
+  int64_t n = 0;
+  if (!b->ev_marks.empty()) {
+    DeviceGuard g(b->device);
+    BCK(b, cudaStreamSynchronize(b->stream), "synchronize");
+    for (auto& m : b->ev_marks) {
+      if (m.first != kind) continue;
+      float ms = 0.0f;
+      BCK(b, cudaEventElapsedTime(&ms, b->ev_pool[m.second], b->ev_pool[m.second + 1]), "event time");
+      tot += ms;
+      ++n;
+    }
+  }
+  *total_ms = tot;
+  *launches = n;
+  return BA_OK;
+}
+
 ba_status ba_batch_set_launch(ba_batch* b, int32_t min_blocks, int32_t prefetch) {
   if (!b) return BA_ERR_INVALID_ARG;
   if ((min_blocks != 4 && min_blocks != 6 && min_blocks != 8) || prefetch < 0 || prefetch > 16)
@@ -1531,6 +1607,7 @@ void ba_batch_destroy(ba_batch* b) {
   cudaFree(b->d_done);
   for (auto st : b->branch) cudaStreamDestroy(st);
   for (auto ev : b->branch_ev) cudaEventDestroy(ev);
+  for (auto ev : b->ev_pool) cudaEventDestroy(ev);
   if (b->own_stream) cudaStreamDestroy(b->stream);
   delete b;
 }

@@ -14,6 +14,14 @@ its steps.
 This module only marshals: it keeps the arrival queue (jobs the library
 answered "does not fit now"), prepares a job's inputs when the library says
 it fits, and collects finished jobs.  All arithmetic runs in the library.
+
+With async_admission=True a job that fits is handed to the library's loader
+thread (ba_server_submit_async): its inputs may still be in production on
+`input_stream` (e.g. generated there by GPU kernels) when it is submitted,
+and its load and set-up run on a stream of their own while this thread keeps
+stepping the resident jobs; the job joins them at the first step after its
+load finished.  The inputs are kept alive until the library no longer reads
+them.
 """
 from __future__ import annotations
 
@@ -46,6 +54,7 @@ class Job:
     stats: dict | None = None
     error: str | None = None  # set when the job failed (its inputs, or the library refused them)
     server_id: int = field(default=0, repr=False)
+    keep: object = field(default=None, repr=False)  # inputs held while the library loads them
 
     @property
     def latency(self) -> float | None:
@@ -57,11 +66,17 @@ class Server:
     iterations per step.  Remaining keyword arguments configure every job's
     handle (precision, rel_tol, max_iters, cuda_stream, ...)."""
 
-    def __init__(self, mem_budget: int, chunk: int = 4, clock=time.perf_counter, **cfg):
+    def __init__(self, mem_budget: int, chunk: int = 4, clock=time.perf_counter, async_admission: bool = False,
+                 input_stream=None, **cfg):
         cfg.setdefault("precision", BA_MIXED)
         self.cfg = ba_config_default(**cfg)
         self.chunk = int(chunk)
         self.clock = clock
+        self.async_admission = bool(async_admission)
+        self.input_stream = None if input_stream is None else (
+            input_stream if isinstance(input_stream, int) else input_stream.cuda_stream)
+        self.loading: list[Job] = []
+        self.dropping: list[Job] = []  # cancelled while loading; inputs held until the load returns
         self.s = ctypes.c_void_p()
         status = _lib.lib().ba_server_create(ctypes.byref(self.cfg), int(mem_budget), ctypes.byref(self.s))
         if status != _lib.BA_OK:
@@ -86,7 +101,7 @@ class Server:
         while self.queue:
             job = self.queue[0]
             if not L.ba_server_fits(self.s, job.n_scans, job.n_voxels, job.n_obs):
-                if self.resident:
+                if self.resident or self.loading:
                     break
                 # nothing resident and still no room: the library reports why (too large for the budget)
                 self.queue.popleft()
@@ -100,7 +115,11 @@ class Server:
                 desc = BaJobDesc(job.n_scans, job.n_voxels, job.n_obs, a[0].ptr, a[1].ptr, a[2].ptr,
                                  BA_AGG_CENTRED, a[3].ptr, _mem_kind(*a))
                 jid = ctypes.c_uint64()
-                self._check(L.ba_server_submit(self.s, ctypes.byref(desc), ctypes.byref(jid)))
+                if self.async_admission:
+                    self._check(L.ba_server_submit_async(self.s, ctypes.byref(desc), self.input_stream,
+                                                         ctypes.byref(jid)))
+                else:
+                    self._check(L.ba_server_submit(self.s, ctypes.byref(desc), ctypes.byref(jid)))
             except Exception as exc:  # a failed job is reported, the stream goes on
                 job.error = f"{type(exc).__name__}: {exc}"
                 job.finished = self.clock()
@@ -108,19 +127,48 @@ class Server:
                 continue
             job.server_id = jid.value
             job.admitted = self.clock()
-            self.resident.append(job)
+            if self.async_admission:
+                job.keep = a
+                self.loading.append(job)
+            else:
+                self.resident.append(job)
             n += 1
         return n
+
+    def _settle_loading(self) -> None:
+        """Jobs whose asynchronous load has returned: resident, or failed."""
+        L = _lib.lib()
+        for job in list(self.loading):
+            state = L.ba_server_job_state(self.s, job.server_id)
+            if state == _lib.BA_JOB_LOADING:
+                continue
+            job.keep = None
+            self.loading.remove(job)
+            if state == _lib.BA_JOB_FAILED:
+                done = ctypes.c_int32()
+                status = L.ba_server_poll(self.s, job.server_id, ctypes.byref(done), None, None)
+                job.error = f"BAError: {_lib.STATUS_NAMES.get(status, status)}: " + \
+                    (L.ba_server_last_error(self.s) or b"").decode()
+                job.finished = self.clock()
+                self.failed.append(job)
+            else:
+                self.resident.append(job)
 
     # -- stepping -----------------------------------------------------------
     def step(self) -> list[Job]:
         """Admit what fits, run one step, collect retired jobs; returns them."""
         self._admit()
-        if not self.resident:
+        if not self.resident and not self.loading and not self.dropping:
             return []
         L = _lib.lib()
         n_res, n_ret = ctypes.c_int32(), ctypes.c_int32()
         self._check(L.ba_server_step(self.s, self.chunk, ctypes.byref(n_res), ctypes.byref(n_ret)))
+        if self.loading:
+            self._settle_loading()
+        for job in list(self.dropping):
+            if L.ba_server_job_state(self.s, job.server_id) != _lib.BA_JOB_LOADING:
+                job.keep = None
+                self.dropping.remove(job)
         out = []
         if n_ret.value:
             now = self.clock()
@@ -146,6 +194,12 @@ class Server:
         elif job in self.resident:
             self._check(_lib.lib().ba_server_cancel(self.s, job.server_id))
             self.resident.remove(job)
+        elif job in self.loading:
+            self._check(_lib.lib().ba_server_cancel(self.s, job.server_id))
+            self.loading.remove(job)
+            # the loader thread may be reading its inputs right now: keep them
+            # until the library has let go of the job
+            self.dropping.append(job)
         else:
             raise ValueError(f"job {job.job_id} is neither queued nor resident")
         job.error = "cancelled"
@@ -158,7 +212,7 @@ class Server:
 
     @property
     def idle(self) -> bool:
-        return not self.queue and not self.resident
+        return not self.queue and not self.resident and not self.loading and not self.dropping
 
     def kernel_launches(self) -> int:
         return int(_lib.lib().ba_server_kernel_launches(self.s))
@@ -168,6 +222,9 @@ class Server:
             _lib.lib().ba_server_destroy(self.s)
             self.s = None
             self.resident = []
+            for job in self.loading + self.dropping:  # the loader thread has stopped
+                job.keep = None
+            self.loading, self.dropping = [], []
 
     def __enter__(self):
         return self

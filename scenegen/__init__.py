@@ -56,7 +56,8 @@ def build(force: bool = False) -> str:
 def build_gpu(force: bool = False) -> str:
     """Compile the CUDA point generator (sm_103a) beside its source."""
     import shutil
-    stale = (not os.path.exists(_GPU_LIB)) or os.path.getmtime(_GPU_SRC) > os.path.getmtime(_GPU_LIB)
+    stale = (not os.path.exists(_GPU_LIB)) or any(
+        os.path.getmtime(src) > os.path.getmtime(_GPU_LIB) for src in (_GPU_SRC, _HDR))
     if force or stale:
         nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
         tmp = _GPU_LIB + f".tmp{os.getpid()}"
@@ -74,6 +75,10 @@ def _load_gpu():
             lib.sgd_points.restype = ctypes.c_int
             lib.sgd_points.argtypes = [ctypes.c_uint64, ctypes.c_int32, ctypes.c_double] + [ctypes.c_void_p] * 5 + \
                 [ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]
+            lib.sgd_points_fast.restype = ctypes.c_int
+            lib.sgd_points_fast.argtypes = lib.sgd_points.argtypes
+            lib.sgd_job.restype = ctypes.c_int
+            lib.sgd_job.argtypes = [ctypes.c_void_p] * 10
             _gpu_lib = lib
     return _gpu_lib
 
@@ -112,6 +117,8 @@ def _load():
             lib.sg_n_points.restype = ctypes.c_int64
             lib.sg_n_points.argtypes = [ctypes.c_void_p]
             lib.sg_copy.argtypes = [ctypes.c_void_p] + [ctypes.c_void_p] * 6
+            lib.sg_voxel_offsets.restype = ctypes.c_int64
+            lib.sg_voxel_offsets.argtypes = [ctypes.POINTER(_Params), ctypes.c_void_p]
             lib.sg_points.restype = ctypes.c_int
             lib.sg_points.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p,
                                       ctypes.c_int]
@@ -236,14 +243,114 @@ class Scene:
             pass
 
 
+def _cparams(p: SceneParams) -> _Params:
+    return _Params(seed=p.seed, n_scans=p.n_scans, pts_per_obs=p.pts_per_obs, n_voxels=p.n_voxels,
+                   obs_min=p.obs_min, obs_max=p.obs_max, box=(ctypes.c_double * 3)(*p.box),
+                   side_min=p.side_min, side_max=p.side_max, noise_sigma=p.noise_sigma,
+                   rot_sigma_deg=p.rot_sigma_deg, trans_sigma=p.trans_sigma,
+                   degenerate_frac=p.degenerate_frac, view_radius=p.view_radius,
+                   perturb_scan0=int(p.perturb_scan0), reserved=0)
+
+
+def voxel_offsets(p: SceneParams, out: np.ndarray | None = None) -> np.ndarray:
+    """Voxel-major observation offsets of the scene p describes (n_voxels + 1
+    int64), from the count stream alone; scenes without a view radius only."""
+    if out is None:
+        out = np.empty(p.n_voxels + 1, dtype=np.int64)
+    assert out.dtype == np.int64 and out.flags.c_contiguous and out.shape == (p.n_voxels + 1,)
+    n = _load().sg_voxel_offsets(ctypes.byref(_cparams(p)), out.ctypes.data)
+    if n < 0:
+        raise ValueError("voxel_offsets needs a scene without a view radius")
+    return out
+
+
+@dataclass
+class DeviceScene:
+    """A scene without a view radius generated on the GPU (sgd_job): the same
+    structure, poses and patches as make_scene(params), as CUDA tensors.
+    Everything is queued on the stream given to make_scene_device and is
+    ready once that stream reaches it."""
+    params: SceneParams
+    n_obs: int
+    voxel_off: object   # (n_voxels + 1,) int64
+    obs_scan: object    # (n_obs,) int32
+    obs_voxel: object   # (n_obs,) int32
+    pose_gt: object     # (n_scans, 12) float64
+    pose_init: object   # (n_scans, 12) float64
+    plane: object       # (n_voxels, 12)
+    extent: object      # (n_voxels, 2)
+    bad: object         # (1,) int32: 1 if the generator met an offset it could not take
+    host_off: np.ndarray = field(default=None, repr=False)  # pinned source of voxel_off
+
+    @property
+    def n_scans(self) -> int:
+        return self.params.n_scans
+
+    @property
+    def n_voxels(self) -> int:
+        return self.params.n_voxels
+
+    def _points(self, fn, obs_begin, obs_end, out, stream):
+        import torch
+        n = (obs_end - obs_begin) * self.params.pts_per_obs
+        assert out.dtype == torch.float64 and out.is_contiguous() and tuple(out.shape) == (n, 3)
+        s = (stream if stream is not None else torch.cuda.current_stream()).cuda_stream
+        rc = fn(self.params.seed, self.params.pts_per_obs, self.params.noise_sigma, self.plane.data_ptr(),
+                self.extent.data_ptr(), self.pose_gt.data_ptr(), self.obs_scan.data_ptr(), self.obs_voxel.data_ptr(),
+                obs_begin, obs_end, out.data_ptr(), s)
+        if rc != 0:
+            raise RuntimeError(f"scenegen GPU point generation failed (CUDA error {rc})")
+        return out
+
+    def points(self, obs_begin, obs_end, out, stream=None):
+        """FP64 points, as Scene.points_device (equal to the host's up to the
+        last bits of the math library)."""
+        return self._points(_load_gpu().sgd_points, obs_begin, obs_end, out, stream)
+
+    def points_fast(self, obs_begin, obs_end, out, stream=None):
+        """Points drawn in FP32 from the same per-observation counters (a few
+        micrometres from the FP64 points; see scenegen_gpu.cu)."""
+        return self._points(_load_gpu().sgd_points_fast, obs_begin, obs_end, out, stream)
+
+
+def pinned_voxel_offsets(p: SceneParams):
+    """voxel_offsets(p) into pinned host memory (a CPU int64 tensor), ready
+    for an asynchronous copy; safe to call from worker threads."""
+    import torch
+    host_off = torch.empty(p.n_voxels + 1, dtype=torch.int64).pin_memory()
+    voxel_offsets(p, host_off.numpy())
+    return host_off
+
+
+def make_scene_device(p: SceneParams, device=None, stream=None, offsets=None) -> DeviceScene:
+    """Generate the scene p on the GPU (no view radius; obs_max <= 64).  The
+    offsets come from the host's count stream (cheap; pass them precomputed
+    by pinned_voxel_offsets as `offsets`), everything else from device
+    kernels queued on `stream` (default: the current stream)."""
+    import torch
+    dev = torch.device("cuda") if device is None else torch.device(device)
+    st = stream if stream is not None else torch.cuda.current_stream(dev)
+    host_off = offsets if offsets is not None else pinned_voxel_offsets(p)
+    n_obs = int(host_off[-1])
+    with torch.cuda.stream(st):
+        e = lambda *shape, dt=torch.float64: torch.empty(shape, dtype=dt, device=dev)
+        voxel_off = host_off.to(dev, non_blocking=True)
+        sc = DeviceScene(p, n_obs, voxel_off, e(max(n_obs, 1), dt=torch.int32)[:n_obs],
+                         e(max(n_obs, 1), dt=torch.int32)[:n_obs], e(p.n_scans, 12), e(p.n_scans, 12),
+                         e(max(p.n_voxels, 1), 12)[: p.n_voxels], e(max(p.n_voxels, 1), 2)[: p.n_voxels],
+                         torch.zeros(1, dtype=torch.int32, device=dev), host_off=host_off)
+    cp = _cparams(p)
+    rc = _load_gpu().sgd_job(ctypes.byref(cp), sc.voxel_off.data_ptr(), sc.pose_gt.data_ptr(),
+                             sc.pose_init.data_ptr(), sc.plane.data_ptr(), sc.extent.data_ptr(),
+                             sc.obs_scan.data_ptr(), sc.obs_voxel.data_ptr(), sc.bad.data_ptr(), st.cuda_stream)
+    if rc != 0:
+        raise RuntimeError(f"scenegen GPU job generation failed ({rc})")
+    return sc
+
+
 def make_scene(p: SceneParams) -> Scene:
     lib = _load()
-    cp = _Params(seed=p.seed, n_scans=p.n_scans, pts_per_obs=p.pts_per_obs, n_voxels=p.n_voxels,
-                 obs_min=p.obs_min, obs_max=p.obs_max, box=(ctypes.c_double * 3)(*p.box),
-                 side_min=p.side_min, side_max=p.side_max, noise_sigma=p.noise_sigma,
-                 rot_sigma_deg=p.rot_sigma_deg, trans_sigma=p.trans_sigma,
-                 degenerate_frac=p.degenerate_frac, view_radius=p.view_radius,
-                 perturb_scan0=int(p.perturb_scan0), reserved=0)
+    cp = _cparams(p)
     h = lib.sg_create(ctypes.byref(cp))
     if not h:
         raise ValueError(f"invalid scene parameters {p}")

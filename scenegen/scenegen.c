@@ -338,6 +338,22 @@ sg_scene* sg_create(const sg_params* params) {
   return s;
 }
 
+int64_t sg_voxel_offsets(const sg_params* p, int64_t* voxel_off) {
+  if (!p || !voxel_off || p->n_scans < 1 || p->n_voxels < 0 || p->obs_min < 1 || p->obs_max < p->obs_min ||
+      p->view_radius > 0.0)
+    return -1;
+  int64_t n = 0;
+  voxel_off[0] = 0;
+  for (int64_t i = 0; i < p->n_voxels; ++i) {
+    rng_t rc = rng_make(p->seed, ST_OBS_COUNT, (uint64_t)i);
+    int64_t k = rng_int(&rc, p->obs_min, p->obs_max);
+    if (k > p->n_scans) k = p->n_scans;
+    n += k;
+    voxel_off[i + 1] = n;
+  }
+  return n;
+}
+
 void sg_destroy(sg_scene* s) {
   if (!s) return;
   free(s->pose_gt);

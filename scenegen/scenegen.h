@@ -61,6 +61,13 @@ void sg_copy(const sg_scene* s, double* pose_gt, double* pose_init, double* plan
  * each, written as xyz triples to out.  Returns 0, or -1 on a bad range. */
 int sg_points(const sg_scene* s, int64_t obs_begin, int64_t obs_end, double* out, int nthreads);
 
+/* Voxel-major observation offsets (n_voxels + 1) of the scene p describes,
+ * from the observation-count stream alone, without building the scene.  Only
+ * for scenes without a view radius, where a voxel's count does not depend on
+ * the scans near it.  Returns n_obs, or -1 for bad parameters or a scene with
+ * a view radius. */
+int64_t sg_voxel_offsets(const sg_params* p, int64_t* voxel_off);
+
 #ifdef __cplusplus
 }
 #endif

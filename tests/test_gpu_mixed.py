@@ -269,3 +269,56 @@ def test_voxel_input_order_changes_only_rounding(mm, precision):
         r, t = pose_errors(a.poses(), b.poses())
         assert r < rot_tol and t < tr_tol
         assert b.cost() == pytest.approx(a.cost(), rel=cost_tol)
+
+
+def _city_slice(scale_side=447.0, n_scans=500, n_voxels=25000):
+    """A 0.05-scale city scene: 500 scans, 25,000 voxels on a 447 m slab (the
+    full city's density), patch sides 0.5-4 m, 5% strips whose second in-plane
+    variance is 2-10 times the noise variance, scans within 200 m (levers up to
+    200 m)."""
+    p = scenegen.config("city", n_scans=n_scans, n_voxels=n_voxels, box=(scale_side, scale_side, 50.0))
+    s = scenegen.make_scene(p)
+    cen = oracle.points_to_centred(s.point_offsets(), s.points())
+    strip = s.extent[:, 1] != s.extent[:, 0]
+    return s, cen, strip
+
+
+def test_mixed_city_strips_against_oracle(mm):
+    """The mixed path against the FP64 oracle where FP32 is hardest: near-
+    degenerate strip voxels and 200 m levers.  Per voxel, lambda_min of the
+    strips and of the other voxels separately; the cost; g and H; then single
+    iterations from the oracle's state."""
+    s, cen, strip = _city_slice()
+    assert 0.03 < strip.mean() < 0.07
+    prob = oracle.ObsProblem(s.n_scans, s.voxel_off, s.obs_scan, cen)
+    lm = oracle.LM(prob, s.pose_init)
+    _, planes = oracle.voxel_pass(prob, s.pose_init)
+    with _mixed(mm) as ba:
+        ba.load_observations(s.n_scans, s.voxel_off, s.obs_scan, cen, s.pose_init)
+        pl = ba.planes()
+        rel = np.abs(pl[:, 0] - planes[:, 0]) / planes[:, 0]
+        print(f"\nlambda_min relative error: strips max {rel[strip].max():.2e} p99 "
+              f"{np.percentile(rel[strip], 99):.2e}; others max {rel[~strip].max():.2e} p99 "
+              f"{np.percentile(rel[~strip], 99):.2e}")
+        assert rel[strip].max() < 5e-6 and rel[~strip].max() < 5e-6
+        # the normal of a strip is fixed up to its eigengap: compare directions
+        # where lambda1 is well separated from lambda0
+        sep = (planes[:, 1] - planes[:, 0]) / planes[:, 2] > 1e-3
+        dots = np.abs(np.sum(pl[sep, 3:6] * planes[sep, 3:6], axis=1))
+        assert np.all(1.0 - dots < 1e-6)
+        assert ba.cost() == pytest.approx(lm.cost, rel=COST_TOL)
+        g, H = ba.gradient()
+        np.testing.assert_allclose(g, lm.g, rtol=0, atol=1e-5 * np.abs(lm.g).max())
+        for j in range(s.n_scans):
+            np.testing.assert_allclose(H[j], lm.H[j], rtol=0, atol=1e-5 * np.abs(lm.H[j]).max())
+        for k in range(4):
+            c_prev = lm.cost
+            ba.set_state(lm.poses, lm.mu, lm.nu)
+            assert ba.cost() == pytest.approx(lm.cost, rel=COST_TOL), k
+            st = ba.iterate(1)
+            acc = lm.step()
+            if bool(st["last_accepted"]) != acc:
+                assert abs(lm.st.last_trial_cost - c_prev) <= COST_TOL * c_prev, k
+                continue
+            r, t = pose_errors(ba.poses(), lm.poses)
+            assert r < ROT_TOL and t < TRANS_TOL, (k, r, t)

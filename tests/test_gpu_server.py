@@ -188,3 +188,110 @@ def test_served_failures_and_cancellation_leave_others_unchanged(mm):
             poses, cost, iters = alone[job.job_id]
             np.testing.assert_array_equal(job.poses, poses)
             assert job.stats["cost"] == cost and job.stats["iters"] == iters
+
+
+def _device_inputs(torch, side, s, agg):
+    """A job's inputs produced on a side stream (copies queued there), as a
+    generator feeding the server would produce them."""
+    with torch.cuda.stream(side):
+        T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().to("cuda", non_blocking=True)
+        return T(s.voxel_off), T(s.obs_scan), T(agg), T(s.pose_init)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_async_admission_equals_alone(mm, precision):
+    """Jobs admitted by the library's loader thread, their inputs still being
+    produced on a side stream when they are submitted, end with exactly the
+    bits they reach solved alone; at most two fit the budget at once."""
+    import torch
+    from paper_2608_14266_gb300.server import Job, Server
+    prec = mm.BA_MIXED if precision == "mixed" else mm.BA_FP64
+    scenes = _scenes(6)
+    chunk = 3
+    cen = [library_clusters(mm, s, po, pts) for s, po, pts in scenes]
+    alone = []
+    for (s, po, pts), agg in zip(scenes, cen):
+        ba = mm.BundleAdjuster(precision=prec, **CFG)
+        ba.load_observations(s.n_scans, s.voxel_off, s.obs_scan, agg, s.pose_init)
+        with mm.Batch() as b:
+            b.add(ba)
+            b.solve(chunk=chunk)
+        alone.append((ba.poses(), ba.cost(), ba.stats()["iters"]))
+        ba.close()
+    est = [sum(mm.ba_estimate_bytes(prec, s.n_scans, s.n_voxels, s.n_obs)) for s, _, _ in scenes]
+    budget = sum(sorted(est)[-2:])
+    side = torch.cuda.Stream()
+    srv = Server(budget, chunk=chunk, precision=prec, async_admission=True, input_stream=side, **CFG)
+    order = [3, 0, 5, 1, 4, 2]
+    submitted, max_used, saw_loading = 0, 0, False
+    while submitted < len(order) or not srv.idle:
+        if submitted < len(order):
+            k = order[submitted]
+            s = scenes[k][0]
+            srv.submit(Job(job_id=k, n_scans=s.n_scans, n_voxels=s.n_voxels, n_obs=s.n_obs,
+                           inputs=lambda s=s, agg=cen[k]: _device_inputs(torch, side, s, agg)))
+            submitted += 1
+        srv._admit()
+        saw_loading = saw_loading or bool(srv.loading)
+        srv.step()
+        max_used = max(max_used, srv.used)
+        assert srv.used <= budget
+    srv.close()
+    assert saw_loading and len(srv.finished) == len(scenes) and not srv.failed
+    for job in srv.finished:
+        poses, cost, iters = alone[job.job_id]
+        np.testing.assert_array_equal(job.poses, poses)
+        assert job.stats["cost"] == cost
+        assert job.stats["iters"] == iters
+
+
+def test_async_admission_failures_and_cancellation(mm):
+    """On the asynchronous path: a job whose clusters the load's validation
+    refuses is reported with the library's message, a job cancelled while
+    being admitted never runs, and the others end with their solo bits; the
+    budget returns to zero."""
+    import ctypes
+    import torch
+    from paper_2608_14266_gb300 import _lib
+    from paper_2608_14266_gb300.server import Job, Server
+    prec = mm.BA_MIXED
+    scenes = _scenes(4)
+    chunk = 3
+    cen = [library_clusters(mm, s, po, pts) for s, po, pts in scenes]
+    alone = {}
+    for k in (0, 2):
+        s = scenes[k][0]
+        ba = mm.BundleAdjuster(precision=prec, **CFG)
+        ba.load_observations(s.n_scans, s.voxel_off, s.obs_scan, cen[k], s.pose_init)
+        with mm.Batch() as b:
+            b.add(ba)
+            b.solve(chunk=chunk)
+        alone[k] = (ba.poses(), ba.cost(), ba.stats()["iters"])
+        ba.close()
+    bad = cen[1].copy()
+    bad[3, 2] = np.inf
+    side = torch.cuda.Stream()
+    agg = {0: cen[0], 1: bad, 2: cen[2], 3: cen[3]}
+    jobs = {k: Job(k, scenes[k][0].n_scans, scenes[k][0].n_voxels, scenes[k][0].n_obs,
+                   inputs=lambda k=k: _device_inputs(torch, side, scenes[k][0], agg[k])) for k in range(4)}
+    with Server(1 << 34, chunk=chunk, precision=prec, async_admission=True, input_stream=side, **CFG) as srv:
+        for k in range(4):
+            srv.submit(jobs[k])
+        srv._admit()
+        assert len(srv.loading) == 4
+        srv.cancel(jobs[3])  # pending or being loaded: dropped either way
+        assert jobs[3].error == "cancelled"
+        state = _lib.lib().ba_server_job_state(srv.s, jobs[3].server_id)
+        assert state in (_lib.BA_JOB_UNKNOWN, _lib.BA_JOB_LOADING)
+        while not srv.idle:
+            srv.step()
+        assert srv.used == 0 and _lib.lib().ba_server_loading(srv.s) == 0
+        assert {j.job_id for j in srv.finished} == {0, 2}
+        assert {j.job_id for j in srv.failed} == {1, 3}
+        assert "BA_ERR_INVALID_ARG" in jobs[1].error and "finite" in jobs[1].error
+        done = ctypes.c_int32()
+        assert _lib.lib().ba_server_poll(srv.s, jobs[1].server_id, ctypes.byref(done), None, None) == 1
+        for job in srv.finished:
+            poses, cost, iters = alone[job.job_id]
+            np.testing.assert_array_equal(job.poses, poses)
+            assert job.stats["cost"] == cost and job.stats["iters"] == iters
