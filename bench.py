@@ -637,11 +637,15 @@ class JobFactory:
             self.buf = torch.empty((chunk_obs * pts_per_obs, 3), dtype=torch.float64, device="cuda")
             self.po = torch.arange(chunk_obs + 1, dtype=torch.int64, device="cuda") * pts_per_obs
 
+    host_s = {"structure": 0.0, "clusters": 0.0}  # host time spent queueing the work
+
     def make(self, params, offsets=None):
         import scenegen
         assert params.pts_per_obs == self.npo
         torch = self.torch
+        t0 = time.perf_counter()
         sc = scenegen.make_scene_device(params, stream=self.stream, offsets=offsets)
+        t1 = time.perf_counter()
         with torch.cuda.stream(self.stream):
             agg = torch.empty((max(sc.n_obs, 1), 10), dtype=torch.float64, device="cuda")[: sc.n_obs]
         for o0 in range(0, sc.n_obs, self.chunk):
@@ -649,6 +653,8 @@ class JobFactory:
             pts = self.buf[: (o1 - o0) * self.npo]
             sc.points_fast(o0, o1, pts, stream=self.stream)
             self.mm.ba_aggregate_points(self.po[: o1 - o0 + 1], pts, agg[o0:o1], stream=self.stream)
+        self.host_s = {"structure": self.host_s["structure"] + (t1 - t0),
+                       "clusters": self.host_s["clusters"] + (time.perf_counter() - t1)}
         return sc, agg
 
 
@@ -901,6 +907,15 @@ def served_result(args, mm, torch, scenegen, oracle_mod=None):
             return _dev_inputs(sc, agg)
 
         k = 0
+        prof = {"steps": 0, "step_s": 0.0, "admit_s": 0.0, "resident_sum": 0, "loading_sum": 0}
+        srv_admit = srv._admit
+
+        def timed_admit():
+            t0 = time.perf_counter()
+            n = srv_admit()
+            prof["admit_s"] += time.perf_counter() - t0
+            return n
+        srv._admit = timed_admit
         while k < m or not srv.idle:
             while nxt < m and nxt < k + 64:  # the offsets (count stream, host) of the next arrivals
                 ahead.append(pool.submit(scenegen.pinned_voxel_offsets, params[nxt]))
@@ -918,18 +933,28 @@ def served_result(args, mm, torch, scenegen, oracle_mod=None):
             if srv.idle:
                 time.sleep(max(0.0, min(order_arrivals[k] - now, 0.01)) if k < m else 0.0)
                 continue
+            t0 = time.perf_counter()
             srv.step()
+            prof["step_s"] += time.perf_counter() - t0
+            prof["steps"] += 1
+            prof["resident_sum"] += len(srv.resident)
+            prof["loading_sum"] += len(srv.loading)
         t_end = clk()
-        out = (srv.finished, srv.failed, t_end, srv.kernel_launches())
+        n_st = max(1, prof["steps"])
+        host = {"steps": prof["steps"], "step_s": prof["step_s"], "admission_s": prof["admit_s"],
+                "generation_queue_s": dict(fac.host_s),
+                "mean_resident": prof["resident_sum"] / n_st, "mean_loading": prof["loading_sum"] / n_st}
+        fac.host_s = {"structure": 0.0, "clusters": 0.0}
+        out = (srv.finished, srv.failed, t_end, srv.kernel_launches(), host)
         srv.close()
         torch.cuda.synchronize()
         return out + (gt_host,)
 
     budget = args.budget_gb * (1 << 30)
-    jobs_m, failed_m, t_m, launches_m, gt_host = serve(arrivals, budget, True)
+    jobs_m, failed_m, t_m, launches_m, host_m, gt_host = serve(arrivals, budget, True)
     # capacity: a burst of the first jobs all arriving at once
     n_burst = min(n_jobs, args.burst_jobs)
-    jobs_b, failed_b, t_b, _, _ = serve(np.zeros(n_burst), budget, False)
+    jobs_b, failed_b, t_b, _, host_b, _ = serve(np.zeros(n_burst), budget, False)
     pool.shutdown()
     torch.cuda.empty_cache()
     # plain FP64, one job at a time, on the first n_sample arrivals of the same stream
@@ -979,7 +1004,8 @@ def served_result(args, mm, torch, scenegen, oracle_mod=None):
         if adm.size else None,
         "iterations_per_job": {"mean": float(iters.mean()), "max": int(iters.max())} if iters.size else None,
         "capacity_burst": {"value": len(jobs_b) / t_b, "unit": "jobs/s", "jobs": n_burst, "seconds": t_b,
-                           "failed": len(failed_b), "latency": latency_summary(jobs_b)},
+                           "failed": len(failed_b), "latency": latency_summary(jobs_b), "host": host_b},
+        "host": host_m,
         "gpu_launches": launches_m,
         "fp64_per_job": None if n_sample == 0 else {
             "value": fp64_value, "unit": "jobs/s", "jobs": n_sample, "seconds": t64,

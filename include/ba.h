@@ -204,6 +204,44 @@ ba_status ba_planes(ba_handle* h, double* out, int32_t mem_kind);
  * BA_HESS_GAUSS_NEWTON).  Either output may be NULL. */
 ba_status ba_gradient(ba_handle* h, double* g, double* H, int32_t mem_kind);
 
+/* ---- Voxel-sharded solve -------------------------------------------------
+ * One problem's voxels split over several handles (e.g. one per GPU, each
+ * holding whole voxels with all their observations and every scan's pose):
+ * the cost (Eq. 1) and the surrogate's g and H (Eq. 3) are sums over voxels,
+ * so each shard computes its part and the parts are added (an all-reduce of
+ * n_scans x 27 values and a scalar per exchange); every shard then runs the
+ * same deterministic per-scan solves and LM decision on the totals, and the
+ * shards' poses stay bit-identical.  One iteration, on every shard:
+ *   ba_shard_partials -> sum over shards -> ba_shard_set_totals
+ *   ba_shard_trial    -> sum of the trial costs over shards -> ba_shard_decide
+ * ba_shard_decide computes, on acceptance, the shard's g and H at the new
+ * poses: read them with ba_shard_partials (their cost partial is then the
+ * accepted trial cost's share; install the summed trial cost as the total).
+ * After a load or ba_set_state exchange the partials again before a trial.
+ *
+ * ba_shard_partials: the handle's g, H (n_scans x 27 doubles: g (6), then
+ * H's upper triangle row by row (21); world frame, rotation first) and cost
+ * over its own voxels at the current poses, to host (synchronises) or device
+ * memory (stream-ordered); either pointer may be NULL.  Call it before
+ * ba_shard_set_totals, which overwrites them. */
+ba_status ba_shard_partials(ba_handle* h, double* gH, double* cost, int32_t mem_kind);
+/* Install the totals over all shards (gH_total in the layout above, host or
+ * device; cost_total >= 0) as this handle's g, H and current cost.  From now
+ * on a scan counts as unobserved only if its total Hessian diagonal is zero.
+ * Synchronises. */
+ba_status ba_shard_set_totals(ba_handle* h, const double* gH_total, double cost_total, int32_t mem_kind);
+/* Per-scan damped solves from the totals and retraction (Algorithm 2,
+ * Solver), then the trial voxel pass over this shard's voxels (CalRes);
+ * *trial_cost receives this shard's part of the trial cost.  No decision.
+ * Synchronises. */
+ba_status ba_shard_trial(ba_handle* h, double* trial_cost);
+/* The LM decision (gain ratio, Nielsen's update; as ba_iterate) with the
+ * trial cost summed over every shard; on acceptance the trial poses become
+ * current and the shard's g, H are computed there (CalJH).  *accepted (may be
+ * NULL) receives the decision.  BA_ERR_NUMERIC if the cost is not finite.
+ * Synchronises. */
+ba_status ba_shard_decide(ba_handle* h, double trial_cost_total, int32_t* accepted);
+
 /* Number of kernel launches the handle has issued since creation. */
 int64_t ba_kernel_launches(const ba_handle* h);
 
@@ -377,7 +415,7 @@ ba_status ba_server_poll(ba_server* s, uint64_t job_id, int32_t* done, double* p
 ba_status ba_server_cancel(ba_server* s, uint64_t job_id);
 /* Asynchronous admission.  Charges the job's estimate plus its load's
  * transient peak against the budget now (BA_ERR_CAPACITY / BA_ERR_INVALID_ARG
- * as ba_server_submit) and returns its id at once; a library thread then
+ * as ba_server_submit) and returns its id at once; a library loader thread then
  * creates the job's handle on a CUDA stream of its own, makes that stream
  * wait for the work already queued on input_stream (a cudaStream_t the
  * caller produced the inputs on, e.g. a side stream generating them; NULL =
@@ -388,7 +426,7 @@ ba_status ba_server_cancel(ba_server* s, uint64_t job_id);
  * a synchronously admitted job.  The inputs described by job (host or device
  * memory) must stay valid and unchanged until ba_server_job_state leaves
  * BA_JOB_LOADING.  A failed load is reported by ba_server_poll.  A user
- * allocator in the configuration is then called from the library thread.
+ * allocator in the configuration is then called from the loader threads.
  * The other ba_server_* calls stay single-threaded: make them from one
  * thread. */
 enum { BA_JOB_UNKNOWN = -1, BA_JOB_LOADING = 0, BA_JOB_RESIDENT = 1, BA_JOB_FINISHED = 2, BA_JOB_FAILED = 3 };
@@ -400,6 +438,9 @@ ba_status ba_server_submit_async(ba_server* s, const ba_job_desc* job, void* inp
 int32_t ba_server_job_state(ba_server* s, uint64_t job_id);
 /* Jobs submitted asynchronously that have not joined the batch yet. */
 int32_t ba_server_loading(const ba_server* s);
+/* Number of loader threads (1 .. 16, default 2), each loading one job at a
+ * time; only before the first ba_server_submit_async (BA_ERR_STATE after). */
+ba_status ba_server_set_loaders(ba_server* s, int32_t n);
 /* 1 if a job of these sizes would be admitted now, else 0 (lets a caller
  * prepare a job's inputs only when they can be taken). */
 int32_t ba_server_fits(const ba_server* s, int32_t n_scans, int64_t n_voxels, int64_t n_obs);

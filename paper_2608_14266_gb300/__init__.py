@@ -506,6 +506,31 @@ class BundleAdjuster:
     def profile_read(self):
         return ba_profile_read(self.h)
 
+    # voxel-sharded solve (ba_shard_* in include/ba.h)
+    def shard_partials(self):
+        """(g, H partials as (n_scans, 27) float64, cost partial) at the current poses."""
+        gH = np.empty((self.n_scans, 27))
+        c = ctypes.c_double()
+        _check(_lib.lib().ba_shard_partials(self.h, gH.ctypes.data, ctypes.byref(c), BA_MEM_HOST), self.h)
+        return gH, c.value
+
+    def shard_set_totals(self, gH_total, cost_total):
+        a = _Arg(gH_total, np.float64)
+        if int(np.prod(a.shape)) != 27 * self.n_scans:
+            raise ValueError("gH_total must hold n_scans x 27 values")
+        _check(_lib.lib().ba_shard_set_totals(self.h, a.ptr, float(cost_total),
+                                              BA_MEM_DEVICE if a.device else BA_MEM_HOST), self.h)
+
+    def shard_trial(self) -> float:
+        c = ctypes.c_double()
+        _check(_lib.lib().ba_shard_trial(self.h, ctypes.byref(c)), self.h)
+        return c.value
+
+    def shard_decide(self, trial_cost_total) -> bool:
+        acc = ctypes.c_int32()
+        _check(_lib.lib().ba_shard_decide(self.h, float(trial_cost_total), ctypes.byref(acc)), self.h)
+        return bool(acc.value)
+
     def close(self):
         if self.h:
             ba_destroy(self.h)

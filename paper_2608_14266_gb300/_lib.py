@@ -104,9 +104,14 @@ _SIGNATURES = {
     "ba_server_cancel": (_I32, [_P, ctypes.c_uint64]),
     "ba_server_submit_async": (_I32, [_P, _P, _P, _P]),
     "ba_batch_profile_enable": (_I32, [_P, _I32]),
+    "ba_shard_partials": (_I32, [_P, _P, _P, _I32]),
+    "ba_shard_set_totals": (_I32, [_P, _P, _D, _I32]),
+    "ba_shard_trial": (_I32, [_P, _P]),
+    "ba_shard_decide": (_I32, [_P, _D, _P]),
     "ba_batch_profile_read": (_I32, [_P, _I32, _P, _P]),
     "ba_server_job_state": (_I32, [_P, ctypes.c_uint64]),
     "ba_server_loading": (_I32, [_P]),
+    "ba_server_set_loaders": (_I32, [_P, _I32]),
     "ba_check_bounded_wait": (_I32, [_I32, _I32]),
     "ba_release_cached_memory": (_I32, [_I32]),
     "ba_check_conversions": (_I32, [_I32, _I64, ctypes.c_uint64, _P]),

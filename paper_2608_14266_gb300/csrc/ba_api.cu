@@ -51,6 +51,7 @@ struct ba_handle {
   double* pred_part = nullptr;
   double* cost_part = nullptr;
   int64_t n_cost = 0;
+  double* d_shard = nullptr;  // voxel-sharded solve: this handle's summed trial cost
   // copy stream and events of a load that overlaps the clusters' copy with the set-up
   cudaStream_t copy_stream = nullptr;
   std::vector<cudaEvent_t> copy_events;
@@ -175,6 +176,7 @@ void release_problem(ba_handle* h) {
   h->in_keep = LoadInput{};
   h->d_state = nullptr;
   h->poses2 = h->planes2 = h->gH = h->pred_part = h->cost_part = nullptr;
+  h->d_shard = nullptr;
 }
 
 // small state-control kernel: flags for the solve loop and cost bookkeeping
@@ -882,6 +884,71 @@ ba_status ba_gradient(ba_handle* h, double* g, double* H, int32_t mem_kind) {
 }
 
 int64_t ba_kernel_launches(const ba_handle* h) { return h ? h->launches : 0; }
+
+ba_status ba_shard_partials(ba_handle* h, double* gH, double* cost, int32_t mem_kind) {
+  ba_status s = check_loaded(h);
+  if (s != BA_OK) return s;
+  if (mem_kind != BA_MEM_HOST && mem_kind != BA_MEM_DEVICE) return fail(h, BA_ERR_INVALID_ARG, "bad mem_kind");
+  DeviceGuard g(h->cfg.device);
+  const cudaMemcpyKind kind = mem_kind == BA_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  if (gH)
+    CK(h, cudaMemcpyAsync(gH, h->gH, sizeof(double) * kGH * (size_t)h->L.n_scans, kind, h->stream), "read g, H");
+  if (cost) CK(h, cudaMemcpyAsync(cost, &h->d_state->cost, sizeof(double), kind, h->stream), "read cost");
+  if (mem_kind == BA_MEM_HOST) CK(h, cudaStreamSynchronize(h->stream), "synchronize");
+  return BA_OK;
+}
+
+ba_status ba_shard_set_totals(ba_handle* h, const double* gH_total, double cost_total, int32_t mem_kind) {
+  ba_status s = check_loaded(h);
+  if (s != BA_OK) return s;
+  if (!gH_total) return fail(h, BA_ERR_INVALID_ARG, "gH_total is NULL");
+  if (mem_kind != BA_MEM_HOST && mem_kind != BA_MEM_DEVICE) return fail(h, BA_ERR_INVALID_ARG, "bad mem_kind");
+  if (!std::isfinite(cost_total) || cost_total < 0.0) return fail(h, BA_ERR_INVALID_ARG, "cost_total must be finite, >= 0");
+  DeviceGuard g(h->cfg.device);
+  const cudaMemcpyKind kind = mem_kind == BA_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  CK(h, cudaMemcpyAsync(h->gH, gH_total, sizeof(double) * kGH * (size_t)h->L.n_scans, kind, h->stream), "g, H");
+  // the host values are consumed before the call returns
+  DevState* st = h->d_state;
+  const int32_t one = 1;
+  CK(h, cudaMemcpyAsync(&st->cost, &cost_total, sizeof(double), cudaMemcpyHostToDevice, h->stream), "cost");
+  CK(h, cudaMemcpyAsync(&st->shard, &one, sizeof(int32_t), cudaMemcpyHostToDevice, h->stream), "shard flag");
+  CK(h, cudaStreamSynchronize(h->stream), "synchronize");
+  return BA_OK;
+}
+
+ba_status ba_shard_trial(ba_handle* h, double* trial_cost) {
+  ba_status s = check_loaded(h);
+  if (s != BA_OK) return s;
+  if (!trial_cost) return fail(h, BA_ERR_INVALID_ARG, "trial_cost is NULL");
+  DeviceGuard g(h->cfg.device);
+  if (!h->d_shard && !(h->d_shard = (double*)dev_alloc(h, h->keep, sizeof(double))))
+    return fail(h, BA_ERR_OOM, "out of device memory");
+  control_kernel<<<1, 1, 0, h->stream>>>(h->d_state, 0, 1);
+  CK(h, cudaGetLastError(), "control");
+  CK(h, launch_solve_f64(h->L, h->poses2, h->gH, h->pred_part, h->d_state, h->mixed ? h->mb.sref : nullptr,
+                         h->mixed ? h->mb.stab2 : nullptr, h->stream),
+     "solve");
+  CK(h, voxel_pass(h, nullptr, 1, -1), "trial voxel pass");
+  CK(h, launch_shard_cost(h->L, h->cost_part, h->d_shard, h->stream), "trial cost");
+  h->launches += 4;
+  CK(h, cudaMemcpyAsync(trial_cost, h->d_shard, sizeof(double), cudaMemcpyDeviceToHost, h->stream), "read cost");
+  CK(h, cudaStreamSynchronize(h->stream), "synchronize");
+  return BA_OK;
+}
+
+ba_status ba_shard_decide(ba_handle* h, double trial_cost_total, int32_t* accepted) {
+  ba_status s = check_loaded(h);
+  if (s != BA_OK) return s;
+  DeviceGuard g(h->cfg.device);
+  CK(h, launch_shard_decide(h->L, h->pred_part, h->d_state, trial_cost_total, h->stream), "decide");
+  CK(h, scan_pass(h, 0), "scan pass");
+  h->launches += 2;
+  DevState st;
+  if ((s = read_state(h, &st)) != BA_OK) return s;
+  if (accepted) *accepted = st.last_accepted;
+  if (!std::isfinite(st.cost)) return fail(h, BA_ERR_NUMERIC, "cost is not finite");
+  return BA_OK;
+}
 
 ba_status ba_release_cached_memory(int32_t device) {
   if (device < 0 || device >= 64) return BA_ERR_INVALID_ARG;

@@ -329,12 +329,17 @@ __global__ void __launch_bounds__(kScanThreads) scan_pass_f64_batch_kernel(const
 __device__ inline double solve_scan(const DevLayout& L, int j, const double* __restrict__ P, double* __restrict__ Pt,
                                     const double* __restrict__ gH, DevState* st, double* dlt, bool* stepped) {
   *stepped = false;
-  const int64_t nobs = L.scan_off[j + 1] - L.scan_off[j];
-  if (j == L.fixed_scan || nobs == 0) {
+  const double* a = gH + (int64_t)j * kGH;
+  // a scan nobody observes keeps its pose: no observation in this handle's
+  // layout, or, for a voxel-sharded solve (g, H totals over all shards), an
+  // all-zero total Hessian diagonal (an observation always makes it nonzero)
+  const bool unseen = st->shard ? (a[6] == 0.0 && a[12] == 0.0 && a[17] == 0.0 && a[21] == 0.0 && a[24] == 0.0 &&
+                                   a[26] == 0.0)
+                                : L.scan_off[j + 1] == L.scan_off[j];
+  if (j == L.fixed_scan || unseen) {
     for (int k = 0; k < 12; ++k) Pt[k] = P[k];
     return 0.0;
   }
-  const double* a = gH + (int64_t)j * kGH;
   double g[6], H[36], A[36], b[6];
   for (int k = 0; k < 6; ++k) g[k] = a[k];
   int idx = 6;
@@ -437,6 +442,24 @@ __global__ void __launch_bounds__(kDecideThreads) decide_kernel(const double* __
   decide_body<kDecideThreads>(cost_part, n_cost, pred_part, n_pred, st, mode, red);
 }
 
+// Voxel-sharded solve: this handle's part of the trial cost (its cost
+// partials summed in the decision's fixed order) ...
+__global__ void __launch_bounds__(kDecideThreads) shard_cost_kernel(const double* __restrict__ cost_part, int64_t n_cost,
+                                                                   double* __restrict__ out) {
+  __shared__ double red[kDecideThreads / 32];
+  const double csum = block_sum<kDecideThreads>(strided_sum<kDecideThreads>(cost_part, n_cost), red);
+  if (threadIdx.x == 0) *out = csum;
+}
+
+// ... and the decision from the trial cost summed over every shard (the
+// predicted reduction comes from the total g, H, so every shard has it whole)
+__global__ void __launch_bounds__(kDecideThreads) shard_decide_kernel(const double* __restrict__ pred_part,
+                                                                     int64_t n_pred, DevState* st, double trial_total) {
+  __shared__ double red[kDecideThreads / 32];
+  const double psum = block_sum<kDecideThreads>(strided_sum<kDecideThreads>(pred_part, n_pred), red);
+  if (threadIdx.x == 0) decide_apply(st, trial_total, psum);
+}
+
 // ---- launchers ---------------------------------------------------------------
 
 cudaError_t launch_voxel_pass_f64(const DevLayout& L, const double* poses2, double* planes2, double* full_out,
@@ -456,6 +479,17 @@ cudaError_t launch_scan_pass_f64(const DevLayout& L, const double* poses2, const
                                  const DevState* st, int force, cudaStream_t stream) {
   if (L.n_scans == 0) return cudaSuccess;
   scan_pass_f64_kernel<<<(unsigned)L.n_scans, kScanThreads, 0, stream>>>(L, poses2, planes2, gH, st, force);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_shard_cost(const DevLayout& L, const double* cost_part, double* out, cudaStream_t stream) {
+  shard_cost_kernel<<<1, kDecideThreads, 0, stream>>>(cost_part, voxel_pass_blocks(L.n_voxels), out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_shard_decide(const DevLayout& L, const double* pred_part, DevState* st, double trial_total,
+                                cudaStream_t stream) {
+  shard_decide_kernel<<<1, kDecideThreads, 0, stream>>>(pred_part, solve_blocks(L.n_scans), st, trial_total);
   return cudaGetLastError();
 }
 

@@ -207,6 +207,8 @@ struct DevState {
   int32_t scan_pending;     // an accepted step needs g, H at the new poses
   int32_t wait_timeout;     // a bounded device-side wait gave up (sticky)
   uint32_t blocks_done;     // voxel-pass blocks finished in the current launch (decision in the last)
+  int32_t shard;            // g, H and cost are totals over several handles' voxels (voxel-sharded solve)
+  int32_t pad_;
 };
 
 // One job of a batch: everything its kernels touch.  A batch launches each
@@ -667,6 +669,8 @@ __device__ inline T block_sum(T v, T* smem /* kThreads / 32 */) {
 // otherwise).  Acceptance flips the current pose/plane buffers.
 // With mode = 1 it only installs the summed cost as the current cost.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ void decide_apply(DevState* st, double csum, double psum);
+
 template <int kThreads>
 __device__ __forceinline__ void decide_body(const double* __restrict__ cost_part, int64_t n_cost,
                                             const double* __restrict__ pred_part, int64_t n_pred, DevState* st,
@@ -683,6 +687,12 @@ __device__ __forceinline__ void decide_body(const double* __restrict__ cost_part
     st->cost = csum;
     return;
   }
+  decide_apply(st, csum, psum);
+}
+
+// The decision itself (thread 0), from the summed trial cost and predicted
+// reduction.
+__device__ __forceinline__ void decide_apply(DevState* st, double csum, double psum) {
   // work on a register copy: one load and one store of the state instead of a
   // chain of dependent global accesses
   DevState s = *st;

@@ -37,6 +37,11 @@ cudaError_t launch_voxel_pass_f64(const DevLayout& L, const double* poses2, doub
 cudaError_t launch_scan_pass_f64(const DevLayout& L, const double* poses2, const double* planes2, double* gH,
                                  const DevState* st, int force, cudaStream_t stream);
 // sref/stab2 non-null: also write the trial FP32 scan table (mixed precision)
+// voxel-sharded solve: this handle's summed trial cost into *out (device);
+// the LM decision from the total trial cost over all shards
+cudaError_t launch_shard_cost(const DevLayout& L, const double* cost_part, double* out, cudaStream_t stream);
+cudaError_t launch_shard_decide(const DevLayout& L, const double* pred_part, DevState* st, double trial_total,
+                                cudaStream_t stream);
 cudaError_t launch_solve_f64(const DevLayout& L, double* poses2, const double* gH, double* pred_part, DevState* st,
                              const double* sref, float* stab2, cudaStream_t stream);
 cudaError_t launch_decide(const double* cost_part, int64_t n_cost, const double* pred_part, int64_t n_pred,

@@ -2,7 +2,7 @@
 // one batch stepping every resident job, retirement of finished jobs to host
 // memory.  Host code only; the arithmetic is in the batch's kernels.
 //
-// Asynchronous admission (ba_server_submit_async): a library thread loads
+// Asynchronous admission (ba_server_submit_async): library threads load
 // each submitted job on a stream of its own (validation, layout build and
 // set-up, with their host synchronisations) while the calling thread keeps
 // stepping the resident jobs, so a new job's set-up overlaps the other jobs'
@@ -69,7 +69,7 @@ struct ba_server {
   std::string err;
   // asynchronous admission: the caller's thread owns `charged`, `failed` and
   // `cancelled`; `pending`, `loaded` and `loading_now` are shared with the
-  // loader thread under `mu`
+  // loader threads under `mu`
   // submitted, not yet attached: (estimate of the loaded job, bytes charged = estimate + load peak)
   std::unordered_map<uint64_t, std::pair<int64_t, int64_t>> charged;
   std::unordered_map<uint64_t, std::pair<ba_status, std::string>> failed;
@@ -78,9 +78,10 @@ struct ba_server {
   std::condition_variable cv_work, cv_done;
   std::deque<PendingLoad> pending;
   std::vector<LoadedJob> loaded;
-  uint64_t loading_now = 0;
+  std::unordered_set<uint64_t> loading_now;  // taken by a loader thread, not returned yet
   bool stop = false;
-  std::thread loader;
+  int n_loaders = 2;
+  std::vector<std::thread> loaders;
 };
 
 namespace {
@@ -114,7 +115,7 @@ ba_status retire(ba_server* s, size_t k) {
 }
 
 
-// The loader thread: one job at a time, on a fresh non-blocking stream that
+// A loader thread: one job at a time, on a fresh non-blocking stream that
 // first waits for the caller's inputs, then create + load + synchronise.  The
 // job's handle keeps that stream for its own calls (reading results,
 // freeing), so attaching it to the batch later waits for nothing.
@@ -128,7 +129,7 @@ void loader_main(ba_server* s) {
       if (s->stop) return;
       p = s->pending.front();
       s->pending.pop_front();
-      s->loading_now = p.id;
+      s->loading_now.insert(p.id);
     }
     LoadedJob L{p.id, nullptr, nullptr, p.desc.n_scans, BA_OK, std::string()};
     cudaError_t e = cudaStreamCreateWithFlags(&L.stream, cudaStreamNonBlocking);
@@ -169,8 +170,8 @@ void loader_main(ba_server* s) {
     }
     {
       std::lock_guard<std::mutex> lk(s->mu);
+      s->loading_now.erase(L.id);
       s->loaded.push_back(std::move(L));
-      s->loading_now = 0;
     }
     s->cv_done.notify_all();
   }
@@ -232,7 +233,9 @@ void stop_loader(ba_server* s) {
     s->stop = true;
   }
   s->cv_work.notify_all();
-  if (s->loader.joinable()) s->loader.join();
+  for (auto& t : s->loaders)
+    if (t.joinable()) t.join();
+  s->loaders.clear();
 }
 
 }  // namespace
@@ -413,7 +416,7 @@ ba_status ba_server_submit_async(ba_server* s, const ba_job_desc* job, void* inp
       return sfail(s, BA_ERR_CUDA, "record the inputs' readiness: %s", cudaGetErrorString(e));
     }
   }
-  if (!s->loader.joinable()) s->loader = std::thread(loader_main, s);
+  while ((int)s->loaders.size() < s->n_loaders) s->loaders.emplace_back(loader_main, s);
   const uint64_t id = s->next_id++;
   s->charged[id] = {keep, keep + peak};
   s->used += keep + peak;
@@ -434,7 +437,7 @@ int32_t ba_server_job_state(ba_server* s, uint64_t job_id) {
     if (r.id == job_id) return BA_JOB_RESIDENT;
   if (!s->charged.count(job_id)) return BA_JOB_UNKNOWN;
   std::lock_guard<std::mutex> lk(s->mu);
-  if (s->loading_now == job_id) return BA_JOB_LOADING;
+  if (s->loading_now.count(job_id)) return BA_JOB_LOADING;
   for (const auto& p : s->pending)
     if (p.id == job_id) return BA_JOB_LOADING;
   for (const auto& L : s->loaded)
@@ -443,6 +446,13 @@ int32_t ba_server_job_state(ba_server* s, uint64_t job_id) {
 }
 
 int32_t ba_server_loading(const ba_server* s) { return s ? (int32_t)s->charged.size() : 0; }
+
+ba_status ba_server_set_loaders(ba_server* s, int32_t n) {
+  if (!s || n < 1 || n > 16) return BA_ERR_INVALID_ARG;
+  if (!s->loaders.empty()) return sfail(s, BA_ERR_STATE, "the loader threads have started");
+  s->n_loaders = n;
+  return BA_OK;
+}
 
 int32_t ba_server_fits(const ba_server* s, int32_t n_scans, int64_t n_voxels, int64_t n_obs) {
   if (!s || n_scans < 1 || n_voxels < 0 || n_obs < 0) return 0;

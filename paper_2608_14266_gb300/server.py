@@ -67,7 +67,7 @@ class Server:
     handle (precision, rel_tol, max_iters, cuda_stream, ...)."""
 
     def __init__(self, mem_budget: int, chunk: int = 4, clock=time.perf_counter, async_admission: bool = False,
-                 input_stream=None, **cfg):
+                 input_stream=None, loaders: int = 2, **cfg):
         cfg.setdefault("precision", BA_MIXED)
         self.cfg = ba_config_default(**cfg)
         self.chunk = int(chunk)
@@ -81,6 +81,7 @@ class Server:
         status = _lib.lib().ba_server_create(ctypes.byref(self.cfg), int(mem_budget), ctypes.byref(self.s))
         if status != _lib.BA_OK:
             raise BAError(status, "ba_server_create")
+        self._check(_lib.lib().ba_server_set_loaders(self.s, int(loaders)))
         self.queue: collections.deque[Job] = collections.deque()
         self.resident: list[Job] = []
         self.finished: list[Job] = []

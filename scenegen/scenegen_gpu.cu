@@ -10,8 +10,7 @@
 //    library), so thousands of jobs can be generated where they are solved;
 //  - sgd_points_fast: the points of such a scene drawn from the same
 //    per-observation counters but in FP32 (uniform variates from the top 23
-//    bits, Box-Muller with the fast intrinsics), one warp per observation,
-//    written as float64.  These points differ from the host's by the FP32
+//    bits, Box-Muller with the fast intrinsics), written as float64.  These points differ from the host's by the FP32
 //    rounding of the draws and of the scan-frame coordinates (a few
 //    micrometres at 100 m), far below the 1-2 cm noise of the workloads; the
 //    GPU's FP64 pipe, narrow on this part, stays out of the per-point work.
@@ -244,54 +243,74 @@ __device__ __forceinline__ float unit32(uint64_t x) {
   return __uint_as_float(0x3f800000u | (uint32_t)(x >> 41)) - 1.0f;
 }
 
-// one warp per observation: the observation's frame terms once (FP64, every
-// lane alike), then its points lane by lane in FP32
-__global__ void __launch_bounds__(256) points_fast_kernel(uint64_t seed, int32_t npo, double sigma,
-                                                          const double* __restrict__ plane,
-                                                          const double* __restrict__ extent,
-                                                          const double* __restrict__ pose_gt,
-                                                          const int32_t* __restrict__ obs_scan,
-                                                          const int32_t* __restrict__ obs_voxel, int64_t obs_begin,
-                                                          int64_t n_obs, double* __restrict__ out) {
-  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (w >= n_obs) return;
-  const int64_t o = obs_begin + w;
-  const int32_t v = obs_voxel[o];
-  const double* P = plane + 12 * (int64_t)v;
-  const double* G = pose_gt + 12 * (int64_t)obs_scan[o];
-  // scan-frame origin of the patch, R^T (c - t), and its axes R^T e1, R^T e2, R^T n
-  float org[3], ax1[3], ax2[3], axn[3];
-  {
+// Per warp 32 observations: first every lane takes one observation's frame
+// terms (FP64, then rounded once: the patch origin in the scan frame
+// R^T (c - t) and its axes R^T e1, R^T e2, R^T n) and its stream key into
+// shared memory -- a GB300 FP64 warp instruction costs the same with one
+// active lane as with 32, so the terms of 32 observations cost what one
+// would -- then the warp draws the observations' points one observation at a
+// time, lane k taking points k, k + 32, ... in FP32.
+constexpr int kFastWarps = 8;
+struct FastObs {
+  float t[14];  // origin (3), e1 (3), e2 (3), n (3) in the scan frame; side lengths s1, s2
+  uint32_t key_lo, key_hi;
+};
+
+__global__ void __launch_bounds__(32 * kFastWarps) points_fast_kernel(
+    uint64_t seed, int32_t npo, double sigma, const double* __restrict__ plane, const double* __restrict__ extent,
+    const double* __restrict__ pose_gt, const int32_t* __restrict__ obs_scan, const int32_t* __restrict__ obs_voxel,
+    int64_t obs_begin, int64_t n_obs, double* __restrict__ out) {
+  __shared__ FastObs sh[kFastWarps][32];
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t w0 = ((int64_t)blockIdx.x * kFastWarps + wib) * 32;  // first observation (relative) of the warp
+  if (w0 >= n_obs) return;  // the whole warp
+  const int64_t mine = w0 + lane;
+  if (mine < n_obs) {
+    const int64_t o = obs_begin + mine;
+    const int32_t v = obs_voxel[o];
+    const double* P = plane + 12 * (int64_t)v;
+    const double* G = pose_gt + 12 * (int64_t)obs_scan[o];
     const double dc[3] = {P[0] - G[9], P[1] - G[10], P[2] - G[11]};
-    for (int d = 0; d < 3; ++d) {
-      org[d] = (float)(G[d] * dc[0] + G[3 + d] * dc[1] + G[6 + d] * dc[2]);
-      ax1[d] = (float)(G[d] * P[6] + G[3 + d] * P[7] + G[6 + d] * P[8]);
-      ax2[d] = (float)(G[d] * P[9] + G[3 + d] * P[10] + G[6 + d] * P[11]);
-      axn[d] = (float)(G[d] * P[3] + G[3 + d] * P[4] + G[6 + d] * P[5]);
-    }
-  }
-  const float s1 = (float)extent[2 * v], s2 = (float)extent[2 * v + 1], sg = (float)sigma;
-  const uint64_t key = mix64(mix64(seed ^ (kStPoints * kStreamMul)) + (uint64_t)o * kGolden);
-  const int draws = sigma > 0.0 ? 4 : 2;
-  double* dst = out + 3 * (w * (int64_t)npo);
-  for (int k = lane; k < npo; k += 32) {
-    uint64_t ctr = (uint64_t)k * draws;
-    const float a = s1 * (unit32(mix64(key + (++ctr) * kGolden)) - 0.5f);
-    const float b = s2 * (unit32(mix64(key + (++ctr) * kGolden)) - 0.5f);
-    float eps = 0.f;
-    if (sigma > 0.0) {
-      // (0, 1] like the host's ((x >> 11) + 1) 2^-53, from the top 32 bits
-      // (relative precision kept for small values, where the log is steep)
-      const float u1 = fmaf(__uint2float_rn((uint32_t)(mix64(key + (++ctr) * kGolden) >> 32)), 2.3283064365386963e-10f,
-                            1.1641532182693481e-10f);
-      const float u2 = unit32(mix64(key + (++ctr) * kGolden));
-      // cos(2 pi u2) = -cos(2 pi u2 - pi), the fast cosine's argument kept in [-pi, pi)
-      eps = sg * (sqrtf(-2.0f * logf(u1)) * -__cosf(6.28318530717958647692f * u2 - 3.14159265358979323846f));
-    }
+    FastObs& f = sh[wib][lane];
 #pragma unroll
-    for (int d = 0; d < 3; ++d)
-      dst[3 * k + d] = f32_to_f64_bits(fmaf(a, ax1[d], fmaf(b, ax2[d], fmaf(eps, axn[d], org[d]))));
+    for (int d = 0; d < 3; ++d) {
+      f.t[d] = (float)(G[d] * dc[0] + G[3 + d] * dc[1] + G[6 + d] * dc[2]);
+      f.t[3 + d] = (float)(G[d] * P[6] + G[3 + d] * P[7] + G[6 + d] * P[8]);
+      f.t[6 + d] = (float)(G[d] * P[9] + G[3 + d] * P[10] + G[6 + d] * P[11]);
+      f.t[9 + d] = (float)(G[d] * P[3] + G[3 + d] * P[4] + G[6 + d] * P[5]);
+    }
+    f.t[12] = (float)extent[2 * v];
+    f.t[13] = (float)extent[2 * v + 1];
+    const uint64_t key = mix64(mix64(seed ^ (kStPoints * kStreamMul)) + (uint64_t)o * kGolden);
+    f.key_lo = (uint32_t)key;
+    f.key_hi = (uint32_t)(key >> 32);
+  }
+  __syncwarp();
+  const float sg = (float)sigma;
+  const int draws = sigma > 0.0 ? 4 : 2;
+  const int nq = (int)min((int64_t)32, n_obs - w0);
+  for (int q = 0; q < nq; ++q) {
+    const FastObs& f = sh[wib][q];
+    const uint64_t key = ((uint64_t)f.key_hi << 32) | f.key_lo;
+    double* dst = out + 3 * ((w0 + q) * (int64_t)npo);
+    for (int k = lane; k < npo; k += 32) {
+      uint64_t ctr = (uint64_t)k * draws;
+      const float a = f.t[12] * (unit32(mix64(key + (++ctr) * kGolden)) - 0.5f);
+      const float b = f.t[13] * (unit32(mix64(key + (++ctr) * kGolden)) - 0.5f);
+      float eps = 0.f;
+      if (sigma > 0.0) {
+        // (0, 1] like the host's ((x >> 11) + 1) 2^-53, from the top 32 bits
+        // (relative precision kept for small values, where the log is steep)
+        const float u1 = fmaf(__uint2float_rn((uint32_t)(mix64(key + (++ctr) * kGolden) >> 32)),
+                              2.3283064365386963e-10f, 1.1641532182693481e-10f);
+        const float u2 = unit32(mix64(key + (++ctr) * kGolden));
+        // cos(2 pi u2) = -cos(2 pi u2 - pi), the fast cosine's argument kept in [-pi, pi)
+        eps = sg * (sqrtf(-2.0f * logf(u1)) * -__cosf(6.28318530717958647692f * u2 - 3.14159265358979323846f));
+      }
+#pragma unroll
+      for (int d = 0; d < 3; ++d)
+        dst[3 * k + d] = f32_to_f64_bits(fmaf(a, f.t[3 + d], fmaf(b, f.t[6 + d], fmaf(eps, f.t[9 + d], f.t[d]))));
+    }
   }
 }
 
@@ -342,7 +361,8 @@ extern "C" int sgd_points_fast(uint64_t seed, int32_t pts_per_obs, double noise_
                                void* stream) {
   const int64_t n = obs_end - obs_begin;
   if (n <= 0 || pts_per_obs < 1) return 0;
-  points_fast_kernel<<<(unsigned)((n * 32 + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
+  const int64_t per_block = 32 * kFastWarps;  // observations per block
+  points_fast_kernel<<<(unsigned)((n + per_block - 1) / per_block), 32 * kFastWarps, 0, (cudaStream_t)stream>>>(
       seed, pts_per_obs, noise_sigma, plane, extent, pose_gt, obs_scan, obs_voxel, obs_begin, n, out);
   return (int)cudaGetLastError();
 }
