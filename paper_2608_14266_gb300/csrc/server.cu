@@ -132,7 +132,12 @@ void loader_main(ba_server* s) {
       s->loading_now.insert(p.id);
     }
     LoadedJob L{p.id, nullptr, nullptr, p.desc.n_scans, BA_OK, std::string()};
-    cudaError_t e = cudaStreamCreateWithFlags(&L.stream, cudaStreamNonBlocking);
+    // the highest priority: a load's blocks are dispatched as soon as SMs
+    // free up, so its set-up (partly FP64-bound) runs beside the resident
+    // jobs' memory-bound iterations instead of after them
+    int least = 0, greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) greatest = 0;
+    cudaError_t e = cudaStreamCreateWithPriority(&L.stream, cudaStreamNonBlocking, greatest);
     if (e != cudaSuccess) {
       cudaGetLastError();
       L.stream = nullptr;
