@@ -168,6 +168,15 @@ def _gpu_id(torch, dev: int) -> str | None:
 # ---------------------------------------------------------------------------
 # inputs
 # ---------------------------------------------------------------------------
+def workload_config(args, scene, world):
+    """The workload a line is measured on (the same for both arms)."""
+    gb = MIXED_ALG_BYTES_PER_OBS * scene.n_obs / 1e9
+    l2 = (f"inputs larger than L2 (every pass streams {gb:.2f} GB of clusters)" if gb > 0.129 else
+          f"inputs of {gb:.3f} GB fit in L2 (no flush: not a timing-rule workload)")
+    return {"workload": WORKLOAD_TEXT[args.workload], "n_scans": scene.n_scans, "n_voxels": scene.n_voxels,
+            "n_obs": scene.n_obs, "l2": l2, "parallelism": f"{world} independent job(s), one per GPU"}
+
+
 def scene_params(scenegen, args, rank):
     p = scenegen.config(args.workload, rep=rank)
     if args.shrink != 1.0:
@@ -357,7 +366,8 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": ips, "unit": "iter/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / ips, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded scene generator)",
-        "config": {"workload": WORKLOAD_TEXT[args.workload], "n_obs": scene.n_obs, "solver": "CPU oracle, FP64"},
+        "config": workload_config(args, scene, 1),
+        "run": {"solver": "CPU oracle, FP64", "iters_per_solve": args.iters_per_solve},
         "plane_obs_per_s": ips * scene.n_obs,
         "e2e": {"value": ips, "unit": "iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "cpu_baseline": {"value": ips, "unit": "iter/s", "cores": 1, "kind": "oracle", "sample": sample,
@@ -554,11 +564,9 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32" if args.precision == "mixed" else "f64",
         "data": "synthetic (seeded scene generator; points clustered on GPU)",
-        "config": {"workload": WORKLOAD_TEXT[args.workload], "n_scans": scene.n_scans,
-                   "n_voxels": scene.n_voxels, "n_obs": scene.n_obs, "precision": args.precision,
-                   "iters_per_solve": S, "accepted_iters": res["accepted"],
-                   "l2": "inputs larger than L2 (per-pass clusters %.2f GB)" % (scene.n_obs * per_obs / 1e9),
-                   "parallelism": f"{world} independent job(s), one per GPU"},
+        "config": workload_config(args, scene, world),
+        "run": {"precision": args.precision, "iters_per_solve": S, "accepted_iters": res["accepted"],
+                "per_pass_cluster_gb": round(scene.n_obs * per_obs / 1e9, 3)},
         "plane_obs_per_s": value * scene.n_obs,
         "fp64_path": fp64,
         "clocks": res["clocks"],
