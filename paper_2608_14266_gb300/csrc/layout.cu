@@ -689,43 +689,39 @@ cudaError_t build_layout(const LoadInput& in, int max_len, bool fill_f64, bool d
 }
 
 // ============================================================================
-// Point clusters (Eq. 2) in centred form: four lanes per observation (eight
-// observations per warp, four consecutive points per load); the mean first,
-// then the scatter about the mean (two passes over the points, the second
-// from cache).  Few lanes per observation keep the FP64 shuffle reductions
-// (GB300's FP64 rate is 1/64 of FP32) small next to the per-point work.
+// Point clusters (Eq. 2) in centred form: two lanes per observation (sixteen
+// observations per warp; the pair reads neighbouring points, so a sector's
+// three coordinates come from one fetch), one pass over the points as sums
+// shifted by the observation's first point p0: with d = p - p0,
+//   m = p0 + (sum d) / N,   S = sum d d^T - (sum d)(sum d)^T / N,
+// algebraically the mean and the scatter about it (Eq. 2 fixes the sums, not
+// their order).  Per point 12 FP64 operations, per observation one
+// reciprocal and one shuffle level: GB300's FP64 rate is 1/64 of FP32 and its
+// FP64 warp instructions cost the same with idle lanes, so few lanes per
+// observation and one pass keep the FP64 instruction count low.
 // ============================================================================
-constexpr int kAggLanes = 4;
+constexpr int kAggLanes = 2;
 
 __global__ void aggregate_points_kernel(int64_t n_obs, const int64_t* __restrict__ off,
                                         const double* __restrict__ pts, double* __restrict__ out) {
   const int64_t o = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kAggLanes;
   const int sub = threadIdx.x & (kAggLanes - 1);
-  const unsigned mask = 0xfu << (threadIdx.x & 28);  // the four lanes of this observation
-  if (o >= n_obs) return;  // all four lanes of a group leave together
+  const unsigned mask = 0x3u << (threadIdx.x & 30);  // the two lanes of this observation
+  if (o >= n_obs) return;  // both lanes of a pair leave together
   const int64_t a = off[o], b = off[o + 1];
-  double sx = 0.0, sy = 0.0, sz = 0.0;
-  for (int64_t k = a + sub; k < b; k += kAggLanes) {
-    sx += pts[3 * k];
-    sy += pts[3 * k + 1];
-    sz += pts[3 * k + 2];
-  }
-#pragma unroll
-  for (int w = kAggLanes / 2; w > 0; w >>= 1) {
-    sx += __shfl_xor_sync(mask, sx, w);
-    sy += __shfl_xor_sync(mask, sy, w);
-    sz += __shfl_xor_sync(mask, sz, w);
-  }
-  const double n = (double)(b - a);
   double* r = out + 10 * o;
   if (b <= a) {
     for (int k = sub; k < 10; k += kAggLanes) r[k] = 0.0;
     return;
   }
-  const double mx = sx / n, my = sy / n, mz = sz / n;
+  const double p0x = pts[3 * a], p0y = pts[3 * a + 1], p0z = pts[3 * a + 2];
+  double sx = 0.0, sy = 0.0, sz = 0.0;
   double c00 = 0.0, c01 = 0.0, c02 = 0.0, c11 = 0.0, c12 = 0.0, c22 = 0.0;
   for (int64_t k = a + sub; k < b; k += kAggLanes) {
-    const double x = pts[3 * k] - mx, y = pts[3 * k + 1] - my, z = pts[3 * k + 2] - mz;
+    const double x = pts[3 * k] - p0x, y = pts[3 * k + 1] - p0y, z = pts[3 * k + 2] - p0z;
+    sx += x;
+    sy += y;
+    sz += z;
     c00 = fma(x, x, c00);
     c01 = fma(x, y, c01);
     c02 = fma(x, z, c02);
@@ -733,29 +729,30 @@ __global__ void aggregate_points_kernel(int64_t n_obs, const int64_t* __restrict
     c12 = fma(y, z, c12);
     c22 = fma(z, z, c22);
   }
-#pragma unroll
-  for (int w = kAggLanes / 2; w > 0; w >>= 1) {
-    c00 += __shfl_xor_sync(mask, c00, w);
-    c01 += __shfl_xor_sync(mask, c01, w);
-    c02 += __shfl_xor_sync(mask, c02, w);
-    c11 += __shfl_xor_sync(mask, c11, w);
-    c12 += __shfl_xor_sync(mask, c12, w);
-    c22 += __shfl_xor_sync(mask, c22, w);
-  }
-  // every lane holds the sums; each writes a share of the record
+  sx += __shfl_xor_sync(mask, sx, 1);
+  sy += __shfl_xor_sync(mask, sy, 1);
+  sz += __shfl_xor_sync(mask, sz, 1);
+  c00 += __shfl_xor_sync(mask, c00, 1);
+  c01 += __shfl_xor_sync(mask, c01, 1);
+  c02 += __shfl_xor_sync(mask, c02, 1);
+  c11 += __shfl_xor_sync(mask, c11, 1);
+  c12 += __shfl_xor_sync(mask, c12, 1);
+  c22 += __shfl_xor_sync(mask, c22, 1);
+  // both lanes hold the sums; each writes half of the record
+  const double n = (double)(b - a);
+  const double rn = 1.0 / n;
+  const double dx = sx * rn, dy = sy * rn, dz = sz * rn;
   if (sub == 0) {
-    r[0] = c00;
-    r[1] = c01;
-    r[2] = c02;
-  } else if (sub == 1) {
-    r[3] = c11;
-    r[4] = c12;
-    r[5] = c22;
-  } else if (sub == 2) {
-    r[6] = mx;
-    r[7] = my;
-    r[8] = mz;
+    r[0] = fma(-sx, dx, c00);
+    r[1] = fma(-sx, dy, c01);
+    r[2] = fma(-sx, dz, c02);
+    r[3] = fma(-sy, dy, c11);
+    r[4] = fma(-sy, dz, c12);
   } else {
+    r[5] = fma(-sz, dz, c22);
+    r[6] = p0x + dx;
+    r[7] = p0y + dy;
+    r[8] = p0z + dz;
     r[9] = n;
   }
 }
