@@ -360,14 +360,15 @@ __device__ inline double solve_scan(const DevLayout& L, int j, const double* __r
     for (int k = 0; k < 12; ++k) Pt[k] = P[k];
     return 0.0;
   }
-  double gd = 0.0, dhd = 0.0;
+  // L = -(g^T D + D^T H D / 2); the quadratic form from H's upper triangle
+  double gd = 0.0, half = 0.0;
   for (int r = 0; r < 6; ++r) {
     gd = fma(g[r], dlt[r], gd);
-    double hr = 0.0;
-    for (int c = 0; c < 6; ++c) hr = fma(H[6 * r + c], dlt[c], hr);
-    dhd = fma(dlt[r], hr, dhd);
+    double hr = 0.5 * H[7 * r] * dlt[r];
+    for (int c = r + 1; c < 6; ++c) hr = fma(H[6 * r + c], dlt[c], hr);
+    half = fma(dlt[r], hr, half);
   }
-  const double pred = -(gd + 0.5 * dhd);
+  const double pred = -(gd + half);
   double E[9];
   so3_exp(dlt, E);
   for (int r = 0; r < 3; ++r)

@@ -490,20 +490,25 @@ __device__ __forceinline__ float4 quat_mul_f(float4 p, float4 q) {
 // LDL^T of the symmetric 6x6 A (full, row-major) without pivoting, then
 // solve A x = b.  Returns false if a pivot is not positive and finite.
 __device__ inline bool ldlt6_solve(const double* A, const double* b, double* x) {
-  double L[6][6], D[6];
+  // LD[i][k] = L[i][k] D[k], kept as the numerator it is (before the scaling
+  // by 1 / D[k]), so every update is one FMA; the pivots' reciprocals serve
+  // the factorisation and the diagonal solve alike (an FP64 division is a
+  // long instruction sequence on this part)
+  double L[6][6], LD[6][6], Di[6];
 #pragma unroll
   for (int j = 0; j < 6; ++j) {
     double dj = A[6 * j + j];
 #pragma unroll
-    for (int k = 0; k < j; ++k) dj -= L[j][k] * L[j][k] * D[k];
+    for (int k = 0; k < j; ++k) dj = fma(-L[j][k], LD[j][k], dj);
     if (!(dj > 0.0) || !isfinite(dj)) return false;
-    D[j] = dj;
-    double inv = 1.0 / dj;
+    const double inv = 1.0 / dj;
+    Di[j] = inv;
 #pragma unroll
     for (int i = j + 1; i < 6; ++i) {
       double v = A[6 * i + j];
 #pragma unroll
-      for (int k = 0; k < j; ++k) v -= L[i][k] * L[j][k] * D[k];
+      for (int k = 0; k < j; ++k) v = fma(-L[i][k], LD[j][k], v);
+      LD[i][j] = v;
       L[i][j] = v * inv;
     }
   }
@@ -512,11 +517,11 @@ __device__ inline bool ldlt6_solve(const double* A, const double* b, double* x) 
   for (int i = 0; i < 6; ++i) {
     double v = b[i];
 #pragma unroll
-    for (int k = 0; k < i; ++k) v -= L[i][k] * y[k];
+    for (int k = 0; k < i; ++k) v = fma(-L[i][k], y[k], v);
     y[i] = v;
   }
 #pragma unroll
-  for (int i = 0; i < 6; ++i) y[i] /= D[i];
+  for (int i = 0; i < 6; ++i) y[i] *= Di[i];
 #pragma unroll
   for (int i = 5; i >= 0; --i) {
     double v = y[i];
@@ -540,15 +545,15 @@ __device__ inline bool ldlt6_solve(const double* A, const double* b, double* x) 
 __device__ inline void so3_exp(const double* phi, double* R) {
   double x = phi[0], y = phi[1], z = phi[2];
   double th2 = x * x + y * y + z * z;
-  double th = sqrt(th2);
   double a, b;
-  if (th < 1e-6) {
+  if (th2 < 1e-12) {
     a = 1.0;
     b = 0.5;
-  } else if (th < 0.1) {
+  } else if (th2 < 0.01) {  // theta < 0.1: the series, no square root
     a = 1.0 + th2 * (-1.0 / 6 + th2 * (1.0 / 120 + th2 * (-1.0 / 5040 + th2 * (1.0 / 362880))));
     b = 0.5 + th2 * (-1.0 / 24 + th2 * (1.0 / 720 + th2 * (-1.0 / 40320 + th2 * (1.0 / 3628800))));
   } else {
+    const double th = sqrt(th2);
     double sh = sin(0.5 * th);
     a = sin(th) / th;
     b = 2.0 * sh * sh / th2;
