@@ -84,11 +84,29 @@ __device__ inline void rot_sym_f(const float* Rf, const float* Sf, float* out) {
 }
 
 
-// warp sum (xor butterfly: every lane ends with the total, in a fixed order)
-__device__ __forceinline__ float warp_allsum(float x) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-  return x;
+// Double-float (hi + lo, two binary32 values) arithmetic from the classical
+// error-free transformations: Knuth's two-sum and the FMA form of Dekker's
+// two-product (the rounding error of a * b is fma(a, b, -a * b) exactly).
+// It carries ~46 significant bits on the FP32 pipe, where GB300 issues 64
+// times the FP64 rate.  The transformations use the _rn intrinsics, which
+// the compiler never contracts into FMAs (a contraction would break their
+// exactness).
+struct DF {
+  float hi, lo;
+};
+
+__device__ __forceinline__ DF df_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return DF{s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+
+// acc + x * (y_hi + y_lo) for a binary32 x
+__device__ __forceinline__ DF df_fma(DF acc, float x, DF y) {
+  const float p = __fmul_rn(x, y.hi);
+  const float e = fmaf(x, y.hi, -p);  // exact error of the product
+  const DF s = df_two_sum(acc.hi, p);
+  return DF{s.hi, __fadd_rn(s.lo, __fadd_rn(acc.lo, fmaf(x, y.lo, e)))};
 }
 
 // FP32 copies of a cluster's scatter, mean and count (integer-arithmetic
@@ -109,17 +127,18 @@ __device__ __forceinline__ void posed_f32(const float* ref32, const float* m, fl
 }
 
 // anchor (FP32-rounded centroid) and starting frame (eigenvectors, normal
-// last, proper rotation) of each voxel at the reference poses, one warp per
-// voxel (lanes over its observations).  Both only seed the iteration (the
-// voxel pass moves the frame and the centroid every pass, and the anchor only
-// has to be an FP32 value near the centroid), so the sums are FP32, about the
-// voxel's first posed mean: an error of the order of an FP32 ulp of the scene
-// coordinates (~1e-4 m at 2 km) moves nothing but the seed.
-__global__ void voxel_frames_kernel(LoadInput in, int64_t v0, int64_t v1, const double* sref, const int32_t* vrank,
-                                    float4* vstate, float4* vanchor, float4* planes2) {
-  const int64_t v = v0 + ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
-  const int lane = threadIdx.x & 31;
-  if (v >= v1) return;  // the whole warp
+// last, proper rotation) of each voxel at the reference poses, one thread per
+// voxel over its observations in order (so 32 voxels' eigen-solves run side by
+// side in a warp).  Both only seed the iteration (the voxel pass moves the
+// frame and the centroid every pass, and the anchor only has to be an FP32
+// value near the centroid), so the sums are FP32, about the voxel's first
+// posed mean: an error of the order of an FP32 ulp of the scene coordinates
+// (~1e-4 m at 2 km) moves nothing but the seed.
+__global__ void __launch_bounds__(128) voxel_frames_kernel(LoadInput in, int64_t v0, int64_t v1, const double* sref,
+                                                           const int32_t* vrank, float4* vstate, float4* vanchor,
+                                                           float4* planes2) {
+  const int64_t v = v0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= v1) return;
   const int64_t a0 = in.voxel_off[v], a1 = in.voxel_off[v + 1];
   float p0[3];
   {
@@ -130,7 +149,7 @@ __global__ void voxel_frames_kernel(LoadInput in, int64_t v0, int64_t v1, const 
     posed_f32(sref32_of(sref, in.n_scans, in.obs_scan[a0]), mf, p0);
   }
   float n = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
-  for (int64_t o = a0 + lane; o < a1; o += 32) {
+  for (int64_t o = a0; o < a1; ++o) {
     double c[10];
     centred_cluster(in.agg + 10 * o, in.agg_form, c);
     float Sf[6], mf[3], N, q[3];
@@ -141,12 +160,11 @@ __global__ void voxel_frames_kernel(LoadInput in, int64_t v0, int64_t v1, const 
     cz = fmaf(N, q[2] - p0[2], cz);
     n += N;
   }
-  n = warp_allsum(n);
-  cx = warp_allsum(cx) / n;
-  cy = warp_allsum(cy) / n;
-  cz = warp_allsum(cz) / n;
+  cx /= n;
+  cy /= n;
+  cz /= n;
   float A[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  for (int64_t o = a0 + lane; o < a1; o += 32) {
+  for (int64_t o = a0; o < a1; ++o) {
     double c[10];
     centred_cluster(in.agg + 10 * o, in.agg_form, c);
     float Sf[6], mf[3], N, q[3], rs[6];
@@ -162,9 +180,6 @@ __global__ void voxel_frames_kernel(LoadInput in, int64_t v0, int64_t v1, const 
     A[4] += fmaf(N * dy, dz, rs[4]);
     A[5] += fmaf(N * dz, dz, rs[5]);
   }
-#pragma unroll
-  for (int k = 0; k < 6; ++k) A[k] = warp_allsum(A[k]);
-  if (lane != 0) return;
   float lam[3], V[9];
   eig3_sym_f(A, lam, V);
   // rows: e1 (largest), e2, n (smallest)
@@ -215,7 +230,8 @@ __device__ void mixed_slot(const LoadInput& in, int64_t o, const double* sref, f
   eig3_sym_f(sf, lam0, v0);  // eigenvectors as rows of v0 (vector c at v0[3c..3c+2])
   // W = V0^T S V0.  The entries of the two smallest directions (W_00,
   // W_01, W_11) are small next to S's largest entries and lose digits to
-  // cancellation in FP32, so they are formed in FP64: W_00 is the normal
+  // cancellation in FP32, so they are formed in double-float arithmetic (~46
+  // bits, from S's FP64 entries; the FP32 eigenvectors are exact): W_00 is the normal
   // variance of a planar cluster, and for a rod-like cluster (two small,
   // nearly equal variances) the voxel normal can be any direction of that
   // pair.  The entries with the largest direction only need absolute
@@ -223,16 +239,31 @@ __device__ void mixed_slot(const LoadInput& in, int64_t o, const double* sref, f
   // rad, a second-order change of the variances).
   float wf[6];
   {
-    const double S[3][3] = {{c[0], c[1], c[2]}, {c[1], c[3], c[4]}, {c[2], c[4], c[5]}};
-    double vd[6];  // v_0, v_1 in FP64 (exact)
+    // S as double-floats: hi the binary32 rounding of each entry, lo the
+    // exact remainder rounded once (one FP64 subtraction per entry)
+    DF Sd[6];
 #pragma unroll
-    for (int q = 0; q < 6; ++q) vd[q] = f32_to_f64(v0[q]);
-    double Sv[2][3];  // S v_k, k = 0, 1 (FP64)
+    for (int q = 0; q < 6; ++q) Sd[q] = DF{sf[q], f64_to_f32(c[q] - f32_to_f64(sf[q]))};
+    const DF S[3][3] = {{Sd[0], Sd[1], Sd[2]}, {Sd[1], Sd[3], Sd[4]}, {Sd[2], Sd[4], Sd[5]}};
+    DF Sv[2][3];  // S v_k, k = 0, 1 (v_k binary32, exact)
+#pragma unroll
     for (int k = 0; k < 2; ++k)
-      for (int r = 0; r < 3; ++r) Sv[k][r] = S[r][0] * vd[3 * k] + S[r][1] * vd[3 * k + 1] + S[r][2] * vd[3 * k + 2];
-    wf[0] = f64_to_f32(vd[0] * Sv[0][0] + vd[1] * Sv[0][1] + vd[2] * Sv[0][2]);
-    wf[1] = f64_to_f32(vd[0] * Sv[1][0] + vd[1] * Sv[1][1] + vd[2] * Sv[1][2]);
-    wf[3] = f64_to_f32(vd[3] * Sv[1][0] + vd[4] * Sv[1][1] + vd[5] * Sv[1][2]);
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        DF acc{0.f, 0.f};
+#pragma unroll
+        for (int q = 0; q < 3; ++q) acc = df_fma(acc, v0[3 * k + q], S[r][q]);
+        Sv[k][r] = acc;
+      }
+    auto dot = [&](int i, int k) {
+      DF acc{0.f, 0.f};
+#pragma unroll
+      for (int r = 0; r < 3; ++r) acc = df_fma(acc, v0[3 * i + r], Sv[k][r]);
+      return __fadd_rn(acc.hi, acc.lo);
+    };
+    wf[0] = dot(0, 0);
+    wf[1] = dot(0, 1);
+    wf[3] = dot(1, 1);
     const float M[3][3] = {{sf[0], sf[1], sf[2]}, {sf[1], sf[3], sf[4]}, {sf[2], sf[4], sf[5]}};
     float T[3];  // S v_2 (FP32)
     for (int r = 0; r < 3; ++r) T[r] = fmaf(M[r][0], v0[6], fmaf(M[r][1], v0[7], M[r][2] * v0[8]));
@@ -402,8 +433,8 @@ cudaError_t build_mixed_voxels(const LoadInput& in, const LayoutBuffers& lb, con
   if (v1 <= v0) return cudaSuccess;
   LoadInput cur = in;
   cur.poses = poses2;  // buffer 0
-  voxel_frames_kernel<<<(unsigned)((v1 - v0 + 3) / 4), 128, 0, stream>>>(cur, v0, v1, mb.sref, lb.vrank, mb.vstate,
-                                                                        mb.vanchor, mb.planes32_2);
+  voxel_frames_kernel<<<(unsigned)((v1 - v0 + 127) / 128), 128, 0, stream>>>(cur, v0, v1, mb.sref, lb.vrank,
+                                                                            mb.vstate, mb.vanchor, mb.planes32_2);
   ++*launches;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || o1 <= o0) return e;
@@ -452,8 +483,8 @@ cudaError_t build_mixed(const LoadInput& in, const LayoutBuffers& lb, const doub
   cur.poses = poses2;  // buffer 0
   const int64_t nv = in.n_voxels;
   if (nv > 0) {
-    voxel_frames_kernel<<<(unsigned)((nv + 3) / 4), 128, 0, stream>>>(cur, 0, nv, mb.sref, lb.vrank, mb.vstate,
-                                                                      mb.vanchor, mb.planes32_2);
+    voxel_frames_kernel<<<(unsigned)((nv + 127) / 128), 128, 0, stream>>>(cur, 0, nv, mb.sref, lb.vrank, mb.vstate,
+                                                                          mb.vanchor, mb.planes32_2);
     ++*launches;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // every slot, padding included, by sorted position (coalesced writes)
