@@ -38,9 +38,10 @@ METRIC = "MM-BA iter/s & plane-obs/s @10k scans; served jobs/s, p99 vs plain FP6
 HBM_PEAK_FALLBACK = 6800.0
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (non-tensor and tensor alike)
 # FP64 voxel pass: floating-point operations per observation in the kernel
-# (an FMA counts as 2): q = R m + t (18), q - a (3), R S R^T (45),
-# N (q - a) (3), accumulation of M (48), sums of N (q - a) and N (4).
-VOXEL_PASS_FLOP_PER_OBS = 121
+# (an FMA counts as 2), with the scatter as its pivoted LDL^T: q = R m + t
+# (18), q - a (3), the columns W of R P^T L (18), D-weighted columns and
+# N (q - a) (12), accumulation of M (48), sums of N (q - a) and N (4).
+VOXEL_PASS_FLOP_PER_OBS = 103
 # bytes one voxel-pass launch must move per observation slot: 10 doubles + a
 # 4-byte scan index (the pose table and per-voxel outputs are small)
 VOXEL_PASS_BYTES_PER_ELEM = 84

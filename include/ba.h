@@ -111,7 +111,8 @@ void ba_config_default(ba_config* cfg);
 ba_status ba_create(const ba_config* cfg, ba_handle** out);
 
 /* Load a problem given as point clusters (Eq. 2), voxel-major CSR.
- *   n_scans >= 1, n_voxels >= 1, n_obs >= 1.
+ *   n_scans >= 1, n_voxels >= 1, n_obs >= n_voxels (else BA_ERR_INVALID_ARG);
+ *   n_scans < 2^29, n_obs < 2^31 (else BA_ERR_CAPACITY).
  *   voxel_offsets: n_voxels + 1 int64, voxel_offsets[0] = 0, strictly
  *     increasing (every voxel has at least one observation), last = n_obs.
  *   obs_scan: n_obs int32 in [0, n_scans).

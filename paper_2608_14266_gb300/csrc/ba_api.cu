@@ -590,6 +590,7 @@ ba_status load_impl(ba_handle* h, int32_t n_scans, int64_t n_voxels, int64_t n_o
 
 ba_status check_sizes(ba_handle* h, int32_t n_scans, int64_t n_voxels, int64_t n_obs, int32_t mem_kind) {
   if (n_scans < 1) return fail(h, BA_ERR_INVALID_ARG, "n_scans must be >= 1");
+  if (n_scans >= (1 << kPermShift)) return fail(h, BA_ERR_CAPACITY, "n_scans must be below 2^29");
   if (n_voxels < 1) return fail(h, BA_ERR_INVALID_ARG, "n_voxels must be >= 1");
   if (n_obs < n_voxels) return fail(h, BA_ERR_INVALID_ARG, "n_obs must be >= n_voxels (one observation per voxel)");
   if (n_obs >= (1ll << 31) || n_voxels >= (1ll << 31))

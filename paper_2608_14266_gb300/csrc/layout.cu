@@ -489,19 +489,26 @@ __global__ void fill_sell_kernel(LoadInput in, const int32_t* vperm, const int32
   const int64_t o0 = real ? in.voxel_off[vperm[p]] : 0;
   for (int64_t k = 0; k < rows; ++k) {
     const int64_t e = base + k * kSlice;
-    double c[10];
-    int32_t scan = 0;
+    double c[10], f[10];
+    uint32_t scan = 0;
     if (k < len) {
       to_centred(in.agg + 10 * (o0 + k), in.agg_form, c);
-      scan = in.obs_scan[o0 + k];
+      // the scatter as its pivoted LDL^T, the mean permuted alike
+      const uint32_t code = ldlt3_pivoted(c, f);
+      int p0, p1, p2;
+      perm_decode(code, p0, p1, p2);
+      f[6] = c[6 + p0];
+      f[7] = c[6 + p1];
+      f[8] = c[6 + p2];
+      f[9] = c[9];
+      scan = (uint32_t)in.obs_scan[o0 + k] | (code << kPermShift);
     } else {
 #pragma unroll
-      for (int q = 0; q < 10; ++q) c[q] = 0.0;
+      for (int q = 0; q < 10; ++q) f[q] = 0.0;
     }
-    if (ve)
 #pragma unroll
-      for (int q = 0; q < 10; ++q) ve[q * n_elems + e] = c[q];
-    ve_scan[e] = scan;
+    for (int q = 0; q < 10; ++q) ve[q * n_elems + e] = f[q];
+    ve_scan[e] = (int32_t)scan;
   }
 }
 

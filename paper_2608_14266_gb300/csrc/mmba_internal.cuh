@@ -14,7 +14,8 @@
 //    consecutive elements.  Rows past a voxel's own length are padding
 //    (never read: vlen bounds the loop).  Cluster values are stored as
 //    structure-of-arrays, component c of element e at ve[c * n_elems + e]:
-//    S (xx, xy, xz, yy, yz, zz), m (x, y, z), N.
+//    the pivoted LDL^T of S (l10, l20, l21, D0, D1, D2), the permuted mean
+//    P m (3), N; the permutation's code sits in the top bits of ve_scan.
 //  * Scan-major copy (the M_s mapper of Algorithm 1): observations sorted
 //    (stably) by scan, scan j owning scan_off[j] .. scan_off[j+1]-1, with
 //    the sorted voxel position of each (se_vox, the M_v mapper) and the
@@ -270,18 +271,32 @@ __device__ __forceinline__ int find_job(const P* prefix, int n_jobs, int64_t b) 
 
 // ---- small FP64 device math ------------------------------------------------
 
-// Symmetric 3x3 eigen-decomposition by cyclic Jacobi rotations (Golub & Van
-// Loan, Matrix Computations, Sec. 8.5).  a = (xx, xy, xz, yy, yz, zz) is
-// overwritten; on return lam[] ascending and vec[3*c + r] = component r of the
-// unit eigenvector of lam[c].  Stops when every off-diagonal entry is below
-// 1e-18 of the geometric mean of its diagonal pair, or after 24 sweeps.
+// Cyclic Jacobi for symmetric 3x3 matrices (Golub & Van Loan, Matrix
+// Computations, Sec. 8.5).
+//
+// One rotation in the (p, q) plane sets apq to zero and rotates the third
+// row/column entries (arp, arq) and the eigenvector estimates vp, vq with it.
+// The tangent of the rotation angle is t = 2e / (1 + sqrt(1 + 4e^2)) with
+// e = apq / (aqq - app).  For |e| < 1e-4 (the usual case once the matrix is
+// nearly diagonal) t is taken from its series e - e^3 + 2e^5 - ... (the
+// Catalan numbers) cut after e^3, relative error below 2e^4 < 2e-16, and
+// c = 1 / sqrt(1 + t^2) from 1 - t^2/2 + 3t^4/8 (error below 5t^6/16, so
+// c^2 + s^2 = 1 to rounding): one division and no square root.
 __device__ __forceinline__ void jacobi_rotate(double& app, double& aqq, double& apq, double& arp, double& arq,
                                               double* vp, double* vq) {
-  double theta = (aqq - app) / (2.0 * apq);
-  double t = fabs(theta) > 1e150 ? 0.5 / theta
-                                 : copysign(1.0, theta) / (fabs(theta) + sqrt(fma(theta, theta, 1.0)));
-  double c = rsqrt(fma(t, t, 1.0));
-  double s = t * c;
+  const double d = aqq - app;
+  double t, c;
+  if (fabs(apq) < 1e-4 * fabs(d)) {
+    const double e = apq / d;
+    t = fma(-e * e, e, e);
+    const double t2 = t * t;
+    c = fma(t2, fma(0.375, t2, -0.5), 1.0);
+  } else {
+    const double theta = d / (2.0 * apq);
+    t = fabs(theta) > 1e150 ? 0.5 / theta : copysign(1.0, theta) / (fabs(theta) + sqrt(fma(theta, theta, 1.0)));
+    c = rsqrt(fma(t, t, 1.0));
+  }
+  const double s = t * c;
   app = fma(-t, apq, app);
   aqq = fma(t, apq, aqq);
   apq = 0.0;
@@ -296,43 +311,12 @@ __device__ __forceinline__ void jacobi_rotate(double& app, double& aqq, double& 
   }
 }
 
+// apq is negligible against its diagonal pair: |apq| <= u sqrt(|app aqq|)
+// with u = 2^-53, compared in squares (eig3_sym scales its matrix so that the
+// largest entry lies in [1, 2), so the squares neither overflow nor lose the
+// entries that matter)
 __device__ __forceinline__ bool jacobi_small(double apq, double app, double aqq) {
-  return apq == 0.0 || fabs(apq) <= 1e-18 * sqrt(fabs(app * aqq));
-}
-
-__device__ inline void eig3_sym(const double* a_in, double lam[3], double vec[9]) {
-  double a00 = a_in[0], a01 = a_in[1], a02 = a_in[2], a11 = a_in[3], a12 = a_in[4], a22 = a_in[5];
-  double v0[3] = {1.0, 0.0, 0.0}, v1[3] = {0.0, 1.0, 0.0}, v2[3] = {0.0, 0.0, 1.0};
-  for (int sweep = 0; sweep < 24; ++sweep) {
-    bool done = true;
-    if (!jacobi_small(a01, a00, a11)) {  // (p, q, r) = (0, 1, 2)
-      jacobi_rotate(a00, a11, a01, a02, a12, v0, v1);
-      done = false;
-    }
-    if (!jacobi_small(a02, a00, a22)) {  // (0, 2, 1)
-      jacobi_rotate(a00, a22, a02, a01, a12, v0, v2);
-      done = false;
-    }
-    if (!jacobi_small(a12, a11, a22)) {  // (1, 2, 0)
-      jacobi_rotate(a11, a22, a12, a01, a02, v1, v2);
-      done = false;
-    }
-    if (done) break;
-  }
-  // sort ascending (stable on ties)
-  double d[3] = {a00, a11, a22};
-  int i0 = 0, i1 = 1, i2 = 2, t;
-  if (d[i1] < d[i0]) { t = i0; i0 = i1; i1 = t; }
-  if (d[i2] < d[i1]) { t = i1; i1 = i2; i2 = t; }
-  if (d[i1] < d[i0]) { t = i0; i0 = i1; i1 = t; }
-  const double* vs[3] = {v0, v1, v2};
-  int order[3] = {i0, i1, i2};
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    lam[c] = d[order[c]];
-#pragma unroll
-    for (int r = 0; r < 3; ++r) vec[3 * c + r] = vs[order[c]][r];
-  }
+  return apq == 0.0 || apq * apq <= 0x1p-106 * fabs(app * aqq);
 }
 
 // FP32 counterpart of eig3_sym for matrices expressed in a frame where they
@@ -409,6 +393,218 @@ __device__ inline void eig3_sym_f(const float* a_in, float lam[3], float vec[9])
     vec[3 + r] = v1[r];
     vec[6 + r] = v2[r];
   }
+}
+
+// Cyclic Jacobi in binary32 from the identity, unsorted: on return F
+// (row-major) is the product of the rotations applied, a proper rotation
+// whose columns approximate the eigenvectors of a.  Stops at binary32
+// resolution (|apq| <= 1e-7 sqrt|app aqq|) or after 6 sweeps.
+__device__ __forceinline__ void jacobi3_frame_f(const float* a_in, float* F) {
+  float a00 = a_in[0], a01 = a_in[1], a02 = a_in[2], a11 = a_in[3], a12 = a_in[4], a22 = a_in[5];
+  float v0[3] = {1.f, 0.f, 0.f}, v1[3] = {0.f, 1.f, 0.f}, v2[3] = {0.f, 0.f, 1.f};
+  auto small = [](float apq, float app, float aqq) {
+    return apq == 0.0f || fabsf(apq) <= 1e-7f * sqrtf(fabsf(app * aqq));
+  };
+  for (int sweep = 0; sweep < 6; ++sweep) {
+    bool done = true;
+    if (!small(a01, a00, a11)) {
+      jacobi_rotate_f(a00, a11, a01, a02, a12, v0, v1);
+      done = false;
+    }
+    if (!small(a02, a00, a22)) {
+      jacobi_rotate_f(a00, a22, a02, a01, a12, v0, v2);
+      done = false;
+    }
+    if (!small(a12, a11, a22)) {
+      jacobi_rotate_f(a11, a22, a12, a01, a02, v1, v2);
+      done = false;
+    }
+    if (done) break;
+  }
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    F[3 * r] = v0[r];
+    F[3 * r + 1] = v1[r];
+    F[3 * r + 2] = v2[r];
+  }
+}
+
+// Symmetric 3x3 eigen-decomposition in FP64.  a = (xx, xy, xz, yy, yz, zz);
+// on return lam[] ascending and vec[3*c + r] = component r of the unit
+// eigenvector of lam[c].
+//
+// The matrix is scaled by a power of two (exact) so that its largest entry
+// lies in [1, 2).  Cyclic Jacobi in binary32 on its rounding gives a rotation
+// close to the eigenvectors; its quaternion q, turned into a rotation matrix
+// Q with the exact normalisation 2 / |q|^2, is orthogonal to FP64 rounding,
+// and Q^T A Q is nearly diagonal (off-diagonal entries of the order of the
+// binary32 rounding of A, against the eigenvalue gaps).  FP64 Jacobi sweeps
+// finish from there, with rotations of the small-angle form, in one to three
+// sweeps instead of four to six from the identity (GB300 runs FP64 at 1/64 of
+// its FP32 rate, so the binary32 sweeps cost little).  Stops when every
+// off-diagonal entry is negligible (jacobi_small) or after 24 sweeps; if the
+// binary32 frame is not usable (non-finite), the sweeps start from the
+// identity.
+__device__ inline void eig3_sym(const double* a_in, double lam[3], double vec[9]) {
+  int emax = 0;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const int ek = (__double2hiint(a_in[k]) >> 20) & 0x7ff;
+    emax = ek > emax ? ek : emax;
+  }
+  int es = 2046 - emax;  // biased exponent of the scale that takes the largest entry to [1, 2)
+  es = es < 1 ? 1 : (es > 2045 ? 2045 : es);
+  const double sc = __hiloint2double(es << 20, 0);
+  const double isc = __hiloint2double((2046 - es) << 20, 0);  // 1 / sc
+  const double A[6] = {a_in[0] * sc, a_in[1] * sc, a_in[2] * sc, a_in[3] * sc, a_in[4] * sc, a_in[5] * sc};
+  float af[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) af[k] = f64_to_f32(A[k]);
+  float F[9], qf[4];
+  jacobi3_frame_f(af, F);
+  mat_to_quat<float>(F, qf);
+  const float nf = qf[0] * qf[0] + qf[1] * qf[1] + qf[2] * qf[2] + qf[3] * qf[3];
+  if (!(nf > 0.999f && nf < 1.001f)) {
+    qf[0] = 1.0f;
+    qf[1] = qf[2] = qf[3] = 0.0f;
+  }
+  const double w = f32_to_f64(qf[0]), x = f32_to_f64(qf[1]), y = f32_to_f64(qf[2]), z = f32_to_f64(qf[3]);
+  const double n2 = fma(w, w, fma(x, x, fma(y, y, z * z)));
+  // 2 / n2: n2 is within 1e-6 of 1, so r0 = 2 - n2 approximates 1 / n2 to
+  // (n2 - 1)^2, and one Newton step for the reciprocal, r0 + r0 (1 - n2 r0),
+  // leaves an error of the order of (n2 - 1)^4, below the FP64 rounding
+  const double r0 = 2.0 - n2;
+  const double s2 = 2.0 * fma(r0, fma(-n2, r0, 1.0), r0);
+  // products of binary32 values are exact in FP64
+  const double xx = x * x, yy = y * y, zz = z * z, xy = x * y, xz = x * z, yz = y * z, wx = w * x, wy = w * y,
+               wz = w * z;
+  const double Q[9] = {fma(-s2, yy + zz, 1.0), s2 * (xy - wz),          s2 * (xz + wy),
+                       s2 * (xy + wz),          fma(-s2, xx + zz, 1.0), s2 * (yz - wx),
+                       s2 * (xz - wy),          s2 * (yz + wx),          fma(-s2, xx + yy, 1.0)};
+  // B = Q^T A Q (upper triangle), through T = A Q
+  double T[9];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    T[c] = fma(A[0], Q[c], fma(A[1], Q[3 + c], A[2] * Q[6 + c]));
+    T[3 + c] = fma(A[1], Q[c], fma(A[3], Q[3 + c], A[4] * Q[6 + c]));
+    T[6 + c] = fma(A[2], Q[c], fma(A[4], Q[3 + c], A[5] * Q[6 + c]));
+  }
+  double b00 = fma(Q[0], T[0], fma(Q[3], T[3], Q[6] * T[6]));
+  double b01 = fma(Q[0], T[1], fma(Q[3], T[4], Q[6] * T[7]));
+  double b02 = fma(Q[0], T[2], fma(Q[3], T[5], Q[6] * T[8]));
+  double b11 = fma(Q[1], T[1], fma(Q[4], T[4], Q[7] * T[7]));
+  double b12 = fma(Q[1], T[2], fma(Q[4], T[5], Q[7] * T[8]));
+  double b22 = fma(Q[2], T[2], fma(Q[5], T[5], Q[8] * T[8]));
+  double v0[3] = {1.0, 0.0, 0.0}, v1[3] = {0.0, 1.0, 0.0}, v2[3] = {0.0, 0.0, 1.0};
+  for (int sweep = 0; sweep < 24; ++sweep) {
+    bool done = true;
+    if (!jacobi_small(b01, b00, b11)) {  // (p, q, r) = (0, 1, 2)
+      jacobi_rotate(b00, b11, b01, b02, b12, v0, v1);
+      done = false;
+    }
+    if (!jacobi_small(b02, b00, b22)) {  // (0, 2, 1)
+      jacobi_rotate(b00, b22, b02, b01, b12, v0, v2);
+      done = false;
+    }
+    if (!jacobi_small(b12, b11, b22)) {  // (1, 2, 0)
+      jacobi_rotate(b11, b22, b12, b01, b02, v1, v2);
+      done = false;
+    }
+    if (done) break;
+  }
+  // ascending, stable on ties; swaps of values keep everything in registers
+  double d0 = b00, d1 = b11, d2 = b22;
+  auto cswap = [](double& da, double& db, double* va, double* vb) {
+    if (db < da) {
+      const double t = da;
+      da = db;
+      db = t;
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        const double u = va[r];
+        va[r] = vb[r];
+        vb[r] = u;
+      }
+    }
+  };
+  cswap(d0, d1, v0, v1);
+  cswap(d1, d2, v1, v2);
+  cswap(d0, d1, v0, v1);
+  lam[0] = d0 * isc;
+  lam[1] = d1 * isc;
+  lam[2] = d2 * isc;
+  // eigenvectors back in the input axes: Q v
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    vec[r] = fma(Q[3 * r], v0[0], fma(Q[3 * r + 1], v0[1], Q[3 * r + 2] * v0[2]));
+    vec[3 + r] = fma(Q[3 * r], v1[0], fma(Q[3 * r + 1], v1[1], Q[3 * r + 2] * v1[2]));
+    vec[6 + r] = fma(Q[3 * r], v2[0], fma(Q[3 * r + 1], v2[1], Q[3 * r + 2] * v2[2]));
+  }
+}
+
+// ---- FP64 slots: pivoted LDL^T of each observation's scatter ----
+//
+// The FP64 voxel pass stores an observation's scatter S (symmetric positive
+// semidefinite) as P S P^T = L D L^T, with P the permutation of complete
+// (diagonal) pivoting, largest remaining diagonal first, and L unit lower
+// triangular (|l| <= 1 for a semidefinite S; Higham, Accuracy and Stability
+// of Numerical Algorithms, Sec. 10.3).  For a scan rotation R, with W the
+// columns of R P^T L,
+//   R S R^T = D0 W0 W0^T + D1 W1 W1^T + D2 W2 W2^T,
+// W0 = R_pi0 + l10 R_pi1 + l20 R_pi2, W1 = R_pi1 + l21 R_pi2, W2 = R_pi2
+// (R_k the k-th column of R): 9 FMAs instead of the 27 of R S, and no square
+// root (a D entry a rounding below zero is kept as it is).  The mean is
+// stored permuted too (P m), so that R m = sum_a R_pia (P m)_a.  The
+// permutation's code (0..5) sits in the top bits of the slot's scan index.
+constexpr int kPermShift = 29;                      // scan index bits below, code above
+constexpr uint32_t kScanMask = (1u << kPermShift) - 1u;
+// 4 bits per code: pi0 | pi1 << 2 (pi2 = 3 - pi0 - pi1); codes 0..5 are the
+// permutations (0 1 2), (0 2 1), (1 0 2), (1 2 0), (2 0 1), (2 1 0)
+constexpr uint32_t kPermTable = 0x629184u;
+
+__device__ __forceinline__ void perm_decode(uint32_t code, int& p0, int& p1, int& p2) {
+  const uint32_t f = (kPermTable >> (4u * code)) & 15u;
+  p0 = (int)(f & 3u);
+  p1 = (int)(f >> 2);
+  p2 = 3 - p0 - p1;
+}
+
+// S = (xx, xy, xz, yy, yz, zz) -> out = (l10, l20, l21, D0, D1, D2); returns
+// the permutation's code.  A zero pivot leaves its column of L zero.  For a
+// semidefinite S every |l| <= 1; where rounding breaks that (a pivot and the
+// entries it divides are all at the rounding level of S, as in the Schur
+// complement of a rank-one scatter) the multiplier is clamped to [-1, 1],
+// which changes the factored matrix only at that level and keeps the terms
+// D_a W_a W_a^T from growing past |S|.
+__device__ __forceinline__ double ldlt_mult(double x, double d) {
+  return d > 0.0 ? fmin(fmax(x / d, -1.0), 1.0) : 0.0;
+}
+
+__device__ inline uint32_t ldlt3_pivoted(const double* S, double* out) {
+  const double Sm[3][3] = {{S[0], S[1], S[2]}, {S[1], S[3], S[4]}, {S[2], S[4], S[5]}};
+  int p0 = 0;
+  if (Sm[1][1] > Sm[p0][p0]) p0 = 1;
+  if (Sm[2][2] > Sm[p0][p0]) p0 = 2;
+  const int ra = p0 == 0 ? 1 : 0, rb = p0 == 2 ? 1 : 2;  // the two others, ascending
+  const double D0 = Sm[p0][p0];
+  const double la = ldlt_mult(Sm[ra][p0], D0), lb = ldlt_mult(Sm[rb][p0], D0);
+  // Schur complement of the pivot on the remaining pair
+  const double saa = fma(-la * D0, la, Sm[ra][ra]), sbb = fma(-lb * D0, lb, Sm[rb][rb]);
+  const double sab = fma(-la * D0, lb, Sm[ra][rb]);
+  const bool a_first = !(sbb > saa);
+  const int p1 = a_first ? ra : rb, p2 = a_first ? rb : ra;
+  const double D1 = a_first ? saa : sbb, s22 = a_first ? sbb : saa;
+  const double l10 = a_first ? la : lb, l20 = a_first ? lb : la;
+  const double l21 = ldlt_mult(sab, D1);
+  out[0] = l10;
+  out[1] = l20;
+  out[2] = l21;
+  out[3] = D0;
+  out[4] = D1;
+  out[5] = fma(-l21 * D1, l21, s22);
+  (void)p2;
+  // code of (p0, p1)
+  return p0 == 0 ? (p1 == 1 ? 0u : 1u) : p0 == 1 ? (p1 == 0 ? 2u : 3u) : (p1 == 0 ? 4u : 5u);
 }
 
 // Per-scan FP32 table entry for the mixed path from an FP64 pose P and its
