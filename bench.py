@@ -380,7 +380,12 @@ def run_reference(args):
 def measure(mm, torch, scene, dev_inputs, precision, steps, warmup, S, barrier, local, profile=True):
     """Times `steps` LM iterations (solves of S iterations from the initial
     poses, state reset outside the timed region) with CUDA events on the
-    library's stream; returns the timing, the kernel breakdown and clocks."""
+    library's stream; returns the timing, the kernel breakdown and clocks.
+
+    The timed pass records no event between the iteration's launches (each
+    event record between two kernels adds its own gap, ~4 us per launch);
+    with profile=True a second timed pass of the same steps brackets every
+    launch with events for the per-kernel times."""
     voxel_off, obs_scan, agg, pose0 = dev_inputs
     stream = torch.cuda.current_stream()
     ba = mm.BundleAdjuster(cuda_stream=stream, precision=precision)
@@ -402,38 +407,45 @@ def measure(mm, torch, scene, dev_inputs, precision, steps, warmup, S, barrier, 
     while left > 0:
         reps.append(min(S, left))
         left -= reps[-1]
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in reps]
-    accepted = 0
-    launches = 0
-    acc0 = ba.stats()["accepted"]
+
+    def timed_pass(kernel_events):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in reps]
+        accepted = launches = 0
+        acc0 = ba.stats()["accepted"]
+        ba.profile(kernel_events)
+        for (e0, e1), n in zip(ev, reps):
+            barrier()
+            torch.cuda.synchronize()
+            l0 = ba.kernel_launches()
+            e0.record(stream)
+            ba.iterate(n, stats=False)
+            e1.record(stream)
+            launches += ba.kernel_launches() - l0
+            torch.cuda.synchronize()
+            acc1 = ba.stats()["accepted"]
+            accepted += acc1 - acc0
+            reset()
+            acc0 = ba.stats()["accepted"]
+        torch.cuda.synchronize()
+        prof = ba.profile_read() if kernel_events else None
+        ba.profile(False)
+        return sum(e0.elapsed_time(e1) for e0, e1 in ev), accepted, launches, prof
+
     clocks = ClockSampler(_gpu_id(torch, local)) if profile else None
     if profile:
         time.sleep(0.3)
-    ba.profile(profile)
     torch.cuda.nvtx.range_push("timed")
     t_wall0 = time.time()
-    for (e0, e1), n in zip(ev, reps):
-        barrier()
-        torch.cuda.synchronize()
-        l0 = ba.kernel_launches()
-        e0.record(stream)
-        ba.iterate(n, stats=False)
-        e1.record(stream)
-        launches += ba.kernel_launches() - l0
-        torch.cuda.synchronize()
-        acc1 = ba.stats()["accepted"]
-        accepted += acc1 - acc0
-        reset()
-        acc0 = ba.stats()["accepted"]
-    torch.cuda.synchronize()
+    ms, accepted, launches, _ = timed_pass(False)
     t_wall1 = time.time()
     torch.cuda.nvtx.range_pop()
-    prof = ba.profile_read() if profile else None
-    ba.profile(False)
     clk = clocks.stop(t_wall0, t_wall1) if clocks else None
-    ms = sum(e0.elapsed_time(e1) for e0, e1 in ev)
+    prof, ms_events = None, None
+    if profile:
+        ms_events, _, _, prof = timed_pass(True)
     ba.close()
-    return {"ms": ms, "accepted": accepted, "launches": launches, "prof": prof, "clocks": clk}
+    return {"ms": ms, "accepted": accepted, "launches": launches, "prof": prof, "clocks": clk,
+            "ms_with_kernel_events": ms_events}
 
 
 def roofline_for(precision, scene, prof, workload):
@@ -577,6 +589,9 @@ def run_ours(args):
                                                 f"{S} iterations + ba_poses to host, per job"},
         "gpu_launches": int(res["launches"]),
         "kernel_ms": {k: {"total_ms": v[0], "launches": v[1]} for k, v in prof.items()},
+        "kernel_events": {"pass": "a second timed pass of the same steps with events around every launch "
+                                  "(the kernel_ms and the roofline's launch times)",
+                          "ms_per_step": res["ms_with_kernel_events"] / args.steps},
         "roofline": roofline,
         "cpu_baseline": cpu,
     }

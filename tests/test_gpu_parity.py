@@ -254,6 +254,84 @@ def test_edge_cases_match_oracle(mm, case):
             np.testing.assert_array_equal(ba.poses()[5:], init[5:])
 
 
+def _degenerate_problem(rng, n_scans=6, n_vox=64):
+    """Planar voxels whose clusters are rank-deficient: one point (zero
+    scatter), two points (rank one), points on a line, points on a line
+    with noise along the plane normal (rank two), and noise-free points on
+    the plane laid out so that the scan frame's z axis is the normal (the
+    scatter's z row zero up to rounding)."""
+    import oracle as orc
+    poses = np.zeros((n_scans, 12))
+    for j in range(n_scans):
+        poses[j, :9] = orc.exp_so3(rng.normal(size=3)).ravel()
+        poses[j, 9:] = rng.uniform(0, 20, 3)
+    lens = rng.integers(3, 9, n_vox)
+    voxel_off = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    obs_scan = np.empty(int(voxel_off[-1]), np.int32)
+    pts, npts = [], []
+    for i, L in enumerate(lens):
+        scans = rng.choice(n_scans, size=L, replace=L > n_scans)
+        R0 = poses[scans[0], :9].reshape(3, 3)
+        n = R0[:, 2] if i % 2 else rng.normal(size=3)  # odd voxels: normal along scan z of their first scan
+        n /= np.linalg.norm(n)
+        e1 = np.cross(n, rng.normal(size=3))
+        e1 /= np.linalg.norm(e1)
+        e2 = np.cross(n, e1)
+        c = rng.uniform(0, 20, 3)
+        for k in range(L):
+            o = voxel_off[i] + k
+            obs_scan[o] = scans[k]
+            shape = (i + k) % 5
+            if shape == 0:  # one point
+                ab = rng.uniform(-0.5, 0.5, (1, 2))
+                off = rng.normal(0, 0.01, (1, 1))
+            elif shape == 1:  # two points
+                ab = rng.uniform(-0.5, 0.5, (2, 2))
+                off = rng.normal(0, 0.01, (2, 1))
+            elif shape == 2:  # on a line
+                t = rng.uniform(-0.5, 0.5, (7, 1))
+                ab = t * rng.normal(size=(1, 2))
+                off = np.zeros((7, 1))
+            elif shape == 3:  # a line, noise along the normal
+                t = rng.uniform(-0.5, 0.5, (7, 1))
+                ab = t * rng.normal(size=(1, 2))
+                off = rng.normal(0, 0.01, (7, 1))
+            else:  # on the plane, no noise
+                ab = rng.uniform(-0.5, 0.5, (9, 2))
+                off = np.zeros((9, 1))
+            w = c + ab[:, :1] * e1 + ab[:, 1:] * e2 + off * n
+            P = poses[scans[k]]
+            pts.append((w - P[9:]) @ P[:9].reshape(3, 3))
+            npts.append(len(w))
+    pts = np.concatenate(pts)
+    po = np.concatenate([[0], np.cumsum(npts)]).astype(np.int64)
+    init = poses.copy()
+    for j in range(1, n_scans):
+        init[j] = orc.retract(poses[j], np.concatenate([rng.normal(0, 0.005, 3), rng.normal(0, 0.02, 3)]))
+    return voxel_off, obs_scan, po, pts, init
+
+
+def test_rank_deficient_clusters_match_oracle(mm):
+    """Clusters whose scatter is zero, rank one or rank two: the voxel pass's
+    factored scatters (pivoted LDL^T) and its eigen-solve against the oracle,
+    then five LM iterations."""
+    rng = np.random.default_rng(2024)
+    n_scans = 6
+    voxel_off, obs_scan, po, pts, init = _degenerate_problem(rng, n_scans)
+    cen = oracle.points_to_centred(po, pts)
+    lm = oracle.LM(oracle.ObsProblem(n_scans, voxel_off, obs_scan, cen), init)
+    with mm.BundleAdjuster() as ba:
+        ba.load_points(n_scans, voxel_off, obs_scan, po, pts, init)
+        assert ba.cost() == pytest.approx(lm.cost, rel=COST_TOL)
+        _compare_planes(ba.planes(), lm.planes)
+        for k in range(5):
+            st = ba.iterate(1)
+            assert bool(st["last_accepted"]) == lm.step(), k
+            assert st["cost"] == pytest.approx(lm.cost, rel=COST_TOL)
+            r, t = pose_errors(ba.poses(), lm.poses)
+            assert r < ROT_TOL and t < TRANS_TOL, (k, r, t)
+
+
 def _expect_invalid(mm, fn, match):
     with pytest.raises(mm.BAError) as ei:
         fn()
