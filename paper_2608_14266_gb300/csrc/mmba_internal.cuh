@@ -321,14 +321,27 @@ __device__ __forceinline__ bool jacobi_small(double apq, double app, double aqq)
 
 // FP32 counterpart of eig3_sym for matrices expressed in a frame where they
 // are close to diagonal (small off-diagonal entries keep the smallest
-// eigenvalue relatively accurate); at most 8 sweeps.
+// eigenvalue relatively accurate); at most 8 sweeps.  The rotation takes the
+// small-angle form of jacobi_rotate when |apq| < 0.01 |aqq - app| (then
+// t = e - e^3 is within 2e^4 < 2e-8 of the exact tangent and
+// c = 1 - t^2/2 + 3t^4/8 within 5t^6/16 < 1e-12 of 1 / sqrt(1 + t^2): an
+// orthogonal rotation to binary32 rounding, from one approximate division);
+// the stopping test compares squares.
 __device__ __forceinline__ void jacobi_rotate_f(float& app, float& aqq, float& apq, float& arp, float& arq, float* vp,
                                                 float* vq) {
-  float theta = (aqq - app) / (2.0f * apq);
-  float t = fabsf(theta) > 1e18f ? 0.5f / theta
-                                 : copysignf(1.0f, theta) / (fabsf(theta) + sqrtf(fmaf(theta, theta, 1.0f)));
-  float c = rsqrtf(fmaf(t, t, 1.0f));
-  float s = t * c;
+  const float d = aqq - app;
+  float t, c;
+  if (fabsf(apq) < 1e-2f * fabsf(d)) {
+    const float e = __fdividef(apq, d);
+    t = fmaf(-e * e, e, e);
+    const float t2 = t * t;
+    c = fmaf(t2, fmaf(0.375f, t2, -0.5f), 1.0f);
+  } else {
+    const float theta = d / (2.0f * apq);
+    t = fabsf(theta) > 1e18f ? 0.5f / theta : copysignf(1.0f, theta) / (fabsf(theta) + sqrtf(fmaf(theta, theta, 1.0f)));
+    c = rsqrtf(fmaf(t, t, 1.0f));
+  }
+  const float s = t * c;
   app = fmaf(-t, apq, app);
   aqq = fmaf(t, apq, aqq);
   apq = 0.0f;
@@ -343,8 +356,9 @@ __device__ __forceinline__ void jacobi_rotate_f(float& app, float& aqq, float& a
   }
 }
 
+// |apq| <= 1e-9 sqrt|app aqq|, in squares
 __device__ __forceinline__ bool jacobi_small_f(float apq, float app, float aqq) {
-  return apq == 0.0f || fabsf(apq) <= 1e-9f * sqrtf(fabsf(app * aqq));
+  return apq == 0.0f || apq * apq <= 1e-18f * fabsf(app * aqq);
 }
 
 __device__ inline void eig3_sym_f(const float* a_in, float lam[3], float vec[9]) {
@@ -402,9 +416,7 @@ __device__ inline void eig3_sym_f(const float* a_in, float lam[3], float vec[9])
 __device__ __forceinline__ void jacobi3_frame_f(const float* a_in, float* F) {
   float a00 = a_in[0], a01 = a_in[1], a02 = a_in[2], a11 = a_in[3], a12 = a_in[4], a22 = a_in[5];
   float v0[3] = {1.f, 0.f, 0.f}, v1[3] = {0.f, 1.f, 0.f}, v2[3] = {0.f, 0.f, 1.f};
-  auto small = [](float apq, float app, float aqq) {
-    return apq == 0.0f || fabsf(apq) <= 1e-7f * sqrtf(fabsf(app * aqq));
-  };
+  auto small = [](float apq, float app, float aqq) { return apq == 0.0f || apq * apq <= 1e-14f * fabsf(app * aqq); };
   for (int sweep = 0; sweep < 6; ++sweep) {
     bool done = true;
     if (!small(a01, a00, a11)) {
