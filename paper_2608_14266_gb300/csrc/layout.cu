@@ -702,25 +702,59 @@ cudaError_t build_layout(const LoadInput& in, int max_len, bool fill_f64, bool d
 // shifted by the observation's first point p0: with d = p - p0,
 //   m = p0 + (sum d) / N,   S = sum d d^T - (sum d)(sum d)^T / N,
 // algebraically the mean and the scatter about it (Eq. 2 fixes the sums, not
-// their order).  Per point 12 FP64 operations, per observation one
-// reciprocal and one shuffle level: GB300's FP64 rate is 1/64 of FP32 and its
-// FP64 warp instructions cost the same with idle lanes, so few lanes per
-// observation and one pass keep the FP64 instruction count low.
+// their order).
+//
+// The sums are exact integer sums in fixed point.  An observation's scale is
+// 2^-F with F = 1076 - E0, E0 the largest biased binary exponent of p0's
+// coordinates: p0's largest coordinate then has its last bit at 2^-F, every
+// coordinate of that size or larger (up to 2^9 times) is an exact integer
+// multiple of 2^-F, and smaller ones are rounded to it (an error below half
+// the last bit of p0's largest coordinate, the resolution of FP64 arithmetic
+// on these points).  d, sum d and sum d d^T are then 64- and 128-bit integer
+// sums with no rounding at all, on the integer pipe; GB300's FP64 pipe (1/64
+// of FP32) only converts the nine sums and forms m and S once per
+// observation.  An observation whose points do not fit (a coordinate over 2^9
+// times p0's largest, a spread over 2^56 steps, more than 2^14 points, or a
+// first point at the origin) takes the same shifted sums in FP64.
 // ============================================================================
 constexpr int kAggLanes = 2;
 
-__global__ void aggregate_points_kernel(int64_t n_obs, const int64_t* __restrict__ off,
-                                        const double* __restrict__ pts, double* __restrict__ out) {
-  const int64_t o = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kAggLanes;
-  const int sub = threadIdx.x & (kAggLanes - 1);
-  const unsigned mask = 0x3u << (threadIdx.x & 30);  // the two lanes of this observation
-  if (o >= n_obs) return;  // both lanes of a pair leave together
-  const int64_t a = off[o], b = off[o + 1];
-  double* r = out + 10 * o;
-  if (b <= a) {
-    for (int k = sub; k < 10; k += kAggLanes) r[k] = 0.0;
-    return;
+// round(p 2^F) to the nearest integer (halves away from zero); ok is cleared
+// when the result would reach 2^62
+__device__ __forceinline__ long long fix_round(double p, int F, bool& ok) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(p);
+  const int E = (int)((b >> 52) & 0x7ffu);
+  const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  const int sh = E - 1075 + F;
+  unsigned long long v = 0;
+  if (E != 0) {  // zero and subnormal values are below the resolution
+    if (sh >= 0) {
+      ok = ok && sh <= 9;
+      v = m << (sh & 15);
+    } else if (sh > -63) {
+      const int r = -sh;
+      v = (m + (1ull << (r - 1))) >> r;
+    }
   }
+  return (b >> 63) ? -(long long)v : (long long)v;
+}
+
+__device__ __forceinline__ double i128_to_double(__int128 v) {
+  const bool neg = v < 0;
+  const unsigned __int128 u = neg ? (unsigned __int128)(-v) : (unsigned __int128)v;
+  const double r = fma((double)(unsigned long long)(u >> 64), 0x1p64, (double)(unsigned long long)u);
+  return neg ? -r : r;
+}
+
+__device__ __forceinline__ __int128 shfl_xor_i128(unsigned mask, __int128 v, int lane) {
+  const unsigned long long lo = (unsigned long long)v, hi = (unsigned long long)((unsigned __int128)v >> 64);
+  const unsigned long long lo2 = __shfl_xor_sync(mask, lo, lane), hi2 = __shfl_xor_sync(mask, hi, lane);
+  return (__int128)(((unsigned __int128)hi2 << 64) | lo2);
+}
+
+// the shifted sums in FP64 (observations the fixed point does not fit)
+__device__ void aggregate_f64(int64_t a, int64_t b, int sub, unsigned mask, const double* __restrict__ pts,
+                              double* __restrict__ r) {
   const double p0x = pts[3 * a], p0y = pts[3 * a + 1], p0z = pts[3 * a + 2];
   double sx = 0.0, sy = 0.0, sz = 0.0;
   double c00 = 0.0, c01 = 0.0, c02 = 0.0, c11 = 0.0, c12 = 0.0, c22 = 0.0;
@@ -745,7 +779,6 @@ __global__ void aggregate_points_kernel(int64_t n_obs, const int64_t* __restrict
   c11 += __shfl_xor_sync(mask, c11, 1);
   c12 += __shfl_xor_sync(mask, c12, 1);
   c22 += __shfl_xor_sync(mask, c22, 1);
-  // both lanes hold the sums; each writes half of the record
   const double n = (double)(b - a);
   const double rn = 1.0 / n;
   const double dx = sx * rn, dy = sy * rn, dz = sz * rn;
@@ -760,6 +793,79 @@ __global__ void aggregate_points_kernel(int64_t n_obs, const int64_t* __restrict
     r[6] = p0x + dx;
     r[7] = p0y + dy;
     r[8] = p0z + dz;
+    r[9] = n;
+  }
+}
+
+__global__ void aggregate_points_kernel(int64_t n_obs, const int64_t* __restrict__ off,
+                                        const double* __restrict__ pts, double* __restrict__ out) {
+  const int64_t o = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kAggLanes;
+  const int sub = threadIdx.x & (kAggLanes - 1);
+  const unsigned mask = 0x3u << (threadIdx.x & 30);  // the two lanes of this observation
+  if (o >= n_obs) return;  // both lanes of a pair leave together
+  const int64_t a = off[o], b = off[o + 1];
+  double* r = out + 10 * o;
+  if (b <= a) {
+    for (int k = sub; k < 10; k += kAggLanes) r[k] = 0.0;
+    return;
+  }
+  const double p0x = pts[3 * a], p0y = pts[3 * a + 1], p0z = pts[3 * a + 2];
+  int E0 = (__double2hiint(p0x) >> 20) & 0x7ff;
+  E0 = max(E0, (__double2hiint(p0y) >> 20) & 0x7ff);
+  E0 = max(E0, (__double2hiint(p0z) >> 20) & 0x7ff);
+  const int F = 1076 - E0;
+  bool ok = E0 != 0 && b - a <= (1 << 14);
+  const long long X0x = fix_round(p0x, F, ok), X0y = fix_round(p0y, F, ok), X0z = fix_round(p0z, F, ok);
+  __int128 s1x = 0, s1y = 0, s1z = 0, s00 = 0, s01 = 0, s02 = 0, s11 = 0, s12 = 0, s22 = 0;
+  constexpr long long kMaxD = 1ll << 56;
+  for (int64_t k = a + sub; k < b && ok; k += kAggLanes) {
+    const long long dx = fix_round(pts[3 * k], F, ok) - X0x;
+    const long long dy = fix_round(pts[3 * k + 1], F, ok) - X0y;
+    const long long dz = fix_round(pts[3 * k + 2], F, ok) - X0z;
+    ok = ok && dx > -kMaxD && dx < kMaxD && dy > -kMaxD && dy < kMaxD && dz > -kMaxD && dz < kMaxD;
+    s1x += dx;
+    s1y += dy;
+    s1z += dz;
+    s00 += (__int128)dx * dx;
+    s01 += (__int128)dx * dy;
+    s02 += (__int128)dx * dz;
+    s11 += (__int128)dy * dy;
+    s12 += (__int128)dy * dz;
+    s22 += (__int128)dz * dz;
+  }
+  // both lanes take the shuffle (a short-circuit would skip it on one of them)
+  const int partner_ok = __shfl_xor_sync(mask, (int)ok, 1);
+  ok = ok && partner_ok != 0;
+  if (!ok) {
+    aggregate_f64(a, b, sub, mask, pts, r);
+    return;
+  }
+  s1x += shfl_xor_i128(mask, s1x, 1);
+  s1y += shfl_xor_i128(mask, s1y, 1);
+  s1z += shfl_xor_i128(mask, s1z, 1);
+  s00 += shfl_xor_i128(mask, s00, 1);
+  s01 += shfl_xor_i128(mask, s01, 1);
+  s02 += shfl_xor_i128(mask, s02, 1);
+  s11 += shfl_xor_i128(mask, s11, 1);
+  s12 += shfl_xor_i128(mask, s12, 1);
+  s22 += shfl_xor_i128(mask, s22, 1);
+  // both lanes hold the exact sums; each forms and writes half of the record
+  const double n = (double)(b - a);
+  const double rn = 1.0 / n;
+  const double sx = ldexp(i128_to_double(s1x), -F), sy = ldexp(i128_to_double(s1y), -F),
+               sz = ldexp(i128_to_double(s1z), -F);
+  const double dx = sx * rn, dy = sy * rn, dz = sz * rn;
+  if (sub == 0) {
+    r[0] = fma(-sx, dx, ldexp(i128_to_double(s00), -2 * F));
+    r[1] = fma(-sx, dy, ldexp(i128_to_double(s01), -2 * F));
+    r[2] = fma(-sx, dz, ldexp(i128_to_double(s02), -2 * F));
+    r[3] = fma(-sy, dy, ldexp(i128_to_double(s11), -2 * F));
+    r[4] = fma(-sy, dz, ldexp(i128_to_double(s12), -2 * F));
+  } else {
+    r[5] = fma(-sz, dz, ldexp(i128_to_double(s22), -2 * F));
+    r[6] = ldexp((double)X0x, -F) + dx;
+    r[7] = ldexp((double)X0y, -F) + dy;
+    r[8] = ldexp((double)X0z, -F) + dz;
     r[9] = n;
   }
 }

@@ -60,6 +60,58 @@ def test_point_clusters_match_oracle(mm):
     assert np.all(np.abs(got[:, :6] - cen[:, :6]) <= 1e-13 * scale)
 
 
+def test_point_clusters_edge_cases_match_oracle(mm):
+    """Clusters the fixed-point sums do not fit, next to ones they do: an
+    observation whose only far point sits on the second lane of its pair, a
+    first point at the origin, a tiny first point with metre-sized others,
+    more than 2^14 points, points near the scan origin with a 3 m spread,
+    coordinates crossing zero, millimetre clusters, far clusters (30 km), one
+    and two points.  Checked against the oracle within its own FP64 rounding
+    (eps times the coordinates' size per term)."""
+    import torch
+    rng = np.random.default_rng(11)
+    obs = []
+    base = rng.normal(0, 0.3, (8, 3)) + np.array([40.0, -20.0, 5.0])
+    far = base.copy()
+    far[3] += np.array([0.0, 900.0, 0.0])  # |d| past the bound, handled by lane 1
+    obs += [far, base]
+    z = rng.normal(0, 0.5, (12, 3))
+    z[0] = 0.0
+    obs.append(z)  # first point at the origin
+    t = rng.normal(0, 1.0, (10, 3))
+    t[0] = np.array([1e-6, -2e-6, 3e-6])
+    obs.append(t)  # first point far smaller than the others
+    obs.append(rng.normal(0, 0.5, (20000, 3)) + np.array([10.0, 10.0, 2.0]))  # more than 2^14 points
+    obs.append(rng.uniform(-3.0, 3.0, (40, 3)))  # near the origin, 3 m spread
+    c = rng.normal(0, 0.4, (33, 3))
+    c[:, 0] += 0.05
+    obs.append(c)  # x crossing zero
+    obs.append(rng.normal(0, 1e-4, (25, 3)) + 1e-3)  # millimetre cluster
+    obs.append(rng.normal(0, 1.0, (30, 3)) + np.array([3.0e4, -2.5e4, 10.0]))  # 30 km away
+    obs.append(np.array([[1.5, -2.5, 0.25]]))
+    obs.append(np.array([[1.5, -2.5, 0.25], [1.75, -2.0, 0.5]]))
+    for _ in range(40):
+        obs.append(rng.normal(0, 0.3, (int(rng.integers(3, 64)), 3)) + rng.uniform(-200, 200, 3))
+    po = np.concatenate([[0], np.cumsum([len(o) for o in obs])]).astype(np.int64)
+    pts = np.concatenate(obs)
+    dev = torch.device("cuda")
+    out = torch.empty((len(obs), 10), dtype=torch.float64, device=dev)
+    mm.ba_aggregate_points(torch.from_numpy(po).to(dev), torch.from_numpy(pts).to(dev), out)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    ref = oracle.points_to_centred(po, pts)
+    np.testing.assert_array_equal(got[:, 9], ref[:, 9])
+    eps = np.finfo(np.float64).eps
+    for i, o in enumerate(obs):
+        big = np.abs(o).max()
+        spread = np.ptp(o, axis=0).max() if len(o) > 1 else 0.0
+        n = len(o)
+        assert np.abs(got[i, 6:9] - ref[i, 6:9]).max() <= 1e-13 + 4 * n * eps * big, i
+        scale = max(np.abs(ref[i, :6]).max(), 1e-300)
+        tol = 1e-13 * scale + 8 * n * eps * big * spread
+        assert np.abs(got[i, :6] - ref[i, :6]).max() <= tol, (i, got[i], ref[i])
+
+
 @pytest.mark.parametrize("which", ["init", "gt"])
 def test_voxel_pass_matches_oracle(mm, which):
     s, pts, po, raw, cen = tiny_scene()
