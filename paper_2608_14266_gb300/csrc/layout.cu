@@ -714,8 +714,9 @@ cudaError_t build_layout(const LoadInput& in, int max_len, bool fill_f64, bool d
 // sums with no rounding at all, on the integer pipe; GB300's FP64 pipe (1/64
 // of FP32) only converts the nine sums and forms m and S once per
 // observation.  An observation whose points do not fit (a coordinate over 2^9
-// times p0's largest, a spread over 2^56 steps, more than 2^14 points, or a
-// first point at the origin) takes the same shifted sums in FP64.
+// times p0's largest, a spread over 2^56 steps, more than 2^14 points, a
+// first point at the origin, or a scale outside 2^-500 .. 2^500) takes the
+// same shifted sums in FP64.
 // ============================================================================
 constexpr int kAggLanes = 2;
 
@@ -739,11 +740,14 @@ __device__ __forceinline__ long long fix_round(double p, int F, bool& ok) {
   return (b >> 63) ? -(long long)v : (long long)v;
 }
 
+// the nearest FP64 values to the magnitude's two 64-bit halves, combined by
+// one FMA (an error of about one unit in the last place); the sign is set in
+// the bits
 __device__ __forceinline__ double i128_to_double(__int128 v) {
   const bool neg = v < 0;
   const unsigned __int128 u = neg ? (unsigned __int128)(-v) : (unsigned __int128)v;
   const double r = fma((double)(unsigned long long)(u >> 64), 0x1p64, (double)(unsigned long long)u);
-  return neg ? -r : r;
+  return __longlong_as_double(__double_as_longlong(r) | ((long long)neg << 63));
 }
 
 __device__ __forceinline__ __int128 shfl_xor_i128(unsigned mask, __int128 v, int lane) {
@@ -814,7 +818,7 @@ __global__ void aggregate_points_kernel(int64_t n_obs, const int64_t* __restrict
   E0 = max(E0, (__double2hiint(p0y) >> 20) & 0x7ff);
   E0 = max(E0, (__double2hiint(p0z) >> 20) & 0x7ff);
   const int F = 1076 - E0;
-  bool ok = E0 != 0 && b - a <= (1 << 14);
+  bool ok = E0 != 0 && F >= -500 && F <= 500 && b - a <= (1 << 14);
   const long long X0x = fix_round(p0x, F, ok), X0y = fix_round(p0y, F, ok), X0z = fix_round(p0z, F, ok);
   __int128 s1x = 0, s1y = 0, s1z = 0, s00 = 0, s01 = 0, s02 = 0, s11 = 0, s12 = 0, s22 = 0;
   constexpr long long kMaxD = 1ll << 56;
@@ -849,25 +853,26 @@ __global__ void aggregate_points_kernel(int64_t n_obs, const int64_t* __restrict
   s11 += shfl_xor_i128(mask, s11, 1);
   s12 += shfl_xor_i128(mask, s12, 1);
   s22 += shfl_xor_i128(mask, s22, 1);
-  // both lanes hold the exact sums; each forms and writes half of the record
+  // Both lanes hold the exact sums.  Each converts five of them and writes
+  // half of the record through one instruction sequence whose operands are
+  // chosen per lane (lane 0: S xx, xy, xz, yy, yz = C - s_a d_b; lane 1: S zz,
+  // then m = p0 + d and N), since GB300 issues an FP64 warp instruction at the
+  // same cost whatever the number of lanes on each side of a branch.
+  const double sc = __hiloint2double((1023 - F) << 20, 0);  // 2^-F (F is in [-500, 500])
+  const double sc2 = sc * sc;
   const double n = (double)(b - a);
   const double rn = 1.0 / n;
-  const double sx = ldexp(i128_to_double(s1x), -F), sy = ldexp(i128_to_double(s1y), -F),
-               sz = ldexp(i128_to_double(s1z), -F);
+  const double sx = i128_to_double(s1x) * sc, sy = i128_to_double(s1y) * sc, sz = i128_to_double(s1z) * sc;
   const double dx = sx * rn, dy = sy * rn, dz = sz * rn;
-  if (sub == 0) {
-    r[0] = fma(-sx, dx, ldexp(i128_to_double(s00), -2 * F));
-    r[1] = fma(-sx, dy, ldexp(i128_to_double(s01), -2 * F));
-    r[2] = fma(-sx, dz, ldexp(i128_to_double(s02), -2 * F));
-    r[3] = fma(-sy, dy, ldexp(i128_to_double(s11), -2 * F));
-    r[4] = fma(-sy, dz, ldexp(i128_to_double(s12), -2 * F));
-  } else {
-    r[5] = fma(-sz, dz, ldexp(i128_to_double(s22), -2 * F));
-    r[6] = ldexp((double)X0x, -F) + dx;
-    r[7] = ldexp((double)X0y, -F) + dy;
-    r[8] = ldexp((double)X0z, -F) + dz;
-    r[9] = n;
-  }
+  const bool l0 = sub == 0;
+  const __int128 v[5] = {l0 ? s00 : s22, l0 ? s01 : (__int128)X0x, l0 ? s02 : (__int128)X0y,
+                         l0 ? s11 : (__int128)X0z, l0 ? s12 : (__int128)0};
+  const double A[5] = {l0 ? -sx : -sz, l0 ? -sx : 1.0, l0 ? -sx : 1.0, l0 ? -sy : 1.0, l0 ? -sy : n};
+  const double B[5] = {l0 ? dx : dz, l0 ? dy : dx, l0 ? dz : dy, l0 ? dy : dz, l0 ? dz : 1.0};
+  const double S[5] = {sc2, l0 ? sc2 : sc, l0 ? sc2 : sc, l0 ? sc2 : sc, sc2};
+  double* w = r + 5 * sub;
+#pragma unroll
+  for (int k = 0; k < 5; ++k) w[k] = fma(A[k], B[k], i128_to_double(v[k]) * S[k]);
 }
 
 cudaError_t launch_aggregate_points(int64_t n_obs, const int64_t* point_off, const double* points, double* agg_out,
