@@ -80,6 +80,7 @@ def _args():
     ap.add_argument("--no-served", action="store_true", help="default run: skip the served workload")
     ap.add_argument("--no-voxelize", action="store_true", help="default run: skip the preprocessing workload")
     ap.add_argument("--rate", type=float, default=200.0, help="served: Poisson arrival rate (jobs/s)")
+    ap.add_argument("--loaders", type=int, default=3, help="served: the server's loader threads")
     ap.add_argument("--budget-gb", type=float, default=120.0, help="served: device memory budget")
     ap.add_argument("--chunk", type=int, default=0,
                     help="batched / served: LM iterations per round (0: 8 batched, 16 served)")
@@ -930,7 +931,7 @@ def served_result(args, mm, torch, scenegen, oracle_mod=None):
         clock0 = time.perf_counter()
         clk = lambda: time.perf_counter() - clock0
         srv = Server(budget, chunk=chunk, clock=clk, precision=mm.BA_MIXED, cuda_stream=main,
-                     async_admission=True, input_stream=side, **SOLVE_CFG)
+                     async_admission=True, input_stream=side, loaders=args.loaders, **SOLVE_CFG)
 
         def inputs(k, off):
             sc, agg = fac.make(params[k], offsets=off)

@@ -439,7 +439,7 @@ ba_status ba_server_submit_async(ba_server* s, const ba_job_desc* job, void* inp
 int32_t ba_server_job_state(ba_server* s, uint64_t job_id);
 /* Jobs submitted asynchronously that have not joined the batch yet. */
 int32_t ba_server_loading(const ba_server* s);
-/* Number of loader threads (1 .. 16, default 2), each loading one job at a
+/* Number of loader threads (1 .. 16, default 3), each loading one job at a
  * time; only before the first ba_server_submit_async (BA_ERR_STATE after). */
 ba_status ba_server_set_loaders(ba_server* s, int32_t n);
 /* 1 if a job of these sizes would be admitted now, else 0 (lets a caller

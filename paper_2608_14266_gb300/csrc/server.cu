@@ -80,7 +80,7 @@ struct ba_server {
   std::vector<LoadedJob> loaded;
   std::unordered_set<uint64_t> loading_now;  // taken by a loader thread, not returned yet
   bool stop = false;
-  int n_loaders = 2;
+  int n_loaders = 3;
   std::vector<std::thread> loaders;
 };
 

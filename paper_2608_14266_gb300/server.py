@@ -67,7 +67,7 @@ class Server:
     handle (precision, rel_tol, max_iters, cuda_stream, ...)."""
 
     def __init__(self, mem_budget: int, chunk: int = 4, clock=time.perf_counter, async_admission: bool = False,
-                 input_stream=None, loaders: int = 2, **cfg):
+                 input_stream=None, loaders: int = 3, **cfg):
         cfg.setdefault("precision", BA_MIXED)
         self.cfg = ba_config_default(**cfg)
         self.chunk = int(chunk)
