@@ -174,6 +174,7 @@ __device__ __forceinline__ void scan_pass_f64_body(const DevLayout& L, const dou
   double acc[kGH];
 #pragma unroll
   for (int k = 0; k < kGH; ++k) acc[k] = 0.0;
+  double dg0 = 0.0, dg1 = 0.0, dg2 = 0.0;  // sums of w_a m'_a (exact Hessian's diagonal)
   const int64_t lo = L.scan_off[j], hi = L.scan_off[j + 1];
   const int64_t no = L.n_obs;
   for (int64_t o = lo + threadIdx.x; o < hi; o += kScanThreads) {
@@ -195,13 +196,13 @@ __device__ __forceinline__ void scan_pass_f64_body(const DevLayout& L, const dou
     const double swy = fma(S01, wx, fma(S11, wy, S12 * wz));
     const double swz = fma(S02, wx, fma(S12, wy, S22 * wz));
     const double mpx = fma(Nr, mx, swx), mpy = fma(Nr, my, swy), mpz = fma(Nr, mz, swz);
-    // gradient
-    acc[0] += mpy * wz - mpz * wy;
-    acc[1] += mpz * wx - mpx * wz;
-    acc[2] += mpx * wy - mpy * wx;
-    acc[3] += Nr * wx;
-    acc[4] += Nr * wy;
-    acc[5] += Nr * wz;
+    // gradient (FMA chains into the sums)
+    acc[0] = fma(mpy, wz, fma(-mpz, wy, acc[0]));
+    acc[1] = fma(mpz, wx, fma(-mpx, wz, acc[1]));
+    acc[2] = fma(mpx, wy, fma(-mpy, wx, acc[2]));
+    acc[3] = fma(Nr, wx, acc[3]);
+    acc[4] = fma(Nr, wy, acc[4]);
+    acc[5] = fma(Nr, wz, acc[5]);
     // P = S + N m m^T
     const double Nmx = N * mx, Nmy = N * my, Nmz = N * mz;
     const double p00 = fma(Nmx, mx, S00), p01 = fma(Nmx, my, S01), p02 = fma(Nmx, mz, S02);
@@ -210,37 +211,33 @@ __device__ __forceinline__ void scan_pass_f64_body(const DevLayout& L, const dou
     const double b00 = wy * p02 - wz * p01, b10 = wz * p00 - wx * p02, b20 = wx * p01 - wy * p00;
     const double b01 = wy * p12 - wz * p11, b11 = wz * p01 - wx * p12, b21 = wx * p11 - wy * p01;
     const double b02 = wy * p22 - wz * p12, b12 = wz * p02 - wx * p22;
-    // C = B [w]x^T : C[r][c] = (B row r) x-dotted -> C[r][c] = sum_k B[r][k] [w]x[c][k]
-    // [w]x rows: (0,-wz,wy), (wz,0,-wx), (-wy,wx,0)
-    double h00 = -wz * b01 + wy * b02;
-    double h01 = wz * b00 - wx * b02;
-    double h02 = -wy * b00 + wx * b01;
-    double h11 = wz * b10 - wx * b12;
-    double h12 = -wy * b10 + wx * b11;
-    double h22 = -wy * b20 + wx * b21;
+    // B [w]x^T into the rotation block; [w]x rows: (0,-wz,wy), (wz,0,-wx), (-wy,wx,0)
+    acc[6] = fma(wy, b02, fma(-wz, b01, acc[6]));
+    acc[7] = fma(wz, b00, fma(-wx, b02, acc[7]));
+    acc[8] = fma(wx, b01, fma(-wy, b00, acc[8]));
+    acc[12] = fma(wz, b10, fma(-wx, b12, acc[12]));
+    acc[13] = fma(wx, b11, fma(-wy, b10, acc[13]));
+    acc[17] = fma(wx, b21, fma(-wy, b20, acc[17]));
     if (!gn) {
-      const double wm = fma(wx, mpx, fma(wy, mpy, wz * mpz));
-      h00 += wx * mpx - wm;
-      h11 += wy * mpy - wm;
-      h22 += wz * mpz - wm;
-      h01 += 0.5 * (wx * mpy + mpx * wy);
-      h02 += 0.5 * (wx * mpz + mpx * wz);
-      h12 += 0.5 * (wy * mpz + mpy * wz);
+      // exact term sym(w m'^T) - (w . m') I: the off-diagonal halves go into
+      // the sums here, the diagonal products into dg (the trace is taken off
+      // once per thread after the loop, as the term is linear)
+      const double hx = 0.5 * mpx, hy = 0.5 * mpy, hz = 0.5 * mpz;
+      acc[7] = fma(wx, hy, fma(hx, wy, acc[7]));
+      acc[8] = fma(wx, hz, fma(hx, wz, acc[8]));
+      acc[13] = fma(wy, hz, fma(hy, wz, acc[13]));
+      dg0 = fma(wx, mpx, dg0);
+      dg1 = fma(wy, mpy, dg1);
+      dg2 = fma(wz, mpz, dg2);
     }
-    acc[6] += h00;
-    acc[7] += h01;
-    acc[8] += h02;
     // rotation-translation block: N (m x w) w^T
     const double cx = Nmy * wz - Nmz * wy, cy = Nmz * wx - Nmx * wz, cz = Nmx * wy - Nmy * wx;
     acc[9] += cx * wx;
     acc[10] += cx * wy;
     acc[11] += cx * wz;
-    acc[12] += h11;
-    acc[13] += h12;
     acc[14] += cy * wx;
     acc[15] += cy * wy;
     acc[16] += cy * wz;
-    acc[17] += h22;
     acc[18] += cz * wx;
     acc[19] += cz * wy;
     acc[20] += cz * wz;
@@ -252,6 +249,12 @@ __device__ __forceinline__ void scan_pass_f64_body(const DevLayout& L, const dou
     acc[24] += Nwy * wy;
     acc[25] += Nwy * wz;
     acc[26] += N * wz * wz;
+  }
+  if (!gn) {
+    const double tr = dg0 + dg1 + dg2;
+    acc[6] += dg0 - tr;
+    acc[12] += dg1 - tr;
+    acc[17] += dg2 - tr;
   }
   // deterministic block reduction
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
