@@ -457,10 +457,14 @@ void ba_server_destroy(ba_server* s);
 /* Stateless point-cluster formation (Eq. 2) on the device: for each of n_obs
  * observations with points point_offsets[o] .. point_offsets[o+1]-1 of
  * points (n x 3 doubles), write the centred cluster (S, m, N) to
- * agg_out[10 * o ..].  All pointers are device memory; stream is a
- * cudaStream_t (NULL = legacy default).  Observations with no point get
- * N = 0 and zeros.  Errors: BA_ERR_INVALID_ARG (n_obs < 0 or NULL
- * pointers), BA_ERR_CUDA. */
+ * agg_out[10 * o ..].  The sums of the points' deviations from the
+ * observation's first point are exact (fixed-point integers at half the last
+ * bit of that point's largest coordinate; smaller coordinates rounded to
+ * it); m and S are formed from them in FP64.  Observations outside that
+ * range (see layout.cu) take the same sums in FP64.  All pointers are device
+ * memory; stream is a cudaStream_t (NULL = legacy default).  Observations
+ * with no point get N = 0 and zeros.  Errors: BA_ERR_INVALID_ARG (n_obs < 0
+ * or NULL pointers), BA_ERR_CUDA. */
 ba_status ba_aggregate_points(int64_t n_obs, const int64_t* point_offsets, const double* points, double* agg_out,
                               void* stream);
 
