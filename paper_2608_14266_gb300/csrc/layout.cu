@@ -720,6 +720,45 @@ cudaError_t build_layout(const LoadInput& in, int max_len, bool fill_f64, bool d
 // ============================================================================
 constexpr int kAggLanes = 2;
 
+// 2^-F as an FP64 value, for F in [-1022, 1022]
+__device__ __forceinline__ double pow2_neg(int F) { return __hiloint2double((1023 - F) << 20, 0); }
+
+// round(p 2^F) to the nearest integer (halves away from zero); ok is cleared
+// when the result would reach 2^62
+__device__ __forceinline__ long long fix_round(double p, int F, bool& ok) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(p);
+  const int E = (int)((b >> 52) & 0x7ffu);
+  const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  const int sh = E - 1075 + F;
+  unsigned long long v = 0;
+  if (E != 0) {  // zero and subnormal values are below the resolution
+    if (sh >= 0) {
+      ok = ok && sh <= 9;
+      v = m << (sh & 15);
+    } else if (sh > -63) {
+      const int r = -sh;
+      v = (m + (1ull << (r - 1))) >> r;
+    }
+  }
+  return (b >> 63) ? -(long long)v : (long long)v;
+}
+
+// the nearest FP64 values to the magnitude's two 64-bit halves, combined by
+// one FMA (an error of about one unit in the last place); the sign is set in
+// the bits
+__device__ __forceinline__ double i128_to_double(__int128 v) {
+  const bool neg = v < 0;
+  const unsigned __int128 u = neg ? (unsigned __int128)(-v) : (unsigned __int128)v;
+  const double r = fma((double)(unsigned long long)(u >> 64), 0x1p64, (double)(unsigned long long)u);
+  return __longlong_as_double(__double_as_longlong(r) | ((long long)neg << 63));
+}
+
+__device__ __forceinline__ __int128 shfl_xor_i128(unsigned mask, __int128 v, int lane) {
+  const unsigned long long lo = (unsigned long long)v, hi = (unsigned long long)((unsigned __int128)v >> 64);
+  const unsigned long long lo2 = __shfl_xor_sync(mask, lo, lane), hi2 = __shfl_xor_sync(mask, hi, lane);
+  return (__int128)(((unsigned __int128)hi2 << 64) | lo2);
+}
+
 // the shifted sums in FP64 (observations the fixed point does not fit)
 __device__ void aggregate_f64(int64_t a, int64_t b, int sub, unsigned mask, const double* __restrict__ pts,
                               double* __restrict__ r) {

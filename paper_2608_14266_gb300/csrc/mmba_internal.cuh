@@ -269,51 +269,6 @@ __device__ __forceinline__ int find_job(const P* prefix, int n_jobs, int64_t b) 
   return lo;
 }
 
-// ---- exact fixed-point sums of points ---------------------------------------
-// Point coordinates scaled by 2^F and rounded to integers, so that sums of
-// deviations and of their products are exact 64- and 128-bit integer sums on
-// the integer pipe (GB300's FP64 pipe runs at 1/64 of FP32); FP64 only
-// converts the sums.
-
-// 2^-F as an FP64 value, for F in [-1022, 1022]
-__device__ __forceinline__ double pow2_neg(int F) { return __hiloint2double((1023 - F) << 20, 0); }
-
-// round(p 2^F) to the nearest integer (halves away from zero); ok is cleared
-// when the result would reach 2^62
-__device__ __forceinline__ long long fix_round(double p, int F, bool& ok) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(p);
-  const int E = (int)((b >> 52) & 0x7ffu);
-  const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-  const int sh = E - 1075 + F;
-  unsigned long long v = 0;
-  if (E != 0) {  // zero and subnormal values are below the resolution
-    if (sh >= 0) {
-      ok = ok && sh <= 9;
-      v = m << (sh & 15);
-    } else if (sh > -63) {
-      const int r = -sh;
-      v = (m + (1ull << (r - 1))) >> r;
-    }
-  }
-  return (b >> 63) ? -(long long)v : (long long)v;
-}
-
-// the nearest FP64 values to the magnitude's two 64-bit halves, combined by
-// one FMA (an error of about one unit in the last place); the sign is set in
-// the bits
-__device__ __forceinline__ double i128_to_double(__int128 v) {
-  const bool neg = v < 0;
-  const unsigned __int128 u = neg ? (unsigned __int128)(-v) : (unsigned __int128)v;
-  const double r = fma((double)(unsigned long long)(u >> 64), 0x1p64, (double)(unsigned long long)u);
-  return __longlong_as_double(__double_as_longlong(r) | ((long long)neg << 63));
-}
-
-__device__ __forceinline__ __int128 shfl_xor_i128(unsigned mask, __int128 v, int lane) {
-  const unsigned long long lo = (unsigned long long)v, hi = (unsigned long long)((unsigned __int128)v >> 64);
-  const unsigned long long lo2 = __shfl_xor_sync(mask, lo, lane), hi2 = __shfl_xor_sync(mask, hi, lane);
-  return (__int128)(((unsigned __int128)hi2 << 64) | lo2);
-}
-
 // ---- small FP64 device math ------------------------------------------------
 
 // Cyclic Jacobi for symmetric 3x3 matrices (Golub & Van Loan, Matrix
