@@ -364,7 +364,6 @@ struct CopyDrain {
   }
 };
 
-constexpr int kMaxCopyChunks = 8;
 
 ba_status load_impl(ba_handle* h, int32_t n_scans, int64_t n_voxels, int64_t n_obs, const int64_t* voxel_off,
                     const int32_t* obs_scan, const double* agg, int32_t agg_form, const double* poses, int32_t mem_kind,
@@ -380,8 +379,8 @@ ba_status load_impl(ba_handle* h, int32_t n_scans, int64_t n_voxels, int64_t n_o
   const bool own = h->mixed;
   // A mixed load of host inputs copies the clusters in chunks of input
   // voxels on a copy stream, and sets up each chunk's voxels (frames,
-  // anchors, slots wherever their slices lie, their scan-major entries) while
-  // the next chunk is on its way.
+  // anchors, slots staged voxel by voxel in the sorted voxel order) while the
+  // next chunk is on its way.
   const bool pipelined = h->mixed && mem_kind == BA_MEM_HOST && agg_mem_kind == BA_MEM_HOST && n_voxels > kWindow;
   in.voxel_off = stage(h, voxel_off, (size_t)n_voxels + 1, mem_kind, own, &e);
   if (e != cudaSuccess) return cuda_fail(h, e, "stage voxel offsets");
@@ -408,11 +407,20 @@ ba_status load_impl(ba_handle* h, int32_t n_scans, int64_t n_voxels, int64_t n_o
   int n_chunks = 0;
   if (pipelined) {
     const int64_t windows = (n_voxels + kWindow - 1) / kWindow;
-    n_chunks = (int)(windows < kMaxCopyChunks ? windows : kMaxCopyChunks);
-    const int64_t per = (windows + n_chunks - 1) / n_chunks;
+    // Chunk sizes in windows, halving towards the end (..., 4, 2, 1), the
+    // first chunk taking the rest: a chunk's set-up takes less time than the
+    // copy of the next chunk, half its size, so the set-ups keep pace and
+    // only the last, one-window chunk's is left when the copy ends.
+    n_chunks = 1;
+    while (n_chunks < kMaxCopyChunks && ((int64_t)1 << n_chunks) - 1 < windows) ++n_chunks;
+    int64_t size[kMaxCopyChunks];
+    for (int k = 1; k < n_chunks; ++k) size[k] = (int64_t)1 << (n_chunks - 1 - k);
+    size[0] = windows - (((int64_t)1 << (n_chunks - 1)) - 1);
     bool bounds_ok = voxel_off[0] == 0 && voxel_off[n_voxels] == n_obs;
+    int64_t w_end = 0;
     for (int k = 0; k < n_chunks && bounds_ok; ++k) {
-      chunk_v[k + 1] = std::min(n_voxels, (int64_t)(k + 1) * per * kWindow);
+      w_end += size[k];
+      chunk_v[k + 1] = std::min(n_voxels, w_end * kWindow);
       const int64_t o0 = voxel_off[chunk_v[k]], o1 = voxel_off[chunk_v[k + 1]];
       bounds_ok = 0 <= o0 && o0 <= o1 && o1 <= n_obs;
     }
@@ -529,27 +537,29 @@ ba_status load_impl(ba_handle* h, int32_t n_scans, int64_t n_voxels, int64_t n_o
     h->in_keep.poses = nullptr;
     if (pipelined) {
       CK(h, build_mixed_begin(in, h->poses2, mb, h->stream, &h->launches), "mixed-precision copies");
-      // slots staged in input order while the chunks arrive, placed in their
-      // slices (spatial windows draw voxels from every chunk) at the end
+      // slots staged in the sorted voxel order and their scan-major entries
+      // filled while the chunks arrive, the slots placed in their slices
+      // (spatial windows draw voxels from every chunk) at the end
       float4* staging = (float4*)dev_alloc(h, h->temp, sizeof(float4) * 3 * (size_t)n_obs);
-      if (!staging) return fail(h, BA_ERR_OOM, "slot staging: out of device memory");
+      uint32_t* chunk_q = (uint32_t*)dev_alloc(h, h->temp, sizeof(uint32_t) * (size_t)n_obs);
+      if (!staging || !chunk_q) return fail(h, BA_ERR_OOM, "slot staging: out of device memory");
+      {
+        // each chunk's scan-major positions, listed while the first chunk is copied
+        ChunkBounds cb{};
+        cb.n = n_chunks;
+        for (int k = 0; k <= n_chunks; ++k) cb.o[k] = voxel_off[chunk_v[k]];
+        CK(h, group_by_chunk(lb.scan_order, n_obs, cb, chunk_q, temp, h->stream, &h->launches), "chunk order");
+      }
       for (int k = 0; k < n_chunks; ++k) {
         const int64_t v0 = chunk_v[k], v1 = chunk_v[k + 1];
         CK(h, cudaStreamWaitEvent(h->stream, h->copy_events[k], 0), "wait for clusters");
         CK(h, launch_validate_agg(in, voxel_off[v0], voxel_off[v1], d_val, h->stream, &h->launches), "validate");
         CK(h, launch_vscale(in, v0, v1, lb.vscale, h->stream, &h->launches), "voxel scales");
-        CK(h, build_mixed_voxels(in, lb, h->poses2, mb, v0, v1, voxel_off[v0], voxel_off[v1], staging, h->stream,
-                                 &h->launches),
+        CK(h, build_mixed_voxels(in, lb, h->poses2, mb, v0, v1, voxel_off[v0], voxel_off[v1], staging, chunk_q,
+                                 h->stream, &h->launches),
            "mixed-precision copies");
       }
-      // the slots to their slices on this stream and the scan-major copy from
-      // the staged slots on the (now idle) copy stream, concurrently
-      CK(h, cudaEventRecord(h->copy_events[kMaxCopyChunks], h->stream), "set-up order");
-      CK(h, cudaStreamWaitEvent(h->copy_stream, h->copy_events[kMaxCopyChunks], 0), "set-up order");
-      CK(h, build_mixed_scan_major(in, lb, mb, staging, h->copy_stream, &h->launches), "mixed-precision copies");
-      CK(h, cudaEventRecord(h->copy_events[0], h->copy_stream), "set-up order");
       CK(h, build_mixed_place(in, lb, mb, staging, h->stream, &h->launches), "mixed-precision copies");
-      CK(h, cudaStreamWaitEvent(h->stream, h->copy_events[0], 0), "set-up order");
       CK(h, build_mixed_end(in, lb, h->poses2, mb, h->stream, &h->launches, true), "mixed-precision copies");
       CK(h, cudaMemcpyAsync(&res, d_val, sizeof res, cudaMemcpyDeviceToHost, h->stream), "validation result");
       CK(h, cudaStreamSynchronize(h->stream), "validation sync");

@@ -273,22 +273,26 @@ cudaError_t radix_sort_pairs64(uint64_t* keys, uint32_t* vals, uint64_t* tmp_key
 // ============================================================================
 __device__ inline void amin(long long* p, long long v) { atomicMin(p, v); }
 
+// every thread of a block reaches the warp reduction (whole warps: the block
+// size is a multiple of 32)
 __global__ void validate_voxels_kernel(LoadInput in, ValidateResult* r) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i > in.n_voxels) return;
-  const int64_t a = in.voxel_off[i];
-  if (i == 0 && a != 0) amin(&r->first_bad_offset, 0);
-  if (i == in.n_voxels) {
-    if (a != in.n_obs) amin(&r->first_bad_offset, i);
-    return;
+  int len = 0;  // the voxel's observation count (capped at 2^31 - 1), 0 if none or invalid
+  if (i <= in.n_voxels) {
+    const int64_t a = in.voxel_off[i];
+    if (i == 0 && a != 0) amin(&r->first_bad_offset, 0);
+    if (i == in.n_voxels) {
+      if (a != in.n_obs) amin(&r->first_bad_offset, i);
+    } else {
+      const int64_t b = in.voxel_off[i + 1];
+      if (b < a || a < 0 || b > in.n_obs) amin(&r->first_bad_offset, i);
+      else if (b == a) amin(&r->first_empty_voxel, i);
+      else len = (int)(b - a > 0x7fffffff ? 0x7fffffff : b - a);
+    }
   }
-  const int64_t b = in.voxel_off[i + 1];
-  if (b < a || a < 0 || b > in.n_obs) amin(&r->first_bad_offset, i);
-  else if (b == a) amin(&r->first_empty_voxel, i);
-  else {
-    const int64_t len = b - a;
-    atomicMax(&r->max_len, (long long)(len > 0x7fffffff ? 0x7fffffff : len));
-  }
+  // one atomic per warp (one per voxel serialises on the single word)
+  const int wmax = __reduce_max_sync(0xffffffffu, len);
+  if ((threadIdx.x & 31) == 0 && wmax > 0) atomicMax(&r->max_len, (long long)wmax);
 }
 
 __global__ void validate_scan_ids_kernel(LoadInput in, ValidateResult* r) {
@@ -538,14 +542,25 @@ __global__ void vscale_kernel(LoadInput in, int64_t v0, int64_t v1, double* vsca
 // the scan-major copy: inside a scan, observations follow the voxel order, so
 // the scan pass gathers the plane records of nearby voxels
 __global__ void scan_keys_kernel(LoadInput in, const int32_t* obs_vox, const int32_t* vrank, const int64_t* pbase,
-                                 uint32_t* keys, uint32_t* vals, int64_t* counts) {
+                                 uint32_t* keys, uint32_t* vals) {
   const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (o >= in.n_obs) return;
   const int32_t v = obs_vox[o];
   const int64_t q = pbase[vrank[v]] + (o - in.voxel_off[v]);
   keys[q] = (uint32_t)in.obs_scan[o];
   vals[q] = (uint32_t)o;
-  atomicAdd((unsigned long long*)(counts + in.obs_scan[o]), 1ull);
+}
+
+// scan_off[j] = the first scan-major position of scan j (n at the end), from
+// the scan ids sorted ascending: position q starts every scan after its
+// predecessor's id up to its own (scans with no observation included), so
+// each entry is written once
+__global__ void scan_off_kernel(const uint32_t* keys, int64_t n, int32_t n_scans, int64_t* scan_off) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q > n) return;
+  const int64_t lo = q == 0 ? 0 : (int64_t)keys[q - 1] + 1;
+  const int64_t hi = q == n ? (int64_t)n_scans : (int64_t)keys[q];
+  for (int64_t j = lo; j <= hi; ++j) scan_off[j] = q;
 }
 
 __global__ void vlen_i64_kernel(const int32_t* vlen, int64_t n_voxels, int64_t* out) {
@@ -573,6 +588,18 @@ __global__ void fill_scan_major_kernel(LoadInput in, const uint32_t* order, cons
   for (int a = 0; a < 10; ++a) se[a * n + q] = c[a];
 }
 
+// chunk index of each scan-major position's observation (its place among
+// the chunk bounds), keyed for a stable one-digit partition
+__global__ void chunk_keys_kernel(const uint32_t* order, int64_t n, ChunkBounds cb, uint32_t* keys, uint32_t* vals) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  const int64_t o = order[q];
+  uint32_t c = 0;
+  for (int k = 1; k < cb.n; ++k) c += o >= cb.o[k] ? 1u : 0u;
+  keys[q] = c;
+  vals[q] = (uint32_t)q;
+}
+
 static int bit_width(uint64_t x) {
   int b = 0;
   while (x) {
@@ -588,6 +615,21 @@ cudaError_t launch_vscale(const LoadInput& in, int64_t v0, int64_t v1, double* v
   vscale_kernel<<<(unsigned)((v1 - v0 + 255) / 256), 256, 0, stream>>>(in, v0, v1, vscale);
   ++*launches;
   return cudaGetLastError();
+}
+
+cudaError_t group_by_chunk(const uint32_t* order, int64_t n_obs, const ChunkBounds& cb, uint32_t* out_q,
+                           Allocator temp, cudaStream_t stream, int64_t* launches) {
+  if (n_obs <= 0) return cudaSuccess;
+  if (cb.n < 1 || cb.n > kMaxCopyChunks) return cudaErrorInvalidValue;
+  uint32_t* keys = (uint32_t*)temp.fn(temp.self, sizeof(uint32_t) * n_obs);
+  uint32_t* tk = (uint32_t*)temp.fn(temp.self, sizeof(uint32_t) * n_obs);
+  uint32_t* tv = (uint32_t*)temp.fn(temp.self, sizeof(uint32_t) * n_obs);
+  int64_t* scratch = (int64_t*)temp.fn(temp.self, sizeof(int64_t) * radix_scratch_count(n_obs));
+  if (!keys || !tk || !tv || !scratch) return cudaErrorMemoryAllocation;
+  chunk_keys_kernel<<<(unsigned)((n_obs + 255) / 256), 256, 0, stream>>>(order, n_obs, cb, keys, out_q);
+  ++*launches;
+  RETURN_IF(cudaGetLastError());
+  return radix_sort_pairs(keys, out_q, tk, tv, n_obs, bit_width((uint64_t)(cb.n - 1)), scratch, stream, launches);
 }
 
 cudaError_t build_layout(const LoadInput& in, int max_len, bool fill_f64, bool defer_scale, Allocator keep,
@@ -670,23 +712,26 @@ cudaError_t build_layout(const LoadInput& in, int max_len, bool fill_f64, bool d
   obs_voxel_kernel<<<(unsigned)((nv + 255) / 256), 256, 0, stream>>>(in, obs_vox, defer_scale ? nullptr : vscale);
   ++*launches;
   RETURN_IF(cudaGetLastError());
-  RETURN_IF(cudaMemsetAsync(out->scan_off, 0, sizeof(int64_t) * (in.n_scans + 1), stream));
   {
-    int64_t* pbase = (int64_t*)temp.fn(temp.self, sizeof(int64_t) * (nv + 1));
+    // kept by a load that stages its slots (they are staged in this order)
+    Allocator pb_alloc = defer_scale ? keep : temp;
+    int64_t* pbase = (int64_t*)pb_alloc.fn(pb_alloc.self, sizeof(int64_t) * (nv + 1));
     int64_t* pscratch = (int64_t*)temp.fn(temp.self, sizeof(int64_t) * scan_scratch_count(nv + 1));
     if (!pbase || !pscratch) return cudaErrorMemoryAllocation;
     vlen_i64_kernel<<<(unsigned)((nv + 255) / 256), 256, 0, stream>>>(out->vlen, nv, pbase);
     ++*launches;
     RETURN_IF(cudaGetLastError());
     RETURN_IF(exclusive_scan_i64(pbase, nv + 1, pscratch, stream, launches));
-    scan_keys_kernel<<<(unsigned)((no + 255) / 256), 256, 0, stream>>>(in, obs_vox, vrank, pbase, keys, vals,
-                                                                       out->scan_off);
+    out->vstart = defer_scale ? pbase : nullptr;
+    scan_keys_kernel<<<(unsigned)((no + 255) / 256), 256, 0, stream>>>(in, obs_vox, vrank, pbase, keys, vals);
     ++*launches;
     RETURN_IF(cudaGetLastError());
   }
   RETURN_IF(radix_sort_pairs(keys, vals, tk, tv, no, bit_width((uint64_t)(in.n_scans - 1)), scratch, stream,
                              launches));
-  RETURN_IF(exclusive_scan_i64(out->scan_off, in.n_scans + 1, scratch, stream, launches));
+  scan_off_kernel<<<(unsigned)((no + 1 + 255) / 256), 256, 0, stream>>>(keys, no, in.n_scans, out->scan_off);
+  ++*launches;
+  RETURN_IF(cudaGetLastError());
   fill_scan_major_kernel<<<(unsigned)((no + 255) / 256), 256, 0, stream>>>(in, vals, obs_vox, vscale, vrank, out->se,
                                                                            out->se_vox);
   ++*launches;

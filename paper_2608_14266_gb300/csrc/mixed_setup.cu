@@ -127,18 +127,36 @@ __device__ __forceinline__ void posed_f32(const float* ref32, const float* m, fl
 }
 
 // anchor (FP32-rounded centroid) and starting frame (eigenvectors, normal
-// last, proper rotation) of each voxel at the reference poses, one thread per
-// voxel over its observations in order (so 32 voxels' eigen-solves run side by
-// side in a warp).  Both only seed the iteration (the voxel pass moves the
-// frame and the centroid every pass, and the anchor only has to be an FP32
-// value near the centroid), so the sums are FP32, about the voxel's first
-// posed mean: an error of the order of an FP32 ulp of the scene coordinates
-// (~1e-4 m at 2 km) moves nothing but the seed.
+// last, proper rotation) of each voxel at the reference poses, kFrameLanes
+// threads per voxel taking its observations in turn (lane l the l-th, then
+// every kFrameLanes-th) in one pass: sums of N d and N d d^T + R S R^T with d
+// the posed mean's offset from the voxel's first posed mean, combined by a
+// butterfly so that every lane holds the same totals, then moved to the
+// centroid (A = M - s s^T / n); the group's first lane solves the 3x3
+// eigenproblem.  Both results only seed the iteration (the voxel pass moves
+// the frame and the centroid every pass, and the anchor only has to be an FP32
+// value near the centroid), so the sums are FP32: errors of the order of an
+// FP32 ulp of the scene coordinates (~1e-4 m at 2 km) and of the voxel's
+// spread move nothing but the seed.
+constexpr int kFrameLanes = 8;
+
+// x summed over the group of kFrameLanes lanes (the same value in every lane:
+// each step adds the same two values in either order)
+__device__ __forceinline__ float group_sum(unsigned mask, float x) {
+#pragma unroll
+  for (int k = 1; k < kFrameLanes; k <<= 1) x += __shfl_xor_sync(mask, x, k);
+  return x;
+}
+
 __global__ void __launch_bounds__(128) voxel_frames_kernel(LoadInput in, int64_t v0, int64_t v1, const double* sref,
                                                            const int32_t* vrank, float4* vstate, float4* vanchor,
                                                            float4* planes2) {
-  const int64_t v = v0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (v >= v1) return;
+  static_assert(32 % kFrameLanes == 0 && 128 % kFrameLanes == 0, "groups must not straddle warps");
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t v = v0 + t / kFrameLanes;
+  const int sub = (int)(t % kFrameLanes);
+  if (v >= v1) return;  // whole groups leave together
+  const unsigned mask = ((1u << kFrameLanes) - 1u) << ((threadIdx.x & 31) & ~(kFrameLanes - 1));
   const int64_t a0 = in.voxel_off[v], a1 = in.voxel_off[v + 1];
   float p0[3];
   {
@@ -148,23 +166,9 @@ __global__ void __launch_bounds__(128) voxel_frames_kernel(LoadInput in, int64_t
     cluster_f32(c, Sf, mf, N);
     posed_f32(sref32_of(sref, in.n_scans, in.obs_scan[a0]), mf, p0);
   }
-  float n = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
-  for (int64_t o = a0; o < a1; ++o) {
-    double c[10];
-    centred_cluster(in.agg + 10 * o, in.agg_form, c);
-    float Sf[6], mf[3], N, q[3];
-    cluster_f32(c, Sf, mf, N);
-    posed_f32(sref32_of(sref, in.n_scans, in.obs_scan[o]), mf, q);
-    cx = fmaf(N, q[0] - p0[0], cx);
-    cy = fmaf(N, q[1] - p0[1], cy);
-    cz = fmaf(N, q[2] - p0[2], cz);
-    n += N;
-  }
-  cx /= n;
-  cy /= n;
-  cz /= n;
-  float A[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  for (int64_t o = a0; o < a1; ++o) {
+  float n = 0.f, sx = 0.f, sy = 0.f, sz = 0.f;
+  float M[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  for (int64_t o = a0 + sub; o < a1; o += kFrameLanes) {
     double c[10];
     centred_cluster(in.agg + 10 * o, in.agg_form, c);
     float Sf[6], mf[3], N, q[3], rs[6];
@@ -172,14 +176,28 @@ __global__ void __launch_bounds__(128) voxel_frames_kernel(LoadInput in, int64_t
     const float* Rf = sref32_of(sref, in.n_scans, in.obs_scan[o]);
     posed_f32(Rf, mf, q);
     rot_sym_f(Rf, Sf, rs);
-    const float dx = (q[0] - p0[0]) - cx, dy = (q[1] - p0[1]) - cy, dz = (q[2] - p0[2]) - cz;
-    A[0] += fmaf(N * dx, dx, rs[0]);
-    A[1] += fmaf(N * dx, dy, rs[1]);
-    A[2] += fmaf(N * dx, dz, rs[2]);
-    A[3] += fmaf(N * dy, dy, rs[3]);
-    A[4] += fmaf(N * dy, dz, rs[4]);
-    A[5] += fmaf(N * dz, dz, rs[5]);
+    const float dx = q[0] - p0[0], dy = q[1] - p0[1], dz = q[2] - p0[2];
+    sx = fmaf(N, dx, sx);
+    sy = fmaf(N, dy, sy);
+    sz = fmaf(N, dz, sz);
+    n += N;
+    M[0] += fmaf(N * dx, dx, rs[0]);
+    M[1] += fmaf(N * dx, dy, rs[1]);
+    M[2] += fmaf(N * dx, dz, rs[2]);
+    M[3] += fmaf(N * dy, dy, rs[3]);
+    M[4] += fmaf(N * dy, dz, rs[4]);
+    M[5] += fmaf(N * dz, dz, rs[5]);
   }
+  n = group_sum(mask, n);
+  sx = group_sum(mask, sx);
+  sy = group_sum(mask, sy);
+  sz = group_sum(mask, sz);
+#pragma unroll
+  for (int k = 0; k < 6; ++k) M[k] = group_sum(mask, M[k]);
+  const float cx = sx / n, cy = sy / n, cz = sz / n;  // centroid - p0
+  const float A[6] = {fmaf(-sx, cx, M[0]), fmaf(-sx, cy, M[1]), fmaf(-sx, cz, M[2]),
+                      fmaf(-sy, cy, M[3]), fmaf(-sy, cz, M[4]), fmaf(-sz, cz, M[5])};
+  if (sub != 0) return;
   float lam[3], V[9];
   eig3_sym_f(A, lam, V);
   // rows: e1 (largest), e2, n (smallest)
@@ -325,26 +343,30 @@ __global__ void fill_sell_mixed_kernel(LoadInput in, const int32_t* vperm, const
   }
 }
 
-// The same slots staged in input order (slot of observation o at
-// staging[3 o]): a pipelined load computes each arriving chunk's slots there,
-// then places them all in their slices once every chunk is done.
+// The same slots staged voxel by voxel in the sorted voxel order (slot of
+// row k of the voxel at sorted position p at staging[3 (vstart[p] + k)]): a
+// pipelined load computes each arriving chunk's slots there (each voxel's
+// rows one contiguous run), then places them all in their slices once every
+// chunk is done, each slice reading one contiguous stretch.
 __global__ void fill_staging_kernel(LoadInput in, int64_t o0, int64_t o1, const int32_t* obs_vox,
-                                    const int32_t* vrank, const double* sref, const float4* vanchor,
-                                    float4* staging) {
+                                    const int32_t* vrank, const int64_t* vstart, const double* sref,
+                                    const float4* vanchor, float4* staging) {
   const int64_t o = o0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (o >= o1) return;
+  const int32_t v = obs_vox[o];
+  const int64_t p = vrank[v];
   float4 s0, s1, s2;
-  mixed_slot(in, o, sref, vanchor[vrank[obs_vox[o]]], s0, s1, s2);
-  staging[3 * o] = s0;
-  staging[3 * o + 1] = s1;
-  staging[3 * o + 2] = s2;
+  mixed_slot(in, o, sref, vanchor[p], s0, s1, s2);
+  float4* dst = staging + 3 * (vstart[p] + (o - in.voxel_off[v]));
+  dst[0] = s0;
+  dst[1] = s1;
+  dst[2] = s2;
 }
 
 // staged slots to their slices, padding rows zero; thread (p, blockIdx.y)
 // as in fill_sell_mixed_kernel (coalesced writes)
-__global__ void place_slots_kernel(const int64_t* voxel_off, const int32_t* vperm, const int32_t* vlen,
-                                   const int64_t* slice_off, int64_t n_voxels, int64_t n_slices,
-                                   const float4* staging, float4* ve32) {
+__global__ void place_slots_kernel(const int64_t* vstart, const int32_t* vlen, const int64_t* slice_off,
+                                   int64_t n_voxels, int64_t n_slices, const float4* staging, float4* ve32) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t s = p >> 5;
   if (s >= n_slices) return;
@@ -352,7 +374,7 @@ __global__ void place_slots_kernel(const int64_t* voxel_off, const int32_t* vper
   const int64_t rows = (slice_off[s + 1] - slice_off[s]) / kSlice;
   const bool real = p < n_voxels;
   const int32_t len = real ? vlen[p] : 0;
-  const int64_t o0 = real ? voxel_off[vperm[p]] : 0;
+  const int64_t o0 = real ? vstart[p] : 0;
   for (int64_t k0 = (int64_t)blockIdx.y * kFillRows; k0 < rows; k0 += (int64_t)gridDim.y * kFillRows) {
     for (int64_t k = k0; k < k0 + kFillRows && k < rows; ++k) {
       const int64_t e = base + k * kSlice;
@@ -374,20 +396,17 @@ __global__ void place_slots_kernel(const int64_t* voxel_off, const int32_t* vper
 // scatter in reference axes rebuilt from its eigenvalues and eigenvector
 // quaternion (R_ref S R_ref^T = V diag(sigma) V^T), each scaled by 2 / N_i.
 // Observation o's slot is at sorted voxel position p, row k:
-// slice_off[p / 32] + 32 k + p % 32, or, with staging non-null, at staging[3 o]
-// (input order).
+// slice_off[p / 32] + 32 k + p % 32, or, with staging non-null, at
+// staging[3 (vstart[p] + k)].
 __device__ __forceinline__ void fill_scan_one(int64_t q, int64_t o, int64_t n_obs, const int32_t* obs_vox,
                                               const double* vscale, const int32_t* vrank, const int64_t* voxel_off,
-                                              const int64_t* slice_off, const float4* ve32, const float4* staging,
-                                              float* se32) {
+                                              const int64_t* slice_off, const float4* ve32, const int64_t* vstart,
+                                              const float4* staging, float* se32) {
   const int32_t v = obs_vox[o];
-  const float4* src;
-  if (staging) {
-    src = staging + 3 * o;
-  } else {
-    const int64_t p = vrank[v];
-    src = ve32 + kVe32 * (slice_off[p >> 5] + (o - voxel_off[v]) * kSlice + (p & 31));
-  }
+  const int64_t p = vrank[v];
+  const int64_t k = o - voxel_off[v];
+  const float4* src =
+      staging ? staging + 3 * (vstart[p] + k) : ve32 + kVe32 * (slice_off[p >> 5] + k * kSlice + (p & 31));
   const float4 s0 = src[0], s1 = src[1], s2 = src[2];
   float V[9];
   quat_to_mat_f(s2.x, s2.y, s2.z, s2.w, V);
@@ -399,24 +418,31 @@ __device__ __forceinline__ void fill_scan_one(int64_t q, int64_t o, int64_t n_ob
 #pragma unroll
     for (int c = r; c < 3; ++c)
       sw[idx++] = fmaf(V[3 * r] * sg[0], V[3 * c], fmaf(V[3 * r + 1] * sg[1], V[3 * c + 1], V[3 * r + 2] * sg[2] * V[3 * c + 2]));
-  const float k = f64_to_f32(vscale[v]);
+  const float ks = f64_to_f32(vscale[v]);
   float4* bN = reinterpret_cast<float4*>(se32);
   float4* S4 = bN + n_obs;
   float2* S2 = reinterpret_cast<float2*>(S4 + n_obs);
-  bN[q] = make_float4(s0.x, s0.y, s0.z, k * s0.w);
-  S4[q] = make_float4(k * sw[0], k * sw[1], k * sw[2], k * sw[3]);
-  S2[q] = make_float2(k * sw[4], k * sw[5]);
+  bN[q] = make_float4(s0.x, s0.y, s0.z, ks * s0.w);
+  S4[q] = make_float4(ks * sw[0], ks * sw[1], ks * sw[2], ks * sw[3]);
+  S2[q] = make_float2(ks * sw[4], ks * sw[5]);
 }
 
-// thread per scan-major position q (order[q] = its observation)
-__global__ void fill_scan_mixed_kernel(int64_t n_obs, const uint32_t* order, const int32_t* obs_vox,
-                                       const double* vscale, const int32_t* vrank, const int64_t* voxel_off,
-                                       const int64_t* slice_off, const float4* ve32, const float4* staging,
+// thread per scan-major position q = qlist[i] (q = i without a list), i in
+// [i0, i1); order[q] = its observation (a pipelined load fills each chunk's
+// entries as the chunk is set up)
+__global__ void fill_scan_mixed_kernel(int64_t n_obs, const uint32_t* qlist, int64_t i0, int64_t i1,
+                                       const uint32_t* order, const int32_t* obs_vox, const double* vscale,
+                                       const int32_t* vrank, const int64_t* voxel_off, const int64_t* slice_off,
+                                       const float4* ve32, const int64_t* vstart, const float4* staging,
                                        float* se32) {
-  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q < n_obs)
-    fill_scan_one(q, order[q], n_obs, obs_vox, vscale, vrank, voxel_off, slice_off, ve32, staging, se32);
+  const int64_t i = i0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= i1) return;
+  const int64_t q = qlist ? (int64_t)qlist[i] : i;
+  fill_scan_one(q, order[q], n_obs, obs_vox, vscale, vrank, voxel_off, slice_off, ve32, vstart, staging, se32);
 }
+
+// blocks of 128 threads for kFrameLanes threads per voxel of n voxels
+unsigned frame_blocks(int64_t n) { return (unsigned)((n * kFrameLanes + 127) / 128); }
 
 }  // namespace
 
@@ -428,20 +454,22 @@ cudaError_t build_mixed_begin(const LoadInput& in, const double* poses2, MixedBu
 }
 
 cudaError_t build_mixed_voxels(const LoadInput& in, const LayoutBuffers& lb, const double* poses2, MixedBuffers& mb,
-                               int64_t v0, int64_t v1, int64_t o0, int64_t o1, float4* staging, cudaStream_t stream,
-                               int64_t* launches) {
+                               int64_t v0, int64_t v1, int64_t o0, int64_t o1, float4* staging,
+                               const uint32_t* chunk_q, cudaStream_t stream, int64_t* launches) {
   if (v1 <= v0) return cudaSuccess;
   LoadInput cur = in;
   cur.poses = poses2;  // buffer 0
-  voxel_frames_kernel<<<(unsigned)((v1 - v0 + 127) / 128), 128, 0, stream>>>(cur, v0, v1, mb.sref, lb.vrank,
-                                                                            mb.vstate, mb.vanchor, mb.planes32_2);
+  voxel_frames_kernel<<<frame_blocks(v1 - v0), 128, 0, stream>>>(cur, v0, v1, mb.sref, lb.vrank, mb.vstate,
+                                                                 mb.vanchor, mb.planes32_2);
   ++*launches;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || o1 <= o0) return e;
   fill_staging_kernel<<<(unsigned)((o1 - o0 + 127) / 128), 128, 0, stream>>>(cur, o0, o1, lb.obs_vox, lb.vrank,
-                                                                            mb.sref, mb.vanchor, staging);
+                                                                            lb.vstart, mb.sref, mb.vanchor, staging);
   ++*launches;
-  return cudaGetLastError();
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  // the chunk's scan-major entries (scattered over the whole copy)
+  return build_mixed_scan_major(in, lb, mb, staging, chunk_q, o0, o1, stream, launches);
 }
 
 cudaError_t build_mixed_place(const LoadInput& in, const LayoutBuffers& lb, MixedBuffers& mb, const float4* staging,
@@ -451,16 +479,18 @@ cudaError_t build_mixed_place(const LoadInput& in, const LayoutBuffers& lb, Mixe
   const unsigned row_blocks =
       (unsigned)std::min<int64_t>(std::max<int64_t>((lb.max_len + kFillRows - 1) / kFillRows, 1), 65535);
   place_slots_kernel<<<dim3((unsigned)((n + 127) / 128), row_blocks), 128, 0, stream>>>(
-      in.voxel_off, lb.vperm, lb.vlen, lb.slice_off, in.n_voxels, lb.n_slices, staging, mb.ve32);
+      lb.vstart, lb.vlen, lb.slice_off, in.n_voxels, lb.n_slices, staging, mb.ve32);
   ++*launches;
   return cudaGetLastError();
 }
 
 cudaError_t build_mixed_scan_major(const LoadInput& in, const LayoutBuffers& lb, MixedBuffers& mb,
-                                   const float4* staging, cudaStream_t stream, int64_t* launches) {
-  const int64_t no = in.n_obs;
-  fill_scan_mixed_kernel<<<(unsigned)((no + 255) / 256), 256, 0, stream>>>(
-      no, lb.scan_order, lb.obs_vox, lb.vscale, lb.vrank, in.voxel_off, lb.slice_off, mb.ve32, staging, mb.se32);
+                                   const float4* staging, const uint32_t* qlist, int64_t i0, int64_t i1,
+                                   cudaStream_t stream, int64_t* launches) {
+  if (i1 <= i0) return cudaSuccess;
+  fill_scan_mixed_kernel<<<(unsigned)((i1 - i0 + 255) / 256), 256, 0, stream>>>(
+      in.n_obs, qlist, i0, i1, lb.scan_order, lb.obs_vox, lb.vscale, lb.vrank, in.voxel_off, lb.slice_off, mb.ve32,
+      lb.vstart, staging, mb.se32);
   ++*launches;
   return cudaGetLastError();
 }
@@ -468,7 +498,7 @@ cudaError_t build_mixed_scan_major(const LoadInput& in, const LayoutBuffers& lb,
 cudaError_t build_mixed_end(const LoadInput& in, const LayoutBuffers& lb, const double* poses2, MixedBuffers& mb,
                             cudaStream_t stream, int64_t* launches, bool scan_filled) {
   if (!scan_filled) {
-    cudaError_t e = build_mixed_scan_major(in, lb, mb, nullptr, stream, launches);
+    cudaError_t e = build_mixed_scan_major(in, lb, mb, nullptr, nullptr, 0, in.n_obs, stream, launches);
     if (e != cudaSuccess) return e;
   }
   ++*launches;
@@ -483,8 +513,8 @@ cudaError_t build_mixed(const LoadInput& in, const LayoutBuffers& lb, const doub
   cur.poses = poses2;  // buffer 0
   const int64_t nv = in.n_voxels;
   if (nv > 0) {
-    voxel_frames_kernel<<<(unsigned)((nv + 127) / 128), 128, 0, stream>>>(cur, 0, nv, mb.sref, lb.vrank, mb.vstate,
-                                                                          mb.vanchor, mb.planes32_2);
+    voxel_frames_kernel<<<frame_blocks(nv), 128, 0, stream>>>(cur, 0, nv, mb.sref, lb.vrank, mb.vstate, mb.vanchor,
+                                                               mb.planes32_2);
     ++*launches;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // every slot, padding included, by sorted position (coalesced writes)

@@ -117,6 +117,9 @@ struct LayoutBuffers {
   int32_t* obs_vox;      // observation -> input voxel
   double* vscale;        // input voxel -> 2 / N_i
   uint32_t* scan_order;  // scan-major position -> observation
+  // kept only by a load with defer_scale: vstart[p] = observations of the
+  // voxels before sorted position p (p = 0 .. n_voxels)
+  int64_t* vstart;
 };
 // `keep` allocates the buffers of *out, `temp` the build's temporaries (the
 // caller frees those after the stream has drained).
@@ -128,6 +131,18 @@ cudaError_t build_layout(const LoadInput& in, int max_len, bool fill_f64, bool d
                          Allocator temp, LayoutBuffers* out, cudaStream_t stream, int64_t* launches);
 cudaError_t launch_vscale(const LoadInput& in, int64_t v0, int64_t v1, double* vscale, cudaStream_t stream,
                           int64_t* launches);
+// A load that copies its clusters in chunks of observations [o[k], o[k + 1])
+// (o[0] = 0, o[n] = n_obs, at most kMaxCopyChunks chunks) groups the
+// scan-major positions by chunk: out_q[o[k] .. o[k + 1]) holds, ascending,
+// the positions q whose observation order[q] lies in chunk k (order is a
+// permutation of 0 .. n_obs - 1).  Temporaries come from temp.
+constexpr int kMaxCopyChunks = 20;  // chunks halving in size: up to 2^20 - 1 windows, more than 2^31 voxels
+struct ChunkBounds {
+  int64_t o[kMaxCopyChunks + 1];
+  int n;
+};
+cudaError_t group_by_chunk(const uint32_t* order, int64_t n_obs, const ChunkBounds& cb, uint32_t* out_q,
+                           Allocator temp, cudaStream_t stream, int64_t* launches);
 
 // ---- mixed precision ----
 cudaError_t launch_voxel_pass_mixed(const DevLayout& L, const DevMixed& X, double* full_out, double* cost_part,
@@ -152,20 +167,24 @@ cudaError_t build_mixed(const LoadInput& in, const LayoutBuffers& lb, const doub
                         cudaStream_t stream, int64_t* launches);
 // The same in stages, for a load that overlaps the clusters' copy: begin
 // (reference poses); input voxels [v0, v1) with their observations [o0, o1)
-// (frames and anchors, and the slots staged in input order, 3 float4 per
-// observation; their clusters on the device); place (every staged slot to its
-// slice, padding zero) and the scan-major copy from the staged slots (the two
-// may run concurrently); end (the scan table; with scan_filled false also the
-// scan-major copy from the placed slots).
+// (frames and anchors, the slots staged voxel by voxel in the sorted voxel
+// order, 3 float4 per observation at lb.vstart, and the observations'
+// scan-major entries; their clusters on the device); place (every staged slot
+// to its slice, padding zero); end (the scan table; with scan_filled false
+// also the scan-major copy from the placed slots).  scan_major fills the
+// scan-major entries at positions qlist[i0 .. i1) (positions i0 .. i1 when
+// qlist is null: chunk_q of group_by_chunk lists a chunk's), from the staged
+// slots when staging is non-null, else from the placed ones.
 cudaError_t build_mixed_begin(const LoadInput& in, const double* poses2, MixedBuffers& mb, cudaStream_t stream,
                               int64_t* launches);
 cudaError_t build_mixed_voxels(const LoadInput& in, const LayoutBuffers& lb, const double* poses2, MixedBuffers& mb,
-                               int64_t v0, int64_t v1, int64_t o0, int64_t o1, float4* staging, cudaStream_t stream,
-                               int64_t* launches);
+                               int64_t v0, int64_t v1, int64_t o0, int64_t o1, float4* staging,
+                               const uint32_t* chunk_q, cudaStream_t stream, int64_t* launches);
 cudaError_t build_mixed_place(const LoadInput& in, const LayoutBuffers& lb, MixedBuffers& mb, const float4* staging,
                               cudaStream_t stream, int64_t* launches);
 cudaError_t build_mixed_scan_major(const LoadInput& in, const LayoutBuffers& lb, MixedBuffers& mb,
-                                   const float4* staging, cudaStream_t stream, int64_t* launches);
+                                   const float4* staging, const uint32_t* qlist, int64_t i0, int64_t i1,
+                                   cudaStream_t stream, int64_t* launches);
 cudaError_t build_mixed_end(const LoadInput& in, const LayoutBuffers& lb, const double* poses2, MixedBuffers& mb,
                             cudaStream_t stream, int64_t* launches, bool scan_filled = false);
 
