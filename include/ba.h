@@ -125,7 +125,11 @@ ba_status ba_create(const ba_config* cfg, ba_handle** out);
  * mappers; the voxels in a spatial order taken from the initial positions of
  * the scans observing them, whatever their input order), and evaluates
  * planes, cost, gradient and Hessian at the initial poses.  Replaces any previously loaded problem.  The LM state (mu, nu,
- * counters) is reset. */
+ * counters) is reset.  A mixed-precision load of host arrays copies the
+ * clusters in chunks (halving in size towards the end) on a stream of the
+ * handle and sets each chunk up while the next one crosses the host link;
+ * the call returns when the whole load is done (or has failed, with every
+ * copy drained). */
 ba_status ba_load_observations(ba_handle* h, int32_t n_scans, int64_t n_voxels, int64_t n_obs,
                                const int64_t* voxel_offsets, const int32_t* obs_scan, const double* agg,
                                int32_t agg_form, const double* poses, int32_t mem_kind);

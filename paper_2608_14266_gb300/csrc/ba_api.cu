@@ -1011,17 +1011,19 @@ int64_t ba_estimate_bytes(int32_t precision, int32_t n_scans, int64_t n_voxels, 
     per_obs = 80 + 4;  // scan-major FP64 copy + se_vox
     per_slot = 80 + 4;
   }
-  const int64_t per_voxel = 8 + 4 + 4 + 4 + 8 + 2 * 32 + 16 + 32 + 8 + 2 * 32 + 16;
+  // (+ 8: the mixed layout's spatial-order observation offsets)
+  const int64_t per_voxel = 8 + 4 + 4 + 4 + 8 + 2 * 32 + 16 + 32 + 8 + 2 * 32 + 16 + (precision == BA_MIXED ? 8 : 0);
   const int64_t per_scan = 8 + 24 * 8 + 27 * 8 + 8 + 26 * 8 + 2 * kTab * 4;
   const int64_t keep = per_obs * n_obs + per_slot * slots + per_voxel * n_voxels + per_scan * (int64_t)n_scans +
                        (1 << 16);
   // load: staged inputs (host inputs), sort keys/values and scratch, the
   // spatial order's per-voxel means and prefixes, and (mixed loads of host
-  // inputs) the slots staged in input order
+  // inputs) the staged slots, the scan-major positions grouped by chunk and
+  // that grouping's sort keys, buffers and scratch
   const int64_t nsort = n_obs > n_voxels ? n_obs : n_voxels;
   if (peak_extra)
-    *peak_extra = (80 + 4 + 8 + (precision == BA_MIXED ? 16 * kVe32 : 0)) * n_obs + 16 * nsort + 24 * nsort / 16 +
-                  (8 + 16 + 8 + 8) * (int64_t)n_voxels;
+    *peak_extra = (80 + 4 + 8 + (precision == BA_MIXED ? 16 * kVe32 + 4 + 12 + 2 : 0)) * n_obs + 16 * nsort +
+                  24 * nsort / 16 + (8 + 16 + 8 + 8) * (int64_t)n_voxels;
   return keep;
 }
 

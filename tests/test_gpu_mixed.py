@@ -214,6 +214,9 @@ def test_pipelined_load_in_several_chunks_equals_device_load(mm):
         a.iterate(2)
         b.iterate(2)
         np.testing.assert_array_equal(a.poses(), b.poses())
+        # the admission estimate still bounds what the handle keeps
+        keep, _ = mm.ba_estimate_bytes(mm.BA_MIXED, s.n_scans, s.n_voxels, s.n_obs)
+        assert a.device_bytes() <= keep
 
 
 def test_pipelined_load_reports_bad_cluster(mm):

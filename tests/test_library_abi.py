@@ -87,7 +87,9 @@ def test_package_does_not_import_the_oracle():
 def test_memory_estimate_is_host_only_and_grows_with_the_problem(built):
     """ba_estimate_bytes (the server's admission figure) needs no device: it
     grows with each size, linearly in the clusters, and its load peak includes
-    the mixed path's input-order slot staging (48 bytes per cluster)."""
+    what a mixed load from host memory adds per cluster: the slot staging (48
+    bytes), the scan-major positions grouped by chunk (4) and that grouping's
+    sort keys, buffers and scratch (14)."""
     import paper_2608_14266_gb300 as mm
     for prec in (mm.BA_FP64, mm.BA_MIXED):
         k0, p0 = mm.ba_estimate_bytes(prec, 100, 10_000, 200_000)
@@ -100,4 +102,4 @@ def test_memory_estimate_is_host_only_and_grows_with_the_problem(built):
         assert abs((k4 - k2) - 2 * (k2 - k0)) <= 1024  # linear in the clusters (200k, 400k, 800k)
     _, p64 = mm.ba_estimate_bytes(mm.BA_FP64, 100, 10_000, 200_000)
     _, pmx = mm.ba_estimate_bytes(mm.BA_MIXED, 100, 10_000, 200_000)
-    assert pmx - p64 == 48 * 200_000
+    assert pmx - p64 == (48 + 4 + 14) * 200_000
