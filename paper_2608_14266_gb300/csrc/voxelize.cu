@@ -405,11 +405,46 @@ __device__ __forceinline__ Piece piece_load_counted(const double* o) {
   return P;
 }
 
+// A block's items taken in order of a small key (0 .. 31; a counting sort in
+// shared memory): returns the block-local index of the item this thread
+// takes, so that items of equal key sit side by side and a warp's lanes run
+// loops of about equal length (a GB300 FP64 warp instruction costs its pipe
+// the same whatever the number of active lanes).  Every thread of the block
+// must call it; the order among equal keys is immaterial to the results.
+constexpr int kOrderBlock = 256;
+__device__ __forceinline__ int block_order_by_key(int key, int* s_cnt, int* s_order) {
+  const int tid = threadIdx.x;
+  if (tid < 32) s_cnt[tid] = 0;
+  __syncthreads();
+  const int r = atomicAdd(&s_cnt[key], 1);
+  __syncthreads();
+  if (tid < 32) {  // exclusive prefix over the 32 keys
+    const int v = s_cnt[tid];
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (tid >= o) incl += y;
+    }
+    s_cnt[tid] = incl - v;
+  }
+  __syncthreads();
+  s_order[s_cnt[key] + r] = tid;
+  __syncthreads();
+  return s_order[tid];
+}
+
 // L1 clusters, pass 2 (per run): the head piece merged in order with the
-// carries of the chunks the run covers, then the centred cluster
-__global__ void l1_finish_kernel(int64_t n1, const int64_t* start, const double* head_piece, const double* carry,
-                                 double* c) {
-  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+// carries of the chunks the run covers, then the centred cluster; a block's
+// 256 runs are taken in order of their carry counts (as in merge_kernel)
+__global__ void __launch_bounds__(kOrderBlock) l1_finish_kernel(int64_t n1, const int64_t* start,
+                                                                const double* head_piece, const double* carry,
+                                                                double* c) {
+  __shared__ int s_cnt[32], s_order[kOrderBlock];
+  const int64_t g0 = (int64_t)blockIdx.x * kOrderBlock + threadIdx.x;
+  const int64_t extra0 = g0 < n1 ? (start[g0 + 1] - 1) / kChunk - start[g0] / kChunk : 0;
+  const int64_t g =
+      (int64_t)blockIdx.x * kOrderBlock + block_order_by_key((int)(extra0 < 31 ? extra0 : 31), s_cnt, s_order);
   if (g >= n1) return;
   Piece acc = piece_load_counted(head_piece + kPieceDoubles * g);
   const int64_t cs = start[g] / kChunk, ce = (start[g + 1] - 1) / kChunk;
@@ -438,12 +473,18 @@ __global__ void gather_keys_kernel(int64_t n, const uint64_t* src, const uint32_
 
 // level-k clusters: the children of each (parent, scan) group merged in
 // order, shifted to the first child's mean (a centred child has a = 0, so
-// its merge is b += S + N dl dl^T, a += N dl)
+// its merge is b += S + N dl dl^T, a += N dl).  A block's 256 groups are
+// taken in order of their child counts, so a warp's lanes merge about as many
+// children each; every group's arithmetic is its own, in order.
 template <typename K>
-__global__ void merge_kernel(int64_t np, const int64_t* start, const uint32_t* vals, const double* child,
-                             const K* pkeys_sorted, const int32_t* cscan, double* c, uint64_t* ckey,
-                             int32_t* oscan) {
-  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(kOrderBlock) merge_kernel(int64_t np, const int64_t* start, const uint32_t* vals,
+                                                            const double* child, const K* pkeys_sorted,
+                                                            const int32_t* cscan, double* c, uint64_t* ckey,
+                                                            int32_t* oscan) {
+  __shared__ int s_cnt[32], s_order[kOrderBlock];
+  const int64_t g0 = (int64_t)blockIdx.x * kOrderBlock + threadIdx.x;
+  const int64_t len0 = g0 < np ? start[g0 + 1] - start[g0] : 0;
+  const int64_t g = (int64_t)blockIdx.x * kOrderBlock + block_order_by_key((int)(len0 < 31 ? len0 : 31), s_cnt, s_order);
   if (g >= np) return;
   const int64_t a = start[g], b = start[g + 1];
   Piece acc;
@@ -903,7 +944,7 @@ ba_status level1(int64_t n, const uint64_t* raw, uint32_t* vals, const int32_t* 
                                                               raw_keys ? raw : nullptr, hp, cr, L.key, L.scan);
   tm.end();
   tm.begin(BA_VOX_CLUSTER_FINISH);
-  l1_finish_kernel<<<blocks_for(n1), 256, 0, st>>>(n1, start, hp, cr, L.c);
+  l1_finish_kernel<<<blocks_for(n1, kOrderBlock), kOrderBlock, 0, st>>>(n1, start, hp, cr, L.c);
   tm.end();
   *launches += 2;
   VCK(cudaGetLastError(), "voxelize clusters");
@@ -948,7 +989,8 @@ ba_status level_up(const Level& ch, Level& P, int32_t n_scans, Buf& tmp, cudaStr
   P.key = tmp.get<uint64_t>(np);
   P.scan = tmp.get<int32_t>(np);
   if (!P.c || !P.key || !P.scan) return vfail(BA_ERR_OOM, "voxelize: out of device memory");
-  merge_kernel<K><<<blocks_for(np), 256, 0, st>>>(np, pst, cv, ch.c, k2, ch.scan, P.c, P.key, P.scan);
+  merge_kernel<K><<<blocks_for(np, kOrderBlock), kOrderBlock, 0, st>>>(np, pst, cv, ch.c, k2, ch.scan, P.c, P.key,
+                                                                       P.scan);
   ++*launches;
   VCK(cudaGetLastError(), "voxelize merge");
   return BA_OK;
@@ -1092,7 +1134,8 @@ ba_status assemble_batches(const L1Ctx& c, int64_t m, const double* c_all, const
   L.key = out.get<uint64_t>(ng);
   L.scan = out.get<int32_t>(ng);
   if (!L.c || !L.key || !L.scan) return vfail(BA_ERR_OOM, "voxelize: out of device memory");
-  merge_kernel<K><<<blocks_for(ng), 256, 0, c.st>>>(ng, start, vals, c_all, keys, scan_all, L.c, L.key, L.scan);
+  merge_kernel<K><<<blocks_for(ng, kOrderBlock), kOrderBlock, 0, c.st>>>(ng, start, vals, c_all, keys, scan_all,
+                                                                          L.c, L.key, L.scan);
   ++*c.launches;
   VCK(cudaGetLastError(), "voxelize merge");
   return BA_OK;
