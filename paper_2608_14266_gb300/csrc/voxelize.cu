@@ -25,6 +25,7 @@
 #include <vector>
 
 #include "../../include/ba.h"
+#include "block_order.cuh"
 #include "mmba_internal.cuh"
 #include "mmba_kernels.h"
 
@@ -403,35 +404,6 @@ __device__ __forceinline__ Piece piece_load_counted(const double* o) {
   Piece P = piece_load(o);
   P.n = (double)__double_as_longlong(P.n);
   return P;
-}
-
-// A block's items taken in order of a small key (0 .. 31; a counting sort in
-// shared memory): returns the block-local index of the item this thread
-// takes, so that items of equal key sit side by side and a warp's lanes run
-// loops of about equal length (a GB300 FP64 warp instruction costs its pipe
-// the same whatever the number of active lanes).  Every thread of the block
-// must call it; the order among equal keys is immaterial to the results.
-constexpr int kOrderBlock = 256;
-__device__ __forceinline__ int block_order_by_key(int key, int* s_cnt, int* s_order) {
-  const int tid = threadIdx.x;
-  if (tid < 32) s_cnt[tid] = 0;
-  __syncthreads();
-  const int r = atomicAdd(&s_cnt[key], 1);
-  __syncthreads();
-  if (tid < 32) {  // exclusive prefix over the 32 keys
-    const int v = s_cnt[tid];
-    int incl = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, incl, o);
-      if (tid >= o) incl += y;
-    }
-    s_cnt[tid] = incl - v;
-  }
-  __syncthreads();
-  s_order[s_cnt[key] + r] = tid;
-  __syncthreads();
-  return s_order[tid];
 }
 
 // L1 clusters, pass 2 (per run): the head piece merged in order with the
