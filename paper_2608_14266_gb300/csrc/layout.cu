@@ -117,12 +117,19 @@ __global__ void __launch_bounds__(kRadixBlock) radix_hist_kernel(const K* keys, 
                                                                  int64_t* hist, int64_t n_tiles) {
   __shared__ int cnt[256];
   cnt[threadIdx.x] = 0;
-  __syncthreads();
   const int64_t base = (int64_t)blockIdx.x * kRadixTile;
+  // every key of the thread loaded before the first count (the loads are then
+  // all in flight at once instead of one per shared-memory atomic)
+  unsigned dig[kRadixItems];
+#pragma unroll
   for (int c = 0; c < kRadixItems; ++c) {
     const int64_t i = base + (int64_t)c * kRadixBlock + threadIdx.x;
-    if (i < n) atomicAdd(&cnt[(unsigned)(keys[i] >> shift) & 255u], 1);
+    dig[c] = i < n ? (unsigned)(keys[i] >> shift) & 255u : 256u;
   }
+  __syncthreads();
+#pragma unroll
+  for (int c = 0; c < kRadixItems; ++c)
+    if (dig[c] < 256u) atomicAdd(&cnt[dig[c]], 1);
   __syncthreads();
   hist[(int64_t)threadIdx.x * n_tiles + blockIdx.x] = cnt[threadIdx.x];
 }
