@@ -186,23 +186,51 @@ __global__ void repack_kernel(int64_t n, const uint64_t* raw, KeyPack p, K* keys
   keys[i] = (K)pack_key(p, ix, iy, iz);
 }
 
-// 1 where a new (key, scan) group starts in sorted order
-template <typename K>
-__device__ __forceinline__ bool group_head(int64_t i, const K* keys, const uint32_t* vals, const int32_t* scan) {
-  return i == 0 || keys[i] != keys[i - 1] || scan[vals[i]] != scan[vals[i - 1]];
-}
-
 // group heads as one 32-bit word per 32 elements (bit k: element 32 w + k
-// starts a group) and the number of heads of each word
+// starts a new (key, scan) group in sorted order) and the number of heads of
+// each word.  A warp makes kHeadWords consecutive words, lane l element l of
+// each, with every load issued before the first comparison; an element's
+// predecessor comes from the lane before (lane 0 loads its own).
+constexpr int kHeadWords = 4;
 template <typename K>
 __global__ void head_mask_kernel(int64_t n, const K* keys, const uint32_t* vals, const int32_t* scan, uint32_t* mask,
                                  int64_t* wcount) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const bool h = i < n && group_head(i, keys, vals, scan);
-  const uint32_t m = __ballot_sync(0xffffffffu, h);
-  if ((threadIdx.x & 31) == 0 && i < n) {
-    mask[i >> 5] = m;
-    wcount[i >> 5] = __popc(m);
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * kHeadWords;
+  K key[kHeadWords], key0[kHeadWords];
+  int32_t sc[kHeadWords], sc0[kHeadWords];
+  uint32_t v[kHeadWords], v0[kHeadWords];
+#pragma unroll
+  for (int k = 0; k < kHeadWords; ++k) {
+    const int64_t i = (w0 + k) * 32 + lane;
+    key[k] = i < n ? keys[i] : (K)0;
+    v[k] = i < n ? vals[i] : 0u;
+    // lane 0: the element before the word
+    const bool pre = lane == 0 && i < n && i > 0;
+    key0[k] = pre ? keys[i - 1] : (K)0;
+    v0[k] = pre ? vals[i - 1] : 0u;
+  }
+#pragma unroll
+  for (int k = 0; k < kHeadWords; ++k) {
+    const int64_t i = (w0 + k) * 32 + lane;
+    sc[k] = i < n ? scan[v[k]] : 0;
+    sc0[k] = (lane == 0 && i < n && i > 0) ? scan[v0[k]] : 0;
+  }
+#pragma unroll
+  for (int k = 0; k < kHeadWords; ++k) {
+    const int64_t i = (w0 + k) * 32 + lane;
+    K pk = __shfl_up_sync(0xffffffffu, key[k], 1);
+    int32_t ps = __shfl_up_sync(0xffffffffu, sc[k], 1);
+    if (lane == 0) {
+      pk = key0[k];
+      ps = sc0[k];
+    }
+    const bool h = i < n && (i == 0 || key[k] != pk || sc[k] != ps);
+    const uint32_t m = __ballot_sync(0xffffffffu, h);
+    if (lane == 0 && i < n) {
+      mask[w0 + k] = m;
+      wcount[w0 + k] = __popc(m);
+    }
   }
 }
 
@@ -833,7 +861,8 @@ ba_status group_starts(int64_t n, const K* keys, const uint32_t* vals, const int
   int64_t* base = tmp.get<int64_t>(nw + 1);
   int64_t* scr = tmp.get<int64_t>(scan_scratch_count(nw + 1));
   if (!mask || !base || !scr) return vfail(BA_ERR_OOM, "voxelize: out of device memory");
-  head_mask_kernel<K><<<blocks_for(n), 256, 0, st>>>(n, keys, vals, scan, mask, base);
+  head_mask_kernel<K><<<blocks_for((nw + kHeadWords - 1) / kHeadWords, 8), 256, 0, st>>>(n, keys, vals, scan, mask,
+                                                                                         base);
   VCK(cudaGetLastError(), "voxelize");
   VCK(cudaMemsetAsync(base + nw, 0, sizeof(int64_t), st), "voxelize");
   VCK(exclusive_scan_i64(base, nw + 1, scr, st, launches), "voxelize");
