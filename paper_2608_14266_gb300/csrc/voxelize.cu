@@ -359,7 +359,7 @@ constexpr int kChunk = 32;  // sorted points per thread
 // divergent stores).  The points reach each thread through shared memory, 8
 // at a time, gathered by its whole warp.
 template <typename K>
-__global__ void __launch_bounds__(128, 4) l1_pieces_kernel(int64_t n, const K* keys, const uint32_t* vals,
+__global__ void __launch_bounds__(128, 5) l1_pieces_kernel(int64_t n, const K* keys, const uint32_t* vals,
                                                         const int32_t* pscan, const double* pts, const int64_t* base,
                                                         const uint32_t* hmask, const uint64_t* raw,
                                                         double* head_piece, double* carry, uint64_t* ckey,
