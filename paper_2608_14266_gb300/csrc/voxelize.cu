@@ -437,7 +437,7 @@ __device__ __forceinline__ Piece piece_load_counted(const double* o) {
 // L1 clusters, pass 2 (per run): the head piece merged in order with the
 // carries of the chunks the run covers, then the centred cluster; a block's
 // 256 runs are taken in order of their carry counts (as in merge_kernel)
-__global__ void __launch_bounds__(kOrderBlock) l1_finish_kernel(int64_t n1, const int64_t* start,
+__global__ void __launch_bounds__(kOrderBlock, 3) l1_finish_kernel(int64_t n1, const int64_t* start,
                                                                 const double* head_piece, const double* carry,
                                                                 double* c) {
   __shared__ int s_cnt[32], s_order[kOrderBlock];
